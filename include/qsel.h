@@ -1,0 +1,206 @@
+/*
+ * qsel.h -- C ABI of the GB300 selected-inversion library.
+ *
+ * The library computes the marginal variances diag(Q^-1) and the log-determinant
+ * gradients tr(Q^-1 dQ/dtheta_j) of the posterior precision of a space-time
+ * latent Gaussian model (Zhumekenov, Krainski, Rue, "Parallel selected
+ * inversion for space-time Gaussian Markov random fields", Section 1 and
+ * Section 2.3, Eq. lgm:4) with the overlapping Rao-Blackwellized Monte Carlo
+ * estimator of Section 3.2.3 (Algorithm 4) and the trace estimator of
+ * Section 3.4.2 (Eq. hyperpar:4):
+ *
+ *   Q = tau (Q_t (x) Q_s) + A^T A / sigma^2,
+ *   Q_s = (kappa^2 C + G) C^-1 (kappa^2 C + G)      (Section 2.1, alpha = 2),
+ *   Q_t = unit-marginal-variance AR(1) precision     (Section 2.2, separable),
+ *   theta = (log kappa, log tau, logit rho).
+ *
+ * Nodes are ordered space-fastest: global index = t * n_s + i for time slab t
+ * and spatial node i (Section 2.2, Eq. spde:7).  Q is block tridiagonal in
+ * time with n_s x n_s blocks.
+ *
+ * Pipeline run by qsel_diag_inv (all on the GPU, stream-ordered):
+ *   1. perturbation right-hand sides r = F^T z1 + A^T z2 / sigma from
+ *      Philox4x32-10 noise (Sections 2.4 and 3.3),
+ *   2. one multi-right-hand-side preconditioned conjugate-gradient solve
+ *      Q X = R for all samples at once (Section 3.3),
+ *   3. per overlapping time subdomain Omega_p^*: exact block-tridiagonal
+ *      factorisation and Takahashi selected inversion (Section 3.2.3),
+ *   4. the Rao-Blackwell correction w = Q_{**}^-1 Q_{*S} x_S and its squares
+ *      (Algorithm 4), restricted to Omega_p.
+ *
+ * Conventions
+ *   - Every function returns a qsel_status; QSEL_OK is 0.  Nothing aborts,
+ *     traps or exits.  A failed call leaves a message in qsel_last_error().
+ *   - The caller owns every input and output buffer.  Inputs are copied at
+ *     qsel_create; the context owns all device memory it allocates.
+ *   - Work is issued on the CUDA stream given in qsel_options (NULL = the
+ *     legacy default stream); every call returns after the stream has reached
+ *     the end of its work (results are ready on return).
+ *   - One context must not be used from two threads at the same time.
+ *   - A CUDA error inside a call is reported as QSEL_ECUDA; the context must
+ *     then be destroyed.
+ */
+#ifndef QSEL_H
+#define QSEL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qsel_ctx qsel_ctx;
+
+typedef enum {
+  QSEL_OK = 0,
+  QSEL_EINVAL = 1,    /* invalid argument (shape, pointer, partition, option)   */
+  QSEL_ENOMEM = 2,    /* device or host allocation failed                       */
+  QSEL_ECUDA = 3,     /* CUDA runtime or launch error                            */
+  QSEL_ENOTSPD = 4,   /* a pivot of a dense factorisation was not positive       */
+  QSEL_ENOCONV = 5,   /* the conjugate-gradient solve hit pcg_max_iter           */
+  QSEL_ETIMEOUT = 6,  /* reserved: a bounded device-side wait gave up            */
+  QSEL_ESTATE = 7     /* call not valid in the context's current state           */
+} qsel_status;
+
+/* Arithmetic of the pipeline. */
+enum {
+  QSEL_FP64 = 0,      /* every kernel computes in IEEE binary64                  */
+  QSEL_MIXED = 1      /* binary32 solves and factorisations, binary64 pivots,
+                         refinement residuals and accumulators                    */
+};
+
+/*
+ * Model inputs (Sections 2.1-2.3).  All pointers are HOST pointers, read
+ * during qsel_create only.
+ *   n_s, n_t       spatial nodes and time slabs, n = n_s * n_t.
+ *   c_diag[n_s]    lumped mass matrix C (strictly positive).
+ *   g_rowptr[n_s+1], g_col[nnz], g_val[nnz]
+ *                  stiffness G in CSR, full symmetric pattern, 0-based.
+ *   obs_mask[n]    1 where node t*n_s+i is observed (A selects these), else 0.
+ *   sigma          observation standard deviation (Q_y = I / sigma^2), > 0.
+ */
+typedef struct {
+  int32_t n_s, n_t;
+  const double *c_diag;
+  const int32_t *g_rowptr;
+  const int32_t *g_col;
+  const double *g_val;
+  const uint8_t *obs_mask;
+  double sigma;
+} qsel_model;
+
+/* Hyperparameters: kappa = exp(log_kappa), tau = exp(log_tau),
+ * rho = 1 / (1 + exp(-logit_rho)). */
+typedef struct {
+  double log_kappa, log_tau, logit_rho;
+} qsel_theta;
+
+/*
+ * Non-overlapping time partition Omega_p = slabs [slab_start[p], slab_start[p+1])
+ * (Section 3.2.2; Section 4 partitions in time).  slab_start is a HOST array of
+ * n_parts + 1 strictly increasing offsets from 0 to n_t, or NULL for the
+ * balanced partition (the first n_t mod n_parts parts get one more slab).
+ */
+typedef struct {
+  int32_t n_parts;
+  const int32_t *slab_start;
+} qsel_partition;
+
+typedef struct {
+  int32_t n_samples;      /* k >= 1: RBMC samples (columns of the PCG solve)       */
+  uint64_t seed;          /* Philox key for the perturbation noise                 */
+  int32_t precision;      /* QSEL_FP64 or QSEL_MIXED                               */
+  double pcg_tol;         /* per-column stop: ||b_c - Q x_c|| <= tol ||b_c||        */
+  int32_t pcg_max_iter;   /* > 0                                                   */
+  int32_t precond_block;  /* block-Jacobi block size: 1 (Jacobi), 16, 32 or 64;
+                             0 = library default                                   */
+  int32_t control_variate;/* reserved, must be 0                                    */
+  void *cuda_stream;      /* cudaStream_t, or NULL for the legacy default stream   */
+} qsel_options;
+
+/* Per-call statistics of the last qsel_diag_inv. */
+typedef struct {
+  int32_t pcg_iterations;     /* iterations until every column met pcg_tol         */
+  double pcg_max_rel_residual;/* max over columns of ||b - Q x|| / ||b|| at exit   */
+  double ms_rhs;              /* device time of each phase, milliseconds           */
+  double ms_pcg;
+  double ms_factor;           /* forward block factorisation (all subdomains)      */
+  double ms_takahashi;        /* backward selected inversion (all subdomains)      */
+  double ms_correction;       /* RB correction sweeps, squares and trace forms     */
+  double ms_total;
+  int64_t kernel_launches;    /* kernels this library launched in the call         */
+} qsel_stats_t;
+
+/*
+ * Create a context: validate and copy the model, build the Q_s sparsity
+ * pattern and the partition (Omega_p extended by `overlap` slabs on each
+ * side, clipped to [0, n_t); separators are the slabs just outside,
+ * Algorithm 3), and allocate device memory.  No estimator work runs yet.
+ *   out        receives the context (set to NULL on failure).
+ *   overlap    n_l >= 0 slabs.
+ * Errors: QSEL_EINVAL (shapes, mesh, mask, partition, options),
+ *         QSEL_ENOMEM, QSEL_ECUDA.
+ */
+qsel_status qsel_create(qsel_ctx **out, const qsel_model *model, const qsel_theta *theta,
+                        const qsel_partition *partition, int32_t overlap,
+                        const qsel_options *opt);
+
+/* Replace theta (structure, partition and options are kept).  The next
+ * qsel_diag_inv / qsel_trace_grads recompute everything.  QSEL_EINVAL for
+ * non-finite values or rho outside (0, 1). */
+qsel_status qsel_set_theta(qsel_ctx *ctx, const qsel_theta *theta);
+
+/*
+ * Run the pipeline (if not already run for the current theta) and write the
+ * RBMC estimate of diag(Q^-1) (Algorithm 4): n doubles in global node order.
+ *   diag_out       caller-allocated, n doubles; HOST memory if out_is_device
+ *                  is 0, DEVICE memory of the context's GPU otherwise.
+ * Errors: QSEL_EINVAL (NULL), QSEL_ENOTSPD, QSEL_ENOCONV, QSEL_ECUDA.
+ */
+qsel_status qsel_diag_inv(qsel_ctx *ctx, double *diag_out, int32_t out_is_device);
+
+/*
+ * RBMC estimate of tr(Q^-1 dQ/dtheta_j) for theta = (log kappa, log tau,
+ * logit rho), by Eq. hyperpar:4: over rows of Omega_p and columns of
+ * Omega_p^*, the selected entries Sigma*_il + (1/k) sum_s w_i w_l times
+ * (dQ_j)_il.  Runs the pipeline if needed.  grads_out: 3 HOST doubles.
+ * Requires overlap >= 1 or a single part (QSEL_EINVAL otherwise): with no
+ * overlap the neighbours of the rows of Omega_p would lie in the separator.
+ */
+qsel_status qsel_trace_grads(qsel_ctx *ctx, double grads_out[3]);
+
+/* Statistics of the last pipeline run. */
+qsel_status qsel_stats(const qsel_ctx *ctx, qsel_stats_t *stats);
+
+/*
+ * Stage-wise checking hooks.
+ *
+ * qsel_debug_set_samples: use X (HOST, n rows x n_samples columns, row-major
+ *   with leading dimension ld >= n_samples) as the global samples instead of
+ *   running steps 1-2; only the separator slabs are read.  Stays in effect
+ *   until qsel_set_theta.
+ * qsel_debug_get_samples: copy the samples of the last run to X (HOST, same
+ *   layout).
+ * qsel_debug_get_rhs: copy the perturbation right-hand sides R of the last
+ *   run (HOST, same layout).  QSEL_ESTATE if the samples were injected.
+ * qsel_debug_get_selinv_diag: copy diag(Q_{Omega_p^* Omega_p^*}^-1) restricted
+ *   to the rows of Omega_p, for every p, in global node order (HOST, n doubles):
+ *   the exact subdomain selected inverse before the correction.
+ */
+qsel_status qsel_debug_set_samples(qsel_ctx *ctx, const double *X, int32_t ld);
+qsel_status qsel_debug_get_samples(const qsel_ctx *ctx, double *X, int32_t ld);
+qsel_status qsel_debug_get_rhs(const qsel_ctx *ctx, double *R, int32_t ld);
+qsel_status qsel_debug_get_selinv_diag(const qsel_ctx *ctx, double *diag_out);
+
+/* Message of the last failed call on ctx (or of the last failed qsel_create
+ * when ctx is NULL).  Never NULL; owned by the library. */
+const char *qsel_last_error(const qsel_ctx *ctx);
+
+/* Free the context and its device memory.  NULL is allowed. */
+void qsel_destroy(qsel_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSEL_H */

@@ -1,0 +1,8 @@
+"""GB300-native overlapping RBMC selected inversion (diag(Q^-1) and log-det
+gradients of space-time SPDE precisions).  The compute path is the CUDA
+library libqsel.so (C ABI in include/qsel.h); ``qsel`` is its thin binding."""
+from . import qsel  # noqa: F401
+from .qsel import (QSEL_FP64, QSEL_MIXED, Context, QselError, load_library,  # noqa: F401
+                   qsel_create, qsel_debug_get_rhs, qsel_debug_get_samples,
+                   qsel_debug_get_selinv_diag, qsel_debug_set_samples, qsel_destroy,
+                   qsel_diag_inv, qsel_last_error, qsel_set_theta, qsel_stats, qsel_trace_grads)

@@ -1,0 +1,444 @@
+// Dense FP64 kernels of the exact subdomain selected inversion.
+//
+// Per overlapping subdomain Omega_p^* (T slabs), Q_{**} is block tridiagonal
+// with diagonal blocks A_tt = a0_t Q_s + diag(obs_t)/sigma^2 and couplings
+// A_{t+1,t} = c_t Q_s (c_t = tau Q_t[t,t+1]).  The block factorisation keeps
+// the pivot blocks D_t (block LDL^T; D_t = L_tt L_tt^T of the block Cholesky):
+//   D_0 = A_00,  D_{t+1} = A_{t+1,t+1} - c_t^2 Q_s D_t^-1 Q_s,
+// and the Takahashi recursion runs backwards with W_t = c_t Q_s D_t^-1
+// (= L_{t+1,t} L_tt^-1):
+//   Sigma_{T-1} = D_{T-1}^-1,
+//   Y_t = Sigma_{t+1} W_t,  Sigma_{t+1,t} = -Y_t,
+//   Sigma_t = D_t^-1 + W_t^T Y_t = D_t^-1 + D_t^-1 (c_t Q_s Y_t).
+// Because the couplings are sparse (the Q_s pattern), only the D_t^-1, the
+// Sigma_{t+1} W_t and the D_t^-1 V products are dense n_s^3 work; they run
+// here as 64 x 64 FP64 tiles.  Every dense matrix is n_pad x n_pad row-major
+// (n_pad = n_s rounded up to 64, identity on the padded diagonal).
+#include "kernels.cuh"
+#include "sweep.cuh"
+
+namespace qsel {
+
+// ---------------------------------------------------------------------------
+// 64 x 64 FP64 tile product: acc += op(A) op(B) over K (multiple of 16).
+// 256 threads, thread (ty, tx) owns rows ty + 16 i and columns tx + 16 j.
+// op(A)(r, kk) = TA ? A[kk * lda + r] : A[r * lda + kk]
+// op(B)(kk, c) = TB ? B[c * ldb + kk] : B[kk * ldb + c]
+// ---------------------------------------------------------------------------
+struct TileSmem {
+  double As[2][16][64];
+  double Bs[2][16][64];
+};
+
+template <bool TA, bool TB>
+__device__ __forceinline__ void tile_load(const double *__restrict__ A, int lda,
+                                          const double *__restrict__ B, int ldb, int k0,
+                                          double ra[4], double rb[4]) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int idx = tid + 256 * u;
+    if (TA) {
+      const int kk = idx >> 6, r = idx & 63;
+      ra[u] = A[(int64_t)(k0 + kk) * lda + r];
+    } else {
+      const int r = idx >> 4, kk = idx & 15;
+      ra[u] = A[(int64_t)r * lda + k0 + kk];
+    }
+    if (TB) {
+      const int c = idx >> 4, kk = idx & 15;
+      rb[u] = B[(int64_t)c * ldb + k0 + kk];
+    } else {
+      const int kk = idx >> 6, c = idx & 63;
+      rb[u] = B[(int64_t)(k0 + kk) * ldb + c];
+    }
+  }
+}
+
+template <bool TA, bool TB>
+__device__ __forceinline__ void tile_store(TileSmem &sm, int buf, const double ra[4],
+                                           const double rb[4]) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int idx = tid + 256 * u;
+    if (TA)
+      sm.As[buf][idx >> 6][idx & 63] = ra[u];
+    else
+      sm.As[buf][idx & 15][idx >> 4] = ra[u];
+    if (TB)
+      sm.Bs[buf][idx & 15][idx >> 4] = rb[u];
+    else
+      sm.Bs[buf][idx >> 6][idx & 63] = rb[u];
+  }
+}
+
+template <bool TA, bool TB>
+__device__ __forceinline__ void tile_mma(TileSmem &sm, const double *__restrict__ A, int lda,
+                                         const double *__restrict__ B, int ldb, int K,
+                                         double acc[4][4]) {
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  double ra[4], rb[4];
+  tile_load<TA, TB>(A, lda, B, ldb, 0, ra, rb);
+  tile_store<TA, TB>(sm, 0, ra, rb);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    const bool more = k0 + 16 < K;
+    if (more) tile_load<TA, TB>(A, lda, B, ldb, k0 + 16, ra, rb);
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sm.As[buf][kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = sm.Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    if (more) {
+      tile_store<TA, TB>(sm, buf ^ 1, ra, rb);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Batched GEMM: C = alpha A B + beta C0 (C0 may alias C).
+// ---------------------------------------------------------------------------
+template <bool LOWER>
+__global__ void __launch_bounds__(256) k_gemm64(GemmBatch bt, int K, int lda, int ldb, int ldc) {
+  __shared__ TileSmem sm;
+  const GemmEntry e = bt.e[blockIdx.z];
+  const int bm = blockIdx.y, bn = blockIdx.x;
+  if (LOWER && bn > bm) return;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  tile_mma<false, false>(sm, e.A + (int64_t)bm * 64 * lda, lda, e.B + (int64_t)bn * 64, ldb, K, acc);
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t row = (int64_t)bm * 64 + ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t idx = row * ldc + bn * 64 + tx + 16 * j;
+      double v = e.alpha * acc[i][j];
+      if (e.beta != 0.0) v = fma(e.beta, e.C0[idx], v);
+      e.C[idx] = v;
+    }
+  }
+}
+
+void launch_gemm(cudaStream_t s, const GemmBatch &b, int M, int N, int K, int lda, int ldb, int ldc,
+                 bool lower) {
+  if (b.count <= 0) return;
+  ++g_launch_count;
+  dim3 grid(N / 64, M / 64, b.count);
+  if (lower)
+    k_gemm64<true><<<grid, 256, 0, s>>>(b, K, lda, ldb, ldc);
+  else
+    k_gemm64<false><<<grid, 256, 0, s>>>(b, K, lda, ldb, ldc);
+}
+
+// ---------------------------------------------------------------------------
+// Blocked symmetric sweep: in-place SPD inverse on the lower 64 x 64 tiles.
+// Step k with pivot tile P = A_kk^-1:
+//   panel  U_i = A_ik P,  V_i = A_ik            (i != k; A_ik = A_ki^T for i < k)
+//   update A_ij -= U_i V_j^T                     (lower tiles, i, j != k)
+//          A_ik <- U_i,  A_kk <- -P
+// After every step the swept matrix holds -A^-1 (Goodnight's sweep operator);
+// the final mirror negates it and fills the upper triangle.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sweep_pivot(SweepBatch bt, int k, int ld, int32_t *err_flag) {
+  __shared__ double S[64 * 65];
+  const SweepEntry e = bt.e[blockIdx.x];
+  const double *T = e.A + (int64_t)k * 64 * ld + k * 64;
+  for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
+    const int r = idx >> 6, c = idx & 63;
+    // the diagonal tile is kept symmetric; read the lower half only
+    S[r * 65 + c] = (r >= c) ? T[(int64_t)r * ld + c] : T[(int64_t)c * ld + r];
+  }
+  __syncthreads();
+  sym_sweep_inverse_smem(S, 65, 64, err_flag);
+  for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
+    const int r = idx >> 6, c = idx & 63;
+    e.P[idx] = -S[r * 65 + c];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_sweep_panel(SweepBatch bt, int k, int ld) {
+  __shared__ TileSmem sm;
+  const SweepEntry e = bt.e[blockIdx.y];
+  const int i = (int)blockIdx.x < k ? (int)blockIdx.x : (int)blockIdx.x + 1;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  double *U = e.U + (int64_t)i * 64 * 64;
+  double *V = e.V + (int64_t)i * 64 * 64;
+  if (i > k) {
+    const double *C = e.A + (int64_t)i * 64 * ld + k * 64;
+    tile_mma<false, false>(sm, C, ld, e.P, 64, 64, acc);
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) V[idx] = C[(int64_t)(idx >> 6) * ld + (idx & 63)];
+  } else {
+    // A_ik = (A_ki)^T, tile (k, i) is in the lower triangle
+    const double *C = e.A + (int64_t)k * 64 * ld + i * 64;
+    tile_mma<true, false>(sm, C, ld, e.P, 64, 64, acc);
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) V[idx] = C[(int64_t)(idx & 63) * ld + (idx >> 6)];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) U[(ty + 16 * a) * 64 + tx + 16 * b] = acc[a][b];
+}
+
+__global__ void __launch_bounds__(256) k_sweep_update(SweepBatch bt, int k, int nt, int ld) {
+  __shared__ TileSmem sm;
+  const SweepEntry e = bt.e[blockIdx.y];
+  // linear index over lower tiles (i >= j): i = floor((sqrt(8 l + 1) - 1) / 2)
+  const int l = blockIdx.x;
+  int i = (int)((sqrt(8.0 * l + 1.0) - 1.0) * 0.5);
+  while ((i + 1) * (i + 2) / 2 <= l) ++i;
+  while (i * (i + 1) / 2 > l) --i;
+  const int j = l - i * (i + 1) / 2;
+  double *Tij = e.A + (int64_t)i * 64 * ld + j * 64;
+  if (i == k && j == k) {
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) Tij[(int64_t)(idx >> 6) * ld + (idx & 63)] = -e.P[idx];
+    return;
+  }
+  if (j == k) {  // i > k: A_ik <- U_i
+    const double *U = e.U + (int64_t)i * 4096;
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) Tij[(int64_t)(idx >> 6) * ld + (idx & 63)] = U[idx];
+    return;
+  }
+  if (i == k) {  // j < k: tile (k, j) holds A_kj = A_jk^T <- U_j^T
+    const double *U = e.U + (int64_t)j * 4096;
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) {
+      const int r = idx >> 6, c = idx & 63;
+      Tij[(int64_t)r * ld + c] = U[c * 64 + r];
+    }
+    return;
+  }
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  tile_mma<false, true>(sm, e.U + (int64_t)i * 4096, 64, e.V + (int64_t)j * 4096, 64, 64, acc);
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      double *p = Tij + (int64_t)(ty + 16 * a) * ld + tx + 16 * b;
+      *p -= acc[a][b];
+    }
+  (void)nt;
+}
+
+// A <- sign * A from the lower tiles, mirrored into the upper triangle (after
+// the sweep the lower tiles hold -A^-1, so the sweep mirrors with sign -1).
+__global__ void __launch_bounds__(256) k_sweep_mirror(SweepBatch bt, int ld, double sign) {
+  __shared__ double S[64 * 65];
+  const SweepEntry e = bt.e[blockIdx.y];
+  const int l = blockIdx.x;
+  int i = (int)((sqrt(8.0 * l + 1.0) - 1.0) * 0.5);
+  while ((i + 1) * (i + 2) / 2 <= l) ++i;
+  while (i * (i + 1) / 2 > l) --i;
+  const int j = l - i * (i + 1) / 2;
+  double *Tij = e.A + (int64_t)i * 64 * ld + j * 64;
+  for (int idx = threadIdx.x; idx < 4096; idx += 256) {
+    const int r = idx >> 6, c = idx & 63;
+    S[r * 65 + c] = Tij[(int64_t)r * ld + c];
+  }
+  __syncthreads();
+  if (i == j) {
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) {
+      const int r = idx >> 6, c = idx & 63;
+      Tij[(int64_t)r * ld + c] = sign * ((r >= c) ? S[r * 65 + c] : S[c * 65 + r]);
+    }
+  } else {
+    double *Tji = e.A + (int64_t)j * 64 * ld + i * 64;
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) {
+      const int r = idx >> 6, c = idx & 63;
+      Tij[(int64_t)r * ld + c] = sign * S[r * 65 + c];
+      Tji[(int64_t)r * ld + c] = sign * S[c * 65 + r];
+    }
+  }
+}
+
+void spd_inverse(cudaStream_t s, const SweepBatch &b, int n_pad, int32_t *err_flag) {
+  if (b.count <= 0) return;
+  const int nt = n_pad / 64;
+  const int n_lower = nt * (nt + 1) / 2;
+  for (int k = 0; k < nt; ++k) {
+    g_launch_count += 3;
+    k_sweep_pivot<<<b.count, 256, 0, s>>>(b, k, n_pad, err_flag);
+    if (nt > 1) k_sweep_panel<<<dim3(nt - 1, b.count), 256, 0, s>>>(b, k, n_pad);
+    k_sweep_update<<<dim3(n_lower, b.count), 256, 0, s>>>(b, k, nt, n_pad);
+  }
+  ++g_launch_count;
+  k_sweep_mirror<<<dim3(n_lower, b.count), 256, 0, s>>>(b, n_pad, -1.0);
+}
+
+void launch_mirror(cudaStream_t s, const SweepBatch &b, int n_pad) {
+  if (b.count <= 0) return;
+  const int nt = n_pad / 64;
+  ++g_launch_count;
+  k_sweep_mirror<<<dim3(nt * (nt + 1) / 2, b.count), 256, 0, s>>>(b, n_pad, 1.0);
+}
+
+// ---------------------------------------------------------------------------
+// Out = alpha Q_s B + beta C on the spatial pattern (row gather): one warp per
+// (row, 128-column chunk), warp-uniform pattern entries, double2 lanes.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sp_rowgather(SpBatch bt, SellPattern pat,
+                                                      const double *__restrict__ val, int n_s,
+                                                      int n_pad, int ncol, int ld) {
+  const SpEntry e = bt.e[blockIdx.y];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nch = ncol / 64;
+  const double alpha = e.alpha * (e.alpha_ptr ? *e.alpha_ptr : 1.0);
+  const int64_t items = (int64_t)n_pad * nch;
+  for (int64_t it = (int64_t)blockIdx.x * 8 + warp; it < items; it += (int64_t)gridDim.x * 8) {
+    const int row = (int)(it / nch);
+    const int col = (int)(it - (int64_t)row * nch) * 64 + 2 * lane;
+    double2 acc = make_double2(0.0, 0.0);
+    if (row < n_s) {
+      const int sl = row >> 5, li = row & 31;
+      const int w = pat.slice_width[sl];
+      const int base = pat.slice_ptr[sl] + li;
+      for (int s = 0; s < w; ++s) {
+        const int j = pat.col[base + s * kSlice];
+        const double v = val[base + s * kSlice];
+        const double2 bv = *reinterpret_cast<const double2 *>(e.B + (int64_t)j * ld + col);
+        acc.x = fma(v, bv.x, acc.x);
+        acc.y = fma(v, bv.y, acc.y);
+      }
+    }
+    acc.x *= alpha;
+    acc.y *= alpha;
+    const int64_t idx = (int64_t)row * ld + col;
+    if (e.C != nullptr && e.beta != 0.0) {
+      const double2 cv = *reinterpret_cast<const double2 *>(e.C + idx);
+      acc.x = fma(e.beta, cv.x, acc.x);
+      acc.y = fma(e.beta, cv.y, acc.y);
+    }
+    *reinterpret_cast<double2 *>(e.Out + idx) = acc;
+  }
+}
+
+void launch_sp_rowgather(cudaStream_t s, const SpBatch &b, const SellPattern &pat, const double *val,
+                         int n_s, int n_pad, int ncol, int ld) {
+  if (b.count <= 0) return;
+  ++g_launch_count;
+  int64_t items = (int64_t)n_pad * (ncol / 64);
+  int grid = (int)((items + 7) / 8);
+  if (grid > 152 * 8) grid = 152 * 8;
+  k_sp_rowgather<<<dim3(grid, b.count), 256, 0, s>>>(b, pat, val, n_s, n_pad, ncol, ld);
+}
+
+// ---------------------------------------------------------------------------
+// D = a0 Q_s + w_obs diag(obs) - c W Q_s (column gather over the symmetric
+// pattern: (W Q_s)[r, l] = sum_{j in pat(l)} W[r, j] Q_s[l, j]).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch bt, SellPattern pat,
+                                                        const double *__restrict__ qs, double obs_w,
+                                                        int n_s, int n_pad) {
+  const SchurEntry e = bt.e[blockIdx.z];
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (l >= n_pad) return;
+  double out;
+  if (r < n_s && l < n_s) {
+    const int sl = l >> 5, li = l & 31;
+    const int w = pat.slice_width[sl];
+    const int base = pat.slice_ptr[sl] + li;
+    double acc = 0.0, aq = 0.0;
+    const double *Wr = e.W ? e.W + (int64_t)r * n_pad : nullptr;
+    for (int s = 0; s < w; ++s) {
+      const int j = pat.col[base + s * kSlice];
+      const double v = qs[base + s * kSlice];
+      if (Wr) acc = fma(Wr[j], v, acc);
+      if (j == r) aq += v;
+    }
+    out = (*e.a0) * aq;
+    if (r == l && e.obs[r]) out += obs_w;
+    if (Wr) out -= (*e.c) * acc;
+  } else {
+    out = (r == l) ? 1.0 : 0.0;
+  }
+  e.D[(int64_t)r * n_pad + l] = out;
+}
+
+void launch_schur_assemble(cudaStream_t s, const SchurBatch &b, const SellPattern &pat,
+                           const double *qs, double obs_w, int n_s, int n_pad) {
+  if (b.count <= 0) return;
+  ++g_launch_count;
+  dim3 grid((n_pad + 255) / 256, n_pad, b.count);
+  k_schur_assemble<<<grid, 256, 0, s>>>(b, pat, qs, obs_w, n_s, n_pad);
+}
+
+// ---------------------------------------------------------------------------
+// diag(S) and the pattern inner products <dQ_s, S>, <Q_s, S> (one block per
+// entry, fixed reduction order).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_extract(ExtractBatch bt, SellPattern pat,
+                                                  const double *__restrict__ qs,
+                                                  const double *__restrict__ dqs, int n_s, int n_pad) {
+  __shared__ double red0[32], red1[32];
+  const ExtractEntry e = bt.e[blockIdx.x];
+  double s0 = 0.0, s1 = 0.0;
+  for (int i = threadIdx.x; i < n_s; i += blockDim.x) {
+    const double *Si = e.S + (int64_t)i * n_pad;
+    if (e.diag_out) e.diag_out[i] = Si[i];
+    if (e.sums) {
+      const int sl = i >> 5, li = i & 31;
+      const int w = pat.slice_width[sl];
+      const int base = pat.slice_ptr[sl] + li;
+      for (int s = 0; s < w; ++s) {
+        const int j = pat.col[base + s * kSlice];
+        const double sv = Si[j];
+        s0 = fma(dqs[base + s * kSlice], sv, s0);
+        s1 = fma(qs[base + s * kSlice], sv, s1);
+      }
+    }
+  }
+  if (!e.sums) return;
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red0[threadIdx.x >> 5] = s0;
+    red1[threadIdx.x >> 5] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += red0[w];
+      b += red1[w];
+    }
+    e.sums[0] = a;
+    e.sums[1] = b;
+  }
+}
+
+void launch_extract(cudaStream_t s, const ExtractBatch &b, const SellPattern &pat, const double *qs,
+                    const double *dqs, int n_s, int n_pad) {
+  if (b.count <= 0) return;
+  ++g_launch_count;
+  k_extract<<<b.count, 1024, 0, s>>>(b, pat, qs, dqs, n_s, n_pad);
+}
+
+}  // namespace qsel

@@ -1,0 +1,180 @@
+// Rao-Blackwell correction terms of the overlapping RBMC estimator
+// (Section 3.2.3, Algorithm 4) and the trace estimator (Section 3.4.2,
+// Eq. hyperpar:4).
+//
+// For subdomain p with local slabs 0..T-1 (global e0 + tau) and own slabs
+// [lo, hi], the correction samples w = Q_{**}^-1 Q_{*S} x_S are given
+// (T x n_pad x ld, zero beyond n_s rows / k columns).  For every own row i of
+// slab tau this kernel adds
+//   diag:   (1/k) sum_s w_i^2
+//   traces: (1/k) sum_s w_i (dQ_j w)_i,
+// with dQ_j block (t, t+d) = e_j(t, d) M_j on the spatial pattern:
+//   j = 0: M = dQ_s/dlog kappa, e = tau Q_t;        j = 1: M = Q_s, e = tau Q_t;
+//   j = 2: M = Q_s, e = tau rho (1 - rho) dQ_t/drho.
+#include "kernels.cuh"
+
+namespace qsel {
+
+constexpr int kCorrGrid = 152 * 2;
+
+int corr_grid() { return kCorrGrid; }
+
+__global__ void __launch_bounds__(256) k_correction_terms(CorrBatch bt, SellPattern pat,
+                                                          const double *__restrict__ qs,
+                                                          const double *__restrict__ dqs,
+                                                          const double *__restrict__ a0,
+                                                          const double *__restrict__ a1,
+                                                          const double *__restrict__ r0,
+                                                          const double *__restrict__ r1, int n_s,
+                                                          int n_pad, int ld, int k) {
+  __shared__ double red[8][3];
+  const CorrEntry e = bt.e[blockIdx.y];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double inv_k = 1.0 / (double)k;
+  const int n_own = (e.hi - e.lo + 1) * n_s;
+  const int64_t slab = (int64_t)n_pad * ld;
+  double tr0 = 0.0, tr1 = 0.0, tr2 = 0.0;
+  for (int item = blockIdx.x * 8 + warp; item < n_own; item += gridDim.x * 8) {
+    const int tl = e.lo + item / n_s;      // local slab
+    const int i = item - (item / n_s) * n_s;
+    const int t = e.e0 + tl;               // global slab
+    const bool has_m = tl > 0, has_p = tl + 1 < e.T;
+    const double ea[3] = {has_m ? a1[t - 1] : 0.0, a0[t], has_p ? a1[t] : 0.0};
+    const double er[3] = {has_m ? r1[t - 1] : 0.0, r0[t], has_p ? r1[t] : 0.0};
+    const int sl = i >> 5, li = i & 31;
+    const int w = pat.slice_width[sl];
+    const int base = pat.slice_ptr[sl] + li;
+    const double *wrow = e.w + tl * slab + (int64_t)i * ld;
+    double sq = 0.0, p0 = 0.0, p1 = 0.0, p2 = 0.0;
+    for (int c = lane; c < ld; c += 32) {
+      double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+      for (int s = 0; s < w; ++s) {
+        const int j = pat.col[base + s * kSlice];
+        const double vq = qs[base + s * kSlice], vd = dqs[base + s * kSlice];
+        const double *wc = e.w + tl * slab + (int64_t)j * ld + c;
+        const double x0 = wc[0];
+        const double xm = has_m ? wc[-slab] : 0.0;
+        const double xp = has_p ? wc[slab] : 0.0;
+        const double za = ea[0] * xm + ea[1] * x0 + ea[2] * xp;
+        const double zr = er[0] * xm + er[1] * x0 + er[2] * xp;
+        g0 = fma(vd, za, g0);
+        g1 = fma(vq, za, g1);
+        g2 = fma(vq, zr, g2);
+      }
+      const double wi = wrow[c];
+      sq = fma(wi, wi, sq);
+      p0 = fma(wi, g0, p0);
+      p1 = fma(wi, g1, p1);
+      p2 = fma(wi, g2, p2);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sq += __shfl_down_sync(0xffffffffu, sq, o);
+      p0 += __shfl_down_sync(0xffffffffu, p0, o);
+      p1 += __shfl_down_sync(0xffffffffu, p1, o);
+      p2 += __shfl_down_sync(0xffffffffu, p2, o);
+    }
+    if (lane == 0) {
+      e.diag_out[(int64_t)t * n_s + i] += sq * inv_k;
+      tr0 += p0;
+      tr1 += p1;
+      tr2 += p2;
+    }
+  }
+  if (lane == 0) {
+    red[warp][0] = tr0;
+    red[warp][1] = tr1;
+    red[warp][2] = tr2;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int ww = 0; ww < 8; ++ww) s += red[ww][threadIdx.x];
+    e.partial[blockIdx.x * 3 + threadIdx.x] = s * inv_k;
+  }
+}
+
+void launch_correction_terms(cudaStream_t s, const CorrBatch &b, const SellPattern &pat,
+                             const double *qs, const double *dqs, const double *a0, const double *a1,
+                             const double *r0, const double *r1, int n_s, int n_pad, int ld, int k) {
+  if (b.count <= 0) return;
+  ++g_launch_count;
+  k_correction_terms<<<dim3(kCorrGrid, b.count), 256, 0, s>>>(b, pat, qs, dqs, a0, a1, r0, r1, n_s,
+                                                              n_pad, ld, k);
+}
+
+// tr_j = sum over own row slabs t of
+//   e_j(t,0) <M_j, Sigma_tt> - e_j(t,+1) <M_j, Y_t> - e_j(t,-1) <M_j, Y_{t-1}>
+// (Sigma_{t,t+1} = -Y_t^T, Sigma_{t,t-1} = -Y_{t-1}, M_j symmetric) plus the
+// correction partials.  One thread, fixed order.
+__global__ void k_trace_combine(const TraceSlab *__restrict__ slabs, int n_slabs,
+                                const double *__restrict__ sums, const double *__restrict__ partials,
+                                int n_partials, const double *__restrict__ a0,
+                                const double *__restrict__ a1, const double *__restrict__ r0,
+                                const double *__restrict__ r1, double *out3) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+  for (int q = 0; q < n_slabs; ++q) {
+    const TraceSlab sl = slabs[q];
+    const int t = sl.t;
+    const double *sd = sums + 2 * sl.sd;
+    t0 += a0[t] * sd[0];
+    t1 += a0[t] * sd[1];
+    t2 += r0[t] * sd[1];
+    if (sl.sy >= 0) {
+      const double *sy = sums + 2 * sl.sy;
+      t0 -= a1[t] * sy[0];
+      t1 -= a1[t] * sy[1];
+      t2 -= r1[t] * sy[1];
+    }
+    if (sl.sym >= 0) {
+      const double *sy = sums + 2 * sl.sym;
+      t0 -= a1[t - 1] * sy[0];
+      t1 -= a1[t - 1] * sy[1];
+      t2 -= r1[t - 1] * sy[1];
+    }
+  }
+  for (int q = 0; q < n_partials; ++q) {
+    t0 += partials[3 * q + 0];
+    t1 += partials[3 * q + 1];
+    t2 += partials[3 * q + 2];
+  }
+  out3[0] = t0;
+  out3[1] = t1;
+  out3[2] = t2;
+}
+
+void launch_trace_combine(cudaStream_t s, const TraceSlab *slabs_dev, int n_slabs, const double *sums,
+                          const double *partials, int n_partials, const double *a0, const double *a1,
+                          const double *r0, const double *r1, double *out3) {
+  ++g_launch_count;
+  k_trace_combine<<<1, 32, 0, s>>>(slabs_dev, n_slabs, sums, partials, n_partials, a0, a1, r0, r1,
+                                   out3);
+}
+
+__global__ void k_add(double *__restrict__ y, const double *__restrict__ x, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] += x[i];
+}
+
+void launch_add(cudaStream_t s, double *y, const double *x, int n) {
+  if (n <= 0) return;
+  ++g_launch_count;
+  int grid = (n + 255) / 256;
+  if (grid > 152 * 8) grid = 152 * 8;
+  k_add<<<grid, 256, 0, s>>>(y, x, n);
+}
+
+__global__ void k_scale_copy(double *__restrict__ dst, const double *__restrict__ src, int n,
+                             double scale) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] = scale * src[i];
+}
+
+void launch_scale_copy(cudaStream_t s, double *dst, const double *src, int n, double scale) {
+  if (n <= 0) return;
+  ++g_launch_count;
+  int grid = (n + 255) / 256;
+  if (grid > 152 * 8) grid = 152 * 8;
+  k_scale_copy<<<grid, 256, 0, s>>>(dst, src, n, scale);
+}
+
+}  // namespace qsel

@@ -1,0 +1,220 @@
+"""ctypes binding of the C ABI in include/qsel.h (argument marshalling only).
+
+Every computation happens in libqsel.so.  The functions keep the C names;
+``Context`` wraps an opaque ``qsel_ctx*`` and owns it.  Loading fails loudly
+when the library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_uint8, c_uint64, c_void_p
+
+import numpy as np
+
+QSEL_FP64 = 0
+QSEL_MIXED = 1
+
+_STATUS = {0: "QSEL_OK", 1: "QSEL_EINVAL", 2: "QSEL_ENOMEM", 3: "QSEL_ECUDA", 4: "QSEL_ENOTSPD",
+           5: "QSEL_ENOCONV", 6: "QSEL_ETIMEOUT", 7: "QSEL_ESTATE"}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libqsel.so")
+
+
+class qsel_model(ctypes.Structure):
+    _fields_ = [("n_s", c_int32), ("n_t", c_int32), ("c_diag", POINTER(c_double)),
+                ("g_rowptr", POINTER(c_int32)), ("g_col", POINTER(c_int32)), ("g_val", POINTER(c_double)),
+                ("obs_mask", POINTER(c_uint8)), ("sigma", c_double)]
+
+
+class qsel_theta(ctypes.Structure):
+    _fields_ = [("log_kappa", c_double), ("log_tau", c_double), ("logit_rho", c_double)]
+
+
+class qsel_partition(ctypes.Structure):
+    _fields_ = [("n_parts", c_int32), ("slab_start", POINTER(c_int32))]
+
+
+class qsel_options(ctypes.Structure):
+    _fields_ = [("n_samples", c_int32), ("seed", c_uint64), ("precision", c_int32), ("pcg_tol", c_double),
+                ("pcg_max_iter", c_int32), ("precond_block", c_int32), ("control_variate", c_int32),
+                ("cuda_stream", c_void_p)]
+
+
+class qsel_stats_t(ctypes.Structure):
+    _fields_ = [("pcg_iterations", c_int32), ("pcg_max_rel_residual", c_double), ("ms_rhs", c_double),
+                ("ms_pcg", c_double), ("ms_factor", c_double), ("ms_takahashi", c_double),
+                ("ms_correction", c_double), ("ms_total", c_double), ("kernel_launches", c_int64)]
+
+
+EXPORTED = ["qsel_create", "qsel_set_theta", "qsel_diag_inv", "qsel_trace_grads", "qsel_stats",
+            "qsel_debug_set_samples", "qsel_debug_get_samples", "qsel_debug_get_rhs",
+            "qsel_debug_get_selinv_diag", "qsel_last_error", "qsel_destroy"]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libqsel.so (raises if it is missing; nothing runs without it)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2309_05435_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = POINTER
+    lib.qsel_create.argtypes = [P(c_void_p), P(qsel_model), P(qsel_theta), P(qsel_partition), c_int32,
+                                P(qsel_options)]
+    lib.qsel_set_theta.argtypes = [c_void_p, P(qsel_theta)]
+    lib.qsel_diag_inv.argtypes = [c_void_p, c_void_p, c_int32]
+    lib.qsel_trace_grads.argtypes = [c_void_p, P(c_double)]
+    lib.qsel_stats.argtypes = [c_void_p, P(qsel_stats_t)]
+    lib.qsel_debug_set_samples.argtypes = [c_void_p, P(c_double), c_int32]
+    lib.qsel_debug_get_samples.argtypes = [c_void_p, P(c_double), c_int32]
+    lib.qsel_debug_get_rhs.argtypes = [c_void_p, P(c_double), c_int32]
+    lib.qsel_debug_get_selinv_diag.argtypes = [c_void_p, P(c_double)]
+    lib.qsel_last_error.argtypes = [c_void_p]
+    lib.qsel_last_error.restype = c_char_p
+    lib.qsel_destroy.argtypes = [c_void_p]
+    lib.qsel_destroy.restype = None
+    for name in EXPORTED[:-2]:
+        getattr(lib, name).restype = c_int32
+    _lib = lib
+    return lib
+
+
+class QselError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(POINTER(ctype))
+
+
+def _check(status: int, handle):
+    if status != 0:
+        msg = load_library().qsel_last_error(handle)
+        raise QselError(status, msg.decode() if msg else "")
+
+
+class Context:
+    """Owner of one qsel_ctx*."""
+
+    def __init__(self, handle, n: int, k: int):
+        self.handle = handle
+        self.n = n
+        self.k = k
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().qsel_destroy(self.handle)
+            self.handle = None
+
+    # convenience methods with the same meaning as the free functions
+    def diag_inv(self, out=None):
+        return qsel_diag_inv(self, out)
+
+    def trace_grads(self):
+        return qsel_trace_grads(self)
+
+    def stats(self):
+        return qsel_stats(self)
+
+
+def qsel_create(n_s, n_t, c_diag, g_rowptr, g_col, g_val, obs_mask, sigma, theta, n_parts=1,
+                slab_start=None, overlap=0, n_samples=64, seed=0, precision=QSEL_FP64, pcg_tol=1e-10,
+                pcg_max_iter=20000, precond_block=0, control_variate=0, cuda_stream=None) -> Context:
+    """Create a context from host arrays (copied by the library)."""
+    lib = load_library()
+    c = np.ascontiguousarray(c_diag, dtype=np.float64)
+    rp = np.ascontiguousarray(g_rowptr, dtype=np.int32)
+    gc = np.ascontiguousarray(g_col, dtype=np.int32)
+    gv = np.ascontiguousarray(g_val, dtype=np.float64)
+    mk = np.ascontiguousarray(obs_mask, dtype=np.uint8)
+    model = qsel_model(int(n_s), int(n_t), _ptr(c, c_double), _ptr(rp, c_int32), _ptr(gc, c_int32),
+                       _ptr(gv, c_double), _ptr(mk, c_uint8), float(sigma))
+    th = qsel_theta(*[float(x) for x in theta])
+    ss = None
+    if slab_start is not None:
+        ss = np.ascontiguousarray(slab_start, dtype=np.int32)
+    part = qsel_partition(int(n_parts), _ptr(ss, c_int32) if ss is not None else None)
+    opt = qsel_options(int(n_samples), int(seed), int(precision), float(pcg_tol), int(pcg_max_iter),
+                       int(precond_block), int(control_variate),
+                       c_void_p(int(cuda_stream)) if cuda_stream else None)
+    h = c_void_p()
+    st = lib.qsel_create(ctypes.byref(h), ctypes.byref(model), ctypes.byref(th), ctypes.byref(part),
+                         int(overlap), ctypes.byref(opt))
+    _check(st, None)
+    return Context(h, int(n_s) * int(n_t), int(n_samples))
+
+
+def qsel_set_theta(ctx: Context, theta):
+    th = qsel_theta(*[float(x) for x in theta])
+    _check(load_library().qsel_set_theta(ctx.handle, ctypes.byref(th)), ctx.handle)
+
+
+def qsel_diag_inv(ctx: Context, out=None):
+    """Estimate of diag(Q^-1).  ``out``: None (returns a new numpy array), a
+    float64 numpy array (host), or a CUDA tensor / object with data_ptr()
+    (device, written in place)."""
+    lib = load_library()
+    if out is None:
+        out = np.empty(ctx.n, dtype=np.float64)
+    if isinstance(out, np.ndarray):
+        if out.dtype != np.float64 or out.size != ctx.n or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous float64 array of n entries")
+        _check(lib.qsel_diag_inv(ctx.handle, out.ctypes.data_as(c_void_p), 0), ctx.handle)
+    else:
+        _check(lib.qsel_diag_inv(ctx.handle, c_void_p(out.data_ptr()), 1), ctx.handle)
+    return out
+
+
+def qsel_trace_grads(ctx: Context) -> np.ndarray:
+    g = np.zeros(3, dtype=np.float64)
+    _check(load_library().qsel_trace_grads(ctx.handle, _ptr(g, c_double)), ctx.handle)
+    return g
+
+
+def qsel_stats(ctx: Context) -> dict:
+    s = qsel_stats_t()
+    _check(load_library().qsel_stats(ctx.handle, ctypes.byref(s)), ctx.handle)
+    return {name: getattr(s, name) for name, _ in qsel_stats_t._fields_}
+
+
+def qsel_debug_set_samples(ctx: Context, X: np.ndarray):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    if X.shape != (ctx.n, ctx.k):
+        raise ValueError(f"X must be {(ctx.n, ctx.k)}")
+    _check(load_library().qsel_debug_set_samples(ctx.handle, _ptr(X, c_double), ctx.k), ctx.handle)
+
+
+def qsel_debug_get_samples(ctx: Context) -> np.ndarray:
+    X = np.empty((ctx.n, ctx.k), dtype=np.float64)
+    _check(load_library().qsel_debug_get_samples(ctx.handle, _ptr(X, c_double), ctx.k), ctx.handle)
+    return X
+
+
+def qsel_debug_get_rhs(ctx: Context) -> np.ndarray:
+    R = np.empty((ctx.n, ctx.k), dtype=np.float64)
+    _check(load_library().qsel_debug_get_rhs(ctx.handle, _ptr(R, c_double), ctx.k), ctx.handle)
+    return R
+
+
+def qsel_debug_get_selinv_diag(ctx: Context) -> np.ndarray:
+    d = np.empty(ctx.n, dtype=np.float64)
+    _check(load_library().qsel_debug_get_selinv_diag(ctx.handle, _ptr(d, c_double)), ctx.handle)
+    return d
+
+
+def qsel_last_error(ctx: Context | None) -> str:
+    msg = load_library().qsel_last_error(ctx.handle if ctx is not None else None)
+    return msg.decode() if msg else ""
+
+
+def qsel_destroy(ctx: Context):
+    ctx.close()

@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads, exports every symbol include/qsel.h declares,
+and rejects invalid arguments before touching the GPU (no compute calls)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import qsel_inputs as qi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2309_05435_gb300 import build, qsel
+    build.build()
+    return qsel.load_library()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "qsel.h")).read()
+    decl = r"^(?:qsel_status|void|const char \*)\s*\**(qsel_[a-z_]+)\s*\("
+    return sorted(set(re.findall(decl, text, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2309_05435_gb300 import qsel
+    declared = header_functions()
+    assert len(declared) >= 11
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(qsel.EXPORTED) == declared
+
+
+def _args(**over):
+    w = qi.workload("grid16_nt8")
+    m = w.mesh()
+    a = dict(n_s=w.n_s, n_t=w.n_t, c_diag=m.c_diag, g_rowptr=m.g_rowptr, g_col=m.g_col, g_val=m.g_val,
+             obs_mask=w.mask(), sigma=w.sigma, theta=w.theta, n_parts=2, overlap=1, n_samples=8)
+    a.update(over)
+    return a
+
+
+@pytest.mark.parametrize("bad,msg", [
+    (dict(sigma=0.0), "sigma"),
+    (dict(n_parts=9), "n_parts"),
+    (dict(overlap=-1), "overlap"),
+    (dict(n_samples=0), "n_samples"),
+    (dict(n_samples=513), "n_samples"),
+    (dict(precond_block=8), "precond_block"),
+    (dict(slab_start=[0, 3, 3, 8], n_parts=3), "increasing"),
+    (dict(slab_start=[0, 5, 7], n_parts=2), "0 to n_t"),
+    (dict(theta=(0.0, 0.0, 40.0)), "rho"),
+    (dict(pcg_tol=0.0), "pcg_tol"),
+])
+def test_invalid_arguments_rejected(lib, bad, msg):
+    from paper_2309_05435_gb300 import qsel
+    with pytest.raises(qsel.QselError) as ei:
+        qsel.qsel_create(**_args(**bad))
+    assert ei.value.status == 1 and msg in str(ei.value)
+
+
+def test_invalid_mesh_rejected(lib):
+    from paper_2309_05435_gb300 import qsel
+    a = _args()
+    c = a["c_diag"].copy()
+    c[3] = 0.0
+    with pytest.raises(qsel.QselError, match="c_diag"):
+        qsel.qsel_create(**dict(a, c_diag=c))
+    col = a["g_col"].copy()
+    col[5] = 10 ** 6
+    with pytest.raises(qsel.QselError, match="g_col"):
+        qsel.qsel_create(**dict(a, g_col=col))
