@@ -116,6 +116,9 @@ typedef struct {
                              0 = library default                                   */
   int32_t control_variate;/* reserved, must be 0                                    */
   void *cuda_stream;      /* cudaStream_t, or NULL for the legacy default stream   */
+  int32_t profile_kernels;/* non-zero: time every launch of the dense tile GEMM,
+                             the sweep update and the SpMM with CUDA events on
+                             the stream (reported in qsel_stats_t)                 */
 } qsel_options;
 
 /* Per-call statistics of the last qsel_diag_inv. */
@@ -129,6 +132,15 @@ typedef struct {
   double ms_correction;       /* RB correction sweeps, squares and trace forms     */
   double ms_total;
   int64_t kernel_launches;    /* kernels this library launched in the call         */
+  /* With profile_kernels: summed event time (ms), algorithmic work and launch
+   * count per kernel class.  Work is FLOPs for the dense tile GEMM and the
+   * sweep update, bytes (x read + y written once) for the SpMM. */
+  double gemm_ms, gemm_flop;
+  int64_t gemm_launches;
+  double sweep_ms, sweep_flop;
+  int64_t sweep_launches;
+  double spmm_ms, spmm_bytes;
+  int64_t spmm_launches;
 } qsel_stats_t;
 
 /*

@@ -80,6 +80,7 @@ struct qsel_ctx {
   int32_t *h_counters = nullptr;
   double *h_small = nullptr;
   cudaEvent_t ev[8]{};
+  Profiler prof;
   bool computed = false, injected = false, have_rhs = false;
   qsel_stats_t stats{};
   std::string last_error;
@@ -751,7 +752,39 @@ static Err run_correction(qsel_ctx *c) {
   return ok();
 }
 
+static Err run_pipeline_body(qsel_ctx *c);
+
 static Err run_pipeline(qsel_ctx *c) {
+  if (c->opt.profile_kernels) {
+    c->prof.reset();
+    g_prof = &c->prof;
+  }
+  Err e = run_pipeline_body(c);
+  g_prof = nullptr;
+  if (e.code == 0 && c->opt.profile_kernels) {
+    double ms[PROF_KINDS] = {0, 0, 0}, work[PROF_KINDS] = {0, 0, 0};
+    int64_t cnt[PROF_KINDS] = {0, 0, 0};
+    for (auto &r : c->prof.recs) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, r.a, r.b);
+      ms[r.kind] += t;
+      work[r.kind] += r.work;
+      cnt[r.kind] += 1;
+    }
+    c->stats.gemm_ms = ms[PROF_GEMM];
+    c->stats.gemm_flop = work[PROF_GEMM];
+    c->stats.gemm_launches = cnt[PROF_GEMM];
+    c->stats.sweep_ms = ms[PROF_SWEEP];
+    c->stats.sweep_flop = work[PROF_SWEEP];
+    c->stats.sweep_launches = cnt[PROF_SWEEP];
+    c->stats.spmm_ms = ms[PROF_SPMM];
+    c->stats.spmm_bytes = work[PROF_SPMM];
+    c->stats.spmm_launches = cnt[PROF_SPMM];
+  }
+  return e;
+}
+
+static Err run_pipeline_body(qsel_ctx *c) {
   cudaStream_t s = c->stream;
   const int64_t launches0 = g_launch_count;
   QSEL_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), s));

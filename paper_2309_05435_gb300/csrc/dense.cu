@@ -141,10 +141,18 @@ void launch_gemm(cudaStream_t s, const GemmBatch &b, int M, int N, int K, int ld
   if (b.count <= 0) return;
   ++g_launch_count;
   dim3 grid(N / 64, M / 64, b.count);
+  Profiler::Rec rec{PROF_GEMM, nullptr, nullptr, 0.0};
+  if (g_prof) {
+    const double mt = M / 64, nt = N / 64;
+    const double tiles = lower ? (nt * (nt + 1) / 2) : mt * nt;
+    rec.work = 2.0 * 64.0 * 64.0 * K * tiles * b.count;
+    g_prof->begin(s, rec);
+  }
   if (lower)
     k_gemm64<true><<<grid, 256, 0, s>>>(b, K, lda, ldb, ldc);
   else
     k_gemm64<false><<<grid, 256, 0, s>>>(b, K, lda, ldb, ldc);
+  if (g_prof) g_prof->end(s, rec);
 }
 
 // ---------------------------------------------------------------------------
@@ -284,7 +292,15 @@ void spd_inverse(cudaStream_t s, const SweepBatch &b, int n_pad, int32_t *err_fl
     g_launch_count += 3;
     k_sweep_pivot<<<b.count, 256, 0, s>>>(b, k, n_pad, err_flag);
     if (nt > 1) k_sweep_panel<<<dim3(nt - 1, b.count), 256, 0, s>>>(b, k, n_pad);
+    Profiler::Rec rec{PROF_SWEEP, nullptr, nullptr, 0.0};
+    if (g_prof) {
+      // rank-64 update of the lower tiles off row/column k: 2 * 64^3 FLOPs each
+      const double upd = (double)n_lower - nt;
+      rec.work = 2.0 * 64.0 * 64.0 * 64.0 * upd * b.count;
+      g_prof->begin(s, rec);
+    }
     k_sweep_update<<<dim3(n_lower, b.count), 256, 0, s>>>(b, k, nt, n_pad);
+    if (g_prof) g_prof->end(s, rec);
   }
   ++g_launch_count;
   k_sweep_mirror<<<dim3(n_lower, b.count), 256, 0, s>>>(b, n_pad, -1.0);

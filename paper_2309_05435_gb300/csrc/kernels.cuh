@@ -1,12 +1,54 @@
 // Host-side launchers of the library's kernels (internal interface).
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace qsel {
 
 // Every launcher increments this counter (reported in qsel_stats).
 extern thread_local int64_t g_launch_count;
+
+// Opt-in per-launch timing of the hot kernels: CUDA events recorded on the
+// launching stream around each launch, with the algorithmic work of the launch
+// (FLOPs or bytes).  Read back after the pipeline has synchronised.
+enum ProfKind { PROF_GEMM = 0, PROF_SWEEP = 1, PROF_SPMM = 2, PROF_KINDS = 3 };
+struct Profiler {
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+    double work;
+  };
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<Rec> recs;
+  cudaEvent_t take() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void begin(cudaStream_t s, Rec &r) {
+    r.a = take();
+    cudaEventRecord(r.a, s);
+  }
+  void end(cudaStream_t s, Rec &r) {
+    r.b = take();
+    cudaEventRecord(r.b, s);
+    recs.push_back(r);
+  }
+  void reset() {
+    used = 0;
+    recs.clear();
+  }
+  ~Profiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+extern thread_local Profiler *g_prof;
 
 // ---------------------------------------------------------------- model.cu
 // Time-structure scalars from theta (one thread).

@@ -11,6 +11,7 @@
 namespace qsel {
 
 thread_local int64_t g_launch_count = 0;
+thread_local Profiler *g_prof = nullptr;
 
 __global__ void k_time_coeffs(double log_kappa, double log_tau, double logit_rho, int n_t,
                               TimeCoeffs tc) {

@@ -224,12 +224,20 @@ __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs a) {
 void launch_bt_spmm(cudaStream_t s, const BtSpmmArgs &a) {
   ++g_launch_count;
   const int grid = bt_spmm_grid(a.n_s * a.n_t);
+  Profiler::Rec rec{PROF_SPMM, nullptr, nullptr, 0.0};
+  if (g_prof) {
+    // algorithmic bytes: read x once, write y once (the spatial pattern and the
+    // neighbouring rows are re-read from cache)
+    rec.work = 2.0 * (double)a.n_s * a.n_t * a.ld * sizeof(double);
+    g_prof->begin(s, rec);
+  }
   if (a.ld % 256 == 0)
     k_bt_spmm<4><<<grid, 256, 0, s>>>(a);
   else if (a.ld % 128 == 0)
     k_bt_spmm<2><<<grid, 256, 0, s>>>(a);
   else
     k_bt_spmm<1><<<grid, 256, 0, s>>>(a);
+  if (g_prof) g_prof->end(s, rec);
 }
 
 // ---------------------------------------------------------------------------
