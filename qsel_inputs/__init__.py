@@ -149,6 +149,8 @@ WORKLOADS = {
     "grid16_nt8": Workload("grid16_nt8", 16, 8, 0.5, 1.0, 0.9, 0.30, 0.5, 2, 1, 64, 1e-10),
     # 64x64 grid, n_t = 64 (n = 262,144): plain FP64, 8 subdomains, overlap 2, 256 samples
     "grid64_nt64": Workload("grid64_nt64", 64, 64, 0.2, 1.0, 0.95, 0.25, 0.5, 8, 2, 256, 1e-10),
+    # 64x64 grid, n_t = 16: same 4096-node blocks with fewer slabs (profiling captures)
+    "grid64_nt16": Workload("grid64_nt16", 64, 16, 0.2, 1.0, 0.95, 0.25, 0.5, 2, 2, 256, 1e-10),
     # 96x96 grid, n_t = 256 (n = 2,359,296): mixed precision, 16 subdomains, overlap 2, 512 samples
     "grid96_nt256": Workload("grid96_nt256", 96, 256, 0.1, 1.0, 0.98, 0.10, 0.5, 16, 2, 512, 1e-10),
 }
