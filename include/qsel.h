@@ -204,8 +204,38 @@ qsel_status qsel_debug_get_samples(const qsel_ctx *ctx, double *X, int32_t ld);
 qsel_status qsel_debug_get_rhs(const qsel_ctx *ctx, double *R, int32_t ld);
 qsel_status qsel_debug_get_selinv_diag(const qsel_ctx *ctx, double *diag_out);
 
-/* Message of the last failed call on ctx (or of the last failed qsel_create
- * when ctx is NULL).  Never NULL; owned by the library. */
+/*
+ * Allocation-free SPD inverse.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc -- code running while a
+ * stream is captured into a CUDA graph (allocation cannot be captured), code
+ * inside a framework whose caching allocator owns the device memory budget,
+ * and latency-bound loops that cannot take the implicit synchronisation of
+ * an allocation.  It runs the library's blocked symmetric-sweep inverse (the
+ * kernel that inverts the pivot blocks of the subdomain factorisation) on one
+ * caller-owned matrix and allocates nothing.
+ *   a_dev        DEVICE pointer to an n x n symmetric positive definite
+ *                matrix, row-major with leading dimension lda; overwritten
+ *                in place with its inverse (both triangles).
+ *   n, lda       1 <= n <= QSEL_NOALLOC_MAX_N, lda >= n.
+ *   cuda_stream  cudaStream_t for the work, or NULL for the legacy default
+ *                stream; the call returns once the stream has finished it.
+ * Scratch: a file-scope device array of QSEL_NOALLOC_MAX_N^2 + 2 * 64 *
+ *   QSEL_NOALLOC_MAX_N + 64^2 doubles (about 9 MiB), held by every GPU that
+ *   loads this part of the library until the process exits.  The first call
+ *   on each device looks up the array's device address with that device
+ *   current; make that first call before any stream capture.  Every call
+ *   shares the array and overwrites what the last call left there, so calls
+ *   that overlap on the GPU (other streams, other host threads) race: the
+ *   caller must serialise them.
+ * Errors: QSEL_EINVAL (NULL pointer, n out of range, lda < n), QSEL_ENOTSPD
+ *   (non-positive pivot), QSEL_ECUDA; the message is in qsel_last_error(NULL).
+ */
+#define QSEL_NOALLOC_MAX_N 1024
+qsel_status qsel_spd_inverse_noalloc(double *a_dev, int32_t n, int32_t lda, void *cuda_stream);
+
+/* Message of the last failed call on ctx, or, when ctx is NULL, of the last
+ * failed qsel_create or qsel_spd_inverse_noalloc on this thread.  Never NULL;
+ * owned by the library. */
 const char *qsel_last_error(const qsel_ctx *ctx);
 
 /* Free the context and its device memory.  NULL is allowed. */

@@ -5,4 +5,5 @@ from . import qsel  # noqa: F401
 from .qsel import (QSEL_FP64, QSEL_MIXED, Context, QselError, load_library,  # noqa: F401
                    qsel_create, qsel_debug_get_rhs, qsel_debug_get_samples,
                    qsel_debug_get_selinv_diag, qsel_debug_set_samples, qsel_destroy,
-                   qsel_diag_inv, qsel_last_error, qsel_set_theta, qsel_stats, qsel_trace_grads)
+                   qsel_diag_inv, qsel_last_error, qsel_set_theta, qsel_spd_inverse_noalloc, qsel_stats,
+                   qsel_trace_grads)

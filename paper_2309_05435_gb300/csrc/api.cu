@@ -110,6 +110,10 @@ struct qsel_ctx {
 
 static thread_local std::string g_create_error;
 
+namespace qsel {
+void set_context_free_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace qsel
+
 static qsel_status finish(qsel_ctx *ctx, const Err &e) {
   if (e.code != 0 && ctx) ctx->last_error = e.msg;
   return (qsel_status)e.code;

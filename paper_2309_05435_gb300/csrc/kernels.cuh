@@ -1,6 +1,7 @@
 // Host-side launchers of the library's kernels (internal interface).
 #pragma once
 
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -49,6 +50,9 @@ struct Profiler {
   }
 };
 extern thread_local Profiler *g_prof;
+
+// Message returned by qsel_last_error(NULL) for calls without a context.
+void set_context_free_error(const std::string &msg);
 
 // ---------------------------------------------------------------- model.cu
 // Time-structure scalars from theta (one thread).

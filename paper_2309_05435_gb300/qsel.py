@@ -52,7 +52,8 @@ class qsel_stats_t(ctypes.Structure):
 
 EXPORTED = ["qsel_create", "qsel_set_theta", "qsel_diag_inv", "qsel_trace_grads", "qsel_stats",
             "qsel_debug_set_samples", "qsel_debug_get_samples", "qsel_debug_get_rhs",
-            "qsel_debug_get_selinv_diag", "qsel_last_error", "qsel_destroy"]
+            "qsel_debug_get_selinv_diag", "qsel_spd_inverse_noalloc", "qsel_last_error", "qsel_destroy"]
+QSEL_NOALLOC_MAX_N = 1024
 
 _lib = None
 
@@ -76,6 +77,7 @@ def load_library(path: str = LIB_PATH):
     lib.qsel_debug_get_samples.argtypes = [c_void_p, P(c_double), c_int32]
     lib.qsel_debug_get_rhs.argtypes = [c_void_p, P(c_double), c_int32]
     lib.qsel_debug_get_selinv_diag.argtypes = [c_void_p, P(c_double)]
+    lib.qsel_spd_inverse_noalloc.argtypes = [c_void_p, c_int32, c_int32, c_void_p]
     lib.qsel_last_error.argtypes = [c_void_p]
     lib.qsel_last_error.restype = c_char_p
     lib.qsel_destroy.argtypes = [c_void_p]
@@ -213,6 +215,16 @@ def qsel_debug_get_selinv_diag(ctx: Context) -> np.ndarray:
     d = np.empty(ctx.n, dtype=np.float64)
     _check(load_library().qsel_debug_get_selinv_diag(ctx.handle, _ptr(d, c_double)), ctx.handle)
     return d
+
+
+def qsel_spd_inverse_noalloc(a, n: int, lda: int | None = None, cuda_stream=None):
+    """Invert the SPD matrix at device address ``a`` (a CUDA tensor or an
+    integer pointer; n x n row-major, leading dimension lda) in place, without
+    any allocation by the library; see qsel.h for the scratch-memory rules."""
+    ptr = a.data_ptr() if hasattr(a, "data_ptr") else int(a)
+    st = load_library().qsel_spd_inverse_noalloc(c_void_p(ptr), int(n), int(lda if lda is not None else n),
+                                                  c_void_p(int(cuda_stream)) if cuda_stream else None)
+    _check(st, None)
 
 
 def qsel_last_error(ctx: Context | None) -> str:
