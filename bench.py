@@ -36,6 +36,8 @@ import qsel_inputs as qi  # noqa: E402
 
 METRIC = "time to diag(Q^-1)+trace grads at 1% rel err; chosen vs plain FP64, 1 GB300"
 FP64_PEAK_TFLOPS = 1.25      # GB300 nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk/SM)
+# DRAM bytes per FLOP of k_gemm64 from one ncu capture (profiles/k_gemm64_grid64_nt16_fp64.md)
+GEMM64_DRAM_BYTES_PER_FLOP = 7.808e9 / 2.749e11
 L2_BYTES = 126 * 2 ** 20
 
 
@@ -284,7 +286,9 @@ def run_native(args):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"kernel": "k_gemm64 (FP64 dense tile GEMM of the Takahashi recursion and the sweeps)",
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                     "traffic": (GEMM64_DRAM_BYTES_PER_FLOP * gemm_flop / gemm_launches) if gemm_launches else None,
+                     "traffic_unit": "bytes per launch (ncu per-FLOP traffic scaled to the average timed launch)",
                      "peak_source": "nominal FP64 rate (recipe); probe measured 1.19 TFLOP/s"},
         "phases_ms": {"rhs": st["ms_rhs"], "pcg": st["ms_pcg"], "factor": st["ms_factor"],
                       "takahashi": st["ms_takahashi"], "correction": st["ms_correction"]},
