@@ -36,6 +36,7 @@ import qsel_inputs as qi  # noqa: E402
 
 METRIC = "time to diag(Q^-1)+trace grads at 1% rel err; chosen vs plain FP64, 1 GB300"
 FP64_PEAK_TFLOPS = 1.25      # GB300 nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/clk/SM)
+FP32_PEAK_TFLOPS = 80.5      # GB300 FP32 CUDA cores (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz)
 # DRAM bytes per FLOP of k_gemm64 from one ncu capture (profiles/k_gemm64_grid64_nt16_fp64.md)
 GEMM64_DRAM_BYTES_PER_FLOP = 7.808e9 / 2.749e11
 L2_BYTES = 126 * 2 ** 20
@@ -51,7 +52,21 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
+                    help="form timed for `value` (mixed = the chosen form)")
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="passes of plain FP64 timed beside the chosen form (0 = skip)")
     return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
 
 
 def workload_inputs(w, rank=0):
@@ -161,42 +176,64 @@ def run_native(args):
     mesh, mask = workload_inputs(w)
     stream = torch.cuda.current_stream()
     seed = 1000 + rank
-    ctx = qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma,
-                           w.theta, n_parts=w.n_parts, overlap=w.overlap, n_samples=w.n_samples, seed=seed,
-                           pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream, profile_kernels=1)
-    out = torch.empty(w.n, dtype=torch.float64, device=f"cuda:{local}")
-    grads = np.zeros(3)
+    dev = f"cuda:{local}"
+    chosen_prec = qsel.QSEL_MIXED if args.precision == "mixed" else qsel.QSEL_FP64
 
-    def step():
-        qsel.qsel_set_theta(ctx, w.theta)
-        qsel.qsel_diag_inv(ctx, out)
-        g = qsel.qsel_trace_grads(ctx)
-        grads[:] = g
-        return qsel.qsel_stats(ctx)
+    def make_ctx(precision, profile=1):
+        return qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma,
+                                w.theta, n_parts=w.n_parts, overlap=w.overlap, n_samples=w.n_samples, seed=seed,
+                                precision=precision, pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream,
+                                profile_kernels=profile)
 
-    for _ in range(args.warmup):
-        step()
-    clocks = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    stats = []
-    for _ in range(args.steps):
-        stats.append(step())
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    ms_local = e0.elapsed_time(e1)
-    t = torch.tensor([ms_local], dtype=torch.float64, device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_total = float(t.item())
+    def timed(ctx, out, warmup, steps, clocks=False):
+        grads = np.zeros(3)
+
+        def step():
+            qsel.qsel_set_theta(ctx, w.theta)
+            qsel.qsel_diag_inv(ctx, out)
+            grads[:] = qsel.qsel_trace_grads(ctx)
+            return qsel.qsel_stats(ctx)
+
+        for _ in range(warmup):
+            step()
+        sampler = ClockSampler(local) if clocks else None
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = [step() for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clk = sampler.stop() if sampler else None
+        t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item()), stats, clk, grads.copy()
+
+    ctx = make_ctx(chosen_prec)
+    out = torch.empty(w.n, dtype=torch.float64, device=dev)
+    ms_total, stats, clk, grads = timed(ctx, out, args.warmup, args.steps, clocks=True)
     ms_per_step = ms_total / args.steps
+    v_chosen = out.cpu().numpy()
+
+    plain = None
+    v_fp64 = None
+    if args.fp64_steps > 0 and chosen_prec != qsel.QSEL_FP64:
+        ctx64 = make_ctx(qsel.QSEL_FP64, profile=0)
+        out64 = torch.empty(w.n, dtype=torch.float64, device=dev)
+        ms64, st64, _, grads64 = timed(ctx64, out64, 1, args.fp64_steps)
+        v_fp64 = out64.cpu().numpy()
+        plain = {"ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps, "warmup": 1,
+                 "pcg_iterations": st64[-1]["pcg_iterations"],
+                 "speedup_chosen_vs_plain": (ms64 / args.fp64_steps) / ms_per_step,
+                 "chosen_vs_fp64_same_seed": {
+                     "diag_max_rel": float(np.max(np.abs(v_chosen - v_fp64) / np.abs(v_fp64))),
+                     "traces_rel": [float(abs(a - b) / abs(b)) for a, b in zip(grads, grads64)]}}
+        ctx64.close()
 
     # end to end through the public API with host buffers
     e2e_s = None
@@ -217,12 +254,12 @@ def run_native(args):
         for _ in range(args.e2e_steps):
             c2 = qsel.qsel_create(w.n_s, w.n_t, c_pin, rp_pin, gc_pin, gv_pin, mk_pin, w.sigma, w.theta,
                                   n_parts=w.n_parts, overlap=w.overlap, n_samples=w.n_samples, seed=seed,
-                                  pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream)
+                                  precision=chosen_prec, pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream)
             qsel.qsel_diag_inv(c2, diag_host)
             qsel.qsel_trace_grads(c2)
             c2.close()
         torch.cuda.synchronize()
-        el = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=f"cuda:{local}")
+        el = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(el, op=dist.ReduceOp.MAX)
         e2e_s = float(el.item()) / (args.e2e_steps * world)
@@ -234,13 +271,32 @@ def run_native(args):
             dist.destroy_process_group()
         return
 
-    # dominant kernel: the FP64 dense tile GEMM
-    gemm_ms = sum(s["gemm_ms"] for s in stats)
-    gemm_flop = sum(s["gemm_flop"] for s in stats)
-    gemm_launches = sum(s["gemm_launches"] for s in stats)
-    sweep_ms = sum(s["sweep_ms"] for s in stats)
-    spmm_ms = sum(s["spmm_ms"] for s in stats)
-    achieved = gemm_flop / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
+    # dominant kernel class of the timed form (by event time)
+    tot = {k: sum(s[k] for s in stats) for k in ("gemm_ms", "gemm_flop", "gemm_launches", "sweep_ms",
+                                                 "sweep_flop", "sweep_launches", "spmm_ms", "spmm_bytes",
+                                                 "spmm_launches")}
+    hbm_peak, hbm_src = measured_peaks()
+    alu_peak = FP64_PEAK_TFLOPS if chosen_prec == qsel.QSEL_FP64 else FP32_PEAK_TFLOPS
+    alu_src = ("nominal FP64 rate (152 SMs x 2.07 GHz x 4 FLOP/clk); FMA-loop probe 1.19 TFLOP/s"
+               if chosen_prec == qsel.QSEL_FP64 else
+               "FP32 CUDA-core rate from unit counts (152 x 128 x 2 x 2.07 GHz); FMA-loop probe 69.6 TFLOP/s")
+    cands = {"gemm": tot["gemm_ms"], "sweep": tot["sweep_ms"], "spmm": tot["spmm_ms"]}
+    dom = max(cands, key=cands.get)
+    if dom == "spmm":
+        ach = tot["spmm_bytes"] / (tot["spmm_ms"] * 1e-3) / 1e9
+        roof = {"kernel": "k_bt_spmm (block-tridiagonal sliced-ELL SpMM, PCG)", "bound": "hbm", "achieved": ach,
+                "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+                "peak_source": hbm_src}
+    else:
+        key = "gemm" if dom == "gemm" else "sweep"
+        ach = tot[f"{key}_flop"] / (tot[f"{key}_ms"] * 1e-3) / 1e12
+        traffic = None
+        if key == "gemm" and chosen_prec == qsel.QSEL_FP64 and tot["gemm_launches"]:
+            traffic = GEMM64_DRAM_BYTES_PER_FLOP * tot["gemm_flop"] / tot["gemm_launches"]
+        roof = {"kernel": "k_gemm64 (dense tile GEMM)" if key == "gemm" else "k_sweep_update (blocked sweep)",
+                "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
+                "traffic": traffic, "peak_source": alu_src}
+    roof["kernels_ms_per_step"] = {k: v / args.steps for k, v in cands.items()}
     st = stats[-1]
 
     accuracy = None
@@ -250,14 +306,15 @@ def run_native(args):
         v_ex = qsel.qsel_diag_inv(ref)
         t_ex = qsel.qsel_trace_grads(ref)
         ref.close()
-        v = out.cpu().numpy()
-        rel = (v - v_ex) / v_ex
+
+        def errs(v, g):
+            r = (v - v_ex) / v_ex
+            return {"eps_diag_rms": float(np.sqrt(np.mean(r ** 2))),
+                    "eps_diag_p99": float(np.quantile(np.abs(r), 0.99)),
+                    "eps_diag_max": float(np.max(np.abs(r))),
+                    "eps_traces": [float(abs(a - b) / abs(b)) for a, b in zip(g, t_ex)]}
         accuracy = {"reference": "exact single-subdomain FP64 selected inversion on the GPU (n_p = 1)",
-                    "eps_diag_rms": float(np.sqrt(np.mean(rel ** 2))),
-                    "eps_diag_p99": float(np.quantile(np.abs(rel), 0.99)),
-                    "eps_diag_max": float(np.max(np.abs(rel))),
-                    "eps_traces": [float(abs(a - b) / abs(b)) for a, b in zip(grads, t_ex)],
-                    "seeds": 1}
+                    "chosen": errs(v_chosen, grads), "seeds": 1}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -265,6 +322,8 @@ def run_native(args):
         cpu = {"value": est, "unit": "s", "cores": cpu_cores(), "kind": "oracle", "sample": desc,
                "sample_seconds": spent}
 
+    form = "mixed precision RBMC (FP32 PCG + FP64 refinement, FP32 tiles + FP64 pivots)" \
+        if chosen_prec == qsel.QSEL_MIXED else "plain FP64 RBMC"
     result = {
         "metric": METRIC,
         "value": ms_per_step / 1e3 / world,
@@ -276,27 +335,20 @@ def run_native(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f32+f64" if chosen_prec == qsel.QSEL_MIXED else "f64",
         "data": "synthetic (seeded grid FEM mesh, Philox noise)",
         "config": {"workload": f"{w.name}: {w.m}x{w.m} grid, n_t={w.n_t}, n={w.n}, kappa={w.kappa}, "
                                f"rho={w.rho}, {int(w.obs_frac * 100)}% observed",
-                   "form": "plain FP64 RBMC", "n_parts": w.n_parts, "overlap": w.overlap,
+                   "form": form, "n_parts": w.n_parts, "overlap": w.overlap,
                    "n_samples": w.n_samples, "pcg_tol": w.pcg_tol,
-                   "l2": "inputs larger than L2 (samples alone %.2f GB)" % (w.n * 256 * 8 / 1e9),
+                   "l2": "inputs larger than L2 (samples alone %.2f GB)" % (w.n * w.n_samples * 8 / 1e9),
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"kernel": "k_gemm64 (FP64 dense tile GEMM of the Takahashi recursion and the sweeps)",
-                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-                     "traffic": (GEMM64_DRAM_BYTES_PER_FLOP * gemm_flop / gemm_launches) if gemm_launches else None,
-                     "traffic_unit": "bytes per launch (ncu per-FLOP traffic scaled to the average timed launch)",
-                     "peak_source": "nominal FP64 rate (recipe); probe measured 1.19 TFLOP/s"},
+        "roofline": roof,
         "phases_ms": {"rhs": st["ms_rhs"], "pcg": st["ms_pcg"], "factor": st["ms_factor"],
                       "takahashi": st["ms_takahashi"], "correction": st["ms_correction"]},
-        "kernel_ms_per_step": {"gemm": gemm_ms / args.steps, "sweep_update": sweep_ms / args.steps,
-                               "spmm": spmm_ms / args.steps},
         "pcg_iterations": st["pcg_iterations"],
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
-        "gemm_launches_per_step": gemm_launches // args.steps,
+        "plain_fp64": plain,
         "clocks": clk,
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "cpu_baseline": cpu,

@@ -32,15 +32,23 @@ static Err fail(int code, const std::string &msg) {
   return e;
 }
 
+// One subdomain of the time partition (Algorithm 3 on whole slabs).
 struct Subdomain {
   int s0, s1, e0, e1, T, lo, hi;
   int sep_left, sep_right;             // separator slabs or -1
-  std::vector<double *> Dinv;          // T dense pivot-block inverses
-  double *SigA = nullptr, *SigB = nullptr, *Y = nullptr, *W = nullptr, *V = nullptr;
-  double *P = nullptr, *U = nullptr, *Vs = nullptr;  // sweep scratch
-  double *wbuf = nullptr;              // T x n_pad x ld correction samples
-  double *ybuf = nullptr, *tmp = nullptr, *bright = nullptr;
-  double *partial = nullptr;           // corr_grid x 3
+  double *partial = nullptr;           // corr_grid x 3 trace partials
+  int slot_base = 0;                   // first pattern-sum slot (2 T slots)
+};
+
+// Dense working set of one subdomain in flight; the wave holds up to
+// kMaxBatch of them and is reused for the next wave.  Element type: double
+// (FP64 path) or float (mixed path).
+struct DenseSlot {
+  std::vector<void *> Dinv;            // T_max pivot-block inverses
+  void *SigA = nullptr, *SigB = nullptr, *Y = nullptr, *W = nullptr, *V = nullptr;
+  void *P = nullptr, *U = nullptr, *Vs = nullptr;  // sweep scratch
+  void *wbuf = nullptr;                // T_max x n_pad x ld correction samples
+  void *ybuf = nullptr, *tmp = nullptr, *bright = nullptr;
 };
 
 }  // namespace qsel
@@ -49,6 +57,7 @@ using namespace qsel;
 
 struct qsel_ctx {
   int n_s = 0, n_t = 0, n = 0, ld = 0, k = 0, n_pad = 0, n_l = 0, bsize = 64;
+  bool mixed = false;
   double sigma = 1.0, obs_w = 1.0;
   qsel_theta theta{};
   qsel_options opt{};
@@ -63,23 +72,30 @@ struct qsel_ctx {
   int32_t *d_obs_index = nullptr;
   int n_obs = 0;
   TimeCoeffs tc{};
-  // sampler
+  // sampler: FP64 right-hand sides and samples; FP64 PCG vectors (FP64 path)
+  // or FP32 PCG vectors plus FP64 residual buffers (mixed path)
   double *d_z1 = nullptr, *d_z2 = nullptr, *d_R = nullptr, *d_X = nullptr;
   double *d_r = nullptr, *d_zv = nullptr, *d_p = nullptr, *d_q = nullptr;
-  double *d_pa = nullptr, *d_pb = nullptr, *d_pblk = nullptr;
+  float *f_x = nullptr, *f_r = nullptr, *f_z = nullptr, *f_p = nullptr, *f_q = nullptr;
+  double *d_pa = nullptr, *d_pb = nullptr;
+  void *d_pblk = nullptr;
   double *d_scal = nullptr;           // alpha, beta, rho, bb, rr (ld each) + max_rel
   int32_t *d_active = nullptr, *d_counters = nullptr;
   // estimator
   std::vector<Subdomain> parts;
-  double *d_diag = nullptr, *d_selinv = nullptr, *d_traces = nullptr, *d_sums = nullptr;
-  double *d_partials = nullptr;
+  std::vector<DenseSlot> slots;
+  int wave = 1, T_max = 1;
+  double *d_diag = nullptr, *d_selinv = nullptr, *d_corr = nullptr, *d_traces = nullptr, *d_sums = nullptr;
+  double *d_partials = nullptr, *d_diag_scratch = nullptr;
   TraceSlab *d_slabs = nullptr;
   int n_trace_slabs = 0;
   int32_t *d_err = nullptr;
   // host staging
   int32_t *h_counters = nullptr;
   double *h_small = nullptr;
-  cudaEvent_t ev[8]{};
+  cudaEvent_t ev[4]{};
+  std::vector<cudaEvent_t> phase_ev;   // pairs per (wave, phase)
+  size_t phase_used = 0;
   Profiler prof;
   bool computed = false, injected = false, have_rhs = false;
   qsel_stats_t stats{};
@@ -99,12 +115,21 @@ struct qsel_ctx {
   Err alloc(T **p, size_t count) {
     return alloc_bytes(reinterpret_cast<void **>(p), count * sizeof(T));
   }
+  cudaEvent_t phase_event() {
+    if (phase_used == phase_ev.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      phase_ev.push_back(e);
+    }
+    return phase_ev[phase_used++];
+  }
   ~qsel_ctx() {
     for (void *p : allocs) cudaFree(p);
     if (h_counters) cudaFreeHost(h_counters);
     if (h_small) cudaFreeHost(h_small);
     for (auto &e : ev)
       if (e) cudaEventDestroy(e);
+    for (auto e : phase_ev) cudaEventDestroy(e);
   }
 };
 
@@ -162,7 +187,8 @@ static Err validate(const qsel_model *m, const qsel_theta *th, const qsel_partit
         return fail(QSEL_EINVAL, "slab_start must be strictly increasing");
   }
   if (opt->n_samples < 1 || opt->n_samples > 512) return fail(QSEL_EINVAL, "n_samples must be in [1, 512]");
-  if (opt->precision != QSEL_FP64) return fail(QSEL_EINVAL, "precision: only QSEL_FP64 is available in this build");
+  if (opt->precision != QSEL_FP64 && opt->precision != QSEL_MIXED)
+    return fail(QSEL_EINVAL, "precision must be QSEL_FP64 or QSEL_MIXED");
   if (!(opt->pcg_tol > 0.0) || opt->pcg_max_iter < 1) return fail(QSEL_EINVAL, "pcg_tol > 0 and pcg_max_iter >= 1 required");
   if (opt->precond_block != 0 && opt->precond_block != 1 && opt->precond_block != 16 &&
       opt->precond_block != 32 && opt->precond_block != 64)
@@ -292,27 +318,37 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   TRY(c->alloc(&c->d_z2, (size_t)std::max(n_obs, 1) * c->ld));
   TRY(c->alloc(&c->d_R, vec));
   TRY(c->alloc(&c->d_X, vec));
-  TRY(c->alloc(&c->d_r, vec));
-  TRY(c->alloc(&c->d_zv, vec));
-  TRY(c->alloc(&c->d_p, vec));
-  TRY(c->alloc(&c->d_q, vec));
+  if (c->mixed) {
+    TRY(c->alloc(&c->d_q, vec));           // Q X for the refinement residual
+    TRY(c->alloc(&c->f_x, vec));
+    TRY(c->alloc(&c->f_r, vec));
+    TRY(c->alloc(&c->f_z, vec));
+    TRY(c->alloc(&c->f_p, vec));
+    TRY(c->alloc(&c->f_q, vec));
+  } else {
+    TRY(c->alloc(&c->d_r, vec));
+    TRY(c->alloc(&c->d_zv, vec));
+    TRY(c->alloc(&c->d_p, vec));
+    TRY(c->alloc(&c->d_q, vec));
+  }
   const int n_tiles = (n + 63) / 64;
-  const int n_pa = std::max(n_tiles, bt_spmm_grid(n));
+  const int n_pa = std::max(std::max(n_tiles, bt_spmm_grid(n)), residual_grid(n));
   TRY(c->alloc(&c->d_pa, (size_t)n_pa * c->ld));
-  TRY(c->alloc(&c->d_pb, (size_t)n_tiles * c->ld));
+  TRY(c->alloc(&c->d_pb, (size_t)n_pa * c->ld));
   const int nblk = (n + c->bsize - 1) / c->bsize;
-  TRY(c->alloc(&c->d_pblk, (size_t)nblk * c->bsize * c->bsize));
+  const size_t esz = c->mixed ? sizeof(float) : sizeof(double);
+  TRY(c->alloc_bytes(&c->d_pblk, (size_t)nblk * c->bsize * c->bsize * esz));
   TRY(c->alloc(&c->d_scal, (size_t)5 * c->ld + 8));
   TRY(c->alloc(&c->d_active, (size_t)c->ld));
   TRY(c->alloc(&c->d_counters, 8));
   QSEL_CUDA_TRY(cudaMemset(c->d_X, 0, vec * sizeof(double)));
 
-  // subdomains
+  // subdomains and trace bookkeeping: 2 pattern-sum slots per (subdomain,
+  // local slab) for Sigma and 2 for Y
   const int n_pad = c->n_pad;
-  const size_t mat = (size_t)n_pad * n_pad;
-  const size_t svec = (size_t)n_pad * c->ld;
   int n_sums = 0;
   std::vector<TraceSlab> tslabs;
+  c->T_max = 1;
   for (int p = 0; p < np; ++p) {
     Subdomain sd;
     sd.s0 = c->slab_start[p];
@@ -324,32 +360,18 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
     sd.hi = sd.s1 - 1 - sd.e0;
     sd.sep_left = sd.e0 > 0 ? sd.e0 - 1 : -1;
     sd.sep_right = sd.e1 < c->n_t ? sd.e1 : -1;
-    sd.Dinv.resize(sd.T);
-    for (int t = 0; t < sd.T; ++t) TRY(c->alloc(&sd.Dinv[t], mat));
-    TRY(c->alloc(&sd.SigA, mat));
-    TRY(c->alloc(&sd.SigB, mat));
-    TRY(c->alloc(&sd.Y, mat));
-    TRY(c->alloc(&sd.W, mat));
-    TRY(c->alloc(&sd.V, mat));
-    TRY(c->alloc(&sd.P, 64 * 64));
-    TRY(c->alloc(&sd.U, (size_t)n_pad * 64));
-    TRY(c->alloc(&sd.Vs, (size_t)n_pad * 64));
-    TRY(c->alloc(&sd.wbuf, (size_t)sd.T * svec));
-    TRY(c->alloc(&sd.ybuf, svec));
-    TRY(c->alloc(&sd.tmp, svec));
-    TRY(c->alloc(&sd.bright, svec));
-    // trace bookkeeping: sums slots 2 per (sd, local slab) for Sigma and for Y
-    const int base_sd = n_sums;
+    sd.slot_base = n_sums;
     n_sums += 2 * sd.T;
     for (int tl = sd.lo; tl <= sd.hi; ++tl) {
       TraceSlab ts;
       ts.t = sd.e0 + tl;
-      ts.sd = base_sd + tl;                              // Sigma_tl
-      ts.sy = (tl + 1 < sd.T) ? base_sd + sd.T + tl : -1;  // Y_tl
-      ts.sym = (tl > 0) ? base_sd + sd.T + tl - 1 : -1;     // Y_{tl-1}
+      ts.sd = sd.slot_base + tl;                                // Sigma_tl
+      ts.sy = (tl + 1 < sd.T) ? sd.slot_base + sd.T + tl : -1;  // Y_tl
+      ts.sym = (tl > 0) ? sd.slot_base + sd.T + tl - 1 : -1;    // Y_{tl-1}
       tslabs.push_back(ts);
     }
-    c->parts.push_back(std::move(sd));
+    c->T_max = std::max(c->T_max, sd.T);
+    c->parts.push_back(sd);
   }
   TRY(c->alloc(&c->d_partials, (size_t)np * corr_grid() * 3));
   QSEL_CUDA_TRY(cudaMemset(c->d_partials, 0, (size_t)np * corr_grid() * 3 * sizeof(double)));
@@ -360,8 +382,41 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   TRY(upload(c, &c->d_slabs, tslabs));
   TRY(c->alloc(&c->d_diag, (size_t)n));
   TRY(c->alloc(&c->d_selinv, (size_t)n));
+  TRY(c->alloc(&c->d_corr, (size_t)n));
   TRY(c->alloc(&c->d_traces, 4));
   TRY(c->alloc(&c->d_err, 4));
+  TRY(c->alloc_bytes(reinterpret_cast<void **>(&c->d_diag_scratch), extract_scratch_bytes(n_pad)));
+
+  // dense working sets: as many subdomains per wave as fit in 85 % of the free
+  // device memory (at most kMaxBatch)
+  const size_t mat = (size_t)n_pad * n_pad * esz;
+  const size_t svec = (size_t)n_pad * c->ld * esz;
+  const size_t per_slot = (size_t)(c->T_max + 5) * mat + 2 * (size_t)n_pad * 64 * esz + 64 * 64 * esz +
+                          (size_t)(c->T_max + 3) * svec + 4096;
+  size_t free_b = 0, total_b = 0;
+  QSEL_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  const size_t fit = (size_t)(0.85 * (double)free_b) / per_slot;
+  if (fit < 1)
+    return fail(QSEL_ENOMEM, "one subdomain's dense working set (" + std::to_string(per_slot >> 20) +
+                                 " MiB) does not fit in device memory");
+  c->wave = (int)std::min<size_t>(std::min<size_t>(fit, (size_t)kMaxBatch), (size_t)np);
+  c->slots.resize(c->wave);
+  for (auto &sl : c->slots) {
+    sl.Dinv.resize(c->T_max);
+    for (auto &d : sl.Dinv) TRY(c->alloc_bytes(&d, mat));
+    TRY(c->alloc_bytes(&sl.SigA, mat));
+    TRY(c->alloc_bytes(&sl.SigB, mat));
+    TRY(c->alloc_bytes(&sl.Y, mat));
+    TRY(c->alloc_bytes(&sl.W, mat));
+    TRY(c->alloc_bytes(&sl.V, mat));
+    TRY(c->alloc_bytes(&sl.P, 64 * 64 * esz));
+    TRY(c->alloc_bytes(&sl.U, (size_t)n_pad * 64 * esz));
+    TRY(c->alloc_bytes(&sl.Vs, (size_t)n_pad * 64 * esz));
+    TRY(c->alloc_bytes(&sl.wbuf, (size_t)c->T_max * svec));
+    TRY(c->alloc_bytes(&sl.ybuf, svec));
+    TRY(c->alloc_bytes(&sl.tmp, svec));
+    TRY(c->alloc_bytes(&sl.bright, svec));
+  }
   QSEL_CUDA_TRY(cudaHostAlloc(&c->h_counters, 64, cudaHostAllocDefault));
   QSEL_CUDA_TRY(cudaHostAlloc(&c->h_small, 64 * sizeof(double), cudaHostAllocDefault));
   for (auto &e : c->ev) QSEL_CUDA_TRY(cudaEventCreate(&e));
@@ -379,18 +434,18 @@ static Err run_model(qsel_ctx *c) {
   return ok();
 }
 
-static PcgVec pcg_vec(qsel_ctx *c) {
-  PcgVec v;
+template <typename T>
+static PcgVec<T> make_pcg(qsel_ctx *c, T *x, T *r, T *z, T *p, T *q) {
+  PcgVec<T> v;
   v.n = c->n;
   v.ld = c->ld;
   v.n_blocks_dot = bt_spmm_grid(c->n);
   v.n_tiles = (c->n + 63) / 64;
-  v.x = c->d_X;
-  v.r = c->d_r;
-  v.z = c->d_zv;
-  v.p = c->d_p;
-  v.q = c->d_q;
-  v.b = c->d_R;
+  v.x = x;
+  v.r = r;
+  v.z = z;
+  v.p = p;
+  v.q = q;
   v.partial_a = c->d_pa;
   v.partial_b = c->d_pb;
   v.alpha = c->d_scal;
@@ -404,28 +459,21 @@ static PcgVec pcg_vec(qsel_ctx *c) {
   return v;
 }
 
-static Err run_sampler(qsel_ctx *c) {
+// Multi-RHS block-Jacobi PCG from x = 0 on the right-hand sides held in v.r.
+// Per-column stop ||r_c|| <= tol ||b_c|| (recursive residual), converged
+// columns frozen; the host polls the active-column count every 8 iterations.
+template <typename T>
+static Err pcg_solve(qsel_ctx *c, const PcgVec<T> &v, const T *pblk, double tol, int max_iter, int *iters,
+                     double *max_rel, bool *converged) {
   cudaStream_t s = c->stream;
-  const size_t vec = (size_t)c->n * c->ld * sizeof(double);
-  launch_philox_normals(s, c->opt.seed, 0u, c->n, c->k, c->ld, c->d_z1);
-  launch_philox_normals(s, c->opt.seed, 1u, c->n_obs, c->k, c->ld, c->d_z2);
-  launch_perturbation_rhs(s, c->pat, c->d_kc, c->n_s, c->n_t, c->ld, c->tc.bdiag, c->tc.scalars,
-                          c->d_z1, c->d_z2, c->d_obs_index, 1.0 / c->sigma, c->d_R);
-  c->have_rhs = true;
-  QSEL_CUDA_TRY(cudaEventRecord(c->ev[1], s));
-  // preconditioner
-  launch_jacobi_setup(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
-                      c->bsize, c->d_pblk, c->d_err);
-  // PCG init: x = 0, r = b, p = 0, z = M^-1 r
-  PcgVec v = pcg_vec(c);
-  QSEL_CUDA_TRY(cudaMemsetAsync(c->d_X, 0, vec, s));
-  QSEL_CUDA_TRY(cudaMemsetAsync(c->d_p, 0, vec, s));
-  QSEL_CUDA_TRY(cudaMemsetAsync(c->d_scal, 0, (size_t)c->ld * sizeof(double), s));  // alpha = 0
-  QSEL_CUDA_TRY(cudaMemcpyAsync(c->d_r, c->d_R, vec, cudaMemcpyDeviceToDevice, s));
-  launch_pcg_update(s, v, c->d_pblk, c->bsize);
-  launch_pcg_reduce_beta(s, v, c->opt.pcg_tol, 1);
-  launch_pcg_p_update(s, v);
-  BtSpmmArgs a{};
+  const size_t vbytes = (size_t)c->n * c->ld * sizeof(T);
+  QSEL_CUDA_TRY(cudaMemsetAsync(v.x, 0, vbytes, s));
+  QSEL_CUDA_TRY(cudaMemsetAsync(v.p, 0, vbytes, s));
+  QSEL_CUDA_TRY(cudaMemsetAsync(v.alpha, 0, (size_t)c->ld * sizeof(double), s));
+  launch_pcg_update<T>(s, v, pblk, c->bsize);
+  launch_pcg_reduce_beta<T>(s, v, tol, 1);
+  launch_pcg_p_update<T>(s, v);
+  BtSpmmArgs<T> a{};
   a.pat = c->pat;
   a.val = c->d_qs;
   a.c0 = c->tc.a0;
@@ -435,324 +483,392 @@ static Err run_sampler(qsel_ctx *c) {
   a.n_s = c->n_s;
   a.n_t = c->n_t;
   a.ld = c->ld;
-  a.x = c->d_p;
-  a.y = c->d_q;
+  a.x = v.p;
+  a.y = v.q;
   a.dot_partial = c->d_pa;
   const int check_every = 8;
   int it = 0;
   bool done = false;
-  // iteration 0 check: all-zero right-hand sides converge immediately
-  QSEL_CUDA_TRY(cudaMemcpyAsync(c->h_counters, c->d_counters, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  QSEL_CUDA_TRY(cudaMemcpyAsync(c->h_counters, v.counters, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   QSEL_CUDA_TRY(cudaStreamSynchronize(s));
   if (c->h_counters[0] == 0) done = true;
-  while (!done && it < c->opt.pcg_max_iter) {
-    const int batch = std::min(check_every, c->opt.pcg_max_iter - it);
+  while (!done && it < max_iter) {
+    const int batch = std::min(check_every, max_iter - it);
     for (int b = 0; b < batch; ++b) {
-      launch_bt_spmm(s, a);
-      launch_pcg_reduce_alpha(s, v);
-      launch_pcg_update(s, v, c->d_pblk, c->bsize);
-      launch_pcg_reduce_beta(s, v, c->opt.pcg_tol, 0);
-      launch_pcg_p_update(s, v);
+      launch_bt_spmm<T>(s, a);
+      launch_pcg_reduce_alpha<T>(s, v);
+      launch_pcg_update<T>(s, v, pblk, c->bsize);
+      launch_pcg_reduce_beta<T>(s, v, tol, 0);
+      launch_pcg_p_update<T>(s, v);
     }
     it += batch;
     QSEL_CUDA_TRY(cudaGetLastError());
-    QSEL_CUDA_TRY(cudaMemcpyAsync(c->h_counters, c->d_counters, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    QSEL_CUDA_TRY(cudaMemcpyAsync(c->h_counters, v.counters, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     QSEL_CUDA_TRY(cudaStreamSynchronize(s));
     if (c->h_counters[0] == 0) done = true;
   }
   QSEL_CUDA_TRY(cudaMemcpyAsync(c->h_small, v.max_rel, sizeof(double), cudaMemcpyDeviceToHost, s));
   QSEL_CUDA_TRY(cudaStreamSynchronize(s));
-  c->stats.pcg_iterations = it;
-  c->stats.pcg_max_rel_residual = c->h_small[0];
-  if (!done)
-    return fail(QSEL_ENOCONV, "PCG did not reach pcg_tol within pcg_max_iter iterations (max relative residual " +
-                                  std::to_string(c->h_small[0]) + ")");
+  *iters = it;
+  *max_rel = c->h_small[0];
+  *converged = done;
   return ok();
 }
 
-// Forward block factorisation (pivot-block inverses) and backward Takahashi
-// recursion for every subdomain, batched in lockstep.
-static Err run_selinv(qsel_ctx *c) {
+// Perturbation right-hand sides and the global samples X = Q^-1 R.
+//   FP64: one PCG in double.
+//   mixed: iterative refinement -- the true residual R - Q X in double, an
+//   FP32 PCG for the correction to a loose inner tolerance, X += correction
+//   in double -- until every column meets pcg_tol in double.
+static Err run_sampler(qsel_ctx *c) {
   cudaStream_t s = c->stream;
-  const int n_pad = c->n_pad, n_s = c->n_s;
-  const int np = (int)c->parts.size();
+  launch_philox_normals(s, c->opt.seed, 0u, c->n, c->k, c->ld, c->d_z1);
+  launch_philox_normals(s, c->opt.seed, 1u, c->n_obs, c->k, c->ld, c->d_z2);
+  launch_perturbation_rhs(s, c->pat, c->d_kc, c->n_s, c->n_t, c->ld, c->tc.bdiag, c->tc.scalars,
+                          c->d_z1, c->d_z2, c->d_obs_index, 1.0 / c->sigma, c->d_R);
+  c->have_rhs = true;
+  QSEL_CUDA_TRY(cudaEventRecord(c->ev[1], s));
+  const size_t vec = (size_t)c->n * c->ld;
+  if (!c->mixed) {
+    double *pblk = static_cast<double *>(c->d_pblk);
+    launch_jacobi_setup<double>(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
+                                c->bsize, pblk, c->d_err);
+    QSEL_CUDA_TRY(cudaMemcpyAsync(c->d_r, c->d_R, vec * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    PcgVec<double> v = make_pcg<double>(c, c->d_X, c->d_r, c->d_zv, c->d_p, c->d_q);
+    int it = 0;
+    double rel = 0.0;
+    bool conv = false;
+    TRY(pcg_solve<double>(c, v, pblk, c->opt.pcg_tol, c->opt.pcg_max_iter, &it, &rel, &conv));
+    c->stats.pcg_iterations = it;
+    c->stats.pcg_max_rel_residual = rel;
+    if (!conv)
+      return fail(QSEL_ENOCONV, "PCG did not reach pcg_tol within pcg_max_iter iterations (max relative residual " +
+                                    std::to_string(rel) + ")");
+    return ok();
+  }
+  float *pblk = static_cast<float *>(c->d_pblk);
+  launch_jacobi_setup<float>(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
+                             c->bsize, pblk, c->d_err);
+  PcgVec<float> v = make_pcg<float>(c, c->f_x, c->f_r, c->f_z, c->f_p, c->f_q);
+  QSEL_CUDA_TRY(cudaMemsetAsync(c->d_X, 0, vec * sizeof(double), s));
+  QSEL_CUDA_TRY(cudaMemsetAsync(c->d_q, 0, vec * sizeof(double), s));
+  BtSpmmArgs<double> a{};
+  a.pat = c->pat;
+  a.val = c->d_qs;
+  a.c0 = c->tc.a0;
+  a.c1 = c->tc.a1;
+  a.obs = c->d_obs;
+  a.obs_w = c->obs_w;
+  a.n_s = c->n_s;
+  a.n_t = c->n_t;
+  a.ld = c->ld;
+  a.x = c->d_X;
+  a.y = c->d_q;
+  a.dot_partial = nullptr;
+  const double inner_tol = 1e-4;
+  const int max_outer = 30;
+  int total = 0;
+  double rel = 1.0;
+  for (int outer = 0;; ++outer) {
+    if (outer > 0) launch_bt_spmm<double>(s, a);
+    launch_residual(s, c->d_R, c->d_q, c->d_z1, c->f_r, c->n, c->ld, c->d_pa, c->d_pb);
+    launch_residual_check(s, c->d_pa, c->d_pb, residual_grid(c->n), c->ld, c->opt.pcg_tol, c->d_counters,
+                          c->d_scal + 5 * c->ld);
+    QSEL_CUDA_TRY(cudaMemcpyAsync(c->h_counters, c->d_counters, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    QSEL_CUDA_TRY(cudaMemcpyAsync(c->h_small, c->d_scal + 5 * c->ld, sizeof(double), cudaMemcpyDeviceToHost, s));
+    QSEL_CUDA_TRY(cudaStreamSynchronize(s));
+    rel = c->h_small[0];
+    if (c->h_counters[0] == 0) break;
+    if (outer == max_outer || total >= c->opt.pcg_max_iter) {
+      c->stats.pcg_iterations = total;
+      c->stats.pcg_max_rel_residual = rel;
+      return fail(QSEL_ENOCONV, "mixed-precision refinement did not reach pcg_tol (max relative residual " +
+                                    std::to_string(rel) + ")");
+    }
+    int it = 0;
+    double inner_rel = 0.0;
+    bool conv = false;
+    TRY(pcg_solve<float>(c, v, pblk, inner_tol, c->opt.pcg_max_iter - total, &it, &inner_rel, &conv));
+    total += it;
+    launch_accumulate(s, c->d_X, c->f_x, (int64_t)vec);
+  }
+  c->stats.pcg_iterations = total;
+  c->stats.pcg_max_rel_residual = rel;
+  return ok();
+}
+
+static void phase_mark(qsel_ctx *c, std::vector<std::pair<cudaEvent_t, int>> &marks, int phase) {
+  cudaEvent_t e = c->phase_event();
+  cudaEventRecord(e, c->stream);
+  marks.emplace_back(e, phase);
+}
+
+// Forward block factorisation, backward Takahashi recursion and RB correction
+// for the subdomains [p0, p1) held in slots 0 .. p1-p0-1, in lockstep.
+template <typename T>
+static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent_t, int>> &marks) {
+  cudaStream_t s = c->stream;
+  const int n_pad = c->n_pad, n_s = c->n_s, ld = c->ld;
+  const size_t svec = (size_t)n_pad * ld;
   int maxT = 0;
-  for (auto &sd : c->parts) maxT = std::max(maxT, sd.T);
-  for (int g0 = 0; g0 < np; g0 += kMaxBatch) {
-    const int g1 = std::min(np, g0 + kMaxBatch);
-    // forward
-    for (int t = 0; t < maxT; ++t) {
-      SchurBatch sb{};
-      SweepBatch wb{};
-      SpBatch gb{};
-      for (int p = g0; p < g1; ++p) {
-        Subdomain &sd = c->parts[p];
-        if (t >= sd.T) continue;
-        const int tg = sd.e0 + t;
-        SchurEntry &se = sb.e[sb.count++];
-        se.W = (t > 0) ? sd.W : nullptr;
-        se.D = sd.Dinv[t];
-        se.a0 = c->tc.a0 + tg;
-        se.c = (t > 0) ? c->tc.a1 + tg - 1 : c->tc.a1;
-        se.obs = c->d_obs + (size_t)tg * n_s;
-        SweepEntry &we = wb.e[wb.count++];
-        we.A = sd.Dinv[t];
-        we.P = sd.P;
-        we.U = sd.U;
-        we.V = sd.Vs;
-        if (t + 1 < sd.T) {
-          SpEntry &ge = gb.e[gb.count++];
-          ge.B = sd.Dinv[t];
-          ge.C = nullptr;
-          ge.Out = sd.W;
-          ge.alpha_ptr = c->tc.a1 + tg;
-          ge.alpha = 1.0;
-          ge.beta = 0.0;
+  for (int p = p0; p < p1; ++p) maxT = std::max(maxT, c->parts[p].T);
+  auto slot = [&](int p) -> DenseSlot & { return c->slots[p - p0]; };
+  auto Dinv = [&](int p, int t) { return static_cast<T *>(slot(p).Dinv[t]); };
+  auto buf = [](void *x) { return static_cast<T *>(x); };
+  phase_mark(c, marks, -1);
+  // ---- forward: D_t assembled (Schur), inverted in place, W_t = c_t Q_s D_t^-1
+  for (int t = 0; t < maxT; ++t) {
+    SchurBatch<T> sb{};
+    SweepBatch<T> wb{};
+    SpBatch<T, T> gb{};
+    for (int p = p0; p < p1; ++p) {
+      Subdomain &sd = c->parts[p];
+      if (t >= sd.T) continue;
+      DenseSlot &sl = slot(p);
+      const int tg = sd.e0 + t;
+      SchurEntry<T> &se = sb.e[sb.count++];
+      se.W = (t > 0) ? buf(sl.W) : nullptr;
+      se.D = Dinv(p, t);
+      se.a0 = c->tc.a0 + tg;
+      se.c = (t > 0) ? c->tc.a1 + tg - 1 : c->tc.a1;
+      se.obs = c->d_obs + (size_t)tg * n_s;
+      SweepEntry<T> &we = wb.e[wb.count++];
+      we.A = Dinv(p, t);
+      we.P = buf(sl.P);
+      we.U = buf(sl.U);
+      we.V = buf(sl.Vs);
+      if (t + 1 < sd.T) {
+        SpEntry<T, T> &ge = gb.e[gb.count++];
+        ge.B = Dinv(p, t);
+        ge.C = nullptr;
+        ge.Out = buf(sl.W);
+        ge.alpha_ptr = c->tc.a1 + tg;
+        ge.alpha = 1.0;
+        ge.beta = 0.0;
+      }
+    }
+    launch_schur_assemble<T>(s, sb, c->pat, c->d_qs, c->obs_w, n_s, n_pad);
+    spd_inverse<T>(s, wb, n_pad, c->d_err);
+    launch_sp_rowgather<T, T>(s, gb, c->pat, c->d_qs, n_s, n_pad, n_pad, n_pad, n_pad);
+  }
+  QSEL_CUDA_TRY(cudaGetLastError());
+  phase_mark(c, marks, 0);
+  // ---- backward: Sigma_{T-1} = D_{T-1}^-1, then Y_t, Sigma_t
+  {
+    ExtractBatch<T> xb{};
+    for (int p = p0; p < p1; ++p) {
+      Subdomain &sd = c->parts[p];
+      const int tl = sd.T - 1;
+      if (tl < sd.lo || tl > sd.hi) continue;
+      ExtractEntry<T> &xe = xb.e[xb.count++];
+      xe.S = Dinv(p, tl);
+      xe.diag_out = c->d_selinv + (size_t)(sd.e0 + tl) * n_s;
+      xe.sums = c->d_sums + 2 * (size_t)(sd.slot_base + tl);
+      xe.D0 = nullptr;
+      xe.V = nullptr;
+    }
+    launch_extract<T>(s, xb, c->pat, c->d_qs, c->d_dqs, n_s, n_pad, c->d_diag_scratch);
+  }
+  std::vector<T *> sig_next(p1 - p0, nullptr);
+  std::vector<int> flip(p1 - p0, 0);
+  for (int p = p0; p < p1; ++p) sig_next[p - p0] = Dinv(p, c->parts[p].T - 1);
+  for (int b = 0; b < maxT; ++b) {
+    SpBatch<T, T> wb{}, vb{};
+    GemmBatch<T> yb{}, sgb{};
+    SweepBatch<T> mb{};
+    ExtractBatch<T> xy{}, xs{};
+    std::vector<int> active;
+    for (int p = p0; p < p1; ++p) {
+      Subdomain &sd = c->parts[p];
+      DenseSlot &sl = slot(p);
+      const int tl = sd.T - 2 - b;
+      if (tl < std::max(sd.lo - 1, 0)) continue;
+      active.push_back(p);
+      const int tg = sd.e0 + tl;
+      SpEntry<T, T> &we = wb.e[wb.count++];
+      we.B = Dinv(p, tl);
+      we.C = nullptr;
+      we.Out = buf(sl.W);
+      we.alpha_ptr = c->tc.a1 + tg;
+      we.alpha = 1.0;
+      we.beta = 0.0;
+      GemmEntry<T> &ye = yb.e[yb.count++];
+      ye.A = sig_next[p - p0];
+      ye.B = buf(sl.W);
+      ye.C0 = nullptr;
+      ye.C = buf(sl.Y);
+      ye.alpha = 1.0;
+      ye.beta = 0.0;
+      const bool y_needed = (tl >= sd.lo && tl <= sd.hi) || (tl + 1 >= sd.lo && tl + 1 <= sd.hi);
+      if (y_needed) {
+        ExtractEntry<T> &xe = xy.e[xy.count++];
+        xe.S = buf(sl.Y);
+        xe.diag_out = nullptr;
+        xe.sums = c->d_sums + 2 * (size_t)(sd.slot_base + sd.T + tl);
+        xe.D0 = nullptr;
+        xe.V = nullptr;
+      }
+      if (tl >= sd.lo) {
+        T *sig_cur = buf(flip[p - p0] ? sl.SigB : sl.SigA);
+        SpEntry<T, T> &ve = vb.e[vb.count++];
+        ve.B = buf(sl.Y);
+        ve.C = nullptr;
+        ve.Out = buf(sl.V);
+        ve.alpha_ptr = c->tc.a1 + tg;
+        ve.alpha = 1.0;
+        ve.beta = 0.0;
+        GemmEntry<T> &ge = sgb.e[sgb.count++];
+        ge.A = Dinv(p, tl);
+        ge.B = buf(sl.V);
+        ge.C0 = Dinv(p, tl);
+        ge.C = sig_cur;
+        ge.alpha = 1.0;
+        ge.beta = 1.0;
+        SweepEntry<T> &me = mb.e[mb.count++];
+        me.A = sig_cur;
+        if (tl <= sd.hi) {
+          ExtractEntry<T> &xe = xs.e[xs.count++];
+          xe.S = sig_cur;
+          xe.diag_out = c->d_selinv + (size_t)tg * n_s;
+          xe.sums = c->d_sums + 2 * (size_t)(sd.slot_base + tl);
+          // mixed path: the Takahashi diagonal accumulated in double
+          xe.D0 = c->mixed ? Dinv(p, tl) : nullptr;
+          xe.V = c->mixed ? buf(sl.V) : nullptr;
         }
       }
-      launch_schur_assemble(s, sb, c->pat, c->d_qs, c->obs_w, n_s, n_pad);
-      spd_inverse(s, wb, n_pad, c->d_err);
-      launch_sp_rowgather(s, gb, c->pat, c->d_qs, n_s, n_pad, n_pad, n_pad);
+    }
+    if (active.empty()) break;
+    launch_sp_rowgather<T, T>(s, wb, c->pat, c->d_qs, n_s, n_pad, n_pad, n_pad, n_pad);
+    launch_gemm<T>(s, yb, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, false);
+    launch_extract<T>(s, xy, c->pat, c->d_qs, c->d_dqs, n_s, n_pad, c->d_diag_scratch);
+    launch_sp_rowgather<T, T>(s, vb, c->pat, c->d_qs, n_s, n_pad, n_pad, n_pad, n_pad);
+    launch_gemm<T>(s, sgb, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, true);
+    launch_mirror<T>(s, mb, n_pad);
+    launch_extract<T>(s, xs, c->pat, c->d_qs, c->d_dqs, n_s, n_pad, c->d_diag_scratch);
+    for (int p : active) {
+      Subdomain &sd = c->parts[p];
+      DenseSlot &sl = slot(p);
+      const int tl = sd.T - 2 - b;
+      if (tl >= sd.lo) {
+        sig_next[p - p0] = buf(flip[p - p0] ? sl.SigB : sl.SigA);
+        flip[p - p0] ^= 1;
+      }
     }
     QSEL_CUDA_TRY(cudaGetLastError());
   }
-  QSEL_CUDA_TRY(cudaEventRecord(c->ev[3], s));
-  for (int g0 = 0; g0 < np; g0 += kMaxBatch) {
-    const int g1 = std::min(np, g0 + kMaxBatch);
-    std::vector<int> slot_base(np, 0);
-    {
-      int acc = 0;
-      for (int p = 0; p < np; ++p) {
-        slot_base[p] = acc;
-        acc += 2 * c->parts[p].T;
+  phase_mark(c, marks, 1);
+  // ---- RB correction: w = Q_{**}^-1 Q_{*S} x_S by the block LDL^T sweeps
+  //   forward  y_0 = b_0, u_t = D_t^-1 y_t, y_{t+1} = b_{t+1} - c_t Q_s u_t
+  //   backward w_{T-1} = u_{T-1}, w_t = u_t - D_t^-1 (c_t Q_s w_{t+1})
+  std::vector<int> grp;
+  for (int p = p0; p < p1; ++p)
+    if (c->parts[p].sep_left >= 0 || c->parts[p].sep_right >= 0) grp.push_back(p);
+  if (!grp.empty()) {
+    SpBatch<double, T> bl{}, br{};
+    for (int p : grp) {
+      Subdomain &sd = c->parts[p];
+      DenseSlot &sl = slot(p);
+      if (sd.sep_left >= 0) {
+        SpEntry<double, T> &e = bl.e[bl.count++];
+        e.B = c->d_X + (size_t)sd.sep_left * n_s * ld;
+        e.C = nullptr;
+        e.Out = buf(sl.ybuf);
+        e.alpha_ptr = c->tc.a1 + sd.sep_left;
+        e.alpha = 1.0;
+        e.beta = 0.0;
+      } else {
+        QSEL_CUDA_TRY(cudaMemsetAsync(sl.ybuf, 0, svec * sizeof(T), s));
+      }
+      if (sd.sep_right >= 0) {
+        SpEntry<double, T> &e = br.e[br.count++];
+        e.B = c->d_X + (size_t)sd.sep_right * n_s * ld;
+        e.C = nullptr;
+        e.Out = buf(sl.bright);
+        e.alpha_ptr = c->tc.a1 + sd.sep_right - 1;
+        e.alpha = 1.0;
+        e.beta = 0.0;
       }
     }
-    // Sigma_{T-1} = Dinv_{T-1}
-    {
-      ExtractBatch xb{};
-      for (int p = g0; p < g1; ++p) {
-        Subdomain &sd = c->parts[p];
-        const int tl = sd.T - 1;
-        if (tl < sd.lo || tl > sd.hi) continue;
-        ExtractEntry &xe = xb.e[xb.count++];
-        xe.S = sd.Dinv[tl];
-        xe.diag_out = c->d_selinv + (size_t)(sd.e0 + tl) * n_s;
-        xe.sums = c->d_sums + 2 * (size_t)(slot_base[p] + tl);
-      }
-      launch_extract(s, xb, c->pat, c->d_qs, c->d_dqs, n_s, n_pad);
+    launch_sp_rowgather<double, T>(s, bl, c->pat, c->d_qs, n_s, n_pad, ld, ld, ld);
+    launch_sp_rowgather<double, T>(s, br, c->pat, c->d_qs, n_s, n_pad, ld, ld, ld);
+    for (int p : grp) {
+      Subdomain &sd = c->parts[p];
+      DenseSlot &sl = slot(p);
+      if (sd.T == 1 && sd.sep_right >= 0) launch_add<T>(s, buf(sl.ybuf), buf(sl.bright), (int64_t)svec);
     }
-    std::vector<double *> sig_next(np, nullptr);
-    std::vector<int> flip(np, 0);
-    for (int p = g0; p < g1; ++p) sig_next[p] = c->parts[p].Dinv[c->parts[p].T - 1];
-    for (int b = 0; b < maxT; ++b) {
-      SpBatch wb{}, vb{};
-      GemmBatch yb{}, sgb{};
-      SweepBatch mb{};
-      ExtractBatch xy{}, xs{};
-      std::vector<int> active;
-      for (int p = g0; p < g1; ++p) {
-        Subdomain &sd = c->parts[p];
-        const int tl = sd.T - 2 - b;
-        if (tl < std::max(sd.lo - 1, 0)) continue;
-        active.push_back(p);
-        const int tg = sd.e0 + tl;
-        SpEntry &we = wb.e[wb.count++];
-        we.B = sd.Dinv[tl];
-        we.C = nullptr;
-        we.Out = sd.W;
-        we.alpha_ptr = c->tc.a1 + tg;
-        we.alpha = 1.0;
-        we.beta = 0.0;
-        GemmEntry &ye = yb.e[yb.count++];
-        ye.A = sig_next[p];
-        ye.B = sd.W;
-        ye.C0 = nullptr;
-        ye.C = sd.Y;
-        ye.alpha = 1.0;
-        ye.beta = 0.0;
-        const bool y_needed = (tl >= sd.lo && tl <= sd.hi) || (tl + 1 >= sd.lo && tl + 1 <= sd.hi);
-        if (y_needed) {
-          ExtractEntry &xe = xy.e[xy.count++];
-          xe.S = sd.Y;
-          xe.diag_out = nullptr;
-          xe.sums = c->d_sums + 2 * (size_t)(slot_base[p] + sd.T + tl);
-        }
-        if (tl >= sd.lo) {
-          double *sig_cur = flip[p] ? sd.SigB : sd.SigA;
-          SpEntry &ve = vb.e[vb.count++];
-          ve.B = sd.Y;
-          ve.C = nullptr;
-          ve.Out = sd.V;
-          ve.alpha_ptr = c->tc.a1 + tg;
-          ve.alpha = 1.0;
-          ve.beta = 0.0;
-          GemmEntry &ge = sgb.e[sgb.count++];
-          ge.A = sd.Dinv[tl];
-          ge.B = sd.V;
-          ge.C0 = sd.Dinv[tl];
-          ge.C = sig_cur;
-          ge.alpha = 1.0;
-          ge.beta = 1.0;
-          SweepEntry &me = mb.e[mb.count++];
-          me.A = sig_cur;
-          if (tl <= sd.hi) {
-            ExtractEntry &xe = xs.e[xs.count++];
-            xe.S = sig_cur;
-            xe.diag_out = c->d_selinv + (size_t)tg * n_s;
-            xe.sums = c->d_sums + 2 * (size_t)(slot_base[p] + tl);
-          }
-        }
-      }
-      if (active.empty()) break;
-      launch_sp_rowgather(s, wb, c->pat, c->d_qs, n_s, n_pad, n_pad, n_pad);
-      launch_gemm(s, yb, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, false);
-      launch_extract(s, xy, c->pat, c->d_qs, c->d_dqs, n_s, n_pad);
-      launch_sp_rowgather(s, vb, c->pat, c->d_qs, n_s, n_pad, n_pad, n_pad);
-      launch_gemm(s, sgb, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, true);
-      launch_mirror(s, mb, n_pad);
-      launch_extract(s, xs, c->pat, c->d_qs, c->d_dqs, n_s, n_pad);
-      for (int p : active) {
-        Subdomain &sd = c->parts[p];
-        const int tl = sd.T - 2 - b;
-        if (tl >= sd.lo) {
-          sig_next[p] = flip[p] ? sd.SigB : sd.SigA;
-          flip[p] ^= 1;
-        }
-      }
-      QSEL_CUDA_TRY(cudaGetLastError());
-    }
-  }
-  return ok();
-}
-
-// RB correction: w = Q_{**}^-1 Q_{*S} x_S by the block LDL^T sweeps
-//   forward  y_0 = b_0, u_t = D_t^-1 y_t, y_{t+1} = b_{t+1} - c_t Q_s u_t
-//   backward w_{T-1} = u_{T-1}, w_t = u_t - D_t^-1 (c_t Q_s w_{t+1})
-// then the squares and trace forms on the own rows.
-static Err run_correction(qsel_ctx *c) {
-  cudaStream_t s = c->stream;
-  const int n_pad = c->n_pad, n_s = c->n_s, ld = c->ld;
-  const int np = (int)c->parts.size();
-  const size_t svec = (size_t)n_pad * ld;
-  int maxT = 0;
-  for (auto &sd : c->parts) maxT = std::max(maxT, sd.T);
-  for (int g0 = 0; g0 < np; g0 += kMaxBatch) {
-    const int g1 = std::min(np, g0 + kMaxBatch);
-    std::vector<int> grp;
-    for (int p = g0; p < g1; ++p)
-      if (c->parts[p].sep_left >= 0 || c->parts[p].sep_right >= 0) grp.push_back(p);
-    if (grp.empty()) continue;
-    // boundary terms
-    {
-      SpBatch bl{}, br{};
-      for (int p : grp) {
-        Subdomain &sd = c->parts[p];
-        if (sd.sep_left >= 0) {
-          SpEntry &e = bl.e[bl.count++];
-          e.B = c->d_X + (size_t)sd.sep_left * n_s * ld;
-          e.C = nullptr;
-          e.Out = sd.ybuf;
-          e.alpha_ptr = c->tc.a1 + sd.sep_left;
-          e.alpha = 1.0;
-          e.beta = 0.0;
-        } else {
-          QSEL_CUDA_TRY(cudaMemsetAsync(sd.ybuf, 0, svec * sizeof(double), s));
-        }
-        if (sd.sep_right >= 0) {
-          SpEntry &e = br.e[br.count++];
-          e.B = c->d_X + (size_t)sd.sep_right * n_s * ld;
-          e.C = nullptr;
-          e.Out = sd.bright;
-          e.alpha_ptr = c->tc.a1 + sd.sep_right - 1;
-          e.alpha = 1.0;
-          e.beta = 0.0;
-        }
-      }
-      launch_sp_rowgather(s, bl, c->pat, c->d_qs, n_s, n_pad, ld, ld);
-      launch_sp_rowgather(s, br, c->pat, c->d_qs, n_s, n_pad, ld, ld);
-      for (int p : grp) {
-        Subdomain &sd = c->parts[p];
-        if (sd.T == 1 && sd.sep_right >= 0) launch_add(s, sd.ybuf, sd.bright, (int)svec);
-      }
-    }
-    // forward sweep
     for (int t = 0; t < maxT; ++t) {
-      GemmBatch ub{};
-      SpBatch yb{};
+      GemmBatch<T> ub{};
+      SpBatch<T, T> yb{};
       for (int p : grp) {
         Subdomain &sd = c->parts[p];
+        DenseSlot &sl = slot(p);
         if (t >= sd.T) continue;
-        GemmEntry &g = ub.e[ub.count++];
-        g.A = sd.Dinv[t];
-        g.B = sd.ybuf;
+        GemmEntry<T> &g = ub.e[ub.count++];
+        g.A = Dinv(p, t);
+        g.B = buf(sl.ybuf);
         g.C0 = nullptr;
-        g.C = sd.wbuf + (size_t)t * svec;
+        g.C = buf(sl.wbuf) + (size_t)t * svec;
         g.alpha = 1.0;
         g.beta = 0.0;
         if (t + 1 < sd.T) {
-          SpEntry &e = yb.e[yb.count++];
-          e.B = sd.wbuf + (size_t)t * svec;
+          SpEntry<T, T> &e = yb.e[yb.count++];
+          e.B = buf(sl.wbuf) + (size_t)t * svec;
           const bool add_right = (t + 1 == sd.T - 1) && sd.sep_right >= 0;
-          e.C = add_right ? sd.bright : nullptr;
-          e.Out = sd.ybuf;
+          e.C = add_right ? buf(sl.bright) : nullptr;
+          e.Out = buf(sl.ybuf);
           e.alpha_ptr = c->tc.a1 + sd.e0 + t;
           e.alpha = -1.0;
           e.beta = add_right ? 1.0 : 0.0;
         }
       }
       if (ub.count == 0) break;
-      launch_gemm(s, ub, n_pad, ld, n_pad, n_pad, ld, ld, false);
-      launch_sp_rowgather(s, yb, c->pat, c->d_qs, n_s, n_pad, ld, ld);
+      launch_gemm<T>(s, ub, n_pad, ld, n_pad, n_pad, ld, ld, false);
+      launch_sp_rowgather<T, T>(s, yb, c->pat, c->d_qs, n_s, n_pad, ld, ld, ld);
     }
-    // backward sweep
     for (int b = 0; b < maxT; ++b) {
-      SpBatch tb{};
-      GemmBatch wb{};
+      SpBatch<T, T> tb{};
+      GemmBatch<T> wb{};
       for (int p : grp) {
         Subdomain &sd = c->parts[p];
+        DenseSlot &sl = slot(p);
         const int t = sd.T - 2 - b;
         if (t < std::max(sd.lo - 1, 0)) continue;
-        SpEntry &e = tb.e[tb.count++];
-        e.B = sd.wbuf + (size_t)(t + 1) * svec;
+        SpEntry<T, T> &e = tb.e[tb.count++];
+        e.B = buf(sl.wbuf) + (size_t)(t + 1) * svec;
         e.C = nullptr;
-        e.Out = sd.tmp;
+        e.Out = buf(sl.tmp);
         e.alpha_ptr = c->tc.a1 + sd.e0 + t;
         e.alpha = 1.0;
         e.beta = 0.0;
-        GemmEntry &g = wb.e[wb.count++];
-        g.A = sd.Dinv[t];
-        g.B = sd.tmp;
-        g.C0 = sd.wbuf + (size_t)t * svec;
-        g.C = sd.wbuf + (size_t)t * svec;
+        GemmEntry<T> &g = wb.e[wb.count++];
+        g.A = Dinv(p, t);
+        g.B = buf(sl.tmp);
+        g.C0 = buf(sl.wbuf) + (size_t)t * svec;
+        g.C = buf(sl.wbuf) + (size_t)t * svec;
         g.alpha = -1.0;
         g.beta = 1.0;
       }
       if (tb.count == 0) break;
-      launch_sp_rowgather(s, tb, c->pat, c->d_qs, n_s, n_pad, ld, ld);
-      launch_gemm(s, wb, n_pad, ld, n_pad, n_pad, ld, ld, false);
+      launch_sp_rowgather<T, T>(s, tb, c->pat, c->d_qs, n_s, n_pad, ld, ld, ld);
+      launch_gemm<T>(s, wb, n_pad, ld, n_pad, n_pad, ld, ld, false);
     }
-    QSEL_CUDA_TRY(cudaGetLastError());
-  }
-  // squares and trace forms on the own rows of every subdomain
-  for (int g0 = 0; g0 < np; g0 += kMaxBatch) {
-    const int g1 = std::min(np, g0 + kMaxBatch);
-    CorrBatch cb{};
-    for (int p = g0; p < g1; ++p) {
+    CorrBatch<T> cb{};
+    for (int p : grp) {
       Subdomain &sd = c->parts[p];
-      if (sd.sep_left < 0 && sd.sep_right < 0) continue;
-      CorrEntry &e = cb.e[cb.count++];
-      e.w = sd.wbuf;
-      e.T = sd.T;
+      CorrEntry<T> &e = cb.e[cb.count++];
+      e.w = buf(slot(p).wbuf);
+      e.T_ = sd.T;
       e.lo = sd.lo;
       e.hi = sd.hi;
       e.e0 = sd.e0;
-      e.diag_out = c->d_diag;
+      e.corr_out = c->d_corr;
       e.partial = sd.partial;
     }
-    launch_correction_terms(s, cb, c->pat, c->d_qs, c->d_dqs, c->tc.a0, c->tc.a1, c->tc.r0, c->tc.r1,
-                            n_s, n_pad, ld, c->k);
+    launch_correction_terms<T>(s, cb, c->pat, c->d_qs, c->d_dqs, c->tc.a0, c->tc.a1, c->tc.r0, c->tc.r1, n_s,
+                               n_pad, ld, c->k);
   }
   QSEL_CUDA_TRY(cudaGetLastError());
+  phase_mark(c, marks, 2);
   return ok();
 }
 
@@ -791,48 +907,52 @@ static Err run_pipeline(qsel_ctx *c) {
 static Err run_pipeline_body(qsel_ctx *c) {
   cudaStream_t s = c->stream;
   const int64_t launches0 = g_launch_count;
+  c->phase_used = 0;
   QSEL_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), s));
+  QSEL_CUDA_TRY(cudaMemsetAsync(c->d_corr, 0, (size_t)c->n * sizeof(double), s));
   QSEL_CUDA_TRY(cudaEventRecord(c->ev[0], s));
   TRY(run_model(c));
   const bool need_samples = c->parts.size() > 1;
-  if (!c->injected) {
-    if (need_samples) {
-      TRY(run_sampler(c));
-    } else {
-      QSEL_CUDA_TRY(cudaEventRecord(c->ev[1], s));
-      c->stats.pcg_iterations = 0;
-      c->stats.pcg_max_rel_residual = 0.0;
-    }
+  c->stats.pcg_iterations = 0;
+  c->stats.pcg_max_rel_residual = 0.0;
+  if (!c->injected && need_samples) {
+    TRY(run_sampler(c));
   } else {
     QSEL_CUDA_TRY(cudaEventRecord(c->ev[1], s));
   }
   QSEL_CUDA_TRY(cudaEventRecord(c->ev[2], s));
-  TRY(run_selinv(c));
-  QSEL_CUDA_TRY(cudaEventRecord(c->ev[4], s));
-  QSEL_CUDA_TRY(cudaMemcpyAsync(c->d_diag, c->d_selinv, (size_t)c->n * sizeof(double),
-                                cudaMemcpyDeviceToDevice, s));
-  TRY(run_correction(c));
-  // traces: selected-inverse pattern sums plus every subdomain's correction partials
-  launch_trace_combine(s, c->d_slabs, c->n_trace_slabs, c->d_sums, c->d_partials,
-                       (int)c->parts.size() * corr_grid(), c->tc.a0, c->tc.a1, c->tc.r0, c->tc.r1,
-                       c->d_traces);
-  QSEL_CUDA_TRY(cudaEventRecord(c->ev[5], s));
+  std::vector<std::pair<cudaEvent_t, int>> marks;
+  const int np = (int)c->parts.size();
+  for (int p0 = 0; p0 < np; p0 += c->wave) {
+    const int p1 = std::min(np, p0 + c->wave);
+    if (c->mixed)
+      TRY(run_wave<float>(c, p0, p1, marks));
+    else
+      TRY(run_wave<double>(c, p0, p1, marks));
+  }
+  launch_sum(s, c->d_diag, c->d_selinv, c->d_corr, c->n);
+  launch_trace_combine(s, c->d_slabs, c->n_trace_slabs, c->d_sums, c->d_partials, np * corr_grid(), c->tc.a0,
+                       c->tc.a1, c->tc.r0, c->tc.r1, c->d_traces);
+  QSEL_CUDA_TRY(cudaEventRecord(c->ev[3], s));
   QSEL_CUDA_TRY(cudaStreamSynchronize(s));
   QSEL_CUDA_TRY(cudaGetLastError());
   int32_t err = 0;
   QSEL_CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
   if (err & 1) return fail(QSEL_ENOTSPD, "a pivot of a dense block factorisation was not positive");
   float ms;
-  auto el = [&](int a, int b) {
-    cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]);
+  auto el = [&](cudaEvent_t a, cudaEvent_t b) {
+    cudaEventElapsedTime(&ms, a, b);
     return (double)ms;
   };
-  c->stats.ms_rhs = c->injected ? 0.0 : el(0, 1);
-  c->stats.ms_pcg = el(1, 2);
-  c->stats.ms_factor = el(2, 3);
-  c->stats.ms_takahashi = el(3, 4);
-  c->stats.ms_correction = el(4, 5);
-  c->stats.ms_total = el(0, 5);
+  c->stats.ms_rhs = (c->injected || !need_samples) ? 0.0 : el(c->ev[0], c->ev[1]);
+  c->stats.ms_pcg = el(c->ev[1], c->ev[2]);
+  double ph[3] = {0, 0, 0};
+  for (size_t i = 1; i < marks.size(); ++i)
+    if (marks[i].second >= 0) ph[marks[i].second] += el(marks[i - 1].first, marks[i].first);
+  c->stats.ms_factor = ph[0];
+  c->stats.ms_takahashi = ph[1];
+  c->stats.ms_correction = ph[2];
+  c->stats.ms_total = el(c->ev[0], c->ev[3]);
   c->stats.kernel_launches = g_launch_count - launches0;
   c->computed = true;
   return ok();
@@ -871,6 +991,7 @@ qsel_status qsel_create(qsel_ctx **out, const qsel_model *model, const qsel_thet
   c->theta = *theta;
   c->opt = *opt;
   c->bsize = opt->precond_block == 0 ? 64 : opt->precond_block;
+  c->mixed = opt->precision == QSEL_MIXED;
   c->stream = reinterpret_cast<cudaStream_t>(opt->cuda_stream);
   e = build(c, model, partition, overlap);
   if (e.code) {

@@ -25,15 +25,15 @@ namespace qsel {
 // op(A)(r, kk) = TA ? A[kk * lda + r] : A[r * lda + kk]
 // op(B)(kk, c) = TB ? B[c * ldb + kk] : B[kk * ldb + c]
 // ---------------------------------------------------------------------------
+template <typename T>
 struct TileSmem {
-  double As[2][16][64];
-  double Bs[2][16][64];
+  T As[2][16][64];
+  T Bs[2][16][64];
 };
 
-template <bool TA, bool TB>
-__device__ __forceinline__ void tile_load(const double *__restrict__ A, int lda,
-                                          const double *__restrict__ B, int ldb, int k0,
-                                          double ra[4], double rb[4]) {
+template <bool TA, bool TB, typename T>
+__device__ __forceinline__ void tile_load(const T *__restrict__ A, int lda, const T *__restrict__ B, int ldb,
+                                          int k0, T ra[4], T rb[4]) {
   const int tid = threadIdx.x;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -55,9 +55,8 @@ __device__ __forceinline__ void tile_load(const double *__restrict__ A, int lda,
   }
 }
 
-template <bool TA, bool TB>
-__device__ __forceinline__ void tile_store(TileSmem &sm, int buf, const double ra[4],
-                                           const double rb[4]) {
+template <bool TA, bool TB, typename T>
+__device__ __forceinline__ void tile_store(TileSmem<T> &sm, int buf, const T ra[4], const T rb[4]) {
   const int tid = threadIdx.x;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -73,12 +72,11 @@ __device__ __forceinline__ void tile_store(TileSmem &sm, int buf, const double r
   }
 }
 
-template <bool TA, bool TB>
-__device__ __forceinline__ void tile_mma(TileSmem &sm, const double *__restrict__ A, int lda,
-                                         const double *__restrict__ B, int ldb, int K,
-                                         double acc[4][4]) {
+template <bool TA, bool TB, typename T>
+__device__ __forceinline__ void tile_mma(TileSmem<T> &sm, const T *__restrict__ A, int lda,
+                                         const T *__restrict__ B, int ldb, int K, T acc[4][4]) {
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  double ra[4], rb[4];
+  T ra[4], rb[4];
   tile_load<TA, TB>(A, lda, B, ldb, 0, ra, rb);
   tile_store<TA, TB>(sm, 0, ra, rb);
   __syncthreads();
@@ -88,7 +86,7 @@ __device__ __forceinline__ void tile_mma(TileSmem &sm, const double *__restrict_
     if (more) tile_load<TA, TB>(A, lda, B, ldb, k0 + 16, ra, rb);
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      double a[4], b[4];
+      T a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = sm.As[buf][kk][ty + 16 * i];
 #pragma unroll
@@ -110,17 +108,17 @@ __device__ __forceinline__ void tile_mma(TileSmem &sm, const double *__restrict_
 // ---------------------------------------------------------------------------
 // Batched GEMM: C = alpha A B + beta C0 (C0 may alias C).
 // ---------------------------------------------------------------------------
-template <bool LOWER>
-__global__ void __launch_bounds__(256) k_gemm64(GemmBatch bt, int K, int lda, int ldb, int ldc) {
-  __shared__ TileSmem sm;
-  const GemmEntry e = bt.e[blockIdx.z];
+template <typename T, bool LOWER>
+__global__ void __launch_bounds__(256) k_gemm64(GemmBatch<T> bt, int K, int lda, int ldb, int ldc) {
+  __shared__ TileSmem<T> sm;
+  const GemmEntry<T> e = bt.e[blockIdx.z];
   const int bm = blockIdx.y, bn = blockIdx.x;
   if (LOWER && bn > bm) return;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
   tile_mma<false, false>(sm, e.A + (int64_t)bm * 64 * lda, lda, e.B + (int64_t)bn * 64, ldb, K, acc);
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
@@ -129,14 +127,15 @@ __global__ void __launch_bounds__(256) k_gemm64(GemmBatch bt, int K, int lda, in
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int64_t idx = row * ldc + bn * 64 + tx + 16 * j;
-      double v = e.alpha * acc[i][j];
-      if (e.beta != 0.0) v = fma(e.beta, e.C0[idx], v);
+      T v = (T)e.alpha * acc[i][j];
+      if (e.beta != 0.0) v = fma((T)e.beta, e.C0[idx], v);
       e.C[idx] = v;
     }
   }
 }
 
-void launch_gemm(cudaStream_t s, const GemmBatch &b, int M, int N, int K, int lda, int ldb, int ldc,
+template <typename T>
+void launch_gemm(cudaStream_t s, const GemmBatch<T> &b, int M, int N, int K, int lda, int ldb, int ldc,
                  bool lower) {
   if (b.count <= 0) return;
   ++g_launch_count;
@@ -149,11 +148,13 @@ void launch_gemm(cudaStream_t s, const GemmBatch &b, int M, int N, int K, int ld
     g_prof->begin(s, rec);
   }
   if (lower)
-    k_gemm64<true><<<grid, 256, 0, s>>>(b, K, lda, ldb, ldc);
+    k_gemm64<T, true><<<grid, 256, 0, s>>>(b, K, lda, ldb, ldc);
   else
-    k_gemm64<false><<<grid, 256, 0, s>>>(b, K, lda, ldb, ldc);
+    k_gemm64<T, false><<<grid, 256, 0, s>>>(b, K, lda, ldb, ldc);
   if (g_prof) g_prof->end(s, rec);
 }
+template void launch_gemm<double>(cudaStream_t, const GemmBatch<double> &, int, int, int, int, int, int, bool);
+template void launch_gemm<float>(cudaStream_t, const GemmBatch<float> &, int, int, int, int, int, int, bool);
 
 // ---------------------------------------------------------------------------
 // Blocked symmetric sweep: in-place SPD inverse on the lower 64 x 64 tiles.
@@ -164,42 +165,46 @@ void launch_gemm(cudaStream_t s, const GemmBatch &b, int M, int N, int K, int ld
 // After every step the swept matrix holds -A^-1 (Goodnight's sweep operator);
 // the final mirror negates it and fills the upper triangle.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_sweep_pivot(SweepBatch bt, int k, int ld, int32_t *err_flag) {
+// The pivot tile is inverted in double whatever T is (the "FP64 pivots" of the
+// mixed path).
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_pivot(SweepBatch<T> bt, int k, int ld, int32_t *err_flag) {
   __shared__ double S[64 * 65];
-  const SweepEntry e = bt.e[blockIdx.x];
-  const double *T = e.A + (int64_t)k * 64 * ld + k * 64;
+  const SweepEntry<T> e = bt.e[blockIdx.x];
+  const T *Tk = e.A + (int64_t)k * 64 * ld + k * 64;
   for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
     const int r = idx >> 6, c = idx & 63;
     // the diagonal tile is kept symmetric; read the lower half only
-    S[r * 65 + c] = (r >= c) ? T[(int64_t)r * ld + c] : T[(int64_t)c * ld + r];
+    S[r * 65 + c] = (double)((r >= c) ? Tk[(int64_t)r * ld + c] : Tk[(int64_t)c * ld + r]);
   }
   __syncthreads();
   sym_sweep_inverse_smem(S, 65, 64, err_flag);
   for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
     const int r = idx >> 6, c = idx & 63;
-    e.P[idx] = -S[r * 65 + c];
+    e.P[idx] = (T)(-S[r * 65 + c]);
   }
 }
 
-__global__ void __launch_bounds__(256) k_sweep_panel(SweepBatch bt, int k, int ld) {
-  __shared__ TileSmem sm;
-  const SweepEntry e = bt.e[blockIdx.y];
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_panel(SweepBatch<T> bt, int k, int ld) {
+  __shared__ TileSmem<T> sm;
+  const SweepEntry<T> e = bt.e[blockIdx.y];
   const int i = (int)blockIdx.x < k ? (int)blockIdx.x : (int)blockIdx.x + 1;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  double *U = e.U + (int64_t)i * 64 * 64;
-  double *V = e.V + (int64_t)i * 64 * 64;
+  T *U = e.U + (int64_t)i * 64 * 64;
+  T *V = e.V + (int64_t)i * 64 * 64;
   if (i > k) {
-    const double *C = e.A + (int64_t)i * 64 * ld + k * 64;
+    const T *C = e.A + (int64_t)i * 64 * ld + k * 64;
     tile_mma<false, false>(sm, C, ld, e.P, 64, 64, acc);
     for (int idx = threadIdx.x; idx < 4096; idx += 256) V[idx] = C[(int64_t)(idx >> 6) * ld + (idx & 63)];
   } else {
     // A_ik = (A_ki)^T, tile (k, i) is in the lower triangle
-    const double *C = e.A + (int64_t)k * 64 * ld + i * 64;
+    const T *C = e.A + (int64_t)k * 64 * ld + i * 64;
     tile_mma<true, false>(sm, C, ld, e.P, 64, 64, acc);
     for (int idx = threadIdx.x; idx < 4096; idx += 256) V[idx] = C[(int64_t)(idx & 63) * ld + (idx >> 6)];
   }
@@ -209,45 +214,46 @@ __global__ void __launch_bounds__(256) k_sweep_panel(SweepBatch bt, int k, int l
     for (int b = 0; b < 4; ++b) U[(ty + 16 * a) * 64 + tx + 16 * b] = acc[a][b];
 }
 
-__global__ void __launch_bounds__(256) k_sweep_update(SweepBatch bt, int k, int nt, int ld) {
-  __shared__ TileSmem sm;
-  const SweepEntry e = bt.e[blockIdx.y];
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_update(SweepBatch<T> bt, int k, int nt, int ld) {
+  __shared__ TileSmem<T> sm;
+  const SweepEntry<T> e = bt.e[blockIdx.y];
   // linear index over lower tiles (i >= j): i = floor((sqrt(8 l + 1) - 1) / 2)
   const int l = blockIdx.x;
   int i = (int)((sqrt(8.0 * l + 1.0) - 1.0) * 0.5);
   while ((i + 1) * (i + 2) / 2 <= l) ++i;
   while (i * (i + 1) / 2 > l) --i;
   const int j = l - i * (i + 1) / 2;
-  double *Tij = e.A + (int64_t)i * 64 * ld + j * 64;
+  T *Tij = e.A + (int64_t)i * 64 * ld + j * 64;
   if (i == k && j == k) {
     for (int idx = threadIdx.x; idx < 4096; idx += 256) Tij[(int64_t)(idx >> 6) * ld + (idx & 63)] = -e.P[idx];
     return;
   }
   if (j == k) {  // i > k: A_ik <- U_i
-    const double *U = e.U + (int64_t)i * 4096;
+    const T *U = e.U + (int64_t)i * 4096;
     for (int idx = threadIdx.x; idx < 4096; idx += 256) Tij[(int64_t)(idx >> 6) * ld + (idx & 63)] = U[idx];
     return;
   }
   if (i == k) {  // j < k: tile (k, j) holds A_kj = A_jk^T <- U_j^T
-    const double *U = e.U + (int64_t)j * 4096;
+    const T *U = e.U + (int64_t)j * 4096;
     for (int idx = threadIdx.x; idx < 4096; idx += 256) {
       const int r = idx >> 6, c = idx & 63;
       Tij[(int64_t)r * ld + c] = U[c * 64 + r];
     }
     return;
   }
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
   tile_mma<false, true>(sm, e.U + (int64_t)i * 4096, 64, e.V + (int64_t)j * 4096, 64, 64, acc);
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      double *p = Tij + (int64_t)(ty + 16 * a) * ld + tx + 16 * b;
+      T *p = Tij + (int64_t)(ty + 16 * a) * ld + tx + 16 * b;
       *p -= acc[a][b];
     }
   (void)nt;
@@ -255,15 +261,17 @@ __global__ void __launch_bounds__(256) k_sweep_update(SweepBatch bt, int k, int 
 
 // A <- sign * A from the lower tiles, mirrored into the upper triangle (after
 // the sweep the lower tiles hold -A^-1, so the sweep mirrors with sign -1).
-__global__ void __launch_bounds__(256) k_sweep_mirror(SweepBatch bt, int ld, double sign) {
-  __shared__ double S[64 * 65];
-  const SweepEntry e = bt.e[blockIdx.y];
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_mirror(SweepBatch<T> bt, int ld, double sign) {
+  __shared__ T S[64 * 65];
+  const SweepEntry<T> e = bt.e[blockIdx.y];
+  const T sg = (T)sign;
   const int l = blockIdx.x;
   int i = (int)((sqrt(8.0 * l + 1.0) - 1.0) * 0.5);
   while ((i + 1) * (i + 2) / 2 <= l) ++i;
   while (i * (i + 1) / 2 > l) --i;
   const int j = l - i * (i + 1) / 2;
-  double *Tij = e.A + (int64_t)i * 64 * ld + j * 64;
+  T *Tij = e.A + (int64_t)i * 64 * ld + j * 64;
   for (int idx = threadIdx.x; idx < 4096; idx += 256) {
     const int r = idx >> 6, c = idx & 63;
     S[r * 65 + c] = Tij[(int64_t)r * ld + c];
@@ -272,26 +280,27 @@ __global__ void __launch_bounds__(256) k_sweep_mirror(SweepBatch bt, int ld, dou
   if (i == j) {
     for (int idx = threadIdx.x; idx < 4096; idx += 256) {
       const int r = idx >> 6, c = idx & 63;
-      Tij[(int64_t)r * ld + c] = sign * ((r >= c) ? S[r * 65 + c] : S[c * 65 + r]);
+      Tij[(int64_t)r * ld + c] = sg * ((r >= c) ? S[r * 65 + c] : S[c * 65 + r]);
     }
   } else {
-    double *Tji = e.A + (int64_t)j * 64 * ld + i * 64;
+    T *Tji = e.A + (int64_t)j * 64 * ld + i * 64;
     for (int idx = threadIdx.x; idx < 4096; idx += 256) {
       const int r = idx >> 6, c = idx & 63;
-      Tij[(int64_t)r * ld + c] = sign * S[r * 65 + c];
-      Tji[(int64_t)r * ld + c] = sign * S[c * 65 + r];
+      Tij[(int64_t)r * ld + c] = sg * S[r * 65 + c];
+      Tji[(int64_t)r * ld + c] = sg * S[c * 65 + r];
     }
   }
 }
 
-void spd_inverse(cudaStream_t s, const SweepBatch &b, int n_pad, int32_t *err_flag) {
+template <typename T>
+void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err_flag) {
   if (b.count <= 0) return;
   const int nt = n_pad / 64;
   const int n_lower = nt * (nt + 1) / 2;
   for (int k = 0; k < nt; ++k) {
     g_launch_count += 3;
-    k_sweep_pivot<<<b.count, 256, 0, s>>>(b, k, n_pad, err_flag);
-    if (nt > 1) k_sweep_panel<<<dim3(nt - 1, b.count), 256, 0, s>>>(b, k, n_pad);
+    k_sweep_pivot<T><<<b.count, 256, 0, s>>>(b, k, n_pad, err_flag);
+    if (nt > 1) k_sweep_panel<T><<<dim3(nt - 1, b.count), 256, 0, s>>>(b, k, n_pad);
     Profiler::Rec rec{PROF_SWEEP, nullptr, nullptr, 0.0};
     if (g_prof) {
       // rank-64 update of the lower tiles off row/column k: 2 * 64^3 FLOPs each
@@ -299,78 +308,93 @@ void spd_inverse(cudaStream_t s, const SweepBatch &b, int n_pad, int32_t *err_fl
       rec.work = 2.0 * 64.0 * 64.0 * 64.0 * upd * b.count;
       g_prof->begin(s, rec);
     }
-    k_sweep_update<<<dim3(n_lower, b.count), 256, 0, s>>>(b, k, nt, n_pad);
+    k_sweep_update<T><<<dim3(n_lower, b.count), 256, 0, s>>>(b, k, nt, n_pad);
     if (g_prof) g_prof->end(s, rec);
   }
   ++g_launch_count;
-  k_sweep_mirror<<<dim3(n_lower, b.count), 256, 0, s>>>(b, n_pad, -1.0);
+  k_sweep_mirror<T><<<dim3(n_lower, b.count), 256, 0, s>>>(b, n_pad, -1.0);
 }
+template void spd_inverse<double>(cudaStream_t, const SweepBatch<double> &, int, int32_t *);
+template void spd_inverse<float>(cudaStream_t, const SweepBatch<float> &, int, int32_t *);
 
-void launch_mirror(cudaStream_t s, const SweepBatch &b, int n_pad) {
+template <typename T>
+void launch_mirror(cudaStream_t s, const SweepBatch<T> &b, int n_pad) {
   if (b.count <= 0) return;
   const int nt = n_pad / 64;
   ++g_launch_count;
-  k_sweep_mirror<<<dim3(nt * (nt + 1) / 2, b.count), 256, 0, s>>>(b, n_pad, 1.0);
+  k_sweep_mirror<T><<<dim3(nt * (nt + 1) / 2, b.count), 256, 0, s>>>(b, n_pad, 1.0);
 }
+template void launch_mirror<double>(cudaStream_t, const SweepBatch<double> &, int);
+template void launch_mirror<float>(cudaStream_t, const SweepBatch<float> &, int);
 
 // ---------------------------------------------------------------------------
 // Out = alpha Q_s B + beta C on the spatial pattern (row gather): one warp per
-// (row, 128-column chunk), warp-uniform pattern entries, double2 lanes.
+// (row, 64-column chunk), warp-uniform pattern entries, 2 elements per lane.
+// Accumulation in the output type.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_sp_rowgather(SpBatch bt, SellPattern pat,
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(256) k_sp_rowgather(SpBatch<TI, TO> bt, SellPattern pat,
                                                       const double *__restrict__ val, int n_s,
-                                                      int n_pad, int ncol, int ld) {
-  const SpEntry e = bt.e[blockIdx.y];
+                                                      int n_pad, int ncol, int ldb, int ldo) {
+  const SpEntry<TI, TO> e = bt.e[blockIdx.y];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nch = ncol / 64;
-  const double alpha = e.alpha * (e.alpha_ptr ? *e.alpha_ptr : 1.0);
+  const TO alpha = (TO)(e.alpha * (e.alpha_ptr ? *e.alpha_ptr : 1.0));
   const int64_t items = (int64_t)n_pad * nch;
   for (int64_t it = (int64_t)blockIdx.x * 8 + warp; it < items; it += (int64_t)gridDim.x * 8) {
     const int row = (int)(it / nch);
     const int col = (int)(it - (int64_t)row * nch) * 64 + 2 * lane;
-    double2 acc = make_double2(0.0, 0.0);
+    TO a0 = TO(0), a1 = TO(0);
     if (row < n_s) {
       const int sl = row >> 5, li = row & 31;
       const int w = pat.slice_width[sl];
       const int base = pat.slice_ptr[sl] + li;
       for (int s = 0; s < w; ++s) {
         const int j = pat.col[base + s * kSlice];
-        const double v = val[base + s * kSlice];
-        const double2 bv = *reinterpret_cast<const double2 *>(e.B + (int64_t)j * ld + col);
-        acc.x = fma(v, bv.x, acc.x);
-        acc.y = fma(v, bv.y, acc.y);
+        const TO v = (TO)val[base + s * kSlice];
+        const TI *bp = e.B + (int64_t)j * ldb + col;
+        a0 = fma(v, (TO)bp[0], a0);
+        a1 = fma(v, (TO)bp[1], a1);
       }
     }
-    acc.x *= alpha;
-    acc.y *= alpha;
-    const int64_t idx = (int64_t)row * ld + col;
+    a0 *= alpha;
+    a1 *= alpha;
+    const int64_t idx = (int64_t)row * ldo + col;
     if (e.C != nullptr && e.beta != 0.0) {
-      const double2 cv = *reinterpret_cast<const double2 *>(e.C + idx);
-      acc.x = fma(e.beta, cv.x, acc.x);
-      acc.y = fma(e.beta, cv.y, acc.y);
+      a0 = fma((TO)e.beta, e.C[idx], a0);
+      a1 = fma((TO)e.beta, e.C[idx + 1], a1);
     }
-    *reinterpret_cast<double2 *>(e.Out + idx) = acc;
+    e.Out[idx] = a0;
+    e.Out[idx + 1] = a1;
   }
 }
 
-void launch_sp_rowgather(cudaStream_t s, const SpBatch &b, const SellPattern &pat, const double *val,
-                         int n_s, int n_pad, int ncol, int ld) {
+template <typename TI, typename TO>
+void launch_sp_rowgather(cudaStream_t s, const SpBatch<TI, TO> &b, const SellPattern &pat, const double *val,
+                         int n_s, int n_pad, int ncol, int ldb, int ldo) {
   if (b.count <= 0) return;
   ++g_launch_count;
   int64_t items = (int64_t)n_pad * (ncol / 64);
   int grid = (int)((items + 7) / 8);
   if (grid > 152 * 8) grid = 152 * 8;
-  k_sp_rowgather<<<dim3(grid, b.count), 256, 0, s>>>(b, pat, val, n_s, n_pad, ncol, ld);
+  k_sp_rowgather<TI, TO><<<dim3(grid, b.count), 256, 0, s>>>(b, pat, val, n_s, n_pad, ncol, ldb, ldo);
 }
+template void launch_sp_rowgather<double, double>(cudaStream_t, const SpBatch<double, double> &,
+                                                  const SellPattern &, const double *, int, int, int, int, int);
+template void launch_sp_rowgather<float, float>(cudaStream_t, const SpBatch<float, float> &, const SellPattern &,
+                                                const double *, int, int, int, int, int);
+template void launch_sp_rowgather<double, float>(cudaStream_t, const SpBatch<double, float> &,
+                                                 const SellPattern &, const double *, int, int, int, int, int);
 
 // ---------------------------------------------------------------------------
 // D = a0 Q_s + w_obs diag(obs) - c W Q_s (column gather over the symmetric
-// pattern: (W Q_s)[r, l] = sum_{j in pat(l)} W[r, j] Q_s[l, j]).
+// pattern: (W Q_s)[r, l] = sum_{j in pat(l)} W[r, j] Q_s[l, j]), in double.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch bt, SellPattern pat,
+template <typename T>
+__global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch<T> bt, SellPattern pat,
                                                         const double *__restrict__ qs, double obs_w,
                                                         int n_s, int n_pad) {
-  const SchurEntry e = bt.e[blockIdx.z];
+  const SchurEntry<T> e = bt.e[blockIdx.z];
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (l >= n_pad) return;
@@ -380,11 +404,11 @@ __global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch bt, SellPatte
     const int w = pat.slice_width[sl];
     const int base = pat.slice_ptr[sl] + li;
     double acc = 0.0, aq = 0.0;
-    const double *Wr = e.W ? e.W + (int64_t)r * n_pad : nullptr;
+    const T *Wr = e.W ? e.W + (int64_t)r * n_pad : nullptr;
     for (int s = 0; s < w; ++s) {
       const int j = pat.col[base + s * kSlice];
       const double v = qs[base + s * kSlice];
-      if (Wr) acc = fma(Wr[j], v, acc);
+      if (Wr) acc = fma((double)Wr[j], v, acc);
       if (j == r) aq += v;
     }
     out = (*e.a0) * aq;
@@ -393,37 +417,68 @@ __global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch bt, SellPatte
   } else {
     out = (r == l) ? 1.0 : 0.0;
   }
-  e.D[(int64_t)r * n_pad + l] = out;
+  e.D[(int64_t)r * n_pad + l] = (T)out;
 }
 
-void launch_schur_assemble(cudaStream_t s, const SchurBatch &b, const SellPattern &pat,
+template <typename T>
+void launch_schur_assemble(cudaStream_t s, const SchurBatch<T> &b, const SellPattern &pat,
                            const double *qs, double obs_w, int n_s, int n_pad) {
   if (b.count <= 0) return;
   ++g_launch_count;
   dim3 grid((n_pad + 255) / 256, n_pad, b.count);
-  k_schur_assemble<<<grid, 256, 0, s>>>(b, pat, qs, obs_w, n_s, n_pad);
+  k_schur_assemble<T><<<grid, 256, 0, s>>>(b, pat, qs, obs_w, n_s, n_pad);
 }
+template void launch_schur_assemble<double>(cudaStream_t, const SchurBatch<double> &, const SellPattern &,
+                                            const double *, double, int, int);
+template void launch_schur_assemble<float>(cudaStream_t, const SchurBatch<float> &, const SellPattern &,
+                                           const double *, double, int, int);
 
 // ---------------------------------------------------------------------------
-// diag(S) and the pattern inner products <dQ_s, S>, <Q_s, S> (one block per
-// entry, fixed reduction order).
+// diag(S) and the pattern inner products <dQ_s, S>, <Q_s, S> in double (one
+// block per entry, fixed reduction order).  With D0 set, the diagonal is
+// instead diag(D0) + diag(D0 V) accumulated in double over column chunks
+// (k_diag64), D0 symmetric so that D0[i, l] = D0[l, i] reads coalesce.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_extract(ExtractBatch bt, SellPattern pat,
+constexpr int kDiagChunks = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_diag64(ExtractBatch<T> bt, int n_s, int n_pad, double *partial) {
+  const ExtractEntry<T> e = bt.e[blockIdx.z];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_s || e.D0 == nullptr || e.diag_out == nullptr) return;
+  const int chunk = (n_s + kDiagChunks - 1) / kDiagChunks;
+  const int l0 = blockIdx.y * chunk, l1 = min(n_s, l0 + chunk);
+  double acc = 0.0;
+  for (int l = l0; l < l1; ++l) acc = fma((double)e.D0[(int64_t)l * n_pad + i], (double)e.V[(int64_t)l * n_pad + i], acc);
+  partial[((int64_t)blockIdx.z * kDiagChunks + blockIdx.y) * n_pad + i] = acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_extract(ExtractBatch<T> bt, SellPattern pat,
                                                   const double *__restrict__ qs,
-                                                  const double *__restrict__ dqs, int n_s, int n_pad) {
+                                                  const double *__restrict__ dqs, int n_s, int n_pad,
+                                                  const double *__restrict__ diag_partial) {
   __shared__ double red0[32], red1[32];
-  const ExtractEntry e = bt.e[blockIdx.x];
+  const ExtractEntry<T> e = bt.e[blockIdx.x];
   double s0 = 0.0, s1 = 0.0;
   for (int i = threadIdx.x; i < n_s; i += blockDim.x) {
-    const double *Si = e.S + (int64_t)i * n_pad;
-    if (e.diag_out) e.diag_out[i] = Si[i];
+    const T *Si = e.S + (int64_t)i * n_pad;
+    if (e.diag_out) {
+      if (e.D0) {
+        double d = (double)e.D0[(int64_t)i * n_pad + i];
+        for (int c = 0; c < kDiagChunks; ++c) d += diag_partial[((int64_t)blockIdx.x * kDiagChunks + c) * n_pad + i];
+        e.diag_out[i] = d;
+      } else {
+        e.diag_out[i] = (double)Si[i];
+      }
+    }
     if (e.sums) {
       const int sl = i >> 5, li = i & 31;
       const int w = pat.slice_width[sl];
       const int base = pat.slice_ptr[sl] + li;
       for (int s = 0; s < w; ++s) {
         const int j = pat.col[base + s * kSlice];
-        const double sv = Si[j];
+        const double sv = (double)Si[j];
         s0 = fma(dqs[base + s * kSlice], sv, s0);
         s1 = fma(qs[base + s * kSlice], sv, s1);
       }
@@ -450,11 +505,26 @@ __global__ void __launch_bounds__(1024) k_extract(ExtractBatch bt, SellPattern p
   }
 }
 
-void launch_extract(cudaStream_t s, const ExtractBatch &b, const SellPattern &pat, const double *qs,
-                    const double *dqs, int n_s, int n_pad) {
+// Scratch for the FP64 diagonal partials (per device, grown on demand by the
+// context through extract_scratch_bytes()).
+size_t extract_scratch_bytes(int n_pad) { return (size_t)kMaxBatch * kDiagChunks * n_pad * sizeof(double); }
+
+template <typename T>
+void launch_extract(cudaStream_t s, const ExtractBatch<T> &b, const SellPattern &pat, const double *qs,
+                    const double *dqs, int n_s, int n_pad, double *diag_scratch) {
   if (b.count <= 0) return;
+  bool any_d0 = false;
+  for (int q = 0; q < b.count; ++q) any_d0 |= (b.e[q].D0 != nullptr);
+  if (any_d0) {
+    ++g_launch_count;
+    k_diag64<T><<<dim3((n_s + 255) / 256, kDiagChunks, b.count), 256, 0, s>>>(b, n_s, n_pad, diag_scratch);
+  }
   ++g_launch_count;
-  k_extract<<<b.count, 1024, 0, s>>>(b, pat, qs, dqs, n_s, n_pad);
+  k_extract<T><<<b.count, 1024, 0, s>>>(b, pat, qs, dqs, n_s, n_pad, diag_scratch);
 }
+template void launch_extract<double>(cudaStream_t, const ExtractBatch<double> &, const SellPattern &,
+                                     const double *, const double *, int, int, double *);
+template void launch_extract<float>(cudaStream_t, const ExtractBatch<float> &, const SellPattern &,
+                                    const double *, const double *, int, int, double *);
 
 }  // namespace qsel

@@ -1,4 +1,8 @@
 // Host-side launchers of the library's kernels (internal interface).
+//
+// Kernels that move sample blocks or dense blocks are templated on the
+// storage/arithmetic type T (double for the FP64 path, float for the mixed
+// path); reductions, pivots and the spatial pattern values stay in double.
 #pragma once
 
 #include <string>
@@ -55,25 +59,21 @@ extern thread_local Profiler *g_prof;
 void set_context_free_error(const std::string &msg);
 
 // ---------------------------------------------------------------- model.cu
-// Time-structure scalars from theta (one thread).
 void launch_time_coeffs(cudaStream_t s, double log_kappa, double log_tau, double logit_rho,
                         int n_t, TimeCoeffs tc);
-// Values of Q_s, dQ_s/dlog kappa and K C^-1/2 on the sliced pattern.
 void launch_qs_values(cudaStream_t s, int n_ent, const double *c_pat, const double *g_pat,
                       const double *h_pat, const double *isqc_pat, const double *scalars,
                       double *qs, double *dqs, double *kc);
 
 // ---------------------------------------------------------------- sampler.cu
-// Standard normals (Philox4x32-10 + Box-Muller), n_rows x ld, zero in
-// columns [k, ld).
 void launch_philox_normals(cudaStream_t s, uint64_t seed, uint32_t stream_id, int n_rows, int k,
                            int ld, double *z);
-// Perturbation RHS r = F^T z1 + A^T z2 / sigma.
 void launch_perturbation_rhs(cudaStream_t s, const SellPattern &pat, const double *kc, int n_s,
                              int n_t, int ld, const double *bdiag, const double *scalars,
                              const double *z1, const double *z2, const int32_t *obs_index,
                              double inv_sigma, double *r);
 
+template <typename T>
 struct BtSpmmArgs {
   SellPattern pat;
   const double *val;      // spatial values on the pattern
@@ -82,122 +82,165 @@ struct BtSpmmArgs {
   const uint8_t *obs;     // observation mask (may be null)
   double obs_w;           // weight of the observation diagonal
   int n_s, n_t, ld;
-  const double *x;
-  double *y;
+  const T *x;
+  T *y;
   double *dot_partial;    // if non-null: per-CTA per-column partial sums of x*y
 };
 int bt_spmm_grid(int n_rows);
-void launch_bt_spmm(cudaStream_t s, const BtSpmmArgs &a);
+template <typename T>
+void launch_bt_spmm(cudaStream_t s, const BtSpmmArgs<T> &a);
 
+template <typename T>
 struct PcgVec {
   int n, ld, n_blocks_dot, n_tiles;
-  double *x, *r, *z, *p, *q, *b;
+  T *x, *r, *z, *p, *q;
   double *partial_a, *partial_b;      // reduction scratch
   double *alpha, *beta, *rho, *bb, *rr;
   int32_t *active;
   int32_t *counters;                  // [0] active columns
   double *max_rel;                    // [0] max relative residual
 };
+template <typename T>
 void launch_jacobi_setup(cudaStream_t s, const SellPattern &pat, const double *qs, const double *a0,
                          const double *a1, const uint8_t *obs, double obs_w, int n_s, int n_t,
-                         int bsize, double *pblk, int32_t *err_flag);
-void launch_pcg_update(cudaStream_t s, const PcgVec &v, const double *pblk, int bsize);
-void launch_pcg_reduce_alpha(cudaStream_t s, const PcgVec &v);
-void launch_pcg_reduce_beta(cudaStream_t s, const PcgVec &v, double tol, int init);
-void launch_pcg_p_update(cudaStream_t s, const PcgVec &v);
+                         int bsize, T *pblk, int32_t *err_flag);
+template <typename T>
+void launch_pcg_update(cudaStream_t s, const PcgVec<T> &v, const T *pblk, int bsize);
+template <typename T>
+void launch_pcg_reduce_alpha(cudaStream_t s, const PcgVec<T> &v);
+template <typename T>
+void launch_pcg_reduce_beta(cudaStream_t s, const PcgVec<T> &v, double tol, int init);
+template <typename T>
+void launch_pcg_p_update(cudaStream_t s, const PcgVec<T> &v);
+
+// Mixed-precision refinement: r = b - y (FP64) with per-CTA per-column
+// partial sums of r^2 and b^2, and the FP32 copy of r.
+int residual_grid(int n);
+void launch_residual(cudaStream_t s, const double *b, const double *y, double *r, float *r32, int n,
+                     int ld, double *partial_rr, double *partial_bb);
+// Per-column totals of the partials and the number of columns with
+// ||r_c|| > tol ||b_c|| (counters[0]); max relative residual in max_rel[0].
+void launch_residual_check(cudaStream_t s, const double *partial_rr, const double *partial_bb, int n_parts,
+                           int ld, double tol, int32_t *counters, double *max_rel);
+// x += (double) d
+void launch_accumulate(cudaStream_t s, double *x, const float *d, int64_t count);
 
 // ---------------------------------------------------------------- dense.cu
 constexpr int kMaxBatch = 16;
 
+template <typename T>
 struct GemmEntry {
-  const double *A, *B, *C0;
-  double *C;
+  const T *A, *B, *C0;
+  T *C;
   double alpha, beta;
 };
+template <typename T>
 struct GemmBatch {
-  GemmEntry e[kMaxBatch];
+  GemmEntry<T> e[kMaxBatch];
   int count;
 };
 // C = alpha A B + beta C0 for row-major M x K and K x N operands (multiples of
 // 64); lower = only tiles on or below the diagonal.
-void launch_gemm(cudaStream_t s, const GemmBatch &b, int M, int N, int K, int lda, int ldb, int ldc,
+template <typename T>
+void launch_gemm(cudaStream_t s, const GemmBatch<T> &b, int M, int N, int K, int lda, int ldb, int ldc,
                  bool lower);
 
+template <typename T>
 struct SweepEntry {
-  double *A;          // n_pad x n_pad, row-major, lower tiles used
-  double *P;          // 64 x 64 scratch
-  double *U, *V;      // n_pad x 64 scratch each (tile-major)
+  T *A;          // n_pad x n_pad, row-major, lower tiles used
+  T *P;          // 64 x 64 scratch
+  T *U, *V;      // n_pad x 64 scratch each (tile-major)
 };
+template <typename T>
 struct SweepBatch {
-  SweepEntry e[kMaxBatch];
+  SweepEntry<T> e[kMaxBatch];
   int count;
 };
 // In-place SPD inverse by the blocked symmetric sweep; A becomes A^-1 with
-// both triangles filled.  err_flag gets bit 1 on a non-positive pivot.
-void spd_inverse(cudaStream_t s, const SweepBatch &b, int n_pad, int32_t *err_flag);
+// both triangles filled.  The 64 x 64 pivot tiles are always inverted in
+// double.  err_flag gets bit 0 on a non-positive pivot.
+template <typename T>
+void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err_flag);
 // Copy the lower tiles of each e[].A into its upper triangle (symmetric fill).
-void launch_mirror(cudaStream_t s, const SweepBatch &b, int n_pad);
+template <typename T>
+void launch_mirror(cudaStream_t s, const SweepBatch<T> &b, int n_pad);
 
+template <typename TI, typename TO>
 struct SpEntry {
-  const double *B;          // dense input, rows indexed by pattern columns
-  const double *C;          // optional additive input (beta term)
-  double *Out;
+  const TI *B;              // dense input, rows indexed by pattern columns
+  const TO *C;              // optional additive input (beta term)
+  TO *Out;
   const double *alpha_ptr;  // optional device scalar multiplying alpha
   double alpha, beta;
 };
+template <typename TI, typename TO>
 struct SpBatch {
-  SpEntry e[kMaxBatch];
+  SpEntry<TI, TO> e[kMaxBatch];
   int count;
 };
 // Out[i, :] = alpha (Q_s B)[i, :] + beta C[i, :] for i < n_s (rows n_s..n_pad-1
-// of Out are set to beta C, or zero when C is null).
-void launch_sp_rowgather(cudaStream_t s, const SpBatch &b, const SellPattern &pat, const double *val,
-                         int n_s, int n_pad, int ncol, int ld);
+// of Out are set to beta C, or zero when C is null).  B has leading dimension
+// ldb, Out and C have ldo.
+template <typename TI, typename TO>
+void launch_sp_rowgather(cudaStream_t s, const SpBatch<TI, TO> &b, const SellPattern &pat,
+                         const double *val, int n_s, int n_pad, int ncol, int ldb, int ldo);
 
+template <typename T>
 struct SchurEntry {
-  const double *W;          // W_{t-1} = c Q_s Dinv_{t-1} (null for the first slab)
-  double *D;                // output diagonal block
+  const T *W;               // W_{t-1} = c Q_s Dinv_{t-1} (null for the first slab)
+  T *D;                     // output diagonal block
   const double *a0;         // device pointer to tau Q_t[t,t]
   const double *c;          // device pointer to the coupling c_{t-1} (ignored if W null)
   const uint8_t *obs;       // mask of slab t (n_s entries)
 };
+template <typename T>
 struct SchurBatch {
-  SchurEntry e[kMaxBatch];
+  SchurEntry<T> e[kMaxBatch];
   int count;
 };
-// D[r, l] = a0 Q_s[r, l] + w_obs obs[r] delta_rl - c (W Q_s)[r, l], identity on padding.
-void launch_schur_assemble(cudaStream_t s, const SchurBatch &b, const SellPattern &pat,
+template <typename T>
+void launch_schur_assemble(cudaStream_t s, const SchurBatch<T> &b, const SellPattern &pat,
                            const double *qs, double obs_w, int n_s, int n_pad);
 
+template <typename T>
 struct ExtractEntry {
-  const double *S;          // n_pad x n_pad dense
+  const T *S;               // n_pad x n_pad dense
   double *diag_out;         // n_s outputs (null: skip)
   double *sums;             // 2 outputs: <dQs, S>_pattern, <Qs, S>_pattern (null: skip)
+  // optional FP64 diagonal: when D0 is set, diag_out gets
+  // D0[i,i] + sum_l D0[i,l] V[l,i] accumulated in double instead of S[i,i]
+  const T *D0, *V;
 };
+template <typename T>
 struct ExtractBatch {
-  ExtractEntry e[kMaxBatch];
+  ExtractEntry<T> e[kMaxBatch];
   int count;
 };
-void launch_extract(cudaStream_t s, const ExtractBatch &b, const SellPattern &pat, const double *qs,
-                    const double *dqs, int n_s, int n_pad);
+// diag_scratch: extract_scratch_bytes(n_pad) bytes of device memory (used when
+// an entry sets D0).
+size_t extract_scratch_bytes(int n_pad);
+template <typename T>
+void launch_extract(cudaStream_t s, const ExtractBatch<T> &b, const SellPattern &pat, const double *qs,
+                    const double *dqs, int n_s, int n_pad, double *diag_scratch);
 
 // ---------------------------------------------------------------- rbmc.cu
+template <typename T>
 struct CorrEntry {
-  const double *w;          // T x n_pad x ld samples of the subdomain correction
-  int T, lo, hi, e0;        // local own range [lo, hi], global slab of local 0
-  double *diag_out;         // global diag output (rows of own slabs added)
+  const T *w;               // T_ x n_pad x ld samples of the subdomain correction
+  int T_, lo, hi, e0;       // slabs, local own range [lo, hi], global slab of local 0
+  double *corr_out;         // global correction output (own rows written)
   double *partial;          // per-CTA trace partials (3 per CTA)
 };
+template <typename T>
 struct CorrBatch {
-  CorrEntry e[kMaxBatch];
+  CorrEntry<T> e[kMaxBatch];
   int count;
 };
 int corr_grid();
-void launch_correction_terms(cudaStream_t s, const CorrBatch &b, const SellPattern &pat,
+template <typename T>
+void launch_correction_terms(cudaStream_t s, const CorrBatch<T> &b, const SellPattern &pat,
                              const double *qs, const double *dqs, const double *a0, const double *a1,
                              const double *r0, const double *r1, int n_s, int n_pad, int ld, int k);
-// Final traces: combines the selected-inverse pattern sums and the correction
-// partials into 3 doubles.
 struct TraceSlab {
   int t;            // global slab of the row block
   int sd, sy, sym;  // indices into sums: Sigma_tt, Y_t (pair t,t+1), Y_{t-1} (pair t-1,t); -1 = absent
@@ -205,7 +248,9 @@ struct TraceSlab {
 void launch_trace_combine(cudaStream_t s, const TraceSlab *slabs_dev, int n_slabs, const double *sums,
                           const double *partials, int n_partials, const double *a0, const double *a1,
                           const double *r0, const double *r1, double *out3);
-void launch_add(cudaStream_t s, double *y, const double *x, int n);
-void launch_scale_copy(cudaStream_t s, double *dst, const double *src, int n, double scale);
+template <typename T>
+void launch_add(cudaStream_t s, T *y, const T *x, int64_t n);
+// out = a + b (n doubles)
+void launch_sum(cudaStream_t s, double *out, const double *a, const double *b, int n);
 
 }  // namespace qsel

@@ -101,7 +101,7 @@ extern "C" qsel_status qsel_spd_inverse_noalloc(double *a_dev, int32_t n, int32_
   const int n_pad = round_up(n, kTile);
   double *A = base;
   int32_t *flag = reinterpret_cast<int32_t *>(base + kFlagOff);
-  SweepBatch b{};
+  SweepBatch<double> b{};
   b.count = 1;
   b.e[0].A = A;
   b.e[0].P = base + kPadMat;

@@ -19,7 +19,8 @@ constexpr int kCorrGrid = 152 * 2;
 
 int corr_grid() { return kCorrGrid; }
 
-__global__ void __launch_bounds__(256) k_correction_terms(CorrBatch bt, SellPattern pat,
+template <typename T>
+__global__ void __launch_bounds__(256) k_correction_terms(CorrBatch<T> bt, SellPattern pat,
                                                           const double *__restrict__ qs,
                                                           const double *__restrict__ dqs,
                                                           const double *__restrict__ a0,
@@ -28,7 +29,7 @@ __global__ void __launch_bounds__(256) k_correction_terms(CorrBatch bt, SellPatt
                                                           const double *__restrict__ r1, int n_s,
                                                           int n_pad, int ld, int k) {
   __shared__ double red[8][3];
-  const CorrEntry e = bt.e[blockIdx.y];
+  const CorrEntry<T> e = bt.e[blockIdx.y];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double inv_k = 1.0 / (double)k;
   const int n_own = (e.hi - e.lo + 1) * n_s;
@@ -38,30 +39,30 @@ __global__ void __launch_bounds__(256) k_correction_terms(CorrBatch bt, SellPatt
     const int tl = e.lo + item / n_s;      // local slab
     const int i = item - (item / n_s) * n_s;
     const int t = e.e0 + tl;               // global slab
-    const bool has_m = tl > 0, has_p = tl + 1 < e.T;
+    const bool has_m = tl > 0, has_p = tl + 1 < e.T_;
     const double ea[3] = {has_m ? a1[t - 1] : 0.0, a0[t], has_p ? a1[t] : 0.0};
     const double er[3] = {has_m ? r1[t - 1] : 0.0, r0[t], has_p ? r1[t] : 0.0};
     const int sl = i >> 5, li = i & 31;
     const int w = pat.slice_width[sl];
     const int base = pat.slice_ptr[sl] + li;
-    const double *wrow = e.w + tl * slab + (int64_t)i * ld;
+    const T *wrow = e.w + tl * slab + (int64_t)i * ld;
     double sq = 0.0, p0 = 0.0, p1 = 0.0, p2 = 0.0;
     for (int c = lane; c < ld; c += 32) {
       double g0 = 0.0, g1 = 0.0, g2 = 0.0;
       for (int s = 0; s < w; ++s) {
         const int j = pat.col[base + s * kSlice];
         const double vq = qs[base + s * kSlice], vd = dqs[base + s * kSlice];
-        const double *wc = e.w + tl * slab + (int64_t)j * ld + c;
-        const double x0 = wc[0];
-        const double xm = has_m ? wc[-slab] : 0.0;
-        const double xp = has_p ? wc[slab] : 0.0;
+        const T *wc = e.w + tl * slab + (int64_t)j * ld + c;
+        const double x0 = (double)wc[0];
+        const double xm = has_m ? (double)wc[-slab] : 0.0;
+        const double xp = has_p ? (double)wc[slab] : 0.0;
         const double za = ea[0] * xm + ea[1] * x0 + ea[2] * xp;
         const double zr = er[0] * xm + er[1] * x0 + er[2] * xp;
         g0 = fma(vd, za, g0);
         g1 = fma(vq, za, g1);
         g2 = fma(vq, zr, g2);
       }
-      const double wi = wrow[c];
+      const double wi = (double)wrow[c];
       sq = fma(wi, wi, sq);
       p0 = fma(wi, g0, p0);
       p1 = fma(wi, g1, p1);
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(256) k_correction_terms(CorrBatch bt, SellPatt
       p2 += __shfl_down_sync(0xffffffffu, p2, o);
     }
     if (lane == 0) {
-      e.diag_out[(int64_t)t * n_s + i] += sq * inv_k;
+      e.corr_out[(int64_t)t * n_s + i] = sq * inv_k;
       tr0 += p0;
       tr1 += p1;
       tr2 += p2;
@@ -93,14 +94,21 @@ __global__ void __launch_bounds__(256) k_correction_terms(CorrBatch bt, SellPatt
   }
 }
 
-void launch_correction_terms(cudaStream_t s, const CorrBatch &b, const SellPattern &pat,
+template <typename T>
+void launch_correction_terms(cudaStream_t s, const CorrBatch<T> &b, const SellPattern &pat,
                              const double *qs, const double *dqs, const double *a0, const double *a1,
                              const double *r0, const double *r1, int n_s, int n_pad, int ld, int k) {
   if (b.count <= 0) return;
   ++g_launch_count;
-  k_correction_terms<<<dim3(kCorrGrid, b.count), 256, 0, s>>>(b, pat, qs, dqs, a0, a1, r0, r1, n_s,
-                                                              n_pad, ld, k);
+  k_correction_terms<T><<<dim3(kCorrGrid, b.count), 256, 0, s>>>(b, pat, qs, dqs, a0, a1, r0, r1, n_s,
+                                                                 n_pad, ld, k);
 }
+template void launch_correction_terms<double>(cudaStream_t, const CorrBatch<double> &, const SellPattern &,
+                                              const double *, const double *, const double *, const double *,
+                                              const double *, const double *, int, int, int, int);
+template void launch_correction_terms<float>(cudaStream_t, const CorrBatch<float> &, const SellPattern &,
+                                             const double *, const double *, const double *, const double *,
+                                             const double *, const double *, int, int, int, int);
 
 // tr_j = sum over own row slabs t of
 //   e_j(t,0) <M_j, Sigma_tt> - e_j(t,+1) <M_j, Y_t> - e_j(t,-1) <M_j, Y_{t-1}>
@@ -151,30 +159,33 @@ void launch_trace_combine(cudaStream_t s, const TraceSlab *slabs_dev, int n_slab
                                    out3);
 }
 
-__global__ void k_add(double *__restrict__ y, const double *__restrict__ x, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] += x[i];
+template <typename T>
+__global__ void k_add(T *__restrict__ y, const T *__restrict__ x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += x[i];
 }
 
-void launch_add(cudaStream_t s, double *y, const double *x, int n) {
+template <typename T>
+void launch_add(cudaStream_t s, T *y, const T *x, int64_t n) {
+  if (n <= 0) return;
+  ++g_launch_count;
+  int64_t grid = (n + 255) / 256;
+  if (grid > 152 * 8) grid = 152 * 8;
+  k_add<T><<<(int)grid, 256, 0, s>>>(y, x, n);
+}
+template void launch_add<double>(cudaStream_t, double *, const double *, int64_t);
+template void launch_add<float>(cudaStream_t, float *, const float *, int64_t);
+
+__global__ void k_sum(double *__restrict__ out, const double *__restrict__ a, const double *__restrict__ b, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = a[i] + b[i];
+}
+
+void launch_sum(cudaStream_t s, double *out, const double *a, const double *b, int n) {
   if (n <= 0) return;
   ++g_launch_count;
   int grid = (n + 255) / 256;
   if (grid > 152 * 8) grid = 152 * 8;
-  k_add<<<grid, 256, 0, s>>>(y, x, n);
-}
-
-__global__ void k_scale_copy(double *__restrict__ dst, const double *__restrict__ src, int n,
-                             double scale) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    dst[i] = scale * src[i];
-}
-
-void launch_scale_copy(cudaStream_t s, double *dst, const double *src, int n, double scale) {
-  if (n <= 0) return;
-  ++g_launch_count;
-  int grid = (n + 255) / 256;
-  if (grid > 152 * 8) grid = 152 * 8;
-  k_scale_copy<<<grid, 256, 0, s>>>(dst, src, n, scale);
+  k_sum<<<grid, 256, 0, s>>>(out, a, b, n);
 }
 
 }  // namespace qsel

@@ -120,14 +120,38 @@ void launch_perturbation_rhs(cudaStream_t s, const SellPattern &pat, const doubl
                                           inv_sigma, r);
 }
 
+// Two adjacent elements of T (16 bytes for double, 8 for float).
+template <typename T>
+struct Pair;
+template <>
+struct Pair<double> {
+  using V = double2;
+};
+template <>
+struct Pair<float> {
+  using V = float2;
+};
+
+template <typename T>
+__device__ __forceinline__ typename Pair<T>::V load2(const T *p) {
+  return *reinterpret_cast<const typename Pair<T>::V *>(p);
+}
+template <typename T>
+__device__ __forceinline__ void store2(T *p, T a, T b) {
+  typename Pair<T>::V v;
+  v.x = a;
+  v.y = b;
+  *reinterpret_cast<typename Pair<T>::V *>(p) = v;
+}
+
 // ---------------------------------------------------------------------------
 // Block-tridiagonal sliced-ELL SpMM over many right-hand sides:
 //   y_t = sum_{d=-1,0,1} c_{t,t+d} (V x_{t+d}) + w_obs diag(obs_t) x_t
 // where V is the spatial matrix on the SELL-32 pattern (Q_s here) and the
-// c's are the per-slab time coefficients.  One warp per (row, 64*V2-column
+// c's are the per-slab time coefficients.  One warp per (row, 64*NV-column
 // chunk); column index and value are warp-uniform broadcasts, the three
-// neighbour rows are read as coalesced double2 vectors.  Optional epilogue:
-// per-CTA, per-column partial sums of x .* y (the PCG curvature <p, Q p>).
+// neighbour rows are read as coalesced 2-element vectors.  Optional epilogue:
+// per-CTA, per-column partial sums of x .* y in double (the PCG curvature).
 // ---------------------------------------------------------------------------
 constexpr int kSpmmGridMax = 152 * 8;
 
@@ -136,13 +160,13 @@ int bt_spmm_grid(int n_rows) {
   return g < kSpmmGridMax ? (g < 1 ? 1 : g) : kSpmmGridMax;
 }
 
-template <int V2>
-__global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs a) {
+template <typename T, int NV>
+__global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs<T> a) {
   __shared__ double red[8][512];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_rows = a.n_s * a.n_t;
   const int ld = a.ld;
-  const int chunk_cols = 64 * V2;
+  const int chunk_cols = 64 * NV;
   const int nchunk = ld / chunk_cols;
   const bool dot = a.dot_partial != nullptr;
   if (dot) {
@@ -161,52 +185,56 @@ __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs a) {
     const double cm = (t > 0) ? a.c1[t - 1] : 0.0;
     const double cp = (t + 1 < a.n_t) ? a.c1[t] : 0.0;
     const int coff = ch * chunk_cols + 2 * lane;
-    double2 acc[V2];
+    T ax[NV], ay[NV];
 #pragma unroll
-    for (int v = 0; v < V2; ++v) acc[v] = make_double2(0.0, 0.0);
+    for (int v = 0; v < NV; ++v) ax[v] = ay[v] = T(0);
     for (int s = 0; s < w; ++s) {
       const int j = a.pat.col[base + s * kSlice];
       const double val = a.val[base + s * kSlice];
-      const double *xc = a.x + ((int64_t)t * a.n_s + j) * ld + coff;
-      const double f0 = c0 * val;
+      const T *xc = a.x + ((int64_t)t * a.n_s + j) * ld + coff;
+      const T f0 = (T)(c0 * val);
 #pragma unroll
-      for (int v = 0; v < V2; ++v) {
-        const double2 xv = *reinterpret_cast<const double2 *>(xc + 64 * v);
-        acc[v].x = fma(f0, xv.x, acc[v].x);
-        acc[v].y = fma(f0, xv.y, acc[v].y);
+      for (int v = 0; v < NV; ++v) {
+        const auto xv = load2(xc + 64 * v);
+        ax[v] = fma(f0, xv.x, ax[v]);
+        ay[v] = fma(f0, xv.y, ay[v]);
       }
       if (t > 0) {
-        const double fm = cm * val;
+        const T fm = (T)(cm * val);
 #pragma unroll
-        for (int v = 0; v < V2; ++v) {
-          const double2 xv = *reinterpret_cast<const double2 *>(xc - slab + 64 * v);
-          acc[v].x = fma(fm, xv.x, acc[v].x);
-          acc[v].y = fma(fm, xv.y, acc[v].y);
+        for (int v = 0; v < NV; ++v) {
+          const auto xv = load2(xc - slab + 64 * v);
+          ax[v] = fma(fm, xv.x, ax[v]);
+          ay[v] = fma(fm, xv.y, ay[v]);
         }
       }
       if (t + 1 < a.n_t) {
-        const double fp = cp * val;
+        const T fp = (T)(cp * val);
 #pragma unroll
-        for (int v = 0; v < V2; ++v) {
-          const double2 xv = *reinterpret_cast<const double2 *>(xc + slab + 64 * v);
-          acc[v].x = fma(fp, xv.x, acc[v].x);
-          acc[v].y = fma(fp, xv.y, acc[v].y);
+        for (int v = 0; v < NV; ++v) {
+          const auto xv = load2(xc + slab + 64 * v);
+          ax[v] = fma(fp, xv.x, ax[v]);
+          ay[v] = fma(fp, xv.y, ay[v]);
         }
       }
     }
-    const double *xr = a.x + (int64_t)row * ld + coff;
-    const double ow = (a.obs != nullptr && a.obs[row]) ? a.obs_w : 0.0;
-    double *yr = a.y + (int64_t)row * ld + coff;
+    const T *xr = a.x + (int64_t)row * ld + coff;
+    const T ow = (a.obs != nullptr && a.obs[row]) ? (T)a.obs_w : T(0);
+    T *yr = a.y + (int64_t)row * ld + coff;
 #pragma unroll
-    for (int v = 0; v < V2; ++v) {
-      double2 xv = make_double2(0.0, 0.0);
-      if (ow != 0.0 || dot) xv = *reinterpret_cast<const double2 *>(xr + 64 * v);
-      acc[v].x = fma(ow, xv.x, acc[v].x);
-      acc[v].y = fma(ow, xv.y, acc[v].y);
-      *reinterpret_cast<double2 *>(yr + 64 * v) = acc[v];
+    for (int v = 0; v < NV; ++v) {
+      T x0 = T(0), x1 = T(0);
+      if (ow != T(0) || dot) {
+        const auto xv = load2(xr + 64 * v);
+        x0 = xv.x;
+        x1 = xv.y;
+      }
+      ax[v] = fma(ow, x0, ax[v]);
+      ay[v] = fma(ow, x1, ay[v]);
+      store2(yr + 64 * v, ax[v], ay[v]);
       if (dot) {
-        red[warp][coff + 64 * v] += xv.x * acc[v].x;
-        red[warp][coff + 64 * v + 1] += xv.y * acc[v].y;
+        red[warp][coff + 64 * v] += (double)x0 * (double)ax[v];
+        red[warp][coff + 64 * v + 1] += (double)x1 * (double)ay[v];
       }
     }
   }
@@ -221,36 +249,40 @@ __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs a) {
   }
 }
 
-void launch_bt_spmm(cudaStream_t s, const BtSpmmArgs &a) {
+template <typename T>
+void launch_bt_spmm(cudaStream_t s, const BtSpmmArgs<T> &a) {
   ++g_launch_count;
   const int grid = bt_spmm_grid(a.n_s * a.n_t);
   Profiler::Rec rec{PROF_SPMM, nullptr, nullptr, 0.0};
   if (g_prof) {
     // algorithmic bytes: read x once, write y once (the spatial pattern and the
     // neighbouring rows are re-read from cache)
-    rec.work = 2.0 * (double)a.n_s * a.n_t * a.ld * sizeof(double);
+    rec.work = 2.0 * (double)a.n_s * a.n_t * a.ld * sizeof(T);
     g_prof->begin(s, rec);
   }
   if (a.ld % 256 == 0)
-    k_bt_spmm<4><<<grid, 256, 0, s>>>(a);
+    k_bt_spmm<T, 4><<<grid, 256, 0, s>>>(a);
   else if (a.ld % 128 == 0)
-    k_bt_spmm<2><<<grid, 256, 0, s>>>(a);
+    k_bt_spmm<T, 2><<<grid, 256, 0, s>>>(a);
   else
-    k_bt_spmm<1><<<grid, 256, 0, s>>>(a);
+    k_bt_spmm<T, 1><<<grid, 256, 0, s>>>(a);
   if (g_prof) g_prof->end(s, rec);
 }
+template void launch_bt_spmm<double>(cudaStream_t, const BtSpmmArgs<double> &);
+template void launch_bt_spmm<float>(cudaStream_t, const BtSpmmArgs<float> &);
 
 // ---------------------------------------------------------------------------
 // Block-Jacobi preconditioner (Section 3.3 names block-Jacobi / IC(0)):
 // contiguous blocks of b global rows; P_blk = (Q_blk)^-1 by the symmetric
-// sweep in shared memory.  Rows past n are padded with the identity.
+// sweep in shared memory (double).  Rows past n are padded with the identity.
 // ---------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(256) k_jacobi_setup(SellPattern pat, const double *__restrict__ qs,
                                                       const double *__restrict__ a0,
                                                       const double *__restrict__ a1,
                                                       const uint8_t *__restrict__ obs, double obs_w,
-                                                      int n_s, int n_t, int b,
-                                                      double *__restrict__ pblk, int32_t *err_flag) {
+                                                      int n_s, int n_t, int b, T *__restrict__ pblk,
+                                                      int32_t *err_flag) {
   __shared__ double S[64 * 65];
   const int n = n_s * n_t;
   const int r0 = blockIdx.x * b;
@@ -282,96 +314,113 @@ __global__ void __launch_bounds__(256) k_jacobi_setup(SellPattern pat, const dou
   }
   __syncthreads();
   sym_sweep_inverse_smem(S, 65, b, err_flag);
-  double *P = pblk + (int64_t)blockIdx.x * b * b;
+  T *P = pblk + (int64_t)blockIdx.x * b * b;
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int i = e / b, j = e - (e / b) * b;
-    P[e] = -S[i * 65 + j];
+    P[e] = (T)(-S[i * 65 + j]);
   }
 }
 
+template <typename T>
 void launch_jacobi_setup(cudaStream_t s, const SellPattern &pat, const double *qs, const double *a0,
                          const double *a1, const uint8_t *obs, double obs_w, int n_s, int n_t,
-                         int bsize, double *pblk, int32_t *err_flag) {
+                         int bsize, T *pblk, int32_t *err_flag) {
   ++g_launch_count;
   const int n = n_s * n_t;
   const int nblk = (n + bsize - 1) / bsize;
-  k_jacobi_setup<<<nblk, bsize >= 16 ? 256 : 32, 0, s>>>(pat, qs, a0, a1, obs, obs_w, n_s, n_t,
-                                                         bsize, pblk, err_flag);
+  k_jacobi_setup<T><<<nblk, bsize >= 16 ? 256 : 32, 0, s>>>(pat, qs, a0, a1, obs, obs_w, n_s, n_t,
+                                                            bsize, pblk, err_flag);
 }
+template void launch_jacobi_setup<double>(cudaStream_t, const SellPattern &, const double *, const double *,
+                                          const double *, const uint8_t *, double, int, int, int, double *,
+                                          int32_t *);
+template void launch_jacobi_setup<float>(cudaStream_t, const SellPattern &, const double *, const double *,
+                                         const double *, const uint8_t *, double, int, int, int, float *,
+                                         int32_t *);
 
 // ---------------------------------------------------------------------------
 // PCG update for a 64-row tile: x += alpha p, r -= alpha q, z = P r (block
-// Jacobi), and per-column partial sums <r, z>, <r, r>.
+// Jacobi), and per-column partial sums <r, z>, <r, r> in double.
 // ---------------------------------------------------------------------------
-constexpr int kPcgUpdateSmem = (64 * 65 + 64 * 64 + 2 * 4 * 64) * (int)sizeof(double);
+template <typename T>
+constexpr int pcg_update_smem() {
+  return (64 * 65 + 64 * 64) * (int)sizeof(T) + 2 * 4 * 64 * (int)sizeof(double);
+}
 
-__global__ void __launch_bounds__(256) k_pcg_update(PcgVec v, const double *__restrict__ pblk, int b) {
-  extern __shared__ double smem_upd[];
-  double (*rs)[65] = reinterpret_cast<double (*)[65]>(smem_upd);
-  double *Ps = smem_upd + 64 * 65;
-  double (*red_a)[64] = reinterpret_cast<double (*)[64]>(Ps + 64 * 64);
-  double (*red_b)[64] = reinterpret_cast<double (*)[64]>(Ps + 64 * 64 + 4 * 64);
+template <typename T>
+__global__ void __launch_bounds__(256) k_pcg_update(PcgVec<T> v, const T *__restrict__ pblk, int b) {
+  extern __shared__ __align__(16) unsigned char smem_upd_raw[];
+  double *red_a = reinterpret_cast<double *>(smem_upd_raw);     // [4][64]
+  double *red_b = red_a + 4 * 64;                               // [4][64]
+  T *rs = reinterpret_cast<T *>(red_b + 4 * 64);                // [64][65]
+  T *Ps = rs + 64 * 65;                                         // [64 * b]
   const int r0 = blockIdx.x * 64;
   const int rows = min(64, v.n - r0);
   const int n_blocks = (v.n + b - 1) / b;
   {
     const int64_t base = (int64_t)(r0 / b) * b * b;
     const int64_t lim = (int64_t)n_blocks * b * b;
-    for (int e = threadIdx.x; e < 64 * b; e += blockDim.x)
-      Ps[e] = (base + e < lim) ? pblk[base + e] : 0.0;
+    for (int e = threadIdx.x; e < 64 * b; e += blockDim.x) Ps[e] = (base + e < lim) ? pblk[base + e] : T(0);
   }
   const int lc = threadIdx.x & 63, rg = threadIdx.x >> 6;
   for (int c0 = 0; c0 < v.ld; c0 += 64) {
     const int col = c0 + lc;
-    const double al = v.alpha[col];
+    const T al = (T)v.alpha[col];
     for (int rr = rg; rr < 64; rr += 4) {
-      double rv = 0.0;
+      T rv = T(0);
       if (rr < rows) {
         const int64_t idx = (int64_t)(r0 + rr) * v.ld + col;
         rv = v.r[idx];
-        if (al != 0.0) {
+        if (al != T(0)) {
           v.x[idx] = fma(al, v.p[idx], v.x[idx]);
           rv = fma(-al, v.q[idx], rv);
           v.r[idx] = rv;
         }
       }
-      rs[rr][lc] = rv;
+      rs[rr * 65 + lc] = rv;
     }
     __syncthreads();
     double sa = 0.0, sb = 0.0;
     for (int rr = rg; rr < rows; rr += 4) {
       const int blk = rr / b, bo = rr - blk * b;
-      const double *Pr = Ps + blk * b * b + bo * b;
+      const T *Pr = Ps + blk * b * b + bo * b;
       const int rb = blk * b;
-      double z = 0.0;
-      for (int jj = 0; jj < b; ++jj) z = fma(Pr[jj], rs[rb + jj][lc], z);
+      T z = T(0);
+      for (int jj = 0; jj < b; ++jj) z = fma(Pr[jj], rs[(rb + jj) * 65 + lc], z);
       v.z[(int64_t)(r0 + rr) * v.ld + col] = z;
-      sa = fma(rs[rr][lc], z, sa);
-      sb = fma(rs[rr][lc], rs[rr][lc], sb);
+      const double rd = (double)rs[rr * 65 + lc];
+      sa = fma(rd, (double)z, sa);
+      sb = fma(rd, rd, sb);
     }
-    red_a[rg][lc] = sa;
-    red_b[rg][lc] = sb;
+    red_a[rg * 64 + lc] = sa;
+    red_b[rg * 64 + lc] = sb;
     __syncthreads();
     if (rg == 0) {
-      v.partial_a[(int64_t)blockIdx.x * v.ld + col] = red_a[0][lc] + red_a[1][lc] + red_a[2][lc] + red_a[3][lc];
-      v.partial_b[(int64_t)blockIdx.x * v.ld + col] = red_b[0][lc] + red_b[1][lc] + red_b[2][lc] + red_b[3][lc];
+      v.partial_a[(int64_t)blockIdx.x * v.ld + col] =
+          red_a[lc] + red_a[64 + lc] + red_a[128 + lc] + red_a[192 + lc];
+      v.partial_b[(int64_t)blockIdx.x * v.ld + col] =
+          red_b[lc] + red_b[64 + lc] + red_b[128 + lc] + red_b[192 + lc];
     }
     __syncthreads();
   }
 }
 
-void launch_pcg_update(cudaStream_t s, const PcgVec &v, const double *pblk, int bsize) {
+template <typename T>
+void launch_pcg_update(cudaStream_t s, const PcgVec<T> &v, const T *pblk, int bsize) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_pcg_update, cudaFuncAttributeMaxDynamicSharedMemorySize, kPcgUpdateSmem);
+    cudaFuncSetAttribute(k_pcg_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, pcg_update_smem<T>());
     attr_set = true;
   }
   ++g_launch_count;
-  k_pcg_update<<<v.n_tiles, 256, kPcgUpdateSmem, s>>>(v, pblk, bsize);
+  k_pcg_update<T><<<v.n_tiles, 256, pcg_update_smem<T>(), s>>>(v, pblk, bsize);
 }
+template void launch_pcg_update<double>(cudaStream_t, const PcgVec<double> &, const double *, int);
+template void launch_pcg_update<float>(cudaStream_t, const PcgVec<float> &, const float *, int);
 
 // alpha_c = rho_c / <p_c, q_c> for active columns, 0 otherwise.
-__global__ void k_pcg_reduce_alpha(PcgVec v) {
+template <typename T>
+__global__ void k_pcg_reduce_alpha(PcgVec<T> v) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= v.ld) return;
   double pq = 0.0;
@@ -379,14 +428,18 @@ __global__ void k_pcg_reduce_alpha(PcgVec v) {
   v.alpha[c] = (v.active[c] && pq != 0.0) ? v.rho[c] / pq : 0.0;
 }
 
-void launch_pcg_reduce_alpha(cudaStream_t s, const PcgVec &v) {
+template <typename T>
+void launch_pcg_reduce_alpha(cudaStream_t s, const PcgVec<T> &v) {
   ++g_launch_count;
-  k_pcg_reduce_alpha<<<(v.ld + 127) / 128, 128, 0, s>>>(v);
+  k_pcg_reduce_alpha<T><<<(v.ld + 127) / 128, 128, 0, s>>>(v);
 }
+template void launch_pcg_reduce_alpha<double>(cudaStream_t, const PcgVec<double> &);
+template void launch_pcg_reduce_alpha<float>(cudaStream_t, const PcgVec<float> &);
 
 // <r, z>, <r, r> -> beta, rho, convergence flags, active count and the
 // maximum relative residual (single block, ld <= 1024 threads).
-__global__ void k_pcg_reduce_beta(PcgVec v, double tol2, int init) {
+template <typename T>
+__global__ void k_pcg_reduce_beta(PcgVec<T> v, double tol2, int init) {
   __shared__ int cnt[32];
   __shared__ double mx[32];
   const int c = threadIdx.x;
@@ -435,33 +488,142 @@ __global__ void k_pcg_reduce_beta(PcgVec v, double tol2, int init) {
   }
 }
 
-void launch_pcg_reduce_beta(cudaStream_t s, const PcgVec &v, double tol, int init) {
+template <typename T>
+void launch_pcg_reduce_beta(cudaStream_t s, const PcgVec<T> &v, double tol, int init) {
   ++g_launch_count;
   int threads = (v.ld + 31) / 32 * 32;
-  k_pcg_reduce_beta<<<1, threads, 0, s>>>(v, tol * tol, init);
+  k_pcg_reduce_beta<T><<<1, threads, 0, s>>>(v, tol * tol, init);
 }
+template void launch_pcg_reduce_beta<double>(cudaStream_t, const PcgVec<double> &, double, int);
+template void launch_pcg_reduce_beta<float>(cudaStream_t, const PcgVec<float> &, double, int);
 
 // p = z + beta p  (p = z where beta is zero, so stale values never leak in).
-__global__ void k_pcg_p_update(PcgVec v) {
+template <typename T>
+__global__ void k_pcg_p_update(PcgVec<T> v) {
   const int64_t total = (int64_t)v.n * v.ld;
   for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 2; e < total;
        e += (int64_t)gridDim.x * blockDim.x * 2) {
     const int c = (int)(e % v.ld);
-    const double2 z = *reinterpret_cast<const double2 *>(v.z + e);
-    double2 p = *reinterpret_cast<const double2 *>(v.p + e);
-    const double b0 = v.beta[c], b1 = v.beta[c + 1];
-    p.x = (b0 != 0.0) ? fma(b0, p.x, z.x) : z.x;
-    p.y = (b1 != 0.0) ? fma(b1, p.y, z.y) : z.y;
-    *reinterpret_cast<double2 *>(v.p + e) = p;
+    const auto z = load2(v.z + e);
+    auto p = load2(v.p + e);
+    const T b0 = (T)v.beta[c], b1 = (T)v.beta[c + 1];
+    const T p0 = (b0 != T(0)) ? fma(b0, p.x, z.x) : z.x;
+    const T p1 = (b1 != T(0)) ? fma(b1, p.y, z.y) : z.y;
+    store2(v.p + e, p0, p1);
   }
 }
 
-void launch_pcg_p_update(cudaStream_t s, const PcgVec &v) {
+template <typename T>
+void launch_pcg_p_update(cudaStream_t s, const PcgVec<T> &v) {
   ++g_launch_count;
   int64_t total = (int64_t)v.n * v.ld / 2;
   int grid = (int)((total + 255) / 256);
   if (grid > 152 * 16) grid = 152 * 16;
-  k_pcg_p_update<<<grid, 256, 0, s>>>(v);
+  k_pcg_p_update<T><<<grid, 256, 0, s>>>(v);
+}
+template void launch_pcg_p_update<double>(cudaStream_t, const PcgVec<double> &);
+template void launch_pcg_p_update<float>(cudaStream_t, const PcgVec<float> &);
+
+// ---------------------------------------------------------------------------
+// Iterative refinement of the FP32 solves (mixed precision): the true
+// residual r = b - Q x is formed in double, its FP32 copy is the right-hand
+// side of the next inner solve, and the FP32 correction is added in double.
+// ---------------------------------------------------------------------------
+constexpr int kResGrid = 152 * 4;
+
+int residual_grid(int n) {
+  int g = (n + 63) / 64;
+  return g < kResGrid ? g : kResGrid;
+}
+
+__global__ void __launch_bounds__(256) k_residual(const double *__restrict__ b, const double *__restrict__ y,
+                                                  double *__restrict__ r, float *__restrict__ r32, int n,
+                                                  int ld, double *__restrict__ prr, double *__restrict__ pbb) {
+  __shared__ double sr[4][64], sbb[4][64];
+  const int lc = threadIdx.x & 63, rg = threadIdx.x >> 6;
+  for (int c0 = 0; c0 < ld; c0 += 64) {
+    const int col = c0 + lc;
+    double a = 0.0, bsum = 0.0;
+    for (int row = blockIdx.x * 4 + rg; row < n; row += gridDim.x * 4) {
+      const int64_t idx = (int64_t)row * ld + col;
+      const double bv = b[idx];
+      const double rv = bv - y[idx];
+      r[idx] = rv;
+      r32[idx] = (float)rv;
+      a = fma(rv, rv, a);
+      bsum = fma(bv, bv, bsum);
+    }
+    sr[rg][lc] = a;
+    sbb[rg][lc] = bsum;
+    __syncthreads();
+    if (rg == 0) {
+      prr[(int64_t)blockIdx.x * ld + col] = sr[0][lc] + sr[1][lc] + sr[2][lc] + sr[3][lc];
+      pbb[(int64_t)blockIdx.x * ld + col] = sbb[0][lc] + sbb[1][lc] + sbb[2][lc] + sbb[3][lc];
+    }
+    __syncthreads();
+  }
+}
+
+void launch_residual(cudaStream_t s, const double *b, const double *y, double *r, float *r32, int n,
+                     int ld, double *partial_rr, double *partial_bb) {
+  ++g_launch_count;
+  k_residual<<<residual_grid(n), 256, 0, s>>>(b, y, r, r32, n, ld, partial_rr, partial_bb);
+}
+
+__global__ void k_residual_check(const double *__restrict__ prr, const double *__restrict__ pbb,
+                                 int n_parts, int ld, double tol2, int32_t *counters, double *max_rel) {
+  __shared__ int cnt[32];
+  __shared__ double mx[32];
+  const int c = threadIdx.x;
+  int bad = 0;
+  double rel = 0.0;
+  if (c < ld) {
+    double rr = 0.0, bb = 0.0;
+    for (int g = 0; g < n_parts; ++g) {
+      rr += prr[(int64_t)g * ld + c];
+      bb += pbb[(int64_t)g * ld + c];
+    }
+    bad = (rr > tol2 * bb) ? 1 : 0;
+    rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    bad += __shfl_down_sync(0xffffffffu, bad, o);
+    rel = fmax(rel, __shfl_down_sync(0xffffffffu, rel, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    cnt[threadIdx.x >> 5] = bad;
+    mx[threadIdx.x >> 5] = rel;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0;
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += cnt[w];
+      m = fmax(m, mx[w]);
+    }
+    counters[0] = a;
+    max_rel[0] = m;
+  }
+}
+
+void launch_residual_check(cudaStream_t s, const double *partial_rr, const double *partial_bb, int n_parts,
+                           int ld, double tol, int32_t *counters, double *max_rel) {
+  ++g_launch_count;
+  k_residual_check<<<1, (ld + 31) / 32 * 32, 0, s>>>(partial_rr, partial_bb, n_parts, ld, tol * tol, counters,
+                                                     max_rel);
+}
+
+__global__ void k_accumulate(double *__restrict__ x, const float *__restrict__ d, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)d[i];
+}
+
+void launch_accumulate(cudaStream_t s, double *x, const float *d, int64_t count) {
+  ++g_launch_count;
+  int64_t grid = (count + 255) / 256;
+  if (grid > 152 * 16) grid = 152 * 16;
+  k_accumulate<<<(int)grid, 256, 0, s>>>(x, d, count);
 }
 
 }  // namespace qsel

@@ -1,0 +1,66 @@
+"""Mixed-precision path (FP32 PCG with FP64 refinement, FP32 dense tiles with
+FP64 pivot tiles and FP64 diagonal accumulation) against the FP64 path and
+the oracle.
+
+Stated per-result tolerances (relative, against the FP64 run of the same
+seed): MIXED_DIAG_TOL for every node of diag(Q^-1) and MIXED_TRACE_TOL for
+each trace gradient.  The sampler is held to the same FP64 residual criterion
+as the FP64 path (the refinement residual is formed in double).
+"""
+import numpy as np
+import pytest
+
+import qsel_inputs as qi
+from oracle import qsel_oracle as o
+from tests.test_gpu_parity import CASES, Case, q  # noqa: F401  (fixture)
+
+pytestmark = pytest.mark.gpu
+
+MIXED_DIAG_TOL = 1e-4
+MIXED_TRACE_TOL = 1e-4
+
+
+def rel(a, b):
+    return np.max(np.abs(a - b) / np.abs(b))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_matches_fp64_same_seed(q, name):
+    c64 = Case(q, name, precision=q.QSEL_FP64)
+    c32 = Case(q, name, precision=q.QSEL_MIXED)
+    v64, t64 = c64.ctx.diag_inv(), c64.ctx.trace_grads()
+    v32, t32 = c32.ctx.diag_inv(), c32.ctx.trace_grads()
+    e_v, e_t = rel(v32, v64), rel(t32, t64)
+    print(f"{name}: mixed vs FP64 diag {e_v:.2e} traces {e_t:.2e}; "
+          f"PCG iters fp64 {c64.ctx.stats()['pcg_iterations']} mixed {c32.ctx.stats()['pcg_iterations']}")
+    assert e_v <= MIXED_DIAG_TOL
+    assert e_t <= MIXED_TRACE_TOL
+
+
+@pytest.mark.parametrize("name", ["grid16_nt8", "ragged13"])
+def test_mixed_sampler_meets_fp64_residual(q, name):
+    tol = 1e-10
+    c = Case(q, name, precision=q.QSEL_MIXED, pcg_tol=tol)
+    c.ctx.diag_inv()
+    assert c.ctx.stats()["pcg_max_rel_residual"] <= tol
+    X = q.qsel_debug_get_samples(c.ctx)
+    Q = o.precision(c.model, c.theta)
+    R = o.rhs(c.model, c.theta, c.seed, c.k)
+    res = np.linalg.norm(R - Q @ X, axis=0) / np.linalg.norm(R, axis=0)
+    assert res.max() <= 10 * tol
+
+
+@pytest.mark.parametrize("name", ["grid16_nt8", "overlap2", "ragged13"])
+def test_mixed_injected_samples_against_oracle(q, name):
+    c = Case(q, name, precision=q.QSEL_MIXED)
+    X = qi.seeded_normal((c.n_s * c.n_t, c.k), 99)
+    q.qsel_debug_set_samples(c.ctx, X)
+    v = c.ctx.diag_inv()
+    t = c.ctx.trace_grads()
+    sel = q.qsel_debug_get_selinv_diag(c.ctx)
+    v_or, t_or, res = o.rbmc(c.model, c.theta, c.slab_start, c.n_l, X)
+    sel_or = np.concatenate([r.sigma_star_diag for r in res])
+    print(f"{name}: mixed vs oracle selinv {rel(sel, sel_or):.2e} diag {rel(v, v_or):.2e} traces {rel(t, t_or):.2e}")
+    assert rel(sel, sel_or) <= MIXED_DIAG_TOL
+    assert rel(v, v_or) <= MIXED_DIAG_TOL
+    assert rel(t, t_or) <= MIXED_TRACE_TOL
