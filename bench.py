@@ -56,6 +56,10 @@ def parse_args():
                     help="form timed for `value` (mixed = the chosen form)")
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="passes of plain FP64 timed beside the chosen form (0 = skip)")
+    ap.add_argument("--sweep", default=None,
+                    help="time-to-accuracy sweep instead of the bench line: comma list of "
+                         "form:n_parts:overlap:n_samples entries, form in {mixed, fp64}")
+    ap.add_argument("--seeds", type=int, default=1, help="RBMC seeds per sweep entry")
     return ap.parse_args()
 
 
@@ -388,8 +392,67 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_sweep(args):
+    """Time one pass (after one warm-up) and measure the error against the exact
+    single-subdomain FP64 result for each requested (form, n_p, n_l, k), with
+    the error definitions of the time-to-1% metric: eps_diag = RMS over nodes
+    and seeds of the relative error, eps_j = RMS over seeds per trace."""
+    import torch
+    from paper_2309_05435_gb300 import build, qsel
+    build.build()
+    w = qi.workload(args.workload)
+    mesh, mask = workload_inputs(w)
+    stream = torch.cuda.current_stream()
+    ref = qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma,
+                           w.theta, n_parts=1, overlap=0, n_samples=1, cuda_stream=stream.cuda_stream)
+    v_ex = qsel.qsel_diag_inv(ref)
+    t_ex = qsel.qsel_trace_grads(ref)
+    ref.close()
+    rows = []
+    for entry in args.sweep.split(","):
+        form, np_, nl, k = entry.split(":")
+        prec = qsel.QSEL_MIXED if form == "mixed" else qsel.QSEL_FP64
+        errs_d, errs_t, times, iters = [], [], [], []
+        for sd in range(args.seeds):
+            ctx = qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask,
+                                   w.sigma, w.theta, n_parts=int(np_), overlap=int(nl), n_samples=int(k),
+                                   seed=2000 + sd, precision=prec, pcg_tol=w.pcg_tol,
+                                   cuda_stream=stream.cuda_stream)
+            out = torch.empty(w.n, dtype=torch.float64, device="cuda")
+            for rep in range(2 if sd == 0 else 1):
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                qsel.qsel_set_theta(ctx, w.theta)
+                qsel.qsel_diag_inv(ctx, out)
+                g = qsel.qsel_trace_grads(ctx)
+                e1.record(stream)
+                torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            iters.append(qsel.qsel_stats(ctx)["pcg_iterations"])
+            ctx.close()
+            v = out.cpu().numpy()
+            errs_d.append(((v - v_ex) / v_ex) ** 2)
+            errs_t.append([((a - b) / b) ** 2 for a, b in zip(g, t_ex)])
+        ed = np.array(errs_d)
+        row = {"form": form, "n_parts": int(np_), "overlap": int(nl), "n_samples": int(k),
+               "ms": float(np.median(times)), "pcg_iterations": int(np.median(iters)),
+               "eps_diag": float(np.sqrt(ed.mean())),
+               "eps_diag_p99": float(np.quantile(np.sqrt(ed.mean(axis=0)), 0.99)),
+               "eps_traces": [float(np.sqrt(np.mean([e[j] for e in errs_t]))) for j in range(3)],
+               "seeds": args.seeds}
+        row["meets_1pct"] = bool(max(row["eps_diag"], *row["eps_traces"]) <= 0.01)
+        print(json.dumps(row), flush=True)
+        rows.append(row)
+    return rows
+
+
 def main():
     args = parse_args()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

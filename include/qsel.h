@@ -58,7 +58,7 @@ typedef enum {
   QSEL_ECUDA = 3,     /* CUDA runtime or launch error                            */
   QSEL_ENOTSPD = 4,   /* a pivot of a dense factorisation was not positive       */
   QSEL_ENOCONV = 5,   /* the conjugate-gradient solve hit pcg_max_iter           */
-  QSEL_ETIMEOUT = 6,  /* reserved: a bounded device-side wait gave up            */
+  QSEL_ETIMEOUT = 6,  /* a bounded device-side wait gave up (tensor-core GEMM)  */
   QSEL_ESTATE = 7     /* call not valid in the context's current state           */
 } qsel_status;
 
@@ -119,6 +119,10 @@ typedef struct {
   int32_t profile_kernels;/* non-zero: time every launch of the dense tile GEMM,
                              the sweep update and the SpMM with CUDA events on
                              the stream (reported in qsel_stats_t)                 */
+  int32_t tensor_passes;  /* QSEL_MIXED dense products: 0 = default (3 when the
+                             GPU has tcgen05 tensor cores, else CUDA cores),
+                             3 = 3xTF32 (FP32-level accuracy), 1 = plain TF32,
+                             -1 = FP32 CUDA cores.  Ignored for QSEL_FP64.        */
 } qsel_options;
 
 /* Per-call statistics of the last qsel_diag_inv. */

@@ -2,6 +2,7 @@
 // perturbation samples -> multi-RHS PCG -> per-subdomain block factorisation
 // and Takahashi selected inversion -> RB correction -> diag and traces.
 #include <algorithm>
+#include <type_traits>
 #include <array>
 #include <cmath>
 #include <cstring>
@@ -58,6 +59,7 @@ using namespace qsel;
 struct qsel_ctx {
   int n_s = 0, n_t = 0, n = 0, ld = 0, k = 0, n_pad = 0, n_l = 0, bsize = 64;
   bool mixed = false;
+  int tc_passes = 0;                  // mixed path: 3 or 1 = tcgen05 TF32 GEMMs, 0 = CUDA-core FP32
   double sigma = 1.0, obs_w = 1.0;
   qsel_theta theta{};
   qsel_options opt{};
@@ -194,6 +196,8 @@ static Err validate(const qsel_model *m, const qsel_theta *th, const qsel_partit
       opt->precond_block != 32 && opt->precond_block != 64)
     return fail(QSEL_EINVAL, "precond_block must be 0, 1, 16, 32 or 64");
   if (opt->control_variate != 0) return fail(QSEL_EINVAL, "control_variate must be 0");
+  if (opt->tensor_passes != 0 && opt->tensor_passes != 1 && opt->tensor_passes != 3 && opt->tensor_passes != -1)
+    return fail(QSEL_EINVAL, "tensor_passes must be 0, 1, 3 or -1");
   return ok();
 }
 
@@ -440,7 +444,7 @@ static PcgVec<T> make_pcg(qsel_ctx *c, T *x, T *r, T *z, T *p, T *q) {
   v.n = c->n;
   v.ld = c->ld;
   v.n_blocks_dot = bt_spmm_grid(c->n);
-  v.n_tiles = (c->n + 63) / 64;
+  v.n_tiles = pcg_update_grid(c->n);
   v.x = x;
   v.r = r;
   v.z = z;
@@ -565,7 +569,9 @@ static Err run_sampler(qsel_ctx *c) {
   a.x = c->d_X;
   a.y = c->d_q;
   a.dot_partial = nullptr;
-  const double inner_tol = 1e-4;
+  // inner FP32 solves stop at the reduction still needed (with a margin),
+  // floored at what FP32 CG reliably attains
+  const double inner_floor = 3e-6;
   const int max_outer = 30;
   int total = 0;
   double rel = 1.0;
@@ -588,6 +594,7 @@ static Err run_sampler(qsel_ctx *c) {
     int it = 0;
     double inner_rel = 0.0;
     bool conv = false;
+    const double inner_tol = std::max(inner_floor, 0.5 * c->opt.pcg_tol / std::max(rel, 1e-300));
     TRY(pcg_solve<float>(c, v, pblk, inner_tol, c->opt.pcg_max_iter - total, &it, &inner_rel, &conv));
     total += it;
     launch_accumulate(s, c->d_X, c->f_x, (int64_t)vec);
@@ -672,7 +679,99 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
   std::vector<T *> sig_next(p1 - p0, nullptr);
   std::vector<int> flip(p1 - p0, 0);
   for (int p = p0; p < p1; ++p) sig_next[p - p0] = Dinv(p, c->parts[p].T - 1);
-  for (int b = 0; b < maxT; ++b) {
+  bool use_tc = false;
+  if constexpr (std::is_same<T, float>::value) use_tc = c->tc_passes > 0;
+  if (use_tc) {
+    if constexpr (std::is_same<T, float>::value) {
+      // Tensor-core form: Wt = c_t D_t^-1 Q_s (= W^T), Yt = Wt Sigma_{t+1} (= Y^T),
+      // Sigma_t = D_t^-1 + Yt (Wt)^T; both products have K-major operands.
+      for (int b = 0; b < maxT; ++b) {
+        SpBatch<T, T> wb{};
+        GemmBatch<T> yb{}, sgb{};
+        SweepBatch<T> mb{};
+        ExtractBatch<T> xy{}, xs{};
+        DiagRowBatch<T> db{};
+        std::vector<int> active;
+        for (int p = p0; p < p1; ++p) {
+          Subdomain &sd = c->parts[p];
+          DenseSlot &sl = slot(p);
+          const int tl = sd.T - 2 - b;
+          if (tl < std::max(sd.lo - 1, 0)) continue;
+          active.push_back(p);
+          const int tg = sd.e0 + tl;
+          SpEntry<T, T> &we = wb.e[wb.count++];
+          we.B = Dinv(p, tl);
+          we.C = nullptr;
+          we.Out = buf(sl.W);
+          we.alpha_ptr = c->tc.a1 + tg;
+          we.alpha = 1.0;
+          we.beta = 0.0;
+          GemmEntry<T> &ye = yb.e[yb.count++];
+          ye.A = buf(sl.W);
+          ye.B = sig_next[p - p0];
+          ye.C0 = nullptr;
+          ye.C = buf(sl.Y);
+          ye.alpha = 1.0;
+          ye.beta = 0.0;
+          const bool y_needed = (tl >= sd.lo && tl <= sd.hi) || (tl + 1 >= sd.lo && tl + 1 <= sd.hi);
+          if (y_needed) {
+            ExtractEntry<T> &xe = xy.e[xy.count++];
+            xe.S = buf(sl.Y);   // <M, Y> = <M, Y^T> for symmetric M
+            xe.diag_out = nullptr;
+            xe.sums = c->d_sums + 2 * (size_t)(sd.slot_base + sd.T + tl);
+            xe.D0 = nullptr;
+            xe.V = nullptr;
+          }
+          if (tl >= sd.lo) {
+            T *sig_cur = buf(flip[p - p0] ? sl.SigB : sl.SigA);
+            GemmEntry<T> &ge = sgb.e[sgb.count++];
+            ge.A = buf(sl.Y);
+            ge.B = buf(sl.W);
+            ge.C0 = Dinv(p, tl);
+            ge.C = sig_cur;
+            ge.alpha = 1.0;
+            ge.beta = 1.0;
+            SweepEntry<T> &me = mb.e[mb.count++];
+            me.A = sig_cur;
+            if (tl <= sd.hi) {
+              ExtractEntry<T> &xe = xs.e[xs.count++];
+              xe.S = sig_cur;
+              xe.diag_out = nullptr;
+              xe.sums = c->d_sums + 2 * (size_t)(sd.slot_base + tl);
+              xe.D0 = nullptr;
+              xe.V = nullptr;
+              DiagRowEntry<T> &de = db.e[db.count++];
+              de.D0 = Dinv(p, tl);
+              de.P = buf(sl.Y);
+              de.R = buf(sl.W);
+              de.diag_out = c->d_selinv + (size_t)tg * n_s;
+            }
+          }
+        }
+        if (active.empty()) break;
+        launch_sp_colgather<T>(s, wb, c->pat, c->d_qs, n_s, n_pad);
+        if (!launch_tc_gemm(s, yb, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, false, c->tc_passes, c->d_err))
+          return fail(QSEL_ECUDA, "tensor-core GEMM: tensor map encoding failed");
+        launch_extract<T>(s, xy, c->pat, c->d_qs, c->d_dqs, n_s, n_pad, c->d_diag_scratch);
+        if (!launch_tc_gemm(s, sgb, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, true, c->tc_passes, c->d_err))
+          return fail(QSEL_ECUDA, "tensor-core GEMM: tensor map encoding failed");
+        launch_diag64_rows<T>(s, db, n_s, n_pad);
+        launch_mirror<T>(s, mb, n_pad);
+        launch_extract<T>(s, xs, c->pat, c->d_qs, c->d_dqs, n_s, n_pad, c->d_diag_scratch);
+        for (int p : active) {
+          Subdomain &sd = c->parts[p];
+          DenseSlot &sl = slot(p);
+          const int tl = sd.T - 2 - b;
+          if (tl >= sd.lo) {
+            sig_next[p - p0] = buf(flip[p - p0] ? sl.SigB : sl.SigA);
+            flip[p - p0] ^= 1;
+          }
+        }
+        QSEL_CUDA_TRY(cudaGetLastError());
+      }
+    }
+  }
+  for (int b = 0; !use_tc && b < maxT; ++b) {
     SpBatch<T, T> wb{}, vb{};
     GemmBatch<T> yb{}, sgb{};
     SweepBatch<T> mb{};
@@ -939,6 +1038,7 @@ static Err run_pipeline_body(qsel_ctx *c) {
   int32_t err = 0;
   QSEL_CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
   if (err & 1) return fail(QSEL_ENOTSPD, "a pivot of a dense block factorisation was not positive");
+  if (err & 2) return fail(QSEL_ETIMEOUT, "a bounded device-side wait of the tensor-core GEMM gave up");
   float ms;
   auto el = [&](cudaEvent_t a, cudaEvent_t b) {
     cudaEventElapsedTime(&ms, a, b);
@@ -992,6 +1092,17 @@ qsel_status qsel_create(qsel_ctx **out, const qsel_model *model, const qsel_thet
   c->opt = *opt;
   c->bsize = opt->precond_block == 0 ? 64 : opt->precond_block;
   c->mixed = opt->precision == QSEL_MIXED;
+  if (c->mixed) {
+    if (opt->tensor_passes == 0)
+      c->tc_passes = tc_gemm_available() ? 3 : 0;
+    else if (opt->tensor_passes > 0)
+      c->tc_passes = opt->tensor_passes;
+    if (c->tc_passes > 0 && !tc_gemm_available()) {
+      g_create_error = "tensor_passes requested but tcgen05 tensor-core GEMMs are not available on this device";
+      delete c;
+      return QSEL_EINVAL;
+    }
+  }
   c->stream = reinterpret_cast<cudaStream_t>(opt->cuda_stream);
   e = build(c, model, partition, overlap);
   if (e.code) {

@@ -387,6 +387,74 @@ template void launch_sp_rowgather<double, float>(cudaStream_t, const SpBatch<dou
                                                  const SellPattern &, const double *, int, int, int, int, int);
 
 // ---------------------------------------------------------------------------
+// Out = alpha B Q_s + beta C (column gather over the symmetric pattern:
+// (B Q_s)[r, l] = sum_{j in pat(l)} B[r, j] Q_s[l, j]); rows and columns past
+// n_s of Out are zero.  With B = D^-1 (symmetric) this is (Q_s D^-1)^T.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_sp_colgather(SpBatch<T, T> bt, SellPattern pat,
+                                                      const double *__restrict__ val, int n_s, int n_pad) {
+  const SpEntry<T, T> e = bt.e[blockIdx.z];
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (l >= n_pad) return;
+  T out = T(0);
+  if (r < n_s && l < n_s) {
+    const int sl = l >> 5, li = l & 31;
+    const int w = pat.slice_width[sl];
+    const int base = pat.slice_ptr[sl] + li;
+    const T *Br = e.B + (int64_t)r * n_pad;
+    T acc = T(0);
+    for (int s = 0; s < w; ++s) {
+      const int j = pat.col[base + s * kSlice];
+      acc = fma(Br[j], (T)val[base + s * kSlice], acc);
+    }
+    out = (T)(e.alpha * (e.alpha_ptr ? *e.alpha_ptr : 1.0)) * acc;
+    if (e.C != nullptr && e.beta != 0.0) out = fma((T)e.beta, e.C[(int64_t)r * n_pad + l], out);
+  }
+  e.Out[(int64_t)r * n_pad + l] = out;
+}
+
+template <typename T>
+void launch_sp_colgather(cudaStream_t s, const SpBatch<T, T> &b, const SellPattern &pat, const double *val,
+                         int n_s, int n_pad) {
+  if (b.count <= 0) return;
+  ++g_launch_count;
+  dim3 grid((n_pad + 255) / 256, n_pad, b.count);
+  k_sp_colgather<T><<<grid, 256, 0, s>>>(b, pat, val, n_s, n_pad);
+}
+template void launch_sp_colgather<double>(cudaStream_t, const SpBatch<double, double> &, const SellPattern &,
+                                          const double *, int, int);
+template void launch_sp_colgather<float>(cudaStream_t, const SpBatch<float, float> &, const SellPattern &,
+                                         const double *, int, int);
+
+// diag_out[i] = D0[i, i] + sum_l P[i, l] R[i, l] accumulated in double (one
+// warp per row, coalesced along the row): the diagonal of
+// Sigma_t = D_t^-1 + Y^T W with P = Y^T and R = W^T.
+template <typename T>
+__global__ void __launch_bounds__(256) k_diag64_rows(DiagRowBatch<T> bt, int n_s, int n_pad) {
+  const DiagRowEntry<T> e = bt.e[blockIdx.y];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
+  if (i >= n_s) return;
+  const T *Pi = e.P + (int64_t)i * n_pad;
+  const T *Ri = e.R + (int64_t)i * n_pad;
+  double acc = 0.0;
+  for (int l = lane; l < n_s; l += 32) acc = fma((double)Pi[l], (double)Ri[l], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) e.diag_out[i] = (double)e.D0[(int64_t)i * n_pad + i] + acc;
+}
+
+template <typename T>
+void launch_diag64_rows(cudaStream_t s, const DiagRowBatch<T> &b, int n_s, int n_pad) {
+  if (b.count <= 0) return;
+  ++g_launch_count;
+  k_diag64_rows<T><<<dim3((n_s + 7) / 8, b.count), 256, 0, s>>>(b, n_s, n_pad);
+}
+template void launch_diag64_rows<double>(cudaStream_t, const DiagRowBatch<double> &, int, int);
+template void launch_diag64_rows<float>(cudaStream_t, const DiagRowBatch<float> &, int, int);
+
+// ---------------------------------------------------------------------------
 // D = a0 Q_s + w_obs diag(obs) - c W Q_s (column gather over the symmetric
 // pattern: (W Q_s)[r, l] = sum_{j in pat(l)} W[r, j] Q_s[l, j]), in double.
 // ---------------------------------------------------------------------------

@@ -104,6 +104,8 @@ template <typename T>
 void launch_jacobi_setup(cudaStream_t s, const SellPattern &pat, const double *qs, const double *a0,
                          const double *a1, const uint8_t *obs, double obs_w, int n_s, int n_t,
                          int bsize, T *pblk, int32_t *err_flag);
+// Grid of the PCG update (also the number of its partial rows, PcgVec::n_tiles).
+int pcg_update_grid(int n);
 template <typename T>
 void launch_pcg_update(cudaStream_t s, const PcgVec<T> &v, const T *pblk, int bsize);
 template <typename T>
@@ -184,6 +186,32 @@ struct SpBatch {
 template <typename TI, typename TO>
 void launch_sp_rowgather(cudaStream_t s, const SpBatch<TI, TO> &b, const SellPattern &pat,
                          const double *val, int n_s, int n_pad, int ncol, int ldb, int ldo);
+
+// Out = alpha B Q_s + beta C on n_pad x n_pad blocks (column gather).
+template <typename T>
+void launch_sp_colgather(cudaStream_t s, const SpBatch<T, T> &b, const SellPattern &pat, const double *val,
+                         int n_s, int n_pad);
+
+template <typename T>
+struct DiagRowEntry {
+  const T *D0, *P, *R;      // diag_out[i] = D0[i,i] + sum_l P[i,l] R[i,l] (double)
+  double *diag_out;
+};
+template <typename T>
+struct DiagRowBatch {
+  DiagRowEntry<T> e[kMaxBatch];
+  int count;
+};
+template <typename T>
+void launch_diag64_rows(cudaStream_t s, const DiagRowBatch<T> &b, int n_s, int n_pad);
+
+// ---------------------------------------------------------------- tc_gemm.cu
+// tcgen05 tensor-core GEMM (FP32 data, TF32 MMAs): C = alpha A B^T + beta C0
+// with A (M x K) and B (N x K) row-major; passes 3 = 3xTF32, 1 = TF32.
+// err gets bit 1 when a bounded wait gives up.
+bool tc_gemm_available();
+bool launch_tc_gemm(cudaStream_t s, const GemmBatch<float> &b, int M, int N, int K, int lda, int ldb, int ldc,
+                    bool lower, int passes, int32_t *err);
 
 template <typename T>
 struct SchurEntry {

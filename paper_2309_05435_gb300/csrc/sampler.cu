@@ -162,7 +162,7 @@ int bt_spmm_grid(int n_rows) {
 
 template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs<T> a) {
-  __shared__ double red[8][512];
+  __shared__ T red[8][512];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_rows = a.n_s * a.n_t;
   const int ld = a.ld;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs<T> a) {
   const int nchunk = ld / chunk_cols;
   const bool dot = a.dot_partial != nullptr;
   if (dot) {
-    for (int c = lane; c < ld; c += 32) red[warp][c] = 0.0;
+    for (int c = lane; c < ld; c += 32) red[warp][c] = T(0);
   }
   const int64_t slab = (int64_t)a.n_s * ld;
   const int64_t items = (int64_t)n_rows * nchunk;
@@ -181,40 +181,46 @@ __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs<T> a) {
     const int sl = i >> 5, li = i & 31;
     const int w = a.pat.slice_width[sl];
     const int base = a.pat.slice_ptr[sl] + li;
-    const double c0 = a.c0[t];
-    const double cm = (t > 0) ? a.c1[t - 1] : 0.0;
-    const double cp = (t + 1 < a.n_t) ? a.c1[t] : 0.0;
+    // per-row scalars in T: the FP32 path issues no double arithmetic per element
+    const T c0 = (T)a.c0[t];
+    const T cm = (t > 0) ? (T)a.c1[t - 1] : T(0);
+    const T cp = (t + 1 < a.n_t) ? (T)a.c1[t] : T(0);
     const int coff = ch * chunk_cols + 2 * lane;
     T ax[NV], ay[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) ax[v] = ay[v] = T(0);
-    for (int s = 0; s < w; ++s) {
-      const int j = a.pat.col[base + s * kSlice];
-      const double val = a.val[base + s * kSlice];
-      const T *xc = a.x + ((int64_t)t * a.n_s + j) * ld + coff;
-      const T f0 = (T)(c0 * val);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const auto xv = load2(xc + 64 * v);
-        ax[v] = fma(f0, xv.x, ax[v]);
-        ay[v] = fma(f0, xv.y, ay[v]);
+    const bool has_m = t > 0, has_p = t + 1 < a.n_t;
+    for (int s0 = 0; s0 < w; s0 += 32) {
+      // the row's pattern entries, one per lane, then broadcast: no dependent
+      // loads inside the neighbour loop
+      int my_col = i;
+      T my_val = T(0);
+      if (s0 + lane < w) {
+        my_col = a.pat.col[base + (s0 + lane) * kSlice];
+        my_val = (T)a.val[base + (s0 + lane) * kSlice];
       }
-      if (t > 0) {
-        const T fm = (T)(cm * val);
+      const int cnt = min(32, w - s0);
+#pragma unroll 4
+      for (int s = 0; s < cnt; ++s) {
+        const int j = __shfl_sync(0xffffffffu, my_col, s);
+        const T val = __shfl_sync(0xffffffffu, my_val, s);
+        const T *xc = a.x + ((int64_t)t * a.n_s + j) * ld + coff;
+        const T f0 = c0 * val, fm = cm * val, fp = cp * val;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const auto xv = load2(xc - slab + 64 * v);
-          ax[v] = fma(fm, xv.x, ax[v]);
-          ay[v] = fma(fm, xv.y, ay[v]);
-        }
-      }
-      if (t + 1 < a.n_t) {
-        const T fp = (T)(cp * val);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const auto xv = load2(xc + slab + 64 * v);
-          ax[v] = fma(fp, xv.x, ax[v]);
-          ay[v] = fma(fp, xv.y, ay[v]);
+          const auto x0 = load2(xc + 64 * v);
+          ax[v] = fma(f0, x0.x, ax[v]);
+          ay[v] = fma(f0, x0.y, ay[v]);
+          if (has_m) {
+            const auto xm = load2(xc - slab + 64 * v);
+            ax[v] = fma(fm, xm.x, ax[v]);
+            ay[v] = fma(fm, xm.y, ay[v]);
+          }
+          if (has_p) {
+            const auto xp = load2(xc + slab + 64 * v);
+            ax[v] = fma(fp, xp.x, ax[v]);
+            ay[v] = fma(fp, xp.y, ay[v]);
+          }
         }
       }
     }
@@ -233,8 +239,8 @@ __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs<T> a) {
       ay[v] = fma(ow, x1, ay[v]);
       store2(yr + 64 * v, ax[v], ay[v]);
       if (dot) {
-        red[warp][coff + 64 * v] += (double)x0 * (double)ax[v];
-        red[warp][coff + 64 * v + 1] += (double)x1 * (double)ay[v];
+        red[warp][coff + 64 * v] = fma(x0, ax[v], red[warp][coff + 64 * v]);
+        red[warp][coff + 64 * v + 1] = fma(x1, ay[v], red[warp][coff + 64 * v + 1]);
       }
     }
   }
@@ -243,7 +249,7 @@ __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs<T> a) {
     for (int c = threadIdx.x; c < ld; c += blockDim.x) {
       double sum = 0.0;
 #pragma unroll
-      for (int ww = 0; ww < 8; ++ww) sum += red[ww][c];
+      for (int ww = 0; ww < 8; ++ww) sum += (double)red[ww][c];
       a.dot_partial[(int64_t)blockIdx.x * ld + c] = sum;
     }
   }
@@ -347,6 +353,13 @@ constexpr int pcg_update_smem() {
   return (64 * 65 + 64 * 64) * (int)sizeof(T) + 2 * 4 * 64 * (int)sizeof(double);
 }
 
+constexpr int kUpdGrid = 152 * 4;
+
+int pcg_update_grid(int n) {
+  const int tiles = (n + 63) / 64;
+  return tiles < kUpdGrid ? tiles : kUpdGrid;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_pcg_update(PcgVec<T> v, const T *__restrict__ pblk, int b) {
   extern __shared__ __align__(16) unsigned char smem_upd_raw[];
@@ -354,46 +367,88 @@ __global__ void __launch_bounds__(256) k_pcg_update(PcgVec<T> v, const T *__rest
   double *red_b = red_a + 4 * 64;                               // [4][64]
   T *rs = reinterpret_cast<T *>(red_b + 4 * 64);                // [64][65]
   T *Ps = rs + 64 * 65;                                         // [64 * b]
-  const int r0 = blockIdx.x * 64;
-  const int rows = min(64, v.n - r0);
   const int n_blocks = (v.n + b - 1) / b;
-  {
-    const int64_t base = (int64_t)(r0 / b) * b * b;
-    const int64_t lim = (int64_t)n_blocks * b * b;
-    for (int e = threadIdx.x; e < 64 * b; e += blockDim.x) Ps[e] = (base + e < lim) ? pblk[base + e] : T(0);
-  }
+  const int n_tiles = (v.n + 63) / 64;
   const int lc = threadIdx.x & 63, rg = threadIdx.x >> 6;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // the reduction that follows accumulates into these
+    v.counters[0] = 0;
+    v.max_rel[0] = 0.0;
+  }
   for (int c0 = 0; c0 < v.ld; c0 += 64) {
     const int col = c0 + lc;
     const T al = (T)v.alpha[col];
-    for (int rr = rg; rr < 64; rr += 4) {
-      T rv = T(0);
-      if (rr < rows) {
-        const int64_t idx = (int64_t)(r0 + rr) * v.ld + col;
-        rv = v.r[idx];
-        if (al != T(0)) {
-          v.x[idx] = fma(al, v.p[idx], v.x[idx]);
-          rv = fma(-al, v.q[idx], rv);
-          v.r[idx] = rv;
+    T sa = T(0), sb = T(0);
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+      const int r0 = tile * 64;
+      const int rows = min(64, v.n - r0);
+      __syncthreads();
+      {
+        // P blocks of this tile, transposed: Ps[blk][j][r] = P_blk[r][j]
+        const int64_t base = (int64_t)(r0 / b) * b * b;
+        const int64_t lim = (int64_t)n_blocks * b * b;
+        for (int e = threadIdx.x; e < 64 * b; e += blockDim.x) {
+          const int blk = e / (b * b), rem = e - blk * b * b;
+          const int r = rem / b, j = rem - r * b;
+          Ps[blk * b * b + j * b + r] = (base + e < lim) ? pblk[base + e] : T(0);
         }
       }
-      rs[rr * 65 + lc] = rv;
+      for (int rr = rg; rr < 64; rr += 4) {
+        T rv = T(0);
+        if (rr < rows) {
+          const int64_t idx = (int64_t)(r0 + rr) * v.ld + col;
+          rv = v.r[idx];
+          if (al != T(0)) {
+            v.x[idx] = fma(al, v.p[idx], v.x[idx]);
+            rv = fma(-al, v.q[idx], rv);
+            v.r[idx] = rv;
+          }
+        }
+        rs[rr * 65 + lc] = rv;
+      }
+      __syncthreads();
+      if (b >= 16) {
+        // thread rows rg*16 .. rg*16+15 lie in one block: 16 accumulators, each
+        // r value read once, the 16 P entries of a column as broadcasts
+        const int rbase = rg * 16;
+        const int blk = rbase / b, bo = rbase - blk * b;
+        const T *Pt = Ps + blk * b * b + bo;
+        const T *rcol = rs + (blk * b) * 65 + lc;
+        T z[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) z[q] = T(0);
+        for (int jj = 0; jj < b; ++jj) {
+          const T rj = rcol[jj * 65];
+          const T *pj = Pt + jj * b;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) z[q] = fma(pj[q], rj, z[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int rr = rbase + q;
+          if (rr < rows) {
+            v.z[(int64_t)(r0 + rr) * v.ld + col] = z[q];
+            const T rd = rs[rr * 65 + lc];
+            sa = fma(rd, z[q], sa);
+            sb = fma(rd, rd, sb);
+          }
+        }
+      } else {
+        for (int rr = rg; rr < rows; rr += 4) {
+          const int blk = rr / b, bo = rr - blk * b;
+          const T *Pt = Ps + blk * b * b + bo;
+          const int rb = blk * b;
+          T z = T(0);
+          for (int jj = 0; jj < b; ++jj) z = fma(Pt[jj * b], rs[(rb + jj) * 65 + lc], z);
+          v.z[(int64_t)(r0 + rr) * v.ld + col] = z;
+          const T rd = rs[rr * 65 + lc];
+          sa = fma(rd, z, sa);
+          sb = fma(rd, rd, sb);
+        }
+      }
     }
-    __syncthreads();
-    double sa = 0.0, sb = 0.0;
-    for (int rr = rg; rr < rows; rr += 4) {
-      const int blk = rr / b, bo = rr - blk * b;
-      const T *Pr = Ps + blk * b * b + bo * b;
-      const int rb = blk * b;
-      T z = T(0);
-      for (int jj = 0; jj < b; ++jj) z = fma(Pr[jj], rs[(rb + jj) * 65 + lc], z);
-      v.z[(int64_t)(r0 + rr) * v.ld + col] = z;
-      const double rd = (double)rs[rr * 65 + lc];
-      sa = fma(rd, (double)z, sa);
-      sb = fma(rd, rd, sb);
-    }
-    red_a[rg * 64 + lc] = sa;
-    red_b[rg * 64 + lc] = sb;
+    red_a[rg * 64 + lc] = (double)sa;
+    red_b[rg * 64 + lc] = (double)sb;
     __syncthreads();
     if (rg == 0) {
       v.partial_a[(int64_t)blockIdx.x * v.ld + col] =
@@ -413,86 +468,82 @@ void launch_pcg_update(cudaStream_t s, const PcgVec<T> &v, const T *pblk, int bs
     attr_set = true;
   }
   ++g_launch_count;
-  k_pcg_update<T><<<v.n_tiles, 256, pcg_update_smem<T>(), s>>>(v, pblk, bsize);
+  k_pcg_update<T><<<v.n_tiles, 256, pcg_update_smem<T>(), s>>>(v, pblk, bsize);  // n_tiles = grid
 }
 template void launch_pcg_update<double>(cudaStream_t, const PcgVec<double> &, const double *, int);
 template void launch_pcg_update<float>(cudaStream_t, const PcgVec<float> &, const float *, int);
 
+// Column sums of per-CTA partial rows: 8 row groups x 32 columns per block,
+// fixed order within each group and across groups.
+__device__ __forceinline__ double column_sum(const double *__restrict__ part, int n_rows, int ld, int c, int rg,
+                                             double (*sh)[33]) {
+  double acc = 0.0;
+  for (int g = rg; g < n_rows; g += 8) acc += part[(int64_t)g * ld + c];
+  sh[rg][threadIdx.x & 31] = acc;
+  __syncthreads();
+  double tot = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) tot += sh[q][threadIdx.x & 31];
+  return tot;
+}
+
 // alpha_c = rho_c / <p_c, q_c> for active columns, 0 otherwise.
 template <typename T>
-__global__ void k_pcg_reduce_alpha(PcgVec<T> v) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= v.ld) return;
-  double pq = 0.0;
-  for (int g = 0; g < v.n_blocks_dot; ++g) pq += v.partial_a[(int64_t)g * v.ld + c];
-  v.alpha[c] = (v.active[c] && pq != 0.0) ? v.rho[c] / pq : 0.0;
+__global__ void __launch_bounds__(256) k_pcg_reduce_alpha(PcgVec<T> v) {
+  __shared__ double sh[8][33];
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31), rg = threadIdx.x >> 5;
+  const double pq = column_sum(v.partial_a, v.n_blocks_dot, v.ld, c, rg, sh);
+  if (rg == 0) v.alpha[c] = (v.active[c] && pq != 0.0) ? v.rho[c] / pq : 0.0;
 }
 
 template <typename T>
 void launch_pcg_reduce_alpha(cudaStream_t s, const PcgVec<T> &v) {
   ++g_launch_count;
-  k_pcg_reduce_alpha<T><<<(v.ld + 127) / 128, 128, 0, s>>>(v);
+  k_pcg_reduce_alpha<T><<<v.ld / 32, 256, 0, s>>>(v);
 }
 template void launch_pcg_reduce_alpha<double>(cudaStream_t, const PcgVec<double> &);
 template void launch_pcg_reduce_alpha<float>(cudaStream_t, const PcgVec<float> &);
 
-// <r, z>, <r, r> -> beta, rho, convergence flags, active count and the
-// maximum relative residual (single block, ld <= 1024 threads).
+// <r, z>, <r, r> -> beta, rho, convergence flags; active count and maximum
+// relative residual by integer atomics (the update kernel zeroed them).
 template <typename T>
-__global__ void k_pcg_reduce_beta(PcgVec<T> v, double tol2, int init) {
-  __shared__ int cnt[32];
-  __shared__ double mx[32];
-  const int c = threadIdx.x;
-  int act = 0;
-  double rel = 0.0;
-  if (c < v.ld) {
-    double rz = 0.0, rr = 0.0;
-    for (int g = 0; g < v.n_tiles; ++g) {
-      rz += v.partial_a[(int64_t)g * v.ld + c];
-      rr += v.partial_b[(int64_t)g * v.ld + c];
-    }
-    if (init) {
-      v.bb[c] = rr;
-      v.rho[c] = rz;
-      v.beta[c] = 0.0;
-      v.active[c] = rr > 0.0 ? 1 : 0;
-    } else if (v.active[c]) {
-      v.beta[c] = v.rho[c] != 0.0 ? rz / v.rho[c] : 0.0;
-      v.rho[c] = rz;
-      if (rr <= tol2 * v.bb[c]) v.active[c] = 0;
-    } else {
-      v.beta[c] = 0.0;
-    }
-    v.rr[c] = rr;
-    act = v.active[c];
-    rel = v.bb[c] > 0.0 ? sqrt(rr / v.bb[c]) : 0.0;
+__global__ void __launch_bounds__(256) k_pcg_reduce_beta(PcgVec<T> v, double tol2, int init) {
+  __shared__ double sh[8][33];
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31), rg = threadIdx.x >> 5;
+  const double rz = column_sum(v.partial_a, v.n_tiles, v.ld, c, rg, sh);
+  __syncthreads();
+  const double rr = column_sum(v.partial_b, v.n_tiles, v.ld, c, rg, sh);
+  if (rg != 0) return;
+  if (init) {
+    v.bb[c] = rr;
+    v.rho[c] = rz;
+    v.beta[c] = 0.0;
+    v.active[c] = rr > 0.0 ? 1 : 0;
+  } else if (v.active[c]) {
+    v.beta[c] = v.rho[c] != 0.0 ? rz / v.rho[c] : 0.0;
+    v.rho[c] = rz;
+    if (rr <= tol2 * v.bb[c]) v.active[c] = 0;
+  } else {
+    v.beta[c] = 0.0;
   }
+  v.rr[c] = rr;
+  int act = v.active[c];
+  double rel = v.bb[c] > 0.0 ? sqrt(rr / v.bb[c]) : 0.0;
   for (int o = 16; o > 0; o >>= 1) {
     act += __shfl_down_sync(0xffffffffu, act, o);
     rel = fmax(rel, __shfl_down_sync(0xffffffffu, rel, o));
   }
-  if ((threadIdx.x & 31) == 0) {
-    cnt[threadIdx.x >> 5] = act;
-    mx[threadIdx.x >> 5] = rel;
-  }
-  __syncthreads();
   if (threadIdx.x == 0) {
-    int a = 0;
-    double m = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      a += cnt[w];
-      m = fmax(m, mx[w]);
-    }
-    v.counters[0] = a;
-    v.max_rel[0] = m;
+    if (act) atomicAdd(v.counters, act);
+    // non-negative doubles order like their bit patterns
+    atomicMax(reinterpret_cast<unsigned long long *>(v.max_rel), (unsigned long long)__double_as_longlong(rel));
   }
 }
 
 template <typename T>
 void launch_pcg_reduce_beta(cudaStream_t s, const PcgVec<T> &v, double tol, int init) {
   ++g_launch_count;
-  int threads = (v.ld + 31) / 32 * 32;
-  k_pcg_reduce_beta<T><<<1, threads, 0, s>>>(v, tol * tol, init);
+  k_pcg_reduce_beta<T><<<v.ld / 32, 256, 0, s>>>(v, tol * tol, init);
 }
 template void launch_pcg_reduce_beta<double>(cudaStream_t, const PcgVec<double> &, double, int);
 template void launch_pcg_reduce_beta<float>(cudaStream_t, const PcgVec<float> &, double, int);

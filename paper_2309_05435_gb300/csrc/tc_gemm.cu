@@ -1,0 +1,419 @@
+// Tensor-core GEMM for the mixed path (sm_100a/sm_103a tcgen05 + TMA).
+//
+//   C = alpha A B^T + beta C0,   A: M x K, B: N x K, C: M x N, all FP32 row-major
+//
+// Both operands are K-major ("TN"), which is what the Takahashi products of
+// the mixed path need: Y^T = W^T Sigma_{t+1} (Sigma symmetric) and
+// Sigma_t = D_t^-1 + Y^T W (B stored as W^T).
+//
+// One CTA computes a 128 x 128 tile of C:
+//   warp 0      one thread issues the TMA loads of 128 x 32 FP32 tiles of A and
+//               B (128-byte rows, 128B swizzle) into a 3-stage ring;
+//   warps 2-5   split every loaded tile into TF32 hi (low 13 mantissa bits
+//               cleared) and lo = x - hi parts in shared memory, then run the
+//               epilogue (tcgen05.ld of the accumulator, alpha/beta, store);
+//   warp 1      owns the 128-column TMEM accumulator; one thread issues
+//               tcgen05.mma.kind::tf32 (M=128, N=128, K=8) for hi*hi, hi*lo and
+//               lo*hi ("3xTF32", FP32-level accuracy with FP32 accumulation) or
+//               for the raw values only (1 pass).
+// Every wait is bounded: after ~2 s the CTA raises bit 1 of *err, stops
+// issuing work, waits (bounded) for what it already issued, frees TMEM and
+// returns.
+#include <cuda.h>
+
+#include <mutex>
+
+#include "kernels.cuh"
+
+namespace qsel {
+namespace tc {
+
+constexpr int BM = 128, BN = 128, BK = 32, STAGES = 3;
+constexpr int TILE_BYTES = BM * BK * 4;          // 16 KiB per operand tile
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;      // A, B, A_lo, B_lo
+constexpr int BAR_BYTES = 256;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr uint32_t kTmemCols = 128;
+
+struct Params {
+  CUtensorMap tmA[kMaxBatch];
+  CUtensorMap tmB[kMaxBatch];
+  float *C[kMaxBatch];
+  const float *C0[kMaxBatch];
+  float alpha[kMaxBatch], beta[kMaxBatch];
+  int M, N, K, ldc, lower, passes;
+  int32_t *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, int32_t *err) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      atomicOr(err, 2);
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand tile with 128-byte rows
+// and the 128B swizzle; 8-row core groups 1024 bytes apart (SBO), descriptor
+// version 1, layout type 2 (SWIZZLE_128B).  The start address advances by 32
+// bytes per K=8 step inside the 128-byte row.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
+// (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+// M >> 4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void named_sync_converters() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Params p) {
+  extern __shared__ unsigned char smem_raw[];
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + STAGES * STAGE_BYTES);
+  // bars[0..S): full (TMA landed), [S..2S): converted, [2S..3S): empty, [3S]: accumulator ready
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3 * STAGES + 1);
+  volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  volatile int *conv_ok = abort + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bn = blockIdx.x, bm = blockIdx.y, z = blockIdx.z;
+  if (p.lower && bn > bm) return;
+  const int nk = p.K / BK;
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto conv_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (2 * STAGES + s); };
+  const uint32_t accum_bar = bar0 + 8u * (3 * STAGES);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(conv_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    mbar_init(accum_bar, 1);
+    *abort = 0;
+    *conv_ok = 1;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const CUtensorMap *tma = &p.tmA[z];
+      const CUtensorMap *tmb = &p.tmB[z];
+      int issued = 0;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES, u = kb / STAGES;
+        if (!mbar_wait(empty_bar(s), (u & 1) ^ 1, abort, p.err)) break;
+        uint8_t *st = base + s * STAGE_BYTES;
+        mbar_expect_tx(full_bar(s), 2 * TILE_BYTES);
+        tma_load_2d(smem_u32(st), tma, kb * BK, bm * BM, full_bar(s));
+        tma_load_2d(smem_u32(st + TILE_BYTES), tmb, kb * BK, bn * BN, full_bar(s));
+        issued = kb + 1;
+      }
+      if (*abort) {
+        // let the loads already issued land before the CTA's shared memory goes away
+        for (int kb = max(0, issued - STAGES); kb < issued; ++kb) {
+          const long long t0 = clock64();
+          uint32_t done = 0;
+          while (!done && clock64() - t0 < kWaitCycles) {
+            asm volatile(
+                "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, q;\n\t}\n"
+                : "=r"(done)
+                : "r"(full_bar(kb % STAGES)), "r"((uint32_t)((kb / STAGES) & 1))
+                : "memory");
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES, u = kb / STAGES;
+        if (!mbar_wait(conv_bar(s), u & 1, abort, p.err)) break;
+        tc_fence_after();
+        const uint32_t st = smem_u32(base + s * STAGE_BYTES);
+        const uint32_t a_hi = st, b_hi = st + TILE_BYTES, a_lo = st + 2 * TILE_BYTES, b_lo = st + 3 * TILE_BYTES;
+#pragma unroll
+        for (int j = 0; j < BK / 8; ++j) {
+          const uint32_t off = j * 32;
+          mma_tf32(tmem, smem_desc(a_hi + off), smem_desc(b_hi + off), (kb | j) != 0);
+          if (p.passes == 3) {
+            mma_tf32(tmem, smem_desc(a_hi + off), smem_desc(b_lo + off), 1u);
+            mma_tf32(tmem, smem_desc(a_lo + off), smem_desc(b_hi + off), 1u);
+          }
+        }
+        mma_commit(empty_bar(s));
+      }
+      // signals the epilogue when every MMA issued so far has completed
+      mma_commit(accum_bar);
+    }
+  } else {
+    // converters (warps 2-5): split the raw tiles into TF32 hi / lo parts
+    const int ct = threadIdx.x - 64;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES, u = kb / STAGES;
+      if (ct == 0) *conv_ok = (mbar_wait(full_bar(s), u & 1, abort, p.err) && !*abort) ? 1 : 0;
+      named_sync_converters();
+      if (!*conv_ok) break;
+      if (p.passes == 3) {
+        float4 *raw = reinterpret_cast<float4 *>(base + s * STAGE_BYTES);
+        float4 *lo = reinterpret_cast<float4 *>(base + s * STAGE_BYTES + 2 * TILE_BYTES);
+        // A then B: 2 x 1024 16-byte chunks; lo mirrors raw at +2 tiles
+        for (int i = ct; i < 2 * TILE_BYTES / 16; i += 128) {
+          float4 v = raw[i];
+          float4 h;
+          h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+          h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+          h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+          h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+          raw[i] = h;
+          lo[i] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      named_sync_converters();
+      if (ct == 0) mbar_arrive(conv_bar(s));
+    }
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 = rows of the tile
+    if (ct == 0) *conv_ok = (mbar_wait(accum_bar, 0, abort, p.err) && !*abort) ? 1 : 0;
+    named_sync_converters();
+    if (*conv_ok) {  // uniform across the four warps: tcgen05.ld is warp-collective
+      tc_fence_after();
+      const int q = warp & 3;
+      const int row = bm * BM + 32 * q + lane;
+      float *C = p.C[z];
+      const float *C0 = p.C0[z];
+      const float alpha = p.alpha[z], beta = p.beta[z];
+#pragma unroll 1
+      for (int cc = 0; cc < BN / 32; ++cc) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cc * 32), v);
+        const int col0 = bn * BN + cc * 32;
+        if (row < p.M && col0 < p.N) {
+          float *crow = C + (int64_t)row * p.ldc + col0;
+          const float *c0row = C0 ? C0 + (int64_t)row * p.ldc + col0 : nullptr;
+          const int ncol = min(32, p.N - col0);
+          if (ncol == 32) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              float4 o = make_float4(alpha * __uint_as_float(v[j]), alpha * __uint_as_float(v[j + 1]),
+                                     alpha * __uint_as_float(v[j + 2]), alpha * __uint_as_float(v[j + 3]));
+              if (c0row != nullptr && beta != 0.0f) {
+                const float4 c = *reinterpret_cast<const float4 *>(c0row + j);
+                o.x = fmaf(beta, c.x, o.x);
+                o.y = fmaf(beta, c.y, o.y);
+                o.z = fmaf(beta, c.z, o.z);
+                o.w = fmaf(beta, c.w, o.w);
+              }
+              *reinterpret_cast<float4 *>(crow + j) = o;
+            }
+          } else {
+            for (int j = 0; j < ncol; ++j) {
+              float o = alpha * __uint_as_float(v[j]);
+              if (c0row != nullptr && beta != 0.0f) o = fmaf(beta, c0row[j], o);
+              crow[j] = o;
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    if (*abort && lane == 0) {
+      // wait (bounded) for MMAs still in flight before the accumulator is freed
+      const long long t0 = clock64();
+      uint32_t done = 0;
+      while (!done && clock64() - t0 < kWaitCycles) {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, q;\n\t}\n"
+            : "=r"(done)
+            : "r"(accum_bar), "r"(0u)
+            : "memory");
+      }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+std::mutex g_mu;
+EncodeFn g_encode = nullptr;
+int g_state = 0;  // 0 unknown, 1 available, -1 unavailable
+
+bool encode_2d(CUtensorMap *tm, const float *ptr, int rows, int cols, int ld) {
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace tc
+
+// True when the current device runs tcgen05 (compute capability 10.x) and the
+// driver provides cuTensorMapEncodeTiled.
+bool tc_gemm_available() {
+  std::lock_guard<std::mutex> lock(tc::g_mu);
+  if (tc::g_state != 0) return tc::g_state > 0;
+  int dev = 0, major = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess || major != 10) {
+    tc::g_state = -1;
+    return false;
+  }
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || fn == nullptr) {
+    cudaGetLastError();
+    tc::g_state = -1;
+    return false;
+  }
+  tc::g_encode = reinterpret_cast<tc::EncodeFn>(fn);
+  if (cudaFuncSetAttribute(tc::k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    tc::g_state = -1;
+    return false;
+  }
+  tc::g_state = 1;
+  return true;
+}
+
+// C = alpha A B^T + beta C0 with A (M x K, lda) and B (N x K, ldb) row-major;
+// K a multiple of 32, lda/ldb/ldc multiples of 4.  Returns false when a tensor
+// map cannot be encoded (nothing is launched then).
+bool launch_tc_gemm(cudaStream_t s, const GemmBatch<float> &b, int M, int N, int K, int lda, int ldb, int ldc,
+                    bool lower, int passes, int32_t *err) {
+  if (b.count <= 0) return true;
+  if (!tc_gemm_available()) return false;
+  tc::Params p;
+  memset(&p, 0, sizeof(p));
+  for (int q = 0; q < b.count; ++q) {
+    if (!tc::encode_2d(&p.tmA[q], b.e[q].A, M, K, lda) || !tc::encode_2d(&p.tmB[q], b.e[q].B, N, K, ldb))
+      return false;
+    p.C[q] = b.e[q].C;
+    p.C0[q] = b.e[q].C0;
+    p.alpha[q] = (float)b.e[q].alpha;
+    p.beta[q] = (float)b.e[q].beta;
+  }
+  p.M = M;
+  p.N = N;
+  p.K = K;
+  p.ldc = ldc;
+  p.lower = lower ? 1 : 0;
+  p.passes = passes;
+  p.err = err;
+  ++g_launch_count;
+  Profiler::Rec rec{PROF_GEMM, nullptr, nullptr, 0.0};
+  const int gm = (M + tc::BM - 1) / tc::BM, gn = (N + tc::BN - 1) / tc::BN;
+  if (g_prof) {
+    const double tiles = lower ? (double)gm * (gm + 1) / 2 : (double)gm * gn;
+    rec.work = 2.0 * tc::BM * tc::BN * (double)K * tiles * b.count;
+    g_prof->begin(s, rec);
+  }
+  tc::k_tc_gemm<<<dim3(gn, gm, b.count), 192, tc::SMEM_BYTES, s>>>(p);
+  if (g_prof) g_prof->end(s, rec);
+  return true;
+}
+
+}  // namespace qsel

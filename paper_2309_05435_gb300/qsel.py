@@ -38,7 +38,7 @@ class qsel_partition(ctypes.Structure):
 class qsel_options(ctypes.Structure):
     _fields_ = [("n_samples", c_int32), ("seed", c_uint64), ("precision", c_int32), ("pcg_tol", c_double),
                 ("pcg_max_iter", c_int32), ("precond_block", c_int32), ("control_variate", c_int32),
-                ("cuda_stream", c_void_p), ("profile_kernels", c_int32)]
+                ("cuda_stream", c_void_p), ("profile_kernels", c_int32), ("tensor_passes", c_int32)]
 
 
 class qsel_stats_t(ctypes.Structure):
@@ -134,7 +134,7 @@ class Context:
 def qsel_create(n_s, n_t, c_diag, g_rowptr, g_col, g_val, obs_mask, sigma, theta, n_parts=1,
                 slab_start=None, overlap=0, n_samples=64, seed=0, precision=QSEL_FP64, pcg_tol=1e-10,
                 pcg_max_iter=20000, precond_block=0, control_variate=0, cuda_stream=None,
-                profile_kernels=0) -> Context:
+                profile_kernels=0, tensor_passes=0) -> Context:
     """Create a context from host arrays (copied by the library)."""
     lib = load_library()
     c = np.ascontiguousarray(c_diag, dtype=np.float64)
@@ -151,7 +151,8 @@ def qsel_create(n_s, n_t, c_diag, g_rowptr, g_col, g_val, obs_mask, sigma, theta
     part = qsel_partition(int(n_parts), _ptr(ss, c_int32) if ss is not None else None)
     opt = qsel_options(int(n_samples), int(seed), int(precision), float(pcg_tol), int(pcg_max_iter),
                        int(precond_block), int(control_variate),
-                       c_void_p(int(cuda_stream)) if cuda_stream else None, int(profile_kernels))
+                       c_void_p(int(cuda_stream)) if cuda_stream else None, int(profile_kernels),
+                       int(tensor_passes))
     h = c_void_p()
     st = lib.qsel_create(ctypes.byref(h), ctypes.byref(model), ctypes.byref(th), ctypes.byref(part),
                          int(overlap), ctypes.byref(opt))
