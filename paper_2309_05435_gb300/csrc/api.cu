@@ -655,7 +655,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       }
     }
     launch_schur_assemble<T>(s, sb, c->pat, c->d_qs, c->obs_w, n_s, n_pad);
-    spd_inverse<T>(s, wb, n_pad, c->d_err);
+    spd_inverse<T>(s, wb, n_pad, c->d_err, c->tc_passes);
     launch_sp_rowgather<T, T>(s, gb, c->pat, c->d_qs, n_s, n_pad, n_pad, n_pad, n_pad);
   }
   QSEL_CUDA_TRY(cudaGetLastError());

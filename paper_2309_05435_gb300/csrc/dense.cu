@@ -17,6 +17,8 @@
 #include "kernels.cuh"
 #include "sweep.cuh"
 
+#include <type_traits>
+
 namespace qsel {
 
 // ---------------------------------------------------------------------------
@@ -214,6 +216,67 @@ __global__ void __launch_bounds__(256) k_sweep_panel(SweepBatch<T> bt, int k, in
     for (int b = 0; b < 4; ++b) U[(ty + 16 * a) * 64 + tx + 16 * b] = acc[a][b];
 }
 
+// Tensor-core variant of the panel: U_i = A_ik P, V_i = A_ik for i != k and
+// U_k = V_k = 0, so that the rank-64 update C -= U V^T over all lower tiles
+// leaves row and column k unchanged (k_sweep_panel_write fills them after).
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_panel_tc(SweepBatch<T> bt, int k, int ld) {
+  __shared__ TileSmem<T> sm;
+  const SweepEntry<T> e = bt.e[blockIdx.y];
+  const int i = blockIdx.x;
+  T *U = e.U + (int64_t)i * 64 * 64;
+  T *V = e.V + (int64_t)i * 64 * 64;
+  if (i == k) {
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) {
+      U[idx] = T(0);
+      V[idx] = T(0);
+    }
+    return;
+  }
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  if (i > k) {
+    const T *C = e.A + (int64_t)i * 64 * ld + k * 64;
+    tile_mma<false, false>(sm, C, ld, e.P, 64, 64, acc);
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) V[idx] = C[(int64_t)(idx >> 6) * ld + (idx & 63)];
+  } else {
+    const T *C = e.A + (int64_t)k * 64 * ld + i * 64;
+    tile_mma<true, false>(sm, C, ld, e.P, 64, 64, acc);
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) V[idx] = C[(int64_t)(idx & 63) * ld + (idx >> 6)];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) U[(ty + 16 * a) * 64 + tx + 16 * b] = acc[a][b];
+}
+
+// Row/column k after the tensor-core update: A_ik <- U_i (i > k),
+// A_kj <- U_j^T (j < k), A_kk <- -P.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_panel_write(SweepBatch<T> bt, int k, int ld) {
+  const SweepEntry<T> e = bt.e[blockIdx.y];
+  const int i = blockIdx.x;
+  if (i == k) {
+    T *Tkk = e.A + (int64_t)k * 64 * ld + k * 64;
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) Tkk[(int64_t)(idx >> 6) * ld + (idx & 63)] = -e.P[idx];
+  } else if (i > k) {
+    T *Tik = e.A + (int64_t)i * 64 * ld + k * 64;
+    const T *U = e.U + (int64_t)i * 4096;
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) Tik[(int64_t)(idx >> 6) * ld + (idx & 63)] = U[idx];
+  } else {
+    T *Tki = e.A + (int64_t)k * 64 * ld + i * 64;
+    const T *U = e.U + (int64_t)i * 4096;
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) {
+      const int r = idx >> 6, c = idx & 63;
+      Tki[(int64_t)r * ld + c] = U[c * 64 + r];
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_sweep_update(SweepBatch<T> bt, int k, int nt, int ld) {
   __shared__ TileSmem<T> sm;
@@ -293,10 +356,45 @@ __global__ void __launch_bounds__(256) k_sweep_mirror(SweepBatch<T> bt, int ld, 
 }
 
 template <typename T>
-void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err_flag) {
+void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err_flag, int tc_passes) {
   if (b.count <= 0) return;
   const int nt = n_pad / 64;
   const int n_lower = nt * (nt + 1) / 2;
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc_passes > 0) {
+      // rank-64 updates on the tensor cores: C -= U V^T over the lower 128-tiles
+      GemmBatch<float> gb{};
+      gb.count = b.count;
+      for (int q = 0; q < b.count; ++q) {
+        gb.e[q].A = b.e[q].U;
+        gb.e[q].B = b.e[q].V;
+        gb.e[q].C0 = b.e[q].A;
+        gb.e[q].C = b.e[q].A;
+        gb.e[q].alpha = -1.0;
+        gb.e[q].beta = 1.0;
+      }
+      for (int k = 0; k < nt; ++k) {
+        g_launch_count += 3;
+        k_sweep_pivot<T><<<b.count, 256, 0, s>>>(b, k, n_pad, err_flag);
+        k_sweep_panel_tc<T><<<dim3(nt, b.count), 256, 0, s>>>(b, k, n_pad);
+        Profiler::Rec rec{PROF_SWEEP, nullptr, nullptr, 0.0};
+        if (g_prof) {
+          rec.work = 2.0 * 64.0 * 64.0 * 64.0 * ((double)n_lower - nt) * b.count;
+          g_prof->begin(s, rec);
+        }
+        const bool prof = g_prof != nullptr;
+        Profiler *saved = g_prof;
+        g_prof = nullptr;  // timed as the sweep, not as a GEMM
+        launch_tc_gemm(s, gb, n_pad, n_pad, 64, 64, 64, n_pad, true, tc_passes, err_flag);
+        g_prof = saved;
+        if (prof) g_prof->end(s, rec);
+        k_sweep_panel_write<T><<<dim3(nt, b.count), 256, 0, s>>>(b, k, n_pad);
+      }
+      ++g_launch_count;
+      k_sweep_mirror<T><<<dim3(n_lower, b.count), 256, 0, s>>>(b, n_pad, -1.0);
+      return;
+    }
+  }
   for (int k = 0; k < nt; ++k) {
     g_launch_count += 3;
     k_sweep_pivot<T><<<b.count, 256, 0, s>>>(b, k, n_pad, err_flag);
@@ -314,8 +412,8 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
   ++g_launch_count;
   k_sweep_mirror<T><<<dim3(n_lower, b.count), 256, 0, s>>>(b, n_pad, -1.0);
 }
-template void spd_inverse<double>(cudaStream_t, const SweepBatch<double> &, int, int32_t *);
-template void spd_inverse<float>(cudaStream_t, const SweepBatch<float> &, int, int32_t *);
+template void spd_inverse<double>(cudaStream_t, const SweepBatch<double> &, int, int32_t *, int);
+template void spd_inverse<float>(cudaStream_t, const SweepBatch<float> &, int, int32_t *, int);
 
 template <typename T>
 void launch_mirror(cudaStream_t s, const SweepBatch<T> &b, int n_pad) {
@@ -471,17 +569,19 @@ __global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch<T> bt, SellPa
     const int sl = l >> 5, li = l & 31;
     const int w = pat.slice_width[sl];
     const int base = pat.slice_ptr[sl] + li;
-    double acc = 0.0, aq = 0.0;
+    // the Schur term accumulates in T (FP32 in the mixed path)
+    T acc = T(0);
+    double aq = 0.0;
     const T *Wr = e.W ? e.W + (int64_t)r * n_pad : nullptr;
     for (int s = 0; s < w; ++s) {
       const int j = pat.col[base + s * kSlice];
       const double v = qs[base + s * kSlice];
-      if (Wr) acc = fma((double)Wr[j], v, acc);
+      if (Wr) acc = fma(Wr[j], (T)v, acc);
       if (j == r) aq += v;
     }
     out = (*e.a0) * aq;
     if (r == l && e.obs[r]) out += obs_w;
-    if (Wr) out -= (*e.c) * acc;
+    if (Wr) out -= (*e.c) * (double)acc;
   } else {
     out = (r == l) ? 1.0 : 0.0;
   }

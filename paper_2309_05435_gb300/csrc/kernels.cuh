@@ -86,6 +86,7 @@ struct BtSpmmArgs {
   T *y;
   double *dot_partial;    // if non-null: per-CTA per-column partial sums of x*y
 };
+// Number of dot-partial rows launch_bt_spmm writes.
 int bt_spmm_grid(int n_rows);
 template <typename T>
 void launch_bt_spmm(cudaStream_t s, const BtSpmmArgs<T> &a);
@@ -160,9 +161,10 @@ struct SweepBatch {
 };
 // In-place SPD inverse by the blocked symmetric sweep; A becomes A^-1 with
 // both triangles filled.  The 64 x 64 pivot tiles are always inverted in
-// double.  err_flag gets bit 0 on a non-positive pivot.
+// double.  err_flag gets bit 0 on a non-positive pivot.  For float with
+// tc_passes > 0 the rank-64 updates run on the tcgen05 tensor cores.
 template <typename T>
-void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err_flag);
+void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err_flag, int tc_passes = 0);
 // Copy the lower tiles of each e[].A into its upper triangle (symmetric fill).
 template <typename T>
 void launch_mirror(cudaStream_t s, const SweepBatch<T> &b, int n_pad);

@@ -8,6 +8,9 @@
 #include "kernels.cuh"
 #include "sweep.cuh"
 
+#include <algorithm>
+#include <type_traits>
+
 namespace qsel {
 
 // ---------------------------------------------------------------------------
@@ -159,6 +162,8 @@ int bt_spmm_grid(int n_rows) {
   int g = (n_rows + 7) / 8;
   return g < kSpmmGridMax ? (g < 1 ? 1 : g) : kSpmmGridMax;
 }
+
+
 
 template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs<T> a) {
@@ -360,6 +365,47 @@ int pcg_update_grid(int n) {
   return tiles < kUpdGrid ? tiles : kUpdGrid;
 }
 
+// x += alpha p, r -= alpha q: streaming, 16-byte vectors, grid-stride.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pcg_axpy(PcgVec<T> v) {
+  using V4 = typename std::conditional<std::is_same<T, float>::value, float4, double2>::type;
+  constexpr int E = (int)(sizeof(V4) / sizeof(T));
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // the reduction that follows accumulates into these
+    v.counters[0] = 0;
+    v.max_rel[0] = 0.0;
+  }
+  const int64_t total = (int64_t)v.n * v.ld / E;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)((e * E) % v.ld);
+    T al[E];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      al[q] = (T)v.alpha[c + q];
+      any |= al[q] != T(0);
+    }
+    if (!any) continue;
+    V4 x = reinterpret_cast<const V4 *>(v.x)[e];
+    V4 r = reinterpret_cast<const V4 *>(v.r)[e];
+    const V4 p = reinterpret_cast<const V4 *>(v.p)[e];
+    const V4 qq = reinterpret_cast<const V4 *>(v.q)[e];
+    T *xs = reinterpret_cast<T *>(&x);
+    T *rs = reinterpret_cast<T *>(&r);
+    const T *ps = reinterpret_cast<const T *>(&p);
+    const T *qs = reinterpret_cast<const T *>(&qq);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      xs[q] = fma(al[q], ps[q], xs[q]);
+      rs[q] = fma(-al[q], qs[q], rs[q]);
+    }
+    reinterpret_cast<V4 *>(v.x)[e] = x;
+    reinterpret_cast<V4 *>(v.r)[e] = r;
+  }
+}
+
+// z = P r for 64-row tiles (block Jacobi, P blocks transposed in shared
+// memory, 16 rows per thread) and per-column partial sums <r, z>, <r, r>.
 template <typename T>
 __global__ void __launch_bounds__(256) k_pcg_update(PcgVec<T> v, const T *__restrict__ pblk, int b) {
   extern __shared__ __align__(16) unsigned char smem_upd_raw[];
@@ -370,14 +416,8 @@ __global__ void __launch_bounds__(256) k_pcg_update(PcgVec<T> v, const T *__rest
   const int n_blocks = (v.n + b - 1) / b;
   const int n_tiles = (v.n + 63) / 64;
   const int lc = threadIdx.x & 63, rg = threadIdx.x >> 6;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    // the reduction that follows accumulates into these
-    v.counters[0] = 0;
-    v.max_rel[0] = 0.0;
-  }
   for (int c0 = 0; c0 < v.ld; c0 += 64) {
     const int col = c0 + lc;
-    const T al = (T)v.alpha[col];
     T sa = T(0), sb = T(0);
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
       const int r0 = tile * 64;
@@ -392,24 +432,18 @@ __global__ void __launch_bounds__(256) k_pcg_update(PcgVec<T> v, const T *__rest
           const int r = rem / b, j = rem - r * b;
           Ps[blk * b * b + j * b + r] = (base + e < lim) ? pblk[base + e] : T(0);
         }
-      }
-      for (int rr = rg; rr < 64; rr += 4) {
-        T rv = T(0);
-        if (rr < rows) {
-          const int64_t idx = (int64_t)(r0 + rr) * v.ld + col;
-          rv = v.r[idx];
-          if (al != T(0)) {
-            v.x[idx] = fma(al, v.p[idx], v.x[idx]);
-            rv = fma(-al, v.q[idx], rv);
-            v.r[idx] = rv;
-          }
+        T rv[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const int rr = rg + 4 * m;
+          rv[m] = (rr < rows) ? v.r[(int64_t)(r0 + rr) * v.ld + col] : T(0);
         }
-        rs[rr * 65 + lc] = rv;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) rs[(rg + 4 * m) * 65 + lc] = rv[m];
       }
       __syncthreads();
       if (b >= 16) {
-        // thread rows rg*16 .. rg*16+15 lie in one block: 16 accumulators, each
-        // r value read once, the 16 P entries of a column as broadcasts
+        // thread rows rg*16 .. rg*16+15 lie in one block: 16 accumulators
         const int rbase = rg * 16;
         const int blk = rbase / b, bo = rbase - blk * b;
         const T *Pt = Ps + blk * b * b + bo;
@@ -467,7 +501,10 @@ void launch_pcg_update(cudaStream_t s, const PcgVec<T> &v, const T *pblk, int bs
     cudaFuncSetAttribute(k_pcg_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, pcg_update_smem<T>());
     attr_set = true;
   }
-  ++g_launch_count;
+  g_launch_count += 2;
+  const int64_t vec = (int64_t)v.n * v.ld / (16 / (int)sizeof(T));
+  const int grid = (int)std::min<int64_t>((vec + 255) / 256, 152 * 8);
+  k_pcg_axpy<T><<<grid, 256, 0, s>>>(v);
   k_pcg_update<T><<<v.n_tiles, 256, pcg_update_smem<T>(), s>>>(v, pblk, bsize);  // n_tiles = grid
 }
 template void launch_pcg_update<double>(cudaStream_t, const PcgVec<double> &, const double *, int);
@@ -551,25 +588,30 @@ template void launch_pcg_reduce_beta<float>(cudaStream_t, const PcgVec<float> &,
 // p = z + beta p  (p = z where beta is zero, so stale values never leak in).
 template <typename T>
 __global__ void k_pcg_p_update(PcgVec<T> v) {
-  const int64_t total = (int64_t)v.n * v.ld;
-  for (int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 2; e < total;
-       e += (int64_t)gridDim.x * blockDim.x * 2) {
-    const int c = (int)(e % v.ld);
-    const auto z = load2(v.z + e);
-    auto p = load2(v.p + e);
-    const T b0 = (T)v.beta[c], b1 = (T)v.beta[c + 1];
-    const T p0 = (b0 != T(0)) ? fma(b0, p.x, z.x) : z.x;
-    const T p1 = (b1 != T(0)) ? fma(b1, p.y, z.y) : z.y;
-    store2(v.p + e, p0, p1);
+  using V4 = typename std::conditional<std::is_same<T, float>::value, float4, double2>::type;
+  constexpr int E = (int)(sizeof(V4) / sizeof(T));
+  const int64_t total = (int64_t)v.n * v.ld / E;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)((e * E) % v.ld);
+    const V4 z = reinterpret_cast<const V4 *>(v.z)[e];
+    V4 p = reinterpret_cast<const V4 *>(v.p)[e];
+    const T *zs = reinterpret_cast<const T *>(&z);
+    T *ps = reinterpret_cast<T *>(&p);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const T bq = (T)v.beta[c + q];
+      ps[q] = (bq != T(0)) ? fma(bq, ps[q], zs[q]) : zs[q];
+    }
+    reinterpret_cast<V4 *>(v.p)[e] = p;
   }
 }
 
 template <typename T>
 void launch_pcg_p_update(cudaStream_t s, const PcgVec<T> &v) {
   ++g_launch_count;
-  int64_t total = (int64_t)v.n * v.ld / 2;
+  int64_t total = (int64_t)v.n * v.ld / (16 / (int)sizeof(T));
   int grid = (int)((total + 255) / 256);
-  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid > 152 * 8) grid = 152 * 8;
   k_pcg_p_update<T><<<grid, 256, 0, s>>>(v);
 }
 template void launch_pcg_p_update<double>(cudaStream_t, const PcgVec<double> &);
