@@ -12,10 +12,13 @@ Features of node (t, i) (14 values):
   0      log Q_ii
   1..8   log |Q_il| of the 8 largest off-diagonal entries of row (t, i),
          sorted descending (log of 1e-30 where the row has fewer)
-  9      time distance from slab t to the nearest separator slab (n_t when
-         there is none)
+  9      time distance from slab t to the nearest separator slab of its
+         subdomain, capped at SEPARATOR_CAP (the cap also when there is none)
   10     graph distance from node i to the mesh boundary (boundary = nodes
-         with fewer stiffness neighbours than the maximum)
+         with fewer stiffness neighbours than the maximum), capped at
+         BOUNDARY_CAP
+Both distances are capped so that a network trained on small models sees
+the same feature range as the large models it is applied to.
   11..13 theta = (log kappa, log tau, logit rho)
 Network: 14 -> 64 -> 64 -> 1, GELU (erf form) on both hidden layers, inputs
 standardised with fixed per-feature mean and scale; the output is
@@ -34,11 +37,14 @@ from . import qsel_oracle as o
 
 N_FEATURES = 14
 HIDDEN = 64
+SEPARATOR_CAP = 16.0
+BOUNDARY_CAP = 8.0
 
 
 def boundary_distance(model: o.Model) -> np.ndarray:
     """Graph distance (stiffness graph) from each spatial node to the nearest
-    boundary node; boundary nodes have fewer neighbours than the maximum."""
+    boundary node, capped at BOUNDARY_CAP; boundary nodes have fewer
+    neighbours than the maximum."""
     G = model.G.tocsr()
     deg = np.array([np.count_nonzero(G.indices[G.indptr[i]:G.indptr[i + 1]] != i) for i in range(model.n_s)])
     dist = np.full(model.n_s, -1, dtype=np.int64)
@@ -54,17 +60,18 @@ def boundary_distance(model: o.Model) -> np.ndarray:
             if dist[j] < 0:
                 dist[j] = dist[i] + 1
                 q.append(j)
-    return dist.astype(np.float64)
+    return np.minimum(dist.astype(np.float64), BOUNDARY_CAP)
 
 
 def separator_distance(n_t: int, slab_start, n_l: int) -> np.ndarray:
     """For every slab: distance to the nearest separator slab of the
-    subdomain that owns it (n_t when that subdomain has no separator)."""
+    subdomain that owns it, capped at SEPARATOR_CAP (the cap when that
+    subdomain has no separator)."""
     out = np.zeros(n_t)
     for part in o.partition(n_t, slab_start, n_l):
         s0, s1 = part.own
         for t in range(s0, s1):
-            out[t] = min([abs(t - s) for s in part.sep], default=n_t)
+            out[t] = min([abs(t - s) for s in part.sep] + [SEPARATOR_CAP])
     return out
 
 

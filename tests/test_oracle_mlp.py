@@ -65,3 +65,19 @@ def test_features_closed_forms_on_grid():
     row[r] = 0
     top = np.sort(row[row > 0])[::-1][:8]
     np.testing.assert_allclose(F[r, 1:9], np.log(top), rtol=1e-13)
+
+
+def test_feature_distance_caps():
+    # 20x20 grid: the boundary distance min(x, y, 19 - x, 19 - y) reaches 9,
+    # capped at 8; one part has no separator, so every slab gets the cap
+    mdl = grid_model(20, 3, obs_frac=0.3)
+    th = theta(0.5, 1.3, 0.8)
+    F = m.features(mdl, th, [0, 3], 1)
+    xs, ys = np.divmod(np.arange(400), 20)
+    bd = np.minimum(np.minimum(np.minimum(xs, ys), np.minimum(19 - xs, 19 - ys)), 8)
+    assert bd.max() == 8 and (np.minimum(np.minimum(xs, ys), np.minimum(19 - xs, 19 - ys)) == 9).any()
+    np.testing.assert_array_equal(F[:400, 10], bd)
+    np.testing.assert_array_equal(F[::400, 9], [m.SEPARATOR_CAP] * 3)
+    # 40 slabs in 2 parts with overlap 1: ext [0,21) sep {21}; slab 0 is 21 away, capped
+    sep = m.separator_distance(40, o.balanced_slab_start(40, 2), 1)
+    assert sep[0] == m.SEPARATOR_CAP and sep[19] == 2 and sep[20] == 2 and sep[39] == m.SEPARATOR_CAP
