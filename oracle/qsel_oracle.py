@@ -314,6 +314,7 @@ class SubdomainResult:
     part: Part
     sigma_star_diag: np.ndarray     # diag(Q_{**}^-1) for rows of Omega_p
     corr_diag: np.ndarray           # (1/k) sum_s w_i^2 for rows of Omega_p
+    corr4_diag: np.ndarray          # (1/k) sum_s w_i^4 for rows of Omega_p
     traces: np.ndarray              # partial traces over rows of Omega_p (3,)
 
 
@@ -347,6 +348,7 @@ def subdomain_estimate(Q, dQs, n_s: int, part: Part, X_sep: dict, k: int):
     own_rows = range(s0 - e0, s1 - e0)
     sig_diag = np.concatenate([np.diag(Sd[t]) for t in own_rows])
     corr = np.concatenate([np.sum(w[t] ** 2, axis=1) / k for t in own_rows])
+    corr4 = np.concatenate([np.sum(w[t] ** 4, axis=1) / k for t in own_rows])
 
     traces = np.zeros(len(dQs))
     for j, dQ in enumerate(dQs):
@@ -364,7 +366,7 @@ def subdomain_estimate(Q, dQs, n_s: int, part: Part, X_sep: dict, k: int):
                 sel = sig + (w[t] @ w[u].T) / k
                 acc += float(np.sum(sel * block(dQ, n_s, e0 + t, e0 + u)))
         traces[j] = acc
-    return SubdomainResult(part, sig_diag, corr, traces)
+    return SubdomainResult(part, sig_diag, corr, corr4, traces)
 
 
 def rbmc(model: Model, theta, slab_start, n_l: int, X: np.ndarray):
@@ -388,6 +390,25 @@ def rbmc(model: Model, theta, slab_start, n_l: int, X: np.ndarray):
         t_hat += res.traces
         results.append(res)
     return v, t_hat, results
+
+
+def error_estimate(v: np.ndarray, results, k: int):
+    """Sample-based standard error of the RBMC estimate (Algorithm 4): the
+    correction of node i is the mean of k values w_i^2, whose variance is
+    estimated by (m4_i - m2_i^2) / (k - 1) with m2, m4 the sample means of
+    w_i^2 and w_i^4.  Returns (per part, global) root mean square over rows of
+    the standard error relative to v_i."""
+    per_part, tot, rows = [], 0.0, 0
+    for res in results:
+        s0, s1 = res.part.own
+        n_s = res.corr_diag.size // (s1 - s0)
+        vv = v[s0 * n_s:s1 * n_s]
+        var = np.maximum(res.corr4_diag - res.corr_diag ** 2, 0.0) / (k - 1)
+        q = var / vv ** 2
+        per_part.append(math.sqrt(q.mean()))
+        tot += q.sum()
+        rows += q.size
+    return np.array(per_part), math.sqrt(tot / rows)
 
 
 # ----------------------------------------------------------------------------

@@ -121,6 +121,29 @@ def test_ar1_error_law_profile():
     assert abs(rmse / math.sqrt(2 / k) - 1) < 0.2, rmse
 
 
+def test_error_estimate_ar1_closed_form():
+    """AR(1) example of Section 3.2.3: w_i = phi^d x_s (separator x_s, distance
+    d), so m2_i = phi^(2d) mean(x_s^2) and m4_i = phi^(4d) mean(x_s^4); the
+    estimated variance of the correction is phi^(4d) (mean x^4 - mean(x^2)^2)
+    / (k - 1), written here from the raw separator samples."""
+    phi, k = 0.95, 64
+    model, th = ar1_model(99, phi)
+    X = o.samples(model, th, 7, k)
+    v, _, res = o.rbmc(model, th, np.array([0, 50, 99]), 0, X)
+    part_err, glob = o.error_estimate(v, res, k)
+    q = []
+    for rows, sep in ((np.arange(50), 50), (np.arange(50, 99), 49)):
+        x = X[sep]
+        d = np.abs(rows - sep)
+        var = phi ** (4 * d) * (np.mean(x ** 4) - np.mean(x ** 2) ** 2) / (k - 1)
+        q.append(var / v[rows] ** 2)
+    np.testing.assert_allclose(part_err, [math.sqrt(a.mean()) for a in q], rtol=1e-12)
+    assert abs(glob - math.sqrt(np.concatenate(q).mean())) <= 1e-12 * glob
+    # a single part has no separator and zero error
+    v1, _, r1 = o.rbmc(model, th, np.array([0, 99]), 0, X)
+    assert o.error_estimate(v1, r1, k)[1] == 0.0
+
+
 @pytest.mark.slow
 def test_rbmc_unbiased_over_seeds():
     """E[v_hat] = diag(Q^-1) and E[t_hat] = t (Eq. var:2): per-node z-scores
