@@ -123,6 +123,10 @@ typedef struct {
                              GPU has tcgen05 tensor cores, else CUDA cores),
                              3 = 3xTF32 (FP32-level accuracy), 1 = plain TF32,
                              -1 = FP32 CUDA cores.  Ignored for QSEL_FP64.        */
+  const int32_t *part_overlap;/* HOST array of n_parts overlaps n_l,p >= 0 (one per
+                             part, read at qsel_create), or NULL: every part uses
+                             the `overlap` argument.  Lets a planner
+                             (qsel_cv_plan) extend each subdomain differently. */
 } qsel_options;
 
 /* Per-call statistics of the last qsel_diag_inv. */
@@ -189,6 +193,19 @@ qsel_status qsel_trace_grads(qsel_ctx *ctx, double grads_out[3]);
 qsel_status qsel_stats(const qsel_ctx *ctx, qsel_stats_t *stats);
 
 /*
+ * Sample-based error estimate of the last diag(Q^-1) estimate.  The
+ * correction of node i is the mean of k values w_i^2 (Algorithm 4); its
+ * variance is estimated by (m4_i - m2_i^2) / (k - 1) with m2, m4 the sample
+ * means of w_i^2 and w_i^4.  Reported per part p as the root mean square over
+ * the rows of Omega_p of (standard error / estimate):
+ *   part_err   HOST array of n_parts doubles, or NULL;
+ *   global_err HOST double, the same over all rows (NULL allowed).
+ * Parts without separators have zero error.  QSEL_ESTATE if the pipeline has
+ * not run, QSEL_EINVAL if n_samples < 2.
+ */
+qsel_status qsel_error_estimate(qsel_ctx *ctx, double *part_err, double *global_err);
+
+/*
  * Stage-wise checking hooks.
  *
  * qsel_debug_set_samples: use X (HOST, n rows x n_samples columns, row-major
@@ -237,9 +254,110 @@ qsel_status qsel_debug_get_selinv_diag(const qsel_ctx *ctx, double *diag_out);
 #define QSEL_NOALLOC_MAX_N 1024
 qsel_status qsel_spd_inverse_noalloc(double *a_dev, int32_t n, int32_t lda, void *cuda_stream);
 
+/*
+ * Learned control variate.  The paper has no learned component; this part
+ * serves the choice of overlap and sample count that the paper makes by hand
+ * from the correlation range (Section 3.2.3, Section 6).  A 14-64-64-1 MLP
+ * with GELU (erf form) activations, BF16 weights and FP32 accumulation
+ * predicts, for every node, y_i = log(c_i / v_i): the share of the variance
+ * v_i = Sigma*_ii + c_i that the Rao-Blackwell correction c_i = E[w_i^2]
+ * carries.  Under Gaussian w the relative standard error of the k-sample
+ * estimate of node i is sqrt(2 / k) c_i / v_i, so the prediction tells how
+ * many samples and how much overlap a target error needs.  The estimate
+ * itself stays plain RBMC at the chosen (overlap, k): it is unbiased whatever
+ * the network predicts, and qsel_error_estimate judges the choice afterwards.
+ *
+ * Features of node (t, i), 14 floats per node, node order t * n_s + i:
+ *   0      log Q_ii
+ *   1..8   log |Q_il| of the 8 largest non-zero off-diagonal entries of the
+ *          row, descending (log 1e-30 where the row has fewer)
+ *   9      time distance from slab t to the nearest separator slab of the
+ *          subdomain that owns it, capped at 16 (16 when it has none)
+ *   10     graph distance of spatial node i to the mesh boundary (nodes with
+ *          fewer stiffness neighbours than the maximum), capped at 8
+ *   11..13 theta
+ * Parameters (float, QSEL_CV_PARAMS_ALL values): W1 (64 x 14, row-major),
+ * b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1), then the per-feature mean
+ * (14) and scale (14) that standardise the inputs.  The first QSEL_CV_PARAMS
+ * are trained.
+ */
+#define QSEL_CV_FEATURES 14
+#define QSEL_CV_PARAMS 5185
+#define QSEL_CV_PARAMS_ALL 5213
+
+typedef struct qsel_cv qsel_cv;
+
+/* Create a network with seeded Glorot-uniform weights, zero biases, mean 0
+ * and scale 1; work is issued on cuda_stream (NULL = legacy default). */
+qsel_status qsel_cv_create(qsel_cv **out, uint64_t seed, void *cuda_stream);
+/* Copy all QSEL_CV_PARAMS_ALL parameters from / to HOST memory (Adam state is
+ * kept on set). */
+qsel_status qsel_cv_set_params(qsel_cv *cv, const float *params);
+qsel_status qsel_cv_get_params(const qsel_cv *cv, float *params);
+/* y_dev[s] = network(X_dev[s, :]) for n samples; DEVICE buffers, X row-major
+ * n x QSEL_CV_FEATURES. */
+qsel_status qsel_cv_predict(const qsel_cv *cv, const float *X_dev, float *y_dev, int32_t n);
+/* Mean squared error (1/n) sum (network(X_s) - y_s)^2 and its gradient with
+ * respect to the QSEL_CV_PARAMS trained parameters (as used: BF16 weights),
+ * written to HOST grad_host (QSEL_CV_PARAMS floats) and loss_host (NULL
+ * allowed).  X_dev, y_dev as in qsel_cv_predict. */
+qsel_status qsel_cv_grad(qsel_cv *cv, const float *X_dev, const float *y_dev, int32_t n, float *grad_host,
+                         float *loss_host);
+/* `steps` full-batch Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate
+ * lr) on the FP32 master parameters, refreshing the BF16 copies after each.
+ * With set_input_stats the input mean and scale (standard deviation, at
+ * least 1e-3) are first set from X.  loss_out (HOST, NULL allowed) receives
+ * the loss of the final parameters. */
+qsel_status qsel_cv_train(qsel_cv *cv, const float *X_dev, const float *y_dev, int32_t n, int32_t steps, float lr,
+                          int32_t set_input_stats, float *loss_out);
+void qsel_cv_destroy(qsel_cv *cv);
+
+/* Features of ctx's model at its current theta and partition, with every
+ * part extended by `overlap` slabs (the context's own overlap is not used),
+ * written to F_dev (DEVICE, n x QSEL_CV_FEATURES floats). */
+qsel_status qsel_cv_features(qsel_ctx *ctx, int32_t overlap, float *F_dev);
+
+/* Training targets y_i = log(cbar_i / (Sigma*_ii + cbar_i)), cbar_i the mean
+ * correction over `count` contexts that ran the same model and theta with
+ * different seeds (their average is the RBMC estimate with all their samples);
+ * ratios below 1e-30 are clamped.  Each context must have run
+ * (qsel_diag_inv).  y_dev: DEVICE, n floats. */
+qsel_status qsel_cv_targets(qsel_ctx *const *ctxs, int32_t count, float *y_dev);
+
+/*
+ * Planner.  For every candidate overlap 1..max_overlap it predicts each part's
+ * mean squared ratio m_p = mean over Omega_p of (c_i / v_i)^2, so that k
+ * samples give the predicted error e_p(k) = sqrt(2 m_p / k).  It then picks
+ * one sample count k (a multiple of 32 in [min_samples, max_samples]; the
+ * samples are shared by every part) and per part the smallest overlap with
+ * e_p(k) <= target, minimising the modelled time
+ *   cost_pcg * k * n + sum_p T_p (cost_dense * n_pad^3 + cost_corr * k * n_pad^2),
+ * T_p = slabs of the extended part, n_pad = n_s rounded up to 64.
+ * Cost coefficients of 0 take GB300 mixed-precision defaults (seconds:
+ * 1.73e-8, 1.37e-13, 2.3e-13).  When no k meets the target everywhere the
+ * plan takes max_samples and max_overlap and sets feasible = 0.
+ */
+typedef struct {
+  double target_rel_err;      /* RMS relative standard error per part, > 0      */
+  int32_t max_overlap;        /* >= 1                                          */
+  int32_t min_samples, max_samples; /* 32 <= min <= max <= 512                  */
+  double cost_pcg, cost_dense, cost_corr;
+} qsel_cv_plan_options;
+
+typedef struct {
+  int32_t n_samples;          /* chosen k                                       */
+  int32_t feasible;           /* 1 if every part meets the target              */
+  double predicted_cost;      /* modelled seconds                              */
+  double predicted_err;       /* max over parts of the predicted error         */
+  int32_t *part_overlap;      /* caller-allocated HOST, n_parts: chosen n_l,p   */
+  double *part_pred_err;      /* caller-allocated HOST, n_parts, or NULL        */
+} qsel_cv_plan_t;
+
+qsel_status qsel_cv_plan(qsel_ctx *ctx, const qsel_cv *cv, const qsel_cv_plan_options *opt, qsel_cv_plan_t *plan);
+
 /* Message of the last failed call on ctx, or, when ctx is NULL, of the last
- * failed qsel_create or qsel_spd_inverse_noalloc on this thread.  Never NULL;
- * owned by the library. */
+ * failed qsel_create, qsel_spd_inverse_noalloc or qsel_cv_* call (those that
+ * take no context) on this thread.  Never NULL; owned by the library. */
 const char *qsel_last_error(const qsel_ctx *ctx);
 
 /* Free the context and its device memory.  NULL is allowed. */

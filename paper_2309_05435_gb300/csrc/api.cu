@@ -88,6 +88,12 @@ struct qsel_ctx {
   std::vector<DenseSlot> slots;
   int wave = 1, T_max = 1;
   double *d_diag = nullptr, *d_selinv = nullptr, *d_corr = nullptr, *d_traces = nullptr, *d_sums = nullptr;
+  double *d_corr4 = nullptr;           // (1/k) sum w^4 per node (error estimate)
+  std::vector<int> part_nl;            // overlap of every part
+  int32_t *d_slab_start = nullptr;     // n_parts + 1 slab offsets
+  double *d_part_sums = nullptr;       // n_parts doubles of per-part reductions
+  float *d_bnd = nullptr, *d_sepd = nullptr;  // feature distances: n_s nodes, n_t slabs
+  float *d_cv_F = nullptr, *d_cv_y = nullptr; // planner scratch, allocated on first use
   double *d_partials = nullptr, *d_diag_scratch = nullptr;
   TraceSlab *d_slabs = nullptr;
   int n_trace_slabs = 0;
@@ -188,6 +194,9 @@ static Err validate(const qsel_model *m, const qsel_theta *th, const qsel_partit
       if (part->slab_start[p + 1] <= part->slab_start[p])
         return fail(QSEL_EINVAL, "slab_start must be strictly increasing");
   }
+  if (opt->part_overlap)
+    for (int p = 0; p < np; ++p)
+      if (opt->part_overlap[p] < 0) return fail(QSEL_EINVAL, "part_overlap entries must be >= 0");
   if (opt->n_samples < 1 || opt->n_samples > 512) return fail(QSEL_EINVAL, "n_samples must be in [1, 512]");
   if (opt->precision != QSEL_FP64 && opt->precision != QSEL_MIXED)
     return fail(QSEL_EINVAL, "precision must be QSEL_FP64 or QSEL_MIXED");
@@ -314,7 +323,45 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
     c->slab_start[0] = 0;
     for (int p = 0; p < np; ++p) c->slab_start[p + 1] = c->slab_start[p] + base + (p < extra ? 1 : 0);
   }
-  c->n_l = overlap;
+  c->part_nl.assign(np, overlap);
+  if (c->opt.part_overlap)
+    for (int p = 0; p < np; ++p) c->part_nl[p] = c->opt.part_overlap[p];
+  c->opt.part_overlap = nullptr;   // the caller's array is not kept
+  c->n_l = *std::min_element(c->part_nl.begin(), c->part_nl.end());
+  {
+    std::vector<int32_t> ss(c->slab_start.begin(), c->slab_start.end());
+    TRY(upload(c, &c->d_slab_start, ss));
+  }
+  TRY(c->alloc(&c->d_part_sums, (size_t)np));
+
+  // graph distance of every spatial node to the mesh boundary (nodes with
+  // fewer stiffness neighbours than the maximum), capped at 8: an input of
+  // the control-variate features
+  {
+    std::vector<int> deg(n_s, 0), dist(n_s, -1), queue;
+    for (int i = 0; i < n_s; ++i)
+      for (int p = m->g_rowptr[i]; p < m->g_rowptr[i + 1]; ++p) deg[i] += (m->g_col[p] != i);
+    const int dmax = *std::max_element(deg.begin(), deg.end());
+    for (int i = 0; i < n_s; ++i)
+      if (deg[i] < dmax) {
+        dist[i] = 0;
+        queue.push_back(i);
+      }
+    for (size_t h = 0; h < queue.size(); ++h) {
+      const int i = queue[h];
+      for (int p = m->g_rowptr[i]; p < m->g_rowptr[i + 1]; ++p) {
+        const int j = m->g_col[p];
+        if (dist[j] < 0) {
+          dist[j] = dist[i] + 1;
+          queue.push_back(j);
+        }
+      }
+    }
+    std::vector<float> bnd(n_s);
+    for (int i = 0; i < n_s; ++i) bnd[i] = queue.empty() ? 0.f : (float)std::min(std::max(dist[i], 0), 8);
+    TRY(upload(c, &c->d_bnd, bnd));
+    TRY(c->alloc(&c->d_sepd, (size_t)c->n_t));
+  }
 
   // sampler buffers
   const size_t vec = (size_t)n * c->ld;
@@ -357,8 +404,8 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
     Subdomain sd;
     sd.s0 = c->slab_start[p];
     sd.s1 = c->slab_start[p + 1];
-    sd.e0 = std::max(0, sd.s0 - overlap);
-    sd.e1 = std::min(c->n_t, sd.s1 + overlap);
+    sd.e0 = std::max(0, sd.s0 - c->part_nl[p]);
+    sd.e1 = std::min(c->n_t, sd.s1 + c->part_nl[p]);
     sd.T = sd.e1 - sd.e0;
     sd.lo = sd.s0 - sd.e0;
     sd.hi = sd.s1 - 1 - sd.e0;
@@ -387,6 +434,7 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   TRY(c->alloc(&c->d_diag, (size_t)n));
   TRY(c->alloc(&c->d_selinv, (size_t)n));
   TRY(c->alloc(&c->d_corr, (size_t)n));
+  TRY(c->alloc(&c->d_corr4, (size_t)n));
   TRY(c->alloc(&c->d_traces, 4));
   TRY(c->alloc(&c->d_err, 4));
   TRY(c->alloc_bytes(reinterpret_cast<void **>(&c->d_diag_scratch), extract_scratch_bytes(n_pad)));
@@ -961,6 +1009,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       e.hi = sd.hi;
       e.e0 = sd.e0;
       e.corr_out = c->d_corr;
+      e.corr4_out = c->d_corr4;
       e.partial = sd.partial;
     }
     launch_correction_terms<T>(s, cb, c->pat, c->d_qs, c->d_dqs, c->tc.a0, c->tc.a1, c->tc.r0, c->tc.r1, n_s,
@@ -1009,6 +1058,7 @@ static Err run_pipeline_body(qsel_ctx *c) {
   c->phase_used = 0;
   QSEL_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), s));
   QSEL_CUDA_TRY(cudaMemsetAsync(c->d_corr, 0, (size_t)c->n * sizeof(double), s));
+  QSEL_CUDA_TRY(cudaMemsetAsync(c->d_corr4, 0, (size_t)c->n * sizeof(double), s));
   QSEL_CUDA_TRY(cudaEventRecord(c->ev[0], s));
   TRY(run_model(c));
   const bool need_samples = c->parts.size() > 1;
@@ -1218,6 +1268,160 @@ qsel_status qsel_debug_get_selinv_diag(const qsel_ctx *ctx, double *diag_out) {
                                    cudaMemcpyDeviceToHost, ctx->stream);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
   if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "copy of selected inverse", __FILE__, __LINE__));
+  return QSEL_OK;
+}
+
+qsel_status qsel_error_estimate(qsel_ctx *ctx, double *part_err, double *global_err) {
+  if (!ctx) return QSEL_EINVAL;
+  if (ctx->k < 2) return finish(ctx, fail(QSEL_EINVAL, "the error estimate needs n_samples >= 2"));
+  if (!ctx->computed) return finish(ctx, fail(QSEL_ESTATE, "pipeline has not run"));
+  const int np = (int)ctx->parts.size();
+  launch_part_error_sums(ctx->stream, ctx->d_corr, ctx->d_corr4, ctx->d_diag, ctx->d_slab_start, np, ctx->n_s,
+                         ctx->k, ctx->d_part_sums);
+  std::vector<double> sums(np);
+  cudaError_t ce = cudaMemcpyAsync(sums.data(), ctx->d_part_sums, np * sizeof(double), cudaMemcpyDeviceToHost,
+                                   ctx->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+  if (ce != cudaSuccess) return finish(ctx, cuda_fail(ce, "error estimate", __FILE__, __LINE__));
+  double tot = 0.0;
+  for (int p = 0; p < np; ++p) {
+    const double rows = (double)(ctx->slab_start[p + 1] - ctx->slab_start[p]) * ctx->n_s;
+    if (part_err) part_err[p] = std::sqrt(sums[p] / rows);
+    tot += sums[p];
+  }
+  if (global_err) *global_err = std::sqrt(tot / (double)ctx->n);
+  return QSEL_OK;
+}
+
+// Control-variate features of the current theta with every part extended by
+// `overlap` slabs (see qsel.h for the definition).
+static Err cv_features(qsel_ctx *c, int overlap, float *F_dev) {
+  const int np = (int)c->parts.size();
+  std::vector<float> sepd(c->n_t, 16.f);
+  for (int p = 0; p < np; ++p) {
+    const int s0 = c->slab_start[p], s1 = c->slab_start[p + 1];
+    const int e0 = std::max(0, s0 - overlap), e1 = std::min(c->n_t, s1 + overlap);
+    for (int t = s0; t < s1; ++t) {
+      float d = 16.f;
+      if (e0 > 0) d = std::min(d, (float)(t - (e0 - 1)));
+      if (e1 < c->n_t) d = std::min(d, (float)(e1 - t));
+      sepd[t] = d;
+    }
+  }
+  TRY(run_model(c));
+  QSEL_CUDA_TRY(cudaMemcpyAsync(c->d_sepd, sepd.data(), c->n_t * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  const double th[3] = {c->theta.log_kappa, c->theta.log_tau, c->theta.logit_rho};
+  launch_cv_features(c->stream, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t, c->d_sepd,
+                     c->d_bnd, th, F_dev);
+  QSEL_CUDA_TRY(cudaStreamSynchronize(c->stream));   // sepd is a host vector
+  QSEL_CUDA_TRY(cudaGetLastError());
+  return ok();
+}
+
+qsel_status qsel_cv_features(qsel_ctx *ctx, int32_t overlap, float *F_dev) {
+  if (!ctx) return QSEL_EINVAL;
+  if (!F_dev || overlap < 0) return finish(ctx, fail(QSEL_EINVAL, "F_dev must not be NULL and overlap >= 0"));
+  return finish(ctx, cv_features(ctx, overlap, F_dev));
+}
+
+qsel_status qsel_cv_targets(qsel_ctx *const *ctxs, int32_t count, float *y_dev) {
+  if (!ctxs || count < 1 || count > kCvMaxTargets || !y_dev) {
+    set_context_free_error("qsel_cv_targets: need 1..8 contexts and a target buffer");
+    return QSEL_EINVAL;
+  }
+  CvTargetArgs a{};
+  a.count = count;
+  for (int q = 0; q < count; ++q) {
+    if (!ctxs[q] || !ctxs[q]->computed || ctxs[q]->n != ctxs[0]->n) {
+      set_context_free_error("qsel_cv_targets: every context must have run on a model of the same size");
+      return ctxs[q] ? QSEL_ESTATE : QSEL_EINVAL;
+    }
+    a.corr[q] = ctxs[q]->d_corr;
+  }
+  qsel_ctx *c = ctxs[0];
+  launch_cv_targets(c->stream, a, c->d_selinv, c->n, y_dev);
+  cudaError_t ce = cudaStreamSynchronize(c->stream);
+  if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "control-variate targets", __FILE__, __LINE__));
+  return QSEL_OK;
+}
+
+qsel_status qsel_cv_plan(qsel_ctx *ctx, const qsel_cv *cv, const qsel_cv_plan_options *o, qsel_cv_plan_t *plan) {
+  if (!ctx) return QSEL_EINVAL;
+  if (!cv || !o || !plan || !plan->part_overlap) return finish(ctx, fail(QSEL_EINVAL, "NULL argument"));
+  if (!(o->target_rel_err > 0.0) || o->max_overlap < 1 || o->min_samples < 32 || o->max_samples > 512 ||
+      o->min_samples > o->max_samples)
+    return finish(ctx, fail(QSEL_EINVAL, "plan options: target > 0, max_overlap >= 1, 32 <= min <= max <= 512"));
+  qsel_ctx *c = ctx;
+  const int np = (int)c->parts.size();
+  if (!c->d_cv_F) {
+    Err e = c->alloc(&c->d_cv_F, (size_t)c->n * QSEL_CV_FEATURES);
+    if (e.code == 0) e = c->alloc(&c->d_cv_y, (size_t)c->n);
+    if (e.code) return finish(c, e);
+  }
+  // m2[nl][p]: mean over Omega_p of the predicted (c_i / v_i)^2
+  std::vector<std::vector<double>> m2(o->max_overlap + 1, std::vector<double>(np, 0.0));
+  for (int nl = 1; nl <= o->max_overlap; ++nl) {
+    Err e = cv_features(c, nl, c->d_cv_F);
+    if (e.code) return finish(c, e);
+    qsel_status st = qsel_cv_predict(cv, c->d_cv_F, c->d_cv_y, c->n);
+    if (st) return finish(c, fail(st, std::string("planner prediction: ") + qsel_last_error(nullptr)));
+    launch_cv_part_m2(c->stream, c->d_cv_y, c->d_slab_start, np, c->n_s, c->d_part_sums);
+    cudaError_t ce = cudaMemcpyAsync(m2[nl].data(), c->d_part_sums, np * sizeof(double), cudaMemcpyDeviceToHost,
+                                     c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "planner reduction", __FILE__, __LINE__));
+    for (int p = 0; p < np; ++p) m2[nl][p] /= (double)(c->slab_start[p + 1] - c->slab_start[p]) * c->n_s;
+  }
+  const double cp = o->cost_pcg > 0 ? o->cost_pcg : 1.73e-8;
+  const double cd = o->cost_dense > 0 ? o->cost_dense : 1.37e-13;
+  const double cc = o->cost_corr > 0 ? o->cost_corr : 2.3e-13;
+  const double npad = (double)c->n_pad;
+  auto slabs = [&](int p, int nl) {
+    return std::min(c->n_t, c->slab_start[p + 1] + nl) - std::max(0, c->slab_start[p] - nl);
+  };
+  auto err = [&](int p, int nl, int k) { return std::sqrt(2.0 * m2[nl][p] / k); };
+  const int k_lo = round_up(o->min_samples, 32);
+  double best = -1.0;
+  std::vector<int> choice(np), best_choice(np);
+  int best_k = 0;
+  for (int k = k_lo; k <= o->max_samples; k += 32) {
+    double cost = cp * (double)k * c->n;
+    bool feasible = true;
+    for (int p = 0; p < np && feasible; ++p) {
+      int pick = -1;
+      for (int nl = 1; nl <= o->max_overlap; ++nl)
+        if (err(p, nl, k) <= o->target_rel_err) {
+          pick = nl;
+          break;
+        }
+      if (pick < 0) feasible = false;
+      choice[p] = pick;
+      if (feasible) cost += slabs(p, pick) * (cd * npad * npad * npad + cc * k * npad * npad);
+    }
+    if (feasible && (best < 0 || cost < best)) {
+      best = cost;
+      best_choice = choice;
+      best_k = k;
+    }
+  }
+  plan->feasible = best >= 0 ? 1 : 0;
+  if (best < 0) {
+    best_k = o->max_samples;
+    best = cp * (double)best_k * c->n;
+    for (int p = 0; p < np; ++p) {
+      best_choice[p] = o->max_overlap;
+      best += slabs(p, o->max_overlap) * (cd * npad * npad * npad + cc * best_k * npad * npad);
+    }
+  }
+  plan->n_samples = best_k;
+  plan->predicted_cost = best;
+  plan->predicted_err = 0.0;
+  for (int p = 0; p < np; ++p) {
+    plan->part_overlap[p] = best_choice[p];
+    const double e = err(p, best_choice[p], best_k);
+    if (plan->part_pred_err) plan->part_pred_err[p] = e;
+    plan->predicted_err = std::max(plan->predicted_err, e);
+  }
   return QSEL_OK;
 }
 

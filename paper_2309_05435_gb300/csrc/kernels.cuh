@@ -259,6 +259,7 @@ struct CorrEntry {
   const T *w;               // T_ x n_pad x ld samples of the subdomain correction
   int T_, lo, hi, e0;       // slabs, local own range [lo, hi], global slab of local 0
   double *corr_out;         // global correction output (own rows written)
+  double *corr4_out;        // (1/k) sum w^4 of the own rows, or nullptr
   double *partial;          // per-CTA trace partials (3 per CTA)
 };
 template <typename T>
@@ -282,5 +283,21 @@ template <typename T>
 void launch_add(cudaStream_t s, T *y, const T *x, int64_t n);
 // out = a + b (n doubles)
 void launch_sum(cudaStream_t s, double *out, const double *a, const double *b, int n);
+// per part: sum over own rows of ((m4 - m2^2) / (k - 1)) / v^2
+void launch_part_error_sums(cudaStream_t s, const double *m2, const double *m4, const double *v,
+                            const int32_t *slab_start_dev, int n_parts, int n_s, int k, double *out);
+
+// ---------------------------------------------------------------- mlp.cu
+void launch_cv_features(cudaStream_t s, const SellPattern &pat, const double *qs, const double *a0,
+                        const double *a1, const uint8_t *obs, double obs_w, int n_s, int n_t, const float *sep_dist,
+                        const float *bnd_dist, const double th[3], float *F);
+void launch_cv_part_m2(cudaStream_t s, const float *y, const int32_t *slab_start_dev, int n_parts, int n_s,
+                       double *out);
+constexpr int kCvMaxTargets = 8;
+struct CvTargetArgs {
+  const double *corr[kCvMaxTargets];
+  int count;
+};
+void launch_cv_targets(cudaStream_t s, const CvTargetArgs &a, const double *sel, int n, float *y);
 
 }  // namespace qsel

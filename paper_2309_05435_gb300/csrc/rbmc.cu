@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) k_correction_terms(CorrBatch<T> bt, SellP
     const int w = pat.slice_width[sl];
     const int base = pat.slice_ptr[sl] + li;
     const T *wrow = e.w + tl * slab + (int64_t)i * ld;
-    double sq = 0.0, p0 = 0.0, p1 = 0.0, p2 = 0.0;
+    double sq = 0.0, q4 = 0.0, p0 = 0.0, p1 = 0.0, p2 = 0.0;
     for (int c = lane; c < ld; c += 32) {
       double g0 = 0.0, g1 = 0.0, g2 = 0.0;
       for (int s = 0; s < w; ++s) {
@@ -64,18 +64,21 @@ __global__ void __launch_bounds__(256) k_correction_terms(CorrBatch<T> bt, SellP
       }
       const double wi = (double)wrow[c];
       sq = fma(wi, wi, sq);
+      q4 = fma(wi * wi, wi * wi, q4);
       p0 = fma(wi, g0, p0);
       p1 = fma(wi, g1, p1);
       p2 = fma(wi, g2, p2);
     }
     for (int o = 16; o > 0; o >>= 1) {
       sq += __shfl_down_sync(0xffffffffu, sq, o);
+      q4 += __shfl_down_sync(0xffffffffu, q4, o);
       p0 += __shfl_down_sync(0xffffffffu, p0, o);
       p1 += __shfl_down_sync(0xffffffffu, p1, o);
       p2 += __shfl_down_sync(0xffffffffu, p2, o);
     }
     if (lane == 0) {
       e.corr_out[(int64_t)t * n_s + i] = sq * inv_k;
+      if (e.corr4_out) e.corr4_out[(int64_t)t * n_s + i] = q4 * inv_k;
       tr0 += p0;
       tr1 += p1;
       tr2 += p2;
@@ -175,6 +178,36 @@ void launch_add(cudaStream_t s, T *y, const T *x, int64_t n) {
 }
 template void launch_add<double>(cudaStream_t, double *, const double *, int64_t);
 template void launch_add<float>(cudaStream_t, float *, const float *, int64_t);
+
+// Per part p: sum over the rows of Omega_p of Var_hat / v_i^2 with
+// Var_hat = (m4_i - m2_i^2) / (k - 1), the estimated variance of the mean of
+// the k values w_i^2.  One CTA per part.
+__global__ void k_part_error_sums(const double *__restrict__ m2, const double *__restrict__ m4,
+                                  const double *__restrict__ v, const int32_t *__restrict__ slab_start, int n_s,
+                                  int k, double *__restrict__ out) {
+  __shared__ double red[256];
+  const int p = blockIdx.x;
+  const int64_t r0 = (int64_t)slab_start[p] * n_s, r1 = (int64_t)slab_start[p + 1] * n_s;
+  const double inv = 1.0 / (double)(k - 1);
+  double a = 0.0;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const double var = fmax(m4[r] - m2[r] * m2[r], 0.0) * inv;
+    a += var / (v[r] * v[r]);
+  }
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[p] = red[0];
+}
+
+void launch_part_error_sums(cudaStream_t s, const double *m2, const double *m4, const double *v,
+                            const int32_t *slab_start_dev, int n_parts, int n_s, int k, double *out) {
+  ++g_launch_count;
+  k_part_error_sums<<<n_parts, 256, 0, s>>>(m2, m4, v, slab_start_dev, n_s, k, out);
+}
 
 __global__ void k_sum(double *__restrict__ out, const double *__restrict__ a, const double *__restrict__ b, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = a[i] + b[i];

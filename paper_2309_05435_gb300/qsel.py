@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_uint8, c_uint64, c_void_p
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int32, c_int64, c_uint8, c_uint64, c_void_p
 
 import numpy as np
 
@@ -38,7 +38,20 @@ class qsel_partition(ctypes.Structure):
 class qsel_options(ctypes.Structure):
     _fields_ = [("n_samples", c_int32), ("seed", c_uint64), ("precision", c_int32), ("pcg_tol", c_double),
                 ("pcg_max_iter", c_int32), ("precond_block", c_int32), ("control_variate", c_int32),
-                ("cuda_stream", c_void_p), ("profile_kernels", c_int32), ("tensor_passes", c_int32)]
+                ("cuda_stream", c_void_p), ("profile_kernels", c_int32), ("tensor_passes", c_int32),
+                ("part_overlap", POINTER(c_int32))]
+
+
+class qsel_cv_plan_options(ctypes.Structure):
+    _fields_ = [("target_rel_err", c_double), ("max_overlap", c_int32), ("min_samples", c_int32),
+                ("max_samples", c_int32), ("cost_pcg", c_double), ("cost_dense", c_double),
+                ("cost_corr", c_double)]
+
+
+class qsel_cv_plan_t(ctypes.Structure):
+    _fields_ = [("n_samples", c_int32), ("feasible", c_int32), ("predicted_cost", c_double),
+                ("predicted_err", c_double), ("part_overlap", POINTER(c_int32)),
+                ("part_pred_err", POINTER(c_double))]
 
 
 class qsel_stats_t(ctypes.Structure):
@@ -52,8 +65,14 @@ class qsel_stats_t(ctypes.Structure):
 
 EXPORTED = ["qsel_create", "qsel_set_theta", "qsel_diag_inv", "qsel_trace_grads", "qsel_stats",
             "qsel_debug_set_samples", "qsel_debug_get_samples", "qsel_debug_get_rhs",
-            "qsel_debug_get_selinv_diag", "qsel_spd_inverse_noalloc", "qsel_last_error", "qsel_destroy"]
+            "qsel_debug_get_selinv_diag", "qsel_spd_inverse_noalloc", "qsel_error_estimate",
+            "qsel_cv_create", "qsel_cv_set_params", "qsel_cv_get_params", "qsel_cv_predict", "qsel_cv_grad",
+            "qsel_cv_train", "qsel_cv_features", "qsel_cv_targets", "qsel_cv_plan",
+            "qsel_cv_destroy", "qsel_last_error", "qsel_destroy"]
 QSEL_NOALLOC_MAX_N = 1024
+QSEL_CV_FEATURES = 14
+QSEL_CV_PARAMS = 5185
+QSEL_CV_PARAMS_ALL = 5213
 
 _lib = None
 
@@ -78,12 +97,25 @@ def load_library(path: str = LIB_PATH):
     lib.qsel_debug_get_rhs.argtypes = [c_void_p, P(c_double), c_int32]
     lib.qsel_debug_get_selinv_diag.argtypes = [c_void_p, P(c_double)]
     lib.qsel_spd_inverse_noalloc.argtypes = [c_void_p, c_int32, c_int32, c_void_p]
+    lib.qsel_error_estimate.argtypes = [c_void_p, P(c_double), P(c_double)]
+    lib.qsel_cv_create.argtypes = [P(c_void_p), c_uint64, c_void_p]
+    lib.qsel_cv_set_params.argtypes = [c_void_p, P(c_float)]
+    lib.qsel_cv_get_params.argtypes = [c_void_p, P(c_float)]
+    lib.qsel_cv_predict.argtypes = [c_void_p, c_void_p, c_void_p, c_int32]
+    lib.qsel_cv_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, P(c_float), P(c_float)]
+    lib.qsel_cv_train.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_float, c_int32, P(c_float)]
+    lib.qsel_cv_features.argtypes = [c_void_p, c_int32, c_void_p]
+    lib.qsel_cv_targets.argtypes = [P(c_void_p), c_int32, c_void_p]
+    lib.qsel_cv_plan.argtypes = [c_void_p, c_void_p, P(qsel_cv_plan_options), P(qsel_cv_plan_t)]
+    lib.qsel_cv_destroy.argtypes = [c_void_p]
+    lib.qsel_cv_destroy.restype = None
     lib.qsel_last_error.argtypes = [c_void_p]
     lib.qsel_last_error.restype = c_char_p
     lib.qsel_destroy.argtypes = [c_void_p]
     lib.qsel_destroy.restype = None
-    for name in EXPORTED[:-2]:
-        getattr(lib, name).restype = c_int32
+    for name in EXPORTED:
+        if name not in ("qsel_cv_destroy", "qsel_last_error", "qsel_destroy"):
+            getattr(lib, name).restype = c_int32
     _lib = lib
     return lib
 
@@ -107,10 +139,11 @@ def _check(status: int, handle):
 class Context:
     """Owner of one qsel_ctx*."""
 
-    def __init__(self, handle, n: int, k: int):
+    def __init__(self, handle, n: int, k: int, n_parts: int = 1):
         self.handle = handle
         self.n = n
         self.k = k
+        self.n_parts = n_parts
 
     def __del__(self):
         self.close()
@@ -134,7 +167,7 @@ class Context:
 def qsel_create(n_s, n_t, c_diag, g_rowptr, g_col, g_val, obs_mask, sigma, theta, n_parts=1,
                 slab_start=None, overlap=0, n_samples=64, seed=0, precision=QSEL_FP64, pcg_tol=1e-10,
                 pcg_max_iter=20000, precond_block=0, control_variate=0, cuda_stream=None,
-                profile_kernels=0, tensor_passes=0) -> Context:
+                profile_kernels=0, tensor_passes=0, part_overlap=None) -> Context:
     """Create a context from host arrays (copied by the library)."""
     lib = load_library()
     c = np.ascontiguousarray(c_diag, dtype=np.float64)
@@ -149,15 +182,20 @@ def qsel_create(n_s, n_t, c_diag, g_rowptr, g_col, g_val, obs_mask, sigma, theta
     if slab_start is not None:
         ss = np.ascontiguousarray(slab_start, dtype=np.int32)
     part = qsel_partition(int(n_parts), _ptr(ss, c_int32) if ss is not None else None)
+    po = None
+    if part_overlap is not None:
+        po = np.ascontiguousarray(part_overlap, dtype=np.int32)
+        if po.size != int(n_parts):
+            raise ValueError("part_overlap needs one entry per part")
     opt = qsel_options(int(n_samples), int(seed), int(precision), float(pcg_tol), int(pcg_max_iter),
                        int(precond_block), int(control_variate),
                        c_void_p(int(cuda_stream)) if cuda_stream else None, int(profile_kernels),
-                       int(tensor_passes))
+                       int(tensor_passes), _ptr(po, c_int32) if po is not None else None)
     h = c_void_p()
     st = lib.qsel_create(ctypes.byref(h), ctypes.byref(model), ctypes.byref(th), ctypes.byref(part),
                          int(overlap), ctypes.byref(opt))
     _check(st, None)
-    return Context(h, int(n_s) * int(n_t), int(n_samples))
+    return Context(h, int(n_s) * int(n_t), int(n_samples), int(n_parts))
 
 
 def qsel_set_theta(ctx: Context, theta):
@@ -226,6 +264,96 @@ def qsel_spd_inverse_noalloc(a, n: int, lda: int | None = None, cuda_stream=None
     st = load_library().qsel_spd_inverse_noalloc(c_void_p(ptr), int(n), int(lda if lda is not None else n),
                                                   c_void_p(int(cuda_stream)) if cuda_stream else None)
     _check(st, None)
+
+
+def qsel_error_estimate(ctx: Context):
+    """(per-part RMS relative standard error, global one) of the last
+    diag(Q^-1) estimate, from the sample moments of w^2."""
+    part = np.zeros(ctx.n_parts, dtype=np.float64)
+    g = c_double(0.0)
+    _check(load_library().qsel_error_estimate(ctx.handle, _ptr(part, c_double), ctypes.byref(g)), ctx.handle)
+    return part, g.value
+
+
+def _dev(a):
+    """Device address of a CUDA tensor (or an integer pointer)."""
+    return c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else int(a))
+
+
+class ControlVariate:
+    """Owner of one qsel_cv* (the control-variate network)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().qsel_cv_destroy(self.handle)
+            self.handle = None
+
+
+def qsel_cv_create(seed: int = 0, cuda_stream=None) -> ControlVariate:
+    h = c_void_p()
+    _check(load_library().qsel_cv_create(ctypes.byref(h), int(seed),
+                                         c_void_p(int(cuda_stream)) if cuda_stream else None), None)
+    return ControlVariate(h)
+
+
+def qsel_cv_set_params(cv: ControlVariate, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != QSEL_CV_PARAMS_ALL:
+        raise ValueError(f"params must hold {QSEL_CV_PARAMS_ALL} values")
+    _check(load_library().qsel_cv_set_params(cv.handle, _ptr(p, c_float)), None)
+
+
+def qsel_cv_get_params(cv: ControlVariate) -> np.ndarray:
+    p = np.empty(QSEL_CV_PARAMS_ALL, dtype=np.float32)
+    _check(load_library().qsel_cv_get_params(cv.handle, _ptr(p, c_float)), None)
+    return p
+
+
+def qsel_cv_predict(cv: ControlVariate, X_dev, y_dev, n: int):
+    _check(load_library().qsel_cv_predict(cv.handle, _dev(X_dev), _dev(y_dev), int(n)), None)
+
+
+def qsel_cv_grad(cv: ControlVariate, X_dev, y_dev, n: int):
+    g = np.empty(QSEL_CV_PARAMS, dtype=np.float32)
+    loss = c_float(0.0)
+    _check(load_library().qsel_cv_grad(cv.handle, _dev(X_dev), _dev(y_dev), int(n), _ptr(g, c_float),
+                                       ctypes.byref(loss)), None)
+    return g, loss.value
+
+
+def qsel_cv_train(cv: ControlVariate, X_dev, y_dev, n: int, steps: int, lr: float, set_input_stats: bool = False):
+    loss = c_float(0.0)
+    _check(load_library().qsel_cv_train(cv.handle, _dev(X_dev), _dev(y_dev), int(n), int(steps), float(lr),
+                                        int(bool(set_input_stats)), ctypes.byref(loss)), None)
+    return loss.value
+
+
+def qsel_cv_features(ctx: Context, overlap: int, F_dev):
+    _check(load_library().qsel_cv_features(ctx.handle, int(overlap), _dev(F_dev)), ctx.handle)
+
+
+def qsel_cv_targets(ctxs, y_dev):
+    arr = (c_void_p * len(ctxs))(*[c.handle.value if isinstance(c.handle, c_void_p) else c.handle for c in ctxs])
+    _check(load_library().qsel_cv_targets(arr, len(ctxs), _dev(y_dev)), ctxs[0].handle)
+
+
+def qsel_cv_plan(ctx: Context, cv: ControlVariate, target_rel_err: float, max_overlap: int = 4,
+                 min_samples: int = 32, max_samples: int = 512, cost_pcg: float = 0.0, cost_dense: float = 0.0,
+                 cost_corr: float = 0.0) -> dict:
+    o = qsel_cv_plan_options(float(target_rel_err), int(max_overlap), int(min_samples), int(max_samples),
+                             float(cost_pcg), float(cost_dense), float(cost_corr))
+    po = np.zeros(ctx.n_parts, dtype=np.int32)
+    pe = np.zeros(ctx.n_parts, dtype=np.float64)
+    plan = qsel_cv_plan_t(0, 0, 0.0, 0.0, _ptr(po, c_int32), _ptr(pe, c_double))
+    _check(load_library().qsel_cv_plan(ctx.handle, cv.handle, ctypes.byref(o), ctypes.byref(plan)), ctx.handle)
+    return {"n_samples": plan.n_samples, "feasible": bool(plan.feasible), "predicted_cost": plan.predicted_cost,
+            "predicted_err": plan.predicted_err, "part_overlap": po, "part_pred_err": pe}
 
 
 def qsel_last_error(ctx: Context | None) -> str:
