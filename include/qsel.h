@@ -320,7 +320,8 @@ qsel_status qsel_cv_features(qsel_ctx *ctx, int32_t overlap, float *F_dev);
 /* Training targets y_i = log(cbar_i / (Sigma*_ii + cbar_i)), cbar_i the mean
  * correction over `count` contexts that ran the same model and theta with
  * different seeds (their average is the RBMC estimate with all their samples);
- * ratios below 1e-30 are clamped.  Each context must have run
+ * ratios below 1e-9 are clamped (they add less than 1e-18 to any planned
+ * squared error).  Each context must have run
  * (qsel_diag_inv).  y_dev: DEVICE, n floats. */
 qsel_status qsel_cv_targets(qsel_ctx *const *ctxs, int32_t count, float *y_dev);
 

@@ -205,16 +205,19 @@ class Part:
     sep: list             # separator slabs S_p (the next slab outside ext, if any)
 
 
-def partition(n_t: int, slab_start, n_l: int) -> list:
+def partition(n_t: int, slab_start, n_l) -> list:
     """Omega_p are contiguous slab ranges [slab_start[p], slab_start[p+1]).  Because
     Q is block tridiagonal in time and every spatial node couples to itself in
     the neighbouring slab, the graph neighbours of a slab range are the two
     adjacent slabs; extending n_l times adds n_l slabs on each side (clipped to
-    the time axis) and the separator is the slab just beyond (Algorithm 3)."""
+    the time axis) and the separator is the slab just beyond (Algorithm 3).
+    n_l is one overlap for every part or a sequence with one per part
+    (Algorithm 3 extends each subdomain on its own)."""
     parts = []
     for p in range(len(slab_start) - 1):
+        nl = int(n_l[p]) if np.ndim(n_l) else int(n_l)
         s0, s1 = int(slab_start[p]), int(slab_start[p + 1])
-        e0, e1 = max(0, s0 - n_l), min(n_t, s1 + n_l)
+        e0, e1 = max(0, s0 - nl), min(n_t, s1 + nl)
         sep = []
         if e0 - 1 >= 0:
             sep.append(e0 - 1)

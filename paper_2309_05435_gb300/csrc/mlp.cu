@@ -353,7 +353,8 @@ void launch_cv_part_m2(cudaStream_t s, const float *y, const int32_t *slab_start
 }
 
 // y_i = log(cbar_i / (sel_i + cbar_i)), cbar_i the mean of the corrections,
-// ratio clamped below at 1e-30.
+// ratio clamped below at 1e-9 (a node below it adds less than 1e-18 to any
+// planned squared error).
 __global__ void k_cv_targets(CvTargetArgs a, const double *__restrict__ sel, int n, float *__restrict__ y) {
   const double inv = 1.0 / a.count;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -362,7 +363,7 @@ __global__ void k_cv_targets(CvTargetArgs a, const double *__restrict__ sel, int
     c *= inv;
     const double v = sel[i] + c;
     double r = c / v;
-    if (!(r > 1e-30)) r = 1e-30;
+    if (!(r > 1e-9)) r = 1e-9;
     y[i] = (float)log(r);
   }
 }

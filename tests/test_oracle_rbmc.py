@@ -169,3 +169,21 @@ def test_rbmc_unbiased_over_seeds():
     assert np.abs(z).max() < 4.5
     zt = (ts.mean(0) - np.array(t_ex)) / (ts.std(0, ddof=1) / math.sqrt(R))
     assert np.abs(zt).max() < 4.5
+
+
+def test_per_part_overlap_equals_uniform_runs():
+    """With one overlap per part, part p of the estimate equals part p of the
+    uniform-overlap estimate with that overlap (parts are independent given
+    the samples, Algorithm 4)."""
+    model = grid_model(5, 9, obs_frac=0.3)
+    th = theta(0.5, 1.0, 0.9)
+    ss = o.balanced_slab_start(9, 3)
+    X = o.samples(model, th, 3, 6)
+    v, t, res = o.rbmc(model, th, ss, [1, 2, 1], X)
+    n_s = 25
+    for p, nl in enumerate([1, 2, 1]):
+        vu, _, ru = o.rbmc(model, th, ss, nl, X)
+        rows = slice(ss[p] * n_s, ss[p + 1] * n_s)
+        np.testing.assert_array_equal(v[rows], vu[rows])
+        np.testing.assert_array_equal(res[p].traces, ru[p].traces)
+    assert res[1].part.ext == (1, 8) and res[0].part.ext == (0, 4)
