@@ -1,14 +1,22 @@
 #!/usr/bin/env python
-"""Benchmark: time to diag(Q^-1) + tr(Q^-1 dQ/dtheta_j) on one GB300.
+"""Benchmark: time to diag(Q^-1) + tr(Q^-1 dQ/dtheta_j) at 1 % relative error
+on one GB300.
 
-One step = one pass of the whole hot path through the C ABI on a resident
-context: qsel_set_theta (invalidates), qsel_diag_inv (perturbation RHS,
-multi-RHS PCG, per-subdomain block factorisation + Takahashi, RB correction)
-and qsel_trace_grads.  Workload: 64 x 64 grid (n_s = 4096), n_t = 64
+The chosen form is mixed precision with the learned control variate: a
+network trained first on the GPU (reported separately, not timed) predicts
+every node's correction share, the planner picks one sample count and an
+overlap per part for a 1 % RMS relative standard error, and RBMC runs at
+those settings.  One step = one pass through the C ABI on a resident
+context: qsel_cv_plan (features + network + plan), qsel_set_theta,
+qsel_diag_inv (perturbation RHS, multi-RHS PCG, per-subdomain block
+factorisation + Takahashi, RB correction), qsel_trace_grads and
+qsel_error_estimate.  Workload: 64 x 64 grid (n_s = 4096), n_t = 64
 (n = 262,144), kappa = 0.2, rho = 0.95, 25 % observed, 8 time subdomains,
-overlap 2, 256 samples, PCG to 1e-10 -- synthetic, seeded.
+PCG to 1e-10 -- synthetic, seeded.  Plain FP64 RBMC at the workload's fixed
+settings (overlap 2, 256 samples) is timed beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+  python bench.py --cv-eval      # held-out evaluation of the control variate
 
 N > 1 runs under torch.distributed.run: every rank solves its own independent
 replica (weak scaling, no data-path collective); the barrier and the max over
@@ -60,7 +68,51 @@ def parse_args():
                     help="time-to-accuracy sweep instead of the bench line: comma list of "
                          "form:n_parts:overlap:n_samples entries, form in {mixed, fp64}")
     ap.add_argument("--seeds", type=int, default=1, help="RBMC seeds per sweep entry")
+    ap.add_argument("--form", choices=["planned", "fixed"], default="planned",
+                    help="planned = control-variate planner picks k and overlaps; fixed = workload settings")
+    ap.add_argument("--target", type=float, default=0.01, help="RMS relative error target of the plan")
+    ap.add_argument("--max-overlap", type=int, default=8)
+    ap.add_argument("--margin", type=float, default=0.85,
+                    help="the planner aims at margin * target (absorbs the prediction error)")
+    ap.add_argument("--cv-train-thetas", type=int, default=32)
+    ap.add_argument("--cv-train-steps", type=int, default=2000)
+    ap.add_argument("--cv-eval", action="store_true",
+                    help="held-out evaluation: 64x64 grid, n_t=128, 8 parts, 8 theta; planned vs plain")
+    ap.add_argument("--cv-eval-thetas", type=int, default=8)
+    ap.add_argument("--cv-fp64-thetas", type=int, default=2,
+                    help="held-out theta on which plain FP64 is also run to the target")
     return ap.parse_args()
+
+
+CV_TRAIN_OVERLAPS = (1, 2, 3, 4, 5, 6, 7, 8)
+
+
+def train_control_variate(args):
+    """Training set from the method itself on 16 x 16 grid models (n_t = 32,
+    4 parts, overlaps 1-8, scrambled-Sobol theta, 2 x 512 samples per target),
+    then full-batch Adam -- all on the GPU through the C ABI."""
+    import torch
+    from paper_2309_05435_gb300 import cv as cvm
+    mesh = qi.grid_mesh(16)
+    spec = cvm.ModelSpec(mesh, 32, qi.obs_mask(256 * 32, 0.25, 5), 0.5, qi.balanced_slab_start(32, 4))
+    thetas = cvm.sobol_thetas(args.cv_train_thetas, seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X, y = cvm.training_set(spec, thetas, CV_TRAIN_OVERLAPS, k=512, seeds=(1, 2))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    s1 = args.cv_train_steps * 3 // 5
+    net = cvm.train(X, y, steps=(s1, args.cv_train_steps - s1), lrs=(3e-3, 5e-4))
+    from paper_2309_05435_gb300 import qsel
+    _, loss = qsel.qsel_cv_grad(net, X, y, X.shape[0])
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    info = {"models": "16x16 grid, n_t=32, 4 parts, overlaps 1-8, 25% observed",
+            "thetas": len(thetas), "samples_per_target": 1024, "training_rows": int(X.shape[0]),
+            "adam_steps": args.cv_train_steps, "final_mse": loss, "target_variance": float(y.var()),
+            "data_s": t1 - t0, "train_s": t2 - t1}
+    return net, info
+
 
 
 def rank_seed(rank: int) -> int:
@@ -205,19 +257,43 @@ def run_native(args):
     dev = f"cuda:{local}"
     chosen_prec = qsel.QSEL_MIXED if args.precision == "mixed" else qsel.QSEL_FP64
 
-    def make_ctx(precision, profile=1):
-        return qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma,
-                                w.theta, n_parts=w.n_parts, overlap=w.overlap, n_samples=w.n_samples, seed=seed,
-                                precision=precision, pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream,
-                                profile_kernels=profile)
+    planned = args.form == "planned" and chosen_prec == qsel.QSEL_MIXED
+    net, cv_info = (train_control_variate(args) if planned else (None, None))
 
-    def timed(ctx, out, warmup, steps, clocks=False):
+    def make_ctx(precision, profile=1, k=None, part_overlap=None):
+        return qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma,
+                                w.theta, n_parts=w.n_parts, overlap=w.overlap,
+                                n_samples=k if k else w.n_samples, seed=seed, precision=precision,
+                                pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream, profile_kernels=profile,
+                                part_overlap=part_overlap)
+
+    def make_plan(ctx):
+        return qsel.qsel_cv_plan(ctx, net, args.margin * args.target, max_overlap=args.max_overlap)
+
+    plan = None
+    k_run, po = w.n_samples, None
+    if planned:
+        probe = make_ctx(chosen_prec, profile=0, k=32)
+        plan = make_plan(probe)
+        probe.close()
+        k_run, po = plan["n_samples"], [int(x) for x in plan["part_overlap"]]
+    # kernels the planner launches per call: time coefficients, Q_s values,
+    # features, network, per-part reduction for every candidate overlap
+    plan_launches = 5 * args.max_overlap if planned else 0
+
+    def timed(ctx, out, warmup, steps, clocks=False, with_plan=False):
         grads = np.zeros(3)
+        errs = []
 
         def step():
+            if with_plan:
+                p = make_plan(ctx)
+                if p["n_samples"] != k_run or [int(x) for x in p["part_overlap"]] != po:
+                    raise RuntimeError("the plan changed between steps at fixed theta")
             qsel.qsel_set_theta(ctx, w.theta)
             qsel.qsel_diag_inv(ctx, out)
             grads[:] = qsel.qsel_trace_grads(ctx)
+            errs.append(qsel.qsel_error_estimate(ctx)[1])
             return qsel.qsel_stats(ctx)
 
         for _ in range(warmup):
@@ -236,28 +312,61 @@ def run_native(args):
             dist.barrier()
         clk = sampler.stop() if sampler else None
         ms = job_time_ms(e0.elapsed_time(e1), world, dist if world > 1 else None, dev)
-        return ms, stats, clk, grads.copy()
+        return ms, stats, clk, grads.copy(), errs[-1]
 
-    ctx = make_ctx(chosen_prec)
+    ctx = make_ctx(chosen_prec, k=k_run, part_overlap=po)
     out = torch.empty(w.n, dtype=torch.float64, device=dev)
-    ms_total, stats, clk, grads = timed(ctx, out, args.warmup, args.steps, clocks=True)
+    ms_total, stats, clk, grads, err_est = timed(ctx, out, args.warmup, args.steps, clocks=True, with_plan=planned)
     ms_per_step = ms_total / args.steps
     v_chosen = out.cpu().numpy()
 
     plain = None
     v_fp64 = None
-    if args.fp64_steps > 0 and chosen_prec != qsel.QSEL_FP64:
+    grads64 = None
+    if args.fp64_steps > 0 and (chosen_prec != qsel.QSEL_FP64 or planned):
         ctx64 = make_ctx(qsel.QSEL_FP64, profile=0)
         out64 = torch.empty(w.n, dtype=torch.float64, device=dev)
-        ms64, st64, _, grads64 = timed(ctx64, out64, 1, args.fp64_steps)
+        ms64, st64, _, grads64, err64 = timed(ctx64, out64, 1, args.fp64_steps)
         v_fp64 = out64.cpu().numpy()
-        plain = {"ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps, "warmup": 1,
-                 "pcg_iterations": st64[-1]["pcg_iterations"],
-                 "speedup_chosen_vs_plain": (ms64 / args.fp64_steps) / ms_per_step,
-                 "chosen_vs_fp64_same_seed": {
-                     "diag_max_rel": float(np.max(np.abs(v_chosen - v_fp64) / np.abs(v_fp64))),
-                     "traces_rel": [float(abs(a - b) / abs(b)) for a, b in zip(grads, grads64)]}}
+        ph = st64[-1]
+        t_fixed = (ph["ms_factor"] + ph["ms_takahashi"]) / 1e3
+        t_per_k = (ph["ms_rhs"] + ph["ms_pcg"] + ph["ms_correction"]) / 1e3 / w.n_samples
+        k_need = w.n_samples * (err64 / args.target) ** 2
+        batches = max(1, math.ceil(k_need / 512))
+        k_batch = min(512, 32 * math.ceil(k_need / 32))
+        t_target = batches * (t_fixed + t_per_k * k_batch)
+        plain = {"settings": f"overlap {w.overlap}, {w.n_samples} samples", "ms_per_step": ms64 / args.fp64_steps,
+                 "steps": args.fp64_steps, "warmup": 1, "pcg_iterations": ph["pcg_iterations"],
+                 "error_estimate": err64,
+                 "time_to_target_model_s": t_target,
+                 "time_to_target_model": (f"k needed = {w.n_samples} (err/target)^2 = {k_need:.0f}; "
+                                          f"{batches} pipeline run(s) of {k_batch} samples, each timed as the "
+                                          "measured k-independent phases (factor, Takahashi) plus the "
+                                          "measured per-sample phases (RHS, PCG, correction) scaled to k; "
+                                          "assumes k known in advance"),
+                 "speedup_chosen_vs_plain_time_to_target": t_target / (ms_per_step / 1e3),
+                 "chosen_vs_fp64_same_seed": None}
+        if not planned:
+            plain["chosen_vs_fp64_same_seed"] = {
+                "diag_max_rel": float(np.max(np.abs(v_chosen - v_fp64) / np.abs(v_fp64))),
+                "traces_rel": [float(abs(a - b) / abs(b)) for a, b in zip(grads, grads64)]}
         ctx64.close()
+
+    # the exact one-part alternative (no separator, no samples) in the same
+    # precision, timed for comparison
+    alt = None
+    v_alt = g_alt = None
+    if planned and args.fp64_steps > 0:
+        ctx1 = qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma,
+                                w.theta, n_parts=1, overlap=0, n_samples=2, precision=chosen_prec,
+                                cuda_stream=stream.cuda_stream)
+        out1 = torch.empty(w.n, dtype=torch.float64, device=dev)
+        ms1, st1, _, g_alt, _ = timed(ctx1, out1, 1, 1)
+        v_alt = out1.cpu().numpy()
+        alt = {"form": "exact single part (n_p = 1), same precision", "s_per_pass": ms1 / 1e3,
+               "planner_model_cost_s": plan["single_part_cost"] if plan else None,
+               "phases_ms": {"factor": st1[-1]["ms_factor"], "takahashi": st1[-1]["ms_takahashi"]}}
+        ctx1.close()
 
     # end to end through the public API with host buffers
     e2e_s = None
@@ -277,8 +386,13 @@ def run_native(args):
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             c2 = qsel.qsel_create(w.n_s, w.n_t, c_pin, rp_pin, gc_pin, gv_pin, mk_pin, w.sigma, w.theta,
-                                  n_parts=w.n_parts, overlap=w.overlap, n_samples=w.n_samples, seed=seed,
-                                  precision=chosen_prec, pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream)
+                                  n_parts=w.n_parts, overlap=w.overlap, n_samples=k_run, seed=seed,
+                                  precision=chosen_prec, pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream,
+                                  part_overlap=po)
+            if planned:
+                p = make_plan(c2)
+                if p["n_samples"] != k_run or [int(x) for x in p["part_overlap"]] != po:
+                    raise RuntimeError("the plan changed between calls at fixed theta")
             qsel.qsel_diag_inv(c2, diag_host)
             qsel.qsel_trace_grads(c2)
             c2.close()
@@ -338,7 +452,11 @@ def run_native(args):
                     "eps_diag_max": float(np.max(np.abs(r))),
                     "eps_traces": [float(abs(a - b) / abs(b)) for a, b in zip(g, t_ex)]}
         accuracy = {"reference": "exact single-subdomain FP64 selected inversion on the GPU (n_p = 1)",
-                    "chosen": errs(v_chosen, grads), "seeds": 1}
+                    "chosen": errs(v_chosen, grads), "chosen_error_estimate": err_est, "seeds": 1}
+        if v_fp64 is not None:
+            accuracy["plain_fp64"] = errs(v_fp64, grads64)
+        if alt is not None:
+            alt["accuracy"] = errs(v_alt, g_alt)
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -348,6 +466,8 @@ def run_native(args):
 
     form = "mixed precision RBMC (FP32 PCG + FP64 refinement, FP32 tiles + FP64 pivots)" \
         if chosen_prec == qsel.QSEL_MIXED else "plain FP64 RBMC"
+    if planned:
+        form += f" + learned control variate planner (target {args.target:g} RMS relative error)"
     result = {
         "metric": METRIC,
         "value": job_value_s(ms_total, args.steps, world),
@@ -363,15 +483,22 @@ def run_native(args):
         "data": "synthetic (seeded grid FEM mesh, Philox noise)",
         "config": {"workload": f"{w.name}: {w.m}x{w.m} grid, n_t={w.n_t}, n={w.n}, kappa={w.kappa}, "
                                f"rho={w.rho}, {int(w.obs_frac * 100)}% observed",
-                   "form": form, "n_parts": w.n_parts, "overlap": w.overlap,
-                   "n_samples": w.n_samples, "pcg_tol": w.pcg_tol,
-                   "l2": "inputs larger than L2 (samples alone %.2f GB)" % (w.n * w.n_samples * 8 / 1e9),
+                   "form": form, "n_parts": w.n_parts, "overlap": po if po else w.overlap,
+                   "n_samples": k_run, "pcg_tol": w.pcg_tol,
+                   "l2": "inputs larger than L2 (samples alone %.2f GB)" % (w.n * k_run * 8 / 1e9),
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "phases_ms": {"rhs": st["ms_rhs"], "pcg": st["ms_pcg"], "factor": st["ms_factor"],
                       "takahashi": st["ms_takahashi"], "correction": st["ms_correction"]},
         "pcg_iterations": st["pcg_iterations"],
-        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)) + plan_launches * args.steps,
+        "plan": None if plan is None else {"n_samples": plan["n_samples"], "part_overlap": po,
+                                           "predicted_err": plan["predicted_err"],
+                                           "predicted_cost_s": plan["predicted_cost"],
+                                           "feasible": plan["feasible"], "error_estimate": err_est,
+                                           "margin": args.margin},
+        "cv_training": cv_info,
+        "alternative": alt,
         "plain_fp64": plain,
         "clocks": clk,
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -468,8 +595,72 @@ def run_sweep(args):
     return rows
 
 
+def run_cv_eval(args):
+    """Held-out evaluation of the learned control variate: 64 x 64 grid,
+    n_t = 128, 8 parts, 25 % observed, scrambled-Sobol theta (seed 2, apart
+    from the training grid).  Per theta: planned mixed RBMC (plan, one run, at
+    most one corrective run) against plain RBMC at overlap 2 that doubles k
+    from 32 (then averages 512-sample batches) until its error estimate meets
+    the target -- in mixed precision on every theta and in FP64 on the first
+    --cv-fp64-thetas.  Errors are also measured against the exact
+    single-subdomain result.  Wall-clock seconds include context creation."""
+    import torch
+    from paper_2309_05435_gb300 import build, qsel
+    from paper_2309_05435_gb300 import cv as cvm
+    build.build()
+    net, info = train_control_variate(args)
+    print(json.dumps({"cv_training": info}), flush=True)
+    mesh = qi.grid_mesh(64)
+    n_t = 128
+    spec = cvm.ModelSpec(mesh, n_t, qi.obs_mask(4096 * n_t, 0.25, 6), 0.5, qi.balanced_slab_start(n_t, 8))
+    rows = []
+    for i, th in enumerate(cvm.sobol_thetas(args.cv_eval_thetas, seed=2)):
+        # exact single-subdomain reference (mixed: its error, ~1e-4, is far below the target)
+        ref = qsel.qsel_create(spec.n_s, n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, spec.mask,
+                               spec.sigma, th, n_parts=1, overlap=0, n_samples=1, precision=qsel.QSEL_MIXED)
+        v_ex = qsel.qsel_diag_inv(ref)
+        ref.close()
+
+        def eps(v):
+            return float(np.sqrt(np.mean(((v - v_ex) / v_ex) ** 2)))
+
+        row = {"theta": [round(x, 4) for x in th], "target": args.target}
+        pl = cvm.solve_planned(spec, th, net, args.target, max_overlap=args.max_overlap, margin=args.margin)
+        row["planned_mixed"] = {"k": pl["k"], "part_overlap": pl["part_overlap"], "runs": len(pl["runs"]),
+                                "samples": pl["samples_drawn"], "err_estimate": pl["err"],
+                                "predicted_err": pl["plan"]["predicted_err"], "eps_vs_exact": eps(pl["v"]),
+                                "plan_s": pl["plan_s"], "wall_s": pl["wall_s"], "met": pl["met"]}
+        forms = [("plain_mixed", qsel.QSEL_MIXED)]
+        if i < args.cv_fp64_thetas:
+            forms.append(("plain_fp64", qsel.QSEL_FP64))
+        for name, prec in forms:
+            r = cvm.solve_plain(spec, th, args.target, overlap=2, precision=prec)
+            row[name] = {"k_total": r["k"], "runs": len(r["runs"]), "samples": r["samples_drawn"],
+                         "err_estimate": r["err"], "eps_vs_exact": eps(r["v"]), "wall_s": r["wall_s"],
+                         "met": r["met"]}
+        row["speedup_vs_plain_mixed"] = row["plain_mixed"]["wall_s"] / pl["wall_s"]
+        if "plain_fp64" in row:
+            row["speedup_vs_plain_fp64"] = row["plain_fp64"]["wall_s"] / pl["wall_s"]
+        print(json.dumps(row), flush=True)
+        rows.append(row)
+    summ = {"summary": "cv_eval", "thetas": len(rows),
+            "planned_met": sum(r["planned_mixed"]["met"] for r in rows),
+            "median_planned_wall_s": float(np.median([r["planned_mixed"]["wall_s"] for r in rows])),
+            "median_plain_mixed_wall_s": float(np.median([r["plain_mixed"]["wall_s"] for r in rows])),
+            "median_speedup_vs_plain_mixed": float(np.median([r["speedup_vs_plain_mixed"] for r in rows])),
+            "planned_samples_total": int(sum(r["planned_mixed"]["samples"] for r in rows)),
+            "plain_mixed_samples_total": int(sum(r["plain_mixed"]["samples"] for r in rows))}
+    fp = [r for r in rows if "plain_fp64" in r]
+    if fp:
+        summ["speedup_vs_plain_fp64"] = [r["speedup_vs_plain_fp64"] for r in fp]
+    print(json.dumps(summ), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.cv_eval:
+        run_cv_eval(args)
+        return
     if args.sweep:
         run_sweep(args)
         return

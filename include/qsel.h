@@ -333,7 +333,8 @@ qsel_status qsel_cv_targets(qsel_ctx *const *ctxs, int32_t count, float *y_dev);
  * samples are shared by every part) and per part the smallest overlap with
  * e_p(k) <= target, minimising the modelled time
  *   cost_pcg * k * n + sum_p T_p (cost_dense * n_pad^3 + cost_corr * k * n_pad^2),
- * T_p = slabs of the extended part, n_pad = n_s rounded up to 64.
+ * T_p = slabs of the extended part, n_pad = n_s rounded up to 64.  The
+ * plan also reports the modelled cost of the exact one-part alternative.
  * Cost coefficients of 0 take GB300 mixed-precision defaults (seconds:
  * 1.73e-8, 1.37e-13, 2.3e-13).  When no k meets the target everywhere the
  * plan takes max_samples and max_overlap and sets feasible = 0.
@@ -350,6 +351,9 @@ typedef struct {
   int32_t feasible;           /* 1 if every part meets the target              */
   double predicted_cost;      /* modelled seconds                              */
   double predicted_err;       /* max over parts of the predicted error         */
+  double single_part_cost;    /* modelled seconds of the exact alternative: one
+                                 part (no separator, no samples), cost_dense *
+                                 n_t * n_pad^3                                   */
   int32_t *part_overlap;      /* caller-allocated HOST, n_parts: chosen n_l,p   */
   double *part_pred_err;      /* caller-allocated HOST, n_parts, or NULL        */
 } qsel_cv_plan_t;

@@ -1415,6 +1415,7 @@ qsel_status qsel_cv_plan(qsel_ctx *ctx, const qsel_cv *cv, const qsel_cv_plan_op
   }
   plan->n_samples = best_k;
   plan->predicted_cost = best;
+  plan->single_part_cost = cd * (double)c->n_t * npad * npad * npad;
   plan->predicted_err = 0.0;
   for (int p = 0; p < np; ++p) {
     plan->part_overlap[p] = best_choice[p];

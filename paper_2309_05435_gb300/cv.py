@@ -101,33 +101,46 @@ def _timed_run(spec, theta, overlap, k, seed, precision, part_overlap=None):
 
 
 def solve_plain(spec: ModelSpec, theta, target: float, overlap: int, k0: int = 32, k_max: int = 512,
-                seed: int = 11, precision=q.QSEL_FP64):
+                seed: int = 11, precision=q.QSEL_FP64, max_batches: int = 8):
     """Plain RBMC without a predictor: fixed overlap, k doubled from k0 until
-    the sample-based error estimate meets the target (or k_max is reached)."""
+    the sample-based error estimate meets the target.  Past k_max, further
+    independent k_max-sample batches (new seeds) are averaged with the last
+    one: the mean of B estimates is the RBMC estimate with B * k_max samples,
+    its error estimate sqrt(sum_b err_b^2) / B (per-batch errors combined as
+    independent)."""
     runs, k, wall, ms, samples = [], k0, 0.0, 0.0, 0
+    batch = []
     while True:
-        v, t, err, w, m = _timed_run(spec, theta, overlap, k, seed, precision)
+        v, t, err, w, m = _timed_run(spec, theta, overlap, k, seed + len(runs), precision)
         runs.append({"k": k, "err": err, "wall_s": w})
         wall += w
         ms += m
         samples += k
-        if err <= target or k >= k_max:
+        if k < k_max:
+            if err <= target:
+                break
+            k = min(2 * k, k_max)
+            continue
+        batch.append((v, t, err))
+        err = math.sqrt(sum(b[2] ** 2 for b in batch)) / len(batch)
+        if err <= target or len(batch) >= max_batches:
+            v = np.mean([b[0] for b in batch], axis=0)
+            t = np.mean([b[1] for b in batch], axis=0)
             break
-        k = min(2 * k, k_max)
-    return {"v": v, "t": t, "err": err, "k": k, "overlap": overlap, "runs": runs, "wall_s": wall,
-            "device_ms": ms, "samples_drawn": samples, "met": err <= target}
+    return {"v": v, "t": t, "err": err, "k": k * max(1, len(batch)), "overlap": overlap, "runs": runs,
+            "wall_s": wall, "device_ms": ms, "samples_drawn": samples, "met": err <= target}
 
 
-def solve_planned(spec: ModelSpec, theta, cv: q.ControlVariate, target: float, max_overlap: int = 4,
-                  k_max: int = 512, seed: int = 11, precision=q.QSEL_MIXED, slack: float = 1.25):
-    """Planned RBMC: predict, plan (one k, overlap per part), run once, judge
-    by the error estimate; a miss beyond `slack` reruns with k scaled by the
-    squared miss (at most k_max)."""
+def solve_planned(spec: ModelSpec, theta, cv: q.ControlVariate, target: float, max_overlap: int = 8,
+                  k_max: int = 512, seed: int = 11, precision=q.QSEL_MIXED, margin: float = 0.85):
+    """Planned RBMC: predict, plan for margin * target (one k, an overlap per
+    part), run once, judge by the error estimate; a miss of the target reruns
+    once with k scaled by (err / (margin * target))^2 (at most k_max)."""
     import torch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     probe = spec.context(theta, 1, 32, seed, precision)
-    plan = q.qsel_cv_plan(probe, cv, target, max_overlap=max_overlap, max_samples=k_max)
+    plan = q.qsel_cv_plan(probe, cv, margin * target, max_overlap=max_overlap, max_samples=k_max)
     probe.close()
     t_plan = time.perf_counter() - t0
     k, po = plan["n_samples"], plan["part_overlap"].copy()
@@ -138,13 +151,13 @@ def solve_planned(spec: ModelSpec, theta, cv: q.ControlVariate, target: float, m
         wall += w
         ms += m
         samples += k
-        if err <= slack * target or k >= k_max or len(runs) >= 2:
+        if err <= target or k >= k_max or len(runs) >= 2:
             break
-        k = min(k_max, int(math.ceil(k * (err / target) ** 2 / 32.0)) * 32)
+        k = min(k_max, int(math.ceil(k * (err / (margin * target)) ** 2 / 32.0)) * 32)
         seed += 1
     return {"v": v, "t": t, "err": err, "k": k, "part_overlap": po.tolist(), "plan": plan, "runs": runs,
             "plan_s": t_plan, "wall_s": wall, "device_ms": ms, "samples_drawn": samples,
-            "met": err <= slack * target}
+            "met": err <= target}
 
 
 def sobol_thetas(n: int, seed: int):

@@ -50,7 +50,7 @@ class qsel_cv_plan_options(ctypes.Structure):
 
 class qsel_cv_plan_t(ctypes.Structure):
     _fields_ = [("n_samples", c_int32), ("feasible", c_int32), ("predicted_cost", c_double),
-                ("predicted_err", c_double), ("part_overlap", POINTER(c_int32)),
+                ("predicted_err", c_double), ("single_part_cost", c_double), ("part_overlap", POINTER(c_int32)),
                 ("part_pred_err", POINTER(c_double))]
 
 
@@ -350,10 +350,11 @@ def qsel_cv_plan(ctx: Context, cv: ControlVariate, target_rel_err: float, max_ov
                              float(cost_pcg), float(cost_dense), float(cost_corr))
     po = np.zeros(ctx.n_parts, dtype=np.int32)
     pe = np.zeros(ctx.n_parts, dtype=np.float64)
-    plan = qsel_cv_plan_t(0, 0, 0.0, 0.0, _ptr(po, c_int32), _ptr(pe, c_double))
+    plan = qsel_cv_plan_t(0, 0, 0.0, 0.0, 0.0, _ptr(po, c_int32), _ptr(pe, c_double))
     _check(load_library().qsel_cv_plan(ctx.handle, cv.handle, ctypes.byref(o), ctypes.byref(plan)), ctx.handle)
     return {"n_samples": plan.n_samples, "feasible": bool(plan.feasible), "predicted_cost": plan.predicted_cost,
-            "predicted_err": plan.predicted_err, "part_overlap": po, "part_pred_err": pe}
+            "predicted_err": plan.predicted_err, "single_part_cost": plan.single_part_cost,
+            "part_overlap": po, "part_pred_err": pe}
 
 
 def qsel_last_error(ctx: Context | None) -> str:
