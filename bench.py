@@ -81,6 +81,11 @@ def parse_args():
     ap.add_argument("--cv-eval-thetas", type=int, default=8)
     ap.add_argument("--cv-fp64-thetas", type=int, default=2,
                     help="held-out theta on which plain FP64 is also run to the target")
+    ap.add_argument("--batch", action="store_true",
+                    help="uneven batch: 64 independent models under one captured graph vs one at a time")
+    ap.add_argument("--batch-models", type=int, default=64)
+    ap.add_argument("--batch-streams", type=int, default=16)
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -656,8 +661,76 @@ def run_cv_eval(args):
     print(json.dumps(summ), flush=True)
 
 
+def run_batch(args):
+    """Uneven batch (grids 16x16 to 64x64, n_t 8 to 128, 2-8 parts, overlap 1,
+    128 samples, mixed precision, PCG to 1e-8, theta per model): one captured
+    graph over a stream pool, replayed; against the same models solved one
+    after another by separate contexts with the same (tuned) settings.  Both
+    sides time device work with CUDA events; the graph's W warm-up replays are
+    untimed and its K replays are timed."""
+    import torch
+    from paper_2309_05435_gb300 import build, qsel
+    build.build()
+    specs = qi.uneven_batch(args.batch_models)
+    meshes = {}
+    models = []
+    for b in specs:
+        if b.m not in meshes:
+            meshes[b.m] = qi.grid_mesh(b.m)
+        me = meshes[b.m]
+        models.append({"n_s": b.n_s, "n_t": b.n_t, "c_diag": me.c_diag, "g_rowptr": me.g_rowptr, "g_col": me.g_col,
+                       "g_val": me.g_val, "obs_mask": b.mask(), "sigma": b.sigma})
+    opts = dict(n_samples=128, seed=1000, precision=qsel.QSEL_MIXED, pcg_tol=1e-8, pcg_max_iter=20000)
+    t0 = time.perf_counter()
+    bt = qsel.qsel_create_batch(models, [b.theta for b in specs], [(b.n_parts, None) for b in specs],
+                                [b.overlap for b in specs], n_streams=args.batch_streams,
+                                autotune=not args.no_autotune, **opts)
+    t_create = time.perf_counter() - t0
+    for _ in range(max(1, args.warmup)):
+        qsel.qsel_batch_run(bt)
+    info0 = qsel.qsel_batch_info(bt)
+    reps = []
+    for _ in range(args.steps):
+        qsel.qsel_batch_run(bt)
+        reps.append(qsel.qsel_batch_info(bt)["ms_replay"])
+    tuning = [qsel.qsel_batch_tuning(bt, i) for i in range(len(specs))]
+    iters = [qsel.qsel_batch_stats(bt, i)["pcg_iterations"] for i in range(len(specs))]
+    v_batch = [qsel.qsel_batch_diag_inv(bt, i) for i in range(min(4, len(specs)))]
+    bt.close()
+    torch.cuda.synchronize()
+    # one model after another, same settings, device time per pipeline
+    seq_ms, same = 0.0, True
+    for i, (b, mdl) in enumerate(zip(specs, models)):
+        tu = tuning[i]
+        ctx = qsel.qsel_create(b.n_s, b.n_t, mdl["c_diag"], mdl["g_rowptr"], mdl["g_col"], mdl["g_val"],
+                               mdl["obs_mask"], b.sigma, b.theta, n_parts=b.n_parts, overlap=b.overlap,
+                               n_samples=128, seed=1000 + i, precision=qsel.QSEL_MIXED, pcg_tol=1e-8,
+                               pcg_max_iter=20000, precond_block=tu["precond_block"],
+                               tensor_passes=tu["tensor_passes"] if tu["tensor_passes"] > 0 else -1)
+        v = ctx.diag_inv()
+        seq_ms += ctx.stats()["ms_total"]
+        if i < len(v_batch):
+            same = same and bool(np.array_equal(v, v_batch[i]))
+        ctx.close()
+    replay_ms = float(np.median(reps))
+    n_total = sum(b.n for b in specs)
+    print(json.dumps({
+        "mode": "batch", "models": len(specs), "nodes_total": int(n_total),
+        "grid_sides": sorted({b.m for b in specs}), "n_t_range": [min(b.n_t for b in specs), max(b.n_t for b in specs)],
+        "replay_ms": replay_ms, "replays": reps, "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / replay_ms,
+        "streams": info0["n_streams"], "capture_ms": info0["ms_capture"], "autotune_ms": info0["ms_autotune"],
+        "create_s": t_create, "launches_per_replay": info0["launches_per_replay"],
+        "pcg_iterations_max": int(max(iters)), "first_models_identical_to_separate_contexts": same,
+        "tuning_counts": {f"{k}": sum(1 for t in tuning if (t["precond_block"], t["tensor_passes"]) == k)
+                          for k in sorted({(t["precond_block"], t["tensor_passes"]) for t in tuning})},
+    }), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.batch:
+        run_batch(args)
+        return
     if args.cv_eval:
         run_cv_eval(args)
         return

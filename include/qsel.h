@@ -360,6 +360,67 @@ typedef struct {
 
 qsel_status qsel_cv_plan(qsel_ctx *ctx, const qsel_cv *cv, const qsel_cv_plan_options *opt, qsel_cv_plan_t *plan);
 
+/*
+ * Batch of independent models (uneven sizes), solved together: the whole
+ * pipeline of every model is captured once into one CUDA graph, one branch
+ * per model on a pool of streams (models placed longest-first on the least
+ * loaded stream), with the sampler's convergence loops as conditional while
+ * nodes driven by the device (no host round trip per check; every loop is
+ * bounded by pcg_max_iter and 30 refinement steps).  Later runs replay the
+ * graph; qsel_batch_set_theta changes a model's theta between replays.
+ * The paper has no batch; it serves many small problems at once (one
+ * problem of the size used here leaves most of a GB300 idle).
+ *   models, thetas, partitions, overlaps: HOST arrays of n_models entries
+ *                (read during the call), as for qsel_create.
+ *   opt          shared options; model i uses seed opt->seed + i.
+ *                opt->cuda_stream is the stream the graph is launched on
+ *                (NULL: the batch creates its own; the legacy default stream
+ *                cannot be captured).  profile_kernels and part_overlap must
+ *                be 0 / NULL.
+ *   n_streams    1..64 streams in the pool.
+ *   autotune     non-zero: for every grid size (n_s) the smallest model of
+ *                that size is run with every block-Jacobi block in {16, 32,
+ *                64} and, in the mixed form with tensor cores, both dense
+ *                tile paths (128x128 tcgen05 tiles, 64x64 CUDA-core tiles);
+ *                the fastest pair is used for every model of that size.
+ * Errors: as qsel_create (message in qsel_batch_last_error(NULL)).
+ */
+typedef struct qsel_batch qsel_batch;
+
+typedef struct {
+  int32_t n_models, n_streams;
+  double ms_replay;           /* device time of the last replay (CUDA events)  */
+  double ms_capture;          /* host time of capture + instantiation          */
+  double ms_autotune;         /* host time of the autotuner at creation        */
+  int64_t launches_per_replay;/* kernels in the graph outside the loop bodies,
+                                 plus one pass of every loop body              */
+  int32_t max_pcg_iterations; /* over models, last replay                      */
+} qsel_batch_info_t;
+
+qsel_status qsel_create_batch(qsel_batch **out, int32_t n_models, const qsel_model *models,
+                              const qsel_theta *thetas, const qsel_partition *partitions, const int32_t *overlaps,
+                              const qsel_options *opt, int32_t n_streams, int32_t autotune);
+/* Capture (first call) and replay the graph; returns when every model is
+ * done.  A failure names the model (QSEL_ENOTSPD, QSEL_ENOCONV,
+ * QSEL_ETIMEOUT, QSEL_ECUDA). */
+qsel_status qsel_batch_run(qsel_batch *b);
+qsel_status qsel_batch_set_theta(qsel_batch *b, int32_t model, const qsel_theta *theta);
+/* Results of model `model` (runs the batch first if needed); layouts as
+ * qsel_diag_inv / qsel_trace_grads. */
+qsel_status qsel_batch_diag_inv(qsel_batch *b, int32_t model, double *diag_out, int32_t out_is_device);
+qsel_status qsel_batch_trace_grads(qsel_batch *b, int32_t model, double grads_out[3]);
+/* Per-model statistics of the last replay: pcg_iterations and
+ * pcg_max_rel_residual (no phase times in a graph). */
+qsel_status qsel_batch_stats(const qsel_batch *b, int32_t model, qsel_stats_t *stats);
+qsel_status qsel_batch_info(const qsel_batch *b, qsel_batch_info_t *info);
+/* The tuned settings of a model and the stream it runs on (NULL allowed). */
+qsel_status qsel_batch_tuning(const qsel_batch *b, int32_t model, int32_t *precond_block, int32_t *tensor_passes,
+                              int32_t *stream);
+/* Message of the last failed call on b (NULL: of the last failed
+ * qsel_create_batch on this thread). */
+const char *qsel_batch_last_error(const qsel_batch *b);
+void qsel_batch_destroy(qsel_batch *b);
+
 /* Message of the last failed call on ctx, or, when ctx is NULL, of the last
  * failed qsel_create, qsel_spd_inverse_noalloc or qsel_cv_* call (those that
  * take no context) on this thread.  Never NULL; owned by the library. */

@@ -2,6 +2,7 @@
 // perturbation samples -> multi-RHS PCG -> per-subdomain block factorisation
 // and Takahashi selected inversion -> RB correction -> diag and traces.
 #include <algorithm>
+#include <chrono>
 #include <type_traits>
 #include <array>
 #include <cmath>
@@ -87,6 +88,7 @@ struct qsel_ctx {
   std::vector<Subdomain> parts;
   std::vector<DenseSlot> slots;
   int wave = 1, T_max = 1;
+  int slot_cap = kMaxBatch;            // at most this many subdomains in flight
   double *d_diag = nullptr, *d_selinv = nullptr, *d_corr = nullptr, *d_traces = nullptr, *d_sums = nullptr;
   double *d_corr4 = nullptr;           // (1/k) sum w^4 per node (error estimate)
   std::vector<int> part_nl;            // overlap of every part
@@ -94,6 +96,14 @@ struct qsel_ctx {
   double *d_part_sums = nullptr;       // n_parts doubles of per-part reductions
   float *d_bnd = nullptr, *d_sepd = nullptr;  // feature distances: n_s nodes, n_t slabs
   float *d_cv_F = nullptr, *d_cv_y = nullptr; // planner scratch, allocated on first use
+  // theta in device memory (read by the model kernel) and its pinned host copy
+  double *d_theta = nullptr, *h_theta = nullptr;
+  // graph mode: the pipeline is captured into a CUDA graph with device-driven
+  // loops (conditional while nodes); no host synchronisation inside
+  bool graph_mode = false;
+  cudaStream_t body_stream[2] = {nullptr, nullptr};  // capture streams of loop bodies
+  int32_t *d_loop = nullptr;           // loop state (see launch_loop_init)
+  double *d_tol2 = nullptr;            // inner tolerance of the refinement, squared
   double *d_partials = nullptr, *d_diag_scratch = nullptr;
   TraceSlab *d_slabs = nullptr;
   int n_trace_slabs = 0;
@@ -135,6 +145,7 @@ struct qsel_ctx {
     for (void *p : allocs) cudaFree(p);
     if (h_counters) cudaFreeHost(h_counters);
     if (h_small) cudaFreeHost(h_small);
+    if (h_theta) cudaFreeHost(h_theta);
     for (auto &e : ev)
       if (e) cudaEventDestroy(e);
     for (auto e : phase_ev) cudaEventDestroy(e);
@@ -451,7 +462,7 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   if (fit < 1)
     return fail(QSEL_ENOMEM, "one subdomain's dense working set (" + std::to_string(per_slot >> 20) +
                                  " MiB) does not fit in device memory");
-  c->wave = (int)std::min<size_t>(std::min<size_t>(fit, (size_t)kMaxBatch), (size_t)np);
+  c->wave = (int)std::min<size_t>(std::min<size_t>(fit, (size_t)std::min(kMaxBatch, c->slot_cap)), (size_t)np);
   c->slots.resize(c->wave);
   for (auto &sl : c->slots) {
     sl.Dinv.resize(c->T_max);
@@ -471,6 +482,11 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   }
   QSEL_CUDA_TRY(cudaHostAlloc(&c->h_counters, 64, cudaHostAllocDefault));
   QSEL_CUDA_TRY(cudaHostAlloc(&c->h_small, 64 * sizeof(double), cudaHostAllocDefault));
+  QSEL_CUDA_TRY(cudaHostAlloc(&c->h_theta, 4 * sizeof(double), cudaHostAllocDefault));
+  TRY(c->alloc(&c->d_theta, 4));
+  TRY(c->alloc(&c->d_loop, 4));
+  TRY(c->alloc(&c->d_tol2, 1));
+  QSEL_CUDA_TRY(cudaMemset(c->d_loop, 0, 4 * sizeof(int32_t)));
   for (auto &e : c->ev) QSEL_CUDA_TRY(cudaEventCreate(&e));
   return ok();
 }
@@ -479,7 +495,13 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
 // Pipeline
 // ---------------------------------------------------------------------------
 static Err run_model(qsel_ctx *c) {
-  launch_time_coeffs(c->stream, c->theta.log_kappa, c->theta.log_tau, c->theta.logit_rho, c->n_t, c->tc);
+  // theta goes through pinned host memory, so a captured graph picks up the
+  // value set before each replay
+  c->h_theta[0] = c->theta.log_kappa;
+  c->h_theta[1] = c->theta.log_tau;
+  c->h_theta[2] = c->theta.logit_rho;
+  QSEL_CUDA_TRY(cudaMemcpyAsync(c->d_theta, c->h_theta, 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  launch_time_coeffs(c->stream, c->d_theta, c->n_t, c->tc);
   launch_qs_values(c->stream, c->n_ent, c->d_c_pat, c->d_g_pat, c->d_h_pat, c->d_isqc_pat,
                    c->tc.scalars, c->d_qs, c->d_dqs, c->d_kc);
   QSEL_CUDA_TRY(cudaGetLastError());
@@ -652,7 +674,170 @@ static Err run_sampler(qsel_ctx *c) {
   return ok();
 }
 
+// ---------------------------------------------------------------------------
+// Graph mode: the sampler's loops become conditional while nodes of the
+// captured graph.  capture_while adds the node at the capture position of s
+// (after `init`, which must set the condition) and captures `body` into it
+// on the body stream of the given depth; the body must end with a kernel
+// that sets the condition.
+// ---------------------------------------------------------------------------
+template <class Init, class Body>
+static Err capture_while(qsel_ctx *c, cudaStream_t s, int depth, Init init, Body body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  QSEL_CUDA_TRY(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
+  if (st != cudaStreamCaptureStatusActive) return fail(QSEL_ESTATE, "graph-mode loop outside a stream capture");
+  cudaGraphConditionalHandle h;
+  QSEL_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+  TRY(init(h));
+  QSEL_CUDA_TRY(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  QSEL_CUDA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+  cudaGraph_t body_graph = np.conditional.phGraph_out[0];
+  QSEL_CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaStream_t b = c->body_stream[depth];
+  QSEL_CUDA_TRY(cudaStreamBeginCaptureToGraph(b, body_graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  Err e = body(b, h);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(b, &captured);
+  if (e.code) return e;
+  if (ce != cudaSuccess) return cuda_fail(ce, "capture of a loop body", __FILE__, __LINE__);
+  return ok();
+}
+
+template <typename T>
+static void pcg_start(qsel_ctx *c, cudaStream_t s, const PcgVec<T> &v, const T *pblk, double tol) {
+  const size_t vbytes = (size_t)c->n * c->ld * sizeof(T);
+  cudaMemsetAsync(v.x, 0, vbytes, s);
+  cudaMemsetAsync(v.p, 0, vbytes, s);
+  cudaMemsetAsync(v.alpha, 0, (size_t)c->ld * sizeof(double), s);
+  launch_pcg_update<T>(s, v, pblk, c->bsize);
+  launch_pcg_reduce_beta<T>(s, v, tol, 1);
+  launch_pcg_p_update<T>(s, v);
+}
+
+template <typename T>
+static void pcg_steps(qsel_ctx *c, cudaStream_t s, const PcgVec<T> &v, const T *pblk, double tol, int count) {
+  BtSpmmArgs<T> a{};
+  a.pat = c->pat;
+  a.val = c->d_qs;
+  a.c0 = c->tc.a0;
+  a.c1 = c->tc.a1;
+  a.obs = c->d_obs;
+  a.obs_w = c->obs_w;
+  a.n_s = c->n_s;
+  a.n_t = c->n_t;
+  a.ld = c->ld;
+  a.x = v.p;
+  a.y = v.q;
+  a.dot_partial = c->d_pa;
+  for (int b = 0; b < count; ++b) {
+    launch_bt_spmm<T>(s, a);
+    launch_pcg_reduce_alpha<T>(s, v);
+    launch_pcg_update<T>(s, v, pblk, c->bsize);
+    launch_pcg_reduce_beta<T>(s, v, tol, 0);
+    launch_pcg_p_update<T>(s, v);
+  }
+}
+
+constexpr int kGraphCheckEvery = 8;
+
+// PCG with the device-driven stop: while (active columns and iterations <
+// max_iter - loop[2]) run 8 iterations.
+template <typename T>
+static Err pcg_graph(qsel_ctx *c, cudaStream_t s, int depth, const PcgVec<T> &v, const T *pblk, double tol) {
+  pcg_start<T>(c, s, v, pblk, tol);
+  const int max_iter = c->opt.pcg_max_iter;
+  return capture_while(
+      c, s, depth,
+      [&](cudaGraphConditionalHandle h) {
+        launch_loop_init(s, h, v.counters, c->d_loop, max_iter);
+        return ok();
+      },
+      [&](cudaStream_t b, cudaGraphConditionalHandle h) {
+        pcg_steps<T>(c, b, v, pblk, tol, kGraphCheckEvery);
+        launch_loop_ctl(b, h, v.counters, c->d_loop, kGraphCheckEvery, max_iter);
+        QSEL_CUDA_TRY(cudaGetLastError());
+        return ok();
+      });
+}
+
+// The sampler of run_sampler, enqueued for capture (no host synchronisation).
+static Err run_sampler_graph(qsel_ctx *c) {
+  cudaStream_t s = c->stream;
+  launch_philox_normals(s, c->opt.seed, 0u, c->n, c->k, c->ld, c->d_z1);
+  launch_philox_normals(s, c->opt.seed, 1u, c->n_obs, c->k, c->ld, c->d_z2);
+  launch_perturbation_rhs(s, c->pat, c->d_kc, c->n_s, c->n_t, c->ld, c->tc.bdiag, c->tc.scalars,
+                          c->d_z1, c->d_z2, c->d_obs_index, 1.0 / c->sigma, c->d_R);
+  const size_t vec = (size_t)c->n * c->ld;
+  QSEL_CUDA_TRY(cudaMemsetAsync(c->d_loop, 0, 4 * sizeof(int32_t), s));
+  if (!c->mixed) {
+    double *pblk = static_cast<double *>(c->d_pblk);
+    launch_jacobi_setup<double>(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
+                                c->bsize, pblk, c->d_err);
+    QSEL_CUDA_TRY(cudaMemcpyAsync(c->d_r, c->d_R, vec * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    PcgVec<double> v = make_pcg<double>(c, c->d_X, c->d_r, c->d_zv, c->d_p, c->d_q);
+    TRY(pcg_graph<double>(c, s, 0, v, pblk, c->opt.pcg_tol));
+    launch_loop_status(s, v.counters, c->d_loop);
+    QSEL_CUDA_TRY(cudaGetLastError());
+    return ok();
+  }
+  float *pblk = static_cast<float *>(c->d_pblk);
+  launch_jacobi_setup<float>(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
+                             c->bsize, pblk, c->d_err);
+  PcgVec<float> v = make_pcg<float>(c, c->f_x, c->f_r, c->f_z, c->f_p, c->f_q);
+  v.tol2_dev = c->d_tol2;
+  QSEL_CUDA_TRY(cudaMemsetAsync(c->d_X, 0, vec * sizeof(double), s));
+  QSEL_CUDA_TRY(cudaMemsetAsync(c->d_q, 0, vec * sizeof(double), s));
+  BtSpmmArgs<double> a{};
+  a.pat = c->pat;
+  a.val = c->d_qs;
+  a.c0 = c->tc.a0;
+  a.c1 = c->tc.a1;
+  a.obs = c->d_obs;
+  a.obs_w = c->obs_w;
+  a.n_s = c->n_s;
+  a.n_t = c->n_t;
+  a.ld = c->ld;
+  a.x = c->d_X;
+  a.y = c->d_q;
+  a.dot_partial = nullptr;
+  const double inner_floor = 3e-6;
+  const int max_outer = 30;
+  const double tol = c->opt.pcg_tol;
+  double *max_rel = c->d_scal + 5 * c->ld;
+  const int max_iter = c->opt.pcg_max_iter;
+  return capture_while(
+      c, s, 0,
+      [&](cudaGraphConditionalHandle h) {
+        launch_residual(s, c->d_R, c->d_q, c->d_z1, c->f_r, c->n, c->ld, c->d_pa, c->d_pb);
+        launch_residual_check(s, c->d_pa, c->d_pb, residual_grid(c->n), c->ld, tol, c->d_counters, max_rel);
+        launch_refine_ctl(s, h, c->d_counters, max_rel, c->d_loop, 1, max_outer, max_iter, tol, inner_floor,
+                          c->d_tol2);
+        return ok();
+      },
+      [&](cudaStream_t b, cudaGraphConditionalHandle h) {
+        TRY(pcg_graph<float>(c, b, 1, v, pblk, 1.0));
+        launch_accumulate(b, c->d_X, c->f_x, (int64_t)vec);
+        launch_bt_spmm<double>(b, a);
+        launch_residual(b, c->d_R, c->d_q, c->d_z1, c->f_r, c->n, c->ld, c->d_pa, c->d_pb);
+        launch_residual_check(b, c->d_pa, c->d_pb, residual_grid(c->n), c->ld, tol, c->d_counters, max_rel);
+        launch_refine_ctl(b, h, c->d_counters, max_rel, c->d_loop, 0, max_outer, max_iter, tol, inner_floor,
+                          c->d_tol2);
+        QSEL_CUDA_TRY(cudaGetLastError());
+        return ok();
+      });
+}
+
 static void phase_mark(qsel_ctx *c, std::vector<std::pair<cudaEvent_t, int>> &marks, int phase) {
+  if (c->graph_mode) return;
   cudaEvent_t e = c->phase_event();
   cudaEventRecord(e, c->stream);
   marks.emplace_back(e, phase);
@@ -1108,13 +1293,161 @@ static Err run_pipeline_body(qsel_ctx *c) {
   return ok();
 }
 
+// The pipeline of run_pipeline_body, stream-ordered and free of host
+// synchronisation and events, for capture into a graph (sampler loops as
+// conditional while nodes).
+static Err enqueue_pipeline_graph(qsel_ctx *c) {
+  cudaStream_t s = c->stream;
+  QSEL_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), s));
+  QSEL_CUDA_TRY(cudaMemsetAsync(c->d_corr, 0, (size_t)c->n * sizeof(double), s));
+  QSEL_CUDA_TRY(cudaMemsetAsync(c->d_corr4, 0, (size_t)c->n * sizeof(double), s));
+  TRY(run_model(c));
+  if (c->parts.size() > 1) {
+    TRY(run_sampler_graph(c));
+  } else {
+    QSEL_CUDA_TRY(cudaMemsetAsync(c->d_loop, 0, 4 * sizeof(int32_t), s));
+  }
+  std::vector<std::pair<cudaEvent_t, int>> marks;
+  const int np = (int)c->parts.size();
+  for (int p0 = 0; p0 < np; p0 += c->wave) {
+    const int p1 = std::min(np, p0 + c->wave);
+    if (c->mixed)
+      TRY(run_wave<float>(c, p0, p1, marks));
+    else
+      TRY(run_wave<double>(c, p0, p1, marks));
+  }
+  launch_sum(s, c->d_diag, c->d_selinv, c->d_corr, c->n);
+  launch_trace_combine(s, c->d_slabs, c->n_trace_slabs, c->d_sums, c->d_partials, np * corr_grid(), c->tc.a0,
+                       c->tc.a1, c->tc.r0, c->tc.r1, c->d_traces);
+  QSEL_CUDA_TRY(cudaGetLastError());
+  return ok();
+}
+
+// After a replay of the graph: error flags, sampler status and statistics.
+static Err collect_graph(qsel_ctx *c) {
+  int32_t err = 0, loop[4] = {0, 0, 0, 0};
+  double rel = 0.0;
+  QSEL_CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  QSEL_CUDA_TRY(cudaMemcpy(loop, c->d_loop, sizeof(loop), cudaMemcpyDeviceToHost));
+  if (c->parts.size() > 1)
+    QSEL_CUDA_TRY(cudaMemcpy(&rel, c->d_scal + 5 * c->ld, sizeof(double), cudaMemcpyDeviceToHost));
+  c->stats = qsel_stats_t{};
+  c->stats.pcg_iterations = loop[2];
+  c->stats.pcg_max_rel_residual = rel;
+  if (err & 1) return fail(QSEL_ENOTSPD, "a pivot of a dense block factorisation was not positive");
+  if (err & 2) return fail(QSEL_ETIMEOUT, "a bounded device-side wait of the tensor-core GEMM gave up");
+  if (loop[3] == QSEL_ENOCONV)
+    return fail(QSEL_ENOCONV, "the sampler did not reach pcg_tol within its iteration limits (max relative residual " +
+                                  std::to_string(rel) + ")");
+  c->computed = true;
+  return ok();
+}
+
+// ---------------------------------------------------------------------------
+// Batch of independent models: one captured graph, one branch per model on a
+// pool of streams (models placed longest-first on the least-loaded stream),
+// the sampler loops device-driven.  An optional autotuner picks, per model
+// size class, the block-Jacobi block and the dense tile path by timing them.
+// ---------------------------------------------------------------------------
+// subdomains in flight per batch model: the batch's concurrency comes from
+// its many models, and two dense working sets per model keep 64 models of
+// up to 64 x 64 x 128 within device memory
+constexpr int kBatchSlots = 2;
+
+struct qsel_batch {
+  std::vector<qsel_ctx *> models;
+  std::vector<int> stream_of;
+  std::vector<double> cost;
+  cudaStream_t main = nullptr;
+  bool own_main = false;
+  std::vector<cudaStream_t> pool;
+  cudaStream_t body[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches_per_replay = 0;
+  double ms_last = 0.0, ms_capture = 0.0, ms_autotune = 0.0;
+  bool computed = false;
+  std::vector<std::array<int, 2>> tuned;   // per model: precond_block, tensor_passes
+  std::string last_error;
+  ~qsel_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto *c : models) qsel_destroy(c);
+    for (auto st : pool) cudaStreamDestroy(st);
+    for (auto st : body)
+      if (st) cudaStreamDestroy(st);
+    if (own_main && main) cudaStreamDestroy(main);
+    for (auto e : join) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+  }
+};
+
+static qsel_status batch_fail(qsel_batch *b, const Err &e) {
+  if (e.code && b) b->last_error = e.msg;
+  return (qsel_status)e.code;
+}
+
+static Err batch_capture(qsel_batch *b) {
+  const int64_t l0 = g_launch_count;
+  const auto w0 = std::chrono::steady_clock::now();
+  QSEL_CUDA_TRY(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeRelaxed));
+  Err e = ok();
+  if (cudaEventRecord(b->fork, b->main) != cudaSuccess) e = fail(QSEL_ECUDA, "fork event");
+  for (auto st : b->pool)
+    if (e.code == 0 && cudaStreamWaitEvent(st, b->fork, 0) != cudaSuccess) e = fail(QSEL_ECUDA, "fork wait");
+  std::vector<int> order(b->models.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return b->cost[x] > b->cost[y]; });
+  for (int i : order) {
+    if (e.code) break;
+    qsel_ctx *c = b->models[i];
+    c->stream = b->pool[b->stream_of[i]];
+    c->body_stream[0] = b->body[0];
+    c->body_stream[1] = b->body[1];
+    c->graph_mode = true;
+    e = enqueue_pipeline_graph(c);
+    if (e.code) e.msg = "model " + std::to_string(i) + ": " + e.msg;
+  }
+  for (size_t j = 0; j < b->pool.size() && e.code == 0; ++j) {
+    if (cudaEventRecord(b->join[j], b->pool[j]) != cudaSuccess ||
+        cudaStreamWaitEvent(b->main, b->join[j], 0) != cudaSuccess)
+      e = fail(QSEL_ECUDA, "join");
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(b->main, &g);
+  if (e.code) {
+    if (g) cudaGraphDestroy(g);
+    return e;
+  }
+  if (ce != cudaSuccess) return cuda_fail(ce, "end of the batch capture", __FILE__, __LINE__);
+  b->graph = g;
+  QSEL_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
+  b->ms_capture = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
+  b->launches_per_replay = g_launch_count - l0;
+  return ok();
+}
+
+// Modelled work of one model (dense slabs x n_pad^3 plus samples x n) for the
+// stream placement.
+static double model_cost(const qsel_ctx *c) {
+  double slabs = 0.0;
+  for (auto &sd : c->parts) slabs += sd.T;
+  const double npad = (double)c->n_pad;
+  return 1.37e-13 * slabs * npad * npad * npad + 1.73e-8 * (double)c->k * c->n;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
 
-qsel_status qsel_create(qsel_ctx **out, const qsel_model *model, const qsel_theta *theta,
-                        const qsel_partition *partition, int32_t overlap, const qsel_options *opt) {
+static qsel_status create_ctx(qsel_ctx **out, const qsel_model *model, const qsel_theta *theta,
+                              const qsel_partition *partition, int32_t overlap, const qsel_options *opt,
+                              int slot_cap) {
   if (!out) {
     g_create_error = "out must not be NULL";
     return QSEL_EINVAL;
@@ -1154,6 +1487,7 @@ qsel_status qsel_create(qsel_ctx **out, const qsel_model *model, const qsel_thet
     }
   }
   c->stream = reinterpret_cast<cudaStream_t>(opt->cuda_stream);
+  c->slot_cap = slot_cap;
   e = build(c, model, partition, overlap);
   if (e.code) {
     g_create_error = e.msg;
@@ -1162,6 +1496,11 @@ qsel_status qsel_create(qsel_ctx **out, const qsel_model *model, const qsel_thet
   }
   *out = c;
   return QSEL_OK;
+}
+
+qsel_status qsel_create(qsel_ctx **out, const qsel_model *model, const qsel_theta *theta,
+                        const qsel_partition *partition, int32_t overlap, const qsel_options *opt) {
+  return create_ctx(out, model, theta, partition, overlap, opt, kMaxBatch);
 }
 
 qsel_status qsel_set_theta(qsel_ctx *ctx, const qsel_theta *theta) {
@@ -1424,6 +1763,254 @@ qsel_status qsel_cv_plan(qsel_ctx *ctx, const qsel_cv *cv, const qsel_cv_plan_op
     plan->predicted_err = std::max(plan->predicted_err, e);
   }
   return QSEL_OK;
+}
+
+qsel_status qsel_create_batch(qsel_batch **out, int32_t n_models, const qsel_model *models,
+                              const qsel_theta *thetas, const qsel_partition *partitions, const int32_t *overlaps,
+                              const qsel_options *opt, int32_t n_streams, int32_t autotune) {
+  if (!out) {
+    g_create_error = "out must not be NULL";
+    return QSEL_EINVAL;
+  }
+  *out = nullptr;
+  if (n_models < 1 || !models || !thetas || !partitions || !overlaps || !opt || n_streams < 1 || n_streams > 64) {
+    g_create_error = "qsel_create_batch: n_models >= 1, non-NULL arrays and 1 <= n_streams <= 64 required";
+    return QSEL_EINVAL;
+  }
+  if (opt->profile_kernels || opt->part_overlap) {
+    g_create_error = "qsel_create_batch: profile_kernels and part_overlap are not available in a batch";
+    return QSEL_EINVAL;
+  }
+  for (int i = 0; i < n_models; ++i) {
+    Err e = validate(&models[i], &thetas[i], &partitions[i], overlaps[i], opt);
+    if (e.code) {
+      g_create_error = "model " + std::to_string(i) + ": " + e.msg;
+      return (qsel_status)e.code;
+    }
+  }
+  qsel_batch *b = new (std::nothrow) qsel_batch();
+  if (!b) {
+    g_create_error = "host allocation failed";
+    return QSEL_ENOMEM;
+  }
+  auto bail = [&](qsel_status st, const std::string &m) {
+    g_create_error = m;
+    delete b;
+    return st;
+  };
+  b->tuned.assign(n_models, {opt->precond_block, opt->tensor_passes});
+  if (autotune) {
+    // per grid size (n_s): time every (block-Jacobi block, dense path) pair on
+    // the smallest model of that size, keep the fastest
+    const auto w0 = std::chrono::steady_clock::now();
+    std::map<int, int> rep;
+    for (int i = 0; i < n_models; ++i) {
+      auto it = rep.find(models[i].n_s);
+      if (it == rep.end() || (int64_t)models[i].n_t * partitions[i].n_parts <
+                                 (int64_t)models[it->second].n_t * partitions[it->second].n_parts)
+        rep[models[i].n_s] = i;
+    }
+    std::vector<std::array<int, 2>> cands;
+    for (int pb : {16, 32, 64}) {
+      if (opt->precision == QSEL_MIXED && tc_gemm_available()) {
+        cands.push_back({pb, 3});
+        cands.push_back({pb, -1});
+      } else {
+        cands.push_back({pb, 0});
+      }
+    }
+    std::map<int, std::array<int, 2>> best;
+    for (auto &kv : rep) {
+      const int i = kv.second;
+      double best_ms = 1e300;
+      for (auto cd : cands) {
+        qsel_options o = *opt;
+        o.precond_block = cd[0];
+        o.tensor_passes = cd[1];
+        o.seed = opt->seed + (uint64_t)i;
+        qsel_ctx *t = nullptr;
+        qsel_status st = create_ctx(&t, &models[i], &thetas[i], &partitions[i], overlaps[i], &o, kBatchSlots);
+        if (st) return bail(st, "autotune: " + g_create_error);
+        double ms = 0.0;
+        Err e = run_pipeline(t);                     // warm-up
+        for (int r = 0; r < 2 && e.code == 0; ++r) {
+          t->computed = false;
+          e = run_pipeline(t);
+          ms += t->stats.ms_total;
+        }
+        qsel_destroy(t);
+        if (e.code) return bail((qsel_status)e.code, "autotune: " + e.msg);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best[kv.first] = cd;
+        }
+      }
+    }
+    for (int i = 0; i < n_models; ++i) b->tuned[i] = best[models[i].n_s];
+    b->ms_autotune = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
+  }
+  if (opt->cuda_stream) {
+    b->main = reinterpret_cast<cudaStream_t>(opt->cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(QSEL_ECUDA, "stream creation failed");
+    b->own_main = true;
+  }
+  b->pool.resize(std::min(n_streams, n_models));
+  for (auto &st : b->pool)
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(QSEL_ECUDA, "stream creation failed");
+  for (auto &st : b->body)
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(QSEL_ECUDA, "stream creation failed");
+  b->join.resize(b->pool.size());
+  for (auto &e : b->join)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bail(QSEL_ECUDA, "event");
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&b->t0) != cudaSuccess || cudaEventCreate(&b->t1) != cudaSuccess)
+    return bail(QSEL_ECUDA, "event creation failed");
+  for (int i = 0; i < n_models; ++i) {
+    qsel_options o = *opt;
+    o.precond_block = b->tuned[i][0];
+    o.tensor_passes = b->tuned[i][1];
+    o.seed = opt->seed + (uint64_t)i;
+    o.cuda_stream = nullptr;
+    qsel_ctx *c = nullptr;
+    qsel_status st = create_ctx(&c, &models[i], &thetas[i], &partitions[i], overlaps[i], &o, kBatchSlots);
+    if (st) return bail(st, "model " + std::to_string(i) + ": " + g_create_error);
+    b->models.push_back(c);
+    b->cost.push_back(model_cost(c));
+  }
+  // longest first onto the least-loaded stream
+  std::vector<int> order(n_models);
+  for (int i = 0; i < n_models; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return b->cost[x] > b->cost[y]; });
+  std::vector<double> load(b->pool.size(), 0.0);
+  b->stream_of.assign(n_models, 0);
+  for (int i : order) {
+    const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->stream_of[i] = j;
+    load[j] += b->cost[i];
+  }
+  *out = b;
+  return QSEL_OK;
+}
+
+qsel_status qsel_batch_run(qsel_batch *b) {
+  if (!b) return QSEL_EINVAL;
+  if (!b->exec) {
+    Err e = batch_capture(b);
+    if (e.code) return batch_fail(b, e);
+  }
+  cudaError_t ce = cudaEventRecord(b->t0, b->main);
+  if (ce == cudaSuccess) ce = cudaGraphLaunch(b->exec, b->main);
+  if (ce == cudaSuccess) ce = cudaEventRecord(b->t1, b->main);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->main);
+  if (ce != cudaSuccess) return batch_fail(b, cuda_fail(ce, "batch graph launch", __FILE__, __LINE__));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, b->t0, b->t1);
+  b->ms_last = ms;
+  for (size_t i = 0; i < b->models.size(); ++i) {
+    Err e = collect_graph(b->models[i]);
+    if (e.code) {
+      e.msg = "model " + std::to_string(i) + ": " + e.msg;
+      b->models[i]->last_error = e.msg;
+      return batch_fail(b, e);
+    }
+  }
+  b->computed = true;
+  return QSEL_OK;
+}
+
+qsel_status qsel_batch_set_theta(qsel_batch *b, int32_t model, const qsel_theta *theta) {
+  if (!b) return QSEL_EINVAL;
+  if (model < 0 || model >= (int)b->models.size() || !theta)
+    return batch_fail(b, fail(QSEL_EINVAL, "model index out of range or theta NULL"));
+  qsel_ctx *c = b->models[model];
+  qsel_status st = qsel_set_theta(c, theta);
+  if (st) return batch_fail(b, fail(st, c->last_error));
+  // the captured copy reads the pinned host theta at every replay
+  c->h_theta[0] = theta->log_kappa;
+  c->h_theta[1] = theta->log_tau;
+  c->h_theta[2] = theta->logit_rho;
+  b->computed = false;
+  return QSEL_OK;
+}
+
+static qsel_status batch_model(qsel_batch *b, int32_t model, qsel_ctx **c) {
+  if (model < 0 || model >= (int)b->models.size())
+    return batch_fail(b, fail(QSEL_EINVAL, "model index out of range"));
+  if (!b->computed) {
+    qsel_status st = qsel_batch_run(b);
+    if (st) return st;
+  }
+  *c = b->models[model];
+  return QSEL_OK;
+}
+
+qsel_status qsel_batch_diag_inv(qsel_batch *b, int32_t model, double *diag_out, int32_t out_is_device) {
+  if (!b) return QSEL_EINVAL;
+  if (!diag_out) return batch_fail(b, fail(QSEL_EINVAL, "diag_out must not be NULL"));
+  qsel_ctx *c = nullptr;
+  qsel_status st = batch_model(b, model, &c);
+  if (st) return st;
+  cudaError_t ce = cudaMemcpy(diag_out, c->d_diag, (size_t)c->n * sizeof(double),
+                              out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  if (ce != cudaSuccess) return batch_fail(b, cuda_fail(ce, "copy of diag", __FILE__, __LINE__));
+  return QSEL_OK;
+}
+
+qsel_status qsel_batch_trace_grads(qsel_batch *b, int32_t model, double grads_out[3]) {
+  if (!b) return QSEL_EINVAL;
+  if (!grads_out) return batch_fail(b, fail(QSEL_EINVAL, "grads_out must not be NULL"));
+  qsel_ctx *c = nullptr;
+  qsel_status st = batch_model(b, model, &c);
+  if (st) return st;
+  if (c->n_l < 1 && c->parts.size() > 1)
+    return batch_fail(b, fail(QSEL_EINVAL, "trace gradients need overlap >= 1 when there are several parts"));
+  cudaError_t ce = cudaMemcpy(grads_out, c->d_traces, 3 * sizeof(double), cudaMemcpyDeviceToHost);
+  if (ce != cudaSuccess) return batch_fail(b, cuda_fail(ce, "copy of traces", __FILE__, __LINE__));
+  return QSEL_OK;
+}
+
+qsel_status qsel_batch_stats(const qsel_batch *b, int32_t model, qsel_stats_t *stats) {
+  if (!b || !stats || model < 0 || model >= (int)b->models.size()) return QSEL_EINVAL;
+  *stats = b->models[model]->stats;
+  return QSEL_OK;
+}
+
+qsel_status qsel_batch_info(const qsel_batch *b, qsel_batch_info_t *info) {
+  if (!b || !info) return QSEL_EINVAL;
+  qsel_batch_info_t t{};
+  t.n_models = (int32_t)b->models.size();
+  t.n_streams = (int32_t)b->pool.size();
+  t.ms_replay = b->ms_last;
+  t.ms_capture = b->ms_capture;
+  t.ms_autotune = b->ms_autotune;
+  t.launches_per_replay = b->launches_per_replay;
+  for (auto *c : b->models) t.max_pcg_iterations = std::max(t.max_pcg_iterations, c->stats.pcg_iterations);
+  *info = t;
+  return QSEL_OK;
+}
+
+qsel_status qsel_batch_tuning(const qsel_batch *b, int32_t model, int32_t *precond_block, int32_t *tensor_passes,
+                              int32_t *stream) {
+  if (!b || model < 0 || model >= (int)b->models.size()) return QSEL_EINVAL;
+  if (precond_block) *precond_block = b->models[model]->bsize;
+  if (tensor_passes) *tensor_passes = b->models[model]->mixed ? b->models[model]->tc_passes : 0;
+  if (stream) *stream = b->stream_of[model];
+  return QSEL_OK;
+}
+
+const char *qsel_batch_last_error(const qsel_batch *b) {
+  if (!b) return g_create_error.c_str();
+  return b->last_error.c_str();
+}
+
+void qsel_batch_destroy(qsel_batch *b) {
+  if (!b) return;
+  if (b->main) cudaStreamSynchronize(b->main);
+  delete b;
 }
 
 const char *qsel_last_error(const qsel_ctx *ctx) {

@@ -59,8 +59,9 @@ extern thread_local Profiler *g_prof;
 void set_context_free_error(const std::string &msg);
 
 // ---------------------------------------------------------------- model.cu
-void launch_time_coeffs(cudaStream_t s, double log_kappa, double log_tau, double logit_rho,
-                        int n_t, TimeCoeffs tc);
+// theta_dev: (log kappa, log tau, logit rho) in device memory, so that a
+// captured graph reads the current theta at every replay
+void launch_time_coeffs(cudaStream_t s, const double *theta_dev, int n_t, TimeCoeffs tc);
 void launch_qs_values(cudaStream_t s, int n_ent, const double *c_pat, const double *g_pat,
                       const double *h_pat, const double *isqc_pat, const double *scalars,
                       double *qs, double *dqs, double *kc);
@@ -100,7 +101,20 @@ struct PcgVec {
   int32_t *active;
   int32_t *counters;                  // [0] active columns
   double *max_rel;                    // [0] max relative residual
+  const double *tol2_dev = nullptr;   // squared stopping tolerance in device memory (overrides the argument)
 };
+// Device-driven loops of captured graphs: the condition of a while node is
+// set by these kernels from the active-column count.
+//   loop[0] iterations of the current solve, loop[1] completed refinement
+//   steps, loop[2] total inner iterations, loop[3] status (0 or QSEL_ENOCONV)
+void launch_loop_init(cudaStream_t s, cudaGraphConditionalHandle h, const int32_t *counters, int32_t *loop,
+                      int max_iter);
+void launch_loop_ctl(cudaStream_t s, cudaGraphConditionalHandle h, const int32_t *counters, int32_t *loop, int step,
+                     int max_iter);
+void launch_loop_status(cudaStream_t s, const int32_t *counters, int32_t *loop);
+void launch_refine_ctl(cudaStream_t s, cudaGraphConditionalHandle h, const int32_t *counters,
+                       const double *max_rel, int32_t *loop, int first, int max_outer, int max_iter, double tol,
+                       double inner_floor, double *tol2_dev);
 template <typename T>
 void launch_jacobi_setup(cudaStream_t s, const SellPattern &pat, const double *qs, const double *a0,
                          const double *a1, const uint8_t *obs, double obs_w, int n_s, int n_t,

@@ -13,9 +13,9 @@ namespace qsel {
 thread_local int64_t g_launch_count = 0;
 thread_local Profiler *g_prof = nullptr;
 
-__global__ void k_time_coeffs(double log_kappa, double log_tau, double logit_rho, int n_t,
-                              TimeCoeffs tc) {
+__global__ void k_time_coeffs(const double *__restrict__ theta, int n_t, TimeCoeffs tc) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double log_kappa = theta[0], log_tau = theta[1], logit_rho = theta[2];
   const double kappa = exp(log_kappa);
   const double tau = exp(log_tau);
   const double rho = 1.0 / (1.0 + exp(-logit_rho));
@@ -50,10 +50,9 @@ __global__ void k_time_coeffs(double log_kappa, double log_tau, double logit_rho
   tc.scalars[4] = -rho;
 }
 
-void launch_time_coeffs(cudaStream_t s, double log_kappa, double log_tau, double logit_rho,
-                        int n_t, TimeCoeffs tc) {
+void launch_time_coeffs(cudaStream_t s, const double *theta_dev, int n_t, TimeCoeffs tc) {
   ++g_launch_count;
-  k_time_coeffs<<<1, 32, 0, s>>>(log_kappa, log_tau, logit_rho, n_t, tc);
+  k_time_coeffs<<<1, 32, 0, s>>>(theta_dev, n_t, tc);
 }
 
 __global__ void k_qs_values(int n_ent, const double *__restrict__ c_pat,

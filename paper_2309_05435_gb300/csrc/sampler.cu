@@ -5,6 +5,7 @@
 // Layout: every n x k block of vectors is row-major with leading dimension
 // ld (a multiple of 64): row t * n_s + i holds the k samples of node i of
 // slab t contiguously, so one warp reads a whole row with 16-byte loads.
+#include "qsel.h"
 #include "kernels.cuh"
 #include "sweep.cuh"
 
@@ -559,7 +560,7 @@ __global__ void __launch_bounds__(256) k_pcg_reduce_beta(PcgVec<T> v, double tol
   } else if (v.active[c]) {
     v.beta[c] = v.rho[c] != 0.0 ? rz / v.rho[c] : 0.0;
     v.rho[c] = rz;
-    if (rr <= tol2 * v.bb[c]) v.active[c] = 0;
+    if (rr <= (v.tol2_dev ? *v.tol2_dev : tol2) * v.bb[c]) v.active[c] = 0;
   } else {
     v.beta[c] = 0.0;
   }
@@ -705,6 +706,82 @@ void launch_residual_check(cudaStream_t s, const double *partial_rr, const doubl
   ++g_launch_count;
   k_residual_check<<<1, (ld + 31) / 32 * 32, 0, s>>>(partial_rr, partial_bb, n_parts, ld, tol * tol, counters,
                                                      max_rel);
+}
+
+// ---------------------------------------------------------------------------
+// Loop control for captured graphs (conditional while nodes).  Every loop
+// body ends with a control kernel that counts iterations, so a loop ends
+// after at most max_iter iterations whatever the data.
+// ---------------------------------------------------------------------------
+__global__ void k_loop_init(cudaGraphConditionalHandle h, const int32_t *counters, int32_t *loop, int max_iter) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  loop[0] = 0;
+  const int limit = max_iter - loop[2];
+  cudaGraphSetConditional(h, (counters[0] > 0 && limit > 0) ? 1u : 0u);
+}
+
+__global__ void k_loop_ctl(cudaGraphConditionalHandle h, const int32_t *counters, int32_t *loop, int step,
+                           int max_iter) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int it = loop[0] + step;
+  loop[0] = it;
+  const int limit = max_iter - loop[2];
+  cudaGraphSetConditional(h, (counters[0] > 0 && it < limit) ? 1u : 0u);
+}
+
+__global__ void k_loop_status(const int32_t *counters, int32_t *loop) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  loop[2] = loop[0];
+  if (counters[0] > 0) loop[3] = QSEL_ENOCONV;
+}
+
+// Refinement loop of the mixed sampler: after a residual check, decide
+// whether another inner solve runs and with which inner tolerance
+// max(floor, 0.5 tol / rel).
+__global__ void k_refine_ctl(cudaGraphConditionalHandle h, const int32_t *counters, const double *max_rel,
+                             int32_t *loop, int first, int max_outer, int max_iter, double tol, double inner_floor,
+                             double *tol2_dev) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (first) {
+    loop[0] = 0;
+    loop[1] = 0;
+    loop[2] = 0;
+    loop[3] = 0;
+  } else {
+    loop[1] += 1;
+    loop[2] += loop[0];
+  }
+  bool go = counters[0] > 0;
+  if (go && (loop[1] >= max_outer || loop[2] >= max_iter)) {
+    loop[3] = QSEL_ENOCONV;
+    go = false;
+  }
+  if (go) {
+    const double it = fmax(inner_floor, 0.5 * tol / fmax(*max_rel, 1e-300));
+    *tol2_dev = it * it;
+  }
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+void launch_loop_init(cudaStream_t s, cudaGraphConditionalHandle h, const int32_t *counters, int32_t *loop,
+                      int max_iter) {
+  ++g_launch_count;
+  k_loop_init<<<1, 32, 0, s>>>(h, counters, loop, max_iter);
+}
+void launch_loop_ctl(cudaStream_t s, cudaGraphConditionalHandle h, const int32_t *counters, int32_t *loop, int step,
+                     int max_iter) {
+  ++g_launch_count;
+  k_loop_ctl<<<1, 32, 0, s>>>(h, counters, loop, step, max_iter);
+}
+void launch_loop_status(cudaStream_t s, const int32_t *counters, int32_t *loop) {
+  ++g_launch_count;
+  k_loop_status<<<1, 32, 0, s>>>(counters, loop);
+}
+void launch_refine_ctl(cudaStream_t s, cudaGraphConditionalHandle h, const int32_t *counters,
+                       const double *max_rel, int32_t *loop, int first, int max_outer, int max_iter, double tol,
+                       double inner_floor, double *tol2_dev) {
+  ++g_launch_count;
+  k_refine_ctl<<<1, 32, 0, s>>>(h, counters, max_rel, loop, first, max_outer, max_iter, tol, inner_floor, tol2_dev);
 }
 
 __global__ void k_accumulate(double *__restrict__ x, const float *__restrict__ d, int64_t count) {

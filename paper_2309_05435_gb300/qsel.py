@@ -42,6 +42,11 @@ class qsel_options(ctypes.Structure):
                 ("part_overlap", POINTER(c_int32))]
 
 
+class qsel_batch_info_t(ctypes.Structure):
+    _fields_ = [("n_models", c_int32), ("n_streams", c_int32), ("ms_replay", c_double), ("ms_capture", c_double),
+                ("ms_autotune", c_double), ("launches_per_replay", c_int64), ("max_pcg_iterations", c_int32)]
+
+
 class qsel_cv_plan_options(ctypes.Structure):
     _fields_ = [("target_rel_err", c_double), ("max_overlap", c_int32), ("min_samples", c_int32),
                 ("max_samples", c_int32), ("cost_pcg", c_double), ("cost_dense", c_double),
@@ -68,7 +73,9 @@ EXPORTED = ["qsel_create", "qsel_set_theta", "qsel_diag_inv", "qsel_trace_grads"
             "qsel_debug_get_selinv_diag", "qsel_spd_inverse_noalloc", "qsel_error_estimate",
             "qsel_cv_create", "qsel_cv_set_params", "qsel_cv_get_params", "qsel_cv_predict", "qsel_cv_grad",
             "qsel_cv_train", "qsel_cv_features", "qsel_cv_targets", "qsel_cv_plan",
-            "qsel_cv_destroy", "qsel_last_error", "qsel_destroy"]
+            "qsel_cv_destroy", "qsel_create_batch", "qsel_batch_run", "qsel_batch_set_theta",
+            "qsel_batch_diag_inv", "qsel_batch_trace_grads", "qsel_batch_stats", "qsel_batch_info",
+            "qsel_batch_tuning", "qsel_batch_last_error", "qsel_batch_destroy", "qsel_last_error", "qsel_destroy"]
 QSEL_NOALLOC_MAX_N = 1024
 QSEL_CV_FEATURES = 14
 QSEL_CV_PARAMS = 5185
@@ -109,12 +116,26 @@ def load_library(path: str = LIB_PATH):
     lib.qsel_cv_plan.argtypes = [c_void_p, c_void_p, P(qsel_cv_plan_options), P(qsel_cv_plan_t)]
     lib.qsel_cv_destroy.argtypes = [c_void_p]
     lib.qsel_cv_destroy.restype = None
+    lib.qsel_create_batch.argtypes = [P(c_void_p), c_int32, P(qsel_model), P(qsel_theta), P(qsel_partition),
+                                      P(c_int32), P(qsel_options), c_int32, c_int32]
+    lib.qsel_batch_run.argtypes = [c_void_p]
+    lib.qsel_batch_set_theta.argtypes = [c_void_p, c_int32, P(qsel_theta)]
+    lib.qsel_batch_diag_inv.argtypes = [c_void_p, c_int32, c_void_p, c_int32]
+    lib.qsel_batch_trace_grads.argtypes = [c_void_p, c_int32, P(c_double)]
+    lib.qsel_batch_stats.argtypes = [c_void_p, c_int32, P(qsel_stats_t)]
+    lib.qsel_batch_info.argtypes = [c_void_p, P(qsel_batch_info_t)]
+    lib.qsel_batch_tuning.argtypes = [c_void_p, c_int32, P(c_int32), P(c_int32), P(c_int32)]
+    lib.qsel_batch_last_error.argtypes = [c_void_p]
+    lib.qsel_batch_last_error.restype = c_char_p
+    lib.qsel_batch_destroy.argtypes = [c_void_p]
+    lib.qsel_batch_destroy.restype = None
     lib.qsel_last_error.argtypes = [c_void_p]
     lib.qsel_last_error.restype = c_char_p
     lib.qsel_destroy.argtypes = [c_void_p]
     lib.qsel_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("qsel_cv_destroy", "qsel_last_error", "qsel_destroy"):
+        if name not in ("qsel_cv_destroy", "qsel_last_error", "qsel_destroy", "qsel_batch_last_error",
+                        "qsel_batch_destroy"):
             getattr(lib, name).restype = c_int32
     _lib = lib
     return lib
@@ -355,6 +376,111 @@ def qsel_cv_plan(ctx: Context, cv: ControlVariate, target_rel_err: float, max_ov
     return {"n_samples": plan.n_samples, "feasible": bool(plan.feasible), "predicted_cost": plan.predicted_cost,
             "predicted_err": plan.predicted_err, "single_part_cost": plan.single_part_cost,
             "part_overlap": po, "part_pred_err": pe}
+
+
+class Batch:
+    """Owner of one qsel_batch* (independent models under one captured graph)."""
+
+    def __init__(self, handle, sizes):
+        self.handle = handle
+        self.sizes = sizes          # n of every model
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().qsel_batch_destroy(self.handle)
+            self.handle = None
+
+
+def _check_batch(status: int, b):
+    if status != 0:
+        msg = load_library().qsel_batch_last_error(b.handle if b is not None else None)
+        raise QselError(status, msg.decode() if msg else "")
+
+
+def qsel_create_batch(models, thetas, partitions, overlaps, n_samples=128, seed=0, precision=QSEL_MIXED,
+                      pcg_tol=1e-8, pcg_max_iter=20000, precond_block=0, tensor_passes=0, cuda_stream=None,
+                      n_streams=16, autotune=False) -> Batch:
+    """models: list of dicts with n_s, n_t, c_diag, g_rowptr, g_col, g_val,
+    obs_mask, sigma (host arrays); partitions: list of (n_parts, slab_start or
+    None); overlaps: list of ints."""
+    lib = load_library()
+    n = len(models)
+    keep = []
+    M = (qsel_model * n)()
+    for i, m in enumerate(models):
+        arrs = [np.ascontiguousarray(m["c_diag"], dtype=np.float64), np.ascontiguousarray(m["g_rowptr"], np.int32),
+                np.ascontiguousarray(m["g_col"], np.int32), np.ascontiguousarray(m["g_val"], np.float64),
+                np.ascontiguousarray(m["obs_mask"], np.uint8)]
+        keep += arrs
+        M[i] = qsel_model(int(m["n_s"]), int(m["n_t"]), _ptr(arrs[0], c_double), _ptr(arrs[1], c_int32),
+                          _ptr(arrs[2], c_int32), _ptr(arrs[3], c_double), _ptr(arrs[4], c_uint8),
+                          float(m["sigma"]))
+    TH = (qsel_theta * n)(*[qsel_theta(*[float(x) for x in th]) for th in thetas])
+    PA = (qsel_partition * n)()
+    for i, (n_parts, ss) in enumerate(partitions):
+        if ss is not None:
+            a = np.ascontiguousarray(ss, dtype=np.int32)
+            keep.append(a)
+            PA[i] = qsel_partition(int(n_parts), _ptr(a, c_int32))
+        else:
+            PA[i] = qsel_partition(int(n_parts), None)
+    OV = np.ascontiguousarray(overlaps, dtype=np.int32)
+    opt = qsel_options(int(n_samples), int(seed), int(precision), float(pcg_tol), int(pcg_max_iter),
+                       int(precond_block), 0, c_void_p(int(cuda_stream)) if cuda_stream else None, 0,
+                       int(tensor_passes), None)
+    h = c_void_p()
+    st = lib.qsel_create_batch(ctypes.byref(h), n, M, TH, PA, _ptr(OV, c_int32), ctypes.byref(opt),
+                               int(n_streams), int(bool(autotune)))
+    _check_batch(st, None)
+    return Batch(h, [int(m["n_s"]) * int(m["n_t"]) for m in models])
+
+
+def qsel_batch_run(b: Batch):
+    _check_batch(load_library().qsel_batch_run(b.handle), b)
+
+
+def qsel_batch_set_theta(b: Batch, model: int, theta):
+    th = qsel_theta(*[float(x) for x in theta])
+    _check_batch(load_library().qsel_batch_set_theta(b.handle, int(model), ctypes.byref(th)), b)
+
+
+def qsel_batch_diag_inv(b: Batch, model: int, out=None):
+    lib = load_library()
+    if out is None:
+        out = np.empty(b.sizes[model], dtype=np.float64)
+    if isinstance(out, np.ndarray):
+        _check_batch(lib.qsel_batch_diag_inv(b.handle, int(model), out.ctypes.data_as(c_void_p), 0), b)
+    else:
+        _check_batch(lib.qsel_batch_diag_inv(b.handle, int(model), c_void_p(out.data_ptr()), 1), b)
+    return out
+
+
+def qsel_batch_trace_grads(b: Batch, model: int) -> np.ndarray:
+    g = np.zeros(3, dtype=np.float64)
+    _check_batch(load_library().qsel_batch_trace_grads(b.handle, int(model), _ptr(g, c_double)), b)
+    return g
+
+
+def qsel_batch_stats(b: Batch, model: int) -> dict:
+    s = qsel_stats_t()
+    _check_batch(load_library().qsel_batch_stats(b.handle, int(model), ctypes.byref(s)), b)
+    return {name: getattr(s, name) for name, _ in qsel_stats_t._fields_}
+
+
+def qsel_batch_info(b: Batch) -> dict:
+    s = qsel_batch_info_t()
+    _check_batch(load_library().qsel_batch_info(b.handle, ctypes.byref(s)), b)
+    return {name: getattr(s, name) for name, _ in qsel_batch_info_t._fields_}
+
+
+def qsel_batch_tuning(b: Batch, model: int) -> dict:
+    pb, tp, st = c_int32(0), c_int32(0), c_int32(0)
+    _check_batch(load_library().qsel_batch_tuning(b.handle, int(model), ctypes.byref(pb), ctypes.byref(tp),
+                                                  ctypes.byref(st)), b)
+    return {"precond_block": pb.value, "tensor_passes": tp.value, "stream": st.value}
 
 
 def qsel_last_error(ctx: Context | None) -> str:

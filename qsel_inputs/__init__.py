@@ -23,7 +23,7 @@ import dataclasses
 import numpy as np
 
 __all__ = ["GridMesh", "grid_mesh", "obs_mask", "Workload", "workload", "WORKLOADS",
-           "seeded_normal", "balanced_slab_start"]
+           "seeded_normal", "balanced_slab_start", "BatchModel", "uneven_batch"]
 
 
 @dataclasses.dataclass(frozen=True)
@@ -158,3 +158,47 @@ WORKLOADS = {
 
 def workload(name: str) -> Workload:
     return WORKLOADS[name]
+
+
+@dataclasses.dataclass(frozen=True)
+class BatchModel:
+    """One model of the uneven batch: grid side, slabs, parts, theta, seed."""
+    m: int
+    n_t: int
+    n_parts: int
+    theta: tuple
+    seed: int
+    overlap: int = 1
+    obs_frac: float = 0.25
+    sigma: float = 0.5
+
+    @property
+    def n_s(self) -> int:
+        return self.m * self.m
+
+    @property
+    def n(self) -> int:
+        return self.n_s * self.n_t
+
+    def mask(self) -> np.ndarray:
+        return obs_mask(self.n, self.obs_frac, self.seed)
+
+
+def uneven_batch(n_models: int = 64, base_seed: int = 1000) -> list:
+    """Independent models of uneven size: model i draws, from a generator
+    seeded with base_seed + i, the grid side m uniformly from {16, 24, ..., 64},
+    n_t uniformly from [8, 128], n_parts uniformly from
+    [2, min(8, n_t // (2 overlap + 1))] with overlap 1, and theta with
+    log kappa ~ U[-3, 0], log tau ~ U[-1, 1], rho ~ U[0.5, 0.99];
+    25 % observed, sigma = 0.5."""
+    out = []
+    for i in range(n_models):
+        rng = np.random.Generator(np.random.Philox(base_seed + i))
+        m = int(rng.choice(np.arange(16, 65, 8)))
+        n_t = int(rng.integers(8, 129))
+        n_p = int(rng.integers(2, min(8, n_t // 3) + 1))
+        lk = float(rng.uniform(-3.0, 0.0))
+        lt = float(rng.uniform(-1.0, 1.0))
+        rho = float(rng.uniform(0.5, 0.99))
+        out.append(BatchModel(m, n_t, n_p, (lk, lt, float(np.log(rho / (1.0 - rho)))), base_seed + i))
+    return out
