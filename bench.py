@@ -152,6 +152,21 @@ def measured_peaks():
         return 6800.0, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
 
 
+def tf32_peak_tflops():
+    """Dense TF32 tensor peak for kernels timed inside a seconds-long step: the
+    measured sustained bf16 peak times the nominal TF32 / bf16 ratio
+    (1.1 / 2.25 PFLOP/s)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        bf16 = float(d["bf16_tflops_sustained"])
+        return bf16 * 1.1 / 2.25, (f"measured sustained bf16 {bf16:.0f} TFLOP/s x nominal TF32/bf16 ratio "
+                                   "1.1/2.25")
+    except (OSError, KeyError, ValueError):
+        return 1700.0 * 1.1 / 2.25, "fallback sustained bf16 1.7 PFLOP/s x nominal TF32/bf16 ratio 1.1/2.25"
+
+
 def workload_inputs(w, rank=0):
     mesh = w.mesh()
     mask = w.mask()
@@ -414,32 +429,49 @@ def run_native(args):
             dist.destroy_process_group()
         return
 
-    # dominant kernel class of the timed form (by event time)
-    tot = {k: sum(s[k] for s in stats) for k in ("gemm_ms", "gemm_flop", "gemm_launches", "sweep_ms",
-                                                 "sweep_flop", "sweep_launches", "spmm_ms", "spmm_bytes",
-                                                 "spmm_launches")}
+    # dominant kernel class of the timed form (by event time), among the
+    # classes with a defined algorithmic work
+    classes = qsel.PROF_CLASSES
+    cms = [sum(s["class_ms"][q] for s in stats) for q in range(len(classes))]
+    cwork = [sum(s["class_work"][q] for s in stats) for q in range(len(classes))]
+    claunch = [sum(s["class_launches"][q] for s in stats) for q in range(len(classes))]
     hbm_peak, hbm_src = measured_peaks()
-    alu_peak = FP64_PEAK_TFLOPS if chosen_prec == qsel.QSEL_FP64 else FP32_PEAK_TFLOPS
-    alu_src = ("nominal FP64 rate (152 SMs x 2.07 GHz x 4 FLOP/clk); FMA-loop probe 1.19 TFLOP/s"
-               if chosen_prec == qsel.QSEL_FP64 else
-               "FP32 CUDA-core rate from unit counts (152 x 128 x 2 x 2.07 GHz); FMA-loop probe 69.6 TFLOP/s")
-    cands = {"gemm": tot["gemm_ms"], "sweep": tot["sweep_ms"], "spmm": tot["spmm_ms"]}
-    dom = max(cands, key=cands.get)
-    if dom == "spmm":
-        ach = tot["spmm_bytes"] / (tot["spmm_ms"] * 1e-3) / 1e9
-        roof = {"kernel": "k_bt_spmm (block-tridiagonal sliced-ELL SpMM, PCG)", "bound": "hbm", "achieved": ach,
-                "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
-                "peak_source": hbm_src}
+    mixed = chosen_prec == qsel.QSEL_MIXED
+    tf32_peak, tf32_src = tf32_peak_tflops()
+    desc = {
+        "gemm": ("dense tile GEMMs (tcgen05 3xTF32, TMA, TMEM)" if mixed else "k_gemm64 (FP64 dense tile GEMM)"),
+        "sweep_update": ("sweep rank-64 updates (tcgen05 3xTF32)" if mixed else "k_sweep_update (FP64)"),
+        "spmm": "k_bt_spmm (block-tridiagonal sliced-ELL SpMM, PCG)",
+        "pivot": "k_sweep_pivot (64x64 FP64 pivot-tile inverses)",
+        "precond": "k_pcg_precond (block-Jacobi apply, register-tiled)",
+    }
+    cand = [q for q, name in enumerate(classes) if name in desc and cwork[q] > 0 and cms[q] > 0]
+    dom = max(cand, key=lambda q: cms[q])
+    name = classes[dom]
+    per_launch_ms = cms[dom] / max(1, claunch[dom])
+    if name == "spmm":
+        ach = cwork[dom] / (cms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "peak_source": hbm_src}
+    elif name in ("gemm", "sweep_update") and mixed:
+        # 3xTF32: three TF32 MMAs per useful product
+        ach = 3.0 * cwork[dom] / (cms[dom] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
+                "peak_source": tf32_src + "; achieved counts the three TF32 products of each 3xTF32 product"}
+    elif name == "pivot" or not mixed:
+        ach = cwork[dom] / (cms[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "nominal FP64 rate (152 SMs x 2.07 GHz x 4 FLOP/clk); FMA-loop probe 1.19 TFLOP/s"}
     else:
-        key = "gemm" if dom == "gemm" else "sweep"
-        ach = tot[f"{key}_flop"] / (tot[f"{key}_ms"] * 1e-3) / 1e12
-        traffic = None
-        if key == "gemm" and chosen_prec == qsel.QSEL_FP64 and tot["gemm_launches"]:
-            traffic = GEMM64_DRAM_BYTES_PER_FLOP * tot["gemm_flop"] / tot["gemm_launches"]
-        roof = {"kernel": "k_gemm64 (dense tile GEMM)" if key == "gemm" else "k_sweep_update (blocked sweep)",
-                "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
-                "traffic": traffic, "peak_source": alu_src}
-    roof["kernels_ms_per_step"] = {k: v / args.steps for k, v in cands.items()}
+        ach = cwork[dom] / (cms[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "FP32 CUDA-core rate from unit counts (152 x 128 x 2 x 2.07 GHz); "
+                               "FMA-loop probe 69.6 TFLOP/s"}
+    traffic = None
+    if name == "gemm" and not mixed and claunch[dom]:
+        traffic = GEMM64_DRAM_BYTES_PER_FLOP * cwork[dom] / claunch[dom]
+    roof = {"kernel": desc[name], **roof, "frac": roof["achieved"] / roof["peak"], "traffic": traffic,
+            "launches": int(claunch[dom]), "avg_launch_ms": per_launch_ms}
+    roof["kernel_classes_ms_per_step"] = {classes[q]: cms[q] / args.steps for q in range(len(classes))}
     st = stats[-1]
 
     accuracy = None

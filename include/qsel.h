@@ -129,6 +129,8 @@ typedef struct {
                              (qsel_cv_plan) extend each subdomain differently. */
 } qsel_options;
 
+#define QSEL_PROF_CLASSES 11
+
 /* Per-call statistics of the last qsel_diag_inv. */
 typedef struct {
   int32_t pcg_iterations;     /* iterations until every column met pcg_tol         */
@@ -149,6 +151,17 @@ typedef struct {
   int64_t sweep_launches;
   double spmm_ms, spmm_bytes;
   int64_t spmm_launches;
+  /* With profile_kernels: event time (ms) and launches per kernel class:
+   * 0 dense tile GEMMs, 1 sweep rank-64 updates, 2 SpMM, 3 pivot-tile
+   * inverses (FP64), 4 sweep panels / write-back / mirror, 5 Schur assembly,
+   * 6 sparse row and column gathers, 7 block-Jacobi apply, 8 other PCG and
+   * refinement vector kernels, 9 RB correction terms, 10 diagonal and pattern
+   * extraction.  Kernels outside these classes are not timed.  class_work is
+   * the algorithmic work where defined (FLOPs for 0, 1, 3, 7; bytes for 2),
+   * else 0. */
+  double class_ms[QSEL_PROF_CLASSES];
+  int64_t class_launches[QSEL_PROF_CLASSES];
+  double class_work[QSEL_PROF_CLASSES];
 } qsel_stats_t;
 
 /*

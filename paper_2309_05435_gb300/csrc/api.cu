@@ -1215,8 +1215,9 @@ static Err run_pipeline(qsel_ctx *c) {
   Err e = run_pipeline_body(c);
   g_prof = nullptr;
   if (e.code == 0 && c->opt.profile_kernels) {
-    double ms[PROF_KINDS] = {0, 0, 0}, work[PROF_KINDS] = {0, 0, 0};
-    int64_t cnt[PROF_KINDS] = {0, 0, 0};
+    static_assert(PROF_KINDS == QSEL_PROF_CLASSES, "profiler classes");
+    double ms[PROF_KINDS] = {}, work[PROF_KINDS] = {};
+    int64_t cnt[PROF_KINDS] = {};
     for (auto &r : c->prof.recs) {
       float t = 0.f;
       cudaEventElapsedTime(&t, r.a, r.b);
@@ -1233,6 +1234,11 @@ static Err run_pipeline(qsel_ctx *c) {
     c->stats.spmm_ms = ms[PROF_SPMM];
     c->stats.spmm_bytes = work[PROF_SPMM];
     c->stats.spmm_launches = cnt[PROF_SPMM];
+    for (int q = 0; q < PROF_KINDS; ++q) {
+      c->stats.class_ms[q] = ms[q];
+      c->stats.class_launches[q] = cnt[q];
+      c->stats.class_work[q] = work[q];
+    }
   }
   return e;
 }
@@ -1821,30 +1827,32 @@ qsel_status qsel_create_batch(qsel_batch **out, int32_t n_models, const qsel_mod
     }
     std::map<int, std::array<int, 2>> best;
     for (auto &kv : rep) {
+      // one context per size (block-Jacobi storage for the largest block);
+      // the candidates switch its block size and dense path between runs
       const int i = kv.second;
+      qsel_options o = *opt;
+      o.precond_block = 64;
+      o.tensor_passes = cands[0][1];
+      o.seed = opt->seed + (uint64_t)i;
+      qsel_ctx *t = nullptr;
+      qsel_status st = create_ctx(&t, &models[i], &thetas[i], &partitions[i], overlaps[i], &o, kBatchSlots);
+      if (st) return bail(st, "autotune: " + g_create_error);
+      Err e = run_pipeline(t);                       // warm-up
       double best_ms = 1e300;
       for (auto cd : cands) {
-        qsel_options o = *opt;
-        o.precond_block = cd[0];
-        o.tensor_passes = cd[1];
-        o.seed = opt->seed + (uint64_t)i;
-        qsel_ctx *t = nullptr;
-        qsel_status st = create_ctx(&t, &models[i], &thetas[i], &partitions[i], overlaps[i], &o, kBatchSlots);
-        if (st) return bail(st, "autotune: " + g_create_error);
-        double ms = 0.0;
-        Err e = run_pipeline(t);                     // warm-up
-        for (int r = 0; r < 2 && e.code == 0; ++r) {
-          t->computed = false;
-          e = run_pipeline(t);
-          ms += t->stats.ms_total;
-        }
-        qsel_destroy(t);
-        if (e.code) return bail((qsel_status)e.code, "autotune: " + e.msg);
-        if (ms < best_ms) {
+        if (e.code) break;
+        t->bsize = cd[0];
+        if (t->mixed) t->tc_passes = cd[1] > 0 ? cd[1] : 0;
+        t->computed = false;
+        e = run_pipeline(t);
+        const double ms = t->stats.ms_total;
+        if (e.code == 0 && ms < best_ms) {
           best_ms = ms;
           best[kv.first] = cd;
         }
       }
+      qsel_destroy(t);
+      if (e.code) return bail((qsel_status)e.code, "autotune: " + e.msg);
     }
     for (int i = 0; i < n_models; ++i) b->tuned[i] = best[models[i].n_s];
     b->ms_autotune = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();

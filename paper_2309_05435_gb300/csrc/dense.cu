@@ -375,8 +375,14 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
       }
       for (int k = 0; k < nt; ++k) {
         g_launch_count += 3;
-        k_sweep_pivot<T><<<b.count, 256, 0, s>>>(b, k, n_pad, err_flag);
-        k_sweep_panel_tc<T><<<dim3(nt, b.count), 256, 0, s>>>(b, k, n_pad);
+        {
+          ProfScope ps_(s, PROF_PIVOT, 2.0 * 64.0 * 64.0 * 64.0 * b.count);
+          k_sweep_pivot<T><<<b.count, 256, 0, s>>>(b, k, n_pad, err_flag);
+        }
+        {
+          ProfScope ps_(s, PROF_PANEL);
+          k_sweep_panel_tc<T><<<dim3(nt, b.count), 256, 0, s>>>(b, k, n_pad);
+        }
         Profiler::Rec rec{PROF_SWEEP, nullptr, nullptr, 0.0};
         if (g_prof) {
           rec.work = 2.0 * 64.0 * 64.0 * 64.0 * ((double)n_lower - nt) * b.count;
@@ -388,17 +394,29 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
         launch_tc_gemm(s, gb, n_pad, n_pad, 64, 64, 64, n_pad, true, tc_passes, err_flag);
         g_prof = saved;
         if (prof) g_prof->end(s, rec);
-        k_sweep_panel_write<T><<<dim3(nt, b.count), 256, 0, s>>>(b, k, n_pad);
+        {
+          ProfScope ps_(s, PROF_PANEL);
+          k_sweep_panel_write<T><<<dim3(nt, b.count), 256, 0, s>>>(b, k, n_pad);
+        }
       }
       ++g_launch_count;
-      k_sweep_mirror<T><<<dim3(n_lower, b.count), 256, 0, s>>>(b, n_pad, -1.0);
+      {
+        ProfScope ps_(s, PROF_PANEL);
+        k_sweep_mirror<T><<<dim3(n_lower, b.count), 256, 0, s>>>(b, n_pad, -1.0);
+      }
       return;
     }
   }
   for (int k = 0; k < nt; ++k) {
     g_launch_count += 3;
-    k_sweep_pivot<T><<<b.count, 256, 0, s>>>(b, k, n_pad, err_flag);
-    if (nt > 1) k_sweep_panel<T><<<dim3(nt - 1, b.count), 256, 0, s>>>(b, k, n_pad);
+    {
+      ProfScope ps_(s, PROF_PIVOT, 2.0 * 64.0 * 64.0 * 64.0 * b.count);
+      k_sweep_pivot<T><<<b.count, 256, 0, s>>>(b, k, n_pad, err_flag);
+    }
+    {
+      ProfScope ps_(s, PROF_PANEL);
+      if (nt > 1) k_sweep_panel<T><<<dim3(nt - 1, b.count), 256, 0, s>>>(b, k, n_pad);
+    }
     Profiler::Rec rec{PROF_SWEEP, nullptr, nullptr, 0.0};
     if (g_prof) {
       // rank-64 update of the lower tiles off row/column k: 2 * 64^3 FLOPs each
@@ -410,7 +428,10 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
     if (g_prof) g_prof->end(s, rec);
   }
   ++g_launch_count;
-  k_sweep_mirror<T><<<dim3(n_lower, b.count), 256, 0, s>>>(b, n_pad, -1.0);
+  {
+    ProfScope ps_(s, PROF_PANEL);
+    k_sweep_mirror<T><<<dim3(n_lower, b.count), 256, 0, s>>>(b, n_pad, -1.0);
+  }
 }
 template void spd_inverse<double>(cudaStream_t, const SweepBatch<double> &, int, int32_t *, int);
 template void spd_inverse<float>(cudaStream_t, const SweepBatch<float> &, int, int32_t *, int);
@@ -420,7 +441,10 @@ void launch_mirror(cudaStream_t s, const SweepBatch<T> &b, int n_pad) {
   if (b.count <= 0) return;
   const int nt = n_pad / 64;
   ++g_launch_count;
-  k_sweep_mirror<T><<<dim3(nt * (nt + 1) / 2, b.count), 256, 0, s>>>(b, n_pad, 1.0);
+  {
+    ProfScope ps_(s, PROF_PANEL);
+    k_sweep_mirror<T><<<dim3(nt * (nt + 1) / 2, b.count), 256, 0, s>>>(b, n_pad, 1.0);
+  }
 }
 template void launch_mirror<double>(cudaStream_t, const SweepBatch<double> &, int);
 template void launch_mirror<float>(cudaStream_t, const SweepBatch<float> &, int);
@@ -475,7 +499,10 @@ void launch_sp_rowgather(cudaStream_t s, const SpBatch<TI, TO> &b, const SellPat
   int64_t items = (int64_t)n_pad * (ncol / 64);
   int grid = (int)((items + 7) / 8);
   if (grid > 152 * 8) grid = 152 * 8;
-  k_sp_rowgather<TI, TO><<<dim3(grid, b.count), 256, 0, s>>>(b, pat, val, n_s, n_pad, ncol, ldb, ldo);
+  {
+    ProfScope ps_(s, PROF_GATHER);
+    k_sp_rowgather<TI, TO><<<dim3(grid, b.count), 256, 0, s>>>(b, pat, val, n_s, n_pad, ncol, ldb, ldo);
+  }
 }
 template void launch_sp_rowgather<double, double>(cudaStream_t, const SpBatch<double, double> &,
                                                   const SellPattern &, const double *, int, int, int, int, int);
@@ -519,7 +546,10 @@ void launch_sp_colgather(cudaStream_t s, const SpBatch<T, T> &b, const SellPatte
   if (b.count <= 0) return;
   ++g_launch_count;
   dim3 grid((n_pad + 255) / 256, n_pad, b.count);
-  k_sp_colgather<T><<<grid, 256, 0, s>>>(b, pat, val, n_s, n_pad);
+  {
+    ProfScope ps_(s, PROF_GATHER);
+    k_sp_colgather<T><<<grid, 256, 0, s>>>(b, pat, val, n_s, n_pad);
+  }
 }
 template void launch_sp_colgather<double>(cudaStream_t, const SpBatch<double, double> &, const SellPattern &,
                                           const double *, int, int);
@@ -547,7 +577,10 @@ template <typename T>
 void launch_diag64_rows(cudaStream_t s, const DiagRowBatch<T> &b, int n_s, int n_pad) {
   if (b.count <= 0) return;
   ++g_launch_count;
-  k_diag64_rows<T><<<dim3((n_s + 7) / 8, b.count), 256, 0, s>>>(b, n_s, n_pad);
+  {
+    ProfScope ps_(s, PROF_EXTRACT);
+    k_diag64_rows<T><<<dim3((n_s + 7) / 8, b.count), 256, 0, s>>>(b, n_s, n_pad);
+  }
 }
 template void launch_diag64_rows<double>(cudaStream_t, const DiagRowBatch<double> &, int, int);
 template void launch_diag64_rows<float>(cudaStream_t, const DiagRowBatch<float> &, int, int);
@@ -594,7 +627,10 @@ void launch_schur_assemble(cudaStream_t s, const SchurBatch<T> &b, const SellPat
   if (b.count <= 0) return;
   ++g_launch_count;
   dim3 grid((n_pad + 255) / 256, n_pad, b.count);
-  k_schur_assemble<T><<<grid, 256, 0, s>>>(b, pat, qs, obs_w, n_s, n_pad);
+  {
+    ProfScope ps_(s, PROF_SCHUR);
+    k_schur_assemble<T><<<grid, 256, 0, s>>>(b, pat, qs, obs_w, n_s, n_pad);
+  }
 }
 template void launch_schur_assemble<double>(cudaStream_t, const SchurBatch<double> &, const SellPattern &,
                                             const double *, double, int, int);
@@ -685,10 +721,16 @@ void launch_extract(cudaStream_t s, const ExtractBatch<T> &b, const SellPattern 
   for (int q = 0; q < b.count; ++q) any_d0 |= (b.e[q].D0 != nullptr);
   if (any_d0) {
     ++g_launch_count;
-    k_diag64<T><<<dim3((n_s + 255) / 256, kDiagChunks, b.count), 256, 0, s>>>(b, n_s, n_pad, diag_scratch);
+    {
+      ProfScope ps_(s, PROF_EXTRACT);
+      k_diag64<T><<<dim3((n_s + 255) / 256, kDiagChunks, b.count), 256, 0, s>>>(b, n_s, n_pad, diag_scratch);
+    }
   }
   ++g_launch_count;
-  k_extract<T><<<b.count, 1024, 0, s>>>(b, pat, qs, dqs, n_s, n_pad, diag_scratch);
+  {
+    ProfScope ps_(s, PROF_EXTRACT);
+    k_extract<T><<<b.count, 1024, 0, s>>>(b, pat, qs, dqs, n_s, n_pad, diag_scratch);
+  }
 }
 template void launch_extract<double>(cudaStream_t, const ExtractBatch<double> &, const SellPattern &,
                                      const double *, const double *, int, int, double *);

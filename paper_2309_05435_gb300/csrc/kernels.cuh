@@ -18,7 +18,20 @@ extern thread_local int64_t g_launch_count;
 // Opt-in per-launch timing of the hot kernels: CUDA events recorded on the
 // launching stream around each launch, with the algorithmic work of the launch
 // (FLOPs or bytes).  Read back after the pipeline has synchronised.
-enum ProfKind { PROF_GEMM = 0, PROF_SWEEP = 1, PROF_SPMM = 2, PROF_KINDS = 3 };
+enum ProfKind {
+  PROF_GEMM = 0,      // dense tile GEMMs (CUDA-core and tcgen05)
+  PROF_SWEEP = 1,     // rank-64 updates of the blocked sweep
+  PROF_SPMM = 2,      // block-tridiagonal SpMM
+  PROF_PIVOT = 3,     // 64x64 pivot-tile inverses (FP64)
+  PROF_PANEL = 4,     // sweep panels, panel write-back, mirror
+  PROF_SCHUR = 5,     // Schur assembly of the pivot blocks
+  PROF_GATHER = 6,    // sparse row / column gathers
+  PROF_PRECOND = 7,   // block-Jacobi apply with the PCG dots
+  PROF_PCGVEC = 8,    // PCG axpy, direction update, reductions, refinement
+  PROF_CORR = 9,      // RB correction terms
+  PROF_EXTRACT = 10,  // diagonal and pattern extraction of Sigma blocks
+  PROF_KINDS = 11
+};
 struct Profiler {
   struct Rec {
     int kind;
@@ -54,6 +67,18 @@ struct Profiler {
   }
 };
 extern thread_local Profiler *g_prof;
+// Times the launches issued during its lifetime as one record of `kind`.
+struct ProfScope {
+  Profiler::Rec rec;
+  cudaStream_t s;
+  Profiler *p;
+  ProfScope(cudaStream_t s_, int kind, double work = 0.0) : rec{kind, nullptr, nullptr, work}, s(s_), p(g_prof) {
+    if (p) p->begin(s, rec);
+  }
+  ~ProfScope() {
+    if (p) p->end(s, rec);
+  }
+};
 
 // Message returned by qsel_last_error(NULL) for calls without a context.
 void set_context_free_error(const std::string &msg);

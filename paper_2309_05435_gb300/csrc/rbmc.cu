@@ -103,6 +103,7 @@ void launch_correction_terms(cudaStream_t s, const CorrBatch<T> &b, const SellPa
                              const double *r0, const double *r1, int n_s, int n_pad, int ld, int k) {
   if (b.count <= 0) return;
   ++g_launch_count;
+  ProfScope ps_(s, PROF_CORR);
   k_correction_terms<T><<<dim3(kCorrGrid, b.count), 256, 0, s>>>(b, pat, qs, dqs, a0, a1, r0, r1, n_s,
                                                                  n_pad, ld, k);
 }

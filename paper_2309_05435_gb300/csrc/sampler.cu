@@ -354,11 +354,6 @@ template void launch_jacobi_setup<float>(cudaStream_t, const SellPattern &, cons
 // PCG update for a 64-row tile: x += alpha p, r -= alpha q, z = P r (block
 // Jacobi), and per-column partial sums <r, z>, <r, r> in double.
 // ---------------------------------------------------------------------------
-template <typename T>
-constexpr int pcg_update_smem() {
-  return (64 * 65 + 64 * 64) * (int)sizeof(T) + 2 * 4 * 64 * (int)sizeof(double);
-}
-
 constexpr int kUpdGrid = 152 * 4;
 
 int pcg_update_grid(int n) {
@@ -405,108 +400,170 @@ __global__ void __launch_bounds__(256) k_pcg_axpy(PcgVec<T> v) {
   }
 }
 
-// z = P r for 64-row tiles (block Jacobi, P blocks transposed in shared
-// memory, 16 rows per thread) and per-column partial sums <r, z>, <r, r>.
-template <typename T>
-__global__ void __launch_bounds__(256) k_pcg_update(PcgVec<T> v, const T *__restrict__ pblk, int b) {
-  extern __shared__ __align__(16) unsigned char smem_upd_raw[];
-  double *red_a = reinterpret_cast<double *>(smem_upd_raw);     // [4][64]
-  double *red_b = red_a + 4 * 64;                               // [4][64]
-  T *rs = reinterpret_cast<T *>(red_b + 4 * 64);                // [64][65]
-  T *Ps = rs + 64 * 65;                                         // [64 * b]
+// z = P r for 64-row tiles (block Jacobi) and per-column partial sums
+// <r, z>, <r, r>.  Per tile the P blocks are staged once in shared memory,
+// transposed (Pt[j][row]); then for every chunk of CW columns the r tile is
+// staged and each thread accumulates an 8-row x (CW/32)-column register tile:
+// per j two 16-byte loads of P (warp broadcast) and one of r feed
+// 8 x (CW/32) FMAs.  Rows of one 8-row group lie in one block (b >= 8).
+template <typename T, int CW>
+struct PrecondSmem {
+  static constexpr int PS = 64 + 16 / (int)sizeof(T);        // Pt row stride (elements)
+  static constexpr int RS = CW + 16 / (int)sizeof(T);        // r tile row stride
+  static constexpr int bytes = (64 * PS + 64 * RS) * (int)sizeof(T) + 2 * 8 * CW * 8 + 2 * 512 * 8;
+};
+
+template <typename T, int CW>
+__global__ void __launch_bounds__(256) k_pcg_precond(PcgVec<T> v, const T *__restrict__ pblk, int b) {
+  using SM = PrecondSmem<T, CW>;
+  constexpr int NC = CW / 32;                                  // columns per thread
+  using VC = typename std::conditional<NC * sizeof(T) == 16, typename std::conditional<std::is_same<T, float>::value, float4, double2>::type,
+                                       typename std::conditional<std::is_same<T, float>::value, float2, double>::type>::type;
+  using V16 = typename std::conditional<std::is_same<T, float>::value, float4, double2>::type;
+  constexpr int E16 = 16 / (int)sizeof(T);
+  extern __shared__ __align__(16) unsigned char smem_pc_raw[];
+  T *Pt = reinterpret_cast<T *>(smem_pc_raw);                  // [64][PS]
+  T *rsm = Pt + 64 * SM::PS;                                   // [64][RS]
+  double *red = reinterpret_cast<double *>(rsm + 64 * SM::RS); // [2][8][CW]
+  double *acc = red + 2 * 8 * CW;                              // [2][512]
+  const int tid = threadIdx.x, rg = tid >> 5, cg = tid & 31;
   const int n_blocks = (v.n + b - 1) / b;
   const int n_tiles = (v.n + 63) / 64;
-  const int lc = threadIdx.x & 63, rg = threadIdx.x >> 6;
-  for (int c0 = 0; c0 < v.ld; c0 += 64) {
-    const int col = c0 + lc;
-    T sa = T(0), sb = T(0);
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-      const int r0 = tile * 64;
-      const int rows = min(64, v.n - r0);
+  for (int c = tid; c < v.ld; c += blockDim.x) {
+    acc[c] = 0.0;
+    acc[512 + c] = 0.0;
+  }
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int r0 = tile * 64;
+    const int rows = min(64, v.n - r0);
+    __syncthreads();
+    {
+      const int64_t base = (int64_t)(r0 / b) * b * b;
+      const int64_t lim = (int64_t)n_blocks * b * b;
+      for (int e = tid; e < 64 * b; e += blockDim.x) {
+        const int blk = e / (b * b), rem = e - blk * b * b;
+        const int r = rem / b, j = rem - r * b;
+        Pt[(blk * b + j) * SM::PS + blk * b + r] = (base + e < lim) ? pblk[base + e] : T(0);
+      }
+    }
+    for (int c0 = 0; c0 < v.ld; c0 += CW) {
       __syncthreads();
-      {
-        // P blocks of this tile, transposed: Ps[blk][j][r] = P_blk[r][j]
-        const int64_t base = (int64_t)(r0 / b) * b * b;
-        const int64_t lim = (int64_t)n_blocks * b * b;
-        for (int e = threadIdx.x; e < 64 * b; e += blockDim.x) {
-          const int blk = e / (b * b), rem = e - blk * b * b;
-          const int r = rem / b, j = rem - r * b;
-          Ps[blk * b * b + j * b + r] = (base + e < lim) ? pblk[base + e] : T(0);
-        }
-        T rv[16];
+      // stage r[r0 .. r0+63][c0 .. c0+CW) with 16-byte loads
+      for (int e = tid; e < 64 * CW / E16; e += blockDim.x) {
+        const int rr = e / (CW / E16), q = e - rr * (CW / E16);
+        V16 val;
+        if (rr < rows) {
+          val = *reinterpret_cast<const V16 *>(v.r + (int64_t)(r0 + rr) * v.ld + c0 + q * E16);
+        } else {
+          T *z = reinterpret_cast<T *>(&val);
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-          const int rr = rg + 4 * m;
-          rv[m] = (rr < rows) ? v.r[(int64_t)(r0 + rr) * v.ld + col] : T(0);
+          for (int u = 0; u < E16; ++u) z[u] = T(0);
         }
-#pragma unroll
-        for (int m = 0; m < 16; ++m) rs[(rg + 4 * m) * 65 + lc] = rv[m];
+        *reinterpret_cast<V16 *>(rsm + rr * SM::RS + q * E16) = val;
       }
       __syncthreads();
-      if (b >= 16) {
-        // thread rows rg*16 .. rg*16+15 lie in one block: 16 accumulators
-        const int rbase = rg * 16;
-        const int blk = rbase / b, bo = rbase - blk * b;
-        const T *Pt = Ps + blk * b * b + bo;
-        const T *rcol = rs + (blk * b) * 65 + lc;
-        T z[16];
+      const int row0 = rg * 8;
+      T z[8][NC];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) z[q] = T(0);
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int q = 0; q < NC; ++q) z[a][q] = T(0);
+      if (b >= 8) {
+        const int jb = (row0 / b) * b;
         for (int jj = 0; jj < b; ++jj) {
-          const T rj = rcol[jj * 65];
-          const T *pj = Pt + jj * b;
+          const int jl = jb + jj;
+          T pv[8];
+          const V16 *pp = reinterpret_cast<const V16 *>(Pt + jl * SM::PS + row0);
 #pragma unroll
-          for (int q = 0; q < 16; ++q) z[q] = fma(pj[q], rj, z[q]);
-        }
+          for (int u = 0; u < 8 / E16; ++u) {
+            const V16 t4 = pp[u];
+            const T *ts = reinterpret_cast<const T *>(&t4);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int rr = rbase + q;
-          if (rr < rows) {
-            v.z[(int64_t)(r0 + rr) * v.ld + col] = z[q];
-            const T rd = rs[rr * 65 + lc];
-            sa = fma(rd, z[q], sa);
-            sb = fma(rd, rd, sb);
+            for (int w = 0; w < E16; ++w) pv[u * E16 + w] = ts[w];
           }
+          const VC rv = *reinterpret_cast<const VC *>(rsm + jl * SM::RS + cg * NC);
+          const T *rs = reinterpret_cast<const T *>(&rv);
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int q = 0; q < NC; ++q) z[a][q] = fma(pv[a], rs[q], z[a][q]);
         }
       } else {
-        for (int rr = rg; rr < rows; rr += 4) {
-          const int blk = rr / b, bo = rr - blk * b;
-          const T *Pt = Ps + blk * b * b + bo;
-          const int rb = blk * b;
-          T z = T(0);
-          for (int jj = 0; jj < b; ++jj) z = fma(Pt[jj * b], rs[(rb + jj) * 65 + lc], z);
-          v.z[(int64_t)(r0 + rr) * v.ld + col] = z;
-          const T rd = rs[rr * 65 + lc];
-          sa = fma(rd, z, sa);
-          sb = fma(rd, rd, sb);
+        // b == 1: Jacobi, P holds the inverse diagonal
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const int rl = row0 + a;
+          const T d = Pt[rl * SM::PS + rl];
+#pragma unroll
+          for (int q = 0; q < NC; ++q) z[a][q] = d * rsm[rl * SM::RS + cg * NC + q];
         }
       }
+      T sa[NC], sb[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) sa[q] = sb[q] = T(0);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int rl = row0 + a;
+        if (rl < rows) {
+          VC out;
+          T *os = reinterpret_cast<T *>(&out);
+#pragma unroll
+          for (int q = 0; q < NC; ++q) {
+            os[q] = z[a][q];
+            const T rd = rsm[rl * SM::RS + cg * NC + q];
+            sa[q] = fma(rd, z[a][q], sa[q]);
+            sb[q] = fma(rd, rd, sb[q]);
+          }
+          *reinterpret_cast<VC *>(v.z + (int64_t)(r0 + rl) * v.ld + c0 + cg * NC) = out;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        red[rg * CW + cg * NC + q] = (double)sa[q];
+        red[8 * CW + rg * CW + cg * NC + q] = (double)sb[q];
+      }
+      __syncthreads();
+      for (int c = tid; c < 2 * CW; c += blockDim.x) {
+        const int which = c / CW, cc = c - which * CW;
+        double s2 = 0.0;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) s2 += red[which * 8 * CW + g * CW + cc];
+        acc[which * 512 + c0 + cc] += s2;
+      }
     }
-    red_a[rg * 64 + lc] = (double)sa;
-    red_b[rg * 64 + lc] = (double)sb;
-    __syncthreads();
-    if (rg == 0) {
-      v.partial_a[(int64_t)blockIdx.x * v.ld + col] =
-          red_a[lc] + red_a[64 + lc] + red_a[128 + lc] + red_a[192 + lc];
-      v.partial_b[(int64_t)blockIdx.x * v.ld + col] =
-          red_b[lc] + red_b[64 + lc] + red_b[128 + lc] + red_b[192 + lc];
-    }
-    __syncthreads();
+  }
+  __syncthreads();
+  for (int c = tid; c < v.ld; c += blockDim.x) {
+    v.partial_a[(int64_t)blockIdx.x * v.ld + c] = acc[c];
+    v.partial_b[(int64_t)blockIdx.x * v.ld + c] = acc[512 + c];
   }
 }
 
 template <typename T>
 void launch_pcg_update(cudaStream_t s, const PcgVec<T> &v, const T *pblk, int bsize) {
+  // 128-column chunks for FP32 when they divide ld, else 64
+  constexpr int CWF = std::is_same<T, float>::value ? 128 : 64;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_pcg_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, pcg_update_smem<T>());
+    cudaFuncSetAttribute(k_pcg_precond<T, CWF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         PrecondSmem<T, CWF>::bytes);
+    cudaFuncSetAttribute(k_pcg_precond<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         PrecondSmem<T, 64>::bytes);
     attr_set = true;
   }
   g_launch_count += 2;
   const int64_t vec = (int64_t)v.n * v.ld / (16 / (int)sizeof(T));
   const int grid = (int)std::min<int64_t>((vec + 255) / 256, 152 * 8);
-  k_pcg_axpy<T><<<grid, 256, 0, s>>>(v);
-  k_pcg_update<T><<<v.n_tiles, 256, pcg_update_smem<T>(), s>>>(v, pblk, bsize);  // n_tiles = grid
+  {
+    ProfScope ps_(s, PROF_PCGVEC);
+    k_pcg_axpy<T><<<grid, 256, 0, s>>>(v);
+  }
+  // algorithmic work: 2 b FLOPs per element of z (b = 1: one multiply)
+  ProfScope ps_(s, PROF_PRECOND, (bsize > 1 ? 2.0 * bsize : 1.0) * (double)v.n * v.ld);
+  if (v.ld % CWF == 0)
+    k_pcg_precond<T, CWF><<<v.n_tiles, 256, PrecondSmem<T, CWF>::bytes, s>>>(v, pblk, bsize);  // n_tiles = grid
+  else
+    k_pcg_precond<T, 64><<<v.n_tiles, 256, PrecondSmem<T, 64>::bytes, s>>>(v, pblk, bsize);
 }
 template void launch_pcg_update<double>(cudaStream_t, const PcgVec<double> &, const double *, int);
 template void launch_pcg_update<float>(cudaStream_t, const PcgVec<float> &, const float *, int);
@@ -537,7 +594,10 @@ __global__ void __launch_bounds__(256) k_pcg_reduce_alpha(PcgVec<T> v) {
 template <typename T>
 void launch_pcg_reduce_alpha(cudaStream_t s, const PcgVec<T> &v) {
   ++g_launch_count;
-  k_pcg_reduce_alpha<T><<<v.ld / 32, 256, 0, s>>>(v);
+  {
+    ProfScope ps_(s, PROF_PCGVEC);
+    k_pcg_reduce_alpha<T><<<v.ld / 32, 256, 0, s>>>(v);
+  }
 }
 template void launch_pcg_reduce_alpha<double>(cudaStream_t, const PcgVec<double> &);
 template void launch_pcg_reduce_alpha<float>(cudaStream_t, const PcgVec<float> &);
@@ -581,7 +641,10 @@ __global__ void __launch_bounds__(256) k_pcg_reduce_beta(PcgVec<T> v, double tol
 template <typename T>
 void launch_pcg_reduce_beta(cudaStream_t s, const PcgVec<T> &v, double tol, int init) {
   ++g_launch_count;
-  k_pcg_reduce_beta<T><<<v.ld / 32, 256, 0, s>>>(v, tol * tol, init);
+  {
+    ProfScope ps_(s, PROF_PCGVEC);
+    k_pcg_reduce_beta<T><<<v.ld / 32, 256, 0, s>>>(v, tol * tol, init);
+  }
 }
 template void launch_pcg_reduce_beta<double>(cudaStream_t, const PcgVec<double> &, double, int);
 template void launch_pcg_reduce_beta<float>(cudaStream_t, const PcgVec<float> &, double, int);
@@ -613,7 +676,10 @@ void launch_pcg_p_update(cudaStream_t s, const PcgVec<T> &v) {
   int64_t total = (int64_t)v.n * v.ld / (16 / (int)sizeof(T));
   int grid = (int)((total + 255) / 256);
   if (grid > 152 * 8) grid = 152 * 8;
-  k_pcg_p_update<T><<<grid, 256, 0, s>>>(v);
+  {
+    ProfScope ps_(s, PROF_PCGVEC);
+    k_pcg_p_update<T><<<grid, 256, 0, s>>>(v);
+  }
 }
 template void launch_pcg_p_update<double>(cudaStream_t, const PcgVec<double> &);
 template void launch_pcg_p_update<float>(cudaStream_t, const PcgVec<float> &);
@@ -661,7 +727,10 @@ __global__ void __launch_bounds__(256) k_residual(const double *__restrict__ b, 
 void launch_residual(cudaStream_t s, const double *b, const double *y, double *r, float *r32, int n,
                      int ld, double *partial_rr, double *partial_bb) {
   ++g_launch_count;
-  k_residual<<<residual_grid(n), 256, 0, s>>>(b, y, r, r32, n, ld, partial_rr, partial_bb);
+  {
+    ProfScope ps_(s, PROF_PCGVEC);
+    k_residual<<<residual_grid(n), 256, 0, s>>>(b, y, r, r32, n, ld, partial_rr, partial_bb);
+  }
 }
 
 __global__ void k_residual_check(const double *__restrict__ prr, const double *__restrict__ pbb,
@@ -793,7 +862,10 @@ void launch_accumulate(cudaStream_t s, double *x, const float *d, int64_t count)
   ++g_launch_count;
   int64_t grid = (count + 255) / 256;
   if (grid > 152 * 16) grid = 152 * 16;
-  k_accumulate<<<(int)grid, 256, 0, s>>>(x, d, count);
+  {
+    ProfScope ps_(s, PROF_PCGVEC);
+    k_accumulate<<<(int)grid, 256, 0, s>>>(x, d, count);
+  }
 }
 
 }  // namespace qsel

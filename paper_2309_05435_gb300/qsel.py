@@ -65,7 +65,20 @@ class qsel_stats_t(ctypes.Structure):
                 ("ms_correction", c_double), ("ms_total", c_double), ("kernel_launches", c_int64),
                 ("gemm_ms", c_double), ("gemm_flop", c_double), ("gemm_launches", c_int64),
                 ("sweep_ms", c_double), ("sweep_flop", c_double), ("sweep_launches", c_int64),
-                ("spmm_ms", c_double), ("spmm_bytes", c_double), ("spmm_launches", c_int64)]
+                ("spmm_ms", c_double), ("spmm_bytes", c_double), ("spmm_launches", c_int64),
+                ("class_ms", c_double * 11), ("class_launches", c_int64 * 11), ("class_work", c_double * 11)]
+
+
+PROF_CLASSES = ("gemm", "sweep_update", "spmm", "pivot", "sweep_panel", "schur", "gather", "precond", "pcg_vec",
+                "correction", "extract")
+
+
+def _fields(s) -> dict:
+    out = {}
+    for name, _ in type(s)._fields_:
+        v = getattr(s, name)
+        out[name] = list(v) if hasattr(v, "_length_") else v
+    return out
 
 
 EXPORTED = ["qsel_create", "qsel_set_theta", "qsel_diag_inv", "qsel_trace_grads", "qsel_stats",
@@ -249,7 +262,7 @@ def qsel_trace_grads(ctx: Context) -> np.ndarray:
 def qsel_stats(ctx: Context) -> dict:
     s = qsel_stats_t()
     _check(load_library().qsel_stats(ctx.handle, ctypes.byref(s)), ctx.handle)
-    return {name: getattr(s, name) for name, _ in qsel_stats_t._fields_}
+    return _fields(s)
 
 
 def qsel_debug_set_samples(ctx: Context, X: np.ndarray):
@@ -467,7 +480,7 @@ def qsel_batch_trace_grads(b: Batch, model: int) -> np.ndarray:
 def qsel_batch_stats(b: Batch, model: int) -> dict:
     s = qsel_stats_t()
     _check_batch(load_library().qsel_batch_stats(b.handle, int(model), ctypes.byref(s)), b)
-    return {name: getattr(s, name) for name, _ in qsel_stats_t._fields_}
+    return _fields(s)
 
 
 def qsel_batch_info(b: Batch) -> dict:

@@ -224,7 +224,8 @@ def test_cv_gain_over_plain_rbmc(q):
     eval_spec = cvm.ModelSpec(mesh, 32, qi.obs_mask(256 * 32, 0.25, 4), 0.5, qi.balanced_slab_start(32, 4))
     for th in cvm.sobol_thetas(2, seed=99):
         th = (th[0], th[1], max(th[2], math.log(0.85 / 0.15)))   # strong time correlation: corrections matter
-        ref = cvm.solve_plain(eval_spec, th, 1e-9, overlap=1, k0=128, k_max=128, precision=q.QSEL_MIXED)
+        ref = cvm.solve_plain(eval_spec, th, 1e-9, overlap=1, k0=128, k_max=128, precision=q.QSEL_MIXED,
+                              max_batches=1)
         target = 0.5 * ref["err"]          # plain needs about 4x the samples: 32 -> 512 in 5 runs
         plain = cvm.solve_plain(eval_spec, th, target, overlap=1, precision=q.QSEL_MIXED)
         planned = cvm.solve_planned(eval_spec, th, net, target, max_overlap=3)
