@@ -172,18 +172,19 @@ template void launch_gemm<float>(cudaStream_t, const GemmBatch<float> &, int, in
 template <typename T>
 __global__ void __launch_bounds__(256) k_sweep_pivot(SweepBatch<T> bt, int k, int ld, int32_t *err_flag) {
   __shared__ double S[64 * 65];
+  __shared__ double col[64], wv[64];
   const SweepEntry<T> e = bt.e[blockIdx.x];
   const T *Tk = e.A + (int64_t)k * 64 * ld + k * 64;
   for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
     const int r = idx >> 6, c = idx & 63;
-    // the diagonal tile is kept symmetric; read the lower half only
-    S[r * 65 + c] = (double)((r >= c) ? Tk[(int64_t)r * ld + c] : Tk[(int64_t)c * ld + r]);
+    // the diagonal tile is kept symmetric; the lower half is what is read
+    if (r >= c) S[r * 65 + c] = (double)Tk[(int64_t)r * ld + c];
   }
   __syncthreads();
-  sym_sweep_inverse_smem(S, 65, 64, err_flag);
+  sym_sweep_inverse64_lower(S, 65, col, wv, err_flag);
   for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
     const int r = idx >> 6, c = idx & 63;
-    e.P[idx] = (T)(-S[r * 65 + c]);
+    e.P[idx] = (T)(-S[(r >= c) ? r * 65 + c : c * 65 + r]);
   }
 }
 

@@ -38,4 +38,55 @@ __device__ inline void sym_sweep_inverse_smem(double *S, int ld_s, int b, int32_
   }
 }
 
+// 64 x 64 version of the sweep above for an SPD tile held in its lower
+// triangle: each pivot snapshots column p (c_i = S_ip) and w_j = c_j / d, then
+// every lower entry is updated with one FMA, S_ij - c_i w_j, by the thread
+// that owns it (2080 entries, at most 9 per thread; blockDim.x must be 256).
+// After the 64 pivots the lower triangle holds that of -S^-1.
+__device__ inline void sym_sweep_inverse64_lower(double *S, int ld_s, double *col, double *wv, int32_t *err_flag) {
+  int ei[9], ej[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const int e = (int)threadIdx.x + q * (int)blockDim.x;
+    ei[q] = -1;
+    ej[q] = 0;
+    if (e < 2080) {
+      int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      while (i * (i + 1) / 2 > e) --i;
+      ei[q] = i;
+      ej[q] = e - i * (i + 1) / 2;
+    }
+  }
+  for (int p = 0; p < 64; ++p) {
+    const double d = S[p * ld_s + p];
+    const double inv = (d > 0.0) ? 1.0 / d : 0.0;
+    if (threadIdx.x < 64) {
+      const int i = threadIdx.x;
+      const double c = (i >= p) ? S[i * ld_s + p] : S[p * ld_s + i];
+      col[i] = c;
+      wv[i] = c * inv;
+    }
+    if (!(d > 0.0) && threadIdx.x == 0 && err_flag) atomicOr(err_flag, 1);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      if (ei[q] >= 0) {
+        const int i = ei[q], j = ej[q];
+        double v;
+        if (i == p && j == p)
+          v = -inv;
+        else if (i == p)
+          v = wv[j];
+        else if (j == p)
+          v = wv[i];
+        else
+          v = fma(-col[i], wv[j], S[i * ld_s + j]);
+        S[i * ld_s + j] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace qsel
