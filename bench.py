@@ -47,6 +47,9 @@ FP64_PEAK_TFLOPS = 1.25      # GB300 nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/c
 FP32_PEAK_TFLOPS = 80.5      # GB300 FP32 CUDA cores (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz)
 # DRAM bytes per FLOP of k_gemm64 from one ncu capture (profiles/k_gemm64_grid64_nt16_fp64.md)
 GEMM64_DRAM_BYTES_PER_FLOP = 7.808e9 / 2.749e11
+# DRAM bytes of one rank-64 sweep update of a 4096^2 FP32 matrix on the tensor
+# cores (profiles/k_tc_gemm_grid64_nt16_mixed.md: 0.094 GB for 2 matrices)
+TC_SWEEP_DRAM_BYTES_PER_MATRIX = 0.094e9 / 2
 L2_BYTES = 126 * 2 ** 20
 
 
@@ -469,6 +472,13 @@ def run_native(args):
     traffic = None
     if name == "gemm" and not mixed and claunch[dom]:
         traffic = GEMM64_DRAM_BYTES_PER_FLOP * cwork[dom] / claunch[dom]
+    if name == "sweep_update" and mixed and claunch[dom] and w.n_s == 4096:
+        # one ncu capture (profiles/k_tc_gemm_grid64_nt16_mixed.md): 0.094 GB per
+        # launch of 2 matrices of 4096^2; scaled by the matrices per launch
+        n_tiles = 64
+        per_matrix_flop = 2.0 * 64 ** 3 * (n_tiles * (n_tiles + 1) / 2 - n_tiles)
+        entries = cwork[dom] / claunch[dom] / per_matrix_flop
+        traffic = TC_SWEEP_DRAM_BYTES_PER_MATRIX * entries
     roof = {"kernel": desc[name], **roof, "frac": roof["achieved"] / roof["peak"], "traffic": traffic,
             "launches": int(claunch[dom]), "avg_launch_ms": per_launch_ms}
     roof["kernel_classes_ms_per_step"] = {classes[q]: cms[q] / args.steps for q in range(len(classes))}

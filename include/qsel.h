@@ -349,7 +349,7 @@ qsel_status qsel_cv_targets(qsel_ctx *const *ctxs, int32_t count, float *y_dev);
  * T_p = slabs of the extended part, n_pad = n_s rounded up to 64.  The
  * plan also reports the modelled cost of the exact one-part alternative.
  * Cost coefficients of 0 take GB300 mixed-precision defaults (seconds:
- * 1.73e-8, 1.37e-13, 2.3e-13).  When no k meets the target everywhere the
+ * 1.53e-8, 1.10e-13, 2.2e-13).  When no k meets the target everywhere the
  * plan takes max_samples and max_overlap and sets feasible = 0.
  */
 typedef struct {

@@ -560,6 +560,7 @@ static Err pcg_solve(qsel_ctx *c, const PcgVec<T> &v, const T *pblk, double tol,
   a.x = v.p;
   a.y = v.q;
   a.dot_partial = c->d_pa;
+  a.tmp = v.z;  // free while the SpMM runs (rewritten by the preconditioner)
   const int check_every = 8;
   int it = 0;
   bool done = false;
@@ -639,6 +640,7 @@ static Err run_sampler(qsel_ctx *c) {
   a.x = c->d_X;
   a.y = c->d_q;
   a.dot_partial = nullptr;
+  a.tmp = c->d_z1;  // free until the residual that follows overwrites it
   // inner FP32 solves stop at the reduction still needed (with a margin),
   // floored at what FP32 CG reliably attains
   const double inner_floor = 3e-6;
@@ -738,6 +740,7 @@ static void pcg_steps(qsel_ctx *c, cudaStream_t s, const PcgVec<T> &v, const T *
   a.x = v.p;
   a.y = v.q;
   a.dot_partial = c->d_pa;
+  a.tmp = v.z;  // free while the SpMM runs (rewritten by the preconditioner)
   for (int b = 0; b < count; ++b) {
     launch_bt_spmm<T>(s, a);
     launch_pcg_reduce_alpha<T>(s, v);
@@ -809,6 +812,7 @@ static Err run_sampler_graph(qsel_ctx *c) {
   a.x = c->d_X;
   a.y = c->d_q;
   a.dot_partial = nullptr;
+  a.tmp = c->d_z1;  // free until the residual that follows overwrites it
   const double inner_floor = 3e-6;
   const int max_outer = 30;
   const double tol = c->opt.pcg_tol;
@@ -1443,7 +1447,7 @@ static double model_cost(const qsel_ctx *c) {
   double slabs = 0.0;
   for (auto &sd : c->parts) slabs += sd.T;
   const double npad = (double)c->n_pad;
-  return 1.37e-13 * slabs * npad * npad * npad + 1.73e-8 * (double)c->k * c->n;
+  return 1.10e-13 * slabs * npad * npad * npad + 1.53e-8 * (double)c->k * c->n;
 }
 
 // ---------------------------------------------------------------------------
@@ -1717,9 +1721,9 @@ qsel_status qsel_cv_plan(qsel_ctx *ctx, const qsel_cv *cv, const qsel_cv_plan_op
     if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "planner reduction", __FILE__, __LINE__));
     for (int p = 0; p < np; ++p) m2[nl][p] /= (double)(c->slab_start[p + 1] - c->slab_start[p]) * c->n_s;
   }
-  const double cp = o->cost_pcg > 0 ? o->cost_pcg : 1.73e-8;
-  const double cd = o->cost_dense > 0 ? o->cost_dense : 1.37e-13;
-  const double cc = o->cost_corr > 0 ? o->cost_corr : 2.3e-13;
+  const double cp = o->cost_pcg > 0 ? o->cost_pcg : 1.53e-8;
+  const double cd = o->cost_dense > 0 ? o->cost_dense : 1.10e-13;
+  const double cc = o->cost_corr > 0 ? o->cost_corr : 2.2e-13;
   const double npad = (double)c->n_pad;
   auto slabs = [&](int p, int nl) {
     return std::min(c->n_t, c->slab_start[p + 1] + nl) - std::max(0, c->slab_start[p] - nl);

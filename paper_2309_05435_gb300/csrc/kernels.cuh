@@ -111,6 +111,7 @@ struct BtSpmmArgs {
   const T *x;
   T *y;
   double *dot_partial;    // if non-null: per-CTA per-column partial sums of x*y
+  T *tmp = nullptr;       // if non-null: n x ld scratch for the time combination
 };
 // Number of dot-partial rows launch_bt_spmm writes.
 int bt_spmm_grid(int n_rows);

@@ -166,7 +166,46 @@ int bt_spmm_grid(int n_rows) {
 
 
 
-template <typename T, int NV>
+// Time combination of the block-tridiagonal product:
+//   zc_t = c0_t x_t + c1_{t-1} x_{t-1} + c1_t x_{t+1}   (16-byte vectors)
+// so that y_t = V zc_t + w_obs diag(obs_t) x_t needs one spatial pass that
+// reads w neighbour rows per output row instead of 3w.
+template <typename T>
+__global__ void __launch_bounds__(256) k_time_combine(BtSpmmArgs<T> a) {
+  using V4 = typename std::conditional<std::is_same<T, float>::value, float4, double2>::type;
+  constexpr int E = (int)(sizeof(V4) / sizeof(T));
+  const int64_t slab = (int64_t)a.n_s * a.ld / E;
+  const int64_t total = slab * a.n_t;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(e / slab);
+    const T c0 = (T)a.c0[t];
+    const T cm = (t > 0) ? (T)a.c1[t - 1] : T(0);
+    const T cp = (t + 1 < a.n_t) ? (T)a.c1[t] : T(0);
+    const V4 x0 = reinterpret_cast<const V4 *>(a.x)[e];
+    V4 z;
+    const T *xs = reinterpret_cast<const T *>(&x0);
+    T *zs = reinterpret_cast<T *>(&z);
+#pragma unroll
+    for (int q = 0; q < E; ++q) zs[q] = c0 * xs[q];
+    if (t > 0) {
+      const V4 xm = reinterpret_cast<const V4 *>(a.x)[e - slab];
+      const T *ms = reinterpret_cast<const T *>(&xm);
+#pragma unroll
+      for (int q = 0; q < E; ++q) zs[q] = fma(cm, ms[q], zs[q]);
+    }
+    if (t + 1 < a.n_t) {
+      const V4 xp = reinterpret_cast<const V4 *>(a.x)[e + slab];
+      const T *ps = reinterpret_cast<const T *>(&xp);
+#pragma unroll
+      for (int q = 0; q < E; ++q) zs[q] = fma(cp, ps[q], zs[q]);
+    }
+    reinterpret_cast<V4 *>(a.tmp)[e] = z;
+  }
+}
+
+// COMB: the neighbour rows are read from the time combination a.tmp (one
+// term per pattern entry) instead of three slabs of a.x.
+template <typename T, int NV, bool COMB>
 __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs<T> a) {
   __shared__ T red[8][512];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -210,6 +249,16 @@ __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs<T> a) {
       for (int s = 0; s < cnt; ++s) {
         const int j = __shfl_sync(0xffffffffu, my_col, s);
         const T val = __shfl_sync(0xffffffffu, my_val, s);
+        if (COMB) {
+          const T *zc = a.tmp + ((int64_t)t * a.n_s + j) * ld + coff;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const auto z0 = load2(zc + 64 * v);
+            ax[v] = fma(val, z0.x, ax[v]);
+            ay[v] = fma(val, z0.y, ay[v]);
+          }
+          continue;
+        }
         const T *xc = a.x + ((int64_t)t * a.n_s + j) * ld + coff;
         const T f0 = c0 * val, fm = cm * val, fp = cp * val;
 #pragma unroll
@@ -272,12 +321,23 @@ void launch_bt_spmm(cudaStream_t s, const BtSpmmArgs<T> &a) {
     rec.work = 2.0 * (double)a.n_s * a.n_t * a.ld * sizeof(T);
     g_prof->begin(s, rec);
   }
-  if (a.ld % 256 == 0)
-    k_bt_spmm<T, 4><<<grid, 256, 0, s>>>(a);
-  else if (a.ld % 128 == 0)
-    k_bt_spmm<T, 2><<<grid, 256, 0, s>>>(a);
-  else
-    k_bt_spmm<T, 1><<<grid, 256, 0, s>>>(a);
+  if (a.tmp) {
+    ++g_launch_count;
+    const int64_t vec = (int64_t)a.n_s * a.n_t * a.ld / (16 / (int)sizeof(T));
+    k_time_combine<T><<<(int)std::min<int64_t>((vec + 255) / 256, 152 * 8), 256, 0, s>>>(a);
+    if (a.ld % 256 == 0)
+      k_bt_spmm<T, 4, true><<<grid, 256, 0, s>>>(a);
+    else if (a.ld % 128 == 0)
+      k_bt_spmm<T, 2, true><<<grid, 256, 0, s>>>(a);
+    else
+      k_bt_spmm<T, 1, true><<<grid, 256, 0, s>>>(a);
+  } else if (a.ld % 256 == 0) {
+    k_bt_spmm<T, 4, false><<<grid, 256, 0, s>>>(a);
+  } else if (a.ld % 128 == 0) {
+    k_bt_spmm<T, 2, false><<<grid, 256, 0, s>>>(a);
+  } else {
+    k_bt_spmm<T, 1, false><<<grid, 256, 0, s>>>(a);
+  }
   if (g_prof) g_prof->end(s, rec);
 }
 template void launch_bt_spmm<double>(cudaStream_t, const BtSpmmArgs<double> &);
