@@ -28,13 +28,26 @@
 namespace qsel {
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BK = 32, STAGES = 3;
-constexpr int TILE_BYTES = BM * BK * 4;          // 16 KiB per operand tile
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;      // A, B, A_lo, B_lo
+constexpr int BM = 128, BK = 32;
+constexpr int TILE_A = BM * BK * 4;              // 16 KiB A tile
 constexpr int BAR_BYTES = 256;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BAR_BYTES + 1024;
+// Configurations: <3 stages, BN = 128> (one CTA per SM) for long K, and
+// <2 stages, BN = 64> for the K = 64 sweep updates: the two K-blocks fit
+// without reusing a stage and two CTAs share an SM, so one CTA's epilogue
+// overlaps the other's loads and MMAs.
+template <int BN>
+__host__ __device__ constexpr int tile_b() {
+  return BN * BK * 4;
+}
+template <int STAGES, int BN>
+__host__ __device__ constexpr int stage_bytes() {
+  return 2 * (TILE_A + tile_b<BN>());            // A, B, A_lo, B_lo
+}
+template <int STAGES, int BN>
+__host__ __device__ constexpr int smem_bytes() {
+  return STAGES * stage_bytes<STAGES, BN>() + BAR_BYTES + 1024;
+}
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
-constexpr uint32_t kTmemCols = 128;
 
 struct Params {
   CUtensorMap tmA[kMaxBatch];
@@ -108,15 +121,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 // Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
 // (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
 // M >> 4 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
+template <int BN>
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      "l"(a), "l"(b), "r"(idesc<BN>()), "r"(accumulate)
       : "memory");
 }
 
@@ -142,7 +158,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 
 __device__ __forceinline__ void named_sync_converters() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-__global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Params p) {
+template <int STAGES, int BN>
+__global__ void __launch_bounds__(192) k_tc_gemm(const __grid_constant__ Params p) {
+  constexpr int TILE_B = tile_b<BN>();
+  constexpr int STAGE_BYTES = stage_bytes<STAGES, BN>();
+  constexpr uint32_t kTmemCols = BN;
   extern __shared__ unsigned char smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t *bars = reinterpret_cast<uint64_t *>(base + STAGES * STAGE_BYTES);
@@ -153,7 +173,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Para
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int bn = blockIdx.x, bm = blockIdx.y, z = blockIdx.z;
-  if (p.lower && bn > bm) return;
+  if (p.lower && bn * BN >= (bm + 1) * BM) return;   // tile entirely above the diagonal
   const int nk = p.K / BK;
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
@@ -192,9 +212,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Para
         const int s = kb % STAGES, u = kb / STAGES;
         if (!mbar_wait(empty_bar(s), (u & 1) ^ 1, abort, p.err)) break;
         uint8_t *st = base + s * STAGE_BYTES;
-        mbar_expect_tx(full_bar(s), 2 * TILE_BYTES);
+        mbar_expect_tx(full_bar(s), TILE_A + TILE_B);
         tma_load_2d(smem_u32(st), tma, kb * BK, bm * BM, full_bar(s));
-        tma_load_2d(smem_u32(st + TILE_BYTES), tmb, kb * BK, bn * BN, full_bar(s));
+        tma_load_2d(smem_u32(st + TILE_A), tmb, kb * BK, bn * BN, full_bar(s));
         issued = kb + 1;
       }
       if (*abort) {
@@ -220,14 +240,14 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Para
         if (!mbar_wait(conv_bar(s), u & 1, abort, p.err)) break;
         tc_fence_after();
         const uint32_t st = smem_u32(base + s * STAGE_BYTES);
-        const uint32_t a_hi = st, b_hi = st + TILE_BYTES, a_lo = st + 2 * TILE_BYTES, b_lo = st + 3 * TILE_BYTES;
+        const uint32_t a_hi = st, b_hi = st + TILE_A, a_lo = st + TILE_A + TILE_B, b_lo = a_lo + TILE_A;
 #pragma unroll
         for (int j = 0; j < BK / 8; ++j) {
           const uint32_t off = j * 32;
-          mma_tf32(tmem, smem_desc(a_hi + off), smem_desc(b_hi + off), (kb | j) != 0);
+          mma_tf32<BN>(tmem, smem_desc(a_hi + off), smem_desc(b_hi + off), (kb | j) != 0);
           if (p.passes == 3) {
-            mma_tf32(tmem, smem_desc(a_hi + off), smem_desc(b_lo + off), 1u);
-            mma_tf32(tmem, smem_desc(a_lo + off), smem_desc(b_hi + off), 1u);
+            mma_tf32<BN>(tmem, smem_desc(a_hi + off), smem_desc(b_lo + off), 1u);
+            mma_tf32<BN>(tmem, smem_desc(a_lo + off), smem_desc(b_hi + off), 1u);
           }
         }
         mma_commit(empty_bar(s));
@@ -245,9 +265,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ Para
       if (!*conv_ok) break;
       if (p.passes == 3) {
         float4 *raw = reinterpret_cast<float4 *>(base + s * STAGE_BYTES);
-        float4 *lo = reinterpret_cast<float4 *>(base + s * STAGE_BYTES + 2 * TILE_BYTES);
-        // A then B: 2 x 1024 16-byte chunks; lo mirrors raw at +2 tiles
-        for (int i = ct; i < 2 * TILE_BYTES / 16; i += 128) {
+        float4 *lo = reinterpret_cast<float4 *>(base + s * STAGE_BYTES + TILE_A + TILE_B);
+        // A then B (16-byte chunks); lo mirrors raw at +(A + B)
+        for (int i = ct; i < (TILE_A + TILE_B) / 16; i += 128) {
           float4 v = raw[i];
           float4 h;
           h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
@@ -336,10 +356,10 @@ std::mutex g_mu;
 EncodeFn g_encode = nullptr;
 int g_state = 0;  // 0 unknown, 1 available, -1 unavailable
 
-bool encode_2d(CUtensorMap *tm, const float *ptr, int rows, int cols, int ld) {
+bool encode_2d(CUtensorMap *tm, const float *ptr, int rows, int cols, int ld, int box_rows) {
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   const CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, estr,
                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -369,8 +389,10 @@ bool tc_gemm_available() {
     return false;
   }
   tc::g_encode = reinterpret_cast<tc::EncodeFn>(fn);
-  if (cudaFuncSetAttribute(tc::k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES) !=
-      cudaSuccess) {
+  if (cudaFuncSetAttribute(tc::k_tc_gemm<3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           tc::smem_bytes<3, 128>()) != cudaSuccess ||
+      cudaFuncSetAttribute(tc::k_tc_gemm<2, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           tc::smem_bytes<2, 64>()) != cudaSuccess) {
     cudaGetLastError();
     tc::g_state = -1;
     return false;
@@ -384,12 +406,15 @@ bool tc_gemm_available() {
 // map cannot be encoded (nothing is launched then).
 bool launch_tc_gemm(cudaStream_t s, const GemmBatch<float> &b, int M, int N, int K, int lda, int ldb, int ldc,
                     bool lower, int passes, int32_t *err) {
+  // K = 64 (the sweep updates): two stages, 128 x 64 tiles, two CTAs per SM
+  const bool narrow = K <= 64;
   if (b.count <= 0) return true;
   if (!tc_gemm_available()) return false;
   tc::Params p;
   memset(&p, 0, sizeof(p));
   for (int q = 0; q < b.count; ++q) {
-    if (!tc::encode_2d(&p.tmA[q], b.e[q].A, M, K, lda) || !tc::encode_2d(&p.tmB[q], b.e[q].B, N, K, ldb))
+    if (!tc::encode_2d(&p.tmA[q], b.e[q].A, M, K, lda, tc::BM) ||
+        !tc::encode_2d(&p.tmB[q], b.e[q].B, N, K, ldb, narrow ? 64 : 128))
       return false;
     p.C[q] = b.e[q].C;
     p.C0[q] = b.e[q].C0;
@@ -405,13 +430,20 @@ bool launch_tc_gemm(cudaStream_t s, const GemmBatch<float> &b, int M, int N, int
   p.err = err;
   ++g_launch_count;
   Profiler::Rec rec{PROF_GEMM, nullptr, nullptr, 0.0};
-  const int gm = (M + tc::BM - 1) / tc::BM, gn = (N + tc::BN - 1) / tc::BN;
+  const int bn_w = narrow ? 64 : 128;
+  const int gm = (M + tc::BM - 1) / tc::BM, gn = (N + bn_w - 1) / bn_w;
   if (g_prof) {
-    const double tiles = lower ? (double)gm * (gm + 1) / 2 : (double)gm * gn;
-    rec.work = 2.0 * tc::BM * tc::BN * (double)K * tiles * b.count;
+    double tiles = 0.0;
+    for (int bm = 0; bm < gm; ++bm)
+      for (int bn = 0; bn < gn; ++bn)
+        if (!lower || bn * bn_w < (bm + 1) * tc::BM) tiles += 1.0;
+    rec.work = 2.0 * tc::BM * bn_w * (double)K * tiles * b.count;
     g_prof->begin(s, rec);
   }
-  tc::k_tc_gemm<<<dim3(gn, gm, b.count), 192, tc::SMEM_BYTES, s>>>(p);
+  if (narrow)
+    tc::k_tc_gemm<2, 64><<<dim3(gn, gm, b.count), 192, tc::smem_bytes<2, 64>(), s>>>(p);
+  else
+    tc::k_tc_gemm<3, 128><<<dim3(gn, gm, b.count), 192, tc::smem_bytes<3, 128>(), s>>>(p);
   if (g_prof) g_prof->end(s, rec);
   return true;
 }
