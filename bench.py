@@ -79,6 +79,9 @@ def parse_args():
                     help="the planner aims at margin * target (absorbs the prediction error)")
     ap.add_argument("--cv-train-thetas", type=int, default=32)
     ap.add_argument("--cv-train-steps", type=int, default=2000)
+    ap.add_argument("--cv-params", default=None,
+                    help="load the control-variate network (QSEL_CV_PARAMS_ALL floats, .npy) instead of training")
+    ap.add_argument("--save-cv-params", default=None, help="save the trained network (.npy)")
     ap.add_argument("--cv-eval", action="store_true",
                     help="held-out evaluation: 64x64 grid, n_t=128, 8 parts, 8 theta; planned vs plain")
     ap.add_argument("--cv-eval-thetas", type=int, default=8)
@@ -281,7 +284,15 @@ def run_native(args):
     chosen_prec = qsel.QSEL_MIXED if args.precision == "mixed" else qsel.QSEL_FP64
 
     planned = args.form == "planned" and chosen_prec == qsel.QSEL_MIXED
-    net, cv_info = (train_control_variate(args) if planned else (None, None))
+    net, cv_info = None, None
+    if planned and args.cv_params:
+        net = qsel.qsel_cv_create(0)
+        qsel.qsel_cv_set_params(net, np.load(args.cv_params))
+        cv_info = {"loaded": os.path.basename(args.cv_params)}
+    elif planned:
+        net, cv_info = train_control_variate(args)
+        if args.save_cv_params:
+            np.save(args.save_cv_params, qsel.qsel_cv_get_params(net))
 
     def make_ctx(precision, profile=1, k=None, part_overlap=None):
         return qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma,
