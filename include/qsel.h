@@ -62,6 +62,12 @@ typedef enum {
   QSEL_ESTATE = 7     /* call not valid in the context's current state           */
 } qsel_status;
 
+/* Samplers of the global samples (qsel_options.sampler). */
+enum {
+  QSEL_SAMPLER_PCG = 0,
+  QSEL_SAMPLER_LANCZOS = 1
+};
+
 /* Arithmetic of the pipeline. */
 enum {
   QSEL_FP64 = 0,      /* every kernel computes in IEEE binary64                  */
@@ -123,6 +129,11 @@ typedef struct {
                              GPU has tcgen05 tensor cores, else CUDA cores),
                              3 = 3xTF32 (FP32-level accuracy), 1 = plain TF32,
                              -1 = FP32 CUDA cores.  Ignored for QSEL_FP64.        */
+  int32_t sampler;        /* QSEL_SAMPLER_PCG (0): perturbation right-hand sides
+                             solved by PCG (Sections 2.4, 3.3); QSEL_SAMPLER_LANCZOS
+                             (1): the preconditioned Krylov sampler of
+                             Algorithm 5.1 (FP64; needs no factored form of Q)  */
+  int32_t lanczos_steps;  /* Krylov dimension m of the Lanczos sampler, 1..1024 */
   const int32_t *part_overlap;/* HOST array of n_parts overlaps n_l,p >= 0 (one per
                              part, read at qsel_create), or NULL: every part uses
                              the `overlap` argument.  Lets a planner
@@ -237,6 +248,11 @@ qsel_status qsel_debug_set_samples(qsel_ctx *ctx, const double *X, int32_t ld);
 qsel_status qsel_debug_get_samples(const qsel_ctx *ctx, double *X, int32_t ld);
 qsel_status qsel_debug_get_rhs(const qsel_ctx *ctx, double *R, int32_t ld);
 qsel_status qsel_debug_get_selinv_diag(const qsel_ctx *ctx, double *diag_out);
+/* Lanczos sampler: the coefficients of T for every column of the last run,
+ * alpha[j * ld + s] and beta[j * ld + s] for step j < lanczos_steps and
+ * column s < n_samples (HOST, ld >= n_samples; beta[j] = ||w_j|| after step
+ * j).  QSEL_ESTATE unless the last run used the Lanczos sampler. */
+qsel_status qsel_debug_get_lanczos(const qsel_ctx *ctx, double *alpha, double *beta, int32_t ld);
 
 /*
  * Allocation-free SPD inverse.  The paper has no counterpart: this entry point
@@ -389,7 +405,7 @@ qsel_status qsel_cv_plan(qsel_ctx *ctx, const qsel_cv *cv, const qsel_cv_plan_op
  *                opt->cuda_stream is the stream the graph is launched on
  *                (NULL: the batch creates its own; the legacy default stream
  *                cannot be captured).  profile_kernels and part_overlap must
- *                be 0 / NULL.
+ *                be 0 / NULL, sampler QSEL_SAMPLER_PCG.
  *   n_streams    1..64 streams in the pool.
  *   autotune     non-zero: for every grid size (n_s) the smallest model of
  *                that size is run with every block-Jacobi block in {16, 32,

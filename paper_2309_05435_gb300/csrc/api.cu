@@ -104,6 +104,14 @@ struct qsel_ctx {
   cudaStream_t body_stream[2] = {nullptr, nullptr};  // capture streams of loop bodies
   int32_t *d_loop = nullptr;           // loop state (see launch_loop_init)
   double *d_tol2 = nullptr;            // inner tolerance of the refinement, squared
+  // Lanczos sampler (allocated on first use)
+  struct {
+    double *vec[3] = {nullptr, nullptr, nullptr};   // v_{j-1}, v_j, w (rotated)
+    double *u = nullptr, *q = nullptr, *xt = nullptr, *linv = nullptr;
+    double *alpha = nullptr, *beta = nullptr, *coef = nullptr, *eta = nullptr, *zero = nullptr;
+    double *partial = nullptr, *dwork = nullptr, *U = nullptr;
+    bool ready = false, ran = false;
+  } lz;
   double *d_partials = nullptr, *d_diag_scratch = nullptr;
   TraceSlab *d_slabs = nullptr;
   int n_trace_slabs = 0;
@@ -218,6 +226,14 @@ static Err validate(const qsel_model *m, const qsel_theta *th, const qsel_partit
   if (opt->control_variate != 0) return fail(QSEL_EINVAL, "control_variate must be 0");
   if (opt->tensor_passes != 0 && opt->tensor_passes != 1 && opt->tensor_passes != 3 && opt->tensor_passes != -1)
     return fail(QSEL_EINVAL, "tensor_passes must be 0, 1, 3 or -1");
+  if (opt->sampler != QSEL_SAMPLER_PCG && opt->sampler != QSEL_SAMPLER_LANCZOS)
+    return fail(QSEL_EINVAL, "sampler must be QSEL_SAMPLER_PCG or QSEL_SAMPLER_LANCZOS");
+  if (opt->sampler == QSEL_SAMPLER_LANCZOS) {
+    if (opt->lanczos_steps < 1 || opt->lanczos_steps > 1024)
+      return fail(QSEL_EINVAL, "lanczos_steps must be in [1, 1024]");
+    if (opt->precond_block != 0 && opt->precond_block != 16 && opt->precond_block != 32 && opt->precond_block != 64)
+      return fail(QSEL_EINVAL, "the Lanczos sampler's block preconditioner takes blocks of 16, 32 or 64 rows");
+  }
   return ok();
 }
 
@@ -840,6 +856,98 @@ static Err run_sampler_graph(qsel_ctx *c) {
       });
 }
 
+// Preconditioned Krylov sampler (Algorithm 5.1), FP64: two passes of m
+// Lanczos steps on L^-1 Q L^-T for all columns at once (see lanczos.cu).
+static Err run_sampler_lanczos(qsel_ctx *c) {
+  cudaStream_t s = c->stream;
+  const int m = c->opt.lanczos_steps;
+  const size_t vec = (size_t)c->n * c->ld;
+  const int b = c->bsize;
+  const int nblk = (c->n + b - 1) / b;
+  if (!c->lz.ready) {
+    for (auto &p : c->lz.vec) TRY(c->alloc(&p, vec));
+    TRY(c->alloc(&c->lz.u, vec));
+    TRY(c->alloc(&c->lz.q, vec));
+    TRY(c->alloc(&c->lz.xt, vec));
+    TRY(c->alloc(&c->lz.linv, (size_t)nblk * b * b));
+    TRY(c->alloc(&c->lz.alpha, (size_t)m * c->ld));
+    TRY(c->alloc(&c->lz.beta, (size_t)m * c->ld));
+    TRY(c->alloc(&c->lz.coef, (size_t)m * c->ld));
+    TRY(c->alloc(&c->lz.eta, (size_t)c->ld));
+    TRY(c->alloc(&c->lz.zero, (size_t)c->ld));
+    TRY(c->alloc(&c->lz.partial, (size_t)lz_grid(c->n) * c->ld));
+    TRY(c->alloc(&c->lz.dwork, (size_t)2 * m * c->ld));
+    TRY(c->alloc(&c->lz.U, (size_t)m * m * c->ld));
+    QSEL_CUDA_TRY(cudaMemset(c->lz.zero, 0, (size_t)c->ld * sizeof(double)));
+    c->lz.ready = true;
+  }
+  launch_philox_normals(s, c->opt.seed, 0u, c->n, c->k, c->ld, c->d_z1);
+  QSEL_CUDA_TRY(cudaEventRecord(c->ev[1], s));
+  launch_bj_cholinv(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t, b, c->lz.linv,
+                    c->d_err);
+  LanczosArgs la{c->n, c->ld, c->k, m};
+  BtSpmmArgs<double> sp{};
+  sp.pat = c->pat;
+  sp.val = c->d_qs;
+  sp.c0 = c->tc.a0;
+  sp.c1 = c->tc.a1;
+  sp.obs = c->d_obs;
+  sp.obs_w = c->obs_w;
+  sp.n_s = c->n_s;
+  sp.n_t = c->n_t;
+  sp.ld = c->ld;
+  sp.dot_partial = nullptr;
+  for (int pass = 0; pass < 2; ++pass) {
+    double *vp = c->lz.vec[0], *v = c->lz.vec[1], *w = c->lz.vec[2];
+    // v_1 = z / eta
+    QSEL_CUDA_TRY(cudaMemcpyAsync(v, c->d_z1, vec * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    QSEL_CUDA_TRY(cudaMemsetAsync(vp, 0, vec * sizeof(double), s));
+    if (pass == 0) {
+      launch_lz_vec(s, 2, la, nullptr, nullptr, v, nullptr, nullptr, nullptr, c->lz.partial);
+      launch_lz_reduce(s, la, c->lz.partial, true, c->lz.eta, nullptr);
+    } else {
+      QSEL_CUDA_TRY(cudaMemsetAsync(c->lz.xt, 0, vec * sizeof(double), s));
+    }
+    launch_lz_scale(s, la, v, c->lz.eta);
+    for (int j = 0; j < m; ++j) {
+      const double *beta_prev = j == 0 ? c->lz.zero : c->lz.beta + (size_t)(j - 1) * c->ld;
+      double *alpha_j = c->lz.alpha + (size_t)j * c->ld;
+      double *beta_j = c->lz.beta + (size_t)j * c->ld;
+      // w = L^-1 Q L^-T v  (the SpMM's time combination uses w as scratch)
+      launch_block_apply(s, c->lz.linv, b, c->n, c->ld, v, c->lz.u, true);
+      sp.x = c->lz.u;
+      sp.y = c->lz.q;
+      sp.tmp = w;
+      launch_bt_spmm<double>(s, sp);
+      launch_block_apply(s, c->lz.linv, b, c->n, c->ld, c->lz.q, w, false);
+      if (pass == 0) {
+        launch_lz_vec(s, 0, la, vp, v, w, nullptr, nullptr, beta_prev, c->lz.partial);
+        launch_lz_reduce(s, la, c->lz.partial, false, alpha_j, nullptr);
+        launch_lz_vec(s, 1, la, nullptr, v, w, nullptr, nullptr, alpha_j, c->lz.partial);
+        launch_lz_reduce(s, la, c->lz.partial, true, beta_j, nullptr);
+      } else {
+        // the same vectors from the stored coefficients, accumulating x~
+        launch_lz_vec(s, 0, la, vp, v, w, c->lz.xt, c->lz.coef + (size_t)j * c->ld, beta_prev, c->lz.partial);
+        launch_lz_vec(s, 1, la, nullptr, v, w, nullptr, nullptr, alpha_j, c->lz.partial);
+      }
+      launch_lz_scale(s, la, w, beta_j);
+      double *t = vp;
+      vp = v;
+      v = w;
+      w = t;
+    }
+    if (pass == 0)
+      launch_lz_quadrature(s, la, c->lz.alpha, c->lz.beta, c->lz.eta, c->lz.dwork, c->lz.U, c->lz.coef, c->d_err);
+  }
+  // rewind the preconditioner: x = L^-T x~
+  launch_block_apply(s, c->lz.linv, b, c->n, c->ld, c->lz.xt, c->d_X, true);
+  QSEL_CUDA_TRY(cudaGetLastError());
+  c->stats.pcg_iterations = m;
+  c->stats.pcg_max_rel_residual = 0.0;
+  c->lz.ran = true;
+  return ok();
+}
+
 static void phase_mark(qsel_ctx *c, std::vector<std::pair<cudaEvent_t, int>> &marks, int phase) {
   if (c->graph_mode) return;
   cudaEvent_t e = c->phase_event();
@@ -1259,8 +1367,12 @@ static Err run_pipeline_body(qsel_ctx *c) {
   const bool need_samples = c->parts.size() > 1;
   c->stats.pcg_iterations = 0;
   c->stats.pcg_max_rel_residual = 0.0;
+  c->lz.ran = false;
   if (!c->injected && need_samples) {
-    TRY(run_sampler(c));
+    if (c->opt.sampler == QSEL_SAMPLER_LANCZOS)
+      TRY(run_sampler_lanczos(c));
+    else
+      TRY(run_sampler(c));
   } else {
     QSEL_CUDA_TRY(cudaEventRecord(c->ev[1], s));
   }
@@ -1284,6 +1396,8 @@ static Err run_pipeline_body(qsel_ctx *c) {
   QSEL_CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
   if (err & 1) return fail(QSEL_ENOTSPD, "a pivot of a dense block factorisation was not positive");
   if (err & 2) return fail(QSEL_ETIMEOUT, "a bounded device-side wait of the tensor-core GEMM gave up");
+  if (err & 8)
+    return fail(QSEL_ENOCONV, "the Lanczos tridiagonal matrix could not be diagonalised or was not positive definite");
   float ms;
   auto el = [&](cudaEvent_t a, cudaEvent_t b) {
     cudaEventElapsedTime(&ms, a, b);
@@ -1787,8 +1901,9 @@ qsel_status qsel_create_batch(qsel_batch **out, int32_t n_models, const qsel_mod
     g_create_error = "qsel_create_batch: n_models >= 1, non-NULL arrays and 1 <= n_streams <= 64 required";
     return QSEL_EINVAL;
   }
-  if (opt->profile_kernels || opt->part_overlap) {
-    g_create_error = "qsel_create_batch: profile_kernels and part_overlap are not available in a batch";
+  if (opt->profile_kernels || opt->part_overlap || opt->sampler != QSEL_SAMPLER_PCG) {
+    g_create_error = "qsel_create_batch: profile_kernels, part_overlap and the Lanczos sampler are not available "
+                     "in a batch";
     return QSEL_EINVAL;
   }
   for (int i = 0; i < n_models; ++i) {
@@ -2023,6 +2138,21 @@ void qsel_batch_destroy(qsel_batch *b) {
   if (!b) return;
   if (b->main) cudaStreamSynchronize(b->main);
   delete b;
+}
+
+qsel_status qsel_debug_get_lanczos(const qsel_ctx *ctx, double *alpha, double *beta, int32_t ld) {
+  if (!ctx) return QSEL_EINVAL;
+  qsel_ctx *c = const_cast<qsel_ctx *>(ctx);
+  if (!alpha || !beta || ld < ctx->k) return finish(c, fail(QSEL_EINVAL, "NULL output or ld < n_samples"));
+  if (!ctx->lz.ran) return finish(c, fail(QSEL_ESTATE, "the last run did not use the Lanczos sampler"));
+  const int m = ctx->opt.lanczos_steps;
+  cudaError_t ce = cudaMemcpy2D(alpha, (size_t)ld * sizeof(double), ctx->lz.alpha, (size_t)ctx->ld * sizeof(double),
+                                (size_t)ctx->k * sizeof(double), m, cudaMemcpyDeviceToHost);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpy2D(beta, (size_t)ld * sizeof(double), ctx->lz.beta, (size_t)ctx->ld * sizeof(double),
+                      (size_t)ctx->k * sizeof(double), m, cudaMemcpyDeviceToHost);
+  if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "copy of Lanczos coefficients", __FILE__, __LINE__));
+  return QSEL_OK;
 }
 
 const char *qsel_last_error(const qsel_ctx *ctx) {

@@ -327,6 +327,23 @@ void launch_sum(cudaStream_t s, double *out, const double *a, const double *b, i
 void launch_part_error_sums(cudaStream_t s, const double *m2, const double *m4, const double *v,
                             const int32_t *slab_start_dev, int n_parts, int n_s, int k, double *out);
 
+// ---------------------------------------------------------------- lanczos.cu
+struct LanczosArgs {
+  int n, ld, k, m;
+};
+int lz_grid(int n);
+void launch_bj_cholinv(cudaStream_t s, const SellPattern &pat, const double *qs, const double *a0, const double *a1,
+                       const uint8_t *obs, double obs_w, int n_s, int n_t, int b, double *linv, int32_t *err_flag);
+void launch_block_apply(cudaStream_t s, const double *linv, int b, int n, int ld, const double *x, double *y,
+                        bool trans);
+void launch_lz_vec(cudaStream_t s, int mode, const LanczosArgs &a, const double *vprev, const double *v, double *w,
+                   double *xt, const double *coef, const double *scal, double *partial);
+void launch_lz_reduce(cudaStream_t s, const LanczosArgs &a, const double *partial, bool sqrt_out, double *out,
+                      double *store);
+void launch_lz_scale(cudaStream_t s, const LanczosArgs &a, double *w, const double *scal);
+void launch_lz_quadrature(cudaStream_t s, const LanczosArgs &a, const double *alpha, const double *beta,
+                          const double *eta, double *dwork, double *U, double *coef, int32_t *err_flag);
+
 // ---------------------------------------------------------------- mlp.cu
 void launch_cv_features(cudaStream_t s, const SellPattern &pat, const double *qs, const double *a0,
                         const double *a1, const uint8_t *obs, double obs_w, int n_s, int n_t, const float *sep_dist,

@@ -8,6 +8,7 @@
 #include "qsel.h"
 #include "kernels.cuh"
 #include "sweep.cuh"
+#include "bjblock.cuh"
 
 #include <algorithm>
 #include <type_traits>
@@ -356,35 +357,7 @@ __global__ void __launch_bounds__(256) k_jacobi_setup(SellPattern pat, const dou
                                                       int n_s, int n_t, int b, T *__restrict__ pblk,
                                                       int32_t *err_flag) {
   __shared__ double S[64 * 65];
-  const int n = n_s * n_t;
-  const int r0 = blockIdx.x * b;
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int i = e / b, j = e - (e / b) * b;
-    S[i * 65 + j] = (i == j && r0 + i >= n) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  for (int rr = threadIdx.x; rr < b; rr += blockDim.x) {
-    const int row = r0 + rr;
-    if (row >= n) continue;
-    const int t = row / n_s, i = row - t * n_s;
-    const int sl = i >> 5, li = i & 31;
-    const int w = pat.slice_width[sl];
-    const int base = pat.slice_ptr[sl] + li;
-    for (int s = 0; s < w; ++s) {
-      const int j = pat.col[base + s * kSlice];
-      const double v = qs[base + s * kSlice];
-      for (int d = -1; d <= 1; ++d) {
-        const int u = t + d;
-        if (u < 0 || u >= n_t) continue;
-        const int colg = u * n_s + j;
-        if (colg < r0 || colg >= r0 + b) continue;
-        const double c = (d == 0) ? a0[t] : (d < 0 ? a1[t - 1] : a1[t]);
-        S[rr * 65 + (colg - r0)] += c * v;
-      }
-    }
-    if (obs != nullptr && obs[row]) S[rr * 65 + rr] += obs_w;
-  }
-  __syncthreads();
+  assemble_diag_block(S, 65, pat, qs, a0, a1, obs, obs_w, n_s, n_t, blockIdx.x * b, b);
   sym_sweep_inverse_smem(S, 65, b, err_flag);
   T *P = pblk + (int64_t)blockIdx.x * b * b;
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {

@@ -53,6 +53,10 @@ def _args(**over):
     (dict(slab_start=[0, 5, 7], n_parts=2), "0 to n_t"),
     (dict(theta=(0.0, 0.0, 40.0)), "rho"),
     (dict(pcg_tol=0.0), "pcg_tol"),
+    (dict(sampler=2), "sampler"),
+    (dict(sampler=1, lanczos_steps=0), "lanczos_steps"),
+    (dict(sampler=1, lanczos_steps=8, precond_block=1), "blocks of 16, 32 or 64"),
+    (dict(part_overlap=[1, -1]), "part_overlap"),
 ])
 def test_invalid_arguments_rejected(lib, bad, msg):
     from paper_2309_05435_gb300 import qsel
