@@ -26,8 +26,9 @@ __global__ void __launch_bounds__(256) k_bj_cholinv(SellPattern pat, const doubl
                                                     const double *__restrict__ a0, const double *__restrict__ a1,
                                                     const uint8_t *__restrict__ obs, double obs_w, int n_s, int n_t,
                                                     int b, double *__restrict__ linv, int32_t *err_flag) {
-  __shared__ double S[64 * 65];
-  __shared__ double X[64 * 65];
+  extern __shared__ __align__(16) double smem_chol[];
+  double *S = smem_chol;              // [64][65]
+  double *X = smem_chol + 64 * 65;    // [64][65]
   assemble_diag_block(S, 65, pat, qs, a0, a1, obs, obs_w, n_s, n_t, blockIdx.x * b, b);
   // right-looking Cholesky, lower triangle of S
   for (int k = 0; k < b; ++k) {
@@ -75,8 +76,9 @@ template <bool TRANS>
 __global__ void __launch_bounds__(256) k_block_apply(const double *__restrict__ linv, int b, int n, int ld,
                                                      const double *__restrict__ x, double *__restrict__ y) {
   constexpr int PS = 66, RS = 66, CW = 64;
-  __shared__ __align__(16) double Bs[64 * PS];
-  __shared__ __align__(16) double xs[64 * RS];
+  extern __shared__ __align__(16) double smem_apply[];
+  double *Bs = smem_apply;            // [64][PS]
+  double *xs = smem_apply + 64 * PS;  // [64][RS]
   const int tid = threadIdx.x, rg = tid >> 5, cg = tid & 31;
   const int n_blocks = (n + b - 1) / b;
   const int n_tiles = (n + 63) / 64;
@@ -330,20 +332,33 @@ __global__ void __launch_bounds__(32) k_lz_quadrature(const LanczosArgs a, const
 // ---------------------------------------------------------------------------
 void launch_bj_cholinv(cudaStream_t s, const SellPattern &pat, const double *qs, const double *a0, const double *a1,
                        const uint8_t *obs, double obs_w, int n_s, int n_t, int b, double *linv, int32_t *err_flag) {
+  constexpr int smem = 2 * 64 * 65 * (int)sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_bj_cholinv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
   ++g_launch_count;
   const int nblk = (n_s * n_t + b - 1) / b;
-  k_bj_cholinv<<<nblk, 256, 0, s>>>(pat, qs, a0, a1, obs, obs_w, n_s, n_t, b, linv, err_flag);
+  k_bj_cholinv<<<nblk, 256, smem, s>>>(pat, qs, a0, a1, obs, obs_w, n_s, n_t, b, linv, err_flag);
 }
 
 void launch_block_apply(cudaStream_t s, const double *linv, int b, int n, int ld, const double *x, double *y,
                         bool trans) {
+  constexpr int smem = 2 * 64 * 66 * (int)sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_block_apply<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_block_apply<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
   ++g_launch_count;
   const int tiles = (n + 63) / 64;
   const int grid = tiles < 152 * 4 ? tiles : 152 * 4;
   if (trans)
-    k_block_apply<true><<<grid, 256, 0, s>>>(linv, b, n, ld, x, y);
+    k_block_apply<true><<<grid, 256, smem, s>>>(linv, b, n, ld, x, y);
   else
-    k_block_apply<false><<<grid, 256, 0, s>>>(linv, b, n, ld, x, y);
+    k_block_apply<false><<<grid, 256, smem, s>>>(linv, b, n, ld, x, y);
 }
 
 void launch_lz_vec(cudaStream_t s, int mode, const LanczosArgs &a, const double *vprev, const double *v, double *w,
