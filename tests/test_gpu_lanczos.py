@@ -59,10 +59,11 @@ def test_mixed_dense_path_with_lanczos_samples(q):
 
 def test_samples_converge_to_exact_with_m(q):
     """Against the dense L^-T Q~^-1/2 z of the same noise: the error of the
-    GPU samples falls geometrically with the Krylov dimension."""
+    GPU samples falls geometrically with the Krylov dimension (cond(Q~) is
+    about 790 here with 16-row blocks: 0.52, 0.020, 1e-6 at m = 4, 40, 160)."""
     name = "overlap2"
     errs = []
-    for m in (4, 12, 40):
+    for m in (4, 40, 160):
         c, _ = _run(q, name, m, 16)
         X = q.qsel_debug_get_samples(c.ctx)
         if m == 4:
@@ -75,7 +76,7 @@ def test_samples_converge_to_exact_with_m(q):
             X_ex = Linv.T @ (U * lam ** -0.5) @ U.T @ o.philox_normals(c.seed, 0, c.model.n, c.k)
         errs.append(np.linalg.norm(X - X_ex) / np.linalg.norm(X_ex))
     print("Lanczos sample error by m:", errs)
-    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-6
+    assert errs[0] > errs[1] > errs[2] and errs[1] < 0.05 and errs[2] < 1e-5
 
 
 def test_lanczos_state_errors(q):
