@@ -92,6 +92,8 @@ def parse_args():
     ap.add_argument("--batch-models", type=int, default=64)
     ap.add_argument("--batch-streams", type=int, default=16)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--lanczos-eval", default=None,
+                    help="comma list of Krylov dimensions: the Lanczos sampler against PCG at the workload")
     return ap.parse_args()
 
 
@@ -779,8 +781,47 @@ def run_batch(args):
     }), flush=True)
 
 
+def run_lanczos_eval(args):
+    """The preconditioned Krylov sampler (Algorithm 5.1) against the PCG
+    perturbation sampler at the workload's fixed settings, mixed dense part:
+    per Krylov dimension m, one pass after one warm-up (CUDA events), the
+    sampler's share of it, and the RBMC error against the exact one-part
+    result (the same error definitions as the bench line)."""
+    import torch
+    from paper_2309_05435_gb300 import build, qsel
+    build.build()
+    w = qi.workload(args.workload)
+    mesh, mask = workload_inputs(w)
+    stream = torch.cuda.current_stream()
+    ref = qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma,
+                           w.theta, n_parts=1, overlap=0, n_samples=1, cuda_stream=stream.cuda_stream)
+    v_ex = qsel.qsel_diag_inv(ref)
+    t_ex = qsel.qsel_trace_grads(ref)
+    ref.close()
+    entries = [("pcg", 0)] + [("lanczos", int(m)) for m in args.lanczos_eval.split(",")]
+    for name, m in entries:
+        kw = dict(sampler=qsel.QSEL_SAMPLER_LANCZOS, lanczos_steps=m) if name == "lanczos" else {}
+        ctx = qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma,
+                               w.theta, n_parts=w.n_parts, overlap=w.overlap, n_samples=w.n_samples, seed=2000,
+                               precision=qsel.QSEL_MIXED, pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream, **kw)
+        for _ in range(2):
+            qsel.qsel_set_theta(ctx, w.theta)
+            v = qsel.qsel_diag_inv(ctx)
+            g = qsel.qsel_trace_grads(ctx)
+        st = qsel.qsel_stats(ctx)
+        ctx.close()
+        r = (v - v_ex) / v_ex
+        print(json.dumps({"sampler": name, "lanczos_steps": m, "workload": w.name, "ms_total": st["ms_total"],
+                          "ms_sampler": st["ms_rhs"] + st["ms_pcg"], "pcg_iterations": st["pcg_iterations"],
+                          "eps_diag_rms": float(np.sqrt(np.mean(r ** 2))),
+                          "eps_traces": [float(abs(a - b) / abs(b)) for a, b in zip(g, t_ex)]}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.lanczos_eval:
+        run_lanczos_eval(args)
+        return
     if args.batch:
         run_batch(args)
         return

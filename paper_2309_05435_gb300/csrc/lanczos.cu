@@ -113,7 +113,11 @@ __global__ void __launch_bounds__(256) k_block_apply(const double *__restrict__ 
       double z[8][2];
 #pragma unroll
       for (int a = 0; a < 8; ++a) z[a][0] = z[a][1] = 0.0;
-      for (int jj = 0; jj < b; ++jj) {
+      // B is triangular within its block: Linv is lower (j <= row), its
+      // transpose upper (j >= row); the zero half is skipped
+      const int j_lo = TRANS ? row0 - jb : 0;
+      const int j_hi = TRANS ? b : row0 + 8 - jb;
+      for (int jj = j_lo; jj < j_hi; ++jj) {
         const int jl = jb + jj;
         const double2 *pp = reinterpret_cast<const double2 *>(Bs + jl * PS + row0);
         double pv[8];
