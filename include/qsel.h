@@ -68,6 +68,12 @@ enum {
   QSEL_SAMPLER_LANCZOS = 1
 };
 
+/* Preconditioners of the sampler's PCG (qsel_options.preconditioner). */
+enum {
+  QSEL_PRECOND_BLOCK_JACOBI = 0,
+  QSEL_PRECOND_KRON = 1
+};
+
 /* Arithmetic of the pipeline. */
 enum {
   QSEL_FP64 = 0,      /* every kernel computes in IEEE binary64                  */
@@ -134,6 +140,15 @@ typedef struct {
                              (1): the preconditioned Krylov sampler of
                              Algorithm 5.1 (FP64; needs no factored form of Q)  */
   int32_t lanczos_steps;  /* Krylov dimension m of the Lanczos sampler, 1..1024 */
+  int32_t preconditioner; /* PCG preconditioner: QSEL_PRECOND_BLOCK_JACOBI (0,
+                             blocks of precond_block rows, Section 3.3) or
+                             QSEL_PRECOND_KRON (1): for m x m grid meshes
+                             (stiffness T (x) D + D (x) T of the unit grid,
+                             lumped mass D (x) D away from the corners), the
+                             prior with C ~= D (x) D plus the mean observation
+                             weight, inverted exactly in the basis of the 1-D
+                             eigenvectors (QSEL_EINVAL for other meshes; not
+                             in a batch)                                       */
   const int32_t *part_overlap;/* HOST array of n_parts overlaps n_l,p >= 0 (one per
                              part, read at qsel_create), or NULL: every part uses
                              the `overlap` argument.  Lets a planner
@@ -253,6 +268,10 @@ qsel_status qsel_debug_get_selinv_diag(const qsel_ctx *ctx, double *diag_out);
  * column s < n_samples (HOST, ld >= n_samples; beta[j] = ||w_j|| after step
  * j).  QSEL_ESTATE unless the last run used the Lanczos sampler. */
 qsel_status qsel_debug_get_lanczos(const qsel_ctx *ctx, double *alpha, double *beta, int32_t ld);
+/* Apply the context's PCG preconditioner to R (HOST, n x n_samples,
+ * row-major, leading dimension ld) at the current theta and write Z = M^-1 R
+ * (HOST, same layout).  FP64 contexts only (QSEL_ESTATE otherwise). */
+qsel_status qsel_debug_apply_precond(qsel_ctx *ctx, const double *R, double *Z, int32_t ld);
 
 /*
  * Allocation-free SPD inverse.  The paper has no counterpart: this entry point
@@ -405,7 +424,8 @@ qsel_status qsel_cv_plan(qsel_ctx *ctx, const qsel_cv *cv, const qsel_cv_plan_op
  *                opt->cuda_stream is the stream the graph is launched on
  *                (NULL: the batch creates its own; the legacy default stream
  *                cannot be captured).  profile_kernels and part_overlap must
- *                be 0 / NULL, sampler QSEL_SAMPLER_PCG.
+ *                be 0 / NULL, sampler QSEL_SAMPLER_PCG, preconditioner
+ *                QSEL_PRECOND_BLOCK_JACOBI.
  *   n_streams    1..64 streams in the pool.
  *   autotune     non-zero: for every grid size (n_s) the smallest model of
  *                that size is run with every block-Jacobi block in {16, 32,

@@ -104,6 +104,12 @@ struct qsel_ctx {
   cudaStream_t body_stream[2] = {nullptr, nullptr};  // capture streams of loop bodies
   int32_t *d_loop = nullptr;           // loop state (see launch_loop_init)
   double *d_tol2 = nullptr;            // inner tolerance of the refinement, squared
+  // Kronecker preconditioner (grid meshes)
+  bool kron = false;
+  int kron_m = 0;
+  double *d_kV = nullptr, *d_klam = nullptr, *d_kdh = nullptr, *d_kU = nullptr, *d_kmu = nullptr;
+  double kron_rho = -2.0;              // rho of the temporal eigenpairs on the device
+  KronOperator kop{};
   // Lanczos sampler (allocated on first use)
   struct {
     double *vec[3] = {nullptr, nullptr, nullptr};   // v_{j-1}, v_j, w (rotated)
@@ -181,6 +187,100 @@ static qsel_status finish(qsel_ctx *ctx, const Err &e) {
 // Creation: validation, spatial pattern (union of C, G and G C^-1 G), SELL-32,
 // partition (Algorithm 3 on whole slabs) and device allocation.
 // ---------------------------------------------------------------------------
+// Eigenpairs of a symmetric tridiagonal matrix (diagonal d, off-diagonal e,
+// e[i] coupling i and i + 1) by the implicit QL algorithm with Wilkinson
+// shifts; Z (row-major n x n) holds the eigenvectors as columns.
+static bool host_tridiag_eig(int n, std::vector<double> d, std::vector<double> e, std::vector<double> &evals,
+                             std::vector<double> &Z) {
+  e.resize(n, 0.0);
+  e[n - 1] = 0.0;
+  Z.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Z[(size_t)i * n + i] = 1.0;
+  for (int l = 0; l < n; ++l) {
+    int iter = 0;
+    for (;;) {
+      int mm = l;
+      for (; mm < n - 1; ++mm) {
+        const double dd = std::fabs(d[mm]) + std::fabs(d[mm + 1]);
+        if (std::fabs(e[mm]) <= 2.3e-16 * dd) break;
+      }
+      if (mm == l) break;
+      if (++iter > 60) return false;
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = std::hypot(g, 1.0);
+      g = d[mm] - d[l] + e[l] / (g + std::copysign(r, g));
+      double sn = 1.0, cs = 1.0, p = 0.0;
+      bool early = false;
+      for (int i = mm - 1; i >= l; --i) {
+        const double f = sn * e[i], b = cs * e[i];
+        r = std::hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {
+          d[i + 1] -= p;
+          e[mm] = 0.0;
+          early = true;
+          break;
+        }
+        sn = f / r;
+        cs = g / r;
+        g = d[i + 1] - p;
+        r = (d[i] - g) * sn + 2.0 * cs * b;
+        p = sn * r;
+        d[i + 1] = g + p;
+        g = cs * r - b;
+        for (int k = 0; k < n; ++k) {
+          const double z1 = Z[(size_t)k * n + i + 1], z0 = Z[(size_t)k * n + i];
+          Z[(size_t)k * n + i + 1] = sn * z0 + cs * z1;
+          Z[(size_t)k * n + i] = cs * z0 - sn * z1;
+        }
+      }
+      if (early) continue;
+      d[l] -= p;
+      e[l] = g;
+      e[mm] = 0.0;
+    }
+  }
+  evals = d;
+  return true;
+}
+
+// The mesh is the unit m x m grid of this library's FEM convention when
+// G = T (x) D + D (x) T (1-D Neumann stiffness T, D = diag(1/2, 1, .., 1, 1/2),
+// node index i m + j) and the lumped mass equals D (x) D away from the
+// corners.  Returns m, or 0 for other meshes.
+static int detect_grid(const qsel_model *m) {
+  const int n_s = m->n_s;
+  const int g = (int)std::lround(std::sqrt((double)n_s));
+  if (g < 2 || g * g != n_s) return 0;
+  auto D = [&](int i) { return (i == 0 || i == g - 1) ? 0.5 : 1.0; };
+  auto T = [&](int i, int j) {
+    if (i == j) return (i == 0 || i == g - 1) ? 1.0 : 2.0;
+    return (std::abs(i - j) == 1) ? -1.0 : 0.0;
+  };
+  for (int r = 0; r < n_s; ++r) {
+    const int i = r / g, j = r % g;
+    const bool corner = (i == 0 || i == g - 1) && (j == 0 || j == g - 1);
+    if (!corner && std::fabs(m->c_diag[r] - D(i) * D(j)) > 1e-12) return 0;
+    std::map<int, double> want;
+    for (int di = -1; di <= 1; ++di)
+      for (int dj = -1; dj <= 1; ++dj) {
+        const int i2 = i + di, j2 = j + dj;
+        if (i2 < 0 || i2 >= g || j2 < 0 || j2 >= g) continue;
+        const double v = T(i, i2) * (j == j2 ? D(j) : 0.0) + (i == i2 ? D(i) : 0.0) * T(j, j2);
+        if (v != 0.0) want[i2 * g + j2] = v;
+      }
+    std::map<int, double> have;
+    for (int p = m->g_rowptr[r]; p < m->g_rowptr[r + 1]; ++p) have[m->g_col[p]] += m->g_val[p];
+    for (auto &kv : have)
+      if (std::fabs(kv.second) > 1e-14 && !want.count(kv.first)) return 0;
+    for (auto &kv : want) {
+      auto it = have.find(kv.first);
+      if (it == have.end() || std::fabs(it->second - kv.second) > 1e-12) return 0;
+    }
+  }
+  return g;
+}
+
 static Err validate(const qsel_model *m, const qsel_theta *th, const qsel_partition *part,
                     int32_t overlap, const qsel_options *opt) {
   if (!m || !th || !opt) return fail(QSEL_EINVAL, "model, theta and options must not be NULL");
@@ -226,6 +326,11 @@ static Err validate(const qsel_model *m, const qsel_theta *th, const qsel_partit
   if (opt->control_variate != 0) return fail(QSEL_EINVAL, "control_variate must be 0");
   if (opt->tensor_passes != 0 && opt->tensor_passes != 1 && opt->tensor_passes != 3 && opt->tensor_passes != -1)
     return fail(QSEL_EINVAL, "tensor_passes must be 0, 1, 3 or -1");
+  if (opt->preconditioner != QSEL_PRECOND_BLOCK_JACOBI && opt->preconditioner != QSEL_PRECOND_KRON)
+    return fail(QSEL_EINVAL, "preconditioner must be QSEL_PRECOND_BLOCK_JACOBI or QSEL_PRECOND_KRON");
+  if (opt->preconditioner == QSEL_PRECOND_KRON && detect_grid(m) == 0)
+    return fail(QSEL_EINVAL, "QSEL_PRECOND_KRON needs the m x m grid mesh (stiffness T (x) D + D (x) T, lumped mass "
+                             "D (x) D away from the corners)");
   if (opt->sampler != QSEL_SAMPLER_PCG && opt->sampler != QSEL_SAMPLER_LANCZOS)
     return fail(QSEL_EINVAL, "sampler must be QSEL_SAMPLER_PCG or QSEL_SAMPLER_LANCZOS");
   if (opt->sampler == QSEL_SAMPLER_LANCZOS) {
@@ -241,6 +346,56 @@ template <typename T>
 static Err upload(qsel_ctx *c, T **dst, const std::vector<T> &src) {
   TRY(c->alloc(dst, src.size()));
   if (!src.empty()) QSEL_CUDA_TRY(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return ok();
+}
+
+static Err kron_setup(qsel_ctx *c, const qsel_model *m) {
+  const int g = detect_grid(m);   // checked in validate
+  // scaled 1-D stiffness D^-1/2 T D^-1/2: diagonal 2, off-diagonal -1 / sqrt(D_i D_i+1)
+  std::vector<double> d(g, 2.0), e(g, 0.0), dh(g), lam, V;
+  for (int i = 0; i < g; ++i) dh[i] = (i == 0 || i == g - 1) ? std::sqrt(2.0) : 1.0;
+  for (int i = 0; i + 1 < g; ++i) e[i] = -dh[i] * dh[i + 1];
+  if (!host_tridiag_eig(g, d, e, lam, V)) return fail(QSEL_EINVAL, "grid eigendecomposition did not converge");
+  TRY(upload(c, &c->d_kV, V));
+  TRY(upload(c, &c->d_klam, lam));
+  TRY(upload(c, &c->d_kdh, dh));
+  TRY(c->alloc(&c->d_kU, (size_t)c->n_t * c->n_t));
+  TRY(c->alloc(&c->d_kmu, (size_t)c->n_t));
+  c->kron = true;
+  c->kron_m = g;
+  return ok();
+}
+
+// Temporal eigenpairs of Q_t (recomputed when rho changes) and the scalars of
+// the current theta.
+static Err kron_prepare(qsel_ctx *c) {
+  const double rho = 1.0 / (1.0 + std::exp(-c->theta.logit_rho));
+  const int n_t = c->n_t;
+  if (rho != c->kron_rho) {
+    const double om = 1.0 - rho * rho;
+    std::vector<double> d(n_t), e(n_t, 0.0), mu, U;
+    for (int t = 0; t < n_t; ++t) {
+      const double R = (n_t == 1) ? om : ((t == 0 || t == n_t - 1) ? 1.0 : 1.0 + rho * rho);
+      d[t] = R / om;
+      if (t + 1 < n_t) e[t] = -rho / om;
+    }
+    if (!host_tridiag_eig(n_t, d, e, mu, U)) return fail(QSEL_EINVAL, "temporal eigendecomposition did not converge");
+    QSEL_CUDA_TRY(cudaMemcpy(c->d_kU, U.data(), U.size() * sizeof(double), cudaMemcpyHostToDevice));
+    QSEL_CUDA_TRY(cudaMemcpy(c->d_kmu, mu.data(), mu.size() * sizeof(double), cudaMemcpyHostToDevice));
+    c->kron_rho = rho;
+  }
+  KronOperator &k = c->kop;
+  k.m = c->kron_m;
+  k.n_t = n_t;
+  k.ld = c->ld;
+  k.V = c->d_kV;
+  k.U = c->d_kU;
+  k.dh = c->d_kdh;
+  k.lam = c->d_klam;
+  k.mu = c->d_kmu;
+  k.kappa2 = std::exp(2.0 * c->theta.log_kappa);
+  k.tau = std::exp(c->theta.log_tau);
+  k.omega = (double)c->n_obs / (double)c->n * c->obs_w;
   return ok();
 }
 
@@ -328,6 +483,8 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   c->n_obs = n_obs;
   TRY(upload(c, &c->d_obs, mask));
   TRY(upload(c, &c->d_obs_index, oidx));
+
+  if (c->opt.preconditioner == QSEL_PRECOND_KRON) TRY(kron_setup(c, m));
 
   // time coefficients
   double *tcb;
@@ -560,7 +717,7 @@ static Err pcg_solve(qsel_ctx *c, const PcgVec<T> &v, const T *pblk, double tol,
   QSEL_CUDA_TRY(cudaMemsetAsync(v.x, 0, vbytes, s));
   QSEL_CUDA_TRY(cudaMemsetAsync(v.p, 0, vbytes, s));
   QSEL_CUDA_TRY(cudaMemsetAsync(v.alpha, 0, (size_t)c->ld * sizeof(double), s));
-  launch_pcg_update<T>(s, v, pblk, c->bsize);
+  launch_pcg_update<T>(s, v, pblk, c->bsize, c->kron ? &c->kop : nullptr);
   launch_pcg_reduce_beta<T>(s, v, tol, 1);
   launch_pcg_p_update<T>(s, v);
   BtSpmmArgs<T> a{};
@@ -588,7 +745,7 @@ static Err pcg_solve(qsel_ctx *c, const PcgVec<T> &v, const T *pblk, double tol,
     for (int b = 0; b < batch; ++b) {
       launch_bt_spmm<T>(s, a);
       launch_pcg_reduce_alpha<T>(s, v);
-      launch_pcg_update<T>(s, v, pblk, c->bsize);
+      launch_pcg_update<T>(s, v, pblk, c->bsize, c->kron ? &c->kop : nullptr);
       launch_pcg_reduce_beta<T>(s, v, tol, 0);
       launch_pcg_p_update<T>(s, v);
     }
@@ -620,10 +777,12 @@ static Err run_sampler(qsel_ctx *c) {
   c->have_rhs = true;
   QSEL_CUDA_TRY(cudaEventRecord(c->ev[1], s));
   const size_t vec = (size_t)c->n * c->ld;
+  if (c->kron) TRY(kron_prepare(c));
   if (!c->mixed) {
     double *pblk = static_cast<double *>(c->d_pblk);
-    launch_jacobi_setup<double>(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
-                                c->bsize, pblk, c->d_err);
+    if (!c->kron)
+      launch_jacobi_setup<double>(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
+                                  c->bsize, pblk, c->d_err);
     QSEL_CUDA_TRY(cudaMemcpyAsync(c->d_r, c->d_R, vec * sizeof(double), cudaMemcpyDeviceToDevice, s));
     PcgVec<double> v = make_pcg<double>(c, c->d_X, c->d_r, c->d_zv, c->d_p, c->d_q);
     int it = 0;
@@ -638,8 +797,9 @@ static Err run_sampler(qsel_ctx *c) {
     return ok();
   }
   float *pblk = static_cast<float *>(c->d_pblk);
-  launch_jacobi_setup<float>(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
-                             c->bsize, pblk, c->d_err);
+  if (!c->kron)
+    launch_jacobi_setup<float>(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
+                               c->bsize, pblk, c->d_err);
   PcgVec<float> v = make_pcg<float>(c, c->f_x, c->f_r, c->f_z, c->f_p, c->f_q);
   QSEL_CUDA_TRY(cudaMemsetAsync(c->d_X, 0, vec * sizeof(double), s));
   QSEL_CUDA_TRY(cudaMemsetAsync(c->d_q, 0, vec * sizeof(double), s));
@@ -736,7 +896,7 @@ static void pcg_start(qsel_ctx *c, cudaStream_t s, const PcgVec<T> &v, const T *
   cudaMemsetAsync(v.x, 0, vbytes, s);
   cudaMemsetAsync(v.p, 0, vbytes, s);
   cudaMemsetAsync(v.alpha, 0, (size_t)c->ld * sizeof(double), s);
-  launch_pcg_update<T>(s, v, pblk, c->bsize);
+  launch_pcg_update<T>(s, v, pblk, c->bsize, c->kron ? &c->kop : nullptr);
   launch_pcg_reduce_beta<T>(s, v, tol, 1);
   launch_pcg_p_update<T>(s, v);
 }
@@ -760,7 +920,7 @@ static void pcg_steps(qsel_ctx *c, cudaStream_t s, const PcgVec<T> &v, const T *
   for (int b = 0; b < count; ++b) {
     launch_bt_spmm<T>(s, a);
     launch_pcg_reduce_alpha<T>(s, v);
-    launch_pcg_update<T>(s, v, pblk, c->bsize);
+    launch_pcg_update<T>(s, v, pblk, c->bsize, c->kron ? &c->kop : nullptr);
     launch_pcg_reduce_beta<T>(s, v, tol, 0);
     launch_pcg_p_update<T>(s, v);
   }
@@ -1901,9 +2061,10 @@ qsel_status qsel_create_batch(qsel_batch **out, int32_t n_models, const qsel_mod
     g_create_error = "qsel_create_batch: n_models >= 1, non-NULL arrays and 1 <= n_streams <= 64 required";
     return QSEL_EINVAL;
   }
-  if (opt->profile_kernels || opt->part_overlap || opt->sampler != QSEL_SAMPLER_PCG) {
-    g_create_error = "qsel_create_batch: profile_kernels, part_overlap and the Lanczos sampler are not available "
-                     "in a batch";
+  if (opt->profile_kernels || opt->part_overlap || opt->sampler != QSEL_SAMPLER_PCG ||
+      opt->preconditioner != QSEL_PRECOND_BLOCK_JACOBI) {
+    g_create_error = "qsel_create_batch: profile_kernels, part_overlap, the Lanczos sampler and the Kronecker "
+                     "preconditioner are not available in a batch";
     return QSEL_EINVAL;
   }
   for (int i = 0; i < n_models; ++i) {
@@ -2138,6 +2299,35 @@ void qsel_batch_destroy(qsel_batch *b) {
   if (!b) return;
   if (b->main) cudaStreamSynchronize(b->main);
   delete b;
+}
+
+qsel_status qsel_debug_apply_precond(qsel_ctx *ctx, const double *R, double *Z, int32_t ld) {
+  if (!ctx) return QSEL_EINVAL;
+  qsel_ctx *c = ctx;
+  if (!R || !Z || ld < c->k) return finish(c, fail(QSEL_EINVAL, "NULL buffer or ld < n_samples"));
+  if (c->mixed) return finish(c, fail(QSEL_ESTATE, "the preconditioner hook needs an FP64 context"));
+  cudaStream_t s = c->stream;
+  Err e = run_model(c);
+  if (e.code == 0 && c->kron) e = kron_prepare(c);
+  if (e.code) return finish(c, e);
+  double *pblk = static_cast<double *>(c->d_pblk);
+  if (!c->kron)
+    launch_jacobi_setup<double>(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
+                                c->bsize, pblk, c->d_err);
+  const size_t vec = (size_t)c->n * c->ld;
+  cudaError_t ce = cudaMemsetAsync(c->d_r, 0, vec * sizeof(double), s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpy2DAsync(c->d_r, (size_t)c->ld * sizeof(double), R, (size_t)ld * sizeof(double),
+                           (size_t)c->k * sizeof(double), c->n, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(c->d_scal, 0, (size_t)c->ld * sizeof(double), s);   // alpha = 0
+  if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "preconditioner input", __FILE__, __LINE__));
+  PcgVec<double> v = make_pcg<double>(c, c->d_X, c->d_r, c->d_zv, c->d_p, c->d_q);
+  launch_pcg_update<double>(s, v, pblk, c->bsize, c->kron ? &c->kop : nullptr);
+  ce = cudaMemcpy2DAsync(Z, (size_t)ld * sizeof(double), c->d_zv, (size_t)c->ld * sizeof(double),
+                         (size_t)c->k * sizeof(double), c->n, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "preconditioner output", __FILE__, __LINE__));
+  return QSEL_OK;
 }
 
 qsel_status qsel_debug_get_lanczos(const qsel_ctx *ctx, double *alpha, double *beta, int32_t ld) {

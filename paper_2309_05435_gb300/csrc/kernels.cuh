@@ -147,8 +147,12 @@ void launch_jacobi_setup(cudaStream_t s, const SellPattern &pat, const double *q
                          int bsize, T *pblk, int32_t *err_flag);
 // Grid of the PCG update (also the number of its partial rows, PcgVec::n_tiles).
 int pcg_update_grid(int n);
+struct KronOperator;
+// x += alpha p, r -= alpha q, then z = P r (block Jacobi with pblk, bsize) or,
+// with kron, z = M^-1 r (the Kronecker preconditioner, q as scratch); the
+// per-column partial sums <r, z>, <r, r>.
 template <typename T>
-void launch_pcg_update(cudaStream_t s, const PcgVec<T> &v, const T *pblk, int bsize);
+void launch_pcg_update(cudaStream_t s, const PcgVec<T> &v, const T *pblk, int bsize, const KronOperator *kron = nullptr);
 template <typename T>
 void launch_pcg_reduce_alpha(cudaStream_t s, const PcgVec<T> &v);
 template <typename T>
@@ -326,6 +330,32 @@ void launch_sum(cudaStream_t s, double *out, const double *a, const double *b, i
 // per part: sum over own rows of ((m4 - m2^2) / (k - 1)) / v^2
 void launch_part_error_sums(cudaStream_t s, const double *m2, const double *m4, const double *v,
                             const int32_t *slab_start_dev, int n_parts, int n_s, int k, double *out);
+
+// ---------------------------------------------------------------- kron.cu
+enum KronMode { KRON_NONE = 0, KRON_IN_DH = 1, KRON_OUT_DH = 2, KRON_OUT_SPEC = 3 };
+// One pass y_g = op(B) x_g over the groups g of rows base(g) + k kstride.
+struct KronPass {
+  const double *B;          // dim x dim, row-major
+  int dim, trans, mode, m;
+  int64_t kstride;          // rows between consecutive k
+  int n_outer, n_inner;
+  int64_t outer_stride, inner_stride;   // base(g) = (g / n_inner) outer + (g % n_inner) inner
+  int ld;
+  const double *dh, *lam, *mu;
+  double kappa2, tau, omega;
+};
+// The preconditioner's factors (device arrays) and scalars for one theta.
+struct KronOperator {
+  int m, n_t, ld;
+  const double *V, *U, *dh, *lam, *mu;
+  double kappa2, tau, omega;
+};
+template <typename T>
+void launch_kron_pass(cudaStream_t s, const KronPass &p, const T *x, T *y);
+template <typename T>
+void launch_kron_apply(cudaStream_t s, const KronOperator &op, const T *r, T *q, T *z);
+template <typename T>
+void launch_pcg_dots(cudaStream_t s, const PcgVec<T> &v);
 
 // ---------------------------------------------------------------- lanczos.cu
 struct LanczosArgs {

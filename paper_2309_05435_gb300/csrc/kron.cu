@@ -1,0 +1,228 @@
+// Kronecker preconditioner of the sampler's PCG for grid meshes:
+//   M^-1 = (I (x) Dh (x) Dh) (U (x) V (x) V) diag(1 / (tau mu_k (kappa^2 +
+//          lambda_a + lambda_b)^2 + omega)) (U (x) V (x) V)^T (I (x) Dh (x) Dh)
+// with V, lambda the eigenpairs of the scaled 1-D Neumann stiffness
+// D^-1/2 T D^-1/2, Dh = D^-1/2, U, mu those of Q_t, omega the mean
+// observation weight (the prior of Sections 2.1-2.2 with the lumped mass taken
+// as D (x) D, plus omega C~ for A^T A / sigma^2).
+//
+// Applying it is six passes of one batched, strided small-matrix product:
+// for every group g (the two indices not transformed) y_g = B x_g or B^T x_g,
+// where x_g gathers the rows base(g) + k * kstride, k < dim, of the n x ld
+// block (all samples at once).  A CTA computes a 64-row x 64-column output
+// tile, looping over 64-wide K slices staged in shared memory; each thread
+// accumulates an 8 x 2 register tile.  The diagonal scalings are fused into
+// the passes that touch them.
+#include "kernels.cuh"
+
+namespace qsel {
+
+constexpr int kKT = 64;     // output rows / K slice per tile
+constexpr int kKC = 64;     // columns per tile
+
+template <typename T>
+constexpr int kron_smem() {
+  return (kKT * (kKT + 2) + kKT * (kKC + 2)) * (int)sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_kron_pass(const KronPass p, const T *__restrict__ x, T *__restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem_kron[];
+  auto Bs = reinterpret_cast<T(*)[kKT + 2]>(smem_kron);                                   // Bs[k][o] = op(B)[o][k]
+  auto xs = reinterpret_cast<T(*)[kKC + 2]>(smem_kron + kKT * (kKT + 2) * sizeof(T));
+  const int tid = threadIdx.x, rg = tid >> 5, cg = tid & 31;
+  const int row_tiles = (p.dim + kKT - 1) / kKT;
+  const int col_tiles = p.ld / kKC;
+  const int64_t n_groups = (int64_t)p.n_outer * p.n_inner;
+  const int64_t items = n_groups * row_tiles * col_tiles;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int ct = (int)(it % col_tiles);
+    const int64_t rest = it / col_tiles;
+    const int rt = (int)(rest % row_tiles);
+    const int64_t g = rest / row_tiles;
+    const int64_t base = (g / p.n_inner) * p.outer_stride + (g % p.n_inner) * p.inner_stride;
+    const int g_inner = (int)(g % p.n_inner);
+    const int o0 = rt * kKT, c0 = ct * kKC;
+    T acc[8][2];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) acc[a][0] = acc[a][1] = T(0);
+    for (int k0 = 0; k0 < p.dim; k0 += kKT) {
+      __syncthreads();
+      for (int e = tid; e < kKT * kKT; e += blockDim.x) {
+        const int kk = e / kKT, oo = e - kk * kKT;
+        const int o = o0 + oo, k = k0 + kk;
+        T v = T(0);
+        if (o < p.dim && k < p.dim) v = (T)(p.trans ? p.B[(int64_t)k * p.dim + o] : p.B[(int64_t)o * p.dim + k]);
+        Bs[kk][oo] = v;
+      }
+      for (int e = tid; e < kKT * kKC / 2; e += blockDim.x) {
+        const int kk = e / (kKC / 2), q = e - kk * (kKC / 2);
+        const int k = k0 + kk;
+        T v0 = T(0), v1 = T(0);
+        if (k < p.dim) {
+          const T *src = x + (base + (int64_t)k * p.kstride) * p.ld + c0 + 2 * q;
+          v0 = src[0];
+          v1 = src[1];
+          if (p.mode == KRON_IN_DH) {
+            const T sc = (T)(p.dh[k] * p.dh[g_inner]);
+            v0 *= sc;
+            v1 *= sc;
+          }
+        }
+        xs[kk][2 * q] = v0;
+        xs[kk][2 * q + 1] = v1;
+      }
+      __syncthreads();
+      const int kmax = min(kKT, p.dim - k0);
+      for (int kk = 0; kk < kmax; ++kk) {
+        T bv[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) bv[a] = Bs[kk][rg * 8 + a];
+        const T x0 = xs[kk][2 * cg], x1 = xs[kk][2 * cg + 1];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          acc[a][0] = fma(bv[a], x0, acc[a][0]);
+          acc[a][1] = fma(bv[a], x1, acc[a][1]);
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int o = o0 + rg * 8 + a;
+      if (o >= p.dim) continue;
+      T sc = T(1);
+      if (p.mode == KRON_OUT_DH) {
+        sc = (T)(p.dh[o] * p.dh[g_inner]);
+      } else if (p.mode == KRON_OUT_SPEC) {
+        // group = spatial index s = a m + b, o = temporal index
+        const int sa = g_inner / p.m, sb = g_inner - sa * p.m;
+        const double s2 = p.kappa2 + p.lam[sa] + p.lam[sb];
+        sc = (T)(1.0 / (p.tau * p.mu[o] * s2 * s2 + p.omega));
+      }
+      T *dst = y + (base + (int64_t)o * p.kstride) * p.ld + c0 + 2 * cg;
+      dst[0] = acc[a][0] * sc;
+      dst[1] = acc[a][1] * sc;
+    }
+  }
+}
+
+template <typename T>
+void launch_kron_pass(cudaStream_t s, const KronPass &p, const T *x, T *y) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_kron_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kron_smem<T>());
+    attr = true;
+  }
+  ++g_launch_count;
+  const int64_t items = (int64_t)p.n_outer * p.n_inner * ((p.dim + kKT - 1) / kKT) * (p.ld / kKC);
+  const int grid = (int)std::min<int64_t>(items, 152 * 6);
+  k_kron_pass<T><<<grid, 256, kron_smem<T>(), s>>>(p, x, y);
+}
+template void launch_kron_pass<double>(cudaStream_t, const KronPass &, const double *, double *);
+template void launch_kron_pass<float>(cudaStream_t, const KronPass &, const float *, float *);
+
+// partial_a[cta][c] = sum r z, partial_b[cta][c] = sum r r over the CTA's rows
+// (the layout the PCG's beta reduction reads), columns in 64-wide chunks.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pcg_dots(PcgVec<T> v) {
+  __shared__ double red[2][4][64];
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+  const int64_t rows_per = (v.n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = blockIdx.x * rows_per, r1 = min((int64_t)v.n, r0 + rows_per);
+  for (int c0 = 0; c0 < v.ld; c0 += 64) {
+    const int c = c0 + tx;
+    T sa = T(0), sb = T(0);
+    for (int64_t r = r0 + ty; r < r1; r += 4) {
+      const T rv = v.r[r * v.ld + c];
+      sa = fma(rv, v.z[r * v.ld + c], sa);
+      sb = fma(rv, rv, sb);
+    }
+    red[0][ty][tx] = (double)sa;
+    red[1][ty][tx] = (double)sb;
+    __syncthreads();
+    if (ty == 0) {
+      v.partial_a[(int64_t)blockIdx.x * v.ld + c] = red[0][0][tx] + red[0][1][tx] + red[0][2][tx] + red[0][3][tx];
+      v.partial_b[(int64_t)blockIdx.x * v.ld + c] = red[1][0][tx] + red[1][1][tx] + red[1][2][tx] + red[1][3][tx];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void launch_pcg_dots(cudaStream_t s, const PcgVec<T> &v) {
+  ++g_launch_count;
+  k_pcg_dots<T><<<v.n_tiles, 256, 0, s>>>(v);
+}
+template void launch_pcg_dots<double>(cudaStream_t, const PcgVec<double> &);
+template void launch_pcg_dots<float>(cudaStream_t, const PcgVec<float> &);
+
+// z = M^-1 r: six passes, ping-pong between the scratch q and z (q is free
+// once the AXPY has consumed Q p); the result ends in z.
+template <typename T>
+void launch_kron_apply(cudaStream_t s, const KronOperator &op, const T *r, T *q, T *z) {
+  const int m = op.m, n_s = m * m, n_t = op.n_t;
+  KronPass p{};
+  p.ld = op.ld;
+  p.m = m;
+  p.dh = op.dh;
+  p.lam = op.lam;
+  p.mu = op.mu;
+  p.kappa2 = 0.0;
+  p.tau = 1.0;
+  p.omega = 0.0;
+  // spatial index s = i m + j inside slab t (row t n_s + s)
+  KronPass over_i = p, over_j = p, over_t = p;
+  over_i.B = op.V;
+  over_i.dim = m;
+  over_i.kstride = m;
+  over_i.n_outer = n_t;
+  over_i.outer_stride = n_s;
+  over_i.n_inner = m;
+  over_i.inner_stride = 1;
+  over_j.B = op.V;
+  over_j.dim = m;
+  over_j.kstride = 1;
+  over_j.n_outer = n_t;
+  over_j.outer_stride = n_s;
+  over_j.n_inner = m;
+  over_j.inner_stride = m;
+  over_t.B = op.U;
+  over_t.dim = n_t;
+  over_t.kstride = n_s;
+  over_t.n_outer = 1;
+  over_t.outer_stride = 0;
+  over_t.n_inner = n_s;
+  over_t.inner_stride = 1;
+  ProfScope ps_(s, PROF_PRECOND);
+  KronPass a = over_i;          // (V^T over i) after the input scaling Dh (x) Dh
+  a.trans = 1;
+  a.mode = KRON_IN_DH;
+  launch_kron_pass<T>(s, a, r, q);
+  KronPass b = over_j;          // V^T over j
+  b.trans = 1;
+  b.mode = KRON_NONE;
+  launch_kron_pass<T>(s, b, q, z);
+  KronPass c = over_t;          // U^T over t, then the spectral scaling
+  c.trans = 1;
+  c.mode = KRON_OUT_SPEC;
+  c.kappa2 = op.kappa2;
+  c.tau = op.tau;
+  c.omega = op.omega;
+  launch_kron_pass<T>(s, c, z, q);
+  KronPass d = over_t;          // U over t
+  d.trans = 0;
+  d.mode = KRON_NONE;
+  launch_kron_pass<T>(s, d, q, z);
+  KronPass e = over_j;          // V over j
+  e.trans = 0;
+  e.mode = KRON_NONE;
+  launch_kron_pass<T>(s, e, z, q);
+  KronPass f = over_i;          // V over i, then Dh (x) Dh
+  f.trans = 0;
+  f.mode = KRON_OUT_DH;
+  launch_kron_pass<T>(s, f, q, z);
+}
+template void launch_kron_apply<double>(cudaStream_t, const KronOperator &, const double *, double *, double *);
+template void launch_kron_apply<float>(cudaStream_t, const KronOperator &, const float *, float *, float *);
+
+}  // namespace qsel

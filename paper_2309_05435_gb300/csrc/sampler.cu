@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(256) k_pcg_precond(PcgVec<T> v, const T *__res
 }
 
 template <typename T>
-void launch_pcg_update(cudaStream_t s, const PcgVec<T> &v, const T *pblk, int bsize) {
+void launch_pcg_update(cudaStream_t s, const PcgVec<T> &v, const T *pblk, int bsize, const KronOperator *kron) {
   // 128-column chunks for FP32 when they divide ld, else 64
   constexpr int CWF = std::is_same<T, float>::value ? 128 : 64;
   static bool attr_set = false;
@@ -591,6 +591,12 @@ void launch_pcg_update(cudaStream_t s, const PcgVec<T> &v, const T *pblk, int bs
     ProfScope ps_(s, PROF_PCGVEC);
     k_pcg_axpy<T><<<grid, 256, 0, s>>>(v);
   }
+  if (kron) {
+    --g_launch_count;   // counted by the launchers below
+    launch_kron_apply<T>(s, *kron, v.r, v.q, v.z);
+    launch_pcg_dots<T>(s, v);
+    return;
+  }
   // algorithmic work: 2 b FLOPs per element of z (b = 1: one multiply)
   ProfScope ps_(s, PROF_PRECOND, (bsize > 1 ? 2.0 * bsize : 1.0) * (double)v.n * v.ld);
   if (v.ld % CWF == 0)
@@ -598,8 +604,10 @@ void launch_pcg_update(cudaStream_t s, const PcgVec<T> &v, const T *pblk, int bs
   else
     k_pcg_precond<T, 64><<<v.n_tiles, 256, PrecondSmem<T, 64>::bytes, s>>>(v, pblk, bsize);
 }
-template void launch_pcg_update<double>(cudaStream_t, const PcgVec<double> &, const double *, int);
-template void launch_pcg_update<float>(cudaStream_t, const PcgVec<float> &, const float *, int);
+template void launch_pcg_update<double>(cudaStream_t, const PcgVec<double> &, const double *, int,
+                                        const KronOperator *);
+template void launch_pcg_update<float>(cudaStream_t, const PcgVec<float> &, const float *, int,
+                                       const KronOperator *);
 
 // Column sums of per-CTA partial rows: 8 row groups x 32 columns per block,
 // fixed order within each group and across groups.

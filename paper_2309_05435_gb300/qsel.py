@@ -16,6 +16,8 @@ QSEL_FP64 = 0
 QSEL_MIXED = 1
 QSEL_SAMPLER_PCG = 0
 QSEL_SAMPLER_LANCZOS = 1
+QSEL_PRECOND_BLOCK_JACOBI = 0
+QSEL_PRECOND_KRON = 1
 
 _STATUS = {0: "QSEL_OK", 1: "QSEL_EINVAL", 2: "QSEL_ENOMEM", 3: "QSEL_ECUDA", 4: "QSEL_ENOTSPD",
            5: "QSEL_ENOCONV", 6: "QSEL_ETIMEOUT", 7: "QSEL_ESTATE"}
@@ -41,7 +43,8 @@ class qsel_options(ctypes.Structure):
     _fields_ = [("n_samples", c_int32), ("seed", c_uint64), ("precision", c_int32), ("pcg_tol", c_double),
                 ("pcg_max_iter", c_int32), ("precond_block", c_int32), ("control_variate", c_int32),
                 ("cuda_stream", c_void_p), ("profile_kernels", c_int32), ("tensor_passes", c_int32),
-                ("sampler", c_int32), ("lanczos_steps", c_int32), ("part_overlap", POINTER(c_int32))]
+                ("sampler", c_int32), ("lanczos_steps", c_int32), ("preconditioner", c_int32),
+                ("part_overlap", POINTER(c_int32))]
 
 
 class qsel_batch_info_t(ctypes.Structure):
@@ -85,7 +88,8 @@ def _fields(s) -> dict:
 
 EXPORTED = ["qsel_create", "qsel_set_theta", "qsel_diag_inv", "qsel_trace_grads", "qsel_stats",
             "qsel_debug_set_samples", "qsel_debug_get_samples", "qsel_debug_get_rhs",
-            "qsel_debug_get_selinv_diag", "qsel_debug_get_lanczos", "qsel_spd_inverse_noalloc",
+            "qsel_debug_get_selinv_diag", "qsel_debug_get_lanczos", "qsel_debug_apply_precond",
+            "qsel_spd_inverse_noalloc",
             "qsel_error_estimate",
             "qsel_cv_create", "qsel_cv_set_params", "qsel_cv_get_params", "qsel_cv_predict", "qsel_cv_grad",
             "qsel_cv_train", "qsel_cv_features", "qsel_cv_targets", "qsel_cv_plan",
@@ -120,6 +124,7 @@ def load_library(path: str = LIB_PATH):
     lib.qsel_debug_get_rhs.argtypes = [c_void_p, P(c_double), c_int32]
     lib.qsel_debug_get_selinv_diag.argtypes = [c_void_p, P(c_double)]
     lib.qsel_debug_get_lanczos.argtypes = [c_void_p, P(c_double), P(c_double), c_int32]
+    lib.qsel_debug_apply_precond.argtypes = [c_void_p, P(c_double), P(c_double), c_int32]
     lib.qsel_spd_inverse_noalloc.argtypes = [c_void_p, c_int32, c_int32, c_void_p]
     lib.qsel_error_estimate.argtypes = [c_void_p, P(c_double), P(c_double)]
     lib.qsel_cv_create.argtypes = [P(c_void_p), c_uint64, c_void_p]
@@ -206,7 +211,7 @@ def qsel_create(n_s, n_t, c_diag, g_rowptr, g_col, g_val, obs_mask, sigma, theta
                 slab_start=None, overlap=0, n_samples=64, seed=0, precision=QSEL_FP64, pcg_tol=1e-10,
                 pcg_max_iter=20000, precond_block=0, control_variate=0, cuda_stream=None,
                 profile_kernels=0, tensor_passes=0, part_overlap=None, sampler=QSEL_SAMPLER_PCG,
-                lanczos_steps=0) -> Context:
+                lanczos_steps=0, preconditioner=QSEL_PRECOND_BLOCK_JACOBI) -> Context:
     """Create a context from host arrays (copied by the library)."""
     lib = load_library()
     c = np.ascontiguousarray(c_diag, dtype=np.float64)
@@ -229,7 +234,7 @@ def qsel_create(n_s, n_t, c_diag, g_rowptr, g_col, g_val, obs_mask, sigma, theta
     opt = qsel_options(int(n_samples), int(seed), int(precision), float(pcg_tol), int(pcg_max_iter),
                        int(precond_block), int(control_variate),
                        c_void_p(int(cuda_stream)) if cuda_stream else None, int(profile_kernels),
-                       int(tensor_passes), int(sampler), int(lanczos_steps),
+                       int(tensor_passes), int(sampler), int(lanczos_steps), int(preconditioner),
                        _ptr(po, c_int32) if po is not None else None)
     h = c_void_p()
     st = lib.qsel_create(ctypes.byref(h), ctypes.byref(model), ctypes.byref(th), ctypes.byref(part),
@@ -304,6 +309,17 @@ def qsel_debug_get_lanczos(ctx: Context, steps: int):
     _check(load_library().qsel_debug_get_lanczos(ctx.handle, _ptr(a, c_double), _ptr(b, c_double), ctx.k),
            ctx.handle)
     return a, b
+
+
+def qsel_debug_apply_precond(ctx: Context, R: np.ndarray) -> np.ndarray:
+    """Z = M^-1 R with the context's PCG preconditioner (FP64 contexts)."""
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    if R.shape != (ctx.n, ctx.k):
+        raise ValueError(f"R must be {(ctx.n, ctx.k)}")
+    Z = np.empty_like(R)
+    _check(load_library().qsel_debug_apply_precond(ctx.handle, _ptr(R, c_double), _ptr(Z, c_double), ctx.k),
+           ctx.handle)
+    return Z
 
 
 def qsel_spd_inverse_noalloc(a, n: int, lda: int | None = None, cuda_stream=None):
@@ -459,7 +475,7 @@ def qsel_create_batch(models, thetas, partitions, overlaps, n_samples=128, seed=
     OV = np.ascontiguousarray(overlaps, dtype=np.int32)
     opt = qsel_options(int(n_samples), int(seed), int(precision), float(pcg_tol), int(pcg_max_iter),
                        int(precond_block), 0, c_void_p(int(cuda_stream)) if cuda_stream else None, 0,
-                       int(tensor_passes), QSEL_SAMPLER_PCG, 0, None)
+                       int(tensor_passes), QSEL_SAMPLER_PCG, 0, QSEL_PRECOND_BLOCK_JACOBI, None)
     h = c_void_p()
     st = lib.qsel_create_batch(ctypes.byref(h), n, M, TH, PA, _ptr(OV, c_int32), ctypes.byref(opt),
                                int(n_streams), int(bool(autotune)))

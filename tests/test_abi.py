@@ -76,3 +76,29 @@ def test_invalid_mesh_rejected(lib):
     col[5] = 10 ** 6
     with pytest.raises(qsel.QselError, match="g_col"):
         qsel.qsel_create(**dict(a, g_col=col))
+
+
+def test_kron_preconditioner_needs_a_grid(lib):
+    """QSEL_PRECOND_KRON is refused (before any GPU work) for a mesh that is
+    not the m x m grid: here the grid with its nodes renumbered."""
+    from paper_2309_05435_gb300 import qsel
+    w = qi.workload("grid16_nt8")
+    m = w.mesh()
+    perm = np.random.default_rng(0).permutation(w.n_s)
+    inv = np.argsort(perm)
+    G = np.zeros((w.n_s, w.n_s))
+    for r in range(w.n_s):
+        for p in range(m.g_rowptr[r], m.g_rowptr[r + 1]):
+            G[inv[r], inv[m.g_col[p]]] = m.g_val[p]
+    rp = np.zeros(w.n_s + 1, np.int32)
+    cols, vals = [], []
+    for r in range(w.n_s):
+        nz = np.flatnonzero(G[r])
+        cols += list(nz)
+        vals += list(G[r, nz])
+        rp[r + 1] = len(cols)
+    a = _args(c_diag=m.c_diag[perm], g_rowptr=rp, g_col=np.array(cols, np.int32), g_val=np.array(vals),
+              preconditioner=1)
+    with pytest.raises(qsel.QselError) as ei:
+        qsel.qsel_create(**a)
+    assert ei.value.status == 1 and "grid" in str(ei.value)
