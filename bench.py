@@ -50,6 +50,9 @@ GEMM64_DRAM_BYTES_PER_FLOP = 7.808e9 / 2.749e11
 # DRAM bytes of one rank-64 sweep update of a 4096^2 FP32 matrix on the tensor
 # cores (profiles/k_tc_gemm_grid64_nt16_mixed.md: 0.094 GB for 2 matrices)
 TC_SWEEP_DRAM_BYTES_PER_MATRIX = 0.094e9 / 2
+# planner's PCG cost per sample and node with the Kronecker preconditioner
+# (seconds; the library default describes 64-row block Jacobi)
+KRON_PCG_COST = 0.36e-8
 L2_BYTES = 126 * 2 ** 20
 
 
@@ -75,6 +78,11 @@ def parse_args():
                     help="planned = control-variate planner picks k and overlaps; fixed = workload settings")
     ap.add_argument("--target", type=float, default=0.01, help="RMS relative error target of the plan")
     ap.add_argument("--max-overlap", type=int, default=8)
+    ap.add_argument("--preconditioner", choices=["kron", "bj"], default="kron",
+                    help="PCG preconditioner of the chosen form: Kronecker grid (kron) or 64-row block Jacobi "
+                         "(bj); plain FP64 always uses block Jacobi, the paper's choice")
+    ap.add_argument("--cost-pcg", type=float, default=None,
+                    help="planner's PCG cost per sample and node in seconds (default: by preconditioner)")
     ap.add_argument("--margin", type=float, default=0.85,
                     help="the planner aims at margin * target (absorbs the prediction error)")
     ap.add_argument("--cv-train-thetas", type=int, default=32)
@@ -296,15 +304,20 @@ def run_native(args):
         if args.save_cv_params:
             np.save(args.save_cv_params, qsel.qsel_cv_get_params(net))
 
-    def make_ctx(precision, profile=1, k=None, part_overlap=None):
+    chosen_pc = qsel.QSEL_PRECOND_KRON if args.preconditioner == "kron" else qsel.QSEL_PRECOND_BLOCK_JACOBI
+    cost_pcg = args.cost_pcg if args.cost_pcg else (KRON_PCG_COST if args.preconditioner == "kron" else 0.0)
+
+    def make_ctx(precision, profile=1, k=None, part_overlap=None, preconditioner=None):
+        pc = chosen_pc if preconditioner is None else preconditioner
         return qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma,
                                 w.theta, n_parts=w.n_parts, overlap=w.overlap,
                                 n_samples=k if k else w.n_samples, seed=seed, precision=precision,
                                 pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream, profile_kernels=profile,
-                                part_overlap=part_overlap)
+                                part_overlap=part_overlap, preconditioner=pc)
 
     def make_plan(ctx):
-        return qsel.qsel_cv_plan(ctx, net, args.margin * args.target, max_overlap=args.max_overlap)
+        return qsel.qsel_cv_plan(ctx, net, args.margin * args.target, max_overlap=args.max_overlap,
+                                 cost_pcg=cost_pcg)
 
     plan = None
     k_run, po = w.n_samples, None
@@ -360,7 +373,7 @@ def run_native(args):
     v_fp64 = None
     grads64 = None
     if args.fp64_steps > 0 and (chosen_prec != qsel.QSEL_FP64 or planned):
-        ctx64 = make_ctx(qsel.QSEL_FP64, profile=0)
+        ctx64 = make_ctx(qsel.QSEL_FP64, profile=0, preconditioner=qsel.QSEL_PRECOND_BLOCK_JACOBI)
         out64 = torch.empty(w.n, dtype=torch.float64, device=dev)
         ms64, st64, _, grads64, err64 = timed(ctx64, out64, 1, args.fp64_steps)
         v_fp64 = out64.cpu().numpy()
@@ -424,7 +437,7 @@ def run_native(args):
             c2 = qsel.qsel_create(w.n_s, w.n_t, c_pin, rp_pin, gc_pin, gv_pin, mk_pin, w.sigma, w.theta,
                                   n_parts=w.n_parts, overlap=w.overlap, n_samples=k_run, seed=seed,
                                   precision=chosen_prec, pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream,
-                                  part_overlap=po)
+                                  part_overlap=po, preconditioner=chosen_pc)
             if planned:
                 p = make_plan(c2)
                 if p["n_samples"] != k_run or [int(x) for x in p["part_overlap"]] != po:
@@ -528,6 +541,7 @@ def run_native(args):
         if chosen_prec == qsel.QSEL_MIXED else "plain FP64 RBMC"
     if planned:
         form += f" + learned control variate planner (target {args.target:g} RMS relative error)"
+    form += ", Kronecker grid preconditioner" if args.preconditioner == "kron" else ", block-Jacobi preconditioner"
     result = {
         "metric": METRIC,
         "value": job_value_s(ms_total, args.steps, world),
