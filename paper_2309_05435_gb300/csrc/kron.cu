@@ -13,26 +13,35 @@
 // tile, looping over 64-wide K slices staged in shared memory; each thread
 // accumulates an 8 x 2 register tile.  The diagonal scalings are fused into
 // the passes that touch them.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace qsel {
 
 constexpr int kKT = 64;     // output rows / K slice per tile
-constexpr int kKC = 64;     // columns per tile
 
-template <typename T>
-constexpr int kron_smem() {
-  return (kKT * (kKT + 2) + kKT * (kKC + 2)) * (int)sizeof(T);
-}
+template <typename T, int CW>
+struct KronSmem {
+  static constexpr int BP = kKT + 16 / (int)sizeof(T);    // padded rows: 16-byte aligned
+  static constexpr int XP = CW + 16 / (int)sizeof(T);
+  static constexpr int bytes = (kKT * BP + kKT * XP) * (int)sizeof(T);
+};
 
-template <typename T>
+// CW columns per tile (64 or 128): each thread accumulates an 8-row x
+// (CW / 32)-column register tile from 16-byte shared loads.
+template <typename T, int CW>
 __global__ void __launch_bounds__(256) k_kron_pass(const KronPass p, const T *__restrict__ x, T *__restrict__ y) {
+  using SM = KronSmem<T, CW>;
+  constexpr int NC = CW / 32;
+  using V16 = typename std::conditional<std::is_same<T, float>::value, float4, double2>::type;
+  constexpr int E16 = 16 / (int)sizeof(T);
   extern __shared__ __align__(16) unsigned char smem_kron[];
-  auto Bs = reinterpret_cast<T(*)[kKT + 2]>(smem_kron);                                   // Bs[k][o] = op(B)[o][k]
-  auto xs = reinterpret_cast<T(*)[kKC + 2]>(smem_kron + kKT * (kKT + 2) * sizeof(T));
+  T *Bs = reinterpret_cast<T *>(smem_kron);                 // Bs[k * BP + o] = op(B)[o][k]
+  T *xs = Bs + kKT * SM::BP;                                // xs[k * XP + c]
   const int tid = threadIdx.x, rg = tid >> 5, cg = tid & 31;
   const int row_tiles = (p.dim + kKT - 1) / kKT;
-  const int col_tiles = p.ld / kKC;
+  const int col_tiles = p.ld / CW;
   const int64_t n_groups = (int64_t)p.n_outer * p.n_inner;
   const int64_t items = n_groups * row_tiles * col_tiles;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
@@ -42,10 +51,12 @@ __global__ void __launch_bounds__(256) k_kron_pass(const KronPass p, const T *__
     const int64_t g = rest / row_tiles;
     const int64_t base = (g / p.n_inner) * p.outer_stride + (g % p.n_inner) * p.inner_stride;
     const int g_inner = (int)(g % p.n_inner);
-    const int o0 = rt * kKT, c0 = ct * kKC;
-    T acc[8][2];
+    const int o0 = rt * kKT, c0 = ct * CW;
+    T acc[8][NC];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) acc[a][0] = acc[a][1] = T(0);
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) acc[a][q] = T(0);
     for (int k0 = 0; k0 < p.dim; k0 += kKT) {
       __syncthreads();
       for (int e = tid; e < kKT * kKT; e += blockDim.x) {
@@ -53,37 +64,44 @@ __global__ void __launch_bounds__(256) k_kron_pass(const KronPass p, const T *__
         const int o = o0 + oo, k = k0 + kk;
         T v = T(0);
         if (o < p.dim && k < p.dim) v = (T)(p.trans ? p.B[(int64_t)k * p.dim + o] : p.B[(int64_t)o * p.dim + k]);
-        Bs[kk][oo] = v;
+        Bs[kk * SM::BP + oo] = v;
       }
-      for (int e = tid; e < kKT * kKC / 2; e += blockDim.x) {
-        const int kk = e / (kKC / 2), q = e - kk * (kKC / 2);
+      for (int e = tid; e < kKT * CW / E16; e += blockDim.x) {
+        const int kk = e / (CW / E16), q = e - kk * (CW / E16);
         const int k = k0 + kk;
-        T v0 = T(0), v1 = T(0);
+        V16 v;
+        T *vs = reinterpret_cast<T *>(&v);
         if (k < p.dim) {
-          const T *src = x + (base + (int64_t)k * p.kstride) * p.ld + c0 + 2 * q;
-          v0 = src[0];
-          v1 = src[1];
+          v = *reinterpret_cast<const V16 *>(x + (base + (int64_t)k * p.kstride) * p.ld + c0 + q * E16);
           if (p.mode == KRON_IN_DH) {
             const T sc = (T)(p.dh[k] * p.dh[g_inner]);
-            v0 *= sc;
-            v1 *= sc;
+#pragma unroll
+            for (int u = 0; u < E16; ++u) vs[u] *= sc;
           }
+        } else {
+#pragma unroll
+          for (int u = 0; u < E16; ++u) vs[u] = T(0);
         }
-        xs[kk][2 * q] = v0;
-        xs[kk][2 * q + 1] = v1;
+        *reinterpret_cast<V16 *>(xs + kk * SM::XP + q * E16) = v;
       }
       __syncthreads();
       const int kmax = min(kKT, p.dim - k0);
       for (int kk = 0; kk < kmax; ++kk) {
-        T bv[8];
+        T bv[8], xv[NC];
+        const V16 *bp = reinterpret_cast<const V16 *>(Bs + kk * SM::BP + rg * 8);
 #pragma unroll
-        for (int a = 0; a < 8; ++a) bv[a] = Bs[kk][rg * 8 + a];
-        const T x0 = xs[kk][2 * cg], x1 = xs[kk][2 * cg + 1];
+        for (int u = 0; u < 8 / E16; ++u) {
+          const V16 t = bp[u];
+          const T *ts = reinterpret_cast<const T *>(&t);
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          acc[a][0] = fma(bv[a], x0, acc[a][0]);
-          acc[a][1] = fma(bv[a], x1, acc[a][1]);
+          for (int w = 0; w < E16; ++w) bv[u * E16 + w] = ts[w];
         }
+#pragma unroll
+        for (int q = 0; q < NC; ++q) xv[q] = xs[kk * SM::XP + cg * NC + q];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int q = 0; q < NC; ++q) acc[a][q] = fma(bv[a], xv[q], acc[a][q]);
       }
     }
 #pragma unroll
@@ -99,24 +117,32 @@ __global__ void __launch_bounds__(256) k_kron_pass(const KronPass p, const T *__
         const double s2 = p.kappa2 + p.lam[sa] + p.lam[sb];
         sc = (T)(1.0 / (p.tau * p.mu[o] * s2 * s2 + p.omega));
       }
-      T *dst = y + (base + (int64_t)o * p.kstride) * p.ld + c0 + 2 * cg;
-      dst[0] = acc[a][0] * sc;
-      dst[1] = acc[a][1] * sc;
+      T *dst = y + (base + (int64_t)o * p.kstride) * p.ld + c0 + cg * NC;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) dst[q] = acc[a][q] * sc;
     }
   }
 }
 
-template <typename T>
-void launch_kron_pass(cudaStream_t s, const KronPass &p, const T *x, T *y) {
+template <typename T, int CW>
+static void kron_pass_cw(cudaStream_t s, const KronPass &p, const T *x, T *y) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_kron_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kron_smem<T>());
+    cudaFuncSetAttribute(k_kron_pass<T, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, KronSmem<T, CW>::bytes);
     attr = true;
   }
-  ++g_launch_count;
-  const int64_t items = (int64_t)p.n_outer * p.n_inner * ((p.dim + kKT - 1) / kKT) * (p.ld / kKC);
+  const int64_t items = (int64_t)p.n_outer * p.n_inner * ((p.dim + kKT - 1) / kKT) * (p.ld / CW);
   const int grid = (int)std::min<int64_t>(items, 152 * 6);
-  k_kron_pass<T><<<grid, 256, kron_smem<T>(), s>>>(p, x, y);
+  k_kron_pass<T, CW><<<grid, 256, KronSmem<T, CW>::bytes, s>>>(p, x, y);
+}
+
+template <typename T>
+void launch_kron_pass(cudaStream_t s, const KronPass &p, const T *x, T *y) {
+  ++g_launch_count;
+  if (p.ld % 128 == 0)
+    kron_pass_cw<T, 128>(s, p, x, y);
+  else
+    kron_pass_cw<T, 64>(s, p, x, y);
 }
 template void launch_kron_pass<double>(cudaStream_t, const KronPass &, const double *, double *);
 template void launch_kron_pass<float>(cudaStream_t, const KronPass &, const float *, float *);

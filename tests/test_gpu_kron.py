@@ -24,10 +24,11 @@ def _grid_ctx(q, m, n_t, k, **kw):
     return ctx, model, th
 
 
-@pytest.mark.parametrize("m,n_t,k", [(16, 8, 64), (13, 7, 10), (6, 70, 33), (9, 130, 64)])
+@pytest.mark.parametrize("m,n_t,k", [(16, 8, 64), (13, 7, 10), (6, 70, 33), (9, 130, 64), (12, 10, 128)])
 def test_applied_preconditioner_matches_oracle(q, m, n_t, k):
     """n_t = 70 and 130 take two and three 64-wide K slices in the temporal
-    passes; m = 13 and 6 take partial tiles."""
+    passes; m = 13 and 6 take partial tiles; 128 samples take the 128-column
+    tiles."""
     ctx, model, th = _grid_ctx(q, m, n_t, k, preconditioner=q.QSEL_PRECOND_KRON)
     R = qi.seeded_normal((model.n, k), 17)
     Z = q.qsel_debug_apply_precond(ctx, R)
