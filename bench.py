@@ -673,7 +673,8 @@ def run_cv_eval(args):
     """Held-out evaluation of the learned control variate: 64 x 64 grid,
     n_t = 128, 8 parts, 25 % observed, scrambled-Sobol theta (seed 2, apart
     from the training grid).  Per theta: planned mixed RBMC (plan, one run, at
-    most one corrective run) against plain RBMC at overlap 2 that doubles k
+    most one corrective run; the chosen --preconditioner) against plain RBMC
+    (block-Jacobi PCG) at overlap 2 that doubles k
     from 32 (then averages 512-sample batches) until its error estimate meets
     the target -- in mixed precision on every theta and in FP64 on the first
     --cv-fp64-thetas.  Errors are also measured against the exact
@@ -682,7 +683,12 @@ def run_cv_eval(args):
     from paper_2309_05435_gb300 import build, qsel
     from paper_2309_05435_gb300 import cv as cvm
     build.build()
-    net, info = train_control_variate(args)
+    if args.cv_params:
+        net = qsel.qsel_cv_create(0)
+        qsel.qsel_cv_set_params(net, np.load(args.cv_params))
+        info = {"loaded": os.path.basename(args.cv_params)}
+    else:
+        net, info = train_control_variate(args)
     print(json.dumps({"cv_training": info}), flush=True)
     mesh = qi.grid_mesh(64)
     n_t = 128
@@ -699,7 +705,10 @@ def run_cv_eval(args):
             return float(np.sqrt(np.mean(((v - v_ex) / v_ex) ** 2)))
 
         row = {"theta": [round(x, 4) for x in th], "target": args.target}
-        pl = cvm.solve_planned(spec, th, net, args.target, max_overlap=args.max_overlap, margin=args.margin)
+        kron = args.preconditioner == "kron"
+        pl = cvm.solve_planned(spec, th, net, args.target, max_overlap=args.max_overlap, margin=args.margin,
+                               preconditioner=qsel.QSEL_PRECOND_KRON if kron else qsel.QSEL_PRECOND_BLOCK_JACOBI,
+                               cost_pcg=KRON_PCG_COST if kron else 0.0)
         row["planned_mixed"] = {"k": pl["k"], "part_overlap": pl["part_overlap"], "runs": len(pl["runs"]),
                                 "samples": pl["samples_drawn"], "err_estimate": pl["err"],
                                 "predicted_err": pl["plan"]["predicted_err"], "eps_vs_exact": eps(pl["v"]),

@@ -45,12 +45,12 @@ class ModelSpec:
         return len(self.slab_start) - 1
 
     def context(self, theta, overlap, k, seed, precision=q.QSEL_MIXED, pcg_tol=1e-8, part_overlap=None,
-                cuda_stream=None) -> q.Context:
+                cuda_stream=None, preconditioner=q.QSEL_PRECOND_BLOCK_JACOBI) -> q.Context:
         return q.qsel_create(self.n_s, self.n_t, self.mesh.c_diag, self.mesh.g_rowptr, self.mesh.g_col,
                              self.mesh.g_val, self.mask, self.sigma, theta, n_parts=self.n_parts,
                              slab_start=self.slab_start, overlap=overlap, n_samples=k, seed=seed,
                              precision=precision, pcg_tol=pcg_tol, pcg_max_iter=50000,
-                             part_overlap=part_overlap, cuda_stream=cuda_stream)
+                             part_overlap=part_overlap, cuda_stream=cuda_stream, preconditioner=preconditioner)
 
 
 def training_set(spec: ModelSpec, thetas, overlaps, k: int = 512, seeds=(1, 2), precision=q.QSEL_MIXED):
@@ -86,11 +86,12 @@ def train(X, y, steps=(1500, 1000), lrs=(3e-3, 5e-4), seed: int = 0) -> q.Contro
     return cv
 
 
-def _timed_run(spec, theta, overlap, k, seed, precision, part_overlap=None):
+def _timed_run(spec, theta, overlap, k, seed, precision, part_overlap=None,
+               preconditioner=q.QSEL_PRECOND_BLOCK_JACOBI):
     import torch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ctx = spec.context(theta, overlap, k, seed, precision, part_overlap=part_overlap)
+    ctx = spec.context(theta, overlap, k, seed, precision, part_overlap=part_overlap, preconditioner=preconditioner)
     v = ctx.diag_inv()
     t = ctx.trace_grads()
     _, err = q.qsel_error_estimate(ctx)
@@ -132,7 +133,8 @@ def solve_plain(spec: ModelSpec, theta, target: float, overlap: int, k0: int = 3
 
 
 def solve_planned(spec: ModelSpec, theta, cv: q.ControlVariate, target: float, max_overlap: int = 8,
-                  k_max: int = 512, seed: int = 11, precision=q.QSEL_MIXED, margin: float = 0.85):
+                  k_max: int = 512, seed: int = 11, precision=q.QSEL_MIXED, margin: float = 0.85,
+                  preconditioner=q.QSEL_PRECOND_BLOCK_JACOBI, cost_pcg: float = 0.0):
     """Planned RBMC: predict, plan for margin * target (one k, an overlap per
     part), run once, judge by the error estimate; a miss of the target reruns
     once with k scaled by (err / (margin * target))^2 (at most k_max)."""
@@ -140,13 +142,15 @@ def solve_planned(spec: ModelSpec, theta, cv: q.ControlVariate, target: float, m
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     probe = spec.context(theta, 1, 32, seed, precision)
-    plan = q.qsel_cv_plan(probe, cv, margin * target, max_overlap=max_overlap, max_samples=k_max)
+    plan = q.qsel_cv_plan(probe, cv, margin * target, max_overlap=max_overlap, max_samples=k_max,
+                          cost_pcg=cost_pcg)
     probe.close()
     t_plan = time.perf_counter() - t0
     k, po = plan["n_samples"], plan["part_overlap"].copy()
     runs, wall, ms, samples = [], t_plan, 0.0, 0
     while True:
-        v, t, err, w, m = _timed_run(spec, theta, 1, k, seed, precision, part_overlap=po)
+        v, t, err, w, m = _timed_run(spec, theta, 1, k, seed, precision, part_overlap=po,
+                                     preconditioner=preconditioner)
         runs.append({"k": k, "part_overlap": po.tolist(), "err": err, "wall_s": w})
         wall += w
         ms += m
