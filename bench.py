@@ -49,7 +49,7 @@ FP32_PEAK_TFLOPS = 80.5      # GB300 FP32 CUDA cores (152 SMs x 128 lanes x 2 FL
 GEMM64_DRAM_BYTES_PER_FLOP = 7.808e9 / 2.749e11
 # DRAM bytes of one rank-64 sweep update of a 4096^2 FP32 matrix on the tensor
 # cores (profiles/k_tc_gemm_grid64_nt16_mixed.md: 0.094 GB for 2 matrices)
-TC_SWEEP_DRAM_BYTES_PER_MATRIX = 0.094e9 / 2
+TC_SWEEP_DRAM_BYTES_PER_MATRIX = 0.0995e9 / 2
 # planner's PCG cost per sample and node with the Kronecker preconditioner
 # (seconds; the library default describes 64-row block Jacobi)
 KRON_PCG_COST = 0.36e-8
@@ -499,8 +499,8 @@ def run_native(args):
     if name == "gemm" and not mixed and claunch[dom]:
         traffic = GEMM64_DRAM_BYTES_PER_FLOP * cwork[dom] / claunch[dom]
     if name == "sweep_update" and mixed and claunch[dom] and w.n_s == 4096:
-        # one ncu capture (profiles/k_tc_gemm_grid64_nt16_mixed.md): 0.094 GB per
-        # launch of 2 matrices of 4096^2; scaled by the matrices per launch
+        # one ncu capture of the K = 64 tile configuration (profiles/k_tc_gemm_grid64_nt16_mixed.md):
+        # 0.0995 GB per launch of 2 matrices of 4096^2; scaled by the matrices per launch
         n_tiles = 64
         per_matrix_flop = 2.0 * 64 ** 3 * (n_tiles * (n_tiles + 1) / 2 - n_tiles)
         entries = cwork[dom] / claunch[dom] / per_matrix_flop

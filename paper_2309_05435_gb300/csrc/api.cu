@@ -48,7 +48,7 @@ struct Subdomain {
 struct DenseSlot {
   std::vector<void *> Dinv;            // T_max pivot-block inverses
   void *SigA = nullptr, *SigB = nullptr, *Y = nullptr, *W = nullptr, *V = nullptr;
-  void *P = nullptr, *U = nullptr, *Vs = nullptr;  // sweep scratch
+  void *P = nullptr, *U = nullptr, *Vs = nullptr, *Wp = nullptr, *Vk = nullptr;  // sweep scratch
   void *wbuf = nullptr;                // T_max x n_pad x ld correction samples
   void *ybuf = nullptr, *tmp = nullptr, *bright = nullptr;
 };
@@ -627,7 +627,10 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   // device memory (at most kMaxBatch)
   const size_t mat = (size_t)n_pad * n_pad * esz;
   const size_t svec = (size_t)n_pad * c->ld * esz;
-  const size_t per_slot = (size_t)(c->T_max + 5) * mat + 2 * (size_t)n_pad * 64 * esz + 64 * 64 * esz +
+  // sweep scratch: U, V and the column panel W (n_pad x 64 kSweepPanel each),
+  // Vk (64 kSweepPanel x 64) and P (64 x 64)
+  const size_t panel = (size_t)n_pad * 64 * kSweepPanel * esz;
+  const size_t per_slot = (size_t)(c->T_max + 5) * mat + 3 * panel + (size_t)(kSweepPanel + 1) * 64 * 64 * esz +
                           (size_t)(c->T_max + 3) * svec + 4096;
   size_t free_b = 0, total_b = 0;
   QSEL_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
@@ -646,8 +649,10 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
     TRY(c->alloc_bytes(&sl.W, mat));
     TRY(c->alloc_bytes(&sl.V, mat));
     TRY(c->alloc_bytes(&sl.P, 64 * 64 * esz));
-    TRY(c->alloc_bytes(&sl.U, (size_t)n_pad * 64 * esz));
-    TRY(c->alloc_bytes(&sl.Vs, (size_t)n_pad * 64 * esz));
+    TRY(c->alloc_bytes(&sl.U, panel));
+    TRY(c->alloc_bytes(&sl.Vs, panel));
+    TRY(c->alloc_bytes(&sl.Wp, panel));
+    TRY(c->alloc_bytes(&sl.Vk, (size_t)kSweepPanel * 64 * 64 * esz));
     TRY(c->alloc_bytes(&sl.wbuf, (size_t)c->T_max * svec));
     TRY(c->alloc_bytes(&sl.ybuf, svec));
     TRY(c->alloc_bytes(&sl.tmp, svec));
@@ -1149,6 +1154,8 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       we.P = buf(sl.P);
       we.U = buf(sl.U);
       we.V = buf(sl.Vs);
+      we.W = buf(sl.Wp);
+      we.Vk = buf(sl.Vk);
       if (t + 1 < sd.T) {
         SpEntry<T, T> &ge = gb.e[gb.count++];
         ge.B = Dinv(p, t);

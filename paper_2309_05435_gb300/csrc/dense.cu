@@ -169,12 +169,11 @@ template void launch_gemm<float>(cudaStream_t, const GemmBatch<float> &, int, in
 // ---------------------------------------------------------------------------
 // The pivot tile is inverted in double whatever T is (the "FP64 pivots" of the
 // mixed path).
+// P = Tk^-1 for the 64 x 64 tile at Tk (row stride ld), from its lower half.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sweep_pivot(SweepBatch<T> bt, int k, int ld, int32_t *err_flag) {
+__device__ __forceinline__ void invert_pivot_tile(const T *Tk, int ld, T *P, int32_t *err_flag) {
   __shared__ double S[64 * 65];
-  __shared__ double col[64], wv[64];
-  const SweepEntry<T> e = bt.e[blockIdx.x];
-  const T *Tk = e.A + (int64_t)k * 64 * ld + k * 64;
+  __shared__ double col[65], wv[64];
   for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
     const int r = idx >> 6, c = idx & 63;
     // the diagonal tile is kept symmetric; the lower half is what is read
@@ -184,8 +183,14 @@ __global__ void __launch_bounds__(256) k_sweep_pivot(SweepBatch<T> bt, int k, in
   sym_sweep_inverse64_lower(S, 65, col, wv, err_flag);
   for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
     const int r = idx >> 6, c = idx & 63;
-    e.P[idx] = (T)(-S[(r >= c) ? r * 65 + c : c * 65 + r]);
+    P[idx] = (T)(-S[(r >= c) ? r * 65 + c : c * 65 + r]);
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_pivot(SweepBatch<T> bt, int k, int ld, int32_t *err_flag) {
+  const SweepEntry<T> e = bt.e[blockIdx.x];
+  invert_pivot_tile(e.A + (int64_t)k * 64 * ld + k * 64, ld, e.P, err_flag);
 }
 
 template <typename T>
@@ -217,63 +222,138 @@ __global__ void __launch_bounds__(256) k_sweep_panel(SweepBatch<T> bt, int k, in
     for (int b = 0; b < 4; ++b) U[(ty + 16 * a) * 64 + tx + 16 * b] = acc[a][b];
 }
 
-// Tensor-core variant of the panel: U_i = A_ik P, V_i = A_ik for i != k and
-// U_k = V_k = 0, so that the rank-64 update C -= U V^T over all lower tiles
-// leaves row and column k unchanged (k_sweep_panel_write fills them after).
+// ---------------------------------------------------------------------------
+// Panel-blocked sweep (tensor-core path).  Pivoting the tiles of a panel
+// K = {k0, ..., k0 + bw - 1} one after the other changes an entry A_ij with
+// i, j outside K by - sum_k U^(k)_i V^(k)_j^T, V^(k) being column k as it
+// stands when k is pivoted and U^(k) = V^(k) P_k.  Those columns depend on the
+// earlier pivots of the panel only through the panel's own columns, so the
+// column panel A[:, K] is gathered into W (n_pad x 64 bw, row stride
+// 64 kSweepPanel), swept there pivot by pivot, and the rest of the matrix
+// receives one rank-64 bw update C -= [U^(k)] [V^(k)]^T on the tensor cores
+// (which also overwrites rows and columns K; the scatter restores them).
+// ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_sweep_panel_tc(SweepBatch<T> bt, int k, int ld) {
+__global__ void __launch_bounds__(256) k_bsweep_gather(SweepBatch<T> bt, int k0, int bw, int ld) {
+  __shared__ T S[64 * 65];
+  const SweepEntry<T> e = bt.e[blockIdx.y];
+  constexpr int ldw = 64 * kSweepPanel;
+  const int i = blockIdx.x;
+  for (int q = 0; q < bw; ++q) {
+    const int j = k0 + q;
+    // A_ij lives in tile (max(i, j), min(i, j)) of the lower triangle
+    const T *src = e.A + (int64_t)max(i, j) * 64 * ld + min(i, j) * 64;
+    for (int idx = threadIdx.x; idx < 4096; idx += 256)
+      S[(idx >> 6) * 65 + (idx & 63)] = src[(int64_t)(idx >> 6) * ld + (idx & 63)];
+    __syncthreads();
+    T *dst = e.W + (int64_t)i * 64 * ldw + q * 64;
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) {
+      const int r = idx >> 6, c = idx & 63;
+      const bool direct = i > j || (i == j && r >= c);
+      dst[(int64_t)r * ldw + c] = direct ? S[r * 65 + c] : S[c * 65 + r];
+    }
+    __syncthreads();
+  }
+}
+
+// Pivot k = k0 + q of the panel: P = W_kq^-1 (FP64), and Vk = rows K of
+// column q as they stand before the pivot.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bsweep_pivot(SweepBatch<T> bt, int k0, int q, int bw, int32_t *err_flag) {
+  const SweepEntry<T> e = bt.e[blockIdx.x];
+  constexpr int ldw = 64 * kSweepPanel;
+  for (int idx = threadIdx.x; idx < bw * 4096; idx += 256)
+    e.Vk[idx] = e.W[(int64_t)(k0 * 64 + (idx >> 6)) * ldw + q * 64 + (idx & 63)];
+  invert_pivot_tile(e.W + (int64_t)(k0 + q) * 64 * ldw + q * 64, ldw, e.P, err_flag);
+}
+
+// One pivot on the panel, CTA per row tile i:
+//   U_i = W_iq P,  V_i = W_iq           (saved at column q of U, V)
+//   W_ij -= U_i Vk_j^T                  (panel columns j != q)
+//   W_iq <- U_i,  W_kj <- U_j^T (j in K),  W_kq <- -P.
+// Row k belongs to no CTA's update, so the writes never overlap.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bsweep_panel(SweepBatch<T> bt, int k0, int q, int bw) {
   __shared__ TileSmem<T> sm;
   const SweepEntry<T> e = bt.e[blockIdx.y];
-  const int i = blockIdx.x;
-  T *U = e.U + (int64_t)i * 64 * 64;
-  T *V = e.V + (int64_t)i * 64 * 64;
+  constexpr int ldw = 64 * kSweepPanel;
+  const int i = blockIdx.x, k = k0 + q;
+  T *Wi = e.W + (int64_t)i * 64 * ldw;
+  T *Ui = e.U + (int64_t)i * 64 * ldw + q * 64;
+  T *Vi = e.V + (int64_t)i * 64 * ldw + q * 64;
   if (i == k) {
     for (int idx = threadIdx.x; idx < 4096; idx += 256) {
-      U[idx] = T(0);
-      V[idx] = T(0);
+      const int64_t o = (int64_t)(idx >> 6) * ldw + (idx & 63);
+      Wi[o + q * 64] = -e.P[idx];
+      Ui[o] = T(0);
+      Vi[o] = T(0);
     }
     return;
   }
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  if (i > k) {
-    const T *C = e.A + (int64_t)i * 64 * ld + k * 64;
-    tile_mma<false, false>(sm, C, ld, e.P, 64, 64, acc);
-    for (int idx = threadIdx.x; idx < 4096; idx += 256) V[idx] = C[(int64_t)(idx >> 6) * ld + (idx & 63)];
-  } else {
-    const T *C = e.A + (int64_t)k * 64 * ld + i * 64;
-    tile_mma<true, false>(sm, C, ld, e.P, 64, 64, acc);
-    for (int idx = threadIdx.x; idx < 4096; idx += 256) V[idx] = C[(int64_t)(idx & 63) * ld + (idx >> 6)];
+  tile_mma<false, false>(sm, Wi + q * 64, ldw, e.P, 64, 64, acc);
+  for (int idx = threadIdx.x; idx < 4096; idx += 256) {
+    const int64_t o = (int64_t)(idx >> 6) * ldw + (idx & 63);
+    Vi[o] = Wi[o + q * 64];
   }
+  __syncthreads();  // column q read before it is overwritten
+  const bool in_panel = i >= k0 && i < k0 + bw;
+  T *Wk = e.W + (int64_t)k * 64 * ldw + (i - k0) * 64;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) U[(ty + 16 * a) * 64 + tx + 16 * b] = acc[a][b];
+    for (int b = 0; b < 4; ++b) {
+      const int r = ty + 16 * a, c = tx + 16 * b;
+      Ui[(int64_t)r * ldw + c] = acc[a][b];
+      Wi[(int64_t)r * ldw + q * 64 + c] = acc[a][b];
+      if (in_panel) Wk[(int64_t)c * ldw + r] = acc[a][b];
+    }
+  __syncthreads();  // U_i complete before it is read back as an operand
+  for (int jj = 0; jj < bw; ++jj) {
+    if (jj == q) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    tile_mma<false, true>(sm, Ui, ldw, e.Vk + jj * 4096, 64, 64, acc);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) Wi[(int64_t)(ty + 16 * a) * ldw + jj * 64 + tx + 16 * b] -= acc[a][b];
+  }
 }
 
-// Row/column k after the tensor-core update: A_ik <- U_i (i > k),
-// A_kj <- U_j^T (j < k), A_kk <- -P.
+// Column panel back into the lower tiles: A_ij for j in K from W row tile i
+// (transposed into tile (j, i) when i < j; panel rows i < j come from row j).
 template <typename T>
-__global__ void __launch_bounds__(256) k_sweep_panel_write(SweepBatch<T> bt, int k, int ld) {
+__global__ void __launch_bounds__(256) k_bsweep_scatter(SweepBatch<T> bt, int k0, int bw, int ld) {
+  __shared__ T S[64 * 65];
   const SweepEntry<T> e = bt.e[blockIdx.y];
+  constexpr int ldw = 64 * kSweepPanel;
   const int i = blockIdx.x;
-  if (i == k) {
-    T *Tkk = e.A + (int64_t)k * 64 * ld + k * 64;
-    for (int idx = threadIdx.x; idx < 4096; idx += 256) Tkk[(int64_t)(idx >> 6) * ld + (idx & 63)] = -e.P[idx];
-  } else if (i > k) {
-    T *Tik = e.A + (int64_t)i * 64 * ld + k * 64;
-    const T *U = e.U + (int64_t)i * 4096;
-    for (int idx = threadIdx.x; idx < 4096; idx += 256) Tik[(int64_t)(idx >> 6) * ld + (idx & 63)] = U[idx];
-  } else {
-    T *Tki = e.A + (int64_t)k * 64 * ld + i * 64;
-    const T *U = e.U + (int64_t)i * 4096;
-    for (int idx = threadIdx.x; idx < 4096; idx += 256) {
-      const int r = idx >> 6, c = idx & 63;
-      Tki[(int64_t)r * ld + c] = U[c * 64 + r];
+  const bool in_panel = i >= k0 && i < k0 + bw;
+  for (int q = 0; q < bw; ++q) {
+    const int j = k0 + q;
+    const T *src = e.W + (int64_t)i * 64 * ldw + q * 64;
+    if (i >= j) {
+      T *dst = e.A + (int64_t)i * 64 * ld + j * 64;
+      for (int idx = threadIdx.x; idx < 4096; idx += 256)
+        dst[(int64_t)(idx >> 6) * ld + (idx & 63)] = src[(int64_t)(idx >> 6) * ldw + (idx & 63)];
+    } else if (!in_panel) {
+      for (int idx = threadIdx.x; idx < 4096; idx += 256)
+        S[(idx >> 6) * 65 + (idx & 63)] = src[(int64_t)(idx >> 6) * ldw + (idx & 63)];
+      __syncthreads();
+      T *dst = e.A + (int64_t)j * 64 * ld + i * 64;
+      for (int idx = threadIdx.x; idx < 4096; idx += 256) {
+        const int r = idx >> 6, c = idx & 63;
+        dst[(int64_t)r * ld + c] = S[c * 65 + r];
+      }
+      __syncthreads();
     }
   }
 }
@@ -363,7 +443,9 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
   const int n_lower = nt * (nt + 1) / 2;
   if constexpr (std::is_same<T, float>::value) {
     if (tc_passes > 0) {
-      // rank-64 updates on the tensor cores: C -= U V^T over the lower 128-tiles
+      // panels of kSweepPanel pivots; the rest of the matrix gets one
+      // rank-64 bw update C -= U V^T per panel over the lower 128-tiles
+      constexpr int ldw = 64 * kSweepPanel;
       GemmBatch<float> gb{};
       gb.count = b.count;
       for (int q = 0; q < b.count; ++q) {
@@ -374,30 +456,42 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
         gb.e[q].alpha = -1.0;
         gb.e[q].beta = 1.0;
       }
-      for (int k = 0; k < nt; ++k) {
-        g_launch_count += 3;
+      for (int k0 = 0; k0 < nt; k0 += kSweepPanel) {
+        const int bw = std::min(kSweepPanel, nt - k0);
+        g_launch_count += 2 + 2 * bw;
         {
-          ProfScope ps_(s, PROF_PIVOT, 2.0 * 64.0 * 64.0 * 64.0 * b.count);
-          k_sweep_pivot<T><<<b.count, 256, 0, s>>>(b, k, n_pad, err_flag);
+          ProfScope ps_(s, PROF_PANEL);
+          k_bsweep_gather<T><<<dim3(nt, b.count), 256, 0, s>>>(b, k0, bw, n_pad);
+        }
+        for (int q = 0; q < bw; ++q) {
+          {
+            ProfScope ps_(s, PROF_PIVOT, 2.0 * 64.0 * 64.0 * 64.0 * b.count);
+            k_bsweep_pivot<T><<<b.count, 256, 0, s>>>(b, k0, q, bw, err_flag);
+          }
+          {
+            ProfScope ps_(s, PROF_PANEL);
+            k_bsweep_panel<T><<<dim3(nt, b.count), 256, 0, s>>>(b, k0, q, bw);
+          }
+        }
+        if (nt > bw) {
+          Profiler::Rec rec{PROF_SWEEP, nullptr, nullptr, 0.0};
+          if (g_prof) {
+            // algorithmic work: the rank-64 bw update of the lower tiles off
+            // the panel's rows and columns
+            const double rest = (double)(nt - bw) * (nt - bw + 1) / 2.0;
+            rec.work = 2.0 * 64.0 * 64.0 * 64.0 * bw * rest * b.count;
+            g_prof->begin(s, rec);
+          }
+          const bool prof = g_prof != nullptr;
+          Profiler *saved = g_prof;
+          g_prof = nullptr;  // timed as the sweep, not as a GEMM
+          launch_tc_gemm(s, gb, n_pad, n_pad, 64 * bw, ldw, ldw, n_pad, true, tc_passes, err_flag);
+          g_prof = saved;
+          if (prof) g_prof->end(s, rec);
         }
         {
           ProfScope ps_(s, PROF_PANEL);
-          k_sweep_panel_tc<T><<<dim3(nt, b.count), 256, 0, s>>>(b, k, n_pad);
-        }
-        Profiler::Rec rec{PROF_SWEEP, nullptr, nullptr, 0.0};
-        if (g_prof) {
-          rec.work = 2.0 * 64.0 * 64.0 * 64.0 * ((double)n_lower - nt) * b.count;
-          g_prof->begin(s, rec);
-        }
-        const bool prof = g_prof != nullptr;
-        Profiler *saved = g_prof;
-        g_prof = nullptr;  // timed as the sweep, not as a GEMM
-        launch_tc_gemm(s, gb, n_pad, n_pad, 64, 64, 64, n_pad, true, tc_passes, err_flag);
-        g_prof = saved;
-        if (prof) g_prof->end(s, rec);
-        {
-          ProfScope ps_(s, PROF_PANEL);
-          k_sweep_panel_write<T><<<dim3(nt, b.count), 256, 0, s>>>(b, k, n_pad);
+          k_bsweep_scatter<T><<<dim3(nt, b.count), 256, 0, s>>>(b, k0, bw, n_pad);
         }
       }
       ++g_launch_count;

@@ -192,11 +192,18 @@ template <typename T>
 void launch_gemm(cudaStream_t s, const GemmBatch<T> &b, int M, int N, int K, int lda, int ldb, int ldc,
                  bool lower);
 
+// Pivot tiles per panel of the tensor-core sweep (the rank of its updates is
+// 64 kSweepPanel).
+constexpr int kSweepPanel = 4;
+
 template <typename T>
 struct SweepEntry {
   T *A;          // n_pad x n_pad, row-major, lower tiles used
   T *P;          // 64 x 64 scratch
-  T *U, *V;      // n_pad x 64 scratch each (tile-major)
+  T *U, *V;      // n_pad x 64 scratch each (tile-major); n_pad x 64 kSweepPanel
+                 // (row-major) on the tensor-core path
+  T *W;          // tensor-core path: column panel, n_pad x 64 kSweepPanel
+  T *Vk;         // tensor-core path: 64 kSweepPanel x 64 (panel rows of the pivot column)
 };
 template <typename T>
 struct SweepBatch {
@@ -206,7 +213,9 @@ struct SweepBatch {
 // In-place SPD inverse by the blocked symmetric sweep; A becomes A^-1 with
 // both triangles filled.  The 64 x 64 pivot tiles are always inverted in
 // double.  err_flag gets bit 0 on a non-positive pivot.  For float with
-// tc_passes > 0 the rank-64 updates run on the tcgen05 tensor cores.
+// tc_passes > 0 the pivots are taken kSweepPanel at a time on a gathered column
+// panel and the rest of the matrix gets one rank-64 kSweepPanel update per
+// panel on the tcgen05 tensor cores (W, Vk and the wide U, V are needed).
 template <typename T>
 void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err_flag, int tc_passes = 0);
 // Copy the lower tiles of each e[].A into its upper triangle (symmetric fill).

@@ -42,7 +42,9 @@ __device__ inline void sym_sweep_inverse_smem(double *S, int ld_s, int b, int32_
 // triangle: each pivot snapshots column p (c_i = S_ip) and w_j = c_j / d, then
 // every lower entry is updated with one FMA, S_ij - c_i w_j, by the thread
 // that owns it (2080 entries, at most 9 per thread; blockDim.x must be 256).
-// After the 64 pivots the lower triangle holds that of -S^-1.
+// Only the 64 column threads form 1 / d; thread 0 leaves it in col[64] for the
+// owner of the diagonal entry (col holds 65 doubles).  After the 64 pivots the
+// lower triangle holds that of -S^-1.
 __device__ inline void sym_sweep_inverse64_lower(double *S, int ld_s, double *col, double *wv, int32_t *err_flag) {
   int ei[9], ej[9];
 #pragma unroll
@@ -51,7 +53,8 @@ __device__ inline void sym_sweep_inverse64_lower(double *S, int ld_s, double *co
     ei[q] = -1;
     ej[q] = 0;
     if (e < 2080) {
-      int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+      // float estimate of the row, made exact by the two corrections
+      int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
       while ((i + 1) * (i + 2) / 2 <= e) ++i;
       while (i * (i + 1) / 2 > e) --i;
       ei[q] = i;
@@ -59,15 +62,18 @@ __device__ inline void sym_sweep_inverse64_lower(double *S, int ld_s, double *co
     }
   }
   for (int p = 0; p < 64; ++p) {
-    const double d = S[p * ld_s + p];
-    const double inv = (d > 0.0) ? 1.0 / d : 0.0;
     if (threadIdx.x < 64) {
+      const double d = S[p * ld_s + p];
+      const double inv = (d > 0.0) ? 1.0 / d : 0.0;
       const int i = threadIdx.x;
       const double c = (i >= p) ? S[i * ld_s + p] : S[p * ld_s + i];
       col[i] = c;
       wv[i] = c * inv;
+      if (i == 0) {
+        col[64] = inv;
+        if (!(d > 0.0) && err_flag) atomicOr(err_flag, 1);
+      }
     }
-    if (!(d > 0.0) && threadIdx.x == 0 && err_flag) atomicOr(err_flag, 1);
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
@@ -75,7 +81,7 @@ __device__ inline void sym_sweep_inverse64_lower(double *S, int ld_s, double *co
         const int i = ei[q], j = ej[q];
         double v;
         if (i == p && j == p)
-          v = -inv;
+          v = -col[64];
         else if (i == p)
           v = wv[j];
         else if (j == p)
