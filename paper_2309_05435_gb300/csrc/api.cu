@@ -48,7 +48,8 @@ struct Subdomain {
 struct DenseSlot {
   std::vector<void *> Dinv;            // T_max pivot-block inverses
   void *SigA = nullptr, *SigB = nullptr, *Y = nullptr, *W = nullptr, *V = nullptr;
-  void *P = nullptr, *U = nullptr, *Vs = nullptr, *Wp = nullptr, *Vk = nullptr;  // sweep scratch
+  void *P = nullptr, *U = nullptr, *Vs = nullptr, *Vk = nullptr;  // sweep scratch
+  void *U2 = nullptr, *V2 = nullptr, *Wp = nullptr, *Wp2 = nullptr;  // tensor-core sweep panels
   void *wbuf = nullptr;                // T_max x n_pad x ld correction samples
   void *ybuf = nullptr, *tmp = nullptr, *bright = nullptr;
 };
@@ -126,6 +127,7 @@ struct qsel_ctx {
   int32_t *h_counters = nullptr;
   double *h_small = nullptr;
   cudaEvent_t ev[4]{};
+  SweepStreams sweep_ss;               // look-ahead of the tensor-core sweep (mixed path)
   std::vector<cudaEvent_t> phase_ev;   // pairs per (wave, phase)
   size_t phase_used = 0;
   Profiler prof;
@@ -162,6 +164,10 @@ struct qsel_ctx {
     if (h_theta) cudaFreeHost(h_theta);
     for (auto &e : ev)
       if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : {sweep_ss.fork, sweep_ss.panel, sweep_ss.gather, sweep_ss.scatter})
+      if (e) cudaEventDestroy(e);
+    if (sweep_ss.hi) cudaStreamDestroy(sweep_ss.hi);
+    if (sweep_ss.lo) cudaStreamDestroy(sweep_ss.lo);
     for (auto e : phase_ev) cudaEventDestroy(e);
   }
 };
@@ -627,10 +633,10 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   // device memory (at most kMaxBatch)
   const size_t mat = (size_t)n_pad * n_pad * esz;
   const size_t svec = (size_t)n_pad * c->ld * esz;
-  // sweep scratch: U, V and the column panel W (n_pad x 64 kSweepPanel each),
-  // Vk (64 kSweepPanel x 64) and P (64 x 64)
+  // sweep scratch: two sets of U, V and the column panel W (n_pad x
+  // 64 kSweepPanel each), Vk (64 kSweepPanel x 64) and P (64 x 64)
   const size_t panel = (size_t)n_pad * 64 * kSweepPanel * esz;
-  const size_t per_slot = (size_t)(c->T_max + 5) * mat + 3 * panel + (size_t)(kSweepPanel + 1) * 64 * 64 * esz +
+  const size_t per_slot = (size_t)(c->T_max + 5) * mat + 6 * panel + (size_t)(kSweepPanel + 1) * 64 * 64 * esz +
                           (size_t)(c->T_max + 3) * svec + 4096;
   size_t free_b = 0, total_b = 0;
   QSEL_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
@@ -652,6 +658,9 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
     TRY(c->alloc_bytes(&sl.U, panel));
     TRY(c->alloc_bytes(&sl.Vs, panel));
     TRY(c->alloc_bytes(&sl.Wp, panel));
+    TRY(c->alloc_bytes(&sl.U2, panel));
+    TRY(c->alloc_bytes(&sl.V2, panel));
+    TRY(c->alloc_bytes(&sl.Wp2, panel));
     TRY(c->alloc_bytes(&sl.Vk, (size_t)kSweepPanel * 64 * 64 * esz));
     TRY(c->alloc_bytes(&sl.wbuf, (size_t)c->T_max * svec));
     TRY(c->alloc_bytes(&sl.ybuf, svec));
@@ -666,6 +675,16 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   TRY(c->alloc(&c->d_tol2, 1));
   QSEL_CUDA_TRY(cudaMemset(c->d_loop, 0, 4 * sizeof(int32_t)));
   for (auto &e : c->ev) QSEL_CUDA_TRY(cudaEventCreate(&e));
+  if (c->mixed) {
+    // the sweep's panels on a high-priority stream, so that their few CTAs are
+    // scheduled ahead of the pending tiles of the concurrent update
+    int least = 0, greatest = 0;
+    QSEL_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    QSEL_CUDA_TRY(cudaStreamCreateWithPriority(&c->sweep_ss.hi, cudaStreamNonBlocking, greatest));
+    QSEL_CUDA_TRY(cudaStreamCreateWithPriority(&c->sweep_ss.lo, cudaStreamNonBlocking, least));
+    for (cudaEvent_t *e : {&c->sweep_ss.fork, &c->sweep_ss.panel, &c->sweep_ss.gather, &c->sweep_ss.scatter})
+      QSEL_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
   return ok();
 }
 
@@ -1154,7 +1173,12 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       we.P = buf(sl.P);
       we.U = buf(sl.U);
       we.V = buf(sl.Vs);
-      we.W = buf(sl.Wp);
+      we.Up[0] = buf(sl.U);
+      we.Vp[0] = buf(sl.Vs);
+      we.Wp[0] = buf(sl.Wp);
+      we.Up[1] = buf(sl.U2);
+      we.Vp[1] = buf(sl.V2);
+      we.Wp[1] = buf(sl.Wp2);
       we.Vk = buf(sl.Vk);
       if (t + 1 < sd.T) {
         SpEntry<T, T> &ge = gb.e[gb.count++];
@@ -1167,7 +1191,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       }
     }
     launch_schur_assemble<T>(s, sb, c->pat, c->d_qs, c->obs_w, n_s, n_pad);
-    spd_inverse<T>(s, wb, n_pad, c->d_err, c->tc_passes);
+    spd_inverse<T>(s, wb, n_pad, c->d_err, c->tc_passes, c->mixed ? &c->sweep_ss : nullptr);
     launch_sp_rowgather<T, T>(s, gb, c->pat, c->d_qs, n_s, n_pad, n_pad, n_pad, n_pad);
   }
   QSEL_CUDA_TRY(cudaGetLastError());
@@ -1716,7 +1740,8 @@ static Err batch_capture(qsel_batch *b) {
   }
   if (ce != cudaSuccess) return cuda_fail(ce, "end of the batch capture", __FILE__, __LINE__);
   b->graph = g;
-  QSEL_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
+  // node priorities carry the sweep's high-priority panel stream into the graph
+  QSEL_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, cudaGraphInstantiateFlagUseNodePriority));
   b->ms_capture = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
   b->launches_per_replay = g_launch_count - l0;
   return ok();

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256) k_sweep_panel(SweepBatch<T> bt, int k, in
 // (which also overwrites rows and columns K; the scatter restores them).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_bsweep_gather(SweepBatch<T> bt, int k0, int bw, int ld) {
+__global__ void __launch_bounds__(256) k_bsweep_gather(SweepBatch<T> bt, int k0, int bw, int ld, int buf) {
   __shared__ T S[64 * 65];
   const SweepEntry<T> e = bt.e[blockIdx.y];
   constexpr int ldw = 64 * kSweepPanel;
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(256) k_bsweep_gather(SweepBatch<T> bt, int k0,
     for (int idx = threadIdx.x; idx < 4096; idx += 256)
       S[(idx >> 6) * 65 + (idx & 63)] = src[(int64_t)(idx >> 6) * ld + (idx & 63)];
     __syncthreads();
-    T *dst = e.W + (int64_t)i * 64 * ldw + q * 64;
+    T *dst = (buf ? e.Wp[1] : e.Wp[0]) + (int64_t)i * 64 * ldw + q * 64;
     for (int idx = threadIdx.x; idx < 4096; idx += 256) {
       const int r = idx >> 6, c = idx & 63;
       const bool direct = i > j || (i == j && r >= c);
@@ -259,12 +259,14 @@ __global__ void __launch_bounds__(256) k_bsweep_gather(SweepBatch<T> bt, int k0,
 // Pivot k = k0 + q of the panel: P = W_kq^-1 (FP64), and Vk = rows K of
 // column q as they stand before the pivot.
 template <typename T>
-__global__ void __launch_bounds__(256) k_bsweep_pivot(SweepBatch<T> bt, int k0, int q, int bw, int32_t *err_flag) {
+__global__ void __launch_bounds__(256) k_bsweep_pivot(SweepBatch<T> bt, int k0, int q, int bw, int buf,
+                                                      int32_t *err_flag) {
   const SweepEntry<T> e = bt.e[blockIdx.x];
   constexpr int ldw = 64 * kSweepPanel;
+  const T *W = (buf ? e.Wp[1] : e.Wp[0]);
   for (int idx = threadIdx.x; idx < bw * 4096; idx += 256)
-    e.Vk[idx] = e.W[(int64_t)(k0 * 64 + (idx >> 6)) * ldw + q * 64 + (idx & 63)];
-  invert_pivot_tile(e.W + (int64_t)(k0 + q) * 64 * ldw + q * 64, ldw, e.P, err_flag);
+    e.Vk[idx] = W[(int64_t)(k0 * 64 + (idx >> 6)) * ldw + q * 64 + (idx & 63)];
+  invert_pivot_tile(W + (int64_t)(k0 + q) * 64 * ldw + q * 64, ldw, e.P, err_flag);
 }
 
 // One pivot on the panel, CTA per row tile i:
@@ -273,14 +275,14 @@ __global__ void __launch_bounds__(256) k_bsweep_pivot(SweepBatch<T> bt, int k0, 
 //   W_iq <- U_i,  W_kj <- U_j^T (j in K),  W_kq <- -P.
 // Row k belongs to no CTA's update, so the writes never overlap.
 template <typename T>
-__global__ void __launch_bounds__(256) k_bsweep_panel(SweepBatch<T> bt, int k0, int q, int bw) {
+__global__ void __launch_bounds__(256) k_bsweep_panel(SweepBatch<T> bt, int k0, int q, int bw, int buf) {
   __shared__ TileSmem<T> sm;
   const SweepEntry<T> e = bt.e[blockIdx.y];
   constexpr int ldw = 64 * kSweepPanel;
   const int i = blockIdx.x, k = k0 + q;
-  T *Wi = e.W + (int64_t)i * 64 * ldw;
-  T *Ui = e.U + (int64_t)i * 64 * ldw + q * 64;
-  T *Vi = e.V + (int64_t)i * 64 * ldw + q * 64;
+  T *Wi = (buf ? e.Wp[1] : e.Wp[0]) + (int64_t)i * 64 * ldw;
+  T *Ui = (buf ? e.Up[1] : e.Up[0]) + (int64_t)i * 64 * ldw + q * 64;
+  T *Vi = (buf ? e.Vp[1] : e.Vp[0]) + (int64_t)i * 64 * ldw + q * 64;
   if (i == k) {
     for (int idx = threadIdx.x; idx < 4096; idx += 256) {
       const int64_t o = (int64_t)(idx >> 6) * ldw + (idx & 63);
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(256) k_bsweep_panel(SweepBatch<T> bt, int k0, 
   }
   __syncthreads();  // column q read before it is overwritten
   const bool in_panel = i >= k0 && i < k0 + bw;
-  T *Wk = e.W + (int64_t)k * 64 * ldw + (i - k0) * 64;
+  T *Wk = (buf ? e.Wp[1] : e.Wp[0]) + (int64_t)k * 64 * ldw + (i - k0) * 64;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(256) k_bsweep_panel(SweepBatch<T> bt, int k0, 
 // Column panel back into the lower tiles: A_ij for j in K from W row tile i
 // (transposed into tile (j, i) when i < j; panel rows i < j come from row j).
 template <typename T>
-__global__ void __launch_bounds__(256) k_bsweep_scatter(SweepBatch<T> bt, int k0, int bw, int ld) {
+__global__ void __launch_bounds__(256) k_bsweep_scatter(SweepBatch<T> bt, int k0, int bw, int ld, int buf) {
   __shared__ T S[64 * 65];
   const SweepEntry<T> e = bt.e[blockIdx.y];
   constexpr int ldw = 64 * kSweepPanel;
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(256) k_bsweep_scatter(SweepBatch<T> bt, int k0
   const bool in_panel = i >= k0 && i < k0 + bw;
   for (int q = 0; q < bw; ++q) {
     const int j = k0 + q;
-    const T *src = e.W + (int64_t)i * 64 * ldw + q * 64;
+    const T *src = (buf ? e.Wp[1] : e.Wp[0]) + (int64_t)i * 64 * ldw + q * 64;
     if (i >= j) {
       T *dst = e.A + (int64_t)i * 64 * ld + j * 64;
       for (int idx = threadIdx.x; idx < 4096; idx += 256)
@@ -356,6 +358,29 @@ __global__ void __launch_bounds__(256) k_bsweep_scatter(SweepBatch<T> bt, int k0
       __syncthreads();
     }
   }
+}
+
+// Look-ahead: the next panel K' was gathered before the update of panel K
+// reached it.  Its rows outside K get that update as a small tensor-core
+// product; its rows K are final in panel K's W, where A_{K', K} stands, and
+// are copied transposed here: Wp[nxt](K, :) = Wp[cur](K', 0 : 64 bw)^T.
+// CTA per (a, c) tile pair, a < bw rows of K, c < bw1 columns of K'.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bsweep_rows(SweepBatch<T> bt, int k0, int bw, int k1, int bw1, int cur) {
+  __shared__ T S[64 * 65];
+  const SweepEntry<T> e = bt.e[blockIdx.y];
+  constexpr int ldw = 64 * kSweepPanel;
+  const int a = (int)blockIdx.x / bw1, c = (int)blockIdx.x % bw1;
+  const T *src = (cur ? e.Wp[1] : e.Wp[0]) + (int64_t)(k1 + c) * 64 * ldw + a * 64;
+  T *dst = (cur ? e.Wp[0] : e.Wp[1]) + (int64_t)(k0 + a) * 64 * ldw + c * 64;
+  for (int idx = threadIdx.x; idx < 4096; idx += 256)
+    S[(idx >> 6) * 65 + (idx & 63)] = src[(int64_t)(idx >> 6) * ldw + (idx & 63)];
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 4096; idx += 256) {
+    const int r = idx >> 6, cc = idx & 63;
+    dst[(int64_t)r * ldw + cc] = S[cc * 65 + r];
+  }
+  (void)bw;
 }
 
 template <typename T>
@@ -437,63 +462,117 @@ __global__ void __launch_bounds__(256) k_sweep_mirror(SweepBatch<T> bt, int ld, 
 }
 
 template <typename T>
-void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err_flag, int tc_passes) {
+void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err_flag, int tc_passes,
+                 const SweepStreams *ss) {
   if (b.count <= 0) return;
   const int nt = n_pad / 64;
   const int n_lower = nt * (nt + 1) / 2;
   if constexpr (std::is_same<T, float>::value) {
     if (tc_passes > 0) {
-      // panels of kSweepPanel pivots; the rest of the matrix gets one
-      // rank-64 bw update C -= U V^T per panel over the lower 128-tiles
+      // Panels of kSweepPanel pivots.  Panel p is pivoted on hi; its rank-64 bw
+      // update of the rest of the matrix and its scatter run on lo while panel
+      // p + 1 (gathered before that update reached it, then patched) is pivoted
+      // on hi.  Buffers alternate with the panel's parity.
       constexpr int ldw = 64 * kSweepPanel;
-      GemmBatch<float> gb{};
-      gb.count = b.count;
-      for (int q = 0; q < b.count; ++q) {
-        gb.e[q].A = b.e[q].U;
-        gb.e[q].B = b.e[q].V;
-        gb.e[q].C0 = b.e[q].A;
-        gb.e[q].C = b.e[q].A;
-        gb.e[q].alpha = -1.0;
-        gb.e[q].beta = 1.0;
+      cudaStream_t hi = s, lo = s;
+      if (ss) {
+        hi = ss->hi;
+        lo = ss->lo;
+        cudaEventRecord(ss->fork, s);
+        cudaStreamWaitEvent(hi, ss->fork, 0);
+        cudaStreamWaitEvent(lo, ss->fork, 0);
       }
-      for (int k0 = 0; k0 < nt; k0 += kSweepPanel) {
-        const int bw = std::min(kSweepPanel, nt - k0);
-        g_launch_count += 2 + 2 * bw;
-        {
-          ProfScope ps_(s, PROF_PANEL);
-          k_bsweep_gather<T><<<dim3(nt, b.count), 256, 0, s>>>(b, k0, bw, n_pad);
+      // C -= A B^T through the tensor cores, timed under class cls
+      auto tc_update = [&](cudaStream_t st, const GemmBatch<float> &gb, int M, int N, int K, int ldc, bool lower,
+                           int cls, double work) {
+        Profiler::Rec rec{cls, nullptr, nullptr, 0.0};
+        const bool prof = g_prof != nullptr;
+        if (prof) {
+          rec.work = work;
+          g_prof->begin(st, rec);
         }
+        Profiler *saved = g_prof;
+        g_prof = nullptr;  // timed under cls, not as a GEMM
+        launch_tc_gemm(st, gb, M, N, K, ldw, ldw, ldc, lower, tc_passes, err_flag);
+        g_prof = saved;
+        if (prof) g_prof->end(st, rec);
+      };
+      const int n_panels = (nt + kSweepPanel - 1) / kSweepPanel;
+      ++g_launch_count;
+      {
+        ProfScope ps_(hi, PROF_PANEL);
+        k_bsweep_gather<T><<<dim3(nt, b.count), 256, 0, hi>>>(b, 0, std::min(kSweepPanel, nt), n_pad, 0);
+      }
+      for (int p = 0; p < n_panels; ++p) {
+        const int k0 = p * kSweepPanel, bw = std::min(kSweepPanel, nt - k0), cur = p & 1;
+        g_launch_count += 2 * bw;
         for (int q = 0; q < bw; ++q) {
           {
-            ProfScope ps_(s, PROF_PIVOT, 2.0 * 64.0 * 64.0 * 64.0 * b.count);
-            k_bsweep_pivot<T><<<b.count, 256, 0, s>>>(b, k0, q, bw, err_flag);
+            ProfScope ps_(hi, PROF_PIVOT, 2.0 * 64.0 * 64.0 * 64.0 * b.count);
+            k_bsweep_pivot<T><<<b.count, 256, 0, hi>>>(b, k0, q, bw, cur, err_flag);
           }
           {
-            ProfScope ps_(s, PROF_PANEL);
-            k_bsweep_panel<T><<<dim3(nt, b.count), 256, 0, s>>>(b, k0, q, bw);
+            ProfScope ps_(hi, PROF_PANEL);
+            k_bsweep_panel<T><<<dim3(nt, b.count), 256, 0, hi>>>(b, k0, q, bw, cur);
           }
+        }
+        if (ss) cudaEventRecord(ss->panel, hi);
+        if (p + 1 < n_panels) {
+          const int k1 = k0 + bw, bw1 = std::min(kSweepPanel, nt - k1);
+          // columns K' as the previous update and scatter left them
+          if (ss && p > 0) cudaStreamWaitEvent(hi, ss->scatter, 0);
+          g_launch_count += 2;
+          {
+            ProfScope ps_(hi, PROF_PANEL);
+            k_bsweep_gather<T><<<dim3(nt, b.count), 256, 0, hi>>>(b, k1, bw1, n_pad, cur ^ 1);
+          }
+          if (ss) cudaEventRecord(ss->gather, hi);
+          GemmBatch<float> fb{};
+          fb.count = b.count;
+          for (int e = 0; e < b.count; ++e) {
+            fb.e[e].A = b.e[e].Up[cur];
+            fb.e[e].B = b.e[e].Vp[cur] + (int64_t)k1 * 64 * ldw;
+            fb.e[e].C0 = b.e[e].Wp[cur ^ 1];
+            fb.e[e].C = b.e[e].Wp[cur ^ 1];
+            fb.e[e].alpha = -1.0;
+            fb.e[e].beta = 1.0;
+          }
+          tc_update(hi, fb, n_pad, 64 * bw1, 64 * bw, ldw, false, PROF_PANEL,
+                    2.0 * n_pad * 64.0 * bw1 * 64.0 * bw * b.count);
+          {
+            ProfScope ps_(hi, PROF_PANEL);
+            k_bsweep_rows<T><<<dim3(bw * bw1, b.count), 256, 0, hi>>>(b, k0, bw, k1, bw1, cur);
+          }
+        }
+        if (ss) {
+          cudaStreamWaitEvent(lo, ss->panel, 0);
+          if (p + 1 < n_panels) cudaStreamWaitEvent(lo, ss->gather, 0);
         }
         if (nt > bw) {
-          Profiler::Rec rec{PROF_SWEEP, nullptr, nullptr, 0.0};
-          if (g_prof) {
-            // algorithmic work: the rank-64 bw update of the lower tiles off
-            // the panel's rows and columns
-            const double rest = (double)(nt - bw) * (nt - bw + 1) / 2.0;
-            rec.work = 2.0 * 64.0 * 64.0 * 64.0 * bw * rest * b.count;
-            g_prof->begin(s, rec);
+          GemmBatch<float> gb{};
+          gb.count = b.count;
+          for (int e = 0; e < b.count; ++e) {
+            gb.e[e].A = b.e[e].Up[cur];
+            gb.e[e].B = b.e[e].Vp[cur];
+            gb.e[e].C0 = b.e[e].A;
+            gb.e[e].C = b.e[e].A;
+            gb.e[e].alpha = -1.0;
+            gb.e[e].beta = 1.0;
           }
-          const bool prof = g_prof != nullptr;
-          Profiler *saved = g_prof;
-          g_prof = nullptr;  // timed as the sweep, not as a GEMM
-          launch_tc_gemm(s, gb, n_pad, n_pad, 64 * bw, ldw, ldw, n_pad, true, tc_passes, err_flag);
-          g_prof = saved;
-          if (prof) g_prof->end(s, rec);
+          // algorithmic work: the rank-64 bw update of the lower tiles off the
+          // panel's rows and columns
+          const double rest = (double)(nt - bw) * (nt - bw + 1) / 2.0;
+          tc_update(lo, gb, n_pad, n_pad, 64 * bw, n_pad, true, PROF_SWEEP,
+                    2.0 * 64.0 * 64.0 * 64.0 * bw * rest * b.count);
         }
+        ++g_launch_count;
         {
-          ProfScope ps_(s, PROF_PANEL);
-          k_bsweep_scatter<T><<<dim3(nt, b.count), 256, 0, s>>>(b, k0, bw, n_pad);
+          ProfScope ps_(lo, PROF_PANEL);
+          k_bsweep_scatter<T><<<dim3(nt, b.count), 256, 0, lo>>>(b, k0, bw, n_pad, cur);
         }
+        if (ss) cudaEventRecord(ss->scatter, lo);
       }
+      if (ss) cudaStreamWaitEvent(s, ss->scatter, 0);
       ++g_launch_count;
       {
         ProfScope ps_(s, PROF_PANEL);
@@ -528,8 +607,9 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
     k_sweep_mirror<T><<<dim3(n_lower, b.count), 256, 0, s>>>(b, n_pad, -1.0);
   }
 }
-template void spd_inverse<double>(cudaStream_t, const SweepBatch<double> &, int, int32_t *, int);
-template void spd_inverse<float>(cudaStream_t, const SweepBatch<float> &, int, int32_t *, int);
+template void spd_inverse<double>(cudaStream_t, const SweepBatch<double> &, int, int32_t *, int,
+                                  const SweepStreams *);
+template void spd_inverse<float>(cudaStream_t, const SweepBatch<float> &, int, int32_t *, int, const SweepStreams *);
 
 template <typename T>
 void launch_mirror(cudaStream_t s, const SweepBatch<T> &b, int n_pad) {

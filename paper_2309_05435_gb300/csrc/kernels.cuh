@@ -200,10 +200,17 @@ template <typename T>
 struct SweepEntry {
   T *A;          // n_pad x n_pad, row-major, lower tiles used
   T *P;          // 64 x 64 scratch
-  T *U, *V;      // n_pad x 64 scratch each (tile-major); n_pad x 64 kSweepPanel
-                 // (row-major) on the tensor-core path
-  T *W;          // tensor-core path: column panel, n_pad x 64 kSweepPanel
+  T *U, *V;      // n_pad x 64 scratch each (tile-major)
+  // tensor-core path, one set per panel parity: the products U, the pivot
+  // columns V and the column panel W, n_pad x 64 kSweepPanel each (row-major)
+  T *Up[2], *Vp[2], *Wp[2];
   T *Vk;         // tensor-core path: 64 kSweepPanel x 64 (panel rows of the pivot column)
+};
+// Streams and events of the tensor-core sweep's look-ahead: the panels run on
+// hi (high priority), the rank-64 kSweepPanel updates and scatters on lo.
+struct SweepStreams {
+  cudaStream_t hi = nullptr, lo = nullptr;
+  cudaEvent_t fork = nullptr, panel = nullptr, gather = nullptr, scatter = nullptr;
 };
 template <typename T>
 struct SweepBatch {
@@ -215,9 +222,12 @@ struct SweepBatch {
 // double.  err_flag gets bit 0 on a non-positive pivot.  For float with
 // tc_passes > 0 the pivots are taken kSweepPanel at a time on a gathered column
 // panel and the rest of the matrix gets one rank-64 kSweepPanel update per
-// panel on the tcgen05 tensor cores (W, Vk and the wide U, V are needed).
+// panel on the tcgen05 tensor cores (Up, Vp, Wp and Vk are needed).  With ss the
+// next panel is pivoted on ss->hi while the update of the current one runs on
+// ss->lo (both joined back into s); without it everything runs on s.
 template <typename T>
-void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err_flag, int tc_passes = 0);
+void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err_flag, int tc_passes = 0,
+                 const SweepStreams *ss = nullptr);
 // Copy the lower tiles of each e[].A into its upper triangle (symmetric fill).
 template <typename T>
 void launch_mirror(cudaStream_t s, const SweepBatch<T> &b, int n_pad);
