@@ -197,7 +197,8 @@ typedef struct {
  * Algorithm 3), and allocate device memory.  No estimator work runs yet.
  *   out        receives the context (set to NULL on failure).
  *   overlap    n_l >= 0 slabs.
- * Errors: QSEL_EINVAL (shapes, mesh, mask, partition, options),
+ * Errors: QSEL_EINVAL (shapes, mesh, mask, partition, options; a row of
+ *         Q_s = K C^-1 K with more than 64 pattern entries),
  *         QSEL_ENOMEM, QSEL_ECUDA.
  */
 qsel_status qsel_create(qsel_ctx **out, const qsel_model *model, const qsel_theta *theta,

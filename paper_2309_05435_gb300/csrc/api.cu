@@ -462,9 +462,13 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   TRY(upload(c, &d_sp, slice_ptr));
   TRY(upload(c, &d_sw, slice_width));
   TRY(upload(c, &d_col, col));
+  if (max_w > kMaxPatternWidth)
+    return fail(QSEL_EINVAL, "the pattern of Q_s has a row with " + std::to_string(max_w) +
+                                 " entries; at most " + std::to_string(kMaxPatternWidth) + " are supported");
   c->pat.n_rows = n_s;
   c->pat.n_slices = n_slices;
   c->pat.max_width = max_w;
+  if (!configure_pattern_kernels(c->pat)) return fail(QSEL_ECUDA, "shared-memory opt-in of the gather kernels failed");
   c->pat.slice_ptr = d_sp;
   c->pat.slice_width = d_sw;
   c->pat.col = d_col;

@@ -626,43 +626,68 @@ template void launch_mirror<float>(cudaStream_t, const SweepBatch<float> &, int)
 
 // ---------------------------------------------------------------------------
 // Out = alpha Q_s B + beta C on the spatial pattern (row gather): one warp per
-// (row, 64-column chunk), warp-uniform pattern entries, 2 elements per lane.
-// Accumulation in the output type.
+// row, the row's pattern entries staged once in the warp's shared slots, then
+// four 64-column chunks at a time (2 elements per lane per chunk, eight
+// independent loads per pattern entry).  Accumulation in the output type.
 // ---------------------------------------------------------------------------
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(256) k_sp_rowgather(SpBatch<TI, TO> bt, SellPattern pat,
                                                       const double *__restrict__ val, int n_s,
                                                       int n_pad, int ncol, int ldb, int ldo) {
+  extern __shared__ __align__(16) unsigned char rg_smem[];
   const SpEntry<TI, TO> e = bt.e[blockIdx.y];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int *w_col = reinterpret_cast<int *>(rg_smem) + warp * pat.max_width;
+  TO *w_val = reinterpret_cast<TO *>(reinterpret_cast<int *>(rg_smem) + 8 * pat.max_width) + warp * pat.max_width;
   const int nch = ncol / 64;
   const TO alpha = (TO)(e.alpha * (e.alpha_ptr ? *e.alpha_ptr : 1.0));
-  const int64_t items = (int64_t)n_pad * nch;
-  for (int64_t it = (int64_t)blockIdx.x * 8 + warp; it < items; it += (int64_t)gridDim.x * 8) {
-    const int row = (int)(it / nch);
-    const int col = (int)(it - (int64_t)row * nch) * 64 + 2 * lane;
-    TO a0 = TO(0), a1 = TO(0);
+  const bool add_c = e.C != nullptr && e.beta != 0.0;
+  const TO beta = (TO)e.beta;
+  for (int row = blockIdx.x * 8 + warp; row < n_pad; row += gridDim.x * 8) {
+    int w = 0;
     if (row < n_s) {
       const int sl = row >> 5, li = row & 31;
-      const int w = pat.slice_width[sl];
+      w = pat.slice_width[sl];
       const int base = pat.slice_ptr[sl] + li;
-      for (int s = 0; s < w; ++s) {
-        const int j = pat.col[base + s * kSlice];
-        const TO v = (TO)val[base + s * kSlice];
-        const TI *bp = e.B + (int64_t)j * ldb + col;
-        a0 = fma(v, (TO)bp[0], a0);
-        a1 = fma(v, (TO)bp[1], a1);
+      for (int s = lane; s < w; s += 32) {
+        w_col[s] = pat.col[base + s * kSlice];
+        w_val[s] = (TO)val[base + s * kSlice];
       }
     }
-    a0 *= alpha;
-    a1 *= alpha;
-    const int64_t idx = (int64_t)row * ldo + col;
-    if (e.C != nullptr && e.beta != 0.0) {
-      a0 = fma((TO)e.beta, e.C[idx], a0);
-      a1 = fma((TO)e.beta, e.C[idx + 1], a1);
+    __syncwarp();
+    TO *orow = e.Out + (int64_t)row * ldo;
+    const TO *crow = add_c ? e.C + (int64_t)row * ldo : nullptr;
+    for (int ch0 = 0; ch0 < nch; ch0 += 4) {
+      TO acc[4][2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = TO(0);
+      for (int s = 0; s < w; ++s) {
+        const TI *bp = e.B + (int64_t)w_col[s] * ldb + 2 * lane;
+        const TO v = w_val[s];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (ch0 + u < nch) {
+            const int col = (ch0 + u) * 64;
+            acc[u][0] = fma(v, (TO)bp[col], acc[u][0]);
+            acc[u][1] = fma(v, (TO)bp[col + 1], acc[u][1]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (ch0 + u < nch) {
+          const int col = (ch0 + u) * 64 + 2 * lane;
+          TO a0 = acc[u][0] * alpha, a1 = acc[u][1] * alpha;
+          if (add_c) {
+            a0 = fma(beta, crow[col], a0);
+            a1 = fma(beta, crow[col + 1], a1);
+          }
+          orow[col] = a0;
+          orow[col + 1] = a1;
+        }
+      }
     }
-    e.Out[idx] = a0;
-    e.Out[idx + 1] = a1;
+    __syncwarp();  // the slots are refilled for the next row
   }
 }
 
@@ -671,12 +696,12 @@ void launch_sp_rowgather(cudaStream_t s, const SpBatch<TI, TO> &b, const SellPat
                          int n_s, int n_pad, int ncol, int ldb, int ldo) {
   if (b.count <= 0) return;
   ++g_launch_count;
-  int64_t items = (int64_t)n_pad * (ncol / 64);
-  int grid = (int)((items + 7) / 8);
+  int grid = (n_pad + 7) / 8;
   if (grid > 152 * 8) grid = 152 * 8;
+  const size_t smem = (size_t)8 * pat.max_width * (sizeof(int) + sizeof(TO));
   {
     ProfScope ps_(s, PROF_GATHER);
-    k_sp_rowgather<TI, TO><<<dim3(grid, b.count), 256, 0, s>>>(b, pat, val, n_s, n_pad, ncol, ldb, ldo);
+    k_sp_rowgather<TI, TO><<<dim3(grid, b.count), 256, smem, s>>>(b, pat, val, n_s, n_pad, ncol, ldb, ldo);
   }
 }
 template void launch_sp_rowgather<double, double>(cudaStream_t, const SpBatch<double, double> &,
@@ -687,32 +712,59 @@ template void launch_sp_rowgather<double, float>(cudaStream_t, const SpBatch<dou
                                                  const SellPattern &, const double *, int, int, int, int, int);
 
 // ---------------------------------------------------------------------------
-// Out = alpha B Q_s + beta C (column gather over the symmetric pattern:
-// (B Q_s)[r, l] = sum_{j in pat(l)} B[r, j] Q_s[l, j]); rows and columns past
-// n_s of Out are zero.  With B = D^-1 (symmetric) this is (Q_s D^-1)^T.
+// Column gathers over the symmetric pattern, (B Q_s)[r, l] =
+// sum_{j in pat(l)} B[r, j] Q_s[l, j].  A block covers 256 columns and
+// kGatherRows rows; each thread keeps its column's pattern (j, Q_s[l, j]) in
+// its own shared slots [s * 256 + t] (no sharing, no block barrier) and reuses
+// it for every row.  Shared memory: max_width * 256 * (4 + sizeof(T)) bytes.
 // ---------------------------------------------------------------------------
+constexpr int kGatherRows = 16;
+
+template <typename T>
+__device__ __forceinline__ int stage_col_pattern(const SellPattern &pat, const double *__restrict__ val, int l,
+                                                 int n_s, int *s_col, T *s_val) {
+  if (l >= n_s) return 0;
+  const int sl = l >> 5, li = l & 31;
+  const int w = pat.slice_width[sl];
+  const int base = pat.slice_ptr[sl] + li;
+  for (int s = 0; s < w; ++s) {
+    s_col[s * 256 + threadIdx.x] = pat.col[base + s * kSlice];
+    s_val[s * 256 + threadIdx.x] = (T)val[base + s * kSlice];
+  }
+  return w;
+}
+
+template <typename T>
+size_t col_pattern_smem(const SellPattern &pat) {
+  return (size_t)pat.max_width * 256 * (sizeof(int) + sizeof(T));
+}
+
+// Out = alpha B Q_s + beta C; rows and columns past n_s of Out are zero.  With
+// B = D^-1 (symmetric) this is (Q_s D^-1)^T.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sp_colgather(SpBatch<T, T> bt, SellPattern pat,
                                                       const double *__restrict__ val, int n_s, int n_pad) {
+  extern __shared__ __align__(16) unsigned char cg_smem[];
+  int *s_col = reinterpret_cast<int *>(cg_smem);
+  T *s_val = reinterpret_cast<T *>(s_col + pat.max_width * 256);
   const SpEntry<T, T> e = bt.e[blockIdx.z];
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y;
+  const int l = blockIdx.x * 256 + threadIdx.x;
   if (l >= n_pad) return;
-  T out = T(0);
-  if (r < n_s && l < n_s) {
-    const int sl = l >> 5, li = l & 31;
-    const int w = pat.slice_width[sl];
-    const int base = pat.slice_ptr[sl] + li;
-    const T *Br = e.B + (int64_t)r * n_pad;
-    T acc = T(0);
-    for (int s = 0; s < w; ++s) {
-      const int j = pat.col[base + s * kSlice];
-      acc = fma(Br[j], (T)val[base + s * kSlice], acc);
+  const int w = stage_col_pattern(pat, val, l, n_s, s_col, s_val);
+  const T alpha = (T)(e.alpha * (e.alpha_ptr ? *e.alpha_ptr : 1.0));
+  const bool add_c = e.C != nullptr && e.beta != 0.0;
+  const int r1 = min(n_pad, (int)(blockIdx.y + 1) * kGatherRows);
+  for (int r = blockIdx.y * kGatherRows; r < r1; ++r) {
+    T out = T(0);
+    if (r < n_s && l < n_s) {
+      const T *Br = e.B + (int64_t)r * n_pad;
+      T acc = T(0);
+      for (int s = 0; s < w; ++s) acc = fma(Br[s_col[s * 256 + threadIdx.x]], s_val[s * 256 + threadIdx.x], acc);
+      out = alpha * acc;
+      if (add_c) out = fma((T)e.beta, e.C[(int64_t)r * n_pad + l], out);
     }
-    out = (T)(e.alpha * (e.alpha_ptr ? *e.alpha_ptr : 1.0)) * acc;
-    if (e.C != nullptr && e.beta != 0.0) out = fma((T)e.beta, e.C[(int64_t)r * n_pad + l], out);
+    e.Out[(int64_t)r * n_pad + l] = out;
   }
-  e.Out[(int64_t)r * n_pad + l] = out;
 }
 
 template <typename T>
@@ -720,10 +772,10 @@ void launch_sp_colgather(cudaStream_t s, const SpBatch<T, T> &b, const SellPatte
                          int n_s, int n_pad) {
   if (b.count <= 0) return;
   ++g_launch_count;
-  dim3 grid((n_pad + 255) / 256, n_pad, b.count);
+  dim3 grid((n_pad + 255) / 256, (n_pad + kGatherRows - 1) / kGatherRows, b.count);
   {
     ProfScope ps_(s, PROF_GATHER);
-    k_sp_colgather<T><<<grid, 256, 0, s>>>(b, pat, val, n_s, n_pad);
+    k_sp_colgather<T><<<grid, 256, col_pattern_smem<T>(pat), s>>>(b, pat, val, n_s, n_pad);
   }
 }
 template void launch_sp_colgather<double>(cudaStream_t, const SpBatch<double, double> &, const SellPattern &,
@@ -762,38 +814,55 @@ template void launch_diag64_rows<float>(cudaStream_t, const DiagRowBatch<float> 
 
 // ---------------------------------------------------------------------------
 // D = a0 Q_s + w_obs diag(obs) - c W Q_s (column gather over the symmetric
-// pattern: (W Q_s)[r, l] = sum_{j in pat(l)} W[r, j] Q_s[l, j]), in double.
+// pattern: (W Q_s)[r, l] = sum_{j in pat(l)} W[r, j] Q_s[l, j]), blocked and
+// staged like k_sp_colgather.  The Schur term accumulates in T; entries on
+// the pattern of Q_s (and the diagonal) are combined in double, the others
+// are -c times the Schur sum in T.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch<T> bt, SellPattern pat,
                                                         const double *__restrict__ qs, double obs_w,
                                                         int n_s, int n_pad) {
+  extern __shared__ __align__(16) unsigned char sa_smem[];
+  int *s_col = reinterpret_cast<int *>(sa_smem);
+  T *s_val = reinterpret_cast<T *>(s_col + pat.max_width * 256);
   const SchurEntry<T> e = bt.e[blockIdx.z];
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y;
+  const int l = blockIdx.x * 256 + threadIdx.x;
   if (l >= n_pad) return;
-  double out;
-  if (r < n_s && l < n_s) {
-    const int sl = l >> 5, li = l & 31;
-    const int w = pat.slice_width[sl];
-    const int base = pat.slice_ptr[sl] + li;
-    // the Schur term accumulates in T (FP32 in the mixed path)
-    T acc = T(0);
-    double aq = 0.0;
-    const T *Wr = e.W ? e.W + (int64_t)r * n_pad : nullptr;
-    for (int s = 0; s < w; ++s) {
-      const int j = pat.col[base + s * kSlice];
-      const double v = qs[base + s * kSlice];
-      if (Wr) acc = fma(Wr[j], (T)v, acc);
-      if (j == r) aq += v;
+  const int w = stage_col_pattern(pat, qs, l, n_s, s_col, s_val);
+  const int base = l < n_s ? pat.slice_ptr[l >> 5] + (l & 31) : 0;
+  const double a0 = *e.a0;
+  const double c = e.W ? *e.c : 0.0;
+  const T neg_c = (T)(-c);
+  const int r1 = min(n_pad, (int)(blockIdx.y + 1) * kGatherRows);
+  for (int r = blockIdx.y * kGatherRows; r < r1; ++r) {
+    T out;
+    if (r < n_s && l < n_s) {
+      const T *Wr = e.W ? e.W + (int64_t)r * n_pad : nullptr;
+      T acc = T(0);
+      double aq = 0.0;
+      bool on_pattern = false;
+      for (int s = 0; s < w; ++s) {
+        const int j = s_col[s * 256 + threadIdx.x];
+        if (Wr) acc = fma(Wr[j], s_val[s * 256 + threadIdx.x], acc);
+        if (j == r) {
+          aq += qs[base + s * kSlice];
+          on_pattern = true;
+        }
+      }
+      if (on_pattern || r == l) {
+        double o = a0 * aq;
+        if (r == l && e.obs[r]) o += obs_w;
+        if (Wr) o -= c * (double)acc;
+        out = (T)o;
+      } else {
+        out = Wr ? neg_c * acc : T(0);
+      }
+    } else {
+      out = (r == l) ? T(1) : T(0);
     }
-    out = (*e.a0) * aq;
-    if (r == l && e.obs[r]) out += obs_w;
-    if (Wr) out -= (*e.c) * (double)acc;
-  } else {
-    out = (r == l) ? 1.0 : 0.0;
+    e.D[(int64_t)r * n_pad + l] = out;
   }
-  e.D[(int64_t)r * n_pad + l] = (T)out;
 }
 
 template <typename T>
@@ -801,12 +870,35 @@ void launch_schur_assemble(cudaStream_t s, const SchurBatch<T> &b, const SellPat
                            const double *qs, double obs_w, int n_s, int n_pad) {
   if (b.count <= 0) return;
   ++g_launch_count;
-  dim3 grid((n_pad + 255) / 256, n_pad, b.count);
+  dim3 grid((n_pad + 255) / 256, (n_pad + kGatherRows - 1) / kGatherRows, b.count);
   {
     ProfScope ps_(s, PROF_SCHUR);
-    k_schur_assemble<T><<<grid, 256, 0, s>>>(b, pat, qs, obs_w, n_s, n_pad);
+    k_schur_assemble<T><<<grid, 256, col_pattern_smem<T>(pat), s>>>(b, pat, qs, obs_w, n_s, n_pad);
   }
 }
+// Opt the pattern-staging kernels in to the shared memory that
+// max_width needs (beyond the default 48 KB); false when it cannot be had.
+bool configure_pattern_kernels(const SellPattern &pat) {
+  const int cg_d = (int)col_pattern_smem<double>(pat), cg_f = (int)col_pattern_smem<float>(pat);
+  const int rg_d = 8 * pat.max_width * (int)(sizeof(int) + sizeof(double));
+  const int rg_f = 8 * pat.max_width * (int)(sizeof(int) + sizeof(float));
+  bool ok = true;
+  ok &= cudaFuncSetAttribute(k_sp_colgather<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, cg_d) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_sp_colgather<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cg_f) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_schur_assemble<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, cg_d) ==
+        cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_schur_assemble<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cg_f) ==
+        cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_sp_rowgather<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, rg_d) ==
+        cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_sp_rowgather<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, rg_f) ==
+        cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_sp_rowgather<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, rg_f) ==
+        cudaSuccess;
+  if (!ok) cudaGetLastError();
+  return ok;
+}
+
 template void launch_schur_assemble<double>(cudaStream_t, const SchurBatch<double> &, const SellPattern &,
                                             const double *, double, int, int);
 template void launch_schur_assemble<float>(cudaStream_t, const SchurBatch<float> &, const SellPattern &,

@@ -294,6 +294,11 @@ struct SchurBatch {
 template <typename T>
 void launch_schur_assemble(cudaStream_t s, const SchurBatch<T> &b, const SellPattern &pat,
                            const double *qs, double obs_w, int n_s, int n_pad);
+// The row / column gathers and the Schur assembly stage each row's or
+// column's pattern in shared memory; widest pattern they accept, and the
+// opt-in of those kernels to the shared memory pat.max_width needs.
+constexpr int kMaxPatternWidth = 64;
+bool configure_pattern_kernels(const SellPattern &pat);
 
 template <typename T>
 struct ExtractEntry {
