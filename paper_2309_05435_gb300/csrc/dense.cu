@@ -815,10 +815,19 @@ template void launch_diag64_rows<float>(cudaStream_t, const DiagRowBatch<float> 
 // ---------------------------------------------------------------------------
 // D = a0 Q_s + w_obs diag(obs) - c W Q_s (column gather over the symmetric
 // pattern: (W Q_s)[r, l] = sum_{j in pat(l)} W[r, j] Q_s[l, j]), blocked and
-// staged like k_sp_colgather.  The Schur term accumulates in T; entries on
-// the pattern of Q_s (and the diagonal) are combined in double, the others
-// are -c times the Schur sum in T.
+// staged like k_sp_colgather.  The Schur term accumulates in T.  Entries off
+// the pattern of Q_s are -c times the Schur sum in T; afterwards each thread
+// rewrites the entries of its column on the pattern (and the diagonal), at
+// most max_width of them, combining the terms in double.  Keeping that path
+// out of the row loop keeps the FP64 pipe out of the common case.
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T schur_sum(const T *__restrict__ Wr, int w, const int *s_col, const T *s_val) {
+  T acc = T(0);
+  for (int s = 0; s < w; ++s) acc = fma(Wr[s_col[s * 256 + threadIdx.x]], s_val[s * 256 + threadIdx.x], acc);
+  return acc;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch<T> bt, SellPattern pat,
                                                         const double *__restrict__ qs, double obs_w,
@@ -830,38 +839,45 @@ __global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch<T> bt, SellPa
   const int l = blockIdx.x * 256 + threadIdx.x;
   if (l >= n_pad) return;
   const int w = stage_col_pattern(pat, qs, l, n_s, s_col, s_val);
-  const int base = l < n_s ? pat.slice_ptr[l >> 5] + (l & 31) : 0;
+  const T neg_c = e.W ? (T)(-*e.c) : T(0);
+  const int r0 = blockIdx.y * kGatherRows, r1 = min(n_pad, r0 + kGatherRows);
+  for (int r = r0; r < r1; ++r) {
+    T out;
+    if (r < n_s && l < n_s)
+      out = e.W ? neg_c * schur_sum(e.W + (int64_t)r * n_pad, w, s_col, s_val) : T(0);
+    else
+      out = (r == l) ? T(1) : T(0);
+    e.D[(int64_t)r * n_pad + l] = out;
+  }
+  if (l >= n_s) return;
+  // entries on the pattern of column l within this block's rows, in double.
+  // A row can fill several slots (padding slots repeat the diagonal with a
+  // zero value): its first slot sums them all.
+  const int base = pat.slice_ptr[l >> 5] + (l & 31);
   const double a0 = *e.a0;
   const double c = e.W ? *e.c : 0.0;
-  const T neg_c = (T)(-c);
-  const int r1 = min(n_pad, (int)(blockIdx.y + 1) * kGatherRows);
-  for (int r = blockIdx.y * kGatherRows; r < r1; ++r) {
-    T out;
-    if (r < n_s && l < n_s) {
-      const T *Wr = e.W ? e.W + (int64_t)r * n_pad : nullptr;
-      T acc = T(0);
-      double aq = 0.0;
-      bool on_pattern = false;
-      for (int s = 0; s < w; ++s) {
-        const int j = s_col[s * 256 + threadIdx.x];
-        if (Wr) acc = fma(Wr[j], s_val[s * 256 + threadIdx.x], acc);
-        if (j == r) {
-          aq += qs[base + s * kSlice];
-          on_pattern = true;
-        }
-      }
-      if (on_pattern || r == l) {
-        double o = a0 * aq;
-        if (r == l && e.obs[r]) o += obs_w;
-        if (Wr) o -= c * (double)acc;
-        out = (T)o;
-      } else {
-        out = Wr ? neg_c * acc : T(0);
-      }
+  bool diag_seen = false;
+  for (int s = 0; s <= w; ++s) {
+    int r;
+    double aq = 0.0;
+    if (s < w) {
+      r = s_col[s * 256 + threadIdx.x];
+      diag_seen |= (r == l);
+      if (r < r0 || r >= r1 || r >= n_s) continue;
+      bool first = true;
+      for (int q = 0; q < s; ++q) first &= (s_col[q * 256 + threadIdx.x] != r);
+      if (!first) continue;
+      for (int q = s; q < w; ++q)
+        if (s_col[q * 256 + threadIdx.x] == r) aq += qs[base + q * kSlice];
     } else {
-      out = (r == l) ? T(1) : T(0);
+      if (diag_seen) break;
+      r = l;  // a diagonal outside the pattern still gets its observation term
+      if (r < r0 || r >= r1) continue;
     }
-    e.D[(int64_t)r * n_pad + l] = out;
+    double o = a0 * aq;
+    if (r == l && e.obs[r]) o += obs_w;
+    if (e.W) o -= c * (double)schur_sum(e.W + (int64_t)r * n_pad, w, s_col, s_val);
+    e.D[(int64_t)r * n_pad + l] = (T)o;
   }
 }
 
