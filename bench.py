@@ -471,7 +471,7 @@ def run_native(args):
         "gemm": ("dense tile GEMMs (tcgen05 3xTF32, TMA, TMEM)" if mixed else "k_gemm64 (FP64 dense tile GEMM)"),
         "sweep_update": ("sweep rank-64 updates (tcgen05 3xTF32)" if mixed else "k_sweep_update (FP64)"),
         "spmm": "k_bt_spmm (block-tridiagonal sliced-ELL SpMM, PCG)",
-        "pivot": "k_sweep_pivot (64x64 FP64 pivot-tile inverses)",
+        "pivot": "k_bsweep_pivot (64x64 pivot-tile inverses: FP64, or double-float on float tiles)",
         "precond": "k_pcg_precond (block-Jacobi apply, register-tiled)",
     }
     cand = [q for q, name in enumerate(classes) if name in desc and cwork[q] > 0 and cms[q] > 0]
@@ -486,10 +486,16 @@ def run_native(args):
         ach = 3.0 * cwork[dom] / (cms[dom] * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
                 "peak_source": tf32_src + "; achieved counts the three TF32 products of each 3xTF32 product"}
-    elif name == "pivot" or not mixed:
+    elif not mixed:
         ach = cwork[dom] / (cms[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "peak_source": "nominal FP64 rate (152 SMs x 2.07 GHz x 4 FLOP/clk); FMA-loop probe 1.19 TFLOP/s"}
+    elif name == "pivot":
+        # double-float pivots: about 15 FP32 operations per useful FLOP
+        ach = cwork[dom] / (cms[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS / 15.0, "unit": "TFLOP/s",
+                "peak_source": "FP32 CUDA-core rate from unit counts / 15 FP32 operations per double-float "
+                               "multiply-subtract"}
     else:
         ach = cwork[dom] / (cms[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -537,7 +543,7 @@ def run_native(args):
         cpu = {"value": est, "unit": "s", "cores": cpu_cores(), "kind": "oracle", "sample": desc,
                "sample_seconds": spent}
 
-    form = "mixed precision RBMC (FP32 PCG + FP64 refinement, FP32 tiles + FP64 pivots)" \
+    form = "mixed precision RBMC (FP32 PCG + FP64 refinement, FP32 tiles + double-float pivots)" \
         if chosen_prec == qsel.QSEL_MIXED else "plain FP64 RBMC"
     if planned:
         form += f" + learned control variate planner (target {args.target:g} RMS relative error)"

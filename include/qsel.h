@@ -77,8 +77,9 @@ enum {
 /* Arithmetic of the pipeline. */
 enum {
   QSEL_FP64 = 0,      /* every kernel computes in IEEE binary64                  */
-  QSEL_MIXED = 1      /* binary32 solves and factorisations, binary64 pivots,
-                         refinement residuals and accumulators                    */
+  QSEL_MIXED = 1      /* binary32 solves and factorisations, double-float
+                         (about 48-bit) pivot tiles, binary64 refinement
+                         residuals and accumulators                               */
 };
 
 /*

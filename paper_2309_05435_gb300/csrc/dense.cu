@@ -167,30 +167,51 @@ template void launch_gemm<float>(cudaStream_t, const GemmBatch<float> &, int, in
 // After every step the swept matrix holds -A^-1 (Goodnight's sweep operator);
 // the final mirror negates it and fills the upper triangle.
 // ---------------------------------------------------------------------------
-// The pivot tile is inverted in double whatever T is (the "FP64 pivots" of the
-// mixed path).
-// P = Tk^-1 for the 64 x 64 tile at Tk (row stride ld), from its lower half.
-template <typename T>
+// P = Tk^-1 for the 64 x 64 tile at Tk (row stride ld), from its lower half:
+// in double for double tiles, in double-float (about 48 bits, on the FP32
+// pipe) for float tiles.  NT threads.
+template <int NT, typename T>
 __device__ __forceinline__ void invert_pivot_tile(const T *Tk, int ld, T *P, int32_t *err_flag) {
-  __shared__ double S[64 * 65];
-  __shared__ double col[65], wv[64];
-  for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
-    const int r = idx >> 6, c = idx & 63;
+  if constexpr (std::is_same<T, float>::value) {
+    __shared__ dfloat Sf[64 * 65];
+    __shared__ dfloat colf[65], wvf[64];
     // the diagonal tile is kept symmetric; the lower half is what is read
-    if (r >= c) S[r * 65 + c] = (double)Tk[(int64_t)r * ld + c];
-  }
-  __syncthreads();
-  sym_sweep_inverse64_lower(S, 65, col, wv, err_flag);
-  for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
-    const int r = idx >> 6, c = idx & 63;
-    P[idx] = (T)(-S[(r >= c) ? r * 65 + c : c * 65 + r]);
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < 64 * 16; idx += NT) {
+      const int r = idx >> 4, c4 = (idx & 15) * 4;
+      const float4 v = *reinterpret_cast<const float4 *>(Tk + (int64_t)r * ld + c4);
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (r >= c4 + u) Sf[r * 65 + c4 + u] = dfloat{vv[u], 0.0f};
+    }
+    __syncthreads();
+    sym_sweep_inverse64_lower_df<NT>(Sf, 65, colf, wvf, err_flag);
+    for (int idx = threadIdx.x; idx < 64 * 64; idx += NT) {
+      const int r = idx >> 6, c = idx & 63;
+      const dfloat v = Sf[(r >= c) ? r * 65 + c : c * 65 + r];
+      P[idx] = -__fadd_rn(v.hi, v.lo);
+    }
+  } else {
+    __shared__ double S[64 * 65];
+    __shared__ double col[65], wv[64];
+    for (int idx = threadIdx.x; idx < 64 * 64; idx += NT) {
+      const int r = idx >> 6, c = idx & 63;
+      if (r >= c) S[r * 65 + c] = (double)Tk[(int64_t)r * ld + c];
+    }
+    __syncthreads();
+    sym_sweep_inverse64_lower<NT>(S, 65, col, wv, err_flag);
+    for (int idx = threadIdx.x; idx < 64 * 64; idx += NT) {
+      const int r = idx >> 6, c = idx & 63;
+      P[idx] = (T)(-S[(r >= c) ? r * 65 + c : c * 65 + r]);
+    }
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_sweep_pivot(SweepBatch<T> bt, int k, int ld, int32_t *err_flag) {
   const SweepEntry<T> e = bt.e[blockIdx.x];
-  invert_pivot_tile(e.A + (int64_t)k * 64 * ld + k * 64, ld, e.P, err_flag);
+  invert_pivot_tile<256>(e.A + (int64_t)k * 64 * ld + k * 64, ld, e.P, err_flag);
 }
 
 template <typename T>
@@ -258,15 +279,24 @@ __global__ void __launch_bounds__(256) k_bsweep_gather(SweepBatch<T> bt, int k0,
 
 // Pivot k = k0 + q of the panel: P = W_kq^-1 (FP64), and Vk = rows K of
 // column q as they stand before the pivot.
+constexpr int kPivotThreads = 512;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_bsweep_pivot(SweepBatch<T> bt, int k0, int q, int bw, int buf,
-                                                      int32_t *err_flag) {
+__global__ void __launch_bounds__(kPivotThreads) k_bsweep_pivot(SweepBatch<T> bt, int k0, int q, int bw, int buf,
+                                                                int32_t *err_flag) {
   const SweepEntry<T> e = bt.e[blockIdx.x];
   constexpr int ldw = 64 * kSweepPanel;
   const T *W = (buf ? e.Wp[1] : e.Wp[0]);
-  for (int idx = threadIdx.x; idx < bw * 4096; idx += 256)
-    e.Vk[idx] = W[(int64_t)(k0 * 64 + (idx >> 6)) * ldw + q * 64 + (idx & 63)];
-  invert_pivot_tile(W + (int64_t)(k0 + q) * 64 * ldw + q * 64, ldw, e.P, err_flag);
+  // 16-byte rows: ldw, q * 64 and the Vk row length are multiples of 4 elements
+  constexpr int V = 16 / sizeof(T);
+  using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < bw * 64 * (64 / V); idx += kPivotThreads) {
+    const int r = idx / (64 / V), c = (idx % (64 / V)) * V;
+    *reinterpret_cast<Vec *>(e.Vk + r * 64 + c) =
+        *reinterpret_cast<const Vec *>(W + (int64_t)(k0 * 64 + r) * ldw + q * 64 + c);
+  }
+  invert_pivot_tile<kPivotThreads>(W + (int64_t)(k0 + q) * 64 * ldw + q * 64, ldw, e.P, err_flag);
 }
 
 // One pivot on the panel, CTA per row tile i:
@@ -509,7 +539,7 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
         for (int q = 0; q < bw; ++q) {
           {
             ProfScope ps_(hi, PROF_PIVOT, 2.0 * 64.0 * 64.0 * 64.0 * b.count);
-            k_bsweep_pivot<T><<<b.count, 256, 0, hi>>>(b, k0, q, bw, cur, err_flag);
+            k_bsweep_pivot<T><<<b.count, kPivotThreads, 0, hi>>>(b, k0, q, bw, cur, err_flag);
           }
           {
             ProfScope ps_(hi, PROF_PANEL);

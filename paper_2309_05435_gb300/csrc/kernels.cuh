@@ -218,8 +218,8 @@ struct SweepBatch {
   int count;
 };
 // In-place SPD inverse by the blocked symmetric sweep; A becomes A^-1 with
-// both triangles filled.  The 64 x 64 pivot tiles are always inverted in
-// double.  err_flag gets bit 0 on a non-positive pivot.  For float with
+// both triangles filled.  The 64 x 64 pivot tiles are inverted in double
+// (double tiles) or double-float (float tiles).  err_flag gets bit 0 on a non-positive pivot.  For float with
 // tc_passes > 0 the pivots are taken kSweepPanel at a time on a gathered column
 // panel and the rest of the matrix gets one rank-64 kSweepPanel update per
 // panel on the tcgen05 tensor cores (Up, Vp, Wp and Vk are needed).  With ss the

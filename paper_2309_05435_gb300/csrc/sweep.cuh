@@ -41,15 +41,17 @@ __device__ inline void sym_sweep_inverse_smem(double *S, int ld_s, int b, int32_
 // 64 x 64 version of the sweep above for an SPD tile held in its lower
 // triangle: each pivot snapshots column p (c_i = S_ip) and w_j = c_j / d, then
 // every lower entry is updated with one FMA, S_ij - c_i w_j, by the thread
-// that owns it (2080 entries, at most 9 per thread; blockDim.x must be 256).
+// that owns it (2080 entries, ceil(2080 / NT) per thread; blockDim.x == NT).
 // Only the 64 column threads form 1 / d; thread 0 leaves it in col[64] for the
 // owner of the diagonal entry (col holds 65 doubles).  After the 64 pivots the
 // lower triangle holds that of -S^-1.
+template <int NT>
 __device__ inline void sym_sweep_inverse64_lower(double *S, int ld_s, double *col, double *wv, int32_t *err_flag) {
-  int ei[9], ej[9];
+  constexpr int EPT = (2080 + NT - 1) / NT;
+  int ei[EPT], ej[EPT];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    const int e = (int)threadIdx.x + q * (int)blockDim.x;
+  for (int q = 0; q < EPT; ++q) {
+    const int e = (int)threadIdx.x + q * NT;
     ei[q] = -1;
     ej[q] = 0;
     if (e < 2080) {
@@ -76,7 +78,7 @@ __device__ inline void sym_sweep_inverse64_lower(double *S, int ld_s, double *co
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
+    for (int q = 0; q < EPT; ++q) {
       if (ei[q] >= 0) {
         const int i = ei[q], j = ej[q];
         double v;
@@ -88,6 +90,105 @@ __device__ inline void sym_sweep_inverse64_lower(double *S, int ld_s, double *co
           v = wv[i];
         else
           v = fma(-col[i], wv[j], S[i * ld_s + j]);
+        S[i * ld_s + j] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (Dekker 1971, "A floating-point technique for
+// extending the available precision"; Knuth, TAOCP vol. 2, 4.2.2): a value is
+// hi + lo with |lo| <= ulp(hi) / 2, about 48 significant bits, on the FP32
+// pipe.  The _rn intrinsics keep the compiler from contracting or
+// reassociating the error terms.
+// ---------------------------------------------------------------------------
+struct dfloat {
+  float hi, lo;
+};
+// s + e = a + b exactly (Knuth's two-sum)
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+// the same for |a| >= |b| (Dekker's fast two-sum)
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);  // exact error of the product
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfloat df_sub(dfloat a, dfloat b) {
+  dfloat s = df_two_sum(a.hi, -b.hi);
+  s.lo = __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo));
+  return df_fast_two_sum(s.hi, s.lo);
+}
+// 1 / d: the float reciprocal and one Newton step r + r (1 - d r), whose
+// residual is formed exactly enough with two fused multiply-adds
+__device__ __forceinline__ dfloat df_recip(dfloat d) {
+  const float r = 1.0f / d.hi;
+  float t = __fmaf_rn(-d.hi, r, 1.0f);
+  t = __fmaf_rn(-d.lo, r, t);
+  return df_fast_two_sum(r, __fmul_rn(r, t));
+}
+
+// sym_sweep_inverse64_lower in double-float: S (64 x 64 lower triangle, row
+// stride ld_s) ends as the lower triangle of -S^-1; col holds 65 entries
+// (col[64] = 1 / d), wv 64.  blockDim.x == NT.
+template <int NT>
+__device__ inline void sym_sweep_inverse64_lower_df(dfloat *S, int ld_s, dfloat *col, dfloat *wv,
+                                                    int32_t *err_flag) {
+  constexpr int EPT = (2080 + NT - 1) / NT;
+  int ei[EPT], ej[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = (int)threadIdx.x + q * NT;
+    ei[q] = -1;
+    ej[q] = 0;
+    if (e < 2080) {
+      int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      while (i * (i + 1) / 2 > e) --i;
+      ei[q] = i;
+      ej[q] = e - i * (i + 1) / 2;
+    }
+  }
+  for (int p = 0; p < 64; ++p) {
+    if (threadIdx.x < 64) {
+      const dfloat d = S[p * ld_s + p];
+      const bool pos = d.hi > 0.0f;
+      const dfloat inv = pos ? df_recip(d) : dfloat{0.0f, 0.0f};
+      const int i = threadIdx.x;
+      const dfloat c = (i >= p) ? S[i * ld_s + p] : S[p * ld_s + i];
+      col[i] = c;
+      wv[i] = df_mul(c, inv);
+      if (i == 0) {
+        col[64] = inv;
+        if (!pos && err_flag) atomicOr(err_flag, 1);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      if (ei[q] >= 0) {
+        const int i = ei[q], j = ej[q];
+        dfloat v;
+        if (i == p && j == p)
+          v = dfloat{-col[64].hi, -col[64].lo};
+        else if (i == p)
+          v = wv[j];
+        else if (j == p)
+          v = wv[i];
+        else
+          v = df_sub(S[i * ld_s + j], df_mul(col[i], wv[j]));
         S[i * ld_s + j] = v;
       }
     }

@@ -1,5 +1,5 @@
 """Mixed-precision path (FP32 PCG with FP64 refinement, FP32 dense tiles with
-FP64 pivot tiles and FP64 diagonal accumulation) against the FP64 path and
+double-float pivot tiles and FP64 diagonal accumulation) against the FP64 path and
 the oracle.
 
 Stated per-result tolerances (relative, against the FP64 run of the same
