@@ -100,6 +100,9 @@ def parse_args():
     ap.add_argument("--batch-models", type=int, default=64)
     ap.add_argument("--batch-streams", type=int, default=16)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--profile-timed", action="store_true",
+                    help="bracket the timed steps of the chosen form with cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off)")
     ap.add_argument("--lanczos-eval", default=None,
                     help="comma list of Krylov dimensions: the Lanczos sampler against PCG at the workload")
     return ap.parse_args()
@@ -353,10 +356,15 @@ def run_native(args):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        profile = clocks and args.profile_timed
+        if profile:
+            torch.cuda.profiler.start()
         e0.record(stream)
         stats = [step() for _ in range(steps)]
         e1.record(stream)
         torch.cuda.synchronize()
+        if profile:
+            torch.cuda.profiler.stop()
         if world > 1:
             dist.barrier()
         clk = sampler.stop() if sampler else None

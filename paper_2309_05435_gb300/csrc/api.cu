@@ -51,6 +51,7 @@ struct DenseSlot {
   void *P = nullptr, *U = nullptr, *Vs = nullptr, *Vk = nullptr;  // sweep scratch
   void *U2 = nullptr, *V2 = nullptr, *Wp = nullptr, *Wp2 = nullptr;  // tensor-core sweep panels
   void *wbuf = nullptr;                // T_max x n_pad x ld correction samples
+  void *tra = nullptr, *trb = nullptr; // ld x n_pad transposes (tensor-core correction products)
   void *ybuf = nullptr, *tmp = nullptr, *bright = nullptr;
 };
 
@@ -641,7 +642,7 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   // 64 kSweepPanel each), Vk (64 kSweepPanel x 64) and P (64 x 64)
   const size_t panel = (size_t)n_pad * 64 * kSweepPanel * esz;
   const size_t per_slot = (size_t)(c->T_max + 5) * mat + 6 * panel + (size_t)(kSweepPanel + 1) * 64 * 64 * esz +
-                          (size_t)(c->T_max + 3) * svec + 4096;
+                          (size_t)(c->T_max + 5) * svec + 4096;
   size_t free_b = 0, total_b = 0;
   QSEL_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   const size_t fit = (size_t)(0.85 * (double)free_b) / per_slot;
@@ -670,6 +671,8 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
     TRY(c->alloc_bytes(&sl.ybuf, svec));
     TRY(c->alloc_bytes(&sl.tmp, svec));
     TRY(c->alloc_bytes(&sl.bright, svec));
+    TRY(c->alloc_bytes(&sl.tra, svec));
+    TRY(c->alloc_bytes(&sl.trb, svec));
   }
   QSEL_CUDA_TRY(cudaHostAlloc(&c->h_counters, 64, cudaHostAllocDefault));
   QSEL_CUDA_TRY(cudaHostAlloc(&c->h_small, 64 * sizeof(double), cudaHostAllocDefault));
@@ -1430,6 +1433,22 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
     }
     launch_sp_rowgather<double, T>(s, bl, c->pat, c->d_qs, n_s, n_pad, ld, ld, ld);
     launch_sp_rowgather<double, T>(s, br, c->pat, c->d_qs, n_s, n_pad, ld, ld, ld);
+    // D_t^-1 times an n_pad x ld block: on the tensor cores in the mixed path
+    // (through the transposed product, with each part's ld x n_pad scratch
+    // tra / trb), else the tile GEMM
+    void *bt[kMaxBatch], *pt[kMaxBatch];
+    auto block_product = [&](const GemmBatch<T> &gb) -> Err {
+      if constexpr (std::is_same<T, float>::value) {
+        if (c->tc_passes > 0) {
+          if (!launch_symm_block_tc(s, gb, reinterpret_cast<float *const *>(bt), reinterpret_cast<float *const *>(pt),
+                                    n_pad, ld, c->tc_passes, c->d_err))
+            return fail(QSEL_ECUDA, "tensor-core GEMM: tensor map encoding failed");
+          return ok();
+        }
+      }
+      launch_gemm<T>(s, gb, n_pad, ld, n_pad, n_pad, ld, ld, false);
+      return ok();
+    };
     for (int p : grp) {
       Subdomain &sd = c->parts[p];
       DenseSlot &sl = slot(p);
@@ -1442,6 +1461,8 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         Subdomain &sd = c->parts[p];
         DenseSlot &sl = slot(p);
         if (t >= sd.T) continue;
+        bt[ub.count] = sl.tra;
+        pt[ub.count] = sl.trb;
         GemmEntry<T> &g = ub.e[ub.count++];
         g.A = Dinv(p, t);
         g.B = buf(sl.ybuf);
@@ -1461,7 +1482,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         }
       }
       if (ub.count == 0) break;
-      launch_gemm<T>(s, ub, n_pad, ld, n_pad, n_pad, ld, ld, false);
+      TRY(block_product(ub));
       launch_sp_rowgather<T, T>(s, yb, c->pat, c->d_qs, n_s, n_pad, ld, ld, ld);
     }
     for (int b = 0; b < maxT; ++b) {
@@ -1479,6 +1500,8 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         e.alpha_ptr = c->tc.a1 + sd.e0 + t;
         e.alpha = 1.0;
         e.beta = 0.0;
+        bt[wb.count] = sl.tra;
+        pt[wb.count] = sl.trb;
         GemmEntry<T> &g = wb.e[wb.count++];
         g.A = Dinv(p, t);
         g.B = buf(sl.tmp);
@@ -1489,7 +1512,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       }
       if (tb.count == 0) break;
       launch_sp_rowgather<T, T>(s, tb, c->pat, c->d_qs, n_s, n_pad, ld, ld, ld);
-      launch_gemm<T>(s, wb, n_pad, ld, n_pad, n_pad, ld, ld, false);
+      TRY(block_product(wb));
     }
     CorrBatch<T> cb{};
     for (int p : grp) {

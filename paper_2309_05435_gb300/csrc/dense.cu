@@ -155,6 +155,62 @@ void launch_gemm(cudaStream_t s, const GemmBatch<T> &b, int M, int N, int K, int
     k_gemm64<T, false><<<grid, 256, 0, s>>>(b, K, lda, ldb, ldc);
   if (g_prof) g_prof->end(s, rec);
 }
+// ---------------------------------------------------------------------------
+// out[r, c] = alpha in[c, r] + beta c0[r, c]   (out, c0: rows x cols with row
+// stride ld_out; in: cols x rows with row stride ld_in), 32 x 32 tiles staged
+// in shared memory so that both sides are read and written along rows.
+// c0 may alias out (each entry is read and written by the same thread).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_transpose_axpby(TransBatch bt, int rows, int cols, int ld_in, int ld_out) {
+  __shared__ float tile[32][33];
+  const TransEntry e = bt.e[blockIdx.z];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    tile[i][threadIdx.x] = (c < cols && r < rows) ? e.in[(int64_t)c * ld_in + r] : 0.0f;
+  }
+  __syncthreads();
+  const bool add_c0 = e.c0 != nullptr && e.beta != 0.0f;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) {
+      float v = e.alpha * tile[threadIdx.x][i];
+      if (add_c0) v = fmaf(e.beta, e.c0[(int64_t)r * ld_out + c], v);
+      e.out[(int64_t)r * ld_out + c] = v;
+    }
+  }
+}
+
+void launch_transpose_axpby(cudaStream_t s, const TransBatch &b, int rows, int cols, int ld_in, int ld_out) {
+  if (b.count <= 0) return;
+  ++g_launch_count;
+  ProfScope ps_(s, PROF_CORR);
+  k_transpose_axpby<<<dim3((cols + 31) / 32, (rows + 31) / 32, b.count), dim3(32, 8), 0, s>>>(b, rows, cols, ld_in,
+                                                                                              ld_out);
+}
+
+bool launch_symm_block_tc(cudaStream_t s, const GemmBatch<float> &b, float *const *bt, float *const *pt, int n_pad,
+                          int ld, int passes, int32_t *err) {
+  if (b.count <= 0) return true;
+  TransBatch tin{}, tout{};
+  GemmBatch<float> g{};
+  tin.count = tout.count = g.count = b.count;
+  for (int q = 0; q < b.count; ++q) {
+    tin.e[q] = TransEntry{b.e[q].B, nullptr, bt[q], 1.0f, 0.0f};
+    g.e[q].A = bt[q];
+    g.e[q].B = b.e[q].A;
+    g.e[q].C0 = nullptr;
+    g.e[q].C = pt[q];
+    g.e[q].alpha = 1.0;
+    g.e[q].beta = 0.0;
+    tout.e[q] = TransEntry{pt[q], b.e[q].C0, b.e[q].C, (float)b.e[q].alpha, (float)b.e[q].beta};
+  }
+  launch_transpose_axpby(s, tin, ld, n_pad, ld, n_pad);
+  if (!launch_tc_gemm(s, g, ld, n_pad, n_pad, n_pad, n_pad, n_pad, false, passes, err)) return false;
+  launch_transpose_axpby(s, tout, n_pad, ld, n_pad, ld);
+  return true;
+}
+
 template void launch_gemm<double>(cudaStream_t, const GemmBatch<double> &, int, int, int, int, int, int, bool);
 template void launch_gemm<float>(cudaStream_t, const GemmBatch<float> &, int, int, int, int, int, int, bool);
 

@@ -277,6 +277,24 @@ void launch_diag64_rows(cudaStream_t s, const DiagRowBatch<T> &b, int n_s, int n
 bool tc_gemm_available();
 bool launch_tc_gemm(cudaStream_t s, const GemmBatch<float> &b, int M, int N, int K, int lda, int ldb, int ldc,
                     bool lower, int passes, int32_t *err);
+// out[r, c] = alpha in[c, r] + beta c0[r, c] for each entry (see dense.cu).
+struct TransEntry {
+  const float *in, *c0;
+  float *out;
+  float alpha, beta;
+};
+struct TransBatch {
+  TransEntry e[kMaxBatch];
+  int count;
+};
+void launch_transpose_axpby(cudaStream_t s, const TransBatch &b, int rows, int cols, int ld_in, int ld_out);
+// C = alpha A B + beta C0 on the tensor cores for an n_pad x n_pad A
+// (b.e[].A) and row-major n_pad x ld blocks B, C0, C: Bt = B^T, then the
+// K-major product Pt = Bt A^T (= (A B)^T, A row-major serves as the N x K
+// operand), C = alpha Pt^T + beta C0; bt[q], pt[q] are ld x n_pad scratch.
+// False when a tensor map cannot be encoded.
+bool launch_symm_block_tc(cudaStream_t s, const GemmBatch<float> &b, float *const *bt, float *const *pt, int n_pad,
+                          int ld, int passes, int32_t *err);
 
 template <typename T>
 struct SchurEntry {
