@@ -110,6 +110,7 @@ struct qsel_ctx {
   bool kron = false;
   int kron_m = 0;
   double *d_kV = nullptr, *d_klam = nullptr, *d_kdh = nullptr, *d_kU = nullptr, *d_kmu = nullptr;
+  void *d_ktab = nullptr;              // the operator's tables in the sampler's element type
   double kron_rho = -2.0;              // rho of the temporal eigenpairs on the device
   KronOperator kop{};
   // Lanczos sampler (allocated on first use)
@@ -368,6 +369,21 @@ static Err kron_setup(qsel_ctx *c, const qsel_model *m) {
   TRY(upload(c, &c->d_kdh, dh));
   TRY(c->alloc(&c->d_kU, (size_t)c->n_t * c->n_t));
   TRY(c->alloc(&c->d_kmu, (size_t)c->n_t));
+  {
+    // V, V^T, U, U^T, dh dh^T, spec (KronOperator), each segment 16-byte aligned
+    const size_t esz = c->mixed ? sizeof(float) : sizeof(double);
+    const size_t seg[6] = {(size_t)g * g, (size_t)g * g, (size_t)c->n_t * c->n_t, (size_t)c->n_t * c->n_t,
+                           (size_t)g * g, (size_t)c->n_t * g * g};
+    size_t off[6], total = 0;
+    for (int i = 0; i < 6; ++i) {
+      off[i] = total;
+      total += (seg[i] * esz + 255) / 256 * 256;
+    }
+    TRY(c->alloc_bytes(&c->d_ktab, total));
+    char *b = static_cast<char *>(c->d_ktab);
+    void **dst[6] = {&c->kop.tV, &c->kop.tVT, &c->kop.tU, &c->kop.tUT, &c->kop.dhdh, &c->kop.spec};
+    for (int i = 0; i < 6; ++i) *dst[i] = b + off[i];
+  }
   c->kron = true;
   c->kron_m = g;
   return ok();
@@ -403,6 +419,11 @@ static Err kron_prepare(qsel_ctx *c) {
   k.kappa2 = std::exp(2.0 * c->theta.log_kappa);
   k.tau = std::exp(c->theta.log_tau);
   k.omega = (double)c->n_obs / (double)c->n * c->obs_w;
+  if (c->mixed)
+    launch_kron_tables<float>(c->stream, k);
+  else
+    launch_kron_tables<double>(c->stream, k);
+  QSEL_CUDA_TRY(cudaGetLastError());
   return ok();
 }
 

@@ -377,21 +377,27 @@ void launch_part_error_sums(cudaStream_t s, const double *m2, const double *m4, 
 enum KronMode { KRON_NONE = 0, KRON_IN_DH = 1, KRON_OUT_DH = 2, KRON_OUT_SPEC = 3 };
 // One pass y_g = op(B) x_g over the groups g of rows base(g) + k kstride.
 struct KronPass {
-  const double *B;          // dim x dim, row-major
-  int dim, trans, mode, m;
+  const void *Bt;           // op(B)^T, dim x dim row-major, in the pass's element type
+  int dim, mode, m;
   int64_t kstride;          // rows between consecutive k
   int n_outer, n_inner;
   int64_t outer_stride, inner_stride;   // base(g) = (g / n_inner) outer + (g % n_inner) inner
   int ld;
-  const double *dh, *lam, *mu;
-  double kappa2, tau, omega;
+  const void *scale;        // KRON_IN_DH / KRON_OUT_DH: dh_k dh_g (m x m);
+                            // KRON_OUT_SPEC: the spectral scaling (n_t x m^2)
 };
 // The preconditioner's factors (device arrays) and scalars for one theta.
 struct KronOperator {
   int m, n_t, ld;
   const double *V, *U, *dh, *lam, *mu;
   double kappa2, tau, omega;
+  // tables in the sampler's element type, rebuilt by launch_kron_tables:
+  // V, V^T, U, U^T, dh_i dh_j (m x m), spec[t m^2 + s] = 1 / (tau mu_t
+  // (kappa^2 + lambda_a + lambda_b)^2 + omega) with s = a m + b
+  void *tV, *tVT, *tU, *tUT, *dhdh, *spec;
 };
+template <typename T>
+void launch_kron_tables(cudaStream_t s, const KronOperator &op);
 template <typename T>
 void launch_kron_pass(cudaStream_t s, const KronPass &p, const T *x, T *y);
 template <typename T>

@@ -38,6 +38,8 @@ __global__ void __launch_bounds__(256) k_kron_pass(const KronPass p, const T *__
   constexpr int E16 = 16 / (int)sizeof(T);
   extern __shared__ __align__(16) unsigned char smem_kron[];
   T *Bs = reinterpret_cast<T *>(smem_kron);                 // Bs[k * BP + o] = op(B)[o][k]
+  const T *Bt = static_cast<const T *>(p.Bt);
+  const T *scale = static_cast<const T *>(p.scale);
   T *xs = Bs + kKT * SM::BP;                                // xs[k * XP + c]
   const int tid = threadIdx.x, rg = tid >> 5, cg = tid & 31;
   const int row_tiles = (p.dim + kKT - 1) / kKT;
@@ -62,9 +64,7 @@ __global__ void __launch_bounds__(256) k_kron_pass(const KronPass p, const T *__
       for (int e = tid; e < kKT * kKT; e += blockDim.x) {
         const int kk = e / kKT, oo = e - kk * kKT;
         const int o = o0 + oo, k = k0 + kk;
-        T v = T(0);
-        if (o < p.dim && k < p.dim) v = (T)(p.trans ? p.B[(int64_t)k * p.dim + o] : p.B[(int64_t)o * p.dim + k]);
-        Bs[kk * SM::BP + oo] = v;
+        Bs[kk * SM::BP + oo] = (o < p.dim && k < p.dim) ? Bt[(int64_t)k * p.dim + o] : T(0);
       }
       for (int e = tid; e < kKT * CW / E16; e += blockDim.x) {
         const int kk = e / (CW / E16), q = e - kk * (CW / E16);
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) k_kron_pass(const KronPass p, const T *__
         if (k < p.dim) {
           v = *reinterpret_cast<const V16 *>(x + (base + (int64_t)k * p.kstride) * p.ld + c0 + q * E16);
           if (p.mode == KRON_IN_DH) {
-            const T sc = (T)(p.dh[k] * p.dh[g_inner]);
+            const T sc = scale[k * p.m + g_inner];
 #pragma unroll
             for (int u = 0; u < E16; ++u) vs[u] *= sc;
           }
@@ -109,14 +109,10 @@ __global__ void __launch_bounds__(256) k_kron_pass(const KronPass p, const T *__
       const int o = o0 + rg * 8 + a;
       if (o >= p.dim) continue;
       T sc = T(1);
-      if (p.mode == KRON_OUT_DH) {
-        sc = (T)(p.dh[o] * p.dh[g_inner]);
-      } else if (p.mode == KRON_OUT_SPEC) {
-        // group = spatial index s = a m + b, o = temporal index
-        const int sa = g_inner / p.m, sb = g_inner - sa * p.m;
-        const double s2 = p.kappa2 + p.lam[sa] + p.lam[sb];
-        sc = (T)(1.0 / (p.tau * p.mu[o] * s2 * s2 + p.omega));
-      }
+      if (p.mode == KRON_OUT_DH)
+        sc = scale[o * p.m + g_inner];
+      else if (p.mode == KRON_OUT_SPEC)  // group = spatial index, o = temporal index
+        sc = scale[(int64_t)o * p.m * p.m + g_inner];
       T *dst = y + (base + (int64_t)o * p.kstride) * p.ld + c0 + cg * NC;
 #pragma unroll
       for (int q = 0; q < NC; ++q) dst[q] = acc[a][q] * sc;
@@ -182,6 +178,58 @@ void launch_pcg_dots(cudaStream_t s, const PcgVec<T> &v) {
 template void launch_pcg_dots<double>(cudaStream_t, const PcgVec<double> &);
 template void launch_pcg_dots<float>(cudaStream_t, const PcgVec<float> &);
 
+// The preconditioner's tables in T for one theta (see KronOperator): the
+// factors and their transposes, dh_i dh_j, and the spectral scaling formed
+// in double and rounded once.
+template <typename T>
+__global__ void __launch_bounds__(256) k_kron_tables(KronOperator op) {
+  const int m = op.m, n_t = op.n_t, n_s = m * m;
+  const int64_t total = 2 * (int64_t)m * m + 2 * (int64_t)n_t * n_t + (int64_t)m * m + (int64_t)n_t * n_s;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = i;
+    if (r < (int64_t)m * m) {
+      static_cast<T *>(op.tV)[r] = (T)op.V[r];
+      continue;
+    }
+    r -= (int64_t)m * m;
+    if (r < (int64_t)m * m) {
+      const int a = (int)(r / m), b = (int)(r % m);
+      static_cast<T *>(op.tVT)[r] = (T)op.V[(int64_t)b * m + a];
+      continue;
+    }
+    r -= (int64_t)m * m;
+    if (r < (int64_t)n_t * n_t) {
+      static_cast<T *>(op.tU)[r] = (T)op.U[r];
+      continue;
+    }
+    r -= (int64_t)n_t * n_t;
+    if (r < (int64_t)n_t * n_t) {
+      const int a = (int)(r / n_t), b = (int)(r % n_t);
+      static_cast<T *>(op.tUT)[r] = (T)op.U[(int64_t)b * n_t + a];
+      continue;
+    }
+    r -= (int64_t)n_t * n_t;
+    if (r < (int64_t)m * m) {
+      const int a = (int)(r / m), b = (int)(r % m);
+      static_cast<T *>(op.dhdh)[r] = (T)(op.dh[a] * op.dh[b]);
+      continue;
+    }
+    r -= (int64_t)m * m;
+    const int t = (int)(r / n_s), s = (int)(r % n_s);
+    const int sa = s / m, sb = s - sa * m;
+    const double s2 = op.kappa2 + op.lam[sa] + op.lam[sb];
+    static_cast<T *>(op.spec)[r] = (T)(1.0 / (op.tau * op.mu[t] * s2 * s2 + op.omega));
+  }
+}
+
+template <typename T>
+void launch_kron_tables(cudaStream_t s, const KronOperator &op) {
+  ++g_launch_count;
+  k_kron_tables<T><<<152, 256, 0, s>>>(op);
+}
+template void launch_kron_tables<double>(cudaStream_t, const KronOperator &);
+template void launch_kron_tables<float>(cudaStream_t, const KronOperator &);
+
 // z = M^-1 r: six passes, ping-pong between the scratch q and z (q is free
 // once the AXPY has consumed Q p); the result ends in z.
 template <typename T>
@@ -190,29 +238,21 @@ void launch_kron_apply(cudaStream_t s, const KronOperator &op, const T *r, T *q,
   KronPass p{};
   p.ld = op.ld;
   p.m = m;
-  p.dh = op.dh;
-  p.lam = op.lam;
-  p.mu = op.mu;
-  p.kappa2 = 0.0;
-  p.tau = 1.0;
-  p.omega = 0.0;
+  p.scale = op.dhdh;
   // spatial index s = i m + j inside slab t (row t n_s + s)
   KronPass over_i = p, over_j = p, over_t = p;
-  over_i.B = op.V;
   over_i.dim = m;
   over_i.kstride = m;
   over_i.n_outer = n_t;
   over_i.outer_stride = n_s;
   over_i.n_inner = m;
   over_i.inner_stride = 1;
-  over_j.B = op.V;
   over_j.dim = m;
   over_j.kstride = 1;
   over_j.n_outer = n_t;
   over_j.outer_stride = n_s;
   over_j.n_inner = m;
   over_j.inner_stride = m;
-  over_t.B = op.U;
   over_t.dim = n_t;
   over_t.kstride = n_s;
   over_t.n_outer = 1;
@@ -220,31 +260,30 @@ void launch_kron_apply(cudaStream_t s, const KronOperator &op, const T *r, T *q,
   over_t.n_inner = n_s;
   over_t.inner_stride = 1;
   ProfScope ps_(s, PROF_PRECOND);
+  // op(B)^T is B for the transposed passes and B^T for the others
   KronPass a = over_i;          // (V^T over i) after the input scaling Dh (x) Dh
-  a.trans = 1;
+  a.Bt = op.tV;
   a.mode = KRON_IN_DH;
   launch_kron_pass<T>(s, a, r, q);
   KronPass b = over_j;          // V^T over j
-  b.trans = 1;
+  b.Bt = op.tV;
   b.mode = KRON_NONE;
   launch_kron_pass<T>(s, b, q, z);
   KronPass c = over_t;          // U^T over t, then the spectral scaling
-  c.trans = 1;
+  c.Bt = op.tU;
   c.mode = KRON_OUT_SPEC;
-  c.kappa2 = op.kappa2;
-  c.tau = op.tau;
-  c.omega = op.omega;
+  c.scale = op.spec;
   launch_kron_pass<T>(s, c, z, q);
   KronPass d = over_t;          // U over t
-  d.trans = 0;
+  d.Bt = op.tUT;
   d.mode = KRON_NONE;
   launch_kron_pass<T>(s, d, q, z);
   KronPass e = over_j;          // V over j
-  e.trans = 0;
+  e.Bt = op.tVT;
   e.mode = KRON_NONE;
   launch_kron_pass<T>(s, e, z, q);
   KronPass f = over_i;          // V over i, then Dh (x) Dh
-  f.trans = 0;
+  f.Bt = op.tVT;
   f.mode = KRON_OUT_DH;
   launch_kron_pass<T>(s, f, q, z);
 }
