@@ -359,60 +359,114 @@ __global__ void __launch_bounds__(kPivotThreads) k_bsweep_pivot(SweepBatch<T> bt
 //   U_i = W_iq P,  V_i = W_iq           (saved at column q of U, V)
 //   W_ij -= U_i Vk_j^T                  (panel columns j != q)
 //   W_iq <- U_i,  W_kj <- U_j^T (j in K),  W_kq <- -P.
-// Row k belongs to no CTA's update, so the writes never overlap.
+// Row k belongs to no CTA's update, so the writes never overlap.  The 64 x 64
+// products stage both operands whole in shared memory, the left one
+// transposed (sA[kk][r]); each thread owns the 4 x 4 block at rows 4 ty,
+// columns 4 tx and reads 4 + 4 operands per k with two 16-byte loads.
+constexpr int kPanelLd = 68;   // padded shared row: 16-byte aligned, staggered banks
+
+__device__ __forceinline__ void panel_mma64(const float *sA, const float *sB, float acc[4][4]) {
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll 8
+  for (int kk = 0; kk < 64; ++kk) {
+    const float4 a = *reinterpret_cast<const float4 *>(sA + kk * kPanelLd + 4 * ty);
+    const float4 b = *reinterpret_cast<const float4 *>(sB + kk * kPanelLd + 4 * tx);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+}
+
+// dst[kk][r] = src[r][kk] for a 64 x 64 tile at src (row stride lds); lanes
+// take consecutive rows so that the shared stores do not conflict
+__device__ __forceinline__ void panel_load_transposed(float *dst, const float *src, int64_t lds) {
+  for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+    const int r = e & 63, k4 = (e >> 6) * 4;
+    const float4 v = *reinterpret_cast<const float4 *>(src + r * lds + k4);
+    dst[(k4 + 0) * kPanelLd + r] = v.x;
+    dst[(k4 + 1) * kPanelLd + r] = v.y;
+    dst[(k4 + 2) * kPanelLd + r] = v.z;
+    dst[(k4 + 3) * kPanelLd + r] = v.w;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_bsweep_panel(SweepBatch<T> bt, int k0, int q, int bw, int buf) {
-  __shared__ TileSmem<T> sm;
+  static_assert(std::is_same<T, float>::value, "the panel-blocked sweep runs on float tiles");
+  __shared__ __align__(16) float sA[64 * kPanelLd];
+  __shared__ __align__(16) float sB[64 * kPanelLd];
   const SweepEntry<T> e = bt.e[blockIdx.y];
   constexpr int ldw = 64 * kSweepPanel;
   const int i = blockIdx.x, k = k0 + q;
-  T *Wi = (buf ? e.Wp[1] : e.Wp[0]) + (int64_t)i * 64 * ldw;
-  T *Ui = (buf ? e.Up[1] : e.Up[0]) + (int64_t)i * 64 * ldw + q * 64;
-  T *Vi = (buf ? e.Vp[1] : e.Vp[0]) + (int64_t)i * 64 * ldw + q * 64;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  float *Wi = (buf ? e.Wp[1] : e.Wp[0]) + (int64_t)i * 64 * ldw;
+  float *Ui = (buf ? e.Up[1] : e.Up[0]) + (int64_t)i * 64 * ldw + q * 64;
+  float *Vi = (buf ? e.Vp[1] : e.Vp[0]) + (int64_t)i * 64 * ldw + q * 64;
   if (i == k) {
     for (int idx = threadIdx.x; idx < 4096; idx += 256) {
       const int64_t o = (int64_t)(idx >> 6) * ldw + (idx & 63);
       Wi[o + q * 64] = -e.P[idx];
-      Ui[o] = T(0);
-      Vi[o] = T(0);
+      Ui[o] = 0.0f;
+      Vi[o] = 0.0f;
     }
     return;
   }
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  T acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-  tile_mma<false, false>(sm, Wi + q * 64, ldw, e.P, 64, 64, acc);
-  for (int idx = threadIdx.x; idx < 4096; idx += 256) {
-    const int64_t o = (int64_t)(idx >> 6) * ldw + (idx & 63);
-    Vi[o] = Wi[o + q * 64];
+  panel_load_transposed(sA, Wi + q * 64, ldw);
+  for (int idx = threadIdx.x; idx < 64 * 16; idx += 256) {
+    const int r = idx >> 4, c4 = (idx & 15) * 4;
+    *reinterpret_cast<float4 *>(sB + r * kPanelLd + c4) = *reinterpret_cast<const float4 *>(e.P + r * 64 + c4);
+    // V_i = A_ik before the pivot
+    *reinterpret_cast<float4 *>(Vi + (int64_t)r * ldw + c4) =
+        *reinterpret_cast<const float4 *>(Wi + (int64_t)r * ldw + q * 64 + c4);
   }
-  __syncthreads();  // column q read before it is overwritten
-  const bool in_panel = i >= k0 && i < k0 + bw;
-  T *Wk = (buf ? e.Wp[1] : e.Wp[0]) + (int64_t)k * 64 * ldw + (i - k0) * 64;
+  __syncthreads();
+  float acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int r = ty + 16 * a, c = tx + 16 * b;
-      Ui[(int64_t)r * ldw + c] = acc[a][b];
-      Wi[(int64_t)r * ldw + q * 64 + c] = acc[a][b];
-      if (in_panel) Wk[(int64_t)c * ldw + r] = acc[a][b];
-    }
-  __syncthreads();  // U_i complete before it is read back as an operand
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+  panel_mma64(sA, sB, acc);
+  __syncthreads();  // sA is reused for U_i below; column q of W was read
+  const bool in_panel = i >= k0 && i < k0 + bw;
+  float *Wk = (buf ? e.Wp[1] : e.Wp[0]) + (int64_t)k * 64 * ldw + (i - k0) * 64;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int r = 4 * ty + a;
+    const float4 v = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+    *reinterpret_cast<float4 *>(Ui + (int64_t)r * ldw + 4 * tx) = v;
+    *reinterpret_cast<float4 *>(Wi + (int64_t)r * ldw + q * 64 + 4 * tx) = v;
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int c = 4 * tx + b;
+    const float4 v = make_float4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
+    // U_i^T staged as the left operand of the updates: sA[kk][r] = U_i[r][kk]
+    *reinterpret_cast<float4 *>(sA + c * kPanelLd + 4 * ty) = v;
+    if (in_panel) *reinterpret_cast<float4 *>(Wk + (int64_t)c * ldw + 4 * ty) = v;
+  }
   for (int jj = 0; jj < bw; ++jj) {
     if (jj == q) continue;
+    __syncthreads();  // sB free, sA complete
+    // sB[kk][c] = Vk_jj[c][kk]
+    panel_load_transposed(sB, e.Vk + jj * 4096, 64);
+    __syncthreads();
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-    tile_mma<false, true>(sm, Ui, ldw, e.Vk + jj * 4096, 64, 64, acc);
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+    panel_mma64(sA, sB, acc);
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) Wi[(int64_t)(ty + 16 * a) * ldw + jj * 64 + tx + 16 * b] -= acc[a][b];
+    for (int a = 0; a < 4; ++a) {
+      float4 *p = reinterpret_cast<float4 *>(Wi + (int64_t)(4 * ty + a) * ldw + jj * 64 + 4 * tx);
+      float4 w = *p;
+      w.x -= acc[a][0];
+      w.y -= acc[a][1];
+      w.z -= acc[a][2];
+      w.w -= acc[a][3];
+      *p = w;
+    }
   }
 }
 

@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(256) k_kron_pass(const KronPass p, const T *__
       }
       __syncthreads();
       const int kmax = min(kKT, p.dim - k0);
+#pragma unroll 4
       for (int kk = 0; kk < kmax; ++kk) {
         T bv[8], xv[NC];
         const V16 *bp = reinterpret_cast<const V16 *>(Bs + kk * SM::BP + rg * 8);
