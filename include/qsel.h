@@ -68,6 +68,13 @@ enum {
   QSEL_SAMPLER_LANCZOS = 1
 };
 
+/* Precision of the 64 x 64 pivot-tile inverses of the QSEL_MIXED dense
+ * factorisation (qsel_options.pivot_precision); QSEL_FP64 always uses binary64. */
+enum {
+  QSEL_PIVOT_DOUBLE_FLOAT = 0,  /* hi + lo binary32 pairs (Dekker), about 48 bits  */
+  QSEL_PIVOT_FP64 = 1           /* binary64                                         */
+};
+
 /* Preconditioners of the sampler's PCG (qsel_options.preconditioner). */
 enum {
   QSEL_PRECOND_BLOCK_JACOBI = 0,
@@ -77,9 +84,10 @@ enum {
 /* Arithmetic of the pipeline. */
 enum {
   QSEL_FP64 = 0,      /* every kernel computes in IEEE binary64                  */
-  QSEL_MIXED = 1      /* binary32 solves and factorisations, double-float
-                         (about 48-bit) pivot tiles, binary64 refinement
-                         residuals and accumulators                               */
+  QSEL_MIXED = 1      /* binary32 solves and factorisations, extended-precision
+                         pivot tiles (double-float or binary64, see
+                         pivot_precision), binary64 refinement residuals and
+                         accumulators                                             */
 };
 
 /*
@@ -154,6 +162,10 @@ typedef struct {
                              part, read at qsel_create), or NULL: every part uses
                              the `overlap` argument.  Lets a planner
                              (qsel_cv_plan) extend each subdomain differently. */
+  int32_t pivot_precision;/* QSEL_MIXED pivot-tile inverses:
+                             QSEL_PIVOT_DOUBLE_FLOAT (0, default; on the binary32
+                             pipe, which GB300 runs 64x faster than binary64) or
+                             QSEL_PIVOT_FP64 (1).  Ignored for QSEL_FP64.       */
 } qsel_options;
 
 #define QSEL_PROF_CLASSES 11

@@ -334,6 +334,8 @@ static Err validate(const qsel_model *m, const qsel_theta *th, const qsel_partit
   if (opt->control_variate != 0) return fail(QSEL_EINVAL, "control_variate must be 0");
   if (opt->tensor_passes != 0 && opt->tensor_passes != 1 && opt->tensor_passes != 3 && opt->tensor_passes != -1)
     return fail(QSEL_EINVAL, "tensor_passes must be 0, 1, 3 or -1");
+  if (opt->pivot_precision != QSEL_PIVOT_DOUBLE_FLOAT && opt->pivot_precision != QSEL_PIVOT_FP64)
+    return fail(QSEL_EINVAL, "pivot_precision must be QSEL_PIVOT_DOUBLE_FLOAT or QSEL_PIVOT_FP64");
   if (opt->preconditioner != QSEL_PRECOND_BLOCK_JACOBI && opt->preconditioner != QSEL_PRECOND_KRON)
     return fail(QSEL_EINVAL, "preconditioner must be QSEL_PRECOND_BLOCK_JACOBI or QSEL_PRECOND_KRON");
   if (opt->preconditioner == QSEL_PRECOND_KRON && detect_grid(m) == 0)
@@ -1196,6 +1198,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       se.a0 = c->tc.a0 + tg;
       se.c = (t > 0) ? c->tc.a1 + tg - 1 : c->tc.a1;
       se.obs = c->d_obs + (size_t)tg * n_s;
+      wb.pivot_fp64 = c->opt.pivot_precision == QSEL_PIVOT_FP64 ? 1 : 0;
       SweepEntry<T> &we = wb.e[wb.count++];
       we.A = Dinv(p, t);
       we.P = buf(sl.P);

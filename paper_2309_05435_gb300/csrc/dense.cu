@@ -224,50 +224,54 @@ template void launch_gemm<float>(cudaStream_t, const GemmBatch<float> &, int, in
 // the final mirror negates it and fills the upper triangle.
 // ---------------------------------------------------------------------------
 // P = Tk^-1 for the 64 x 64 tile at Tk (row stride ld), from its lower half:
-// in double for double tiles, in double-float (about 48 bits, on the FP32
-// pipe) for float tiles.  NT threads.
+// in binary64 for double tiles; for float tiles in double-float (about 48
+// bits, on the FP32 pipe) or, with fp64, in binary64.  NT threads.
 template <int NT, typename T>
-__device__ __forceinline__ void invert_pivot_tile(const T *Tk, int ld, T *P, int32_t *err_flag) {
+__device__ __forceinline__ void invert_pivot_tile(const T *Tk, int ld, T *P, int32_t *err_flag, bool fp64) {
+  // one buffer for either arithmetic (dfloat and double are both 8 bytes)
+  __shared__ __align__(16) unsigned char pv_smem[(64 * 65 + 65 + 64) * 8];
   if constexpr (std::is_same<T, float>::value) {
-    __shared__ dfloat Sf[64 * 65];
-    __shared__ dfloat colf[65], wvf[64];
-    // the diagonal tile is kept symmetric; the lower half is what is read
+    if (!fp64) {
+      dfloat *Sf = reinterpret_cast<dfloat *>(pv_smem);
+      dfloat *colf = Sf + 64 * 65, *wvf = colf + 65;
+      // the diagonal tile is kept symmetric; the lower half is what is read
 #pragma unroll 4
-    for (int idx = threadIdx.x; idx < 64 * 16; idx += NT) {
-      const int r = idx >> 4, c4 = (idx & 15) * 4;
-      const float4 v = *reinterpret_cast<const float4 *>(Tk + (int64_t)r * ld + c4);
-      const float vv[4] = {v.x, v.y, v.z, v.w};
+      for (int idx = threadIdx.x; idx < 64 * 16; idx += NT) {
+        const int r = idx >> 4, c4 = (idx & 15) * 4;
+        const float4 v = *reinterpret_cast<const float4 *>(Tk + (int64_t)r * ld + c4);
+        const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (r >= c4 + u) Sf[r * 65 + c4 + u] = dfloat{vv[u], 0.0f};
+        for (int u = 0; u < 4; ++u)
+          if (r >= c4 + u) Sf[r * 65 + c4 + u] = dfloat{vv[u], 0.0f};
+      }
+      __syncthreads();
+      sym_sweep_inverse64_lower_df<NT>(Sf, 65, colf, wvf, err_flag);
+      for (int idx = threadIdx.x; idx < 64 * 64; idx += NT) {
+        const int r = idx >> 6, c = idx & 63;
+        const dfloat v = Sf[(r >= c) ? r * 65 + c : c * 65 + r];
+        P[idx] = -__fadd_rn(v.hi, v.lo);
+      }
+      return;
     }
-    __syncthreads();
-    sym_sweep_inverse64_lower_df<NT>(Sf, 65, colf, wvf, err_flag);
-    for (int idx = threadIdx.x; idx < 64 * 64; idx += NT) {
-      const int r = idx >> 6, c = idx & 63;
-      const dfloat v = Sf[(r >= c) ? r * 65 + c : c * 65 + r];
-      P[idx] = -__fadd_rn(v.hi, v.lo);
-    }
-  } else {
-    __shared__ double S[64 * 65];
-    __shared__ double col[65], wv[64];
-    for (int idx = threadIdx.x; idx < 64 * 64; idx += NT) {
-      const int r = idx >> 6, c = idx & 63;
-      if (r >= c) S[r * 65 + c] = (double)Tk[(int64_t)r * ld + c];
-    }
-    __syncthreads();
-    sym_sweep_inverse64_lower<NT>(S, 65, col, wv, err_flag);
-    for (int idx = threadIdx.x; idx < 64 * 64; idx += NT) {
-      const int r = idx >> 6, c = idx & 63;
-      P[idx] = (T)(-S[(r >= c) ? r * 65 + c : c * 65 + r]);
-    }
+  }
+  double *S = reinterpret_cast<double *>(pv_smem);
+  double *col = S + 64 * 65, *wv = col + 65;
+  for (int idx = threadIdx.x; idx < 64 * 64; idx += NT) {
+    const int r = idx >> 6, c = idx & 63;
+    if (r >= c) S[r * 65 + c] = (double)Tk[(int64_t)r * ld + c];
+  }
+  __syncthreads();
+  sym_sweep_inverse64_lower<NT>(S, 65, col, wv, err_flag);
+  for (int idx = threadIdx.x; idx < 64 * 64; idx += NT) {
+    const int r = idx >> 6, c = idx & 63;
+    P[idx] = (T)(-S[(r >= c) ? r * 65 + c : c * 65 + r]);
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_sweep_pivot(SweepBatch<T> bt, int k, int ld, int32_t *err_flag) {
   const SweepEntry<T> e = bt.e[blockIdx.x];
-  invert_pivot_tile<256>(e.A + (int64_t)k * 64 * ld + k * 64, ld, e.P, err_flag);
+  invert_pivot_tile<256>(e.A + (int64_t)k * 64 * ld + k * 64, ld, e.P, err_flag, bt.pivot_fp64 != 0);
 }
 
 template <typename T>
@@ -352,7 +356,8 @@ __global__ void __launch_bounds__(kPivotThreads) k_bsweep_pivot(SweepBatch<T> bt
     *reinterpret_cast<Vec *>(e.Vk + r * 64 + c) =
         *reinterpret_cast<const Vec *>(W + (int64_t)(k0 * 64 + r) * ldw + q * 64 + c);
   }
-  invert_pivot_tile<kPivotThreads>(W + (int64_t)(k0 + q) * 64 * ldw + q * 64, ldw, e.P, err_flag);
+  invert_pivot_tile<kPivotThreads>(W + (int64_t)(k0 + q) * 64 * ldw + q * 64, ldw, e.P, err_flag,
+                                   bt.pivot_fp64 != 0);
 }
 
 // One pivot on the panel, CTA per row tile i:

@@ -216,6 +216,7 @@ template <typename T>
 struct SweepBatch {
   SweepEntry<T> e[kMaxBatch];
   int count;
+  int pivot_fp64;  // float tiles: pivot inverses in binary64 instead of double-float
 };
 // In-place SPD inverse by the blocked symmetric sweep; A becomes A^-1 with
 // both triangles filled.  The 64 x 64 pivot tiles are inverted in double

@@ -18,6 +18,8 @@ QSEL_SAMPLER_PCG = 0
 QSEL_SAMPLER_LANCZOS = 1
 QSEL_PRECOND_BLOCK_JACOBI = 0
 QSEL_PRECOND_KRON = 1
+QSEL_PIVOT_DOUBLE_FLOAT = 0
+QSEL_PIVOT_FP64 = 1
 
 _STATUS = {0: "QSEL_OK", 1: "QSEL_EINVAL", 2: "QSEL_ENOMEM", 3: "QSEL_ECUDA", 4: "QSEL_ENOTSPD",
            5: "QSEL_ENOCONV", 6: "QSEL_ETIMEOUT", 7: "QSEL_ESTATE"}
@@ -44,7 +46,7 @@ class qsel_options(ctypes.Structure):
                 ("pcg_max_iter", c_int32), ("precond_block", c_int32), ("control_variate", c_int32),
                 ("cuda_stream", c_void_p), ("profile_kernels", c_int32), ("tensor_passes", c_int32),
                 ("sampler", c_int32), ("lanczos_steps", c_int32), ("preconditioner", c_int32),
-                ("part_overlap", POINTER(c_int32))]
+                ("part_overlap", POINTER(c_int32)), ("pivot_precision", c_int32)]
 
 
 class qsel_batch_info_t(ctypes.Structure):
@@ -211,7 +213,8 @@ def qsel_create(n_s, n_t, c_diag, g_rowptr, g_col, g_val, obs_mask, sigma, theta
                 slab_start=None, overlap=0, n_samples=64, seed=0, precision=QSEL_FP64, pcg_tol=1e-10,
                 pcg_max_iter=20000, precond_block=0, control_variate=0, cuda_stream=None,
                 profile_kernels=0, tensor_passes=0, part_overlap=None, sampler=QSEL_SAMPLER_PCG,
-                lanczos_steps=0, preconditioner=QSEL_PRECOND_BLOCK_JACOBI) -> Context:
+                lanczos_steps=0, preconditioner=QSEL_PRECOND_BLOCK_JACOBI,
+                pivot_precision=QSEL_PIVOT_DOUBLE_FLOAT) -> Context:
     """Create a context from host arrays (copied by the library)."""
     lib = load_library()
     c = np.ascontiguousarray(c_diag, dtype=np.float64)
@@ -235,7 +238,7 @@ def qsel_create(n_s, n_t, c_diag, g_rowptr, g_col, g_val, obs_mask, sigma, theta
                        int(precond_block), int(control_variate),
                        c_void_p(int(cuda_stream)) if cuda_stream else None, int(profile_kernels),
                        int(tensor_passes), int(sampler), int(lanczos_steps), int(preconditioner),
-                       _ptr(po, c_int32) if po is not None else None)
+                       _ptr(po, c_int32) if po is not None else None, int(pivot_precision))
     h = c_void_p()
     st = lib.qsel_create(ctypes.byref(h), ctypes.byref(model), ctypes.byref(th), ctypes.byref(part),
                          int(overlap), ctypes.byref(opt))
@@ -475,7 +478,8 @@ def qsel_create_batch(models, thetas, partitions, overlaps, n_samples=128, seed=
     OV = np.ascontiguousarray(overlaps, dtype=np.int32)
     opt = qsel_options(int(n_samples), int(seed), int(precision), float(pcg_tol), int(pcg_max_iter),
                        int(precond_block), 0, c_void_p(int(cuda_stream)) if cuda_stream else None, 0,
-                       int(tensor_passes), QSEL_SAMPLER_PCG, 0, QSEL_PRECOND_BLOCK_JACOBI, None)
+                       int(tensor_passes), QSEL_SAMPLER_PCG, 0, QSEL_PRECOND_BLOCK_JACOBI, None,
+                       QSEL_PIVOT_DOUBLE_FLOAT)
     h = c_void_p()
     st = lib.qsel_create_batch(ctypes.byref(h), n, M, TH, PA, _ptr(OV, c_int32), ctypes.byref(opt),
                                int(n_streams), int(bool(autotune)))

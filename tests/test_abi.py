@@ -57,6 +57,7 @@ def _args(**over):
     (dict(sampler=1, lanczos_steps=0), "lanczos_steps"),
     (dict(sampler=1, lanczos_steps=8, precond_block=1), "blocks of 16, 32 or 64"),
     (dict(part_overlap=[1, -1]), "part_overlap"),
+    (dict(pivot_precision=2), "pivot_precision"),
 ])
 def test_invalid_arguments_rejected(lib, bad, msg):
     from paper_2309_05435_gb300 import qsel

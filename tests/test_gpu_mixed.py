@@ -80,6 +80,26 @@ def test_mixed_dense_paths_match_fp64(q, name, passes):
     assert rel(tm, t64) <= MIXED_TRACE_TOL
 
 
+@pytest.mark.parametrize("name", ["grid16_nt8", "ragged13", "overlap2"])
+def test_pivot_precisions_match_fp64(q, name):
+    """Double-float (default) and binary64 pivot-tile inverses both stay within
+    the stated mixed tolerance of the FP64 run (same seed), and within
+    FP32-level agreement of each other: the pivots are not what limits the
+    mixed path's accuracy."""
+    c64 = Case(q, name, precision=q.QSEL_FP64)
+    cdf = Case(q, name, precision=q.QSEL_MIXED, pivot_precision=q.QSEL_PIVOT_DOUBLE_FLOAT)
+    cfp = Case(q, name, precision=q.QSEL_MIXED, pivot_precision=q.QSEL_PIVOT_FP64)
+    v64, t64 = c64.ctx.diag_inv(), c64.ctx.trace_grads()
+    vdf, tdf = cdf.ctx.diag_inv(), cdf.ctx.trace_grads()
+    vfp, tfp = cfp.ctx.diag_inv(), cfp.ctx.trace_grads()
+    print(f"{name}: double-float pivots diag {rel(vdf, v64):.2e} traces {rel(tdf, t64):.2e}; "
+          f"FP64 pivots diag {rel(vfp, v64):.2e} traces {rel(tfp, t64):.2e}; between {rel(vdf, vfp):.2e}")
+    for v, t in ((vdf, tdf), (vfp, tfp)):
+        assert rel(v, v64) <= MIXED_DIAG_TOL
+        assert rel(t, t64) <= MIXED_TRACE_TOL
+    assert rel(vdf, vfp) <= MIXED_DIAG_TOL
+
+
 def test_plain_tf32_error_is_reported(q):
     """Plain TF32 products (10-bit mantissa) are an option, not the default:
     their error against FP64 is far above the 3xTF32 one and is only bounded
