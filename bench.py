@@ -47,9 +47,6 @@ FP64_PEAK_TFLOPS = 1.25      # GB300 nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/c
 FP32_PEAK_TFLOPS = 80.5      # GB300 FP32 CUDA cores (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz)
 # DRAM bytes per FLOP of k_gemm64 from one ncu capture (profiles/k_gemm64_grid64_nt16_fp64.md)
 GEMM64_DRAM_BYTES_PER_FLOP = 7.808e9 / 2.749e11
-# DRAM bytes of one rank-64 sweep update of a 4096^2 FP32 matrix on the tensor
-# cores (profiles/k_tc_gemm_grid64_nt16_mixed.md: 0.094 GB for 2 matrices)
-TC_SWEEP_DRAM_BYTES_PER_MATRIX = 0.0995e9 / 2
 # planner's PCG cost per sample and node with the Kronecker preconditioner
 # (seconds; the library default describes 64-row block Jacobi)
 KRON_PCG_COST = 0.36e-8
@@ -477,10 +474,11 @@ def run_native(args):
     tf32_peak, tf32_src = tf32_peak_tflops()
     desc = {
         "gemm": ("dense tile GEMMs (tcgen05 3xTF32, TMA, TMEM)" if mixed else "k_gemm64 (FP64 dense tile GEMM)"),
-        "sweep_update": ("sweep rank-64 updates (tcgen05 3xTF32)" if mixed else "k_sweep_update (FP64)"),
+        "sweep_update": ("sweep panel updates, rank 256 (tcgen05 3xTF32)" if mixed else "k_sweep_update (FP64)"),
         "spmm": "k_bt_spmm (block-tridiagonal sliced-ELL SpMM, PCG)",
         "pivot": "k_bsweep_pivot (64x64 pivot-tile inverses: FP64, or double-float on float tiles)",
-        "precond": "k_pcg_precond (block-Jacobi apply, register-tiled)",
+        "precond": ("k_kron_pass x6 (Kronecker grid preconditioner)" if args.preconditioner == "kron"
+                    else "k_pcg_precond (block-Jacobi apply, register-tiled)"),
     }
     cand = [q for q, name in enumerate(classes) if name in desc and cwork[q] > 0 and cms[q] > 0]
     dom = max(cand, key=lambda q: cms[q])
@@ -512,13 +510,6 @@ def run_native(args):
     traffic = None
     if name == "gemm" and not mixed and claunch[dom]:
         traffic = GEMM64_DRAM_BYTES_PER_FLOP * cwork[dom] / claunch[dom]
-    if name == "sweep_update" and mixed and claunch[dom] and w.n_s == 4096:
-        # one ncu capture of the K = 64 tile configuration (profiles/k_tc_gemm_grid64_nt16_mixed.md):
-        # 0.0995 GB per launch of 2 matrices of 4096^2; scaled by the matrices per launch
-        n_tiles = 64
-        per_matrix_flop = 2.0 * 64 ** 3 * (n_tiles * (n_tiles + 1) / 2 - n_tiles)
-        entries = cwork[dom] / claunch[dom] / per_matrix_flop
-        traffic = TC_SWEEP_DRAM_BYTES_PER_MATRIX * entries
     roof = {"kernel": desc[name], **roof, "frac": roof["achieved"] / roof["peak"], "traffic": traffic,
             "launches": int(claunch[dom]), "avg_launch_ms": per_launch_ms}
     roof["kernel_classes_ms_per_step"] = {classes[q]: cms[q] / args.steps for q in range(len(classes))}
