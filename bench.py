@@ -47,6 +47,9 @@ FP64_PEAK_TFLOPS = 1.25      # GB300 nominal FP64 (152 SMs x 2.07 GHz x 4 FLOP/c
 FP32_PEAK_TFLOPS = 80.5      # GB300 FP32 CUDA cores (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz)
 # DRAM bytes per FLOP of k_gemm64 from one ncu capture (profiles/k_gemm64_grid64_nt16_fp64.md)
 GEMM64_DRAM_BYTES_PER_FLOP = 7.808e9 / 2.749e11
+# DRAM bytes of one rank-256 sweep panel update of a 4096^2 FP32 matrix on the
+# tensor cores (profiles/k_tc_gemm_grid64_nt16_mixed.md: 104.8 MB for 2 matrices)
+TC_UPDATE_DRAM_BYTES_PER_MATRIX = 104.8e6 / 2
 # planner's PCG cost per sample and node with the Kronecker preconditioner
 # (seconds; the library default describes 64-row block Jacobi)
 KRON_PCG_COST = 0.36e-8
@@ -510,6 +513,13 @@ def run_native(args):
     traffic = None
     if name == "gemm" and not mixed and claunch[dom]:
         traffic = GEMM64_DRAM_BYTES_PER_FLOP * cwork[dom] / claunch[dom]
+    if name == "sweep_update" and mixed and claunch[dom] and w.n_s == 4096:
+        # one ncu capture of the rank-256 update (2 matrices of 4096^2), scaled by the
+        # matrices per launch: the class's work is 2 64^2 256 FLOP per lower tile
+        # off the panel, (nt - 4)(nt - 3) / 2 tiles per matrix
+        nt = 64
+        per_matrix_flop = 2.0 * 64 * 64 * 256 * (nt - 4) * (nt - 3) / 2
+        traffic = TC_UPDATE_DRAM_BYTES_PER_MATRIX * (cwork[dom] / claunch[dom] / per_matrix_flop)
     roof = {"kernel": desc[name], **roof, "frac": roof["achieved"] / roof["peak"], "traffic": traffic,
             "launches": int(claunch[dom]), "avg_launch_ms": per_launch_ms}
     roof["kernel_classes_ms_per_step"] = {classes[q]: cms[q] / args.steps for q in range(len(classes))}
