@@ -130,6 +130,8 @@ struct qsel_ctx {
   double *h_small = nullptr;
   cudaEvent_t ev[4]{};
   SweepStreams sweep_ss;               // look-ahead of the tensor-core sweep (mixed path)
+  cudaStream_t pcg_stream = nullptr;   // the PCG sampler, beside the first wave's dense part
+  cudaEvent_t ev_fork = nullptr, ev_samples = nullptr;
   std::vector<cudaEvent_t> phase_ev;   // pairs per (wave, phase)
   size_t phase_used = 0;
   Profiler prof;
@@ -170,6 +172,9 @@ struct qsel_ctx {
       if (e) cudaEventDestroy(e);
     if (sweep_ss.hi) cudaStreamDestroy(sweep_ss.hi);
     if (sweep_ss.lo) cudaStreamDestroy(sweep_ss.lo);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_samples) cudaEventDestroy(ev_samples);
+    if (pcg_stream) cudaStreamDestroy(pcg_stream);
     for (auto e : phase_ev) cudaEventDestroy(e);
   }
 };
@@ -705,6 +710,9 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   TRY(c->alloc(&c->d_tol2, 1));
   QSEL_CUDA_TRY(cudaMemset(c->d_loop, 0, 4 * sizeof(int32_t)));
   for (auto &e : c->ev) QSEL_CUDA_TRY(cudaEventCreate(&e));
+  QSEL_CUDA_TRY(cudaStreamCreateWithFlags(&c->pcg_stream, cudaStreamNonBlocking));
+  QSEL_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  QSEL_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_samples, cudaEventDisableTiming));
   if (c->mixed) {
     // the sweep's panels on a high-priority stream, so that their few CTAs are
     // scheduled ahead of the pending tiles of the concurrent update
@@ -1171,8 +1179,9 @@ static void phase_mark(qsel_ctx *c, std::vector<std::pair<cudaEvent_t, int>> &ma
 
 // Forward block factorisation, backward Takahashi recursion and RB correction
 // for the subdomains [p0, p1) held in slots 0 .. p1-p0-1, in lockstep.
+// stages: 1 = factorisation and Takahashi, 2 = correction (needs the samples).
 template <typename T>
-static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent_t, int>> &marks) {
+static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent_t, int>> &marks, int stages = 3) {
   cudaStream_t s = c->stream;
   const int n_pad = c->n_pad, n_s = c->n_s, ld = c->ld;
   const size_t svec = (size_t)n_pad * ld;
@@ -1181,6 +1190,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
   auto slot = [&](int p) -> DenseSlot & { return c->slots[p - p0]; };
   auto Dinv = [&](int p, int t) { return static_cast<T *>(slot(p).Dinv[t]); };
   auto buf = [](void *x) { return static_cast<T *>(x); };
+  if (stages & 1) {
   phase_mark(c, marks, -1);
   // ---- forward: D_t assembled (Schur), inverted in place, W_t = c_t Q_s D_t^-1
   for (int t = 0; t < maxT; ++t) {
@@ -1423,6 +1433,8 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
     QSEL_CUDA_TRY(cudaGetLastError());
   }
   phase_mark(c, marks, 1);
+  }  // stages & 1
+  if (!(stages & 2)) return ok();
   // ---- RB correction: w = Q_{**}^-1 Q_{*S} x_S by the block LDL^T sweeps
   //   forward  y_0 = b_0, u_t = D_t^-1 y_t, y_{t+1} = b_{t+1} - c_t Q_s u_t
   //   backward w_{T-1} = u_{T-1}, w_t = u_t - D_t^-1 (c_t Q_s w_{t+1})
@@ -1610,24 +1622,42 @@ static Err run_pipeline_body(qsel_ctx *c) {
   c->stats.pcg_iterations = 0;
   c->stats.pcg_max_rel_residual = 0.0;
   c->lz.ran = false;
-  if (!c->injected && need_samples) {
-    if (c->opt.sampler == QSEL_SAMPLER_LANCZOS)
-      TRY(run_sampler_lanczos(c));
-    else
-      TRY(run_sampler(c));
-  } else {
-    QSEL_CUDA_TRY(cudaEventRecord(c->ev[1], s));
-  }
-  QSEL_CUDA_TRY(cudaEventRecord(c->ev[2], s));
   std::vector<std::pair<cudaEvent_t, int>> marks;
   const int np = (int)c->parts.size();
-  for (int p0 = 0; p0 < np; p0 += c->wave) {
-    const int p1 = std::min(np, p0 + c->wave);
-    if (c->mixed)
-      TRY(run_wave<float>(c, p0, p1, marks));
+  auto wave = [&](int p0, int p1, int stages) -> Err {
+    return c->mixed ? run_wave<float>(c, p0, p1, marks, stages) : run_wave<double>(c, p0, p1, marks, stages);
+  };
+  int first = 0;   // first wave still to run in full
+  if (!c->injected && need_samples && c->opt.sampler == QSEL_SAMPLER_PCG) {
+    // The samples are needed only by the correction: the first wave's
+    // factorisation and Takahashi recursion are enqueued on the context's
+    // stream and run while the PCG (whose host loop synchronises only its
+    // own stream) runs on pcg_stream.
+    QSEL_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
+    first = std::min(np, c->wave);
+    TRY(wave(0, first, 1));
+    QSEL_CUDA_TRY(cudaStreamWaitEvent(c->pcg_stream, c->ev_fork, 0));
+    c->stream = c->pcg_stream;
+    Err e = run_sampler(c);
+    if (e.code == 0 && cudaEventRecord(c->ev[2], c->pcg_stream) != cudaSuccess)
+      e = fail(QSEL_ECUDA, "event record failed");
+    if (e.code == 0 && cudaEventRecord(c->ev_samples, c->pcg_stream) != cudaSuccess)
+      e = fail(QSEL_ECUDA, "event record failed");
+    c->stream = s;
+    if (e.code) {
+      cudaStreamSynchronize(s);   // leave no dense work of this call in flight
+      return e;
+    }
+    QSEL_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_samples, 0));
+    TRY(wave(0, first, 2));
+  } else {
+    if (!c->injected && need_samples)
+      TRY(run_sampler_lanczos(c));
     else
-      TRY(run_wave<double>(c, p0, p1, marks));
+      QSEL_CUDA_TRY(cudaEventRecord(c->ev[1], s));
+    QSEL_CUDA_TRY(cudaEventRecord(c->ev[2], s));
   }
+  for (int p0 = first; p0 < np; p0 += c->wave) TRY(wave(p0, std::min(np, p0 + c->wave), 3));
   launch_sum(s, c->d_diag, c->d_selinv, c->d_corr, c->n);
   launch_trace_combine(s, c->d_slabs, c->n_trace_slabs, c->d_sums, c->d_partials, np * corr_grid(), c->tc.a0,
                        c->tc.a1, c->tc.r0, c->tc.r1, c->d_traces);
