@@ -1628,11 +1628,13 @@ static Err run_pipeline_body(qsel_ctx *c) {
     return c->mixed ? run_wave<float>(c, p0, p1, marks, stages) : run_wave<double>(c, p0, p1, marks, stages);
   };
   int first = 0;   // first wave still to run in full
-  if (!c->injected && need_samples && c->opt.sampler == QSEL_SAMPLER_PCG) {
+  if (c->mixed && !c->injected && need_samples && c->opt.sampler == QSEL_SAMPLER_PCG) {
     // The samples are needed only by the correction: the first wave's
     // factorisation and Takahashi recursion are enqueued on the context's
     // stream and run while the PCG (whose host loop synchronises only its
-    // own stream) runs on pcg_stream.
+    // own stream) runs on pcg_stream.  Mixed form only: in FP64 both parts
+    // run on the FP64 pipe, and sequential phases keep its phase times
+    // (which the plain-FP64 time-to-target model scales) additive.
     QSEL_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
     first = std::min(np, c->wave);
     TRY(wave(0, first, 1));
