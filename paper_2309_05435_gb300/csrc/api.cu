@@ -1653,10 +1653,12 @@ static Err run_pipeline_body(qsel_ctx *c) {
     QSEL_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_samples, 0));
     TRY(wave(0, first, 2));
   } else {
-    if (!c->injected && need_samples)
+    if (c->injected || !need_samples)
+      QSEL_CUDA_TRY(cudaEventRecord(c->ev[1], s));
+    else if (c->opt.sampler == QSEL_SAMPLER_LANCZOS)
       TRY(run_sampler_lanczos(c));
     else
-      QSEL_CUDA_TRY(cudaEventRecord(c->ev[1], s));
+      TRY(run_sampler(c));
     QSEL_CUDA_TRY(cudaEventRecord(c->ev[2], s));
   }
   for (int p0 = first; p0 < np; p0 += c->wave) TRY(wave(p0, std::min(np, p0 + c->wave), 3));
