@@ -242,6 +242,45 @@ qsel_status qsel_diag_inv(qsel_ctx *ctx, double *diag_out, int32_t out_is_device
  */
 qsel_status qsel_trace_grads(qsel_ctx *ctx, double grads_out[3]);
 
+/*
+ * Posterior mean and the gradient of the hyperparameter marginal, for the
+ * model without fixed effects (Section 2.3, Eq. mean:5 with n_beta = 0;
+ * Section 3.4, Eqs. hyperpar:1, 3, 4).
+ *
+ * qsel_set_data: the data y on the observed nodes, y_obs[q] for the q-th
+ * observed node in increasing index order (n_obs HOST doubles, copied).
+ * Errors: QSEL_EINVAL (NULL, no observed nodes), QSEL_ECUDA.
+ */
+qsel_status qsel_set_data(qsel_ctx *ctx, const double *y_obs);
+
+/*
+ * mu = Q^-1 A^T y / sigma^2 at the current theta, by the sampler's solver
+ * (multi-RHS PCG in FP64, or FP32 PCG with FP64 refinement for QSEL_MIXED,
+ * to pcg_tol).  mu_out: n doubles (host, or device with out_is_device).  The
+ * solve reuses the sampler's right-hand-side and sample buffers
+ * (qsel_debug_get_samples / get_rhs no longer return the last run's, and
+ * samples injected by qsel_debug_set_samples are dropped: the next pipeline
+ * run samples afresh); results of qsel_diag_inv / qsel_trace_grads are kept.
+ * Errors: QSEL_ESTATE (no data), QSEL_ENOCONV, QSEL_ECUDA.
+ */
+qsel_status qsel_posterior_mean(qsel_ctx *ctx, double *mu_out, int32_t out_is_device);
+
+/*
+ * grad_out[j] = d log p(y | theta) / d theta_j (the marginal without the
+ * hyperprior; add its gradient for log pi(theta | y)):
+ *   1/2 d log|Q_x| / d theta_j - 1/2 tr(Q^-1 dQ_j) - 1/2 mu^T dQ_j mu,
+ * with Q_x = tau Q_t (x) Q_s, dQ_j = dQ_x_j, the trace the RBMC estimate of
+ * qsel_trace_grads (exact with a single part), mu the posterior mean, and
+ * d log|Q_x| in closed form: 4 n_t kappa^2 tr(K^-1 C), n, n_s 2 rho^2
+ * (n_t - 1) / (1 + rho) (K^-1 by the blocked sweep in binary64 on a dense
+ * n_pad x n_pad matrix allocated at the first call).  Runs the pipeline if
+ * needed.  terms_out (9 HOST doubles, or NULL): the prior log-determinant
+ * derivatives, the traces and the quadratic forms mu^T dQ_j mu.
+ * Errors: QSEL_EINVAL (NULL grad_out; overlap 0 with several parts),
+ * QSEL_ESTATE (no data), QSEL_ENOTSPD, QSEL_ENOCONV, QSEL_ECUDA.
+ */
+qsel_status qsel_loglik_grad(qsel_ctx *ctx, double grad_out[3], double terms_out[9]);
+
 /* Statistics of the last pipeline run. */
 qsel_status qsel_stats(const qsel_ctx *ctx, qsel_stats_t *stats);
 

@@ -74,6 +74,13 @@ struct qsel_ctx {
   double *d_c_pat = nullptr, *d_g_pat = nullptr, *d_h_pat = nullptr, *d_isqc_pat = nullptr;
   double *d_qs = nullptr, *d_dqs = nullptr, *d_kc = nullptr;
   uint8_t *d_obs = nullptr;
+  // posterior mean and hyperparameter gradient (qsel_set_data and after)
+  double *d_cdiag = nullptr;           // lumped mass diagonal
+  double *d_y = nullptr;               // data on the observed nodes
+  double *d_mu = nullptr;              // posterior mean, n
+  double *d_hyp = nullptr;             // quadratic forms (3), gradient (3), terms (9)
+  double *d_K = nullptr, *d_Kp = nullptr, *d_Ku = nullptr, *d_Kv = nullptr;   // dense K, sweep scratch
+  bool have_data = false;
   int32_t *d_obs_index = nullptr;
   int n_obs = 0;
   TimeCoeffs tc{};
@@ -522,6 +529,7 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   c->n_obs = n_obs;
   TRY(upload(c, &c->d_obs, mask));
   TRY(upload(c, &c->d_obs_index, oidx));
+  TRY(upload(c, &c->d_cdiag, std::vector<double>(m->c_diag, m->c_diag + n_s)));
 
   if (c->opt.preconditioner == QSEL_PRECOND_KRON) TRY(kron_setup(c, m));
 
@@ -830,6 +838,8 @@ static Err pcg_solve(qsel_ctx *c, const PcgVec<T> &v, const T *pblk, double tol,
 //   mixed: iterative refinement -- the true residual R - Q X in double, an
 //   FP32 PCG for the correction to a loose inner tolerance, X += correction
 //   in double -- until every column meets pcg_tol in double.
+static Err solve_R(qsel_ctx *c);
+
 static Err run_sampler(qsel_ctx *c) {
   cudaStream_t s = c->stream;
   launch_philox_normals(s, c->opt.seed, 0u, c->n, c->k, c->ld, c->d_z1);
@@ -838,6 +848,15 @@ static Err run_sampler(qsel_ctx *c) {
                           c->d_z1, c->d_z2, c->d_obs_index, 1.0 / c->sigma, c->d_R);
   c->have_rhs = true;
   QSEL_CUDA_TRY(cudaEventRecord(c->ev[1], s));
+  return solve_R(c);
+}
+
+// X = Q^-1 R for the right-hand sides in d_R (all ld columns; zero columns
+// are inactive from the start): multi-RHS PCG in FP64, or FP32 PCG inside
+// FP64 iterative refinement for the mixed form.  Records pcg_iterations and
+// pcg_max_rel_residual.
+static Err solve_R(qsel_ctx *c) {
+  cudaStream_t s = c->stream;
   const size_t vec = (size_t)c->n * c->ld;
   if (c->kron) TRY(kron_prepare(c));
   if (!c->mixed) {
@@ -1946,6 +1965,133 @@ qsel_status qsel_trace_grads(qsel_ctx *ctx, double grads_out[3]) {
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
   if (ce != cudaSuccess) return finish(ctx, cuda_fail(ce, "copy of traces", __FILE__, __LINE__));
   for (int j = 0; j < 3; ++j) grads_out[j] = ctx->h_small[j];
+  return QSEL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Posterior mean and the gradient of the hyperparameter marginal (hyper.cu).
+// ---------------------------------------------------------------------------
+qsel_status qsel_set_data(qsel_ctx *ctx, const double *y_obs) {
+  if (!ctx) return QSEL_EINVAL;
+  qsel_ctx *c = ctx;
+  if (!y_obs) return finish(c, fail(QSEL_EINVAL, "y_obs must not be NULL"));
+  if (c->n_obs < 1) return finish(c, fail(QSEL_EINVAL, "the model has no observed nodes"));
+  Err e = ok();
+  if (!c->d_y) e = c->alloc(&c->d_y, (size_t)c->n_obs);
+  if (e.code == 0) {
+    const cudaError_t ce = cudaMemcpy(c->d_y, y_obs, (size_t)c->n_obs * sizeof(double), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) e = cuda_fail(ce, "copy of the data", __FILE__, __LINE__);
+  }
+  if (e.code) return finish(c, e);
+  c->have_data = true;
+  return QSEL_OK;
+}
+
+// mu = Q^-1 A^T y / sigma^2 with the sampler's solver, into d_mu; leaves mu
+// in column 0 of d_X (the other columns zero).  The sampler's right-hand
+// sides and samples are overwritten; the statistics of the last
+// qsel_diag_inv are kept.
+static Err compute_mean(qsel_ctx *c) {
+  if (!c->have_data) return fail(QSEL_ESTATE, "no data: call qsel_set_data first");
+  cudaStream_t s = c->stream;
+  if (!c->d_mu) TRY(c->alloc(&c->d_mu, (size_t)c->n));
+  TRY(run_model(c));
+  QSEL_CUDA_TRY(cudaMemsetAsync(c->d_R, 0, (size_t)c->n * c->ld * sizeof(double), s));
+  launch_data_rhs(s, c->d_R, c->ld, c->d_obs, c->d_obs_index, c->d_y, c->n, 1.0 / (c->sigma * c->sigma));
+  c->have_rhs = false;
+  c->injected = false;   // injected samples, if any, are overwritten: later runs sample afresh
+  const int it0 = c->stats.pcg_iterations;
+  const double rel0 = c->stats.pcg_max_rel_residual;
+  Err e = solve_R(c);
+  c->stats.pcg_iterations = it0;
+  c->stats.pcg_max_rel_residual = rel0;
+  TRY(e);
+  QSEL_CUDA_TRY(cudaMemcpy2DAsync(c->d_mu, sizeof(double), c->d_X, (size_t)c->ld * sizeof(double), sizeof(double),
+                                  (size_t)c->n, cudaMemcpyDeviceToDevice, s));
+  QSEL_CUDA_TRY(cudaGetLastError());
+  return ok();
+}
+
+qsel_status qsel_posterior_mean(qsel_ctx *ctx, double *mu_out, int32_t out_is_device) {
+  if (!ctx) return QSEL_EINVAL;
+  qsel_ctx *c = ctx;
+  if (!mu_out) return finish(c, fail(QSEL_EINVAL, "mu_out must not be NULL"));
+  Err e = compute_mean(c);
+  if (e.code) return finish(c, e);
+  cudaError_t ce = cudaMemcpyAsync(mu_out, c->d_mu, (size_t)c->n * sizeof(double),
+                                   out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "copy of the posterior mean", __FILE__, __LINE__));
+  return QSEL_OK;
+}
+
+qsel_status qsel_loglik_grad(qsel_ctx *ctx, double grad_out[3], double terms_out[9]) {
+  if (!ctx) return QSEL_EINVAL;
+  qsel_ctx *c = ctx;
+  if (!grad_out) return finish(c, fail(QSEL_EINVAL, "grad_out must not be NULL"));
+  if (c->n_l < 1 && c->parts.size() > 1)
+    return finish(c, fail(QSEL_EINVAL, "trace gradients need overlap >= 1 when there are several parts"));
+  if (!c->have_data) return finish(c, fail(QSEL_ESTATE, "no data: call qsel_set_data first"));
+  // tr(Q^-1 dQ_j) of the current theta (the RBMC estimate), then mu
+  Err e = ensure(c);
+  if (e.code == 0) e = compute_mean(c);
+  if (e.code) return finish(c, e);
+  cudaStream_t s = c->stream;
+  const int n_pad = c->n_pad;
+  if (!c->d_hyp) e = c->alloc(&c->d_hyp, 15);
+  if (e.code == 0 && !c->d_K) e = c->alloc(&c->d_K, (size_t)n_pad * n_pad);
+  if (e.code == 0 && !c->d_Kp) e = c->alloc(&c->d_Kp, 64 * 64);
+  if (e.code == 0 && !c->d_Ku) e = c->alloc(&c->d_Ku, (size_t)n_pad * 64);
+  if (e.code == 0 && !c->d_Kv) e = c->alloc(&c->d_Kv, (size_t)n_pad * 64);
+  if (e.code) return finish(c, e);
+  // mu^T dQ_j mu: dQ_j mu by the block-tridiagonal SpMM with the derivative's
+  // coefficients (no observation term), its per-column dot partials with mu
+  BtSpmmArgs<double> a{};
+  a.pat = c->pat;
+  a.obs = nullptr;
+  a.obs_w = 0.0;
+  a.n_s = c->n_s;
+  a.n_t = c->n_t;
+  a.ld = c->ld;
+  a.x = c->d_X;
+  a.y = c->d_q;
+  a.dot_partial = c->d_pa;
+  a.tmp = c->d_z1;
+  const double *vals[3] = {c->d_dqs, c->d_qs, c->d_qs};
+  const double *c0s[3] = {c->tc.a0, c->tc.a0, c->tc.r0};
+  const double *c1s[3] = {c->tc.a1, c->tc.a1, c->tc.r1};
+  for (int j = 0; j < 3; ++j) {
+    a.val = vals[j];
+    a.c0 = c0s[j];
+    a.c1 = c1s[j];
+    launch_bt_spmm<double>(s, a);
+    launch_column_sum(s, c->d_pa, bt_spmm_grid(c->n), c->ld, 0, c->d_hyp + j);
+  }
+  // tr(K^-1 C) for the prior's log-determinant: K^-1 by the blocked sweep
+  cudaError_t ce = cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(c->d_K, 0, (size_t)n_pad * n_pad * sizeof(double), s);
+  if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "memset", __FILE__, __LINE__));
+  launch_dense_K(s, c->d_K, n_pad, c->pat, c->d_c_pat, c->d_g_pat, c->d_theta, c->n_s);
+  SweepBatch<double> kb{};
+  kb.count = 1;
+  kb.e[0].A = c->d_K;
+  kb.e[0].P = c->d_Kp;
+  kb.e[0].U = c->d_Ku;
+  kb.e[0].V = c->d_Kv;
+  spd_inverse<double>(s, kb, n_pad, c->d_err, 0);
+  launch_loglik_combine(s, c->d_K, n_pad, c->d_cdiag, c->n_s, c->n_t, c->d_theta, c->d_traces, c->d_hyp,
+                        c->d_hyp + 3, c->d_hyp + 6);
+  int32_t err = 0;
+  ce = cudaMemcpyAsync(c->h_small, c->d_hyp + 3, 12 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(c->h_counters, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce == cudaSuccess) ce = cudaGetLastError();
+  if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "hyperparameter gradient", __FILE__, __LINE__));
+  err = c->h_counters[0];
+  if (err & 1) return finish(c, fail(QSEL_ENOTSPD, "K = kappa^2 C + G was not positive definite"));
+  for (int j = 0; j < 3; ++j) grad_out[j] = c->h_small[j];
+  if (terms_out)
+    for (int j = 0; j < 9; ++j) terms_out[j] = c->h_small[3 + j];
   return QSEL_OK;
 }
 

@@ -406,6 +406,17 @@ void launch_kron_apply(cudaStream_t s, const KronOperator &op, const T *r, T *q,
 template <typename T>
 void launch_pcg_dots(cudaStream_t s, const PcgVec<T> &v);
 
+// ---------------------------------------------------------------- hyper.cu
+// Posterior mean and hyperparameter gradient (see hyper.cu).
+void launch_data_rhs(cudaStream_t s, double *R, int ld, const uint8_t *obs, const int32_t *obs_index,
+                     const double *y, int n, double inv_s2);
+void launch_column_sum(cudaStream_t s, const double *partial, int rows, int ld, int col, double *out);
+void launch_dense_K(cudaStream_t s, double *K, int n_pad, const SellPattern &pat, const double *c_pat,
+                    const double *g_pat, const double *theta, int n_s);
+void launch_loglik_combine(cudaStream_t s, const double *Kinv, int n_pad, const double *c_diag, int n_s, int n_t,
+                           const double *theta, const double *traces, const double *quad, double *grad,
+                           double *terms);
+
 // ---------------------------------------------------------------- lanczos.cu
 struct LanczosArgs {
   int n, ld, k, m;

@@ -89,6 +89,7 @@ def _fields(s) -> dict:
 
 
 EXPORTED = ["qsel_create", "qsel_set_theta", "qsel_diag_inv", "qsel_trace_grads", "qsel_stats",
+            "qsel_set_data", "qsel_posterior_mean", "qsel_loglik_grad",
             "qsel_debug_set_samples", "qsel_debug_get_samples", "qsel_debug_get_rhs",
             "qsel_debug_get_selinv_diag", "qsel_debug_get_lanczos", "qsel_debug_apply_precond",
             "qsel_spd_inverse_noalloc",
@@ -120,6 +121,9 @@ def load_library(path: str = LIB_PATH):
     lib.qsel_set_theta.argtypes = [c_void_p, P(qsel_theta)]
     lib.qsel_diag_inv.argtypes = [c_void_p, c_void_p, c_int32]
     lib.qsel_trace_grads.argtypes = [c_void_p, P(c_double)]
+    lib.qsel_set_data.argtypes = [c_void_p, P(c_double)]
+    lib.qsel_posterior_mean.argtypes = [c_void_p, c_void_p, c_int32]
+    lib.qsel_loglik_grad.argtypes = [c_void_p, P(c_double), P(c_double)]
     lib.qsel_stats.argtypes = [c_void_p, P(qsel_stats_t)]
     lib.qsel_debug_set_samples.argtypes = [c_void_p, P(c_double), c_int32]
     lib.qsel_debug_get_samples.argtypes = [c_void_p, P(c_double), c_int32]
@@ -244,6 +248,34 @@ def qsel_create(n_s, n_t, c_diag, g_rowptr, g_col, g_val, obs_mask, sigma, theta
                          int(overlap), ctypes.byref(opt))
     _check(st, None)
     return Context(h, int(n_s) * int(n_t), int(n_samples), int(n_parts))
+
+
+def qsel_set_data(ctx: Context, y_obs):
+    """Data on the observed nodes, in increasing node order (n_obs values)."""
+    y = np.ascontiguousarray(y_obs, dtype=np.float64)
+    _check(load_library().qsel_set_data(ctx.handle, _ptr(y, c_double)), ctx.handle)
+
+
+def qsel_posterior_mean(ctx: Context, out=None):
+    """mu = Q^-1 A^T y / sigma^2 (numpy array, or into a device tensor `out`)."""
+    lib = load_library()
+    if out is not None:
+        _check(lib.qsel_posterior_mean(ctx.handle, c_void_p(out.data_ptr()), 1), ctx.handle)
+        return out
+    mu = np.empty(ctx.n, dtype=np.float64)
+    _check(lib.qsel_posterior_mean(ctx.handle, _ptr(mu, c_double), 0), ctx.handle)
+    return mu
+
+
+def qsel_loglik_grad(ctx: Context, with_terms=False):
+    """Gradient of log p(y | theta); with_terms also returns (prior log-det
+    derivatives, traces, quadratic forms), each of length 3."""
+    g = np.zeros(3)
+    t = np.zeros(9)
+    _check(load_library().qsel_loglik_grad(ctx.handle, _ptr(g, c_double), _ptr(t, c_double)), ctx.handle)
+    if with_terms:
+        return g, (t[0:3].copy(), t[3:6].copy(), t[6:9].copy())
+    return g
 
 
 def qsel_set_theta(ctx: Context, theta):
