@@ -100,6 +100,8 @@ def parse_args():
     ap.add_argument("--batch-models", type=int, default=64)
     ap.add_argument("--batch-streams", type=int, default=16)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--hyper-eval", action="store_true",
+                    help="time the posterior mean and the hyperparameter gradient (mixed and FP64)")
     ap.add_argument("--profile-timed", action="store_true",
                     help="bracket the timed steps of the chosen form with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
@@ -855,8 +857,58 @@ def run_lanczos_eval(args):
                           "eps_traces": [float(abs(a - b) / abs(b)) for a, b in zip(g, t_ex)]}), flush=True)
 
 
+def run_hyper_eval(args):
+    """Posterior mean and hyperparameter gradient (qsel_loglik_grad) at the
+    workload: per precision one evaluation after one warm-up, CUDA events on
+    the library's stream around set_theta + the gradient (pipeline, posterior
+    mean, quadratic forms, prior term), then the posterior mean alone.  The
+    data are seeded normal values on the observed nodes (the cost does not
+    depend on them)."""
+    import torch
+    from paper_2309_05435_gb300 import build, qsel
+    build.build()
+    w = qi.workload(args.workload)
+    mesh, mask = workload_inputs(w)
+    stream = torch.cuda.current_stream()
+    y = qi.seeded_normal((int(np.count_nonzero(mask)), 1), 7)[:, 0]
+    out = {}
+    for name, prec, pre in (("mixed", qsel.QSEL_MIXED, qsel.QSEL_PRECOND_KRON),
+                            ("fp64", qsel.QSEL_FP64, qsel.QSEL_PRECOND_BLOCK_JACOBI)):
+        ctx = qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma,
+                               w.theta, n_parts=w.n_parts, overlap=w.overlap, n_samples=w.n_samples, seed=3000,
+                               precision=prec, pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream, preconditioner=pre)
+        qsel.qsel_set_data(ctx, y)
+        qsel.qsel_set_theta(ctx, w.theta)
+        qsel.qsel_loglik_grad(ctx)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        qsel.qsel_set_theta(ctx, w.theta)
+        g, (prior, tr, quad) = qsel.qsel_loglik_grad(ctx, with_terms=True)
+        e1.record(stream)
+        qsel.qsel_posterior_mean(ctx)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        st = qsel.qsel_stats(ctx)
+        ctx.close()
+        out[name] = {"grad_ms": e0.elapsed_time(e1), "pipeline_ms": st["ms_total"],
+                     "posterior_mean_ms": e1.elapsed_time(e2), "grad": [float(x) for x in g],
+                     "prior_logdet_grad": [float(x) for x in prior], "traces": [float(x) for x in tr],
+                     "quadratic_forms": [float(x) for x in quad]}
+    rel = [abs(a - b) / max(abs(b), 1e-300) for a, b in zip(out["mixed"]["grad"], out["fp64"]["grad"])]
+    print(json.dumps({"mode": "hyper_eval", "workload": w.name, "n_parts": w.n_parts, "overlap": w.overlap,
+                      "n_samples": w.n_samples, **out,
+                      "speedup_mixed_vs_fp64": out["fp64"]["grad_ms"] / out["mixed"]["grad_ms"],
+                      "grad_rel_diff_mixed_vs_fp64": rel,
+                      "note": "same seed, so the same Philox noise and samples up to the solves' tolerance: the "
+                              "difference is the mixed form's arithmetic"}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.hyper_eval:
+        run_hyper_eval(args)
+        return
     if args.lanczos_eval:
         run_lanczos_eval(args)
         return
