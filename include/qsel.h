@@ -191,9 +191,11 @@ typedef struct {
   double spmm_ms, spmm_bytes;
   int64_t spmm_launches;
   /* With profile_kernels: event time (ms) and launches per kernel class:
-   * 0 dense tile GEMMs, 1 sweep rank-64 updates, 2 SpMM, 3 pivot-tile
-   * inverses (FP64), 4 sweep panels / write-back / mirror, 5 Schur assembly,
-   * 6 sparse row and column gathers, 7 block-Jacobi apply, 8 other PCG and
+   * 0 dense tile GEMMs, 1 sweep updates (rank 64, or rank 256 per panel in
+   * the mixed form), 2 SpMM, 3 pivot-tile inverses, 4 sweep panels (gathers,
+   * panel steps and patches, scatters, mirror), 5 Schur assembly, 6 sparse
+   * row and column gathers, 7 preconditioner apply (block Jacobi or the
+   * Kronecker passes), 8 other PCG and
    * refinement vector kernels, 9 RB correction terms, 10 diagonal and pattern
    * extraction.  Kernels outside these classes are not timed.  class_work is
    * the algorithmic work where defined (FLOPs for 0, 1, 3, 7; bytes for 2),

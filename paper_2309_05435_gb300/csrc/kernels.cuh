@@ -20,13 +20,13 @@ extern thread_local int64_t g_launch_count;
 // (FLOPs or bytes).  Read back after the pipeline has synchronised.
 enum ProfKind {
   PROF_GEMM = 0,      // dense tile GEMMs (CUDA-core and tcgen05)
-  PROF_SWEEP = 1,     // rank-64 updates of the blocked sweep
+  PROF_SWEEP = 1,     // updates of the blocked sweep (rank 64, or rank 64 kSweepPanel per panel)
   PROF_SPMM = 2,      // block-tridiagonal SpMM
   PROF_PIVOT = 3,     // 64x64 pivot-tile inverses (FP64)
-  PROF_PANEL = 4,     // sweep panels, panel write-back, mirror
+  PROF_PANEL = 4,     // sweep panels: gathers, panel steps and patches, scatters, mirror
   PROF_SCHUR = 5,     // Schur assembly of the pivot blocks
   PROF_GATHER = 6,    // sparse row / column gathers
-  PROF_PRECOND = 7,   // block-Jacobi apply with the PCG dots
+  PROF_PRECOND = 7,   // preconditioner apply (block Jacobi, or the Kronecker passes) with the PCG dots
   PROF_PCGVEC = 8,    // PCG axpy, direction update, reductions, refinement
   PROF_CORR = 9,      // RB correction terms
   PROF_EXTRACT = 10,  // diagonal and pattern extraction of Sigma blocks

@@ -31,10 +31,10 @@ namespace tc {
 constexpr int BM = 128, BK = 32;
 constexpr int TILE_A = BM * BK * 4;              // 16 KiB A tile
 constexpr int BAR_BYTES = 256;
-// Configurations: <3 stages, BN = 128> (one CTA per SM) for long K, and
-// <2 stages, BN = 64> for the K = 64 sweep updates: the two K-blocks fit
-// without reusing a stage and two CTAs share an SM, so one CTA's epilogue
-// overlaps the other's loads and MMAs.
+// Configurations: <3 stages, BN = 128> (one CTA per SM) for K > 64, and
+// <2 stages, BN = 64> for K = 64 (the last, one-tile panel of the sweep and
+// the one-pivot sweep): the two K-blocks fit without reusing a stage and two
+// CTAs share an SM, so one CTA's epilogue overlaps the other's loads and MMAs.
 template <int BN>
 __host__ __device__ constexpr int tile_b() {
   return BN * BK * 4;
