@@ -94,3 +94,74 @@ def loglik_grad(model: o.Model, theta, y_obs: np.ndarray, traces=None) -> np.nda
     if traces is None:
         _, traces = o.exact_selinv(o.precision(model, theta), o.precision_derivatives(model, theta))
     return 0.5 * prior_logdet_grad(model, theta) - 0.5 * np.asarray(traces) - 0.5 * quadratic_terms(model, theta, mu)
+
+
+# ----------------------------------------------------------------------------
+# Fixed effects (Section 2.3, Eqs. mean:4-5 and var:1; Eq. hyperpar:3)
+# ----------------------------------------------------------------------------
+# y = A_u u + Z beta + eps with beta ~ N(0, I / beta_prec) (Z: n_obs x n_beta).
+# Joint precision over (u, beta):
+#   Q_uu = Q,  Q_ub = A_u^T Z / sigma^2,  Q_bb = beta_prec I + Z^T Z / sigma^2;
+# with W = Q_uu^-1 Q_ub and the Schur complement S = Q_bb - Q_bu W:
+#   mu_beta = S^-1 (Z^T y / sigma^2 - Q_bu Q_uu^-1 A_u^T y / sigma^2),
+#   mu_u = Q_uu^-1 (A_u^T y / sigma^2) - W mu_beta,          (Eq. mean:5)
+#   Var(beta) = S^-1,  diag Var(u) = diag(Q_uu^-1) + diag(W S^-1 W^T),  (Eq. var:1)
+#   d log|Q| / d theta_j = tr(Q_uu^-1 dQ_j) + tr(S^-1 W^T dQ_j W),     (Eq. hyperpar:3)
+# (dS_j = -Q_bu d(Q_uu^-1) Q_ub = W^T dQ_j W; Q_ub and Q_bb do not depend on theta),
+# and the gradient of log p(y | theta) keeps the form above with these.
+
+
+def fixed_effects(model: o.Model, theta, y_obs, Z, beta_prec):
+    """(mu_u, mu_beta, Var(beta), diag(W S^-1 W^T), W) by the formulas above
+    (sparse solves with Q_uu)."""
+    Z = np.asarray(Z, dtype=float)
+    s2 = model.sigma ** 2
+    obs = np.flatnonzero(model.obs_mask)
+    Q = o.precision(model, theta).tocsc()
+    Qub = np.zeros((model.n, Z.shape[1]))
+    Qub[obs, :] = Z / s2
+    lu = spla.splu(Q)
+    W = lu.solve(Qub)
+    w0 = lu.solve(data_rhs(model, y_obs))
+    S = beta_prec * np.eye(Z.shape[1]) + Z.T @ Z / s2 - Qub.T @ W
+    m = Z.T @ np.asarray(y_obs, dtype=float) / s2 - Qub.T @ w0
+    Sinv = np.linalg.inv(S)
+    mu_b = Sinv @ m
+    mu_u = w0 - W @ mu_b
+    return mu_u, mu_b, Sinv, np.einsum("ra,ab,rb->r", W, Sinv, W), W
+
+
+def log_marginal_fe(model: o.Model, theta, y_obs, Z, beta_prec) -> float:
+    """log p(y | theta) with the fixed effects integrated out, by the ratio of
+    Eq. hyperpar:1 at the joint mode: 1/2 log|Q_x| + n_beta/2 log beta_prec
+    - 1/2 log|Q_uu| - 1/2 log|S| - |y - A mu_u - Z mu_beta|^2 / (2 sigma^2)
+    - 1/2 mu_u^T Q_x mu_u - beta_prec/2 |mu_beta|^2 - n_obs/2 log(2 pi sigma^2)."""
+    y = np.asarray(y_obs, dtype=float)
+    Z = np.asarray(Z, dtype=float)
+    obs = np.flatnonzero(model.obs_mask)
+    mu_u, mu_b, Sinv, _, _ = fixed_effects(model, theta, y, Z, beta_prec)
+    Qx = prior_precision(model, theta)
+    Q = o.precision(model, theta)
+    s2 = model.sigma ** 2
+    r = y - mu_u[obs] - Z @ mu_b
+    _, ld_Sinv = np.linalg.slogdet(Sinv)
+    return float(0.5 * o.logdet(Qx, model.n_s, model.n_t) + 0.5 * Z.shape[1] * math.log(beta_prec)
+                 - 0.5 * o.logdet(Q, model.n_s, model.n_t) + 0.5 * ld_Sinv - 0.5 * (r @ r) / s2
+                 - 0.5 * mu_u @ (Qx @ mu_u) - 0.5 * beta_prec * (mu_b @ mu_b)
+                 - 0.5 * len(obs) * math.log(2.0 * math.pi * s2))
+
+
+def schur_traces(model: o.Model, theta, W, Sinv) -> np.ndarray:
+    """tr(S^-1 W^T dQ_j W) for j = log kappa, log tau, logit rho."""
+    return np.array([float(np.sum(Sinv * (W.T @ (d @ W)))) for d in o.precision_derivatives(model, theta)])
+
+
+def loglik_grad_fe(model: o.Model, theta, y_obs, Z, beta_prec, traces=None) -> np.ndarray:
+    """Gradient of log_marginal_fe: 1/2 d log|Q_x| - 1/2 (tr(Q_uu^-1 dQ_j) +
+    tr(S^-1 W^T dQ_j W)) - 1/2 mu_u^T dQ_j mu_u (traces: tr(Q_uu^-1 dQ_j),
+    default exact)."""
+    mu_u, _, Sinv, _, W = fixed_effects(model, theta, y_obs, Z, beta_prec)
+    if traces is None:
+        _, traces = o.exact_selinv(o.precision(model, theta), o.precision_derivatives(model, theta))
+    return (0.5 * prior_logdet_grad(model, theta) - 0.5 * (np.asarray(traces) + schur_traces(model, theta, W, Sinv))
+            - 0.5 * quadratic_terms(model, theta, mu_u))

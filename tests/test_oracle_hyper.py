@@ -74,3 +74,57 @@ def test_prior_logdet_gradient_closed_forms():
         if n_t == 1:
             assert g[2] == 0.0
         assert g[1] == mdl.n
+
+
+# ---------------------------------------------------------------- fixed effects
+def _setup_fe(m=4, n_t=3, n_beta=3):
+    mdl, th, y = _setup(m, n_t)
+    Z = qi.seeded_normal((len(y), n_beta), 8)
+    return mdl, th, y, Z, 0.5
+
+
+def _joint_covariance(mdl, th, Z, beta_prec):
+    """Data covariance with beta integrated out: sigma^2 I + A Q_x^-1 A^T + Z Z^T / beta_prec."""
+    Syy, Sx, obs = _data_covariance(mdl, th)
+    return Syy + Z @ Z.T / beta_prec, Sx, obs
+
+
+def test_fixed_effects_mean_and_variances_match_the_joint_gaussian():
+    """mu_u, mu_beta by the Kalman form of the joint prior (u, beta); Var(beta)
+    and diag Var(u) (Eq. var:1) from the dense joint posterior covariance."""
+    mdl, th, y, Z, bp = _setup_fe()
+    C, Sx, obs = _joint_covariance(mdl, th, Z, bp)
+    a = np.linalg.solve(C, y)
+    mu_u_k = Sx[:, obs] @ a
+    mu_b_k = Z.T @ a / bp
+    mu_u, mu_b, Sinv, corr, _ = h.fixed_effects(mdl, th, y, Z, bp)
+    np.testing.assert_allclose(mu_u, mu_u_k, rtol=1e-8, atol=1e-11)
+    np.testing.assert_allclose(mu_b, mu_b_k, rtol=1e-8, atol=1e-11)
+    # joint posterior precision, dense
+    n, nb = mdl.n, Z.shape[1]
+    J = np.zeros((n + nb, n + nb))
+    J[:n, :n] = o.precision(mdl, th).toarray()
+    J[obs, n:] = Z / mdl.sigma ** 2
+    J[n:, obs] = Z.T / mdl.sigma ** 2
+    J[n:, n:] = bp * np.eye(nb) + Z.T @ Z / mdl.sigma ** 2
+    Jinv = np.linalg.inv(J)
+    np.testing.assert_allclose(Sinv, Jinv[n:, n:], rtol=1e-8, atol=1e-12)
+    Quu_inv = np.linalg.inv(J[:n, :n])
+    np.testing.assert_allclose(np.diag(Quu_inv) + corr, np.diag(Jinv)[:n], rtol=1e-8, atol=1e-12)
+
+
+def test_fixed_effects_log_marginal_and_gradient():
+    mdl, th, y, Z, bp = _setup_fe(5, 4)
+    C, _, _ = _joint_covariance(mdl, th, Z, bp)
+    sign, ld = np.linalg.slogdet(C)
+    direct = -0.5 * (ld + y @ np.linalg.solve(C, y) + len(y) * math.log(2.0 * math.pi))
+    assert sign > 0
+    assert abs(h.log_marginal_fe(mdl, th, y, Z, bp) - direct) < 1e-9 * max(1.0, abs(direct))
+    g = h.loglik_grad_fe(mdl, th, y, Z, bp)
+    step = 1e-5
+    for j in range(3):
+        tp, tm = list(th), list(th)
+        tp[j] += step
+        tm[j] -= step
+        fd = (h.log_marginal_fe(mdl, tp, y, Z, bp) - h.log_marginal_fe(mdl, tm, y, Z, bp)) / (2 * step)
+        assert abs(g[j] - fd) < 1e-5 * max(1.0, abs(fd)), (j, g[j], fd)
