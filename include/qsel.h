@@ -283,6 +283,29 @@ qsel_status qsel_posterior_mean(qsel_ctx *ctx, double *mu_out, int32_t out_is_de
  */
 qsel_status qsel_loglik_grad(qsel_ctx *ctx, double grad_out[3], double terms_out[9]);
 
+/*
+ * Fixed effects: y = A u + Z beta + eps with beta ~ N(0, I / beta_prec)
+ * (Section 2.3, Eqs. mean:4-5, var:1; Eq. hyperpar:3).  Z: n_obs x n_beta
+ * row-major HOST array (rows in the order of y_obs), copied; 0 <= n_beta <=
+ * 63; n_beta = 0 removes them.  With fixed effects qsel_posterior_mean
+ * returns mu_u and qsel_loglik_grad adds tr(S^-1 W^T dQ_j W) to the trace
+ * term (S the Schur complement of Q_uu in the joint precision, W =
+ * Q_uu^-1 A^T Z / sigma^2, both from the same multi-RHS solve as mu).
+ * Errors: QSEL_EINVAL (range, NULL Z, beta_prec <= 0), QSEL_ECUDA.
+ */
+qsel_status qsel_set_covariates(qsel_ctx *ctx, int32_t n_beta, const double *Z, double beta_prec);
+
+/*
+ * mu_beta (n_beta HOST doubles), Var(beta) = S^-1 (n_beta^2, row-major HOST)
+ * and the correction diag(W S^-1 W^T) that Eq. var:1 adds to diag(Q_uu^-1)
+ * (n doubles, host or device with corr_is_device); any output may be NULL.
+ * Solves as qsel_posterior_mean.
+ * Errors: QSEL_ESTATE (no data or no covariates), QSEL_ENOTSPD, QSEL_ENOCONV,
+ * QSEL_ECUDA.
+ */
+qsel_status qsel_fixed_effects(qsel_ctx *ctx, double *mu_beta_out, double *var_beta_out, double *var_u_corr_out,
+                               int32_t corr_is_device);
+
 /* Statistics of the last pipeline run. */
 qsel_status qsel_stats(const qsel_ctx *ctx, qsel_stats_t *stats);
 

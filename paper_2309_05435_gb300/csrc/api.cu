@@ -81,6 +81,18 @@ struct qsel_ctx {
   double *d_hyp = nullptr;             // quadratic forms (3), gradient (3), terms (9)
   double *d_K = nullptr, *d_Kp = nullptr, *d_Ku = nullptr, *d_Kv = nullptr;   // dense K, sweep scratch
   bool have_data = false;
+  // fixed effects (qsel_set_covariates): Z (n_obs x n_beta), the observed
+  // nodes in order, and S, m, S^-1, mu_beta, C, Schur traces (3), diag corr (n)
+  int n_beta = 0;
+  double beta_prec = 1.0;
+  double *d_Z = nullptr, *d_fe = nullptr, *d_fecorr = nullptr;
+  int32_t *d_obs_nodes = nullptr;
+  double *fe_S() { return d_fe; }
+  double *fe_m() { return d_fe + 64 * 64; }
+  double *fe_Sinv() { return d_fe + 64 * 64 + 64; }
+  double *fe_mu() { return d_fe + 2 * 64 * 64 + 64; }
+  double *fe_C() { return d_fe + 2 * 64 * 64 + 128; }
+  double *fe_trace() { return d_fe + 3 * 64 * 64 + 128; }
   int32_t *d_obs_index = nullptr;
   int n_obs = 0;
   TimeCoeffs tc{};
@@ -1987,6 +1999,42 @@ qsel_status qsel_set_data(qsel_ctx *ctx, const double *y_obs) {
   return QSEL_OK;
 }
 
+qsel_status qsel_set_covariates(qsel_ctx *ctx, int32_t n_beta, const double *Z, double beta_prec) {
+  if (!ctx) return QSEL_EINVAL;
+  qsel_ctx *c = ctx;
+  if (n_beta < 0 || n_beta > 63 || n_beta + 1 > c->ld)
+    return finish(c, fail(QSEL_EINVAL, "n_beta must lie in [0, 63]"));
+  if (n_beta > 0 && (!Z || !(beta_prec > 0.0) || !std::isfinite(beta_prec)))
+    return finish(c, fail(QSEL_EINVAL, "fixed effects need Z and a finite beta_prec > 0"));
+  if (n_beta > 0 && c->n_obs < 1) return finish(c, fail(QSEL_EINVAL, "the model has no observed nodes"));
+  Err e = ok();
+  if (n_beta > 0) {
+    if (!c->d_fe) e = c->alloc(&c->d_fe, (size_t)3 * 64 * 64 + 128 + 8);
+    if (e.code == 0 && !c->d_fecorr) e = c->alloc(&c->d_fecorr, (size_t)c->n);
+    if (e.code == 0 && !c->d_obs_nodes) {
+      // the observed nodes in increasing order (host index bookkeeping)
+      std::vector<int32_t> nodes;
+      nodes.reserve(c->n_obs);
+      std::vector<uint8_t> mask(c->n);
+      const cudaError_t ce = cudaMemcpy(mask.data(), c->d_obs, c->n, cudaMemcpyDeviceToHost);
+      if (ce != cudaSuccess) e = cuda_fail(ce, "copy of the observation mask", __FILE__, __LINE__);
+      for (int r = 0; e.code == 0 && r < c->n; ++r)
+        if (mask[r]) nodes.push_back(r);
+      if (e.code == 0) e = upload(c, &c->d_obs_nodes, nodes);
+    }
+    if (e.code == 0 && !c->d_Z) e = c->alloc(&c->d_Z, (size_t)c->n_obs * 63);   // room for any n_beta
+    if (e.code == 0) {
+      const cudaError_t ce =
+          cudaMemcpy(c->d_Z, Z, (size_t)c->n_obs * n_beta * sizeof(double), cudaMemcpyHostToDevice);
+      if (ce != cudaSuccess) e = cuda_fail(ce, "copy of the covariates", __FILE__, __LINE__);
+    }
+  }
+  if (e.code) return finish(c, e);
+  c->n_beta = n_beta;
+  c->beta_prec = n_beta > 0 ? beta_prec : 1.0;
+  return QSEL_OK;
+}
+
 // mu = Q^-1 A^T y / sigma^2 with the sampler's solver, into d_mu; leaves mu
 // in column 0 of d_X (the other columns zero).  The sampler's right-hand
 // sides and samples are overwritten; the statistics of the last
@@ -1997,7 +2045,9 @@ static Err compute_mean(qsel_ctx *c) {
   if (!c->d_mu) TRY(c->alloc(&c->d_mu, (size_t)c->n));
   TRY(run_model(c));
   QSEL_CUDA_TRY(cudaMemsetAsync(c->d_R, 0, (size_t)c->n * c->ld * sizeof(double), s));
-  launch_data_rhs(s, c->d_R, c->ld, c->d_obs, c->d_obs_index, c->d_y, c->n, 1.0 / (c->sigma * c->sigma));
+  const double inv_s2 = 1.0 / (c->sigma * c->sigma);
+  launch_data_rhs(s, c->d_R, c->ld, c->d_obs, c->d_obs_index, c->d_y, c->n, inv_s2);
+  if (c->n_beta > 0) launch_fe_rhs(s, c->d_R, c->ld, c->d_obs_nodes, c->d_Z, c->n_obs, c->n_beta, inv_s2);
   c->have_rhs = false;
   c->injected = false;   // injected samples, if any, are overwritten: later runs sample afresh
   const int it0 = c->stats.pcg_iterations;
@@ -2006,8 +2056,21 @@ static Err compute_mean(qsel_ctx *c) {
   c->stats.pcg_iterations = it0;
   c->stats.pcg_max_rel_residual = rel0;
   TRY(e);
-  QSEL_CUDA_TRY(cudaMemcpy2DAsync(c->d_mu, sizeof(double), c->d_X, (size_t)c->ld * sizeof(double), sizeof(double),
-                                  (size_t)c->n, cudaMemcpyDeviceToDevice, s));
+  if (c->n_beta > 0) {
+    // fixed effects: S, m over the observed nodes, S^-1 and mu_beta, then
+    // mu_u = X[:, 0] - W mu_beta (written back to X[:, 0]) and diag(W S^-1 W^T)
+    QSEL_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), s));
+    launch_fe_schur(s, c->d_X, c->ld, c->d_obs_nodes, c->d_Z, c->d_y, c->n_obs, c->n_beta, inv_s2, c->beta_prec,
+                    c->fe_S(), c->fe_m());
+    launch_fe_solve(s, c->fe_S(), c->fe_m(), c->n_beta, c->fe_Sinv(), c->fe_mu(), c->d_err);
+    launch_fe_mean(s, c->d_X, c->ld, c->n, c->n_beta, c->fe_mu(), c->fe_Sinv(), c->d_mu, c->d_fecorr);
+    QSEL_CUDA_TRY(cudaMemcpyAsync(c->h_counters, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    QSEL_CUDA_TRY(cudaStreamSynchronize(s));
+    if (c->h_counters[0] & 1) return fail(QSEL_ENOTSPD, "the Schur complement of the fixed effects was not positive");
+  } else {
+    QSEL_CUDA_TRY(cudaMemcpy2DAsync(c->d_mu, sizeof(double), c->d_X, (size_t)c->ld * sizeof(double), sizeof(double),
+                                    (size_t)c->n, cudaMemcpyDeviceToDevice, s));
+  }
   QSEL_CUDA_TRY(cudaGetLastError());
   return ok();
 }
@@ -2022,6 +2085,30 @@ qsel_status qsel_posterior_mean(qsel_ctx *ctx, double *mu_out, int32_t out_is_de
                                    out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
   if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "copy of the posterior mean", __FILE__, __LINE__));
+  return QSEL_OK;
+}
+
+qsel_status qsel_fixed_effects(qsel_ctx *ctx, double *mu_beta_out, double *var_beta_out, double *var_u_corr_out,
+                               int32_t corr_is_device) {
+  if (!ctx) return QSEL_EINVAL;
+  qsel_ctx *c = ctx;
+  if (c->n_beta < 1) return finish(c, fail(QSEL_ESTATE, "no fixed effects: call qsel_set_covariates first"));
+  Err e = compute_mean(c);
+  if (e.code) return finish(c, e);
+  const int nb = c->n_beta;
+  cudaStream_t s = c->stream;
+  cudaError_t ce = cudaSuccess;
+  std::vector<double> mu(nb), sinv((size_t)nb * nb);
+  ce = cudaMemcpyAsync(mu.data(), c->fe_mu(), nb * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(sinv.data(), c->fe_Sinv(), (size_t)nb * nb * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess && var_u_corr_out)
+    ce = cudaMemcpyAsync(var_u_corr_out, c->d_fecorr, (size_t)c->n * sizeof(double),
+                         corr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "copy of the fixed effects", __FILE__, __LINE__));
+  if (mu_beta_out) std::copy(mu.begin(), mu.end(), mu_beta_out);
+  if (var_beta_out) std::copy(sinv.begin(), sinv.end(), var_beta_out);
   return QSEL_OK;
 }
 
@@ -2066,6 +2153,9 @@ qsel_status qsel_loglik_grad(qsel_ctx *ctx, double grad_out[3], double terms_out
     a.c1 = c1s[j];
     launch_bt_spmm<double>(s, a);
     launch_column_sum(s, c->d_pa, bt_spmm_grid(c->n), c->ld, 0, c->d_hyp + j);
+    // fixed effects: tr(S^-1 W^T dQ_j W) from the same product
+    if (c->n_beta > 0)
+      launch_fe_schur_trace(s, c->d_X, c->d_q, c->ld, c->n, c->n_beta, c->fe_Sinv(), c->fe_C(), c->fe_trace() + j);
   }
   // tr(K^-1 C) for the prior's log-determinant: K^-1 by the blocked sweep
   cudaError_t ce = cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), s);
@@ -2079,8 +2169,8 @@ qsel_status qsel_loglik_grad(qsel_ctx *ctx, double grad_out[3], double terms_out
   kb.e[0].U = c->d_Ku;
   kb.e[0].V = c->d_Kv;
   spd_inverse<double>(s, kb, n_pad, c->d_err, 0);
-  launch_loglik_combine(s, c->d_K, n_pad, c->d_cdiag, c->n_s, c->n_t, c->d_theta, c->d_traces, c->d_hyp,
-                        c->d_hyp + 3, c->d_hyp + 6);
+  launch_loglik_combine(s, c->d_K, n_pad, c->d_cdiag, c->n_s, c->n_t, c->d_theta, c->d_traces,
+                        c->n_beta > 0 ? c->fe_trace() : nullptr, c->d_hyp, c->d_hyp + 3, c->d_hyp + 6);
   int32_t err = 0;
   ce = cudaMemcpyAsync(c->h_small, c->d_hyp + 3, 12 * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(c->h_counters, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);

@@ -414,8 +414,19 @@ void launch_column_sum(cudaStream_t s, const double *partial, int rows, int ld, 
 void launch_dense_K(cudaStream_t s, double *K, int n_pad, const SellPattern &pat, const double *c_pat,
                     const double *g_pat, const double *theta, int n_s);
 void launch_loglik_combine(cudaStream_t s, const double *Kinv, int n_pad, const double *c_diag, int n_s, int n_t,
-                           const double *theta, const double *traces, const double *quad, double *grad,
-                           double *terms);
+                           const double *theta, const double *traces, const double *extra, const double *quad,
+                           double *grad, double *terms);
+// fixed effects (see hyper.cu)
+void launch_fe_rhs(cudaStream_t s, double *R, int ld, const int32_t *obs_nodes, const double *Z, int n_obs,
+                   int n_beta, double inv_s2);
+void launch_fe_schur(cudaStream_t s, const double *X, int ld, const int32_t *obs_nodes, const double *Z,
+                     const double *y, int n_obs, int n_beta, double inv_s2, double beta_prec, double *S, double *m);
+void launch_fe_solve(cudaStream_t s, const double *S, const double *m, int n_beta, double *Sinv, double *mu_beta,
+                     int32_t *err_flag);
+void launch_fe_mean(cudaStream_t s, double *X, int ld, int n, int n_beta, const double *mu_beta, const double *Sinv,
+                    double *mu, double *corr);
+void launch_fe_schur_trace(cudaStream_t s, const double *X, const double *Y, int ld, int n, int n_beta,
+                           const double *Sinv, double *C, double *out);
 
 // ---------------------------------------------------------------- lanczos.cu
 struct LanczosArgs {

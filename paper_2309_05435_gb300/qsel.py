@@ -89,7 +89,8 @@ def _fields(s) -> dict:
 
 
 EXPORTED = ["qsel_create", "qsel_set_theta", "qsel_diag_inv", "qsel_trace_grads", "qsel_stats",
-            "qsel_set_data", "qsel_posterior_mean", "qsel_loglik_grad",
+            "qsel_set_data", "qsel_posterior_mean", "qsel_loglik_grad", "qsel_set_covariates",
+            "qsel_fixed_effects",
             "qsel_debug_set_samples", "qsel_debug_get_samples", "qsel_debug_get_rhs",
             "qsel_debug_get_selinv_diag", "qsel_debug_get_lanczos", "qsel_debug_apply_precond",
             "qsel_spd_inverse_noalloc",
@@ -124,6 +125,8 @@ def load_library(path: str = LIB_PATH):
     lib.qsel_set_data.argtypes = [c_void_p, P(c_double)]
     lib.qsel_posterior_mean.argtypes = [c_void_p, c_void_p, c_int32]
     lib.qsel_loglik_grad.argtypes = [c_void_p, P(c_double), P(c_double)]
+    lib.qsel_set_covariates.argtypes = [c_void_p, c_int32, P(c_double), c_double]
+    lib.qsel_fixed_effects.argtypes = [c_void_p, P(c_double), P(c_double), P(c_double), c_int32]
     lib.qsel_stats.argtypes = [c_void_p, P(qsel_stats_t)]
     lib.qsel_debug_set_samples.argtypes = [c_void_p, P(c_double), c_int32]
     lib.qsel_debug_get_samples.argtypes = [c_void_p, P(c_double), c_int32]
@@ -265,6 +268,25 @@ def qsel_posterior_mean(ctx: Context, out=None):
     mu = np.empty(ctx.n, dtype=np.float64)
     _check(lib.qsel_posterior_mean(ctx.handle, _ptr(mu, c_double), 0), ctx.handle)
     return mu
+
+
+def qsel_set_covariates(ctx: Context, Z, beta_prec):
+    """Fixed effects: Z (n_obs x n_beta, rows in the order of the data),
+    beta ~ N(0, I / beta_prec); an empty Z removes them."""
+    Zc = np.ascontiguousarray(Z, dtype=np.float64)
+    nb = 0 if Zc.size == 0 else int(Zc.shape[1])
+    _check(load_library().qsel_set_covariates(ctx.handle, nb, _ptr(Zc, c_double) if nb else None,
+                                              float(beta_prec)), ctx.handle)
+
+
+def qsel_fixed_effects(ctx: Context, n_beta: int):
+    """(mu_beta, Var(beta), diag(W S^-1 W^T)) as numpy arrays."""
+    mu = np.empty(n_beta)
+    var = np.empty((n_beta, n_beta))
+    corr = np.empty(ctx.n)
+    _check(load_library().qsel_fixed_effects(ctx.handle, _ptr(mu, c_double), _ptr(var, c_double),
+                                             _ptr(corr, c_double), 0), ctx.handle)
+    return mu, var, corr
 
 
 def qsel_loglik_grad(ctx: Context, with_terms=False):

@@ -98,3 +98,41 @@ def test_optimizer_reaches_the_oracle_mode(q):
     th, hist = hyper.optimize_theta(ctx, y, th0)
     print(f"GPU mode {th} after {len(hist)} steps; oracle mode {res.x}")
     assert np.max(np.abs(th - res.x)) < 1e-4
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fixed_effects_match_oracle(q, precision):
+    """mu_u, mu_beta, Var(beta) and the Eq. var:1 correction against the
+    oracle's Schur-complement formulas (verified there against the joint
+    Gaussian)."""
+    prec = q.QSEL_FP64 if precision == "fp64" else q.QSEL_MIXED
+    c = Case(q, "grid16_nt8", precision=prec, pcg_tol=1e-10)
+    y = _y(c)
+    Z = qi.seeded_normal((len(y), 3), 8)
+    q.qsel_set_data(c.ctx, y)
+    q.qsel_set_covariates(c.ctx, Z, 0.5)
+    mu = q.qsel_posterior_mean(c.ctx)
+    mu_b, var_b, corr = q.qsel_fixed_effects(c.ctx, 3)
+    mu_or, mu_b_or, Sinv_or, corr_or, _ = h.fixed_effects(c.model, c.theta, y, Z, 0.5)
+    print(f"{precision}: mu_u {_rel(mu, mu_or):.2e} mu_beta {_rel(mu_b, mu_b_or):.2e} "
+          f"Var(beta) {_rel(var_b, Sinv_or):.2e} corr {_rel(corr, corr_or):.2e}")
+    for a, b in ((mu, mu_or), (mu_b, mu_b_or), (var_b, Sinv_or), (corr, corr_or)):
+        assert _rel(a, b) < 1e-7
+
+
+def test_loglik_grad_with_fixed_effects_single_part(q):
+    c = Case(q, "grid16_nt8", precision=q.QSEL_FP64, parts=1, overlap=0, pcg_tol=1e-10)
+    y = _y(c)
+    Z = qi.seeded_normal((len(y), 2), 9)
+    q.qsel_set_data(c.ctx, y)
+    q.qsel_set_covariates(c.ctx, Z, 2.0)
+    g, (prior, tr, quad) = q.qsel_loglik_grad(c.ctx, with_terms=True)
+    g_or = h.loglik_grad_fe(c.model, c.theta, y, Z, 2.0)
+    scale = 0.5 * (np.abs(prior) + np.abs(tr) + np.abs(quad))
+    print(f"fixed effects: gradient {g} oracle {g_or}")
+    assert np.all(np.abs(g - g_or) <= 1e-7 * scale)
+    # removing the covariates restores the model without fixed effects
+    q.qsel_set_covariates(c.ctx, np.zeros((len(y), 0)), 1.0)
+    g0 = q.qsel_loglik_grad(c.ctx)
+    g0_or = h.loglik_grad(c.model, c.theta, y)
+    assert np.all(np.abs(g0 - g0_or) <= 1e-7 * scale)
