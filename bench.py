@@ -100,6 +100,7 @@ def parse_args():
     ap.add_argument("--batch-models", type=int, default=64)
     ap.add_argument("--batch-streams", type=int, default=16)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--hyper-eval", action="store_true",
                     help="time the posterior mean and the hyperparameter gradient (mixed and FP64)")
     ap.add_argument("--profile-timed", action="store_true",
@@ -273,6 +274,22 @@ def oracle_sample(w):
 
 def cpu_cores():
     return os.cpu_count() or 1
+
+
+def oracle_sample_single_thread(w):
+    """The same oracle sample in a child process whose BLAS / OpenMP pools are
+    limited to one thread before numpy loads; (extrapolated seconds, sample
+    seconds) or None if the child fails."""
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[var] = "1"
+    try:
+        p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload", w.name],
+                           env=env, capture_output=True, text=True, timeout=600)
+        d = json.loads(p.stdout.strip().splitlines()[-1])
+        return d["est"], d["spent"]
+    except Exception:   # a missing single-thread figure must not fail the bench line
+        return None
 
 
 # ----------------------------------------------------------------------------
@@ -553,6 +570,9 @@ def run_native(args):
         est, spent, desc = oracle_sample(w)
         cpu = {"value": est, "unit": "s", "cores": cpu_cores(), "kind": "oracle", "sample": desc,
                "sample_seconds": spent}
+        one = oracle_sample_single_thread(w)
+        if one is not None:
+            cpu["single_thread_value"], cpu["single_thread_sample_seconds"] = one
 
     form = "mixed precision RBMC (FP32 PCG + FP64 refinement, FP32 tiles + double-float pivots)" \
         if chosen_prec == qsel.QSEL_MIXED else "plain FP64 RBMC"
@@ -906,6 +926,10 @@ def run_hyper_eval(args):
 
 def main():
     args = parse_args()
+    if args.oracle_sample:
+        est, spent, _ = oracle_sample(qi.workload(args.workload))
+        print(json.dumps({"est": est, "spent": spent}), flush=True)
+        return
     if args.hyper_eval:
         run_hyper_eval(args)
         return
