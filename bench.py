@@ -566,7 +566,7 @@ def run_native(args):
             alt["accuracy"] = errs(v_alt, g_alt)
 
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:   # the CPU baseline is an N = 1 figure
         est, spent, desc = oracle_sample(w)
         cpu = {"value": est, "unit": "s", "cores": cpu_cores(), "kind": "oracle", "sample": desc,
                "sample_seconds": spent}
