@@ -24,7 +24,8 @@
  *   2. one multi-right-hand-side preconditioned conjugate-gradient solve
  *      Q X = R for all samples at once (Section 3.3),
  *   3. per overlapping time subdomain Omega_p^*: exact block-tridiagonal
- *      factorisation and Takahashi selected inversion (Section 3.2.3),
+ *      factorisation and Takahashi selected inversion (Section 3.2.3; in the
+ *      mixed form concurrently with step 2, which only step 4 needs),
  *   4. the Rao-Blackwell correction w = Q_{**}^-1 Q_{*S} x_S and its squares
  *      (Algorithm 4), restricted to Omega_p.
  *
@@ -35,7 +36,10 @@
  *     qsel_create; the context owns all device memory it allocates.
  *   - Work is issued on the CUDA stream given in qsel_options (NULL = the
  *     legacy default stream); every call returns after the stream has reached
- *     the end of its work (results are ready on return).
+ *     the end of its work (results are ready on return).  Inside a call the
+ *     context may fork work onto non-blocking streams of its own (the PCG
+ *     beside the first wave's factorisation, the sweep's look-ahead) and
+ *     joins them back into that stream before it returns.
  *   - One context must not be used from two threads at the same time.
  *   - A CUDA error inside a call is reported as QSEL_ECUDA; the context must
  *     then be destroyed.
