@@ -332,7 +332,8 @@ qsel_status qsel_error_estimate(qsel_ctx *ctx, double *part_err, double *global_
  * qsel_debug_set_samples: use X (HOST, n rows x n_samples columns, row-major
  *   with leading dimension ld >= n_samples) as the global samples instead of
  *   running steps 1-2; only the separator slabs are read.  Stays in effect
- *   until qsel_set_theta.
+ *   until qsel_set_theta or a solve of qsel_posterior_mean /
+ *   qsel_fixed_effects / qsel_loglik_grad, which reuses the sample buffers.
  * qsel_debug_get_samples: copy the samples of the last run to X (HOST, same
  *   layout).
  * qsel_debug_get_rhs: copy the perturbation right-hand sides R of the last
