@@ -358,27 +358,31 @@ qsel_status qsel_debug_apply_precond(qsel_ctx *ctx, const double *R, double *Z, 
 
 /*
  * Allocation-free SPD inverse.  The paper has no counterpart: this entry point
- * exists for callers that cannot call cudaMalloc -- code running while a
- * stream is captured into a CUDA graph (allocation cannot be captured), code
- * inside a framework whose caching allocator owns the device memory budget,
- * and latency-bound loops that cannot take the implicit synchronisation of
- * an allocation.  It runs the library's blocked symmetric-sweep inverse (the
- * kernel that inverts the pivot blocks of the subdomain factorisation) on one
- * caller-owned matrix and allocates nothing.
+ * exists for callers that cannot let a library call cudaMalloc -- code inside
+ * a framework whose caching allocator owns the device memory budget (an
+ * allocation outside it can fail or fragment memory the framework has
+ * reserved), and long-running services that must keep their device memory
+ * footprint fixed after start-up.  It runs the library's blocked
+ * symmetric-sweep inverse (the kernel that inverts the pivot blocks of the
+ * subdomain factorisation) on one caller-owned matrix and allocates nothing.
  *   a_dev        DEVICE pointer to an n x n symmetric positive definite
  *                matrix, row-major with leading dimension lda; overwritten
  *                in place with its inverse (both triangles).
  *   n, lda       1 <= n <= QSEL_NOALLOC_MAX_N, lda >= n.
  *   cuda_stream  cudaStream_t for the work, or NULL for the legacy default
- *                stream; the call returns once the stream has finished it.
+ *                stream.  The call copies its pivot status back to the host
+ *                and synchronises this stream before it returns (on the
+ *                legacy stream that also waits for the other work on it).
  * Scratch: a file-scope device array of QSEL_NOALLOC_MAX_N^2 + 2 * 64 *
  *   QSEL_NOALLOC_MAX_N + 64^2 doubles (about 9 MiB), held by every GPU that
  *   loads this part of the library until the process exits.  The first call
  *   on each device looks up the array's device address with that device
- *   current; make that first call before any stream capture.  Every call
- *   shares the array and overwrites what the last call left there, so calls
- *   that overlap on the GPU (other streams, other host threads) race: the
- *   caller must serialise them.
+ *   current (set-up); make that first call before any stream capture.  The
+ *   looked-up address does not survive a device reset (cudaDeviceReset):
+ *   calls after a reset are not supported.  Every call shares the array and
+ *   overwrites what the last call left there (the status word is cleared at
+ *   the start of each call), so calls that overlap on the GPU (other streams,
+ *   other host threads) race: the caller must serialise them.
  * Errors: QSEL_EINVAL (NULL pointer, n out of range, lda < n), QSEL_ENOTSPD
  *   (non-positive pivot), QSEL_ECUDA; the message is in qsel_last_error(NULL).
  */

@@ -1,13 +1,14 @@
 // Allocation-free SPD inverse (qsel_spd_inverse_noalloc in qsel.h).
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured into a CUDA graph (allocation is not a capturable operation), code
-// inside a framework whose caching allocator already owns the device memory
-// budget, and latency-bound loops where an implicit device synchronisation
-// from an allocation is not acceptable.  This entry point serves them: it
-// inverts one SPD matrix in place in caller-owned device memory, using as
-// scratch only the file-scope array below, which every GPU that loads this
-// module holds until the process exits.
+// Some callers cannot let a library call cudaMalloc: code inside a framework
+// whose caching allocator already owns the device memory budget (a foreign
+// allocation can fail or fragment what the framework reserved), and
+// long-running services that must keep their device memory footprint fixed
+// after start-up.  This entry point serves them: it inverts one SPD matrix in
+// place in caller-owned device memory, using as scratch only the file-scope
+// array below, which every GPU that loads this module holds until the
+// process exits.  The call reads its pivot status back to the host and
+// synchronises the caller's stream before it returns.
 #include <mutex>
 
 #include "qsel.h"
@@ -58,7 +59,8 @@ struct ErrorSink {
 
 // Device address of the scratch array on the current device, looked up once
 // per device with that device current (the host-side symbol is only a
-// stand-in and must never be passed to a kernel).
+// stand-in and must never be passed to a kernel).  A device reset would
+// invalidate the cached address; calls after one are not supported.
 cudaError_t scratch_on_current_device(double **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -1,10 +1,11 @@
 """The allocation-free entry point qsel_spd_inverse_noalloc, checked against
 the library's regular path.
 
-Callers such as code running under CUDA-graph stream capture, or inside a
-framework whose allocator owns the device memory, cannot let the library
-call cudaMalloc.  For them the library offers one SPD inverse that works in
-caller-owned device memory with a fixed, shared scratch array.  A one-slab,
+Callers inside a framework whose caching allocator owns the device memory
+budget, or services that must keep their device memory footprint fixed after
+start-up, cannot let the library call cudaMalloc.  For them the library
+offers one SPD inverse that works in caller-owned device memory with a fixed,
+shared scratch array.  A one-slab,
 one-part model makes the regular path (qsel_diag_inv) return exactly
 diag(A^-1) for the pivot block A = tau Q_t[0,0] Q_s + A_obs^T A_obs / sigma^2,
 so the diagonal of the no-alloc inverse of that same A must match it to the
