@@ -224,6 +224,11 @@ qsel_status qsel_create(qsel_ctx **out, const qsel_model *model, const qsel_thet
                         const qsel_partition *partition, int32_t overlap,
                         const qsel_options *opt);
 
+/* Replace the Philox key of the perturbation noise (qsel_options.seed); the
+ * next qsel_diag_inv / qsel_trace_grads draw new samples.  Injected samples
+ * are dropped. */
+qsel_status qsel_set_seed(qsel_ctx *ctx, uint64_t seed);
+
 /* Replace theta (structure, partition and options are kept).  The next
  * qsel_diag_inv / qsel_trace_grads recompute everything.  QSEL_EINVAL for
  * non-finite values or rho outside (0, 1). */
@@ -357,6 +362,20 @@ qsel_status qsel_debug_get_lanczos(const qsel_ctx *ctx, double *alpha, double *b
 qsel_status qsel_debug_apply_precond(qsel_ctx *ctx, const double *R, double *Z, int32_t ld);
 
 /*
+ * Test hook for the bounded device-side waits of the tensor-core GEMM (the
+ * mixed form's tcgen05 products).  Nothing faults: with skip_loads non-zero
+ * the GEMM's producer issues no TMA load, so the waits of its other warps on
+ * the empty stages run out after wait_cycles clock cycles (0 = the default,
+ * about 2 s); every CTA then sets its error bit, waits (bounded) for the
+ * tensor-core work it issued, frees its tensor memory and returns, and the
+ * calling qsel_diag_inv reports QSEL_ETIMEOUT (its results are then
+ * meaningless; destroy the context).  wait_cycles alone shortens the limit of
+ * every wait.  Process-wide; qsel_debug_tc_wait(0, 0) restores normal
+ * operation.  Errors: QSEL_EINVAL for wait_cycles < 0.
+ */
+qsel_status qsel_debug_tc_wait(int32_t skip_loads, int64_t wait_cycles);
+
+/*
  * Allocation-free SPD inverse.  The paper has no counterpart: this entry point
  * exists for callers that cannot let a library call cudaMalloc -- code inside
  * a framework whose caching allocator owns the device memory budget (an
@@ -461,36 +480,49 @@ qsel_status qsel_cv_features(qsel_ctx *ctx, int32_t overlap, float *F_dev);
 qsel_status qsel_cv_targets(qsel_ctx *const *ctxs, int32_t count, float *y_dev);
 
 /*
- * Planner.  For every candidate overlap 1..max_overlap it predicts each part's
- * mean squared ratio m_p = mean over Omega_p of (c_i / v_i)^2, so that k
- * samples give the predicted error e_p(k) = sqrt(2 m_p / k).  It then picks
- * one sample count k (a multiple of 32 in [min_samples, max_samples]; the
- * samples are shared by every part) and per part the smallest overlap with
- * e_p(k) <= target, minimising the modelled time
+ * Planner.  The network predicts every node's ratio c_i / v_i at each time
+ * distance d = 1..16 to the nearest separator (16 = the feature's cap); for a
+ * part p extended by n_l slabs, m_p = mean over Omega_p of the predicted
+ * (c_i / v_i)^2 at the node's distance, so that k samples give the
+ * predicted error e_p(k) = sqrt(2 m_p / k) (a part without a separator is
+ * exact: e_p = 0).  For every candidate partition the planner picks one
+ * sample count k (a multiple of 32 in [min_samples, max_samples]; the
+ * samples are shared by every part) and per part the smallest overlap
+ * 1..max_overlap with e_p(k) <= target, minimising the modelled time
  *   cost_pcg * k * n + sum_p T_p (cost_dense * n_pad^3 + cost_corr * k * n_pad^2),
- * T_p = slabs of the extended part, n_pad = n_s rounded up to 64.  The
- * plan also reports the modelled cost of the exact one-part alternative.
- * Cost coefficients of 0 take GB300 mixed-precision defaults (seconds:
- * 1.53e-8, 1.10e-13, 2.2e-13).  When no k meets the target everywhere the
- * plan takes max_samples and max_overlap and sets feasible = 0.
+ * T_p = slabs of the extended part, n_pad = n_s rounded up to 64; it returns
+ * the cheapest candidate.  Candidates: the balanced partitions into each of
+ * part_counts (a count of 1 is the exact one-part form, cost cost_dense *
+ * n_t * n_pad^3, no samples: n_samples = 0), or, with n_part_counts = 0, the
+ * context's own partition.  The plan also reports the modelled cost of the
+ * exact one-part alternative.  Cost coefficients of 0 take GB300
+ * mixed-precision defaults (seconds: 1.53e-8, 1.10e-13, 2.2e-13).  When no
+ * candidate meets the target everywhere the plan takes the first candidate
+ * at max_samples and max_overlap and sets feasible = 0.
  */
 typedef struct {
   double target_rel_err;      /* RMS relative standard error per part, > 0      */
   int32_t max_overlap;        /* >= 1                                          */
   int32_t min_samples, max_samples; /* 32 <= min <= max <= 512                  */
   double cost_pcg, cost_dense, cost_corr;
+  const int32_t *part_counts; /* HOST, n_part_counts entries in 1..n_t, or NULL */
+  int32_t n_part_counts;      /* 0 = plan the context's own partition           */
 } qsel_cv_plan_options;
 
 typedef struct {
-  int32_t n_samples;          /* chosen k                                       */
+  int32_t n_samples;          /* chosen k (0 for the one-part form)             */
   int32_t feasible;           /* 1 if every part meets the target              */
   double predicted_cost;      /* modelled seconds                              */
   double predicted_err;       /* max over parts of the predicted error         */
   double single_part_cost;    /* modelled seconds of the exact alternative: one
                                  part (no separator, no samples), cost_dense *
                                  n_t * n_pad^3                                   */
-  int32_t *part_overlap;      /* caller-allocated HOST, n_parts: chosen n_l,p   */
-  double *part_pred_err;      /* caller-allocated HOST, n_parts, or NULL        */
+  int32_t *part_overlap;      /* caller-allocated HOST, room for the largest
+                                 candidate's part count: chosen n_l,p           */
+  double *part_pred_err;      /* caller-allocated HOST, same size, or NULL      */
+  int32_t n_parts;            /* part count of the chosen partition            */
+  int32_t *slab_start;        /* caller-allocated HOST (largest count + 1), or
+                                 NULL: offsets of the chosen partition          */
 } qsel_cv_plan_t;
 
 qsel_status qsel_cv_plan(qsel_ctx *ctx, const qsel_cv *cv, const qsel_cv_plan_options *opt, qsel_cv_plan_t *plan);

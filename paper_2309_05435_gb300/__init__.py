@@ -9,5 +9,6 @@ from .qsel import (QSEL_FP64, QSEL_MIXED, Batch, Context, ControlVariate, QselEr
                    qsel_error_estimate, qsel_debug_get_rhs, qsel_debug_get_samples,
                    qsel_debug_get_selinv_diag, qsel_debug_set_samples, qsel_destroy,
                    qsel_diag_inv, qsel_fixed_effects, qsel_last_error, qsel_loglik_grad, qsel_posterior_mean,
-                   qsel_set_covariates, qsel_set_data, qsel_set_theta, qsel_spd_inverse_noalloc, qsel_stats,
+                   qsel_set_covariates, qsel_set_data, qsel_set_seed, qsel_set_theta, qsel_spd_inverse_noalloc,
+                   qsel_stats,
                    qsel_trace_grads)

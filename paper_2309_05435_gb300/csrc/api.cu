@@ -117,6 +117,8 @@ struct qsel_ctx {
   double *d_part_sums = nullptr;       // n_parts doubles of per-part reductions
   float *d_bnd = nullptr, *d_sepd = nullptr;  // feature distances: n_s nodes, n_t slabs
   float *d_cv_F = nullptr, *d_cv_y = nullptr; // planner scratch, allocated on first use
+  double *d_cv_sums = nullptr;         // planner: per-slab sums (n_t)
+  int32_t *d_cv_slabs = nullptr;       // planner: slab offsets 0 .. n_t
   // theta in device memory (read by the model kernel) and its pinned host copy
   double *d_theta = nullptr, *h_theta = nullptr;
   // graph mode: the pipeline is captured into a CUDA graph with device-driven
@@ -1701,8 +1703,10 @@ static Err run_pipeline_body(qsel_ctx *c) {
   QSEL_CUDA_TRY(cudaGetLastError());
   int32_t err = 0;
   QSEL_CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
-  if (err & 1) return fail(QSEL_ENOTSPD, "a pivot of a dense block factorisation was not positive");
+  // a timed-out GEMM leaves its output unwritten, so later pivots are
+  // meaningless: the timeout is reported first
   if (err & 2) return fail(QSEL_ETIMEOUT, "a bounded device-side wait of the tensor-core GEMM gave up");
+  if (err & 1) return fail(QSEL_ENOTSPD, "a pivot of a dense block factorisation was not positive");
   if (err & 8)
     return fail(QSEL_ENOCONV, "the Lanczos tridiagonal matrix could not be diagonalised or was not positive definite");
   float ms;
@@ -1765,8 +1769,10 @@ static Err collect_graph(qsel_ctx *c) {
   c->stats = qsel_stats_t{};
   c->stats.pcg_iterations = loop[2];
   c->stats.pcg_max_rel_residual = rel;
-  if (err & 1) return fail(QSEL_ENOTSPD, "a pivot of a dense block factorisation was not positive");
+  // a timed-out GEMM leaves its output unwritten, so later pivots are
+  // meaningless: the timeout is reported first
   if (err & 2) return fail(QSEL_ETIMEOUT, "a bounded device-side wait of the tensor-core GEMM gave up");
+  if (err & 1) return fail(QSEL_ENOTSPD, "a pivot of a dense block factorisation was not positive");
   if (loop[3] == QSEL_ENOCONV)
     return fail(QSEL_ENOCONV, "the sampler did not reach pcg_tol within its iteration limits (max relative residual " +
                                   std::to_string(rel) + ")");
@@ -1941,6 +1947,15 @@ qsel_status qsel_set_theta(qsel_ctx *ctx, const qsel_theta *theta) {
       !std::isfinite(theta->logit_rho) || std::fabs(theta->logit_rho) > 36.0)
     return finish(ctx, fail(QSEL_EINVAL, "theta must be finite with |logit rho| <= 36"));
   ctx->theta = *theta;
+  ctx->computed = false;
+  ctx->injected = false;
+  ctx->have_rhs = false;
+  return QSEL_OK;
+}
+
+qsel_status qsel_set_seed(qsel_ctx *ctx, uint64_t seed) {
+  if (!ctx) return QSEL_EINVAL;
+  ctx->opt.seed = seed;
   ctx->computed = false;
   ctx->injected = false;
   ctx->have_rhs = false;
@@ -2269,21 +2284,31 @@ qsel_status qsel_error_estimate(qsel_ctx *ctx, double *part_err, double *global_
   return QSEL_OK;
 }
 
+// Time distance (capped at 16) from slab t of part [s0, s1) to the nearest
+// separator slab of the part extended by `overlap` slabs; 16 when it has none.
+static float sep_distance(int t, int s0, int s1, int overlap, int n_t) {
+  const int e0 = std::max(0, s0 - overlap), e1 = std::min(n_t, s1 + overlap);
+  float d = 16.f;
+  if (e0 > 0) d = std::min(d, (float)(t - (e0 - 1)));
+  if (e1 < n_t) d = std::min(d, (float)(e1 - t));
+  return d;
+}
+
+static Err cv_features_sepd(qsel_ctx *c, const std::vector<float> &sepd, float *F_dev);
+
 // Control-variate features of the current theta with every part extended by
 // `overlap` slabs (see qsel.h for the definition).
 static Err cv_features(qsel_ctx *c, int overlap, float *F_dev) {
   const int np = (int)c->parts.size();
   std::vector<float> sepd(c->n_t, 16.f);
-  for (int p = 0; p < np; ++p) {
-    const int s0 = c->slab_start[p], s1 = c->slab_start[p + 1];
-    const int e0 = std::max(0, s0 - overlap), e1 = std::min(c->n_t, s1 + overlap);
-    for (int t = s0; t < s1; ++t) {
-      float d = 16.f;
-      if (e0 > 0) d = std::min(d, (float)(t - (e0 - 1)));
-      if (e1 < c->n_t) d = std::min(d, (float)(e1 - t));
-      sepd[t] = d;
-    }
-  }
+  for (int p = 0; p < np; ++p)
+    for (int t = c->slab_start[p]; t < c->slab_start[p + 1]; ++t)
+      sepd[t] = sep_distance(t, c->slab_start[p], c->slab_start[p + 1], overlap, c->n_t);
+  return cv_features_sepd(c, sepd, F_dev);
+}
+
+// Features with the given separator distance of every slab.
+static Err cv_features_sepd(qsel_ctx *c, const std::vector<float> &sepd, float *F_dev) {
   TRY(run_model(c));
   QSEL_CUDA_TRY(cudaMemcpyAsync(c->d_sepd, sepd.data(), c->n_t * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   const double th[3] = {c->theta.log_kappa, c->theta.log_tau, c->theta.logit_rho};
@@ -2328,77 +2353,137 @@ qsel_status qsel_cv_plan(qsel_ctx *ctx, const qsel_cv *cv, const qsel_cv_plan_op
       o->min_samples > o->max_samples)
     return finish(ctx, fail(QSEL_EINVAL, "plan options: target > 0, max_overlap >= 1, 32 <= min <= max <= 512"));
   qsel_ctx *c = ctx;
-  const int np = (int)c->parts.size();
+  const int n_t = c->n_t;
+  if (o->n_part_counts < 0 || (o->n_part_counts > 0 && !o->part_counts))
+    return finish(c, fail(QSEL_EINVAL, "plan options: part_counts must hold n_part_counts entries"));
+  for (int q = 0; q < o->n_part_counts; ++q)
+    if (o->part_counts[q] < 1 || o->part_counts[q] > n_t)
+      return finish(c, fail(QSEL_EINVAL, "plan options: every part count must be in 1..n_t"));
   if (!c->d_cv_F) {
     Err e = c->alloc(&c->d_cv_F, (size_t)c->n * QSEL_CV_FEATURES);
     if (e.code == 0) e = c->alloc(&c->d_cv_y, (size_t)c->n);
+    if (e.code == 0) e = c->alloc(&c->d_cv_sums, (size_t)n_t);
+    if (e.code == 0) {
+      std::vector<int32_t> every(n_t + 1);
+      for (int t = 0; t <= n_t; ++t) every[t] = t;
+      e = upload(c, &c->d_cv_slabs, every);
+    }
     if (e.code) return finish(c, e);
   }
-  // m2[nl][p]: mean over Omega_p of the predicted (c_i / v_i)^2
-  std::vector<std::vector<double>> m2(o->max_overlap + 1, std::vector<double>(np, 0.0));
-  for (int nl = 1; nl <= o->max_overlap; ++nl) {
-    Err e = cv_features(c, nl, c->d_cv_F);
+  // S[d][t]: sum over the nodes of slab t of the predicted (c_i / v_i)^2 when
+  // the slab lies d slabs from the nearest separator (d = 1..16, the feature's
+  // cap).  Every plan below is a lookup in this table.
+  constexpr int kMaxD = 16;
+  std::vector<double> S((size_t)(kMaxD + 1) * n_t, 0.0);
+  for (int d = 1; d <= kMaxD; ++d) {
+    Err e = cv_features_sepd(c, std::vector<float>(n_t, (float)d), c->d_cv_F);
     if (e.code) return finish(c, e);
     qsel_status st = qsel_cv_predict(cv, c->d_cv_F, c->d_cv_y, c->n);
     if (st) return finish(c, fail(st, std::string("planner prediction: ") + qsel_last_error(nullptr)));
-    launch_cv_part_m2(c->stream, c->d_cv_y, c->d_slab_start, np, c->n_s, c->d_part_sums);
-    cudaError_t ce = cudaMemcpyAsync(m2[nl].data(), c->d_part_sums, np * sizeof(double), cudaMemcpyDeviceToHost,
-                                     c->stream);
+    launch_cv_part_m2(c->stream, c->d_cv_y, c->d_cv_slabs, n_t, c->n_s, c->d_cv_sums);
+    cudaError_t ce = cudaMemcpyAsync(S.data() + (size_t)d * n_t, c->d_cv_sums, n_t * sizeof(double),
+                                     cudaMemcpyDeviceToHost, c->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
     if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "planner reduction", __FILE__, __LINE__));
-    for (int p = 0; p < np; ++p) m2[nl][p] /= (double)(c->slab_start[p + 1] - c->slab_start[p]) * c->n_s;
   }
   const double cp = o->cost_pcg > 0 ? o->cost_pcg : 1.53e-8;
   const double cd = o->cost_dense > 0 ? o->cost_dense : 1.10e-13;
   const double cc = o->cost_corr > 0 ? o->cost_corr : 2.2e-13;
   const double npad = (double)c->n_pad;
-  auto slabs = [&](int p, int nl) {
-    return std::min(c->n_t, c->slab_start[p + 1] + nl) - std::max(0, c->slab_start[p] - nl);
+  const double single_cost = cd * (double)n_t * npad * npad * npad;
+  // candidate partitions: balanced ones of the requested part counts, or the
+  // context's own
+  std::vector<std::vector<int>> cands;
+  if (o->n_part_counts > 0) {
+    for (int q = 0; q < o->n_part_counts; ++q) {
+      const int np = o->part_counts[q];
+      std::vector<int> ss(np + 1, 0);
+      for (int p = 0; p < np; ++p) ss[p + 1] = ss[p] + n_t / np + (p < n_t % np ? 1 : 0);
+      cands.push_back(ss);
+    }
+  } else {
+    cands.push_back(c->slab_start);
+  }
+  struct Choice {
+    double cost = -1.0;
+    int k = 0;
+    std::vector<int> ss, nl;
+    std::vector<double> err;
   };
-  auto err = [&](int p, int nl, int k) { return std::sqrt(2.0 * m2[nl][p] / k); };
-  const int k_lo = round_up(o->min_samples, 32);
-  double best = -1.0;
-  std::vector<int> choice(np), best_choice(np);
-  int best_k = 0;
-  for (int k = k_lo; k <= o->max_samples; k += 32) {
-    double cost = cp * (double)k * c->n;
-    bool feasible = true;
-    for (int p = 0; p < np && feasible; ++p) {
-      int pick = -1;
-      for (int nl = 1; nl <= o->max_overlap; ++nl)
-        if (err(p, nl, k) <= o->target_rel_err) {
-          pick = nl;
-          break;
+  Choice best, fallback;
+  for (const auto &ss : cands) {
+    const int np = (int)ss.size() - 1;
+    if (np == 1) {   // exact one-part form: no separator, no samples
+      if (best.cost < 0 || single_cost < best.cost) {
+        best.cost = single_cost;
+        best.k = 0;
+        best.ss = ss;
+        best.nl.assign(1, 0);
+        best.err.assign(1, 0.0);
+      }
+      continue;
+    }
+    // m2[nl][p]: mean over Omega_p of the predicted squared ratio
+    std::vector<std::vector<double>> m2(o->max_overlap + 1, std::vector<double>(np, 0.0));
+    for (int nl = 1; nl <= o->max_overlap; ++nl)
+      for (int p = 0; p < np; ++p) {
+        const int s0 = ss[p], s1 = ss[p + 1];
+        if (std::max(0, s0 - nl) == 0 && std::min(n_t, s1 + nl) == n_t) continue;   // no separator: exact
+        double acc = 0.0;
+        for (int t = s0; t < s1; ++t) {
+          const int d = (int)sep_distance(t, s0, s1, nl, n_t);
+          acc += S[(size_t)d * n_t + t];
         }
-      if (pick < 0) feasible = false;
-      choice[p] = pick;
-      if (feasible) cost += slabs(p, pick) * (cd * npad * npad * npad + cc * k * npad * npad);
+        m2[nl][p] = acc / ((double)(s1 - s0) * c->n_s);
+      }
+    auto slabs = [&](int p, int nl) { return std::min(n_t, ss[p + 1] + nl) - std::max(0, ss[p] - nl); };
+    auto err = [&](int p, int nl, int k) { return std::sqrt(2.0 * m2[nl][p] / k); };
+    for (int k = round_up(o->min_samples, 32); k <= o->max_samples; k += 32) {
+      double cost = cp * (double)k * c->n;
+      std::vector<int> pick(np, -1);
+      bool feasible = true;
+      for (int p = 0; p < np && feasible; ++p) {
+        for (int nl = 1; nl <= o->max_overlap && pick[p] < 0; ++nl)
+          if (err(p, nl, k) <= o->target_rel_err) pick[p] = nl;
+        feasible = pick[p] > 0;
+        if (feasible) cost += slabs(p, pick[p]) * (cd * npad * npad * npad + cc * k * npad * npad);
+      }
+      if (feasible && (best.cost < 0 || cost < best.cost)) {
+        best.cost = cost;
+        best.k = k;
+        best.ss = ss;
+        best.nl = pick;
+        best.err.resize(np);
+        for (int p = 0; p < np; ++p) best.err[p] = err(p, pick[p], k);
+      }
     }
-    if (feasible && (best < 0 || cost < best)) {
-      best = cost;
-      best_choice = choice;
-      best_k = k;
+    if (fallback.cost < 0) {   // best effort at the limits, first candidate
+      fallback.k = o->max_samples;
+      fallback.cost = cp * (double)fallback.k * c->n;
+      fallback.ss = ss;
+      fallback.nl.assign(np, o->max_overlap);
+      fallback.err.resize(np);
+      for (int p = 0; p < np; ++p) {
+        fallback.cost += slabs(p, o->max_overlap) * (cd * npad * npad * npad + cc * fallback.k * npad * npad);
+        fallback.err[p] = err(p, o->max_overlap, fallback.k);
+      }
     }
   }
-  plan->feasible = best >= 0 ? 1 : 0;
-  if (best < 0) {
-    best_k = o->max_samples;
-    best = cp * (double)best_k * c->n;
-    for (int p = 0; p < np; ++p) {
-      best_choice[p] = o->max_overlap;
-      best += slabs(p, o->max_overlap) * (cd * npad * npad * npad + cc * best_k * npad * npad);
-    }
-  }
-  plan->n_samples = best_k;
-  plan->predicted_cost = best;
-  plan->single_part_cost = cd * (double)c->n_t * npad * npad * npad;
+  plan->feasible = best.cost >= 0 ? 1 : 0;
+  const Choice &ch = best.cost >= 0 ? best : fallback;
+  const int np = (int)ch.ss.size() - 1;
+  plan->n_samples = ch.k;
+  plan->predicted_cost = ch.cost;
+  plan->single_part_cost = single_cost;
+  plan->n_parts = np;
   plan->predicted_err = 0.0;
   for (int p = 0; p < np; ++p) {
-    plan->part_overlap[p] = best_choice[p];
-    const double e = err(p, best_choice[p], best_k);
-    if (plan->part_pred_err) plan->part_pred_err[p] = e;
-    plan->predicted_err = std::max(plan->predicted_err, e);
+    plan->part_overlap[p] = ch.nl[p];
+    if (plan->part_pred_err) plan->part_pred_err[p] = ch.err[p];
+    plan->predicted_err = std::max(plan->predicted_err, ch.err[p]);
   }
+  if (plan->slab_start)
+    for (int p = 0; p <= np; ++p) plan->slab_start[p] = ch.ss[p];
   return QSEL_OK;
 }
 

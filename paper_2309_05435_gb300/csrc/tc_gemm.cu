@@ -9,20 +9,23 @@
 // One CTA computes a 128 x 128 tile of C:
 //   warp 0      one thread issues the TMA loads of 128 x 32 FP32 tiles of A and
 //               B (128-byte rows, 128B swizzle) into a 3-stage ring;
-//   warps 2-5   split every loaded tile into TF32 hi (low 13 mantissa bits
-//               cleared) and lo = x - hi parts in shared memory, then run the
+//   warps 2-5   split every loaded tile into TF32 hi = rn(x) and lo =
+//               rn(x - hi) parts (rn = round to nearest TF32, so hi + lo
+//               holds x to about 2^-23) in shared memory, then run the
 //               epilogue (tcgen05.ld of the accumulator, alpha/beta, store);
 //   warp 1      owns the 128-column TMEM accumulator; one thread issues
 //               tcgen05.mma.kind::tf32 (M=128, N=128, K=8) for hi*hi, hi*lo and
 //               lo*hi ("3xTF32", FP32-level accuracy with FP32 accumulation) or
 //               for the raw values only (1 pass).
-// Every wait is bounded: after ~2 s the CTA raises bit 1 of *err, stops
-// issuing work, waits (bounded) for what it already issued, frees TMEM and
-// returns.
+// Every wait is bounded: after ~2 s (or the limit set by the test hook
+// qsel_debug_tc_wait) the CTA raises bit 1 of *err, stops issuing work, waits
+// (bounded) for what it already issued, frees TMEM and returns.
 #include <cuda.h>
 
+#include <atomic>
 #include <mutex>
 
+#include "qsel.h"
 #include "kernels.cuh"
 
 namespace qsel {
@@ -57,6 +60,8 @@ struct Params {
   float alpha[kMaxBatch], beta[kMaxBatch];
   int M, N, K, ldc, lower, passes;
   int32_t *err;
+  long long wait_cycles;   // limit of every wait on a stage or the accumulator
+  int skip_loads;          // test hook: the producer issues no TMA load
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -76,7 +81,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 }
 
 // Bounded wait for the completion of the phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, int32_t *err) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, int32_t *err,
+                                          long long limit) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
@@ -89,7 +95,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
         : "memory");
     if (done) return true;
     if (*abort) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       atomicOr(err, 2);
       *abort = 1;
       return false;
@@ -156,6 +162,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// x rounded to the nearest TF32 value (10 explicit mantissa bits; the low 13
+// bits of the result are zero).
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 __device__ __forceinline__ void named_sync_converters() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 template <int STAGES, int BN>
@@ -208,9 +222,9 @@ __global__ void __launch_bounds__(192) k_tc_gemm(const __grid_constant__ Params 
       const CUtensorMap *tma = &p.tmA[z];
       const CUtensorMap *tmb = &p.tmB[z];
       int issued = 0;
-      for (int kb = 0; kb < nk; ++kb) {
+      for (int kb = 0; kb < nk && !p.skip_loads; ++kb) {
         const int s = kb % STAGES, u = kb / STAGES;
-        if (!mbar_wait(empty_bar(s), (u & 1) ^ 1, abort, p.err)) break;
+        if (!mbar_wait(empty_bar(s), (u & 1) ^ 1, abort, p.err, p.wait_cycles)) break;
         uint8_t *st = base + s * STAGE_BYTES;
         mbar_expect_tx(full_bar(s), TILE_A + TILE_B);
         tma_load_2d(smem_u32(st), tma, kb * BK, bm * BM, full_bar(s));
@@ -237,7 +251,7 @@ __global__ void __launch_bounds__(192) k_tc_gemm(const __grid_constant__ Params 
     if (lane == 0) {
       for (int kb = 0; kb < nk; ++kb) {
         const int s = kb % STAGES, u = kb / STAGES;
-        if (!mbar_wait(conv_bar(s), u & 1, abort, p.err)) break;
+        if (!mbar_wait(conv_bar(s), u & 1, abort, p.err, p.wait_cycles)) break;
         tc_fence_after();
         const uint32_t st = smem_u32(base + s * STAGE_BYTES);
         const uint32_t a_hi = st, b_hi = st + TILE_A, a_lo = st + TILE_A + TILE_B, b_lo = a_lo + TILE_A;
@@ -260,7 +274,7 @@ __global__ void __launch_bounds__(192) k_tc_gemm(const __grid_constant__ Params 
     const int ct = threadIdx.x - 64;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES, u = kb / STAGES;
-      if (ct == 0) *conv_ok = (mbar_wait(full_bar(s), u & 1, abort, p.err) && !*abort) ? 1 : 0;
+      if (ct == 0) *conv_ok = (mbar_wait(full_bar(s), u & 1, abort, p.err, p.wait_cycles) && !*abort) ? 1 : 0;
       named_sync_converters();
       if (!*conv_ok) break;
       if (p.passes == 3) {
@@ -270,12 +284,12 @@ __global__ void __launch_bounds__(192) k_tc_gemm(const __grid_constant__ Params 
         for (int i = ct; i < (TILE_A + TILE_B) / 16; i += 128) {
           float4 v = raw[i];
           float4 h;
-          h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-          h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-          h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-          h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+          h.x = tf32_rn(v.x);
+          h.y = tf32_rn(v.y);
+          h.z = tf32_rn(v.z);
+          h.w = tf32_rn(v.w);
           raw[i] = h;
-          lo[i] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+          lo[i] = make_float4(tf32_rn(v.x - h.x), tf32_rn(v.y - h.y), tf32_rn(v.z - h.z), tf32_rn(v.w - h.w));
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -283,7 +297,7 @@ __global__ void __launch_bounds__(192) k_tc_gemm(const __grid_constant__ Params 
       if (ct == 0) mbar_arrive(conv_bar(s));
     }
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 = rows of the tile
-    if (ct == 0) *conv_ok = (mbar_wait(accum_bar, 0, abort, p.err) && !*abort) ? 1 : 0;
+    if (ct == 0) *conv_ok = (mbar_wait(accum_bar, 0, abort, p.err, p.wait_cycles) && !*abort) ? 1 : 0;
     named_sync_converters();
     if (*conv_ok) {  // uniform across the four warps: tcgen05.ld is warp-collective
       tc_fence_after();
@@ -355,6 +369,9 @@ using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, vo
 std::mutex g_mu;
 EncodeFn g_encode = nullptr;
 int g_state = 0;  // 0 unknown, 1 available, -1 unavailable
+// test hook (qsel_debug_tc_wait): skip the loads and / or shorten the waits
+std::atomic<int> g_skip_loads{0};
+std::atomic<long long> g_wait_cycles{0};
 
 bool encode_2d(CUtensorMap *tm, const float *ptr, int rows, int cols, int ld, int box_rows) {
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
@@ -428,6 +445,9 @@ bool launch_tc_gemm(cudaStream_t s, const GemmBatch<float> &b, int M, int N, int
   p.lower = lower ? 1 : 0;
   p.passes = passes;
   p.err = err;
+  const long long wc = tc::g_wait_cycles.load();
+  p.wait_cycles = wc > 0 ? wc : tc::kWaitCycles;
+  p.skip_loads = tc::g_skip_loads.load();
   ++g_launch_count;
   Profiler::Rec rec{PROF_GEMM, nullptr, nullptr, 0.0};
   const int bn_w = narrow ? 64 : 128;
@@ -449,3 +469,10 @@ bool launch_tc_gemm(cudaStream_t s, const GemmBatch<float> &b, int M, int N, int
 }
 
 }  // namespace qsel
+
+extern "C" qsel_status qsel_debug_tc_wait(int32_t skip_loads, int64_t wait_cycles) {
+  if (wait_cycles < 0) return QSEL_EINVAL;
+  qsel::tc::g_skip_loads.store(skip_loads ? 1 : 0);
+  qsel::tc::g_wait_cycles.store((long long)wait_cycles);
+  return QSEL_OK;
+}

@@ -57,13 +57,13 @@ class qsel_batch_info_t(ctypes.Structure):
 class qsel_cv_plan_options(ctypes.Structure):
     _fields_ = [("target_rel_err", c_double), ("max_overlap", c_int32), ("min_samples", c_int32),
                 ("max_samples", c_int32), ("cost_pcg", c_double), ("cost_dense", c_double),
-                ("cost_corr", c_double)]
+                ("cost_corr", c_double), ("part_counts", POINTER(c_int32)), ("n_part_counts", c_int32)]
 
 
 class qsel_cv_plan_t(ctypes.Structure):
     _fields_ = [("n_samples", c_int32), ("feasible", c_int32), ("predicted_cost", c_double),
                 ("predicted_err", c_double), ("single_part_cost", c_double), ("part_overlap", POINTER(c_int32)),
-                ("part_pred_err", POINTER(c_double))]
+                ("part_pred_err", POINTER(c_double)), ("n_parts", c_int32), ("slab_start", POINTER(c_int32))]
 
 
 class qsel_stats_t(ctypes.Structure):
@@ -88,12 +88,12 @@ def _fields(s) -> dict:
     return out
 
 
-EXPORTED = ["qsel_create", "qsel_set_theta", "qsel_diag_inv", "qsel_trace_grads", "qsel_stats",
+EXPORTED = ["qsel_create", "qsel_set_seed", "qsel_set_theta", "qsel_diag_inv", "qsel_trace_grads", "qsel_stats",
             "qsel_set_data", "qsel_posterior_mean", "qsel_loglik_grad", "qsel_set_covariates",
             "qsel_fixed_effects",
             "qsel_debug_set_samples", "qsel_debug_get_samples", "qsel_debug_get_rhs",
             "qsel_debug_get_selinv_diag", "qsel_debug_get_lanczos", "qsel_debug_apply_precond",
-            "qsel_spd_inverse_noalloc",
+            "qsel_spd_inverse_noalloc", "qsel_debug_tc_wait",
             "qsel_error_estimate",
             "qsel_cv_create", "qsel_cv_set_params", "qsel_cv_get_params", "qsel_cv_predict", "qsel_cv_grad",
             "qsel_cv_train", "qsel_cv_features", "qsel_cv_targets", "qsel_cv_plan",
@@ -120,6 +120,7 @@ def load_library(path: str = LIB_PATH):
     lib.qsel_create.argtypes = [P(c_void_p), P(qsel_model), P(qsel_theta), P(qsel_partition), c_int32,
                                 P(qsel_options)]
     lib.qsel_set_theta.argtypes = [c_void_p, P(qsel_theta)]
+    lib.qsel_set_seed.argtypes = [c_void_p, c_uint64]
     lib.qsel_diag_inv.argtypes = [c_void_p, c_void_p, c_int32]
     lib.qsel_trace_grads.argtypes = [c_void_p, P(c_double)]
     lib.qsel_set_data.argtypes = [c_void_p, P(c_double)]
@@ -135,6 +136,7 @@ def load_library(path: str = LIB_PATH):
     lib.qsel_debug_get_lanczos.argtypes = [c_void_p, P(c_double), P(c_double), c_int32]
     lib.qsel_debug_apply_precond.argtypes = [c_void_p, P(c_double), P(c_double), c_int32]
     lib.qsel_spd_inverse_noalloc.argtypes = [c_void_p, c_int32, c_int32, c_void_p]
+    lib.qsel_debug_tc_wait.argtypes = [c_int32, c_int64]
     lib.qsel_error_estimate.argtypes = [c_void_p, P(c_double), P(c_double)]
     lib.qsel_cv_create.argtypes = [P(c_void_p), c_uint64, c_void_p]
     lib.qsel_cv_set_params.argtypes = [c_void_p, P(c_float)]
@@ -300,6 +302,11 @@ def qsel_loglik_grad(ctx: Context, with_terms=False):
     return g
 
 
+def qsel_set_seed(ctx: Context, seed: int):
+    """New Philox key: the next run draws new samples."""
+    _check(load_library().qsel_set_seed(ctx.handle, int(seed)), ctx.handle)
+
+
 def qsel_set_theta(ctx: Context, theta):
     th = qsel_theta(*[float(x) for x in theta])
     _check(load_library().qsel_set_theta(ctx.handle, ctypes.byref(th)), ctx.handle)
@@ -389,6 +396,12 @@ def qsel_spd_inverse_noalloc(a, n: int, lda: int | None = None, cuda_stream=None
     _check(st, None)
 
 
+def qsel_debug_tc_wait(skip_loads: bool, wait_cycles: int = 0):
+    """Test hook of the tensor-core GEMM's bounded waits (see qsel.h);
+    qsel_debug_tc_wait(False, 0) restores normal operation."""
+    _check(load_library().qsel_debug_tc_wait(1 if skip_loads else 0, int(wait_cycles)), None)
+
+
 def qsel_error_estimate(ctx: Context):
     """(per-part RMS relative standard error, global one) of the last
     diag(Q^-1) estimate, from the sample moments of w^2."""
@@ -468,16 +481,24 @@ def qsel_cv_targets(ctxs, y_dev):
 
 def qsel_cv_plan(ctx: Context, cv: ControlVariate, target_rel_err: float, max_overlap: int = 4,
                  min_samples: int = 32, max_samples: int = 512, cost_pcg: float = 0.0, cost_dense: float = 0.0,
-                 cost_corr: float = 0.0) -> dict:
+                 cost_corr: float = 0.0, part_counts=None) -> dict:
+    """Plan (k, per-part overlaps) for the context's partition, or, with
+    part_counts, also choose among balanced partitions (1 = exact one part)."""
+    pc = None if not part_counts else np.ascontiguousarray(part_counts, dtype=np.int32)
     o = qsel_cv_plan_options(float(target_rel_err), int(max_overlap), int(min_samples), int(max_samples),
-                             float(cost_pcg), float(cost_dense), float(cost_corr))
-    po = np.zeros(ctx.n_parts, dtype=np.int32)
-    pe = np.zeros(ctx.n_parts, dtype=np.float64)
-    plan = qsel_cv_plan_t(0, 0, 0.0, 0.0, 0.0, _ptr(po, c_int32), _ptr(pe, c_double))
+                             float(cost_pcg), float(cost_dense), float(cost_corr),
+                             _ptr(pc, c_int32) if pc is not None else None, 0 if pc is None else len(pc))
+    room = max(ctx.n_parts, int(pc.max()) if pc is not None else 0)
+    po = np.zeros(room, dtype=np.int32)
+    pe = np.zeros(room, dtype=np.float64)
+    ss = np.zeros(room + 1, dtype=np.int32)
+    plan = qsel_cv_plan_t(0, 0, 0.0, 0.0, 0.0, _ptr(po, c_int32), _ptr(pe, c_double), 0, _ptr(ss, c_int32))
     _check(load_library().qsel_cv_plan(ctx.handle, cv.handle, ctypes.byref(o), ctypes.byref(plan)), ctx.handle)
+    npart = plan.n_parts
     return {"n_samples": plan.n_samples, "feasible": bool(plan.feasible), "predicted_cost": plan.predicted_cost,
             "predicted_err": plan.predicted_err, "single_part_cost": plan.single_part_cost,
-            "part_overlap": po, "part_pred_err": pe}
+            "n_parts": npart, "slab_start": ss[:npart + 1].copy(),
+            "part_overlap": po[:npart].copy(), "part_pred_err": pe[:npart].copy()}
 
 
 class Batch:

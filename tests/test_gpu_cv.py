@@ -204,6 +204,25 @@ def test_planner_with_constant_prediction(q):
     assert plan["n_samples"] == 128
 
 
+def test_planner_chooses_part_count(q):
+    """With candidate part counts the planner also picks the partition: under
+    a constant prediction every partition needs the same k, so the one with
+    the fewest factorised slabs wins (two parts of five slabs, overlap 1:
+    12 slabs, against 16 for four parts); with 1 among the candidates the
+    exact one-part form (n_t slabs, no samples, error 0) is cheaper still."""
+    c = Case(q, "uneven4")                                   # n_t = 10, four parts
+    cv = _constant_network(q, 0.05)
+    plan = q.qsel_cv_plan(c.ctx, cv, 0.01, max_overlap=3, part_counts=[4, 2])
+    assert plan["feasible"] and plan["n_parts"] == 2 and list(plan["slab_start"]) == [0, 5, 10]
+    assert plan["n_samples"] == 64 and list(plan["part_overlap"]) == [1, 1]
+    plan = q.qsel_cv_plan(c.ctx, cv, 0.01, max_overlap=3, part_counts=[4, 2, 1])
+    assert plan["n_parts"] == 1 and plan["n_samples"] == 0 and plan["predicted_err"] == 0.0
+    assert plan["predicted_cost"] == pytest.approx(plan["single_part_cost"])
+    # without candidates: the context's own four parts, as before
+    plan = q.qsel_cv_plan(c.ctx, cv, 0.01, max_overlap=3)
+    assert plan["n_parts"] == 4 and list(plan["slab_start"]) == [0, 3, 6, 8, 10]
+
+
 def test_cv_gain_over_plain_rbmc(q):
     """What the trained network gains.  Train on GPU-produced targets of small
     models (16 x 16 grid, 24 slabs, 3 parts, overlaps 1-3, 12 theta), then on
