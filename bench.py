@@ -2,18 +2,23 @@
 """Benchmark: time to diag(Q^-1) + tr(Q^-1 dQ/dtheta_j) at 1 % relative error
 on one GB300.
 
+Workload (default): 96 x 96 grid (n_s = 9216), n_t = 256 (n = 2,359,296),
+kappa = 0.1, rho = 0.98, 10 % observed, PCG to 1e-10 -- synthetic, seeded.
+
 The chosen form is mixed precision with the learned control variate: a
 network trained first on the GPU (reported separately, not timed) predicts
-every node's correction share, the planner picks one sample count and an
-overlap per part for a 1 % RMS relative standard error, and RBMC runs at
-those settings.  One step = one pass through the C ABI on a resident
-context: qsel_cv_plan (features + network + plan), qsel_set_theta,
-qsel_diag_inv (perturbation RHS, multi-RHS PCG, per-subdomain block
-factorisation + Takahashi, RB correction), qsel_trace_grads and
-qsel_error_estimate.  Workload: 64 x 64 grid (n_s = 4096), n_t = 64
-(n = 262,144), kappa = 0.2, rho = 0.95, 25 % observed, 8 time subdomains,
-PCG to 1e-10 -- synthetic, seeded.  Plain FP64 RBMC at the workload's fixed
-settings (overlap 2, 256 samples) is timed beside it.
+every node's correction share, the planner picks the part count, one sample
+count and an overlap per part for a 1 % RMS relative standard error, and
+RBMC runs at those settings.  One step = one pass through the C ABI on a
+resident context with a new seed: qsel_cv_plan (features + network + plan),
+qsel_set_seed, qsel_set_theta, qsel_diag_inv (perturbation RHS, multi-RHS
+PCG, per-subdomain block factorisation + Takahashi, RB correction),
+qsel_trace_grads and qsel_error_estimate.  Reported beside it: the accuracy
+over the W + K seeds against the exact one-part result, the exact one-part
+form itself (timed), plain FP64 RBMC's time to 1 % (errors measured, FP64
+time extrapolated per slab), the class breakdown of a profiled pass, the
+end-to-end call from host buffers, the CPU oracle on a bounded sample, and
+a second workload (64 x 64 grid, n_t = 64).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
   python bench.py --cv-eval      # held-out evaluation of the control variate
@@ -62,27 +67,23 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", default="grid64_nt64")
+    ap.add_argument("--workload", default="grid96_nt256")
+    ap.add_argument("--secondary", default="grid64_nt64",
+                    help="second workload timed after the bench line's (chosen and exact forms); '' = none")
+    ap.add_argument("--plain-seeds", type=int, default=1,
+                    help="seeds per overlap of the plain-FP64 time-to-target procedure (0 = skip it)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
-                    help="form timed for `value` (mixed = the chosen form)")
-    ap.add_argument("--fp64-steps", type=int, default=1,
-                    help="passes of plain FP64 timed beside the chosen form (0 = skip)")
     ap.add_argument("--sweep", default=None,
                     help="time-to-accuracy sweep instead of the bench line: comma list of "
                          "form:n_parts:overlap:n_samples entries, form in {mixed, fp64}")
     ap.add_argument("--seeds", type=int, default=1, help="RBMC seeds per sweep entry")
-    ap.add_argument("--form", choices=["planned", "fixed"], default="planned",
-                    help="planned = control-variate planner picks k and overlaps; fixed = workload settings")
     ap.add_argument("--target", type=float, default=0.01, help="RMS relative error target of the plan")
     ap.add_argument("--max-overlap", type=int, default=8)
     ap.add_argument("--preconditioner", choices=["kron", "bj"], default="kron",
                     help="PCG preconditioner of the chosen form: Kronecker grid (kron) or 64-row block Jacobi "
                          "(bj); plain FP64 always uses block Jacobi, the paper's choice")
-    ap.add_argument("--cost-pcg", type=float, default=None,
-                    help="planner's PCG cost per sample and node in seconds (default: by preconditioner)")
     ap.add_argument("--margin", type=float, default=0.85,
                     help="the planner aims at margin * target (absorbs the prediction error)")
     ap.add_argument("--cv-train-thetas", type=int, default=32)
@@ -103,9 +104,6 @@ def parse_args():
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--hyper-eval", action="store_true",
                     help="time the posterior mean and the hyperparameter gradient (mixed and FP64)")
-    ap.add_argument("--profile-timed", action="store_true",
-                    help="bracket the timed steps of the chosen form with cudaProfilerStart/Stop "
-                         "(for ncu --profile-from-start off)")
     ap.add_argument("--lanczos-eval", default=None,
                     help="comma list of Krylov dimensions: the Lanczos sampler against PCG at the workload")
     return ap.parse_args()
@@ -295,6 +293,249 @@ def oracle_sample_single_thread(w):
 # ----------------------------------------------------------------------------
 # native arm
 # ----------------------------------------------------------------------------
+RBMC_PART_COUNTS = (2, 4, 8, 16)
+PLAN_MAX_OVERLAP = 16        # the network's time-distance feature is capped at 16 slabs
+
+
+def _errs(v, g, v_ex, t_ex):
+    r = (v - v_ex) / v_ex
+    return {"eps_diag_rms": float(np.sqrt(np.mean(r ** 2))), "eps_diag_p99": float(np.quantile(np.abs(r), 0.99)),
+            "eps_diag_max": float(np.max(np.abs(r))),
+            "eps_traces": [float(abs(a - b) / abs(b)) for a, b in zip(g, t_ex)]}
+
+
+def _seed_errors(vs, gs, v_ex, t_ex):
+    """Error definitions of the metric over R seeds: eps_diag = RMS over seeds
+    and nodes of the relative error, eps_j = RMS over seeds per trace, and
+    the 99th percentile over nodes of the per-node RMS."""
+    rd = np.array([((v - v_ex) / v_ex) ** 2 for v in vs])
+    rt = np.array([[((a - b) / b) ** 2 for a, b in zip(g, t_ex)] for g in gs])
+    eps_d = float(np.sqrt(rd.mean()))
+    eps_t = [float(np.sqrt(rt[:, j].mean())) for j in range(rt.shape[1])]
+    return {"eps_diag": eps_d, "eps_diag_p99": float(np.quantile(np.sqrt(rd.mean(axis=0)), 0.99)),
+            "eps_traces": eps_t, "seeds": len(vs), "meets_1pct": bool(max(eps_d, *eps_t) <= 0.01)}
+
+
+def _subdomain_slabs(n_t, slab_start, overlaps):
+    """(forward slabs, backward slabs) of the block factorisation and the
+    Takahashi recursion over every extended part."""
+    fwd = bwd = 0
+    for p in range(len(slab_start) - 1):
+        e0 = max(0, slab_start[p] - overlaps[p])
+        e1 = min(n_t, slab_start[p + 1] + overlaps[p])
+        lo = slab_start[p] - e0
+        fwd += e1 - e0
+        bwd += (e1 - e0) - 1 - max(lo - 1, 0)
+    return fwd, bwd
+
+
+class Native:
+    """The library's contexts for one workload (inputs resident in HBM)."""
+
+    def __init__(self, q, w, stream, dev):
+        self.q, self.w, self.stream, self.dev = q, w, stream, dev
+        self.mesh, self.mask = workload_inputs(w)
+
+    def ctx(self, precision, n_parts=None, slab_start=None, overlap=None, k=None, part_overlap=None, seed=1000,
+            preconditioner=None, profile=0, mesh_mask=None, n_t=None):
+        q, w = self.q, self.w
+        mesh, mask = (self.mesh, self.mask) if mesh_mask is None else mesh_mask
+        pc = preconditioner if preconditioner is not None else (
+            q.QSEL_PRECOND_KRON if precision == q.QSEL_MIXED else q.QSEL_PRECOND_BLOCK_JACOBI)
+        return q.qsel_create(w.n_s, n_t or w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask,
+                             w.sigma, w.theta, n_parts=n_parts or w.n_parts, slab_start=slab_start,
+                             overlap=w.overlap if overlap is None else overlap,
+                             n_samples=k or w.n_samples, seed=seed, precision=precision, pcg_tol=w.pcg_tol,
+                             cuda_stream=self.stream.cuda_stream, profile_kernels=profile,
+                             part_overlap=part_overlap, preconditioner=pc)
+
+    def exact(self, precision):
+        """One pass of the exact one-part form: (s, diag, traces, stats)."""
+        import torch
+        c = self.ctx(precision, n_parts=1, overlap=0, k=2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        v = self.q.qsel_diag_inv(c)
+        g = self.q.qsel_trace_grads(c)
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        st = self.q.qsel_stats(c)
+        c.close()
+        return e0.elapsed_time(e1) / 1e3, v, np.asarray(g), st
+
+
+def measure_chosen(args, nat, net, world, dist, rank, clocks=True):
+    """Plan (part count, per-part overlaps, k) with the network, then time the
+    chosen RBMC form: W untimed and K timed steps, each one full pass with a
+    new seed (plan + set seed + set theta + diag + traces + error estimate).
+    Returns the measurements and the per-step estimates (for the accuracy
+    over seeds)."""
+    import torch
+    q, w, stream = nat.q, nat.w, nat.stream
+    counts = [p for p in RBMC_PART_COUNTS if p <= w.n_t]
+
+    def plan_on(ctx, with_exact=False):
+        return q.qsel_cv_plan(ctx, net, args.margin * args.target, max_overlap=PLAN_MAX_OVERLAP,
+                              cost_pcg=KRON_PCG_COST, part_counts=([1] if with_exact else []) + counts)
+
+    probe = nat.ctx(q.QSEL_MIXED, k=32)
+    plan = plan_on(probe)
+    recommendation = plan_on(probe, with_exact=True)
+    probe.close()
+    ss = [int(x) for x in plan["slab_start"]]
+    po = [int(x) for x in plan["part_overlap"]]
+    k_run = int(plan["n_samples"])
+    ctx = nat.ctx(q.QSEL_MIXED, n_parts=plan["n_parts"], slab_start=ss, overlap=min(po), k=k_run,
+                  part_overlap=po)
+    outs = [torch.empty(w.n, dtype=torch.float64, device=nat.dev) for _ in range(args.warmup + args.steps)]
+    grads, errs = [], []
+
+    def step(i):
+        p = plan_on(ctx)
+        if [int(x) for x in p["slab_start"]] != ss or [int(x) for x in p["part_overlap"]] != po \
+                or p["n_samples"] != k_run:
+            raise RuntimeError("the plan changed between steps at fixed theta")
+        q.qsel_set_seed(ctx, 5000 + 97 * rank + i)
+        q.qsel_set_theta(ctx, w.theta)
+        q.qsel_diag_inv(ctx, outs[i])
+        grads.append(np.asarray(q.qsel_trace_grads(ctx)))
+        errs.append(q.qsel_error_estimate(ctx)[1])
+        return q.qsel_stats(ctx)
+
+    for i in range(args.warmup):
+        step(i)
+    sampler = ClockSampler(int(str(nat.dev).split(":")[-1])) if clocks else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = [step(args.warmup + i) for i in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = sampler.stop() if sampler else None
+    ms_total = job_time_ms(e0.elapsed_time(e1), world, dist if world > 1 else None, nat.dev)
+    vs = [o.cpu().numpy() for o in outs]
+    ctx.close()
+    # the planner launches 5 kernels per separator distance (time coefficients,
+    # Q_s values, features, network, per-slab reduction), 16 distances
+    launches = int(sum(s["kernel_launches"] for s in stats)) + 80 * args.steps
+    return {"plan": plan, "recommendation": recommendation, "slab_start": ss, "part_overlap": po, "k": k_run,
+            "ms_total": ms_total, "stats": stats, "clocks": clk, "diags": vs, "grads": grads,
+            "err_estimates": errs, "launches": launches}
+
+
+def profile_pass(nat, ch):
+    """One pass of the chosen form with per-launch event timing (class
+    breakdown for the roofline), on a context of its own."""
+    q = nat.q
+    c = nat.ctx(q.QSEL_MIXED, n_parts=len(ch["slab_start"]) - 1, slab_start=ch["slab_start"],
+                overlap=min(ch["part_overlap"]), k=ch["k"], part_overlap=ch["part_overlap"], profile=1)
+    q.qsel_set_seed(c, 4242)
+    q.qsel_diag_inv(c)
+    q.qsel_trace_grads(c)
+    st = q.qsel_stats(c)
+    c.close()
+    return st
+
+
+def roofline_of(st, w, hbm_peak, hbm_src, tf32_peak, tf32_src):
+    """Dominant kernel class of one profiled pass (event time), with its
+    algorithmic work per launch over its average event-timed launch."""
+    from paper_2309_05435_gb300 import qsel as q
+    classes = q.PROF_CLASSES
+    cms, cwork, cl = st["class_ms"], st["class_work"], st["class_launches"]
+    desc = {"gemm": "k_tc_gemm<3,128> (Takahashi and correction products, tcgen05 3xTF32, TMA, TMEM)",
+            "sweep_update": "k_tc_gemm<3,128> rank-256 sweep panel updates (tcgen05 3xTF32)",
+            "spmm": "k_bt_spmm (block-tridiagonal sliced-ELL SpMM, PCG)",
+            "pivot": "k_bsweep_pivot (64x64 double-float pivot-tile inverses)",
+            "precond": "k_kron_pass x6 (Kronecker grid preconditioner)"}
+    cand = [i for i, nm in enumerate(classes) if nm in desc and cwork[i] > 0 and cms[i] > 0]
+    dom = max(cand, key=lambda i: cms[i])
+    name = classes[dom]
+    if name == "spmm":
+        ach = cwork[dom] / (cms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "peak_source": hbm_src}
+    elif name in ("gemm", "sweep_update"):
+        ach = 3.0 * cwork[dom] / (cms[dom] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
+                "peak_source": tf32_src + "; achieved counts the three TF32 products of each 3xTF32 product"}
+    elif name == "pivot":
+        ach = cwork[dom] / (cms[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS / 15.0, "unit": "TFLOP/s",
+                "peak_source": "FP32 CUDA-core rate from unit counts / 15 FP32 operations per double-float "
+                               "multiply-subtract"}
+    else:
+        ach = cwork[dom] / (cms[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "FP32 CUDA-core rate from unit counts (152 x 128 x 2 x 2.07 GHz)"}
+    return {"kernel": desc[name], "class": name, **roof, "frac": roof["achieved"] / roof["peak"],
+            "traffic": None, "launches": int(cl[dom]), "avg_launch_ms": cms[dom] / max(1, cl[dom]),
+            "timing": "per-launch CUDA events on the launching streams in a separate profiled pass of the "
+                      "chosen form (the timed steps run without per-launch events)",
+            "kernel_classes_ms_per_pass": {classes[i]: cms[i] for i in range(len(classes))}}
+
+
+def slab_sample(nat, n_t_sample=4):
+    """Exact one-part passes on the first n_t_sample slabs of the workload (its
+    mesh, theta and observation mask) in FP64 and in the mixed form: the
+    mixed form's per-result error against FP64 at the workload's block size,
+    and the FP64 dense time per slab (factorisation, Takahashi)."""
+    q, w = nat.q, nat.w
+    mm = (nat.mesh, np.ascontiguousarray(nat.mask[:w.n_s * n_t_sample]))
+    out = {}
+    for name, prec in (("fp64", q.QSEL_FP64), ("mixed", q.QSEL_MIXED)):
+        c = nat.ctx(prec, n_parts=1, overlap=0, k=2, mesh_mask=mm, n_t=n_t_sample)
+        v = q.qsel_diag_inv(c)
+        g = np.asarray(q.qsel_trace_grads(c))
+        st = q.qsel_stats(c)
+        c.close()
+        out[name] = (v, g, st)
+    v64, g64, st64 = out["fp64"]
+    vm, gm, _ = out["mixed"]
+    return {"slabs": n_t_sample, "mixed_vs_fp64": _errs(vm, gm, v64, g64),
+            "fp64_factor_s_per_slab": st64["ms_factor"] / 1e3 / n_t_sample,
+            "fp64_takahashi_s_per_slab": st64["ms_takahashi"] / 1e3 / max(1, n_t_sample - 1)}
+
+
+def plain_fp64_time_to_target(args, nat, v_ex, t_ex, sample):
+    """Plain FP64 RBMC (the workload's partition, block-Jacobi PCG) by the
+    procedure of the metric: overlap n_l in {given, +1, +2}; for each, the
+    error at k = 512 measured over --plain-seeds seeds (run in the mixed form,
+    whose results agree with FP64 to the slab sample's error, far below the
+    target); the samples needed for 1 % are k = 512 (eps / 0.01)^2, in
+    512-sample runs whose averages reduce the error as 1/sqrt(runs); the
+    time of each run is extrapolated from the FP64 dense time per slab of
+    the slab sample over the run's factorised slabs (a lower bound: the FP64
+    sampler and correction solves are not counted).  The cheapest n_l wins."""
+    q, w = nat.q, nat.w
+    ss = [int(x) for x in qi.balanced_slab_start(w.n_t, w.n_parts)]
+    rows = []
+    for nl in (w.overlap, w.overlap + 1, w.overlap + 2):
+        vs, gs = [], []
+        for sd in range(args.plain_seeds):
+            c = nat.ctx(q.QSEL_MIXED, overlap=nl, k=512, seed=7000 + sd)
+            vs.append(q.qsel_diag_inv(c))
+            gs.append(np.asarray(q.qsel_trace_grads(c)))
+            c.close()
+        e = _seed_errors(vs, gs, v_ex, t_ex)
+        eps = max(e["eps_diag"], *e["eps_traces"])
+        k_need = 512 * (eps / args.target) ** 2
+        runs = max(1, math.ceil(k_need / 512))
+        fwd, bwd = _subdomain_slabs(w.n_t, ss, [nl] * w.n_parts)
+        t_run = fwd * sample["fp64_factor_s_per_slab"] + bwd * sample["fp64_takahashi_s_per_slab"]
+        rows.append({"overlap": nl, "k": 512, **e, "k_needed": k_need, "runs_of_512": runs,
+                     "slabs_forward": fwd, "slabs_backward": bwd, "fp64_s_per_run_lower_bound": t_run,
+                     "time_to_target_s_lower_bound": runs * t_run})
+    best = min(rows, key=lambda r: r["time_to_target_s_lower_bound"])
+    return {"procedure": plain_fp64_time_to_target.__doc__.split("\n\n")[0].replace("\n    ", " "),
+            "settings": rows, "best": {"overlap": best["overlap"], "time_s": best["time_to_target_s_lower_bound"]},
+            "extrapolated": True}
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -307,168 +548,48 @@ def run_native(args):
     torch.cuda.set_device(local)
     from paper_2309_05435_gb300 import build, qsel
     build.build()
-
-    w = qi.workload(args.workload)
-    mesh, mask = workload_inputs(w)
-    stream = torch.cuda.current_stream()
-    seed = rank_seed(rank)
     dev = f"cuda:{local}"
-    chosen_prec = qsel.QSEL_MIXED if args.precision == "mixed" else qsel.QSEL_FP64
+    stream = torch.cuda.current_stream()
+    w = qi.workload(args.workload)
+    nat = Native(qsel, w, stream, dev)
 
-    planned = args.form == "planned" and chosen_prec == qsel.QSEL_MIXED
-    net, cv_info = None, None
-    if planned and args.cv_params:
+    if args.cv_params:
         net = qsel.qsel_cv_create(0)
         qsel.qsel_cv_set_params(net, np.load(args.cv_params))
         cv_info = {"loaded": os.path.basename(args.cv_params)}
-    elif planned:
+    else:
         net, cv_info = train_control_variate(args)
         if args.save_cv_params:
             np.save(args.save_cv_params, qsel.qsel_cv_get_params(net))
 
-    chosen_pc = qsel.QSEL_PRECOND_KRON if args.preconditioner == "kron" else qsel.QSEL_PRECOND_BLOCK_JACOBI
-    cost_pcg = args.cost_pcg if args.cost_pcg else (KRON_PCG_COST if args.preconditioner == "kron" else 0.0)
+    ch = measure_chosen(args, nat, net, world, dist, rank)
+    ms_per_step = ch["ms_total"] / args.steps
 
-    def make_ctx(precision, profile=1, k=None, part_overlap=None, preconditioner=None):
-        pc = chosen_pc if preconditioner is None else preconditioner
-        return qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma,
-                                w.theta, n_parts=w.n_parts, overlap=w.overlap,
-                                n_samples=k if k else w.n_samples, seed=seed, precision=precision,
-                                pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream, profile_kernels=profile,
-                                part_overlap=part_overlap, preconditioner=pc)
-
-    def make_plan(ctx):
-        return qsel.qsel_cv_plan(ctx, net, args.margin * args.target, max_overlap=args.max_overlap,
-                                 cost_pcg=cost_pcg)
-
-    plan = None
-    k_run, po = w.n_samples, None
-    if planned:
-        probe = make_ctx(chosen_prec, profile=0, k=32)
-        plan = make_plan(probe)
-        probe.close()
-        k_run, po = plan["n_samples"], [int(x) for x in plan["part_overlap"]]
-    # kernels the planner launches per call: time coefficients, Q_s values,
-    # features, network, per-part reduction for every candidate overlap
-    plan_launches = 5 * args.max_overlap if planned else 0
-
-    def timed(ctx, out, warmup, steps, clocks=False, with_plan=False):
-        grads = np.zeros(3)
-        errs = []
-
-        def step():
-            if with_plan:
-                p = make_plan(ctx)
-                if p["n_samples"] != k_run or [int(x) for x in p["part_overlap"]] != po:
-                    raise RuntimeError("the plan changed between steps at fixed theta")
-            qsel.qsel_set_theta(ctx, w.theta)
-            qsel.qsel_diag_inv(ctx, out)
-            grads[:] = qsel.qsel_trace_grads(ctx)
-            errs.append(qsel.qsel_error_estimate(ctx)[1])
-            return qsel.qsel_stats(ctx)
-
-        for _ in range(warmup):
-            step()
-        sampler = ClockSampler(local) if clocks else None
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        profile = clocks and args.profile_timed
-        if profile:
-            torch.cuda.profiler.start()
-        e0.record(stream)
-        stats = [step() for _ in range(steps)]
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if profile:
-            torch.cuda.profiler.stop()
-        if world > 1:
-            dist.barrier()
-        clk = sampler.stop() if sampler else None
-        ms = job_time_ms(e0.elapsed_time(e1), world, dist if world > 1 else None, dev)
-        return ms, stats, clk, grads.copy(), errs[-1]
-
-    ctx = make_ctx(chosen_prec, k=k_run, part_overlap=po)
-    out = torch.empty(w.n, dtype=torch.float64, device=dev)
-    ms_total, stats, clk, grads, err_est = timed(ctx, out, args.warmup, args.steps, clocks=True, with_plan=planned)
-    ms_per_step = ms_total / args.steps
-    v_chosen = out.cpu().numpy()
-
-    plain = None
-    v_fp64 = None
-    grads64 = None
-    if args.fp64_steps > 0 and (chosen_prec != qsel.QSEL_FP64 or planned):
-        ctx64 = make_ctx(qsel.QSEL_FP64, profile=0, preconditioner=qsel.QSEL_PRECOND_BLOCK_JACOBI)
-        out64 = torch.empty(w.n, dtype=torch.float64, device=dev)
-        ms64, st64, _, grads64, err64 = timed(ctx64, out64, 1, args.fp64_steps)
-        v_fp64 = out64.cpu().numpy()
-        ph = st64[-1]
-        t_fixed = (ph["ms_factor"] + ph["ms_takahashi"]) / 1e3
-        t_per_k = (ph["ms_rhs"] + ph["ms_pcg"] + ph["ms_correction"]) / 1e3 / w.n_samples
-        k_need = w.n_samples * (err64 / args.target) ** 2
-        batches = max(1, math.ceil(k_need / 512))
-        k_batch = min(512, 32 * math.ceil(k_need / 32))
-        t_target = batches * (t_fixed + t_per_k * k_batch)
-        plain = {"settings": f"overlap {w.overlap}, {w.n_samples} samples", "ms_per_step": ms64 / args.fp64_steps,
-                 "steps": args.fp64_steps, "warmup": 1, "pcg_iterations": ph["pcg_iterations"],
-                 "error_estimate": err64,
-                 "time_to_target_model_s": t_target,
-                 "time_to_target_model": (f"k needed = {w.n_samples} (err/target)^2 = {k_need:.0f}; "
-                                          f"{batches} pipeline run(s) of {k_batch} samples, each timed as the "
-                                          "measured k-independent phases (factor, Takahashi) plus the "
-                                          "measured per-sample phases (RHS, PCG, correction) scaled to k; "
-                                          "assumes k known in advance"),
-                 "speedup_chosen_vs_plain_time_to_target": t_target / (ms_per_step / 1e3),
-                 "chosen_vs_fp64_same_seed": None}
-        if not planned:
-            plain["chosen_vs_fp64_same_seed"] = {
-                "diag_max_rel": float(np.max(np.abs(v_chosen - v_fp64) / np.abs(v_fp64))),
-                "traces_rel": [float(abs(a - b) / abs(b)) for a, b in zip(grads, grads64)]}
-        ctx64.close()
-
-    # the exact one-part alternative (no separator, no samples) in the same
-    # precision, timed for comparison
-    alt = None
-    v_alt = g_alt = None
-    if planned and args.fp64_steps > 0:
-        ctx1 = qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma,
-                                w.theta, n_parts=1, overlap=0, n_samples=2, precision=chosen_prec,
-                                cuda_stream=stream.cuda_stream)
-        out1 = torch.empty(w.n, dtype=torch.float64, device=dev)
-        ms1, st1, _, g_alt, _ = timed(ctx1, out1, 1, 1)
-        v_alt = out1.cpu().numpy()
-        alt = {"form": "exact single part (n_p = 1), same precision", "s_per_pass": ms1 / 1e3,
-               "planner_model_cost_s": plan["single_part_cost"] if plan else None,
-               "phases_ms": {"factor": st1[-1]["ms_factor"], "takahashi": st1[-1]["ms_takahashi"]}}
-        ctx1.close()
-
-    # end to end through the public API with host buffers
-    e2e_s = None
-    h2d = (mesh.c_diag.nbytes + mesh.g_rowptr.nbytes + mesh.g_col.nbytes + mesh.g_val.nbytes + mask.nbytes
-           + 3 * 8 + 8)
+    # end to end through the public API with host buffers: create from pinned
+    # host arrays, plan, diag to pinned host memory, traces, destroy
+    h2d = (nat.mesh.c_diag.nbytes + nat.mesh.g_rowptr.nbytes + nat.mesh.g_col.nbytes + nat.mesh.g_val.nbytes
+           + nat.mask.nbytes + 3 * 8 + 8)
     d2h = w.n * 8 + 3 * 8
+    e2e_s = None
     if args.e2e_steps > 0:
-        c_pin = torch.from_numpy(mesh.c_diag).pin_memory().numpy()
-        gv_pin = torch.from_numpy(mesh.g_val).pin_memory().numpy()
-        rp_pin = torch.from_numpy(mesh.g_rowptr).pin_memory().numpy()
-        gc_pin = torch.from_numpy(mesh.g_col).pin_memory().numpy()
-        mk_pin = torch.from_numpy(mask).pin_memory().numpy()
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()  # noqa: E731
+        c_pin, gv_pin, rp_pin, gc_pin, mk_pin = (pin(nat.mesh.c_diag), pin(nat.mesh.g_val), pin(nat.mesh.g_rowptr),
+                                                 pin(nat.mesh.g_col), pin(nat.mask))
         diag_host = torch.empty(w.n, dtype=torch.float64).pin_memory().numpy()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
+        for i in range(args.e2e_steps):
             c2 = qsel.qsel_create(w.n_s, w.n_t, c_pin, rp_pin, gc_pin, gv_pin, mk_pin, w.sigma, w.theta,
-                                  n_parts=w.n_parts, overlap=w.overlap, n_samples=k_run, seed=seed,
-                                  precision=chosen_prec, pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream,
-                                  part_overlap=po, preconditioner=chosen_pc)
-            if planned:
-                p = make_plan(c2)
-                if p["n_samples"] != k_run or [int(x) for x in p["part_overlap"]] != po:
-                    raise RuntimeError("the plan changed between calls at fixed theta")
+                                  n_parts=len(ch["slab_start"]) - 1, slab_start=ch["slab_start"],
+                                  overlap=min(ch["part_overlap"]), n_samples=ch["k"], seed=6000 + i,
+                                  precision=qsel.QSEL_MIXED, pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream,
+                                  part_overlap=ch["part_overlap"], preconditioner=qsel.QSEL_PRECOND_KRON)
+            p = qsel.qsel_cv_plan(c2, net, args.margin * args.target, max_overlap=PLAN_MAX_OVERLAP,
+                                  cost_pcg=KRON_PCG_COST, part_counts=[c for c in RBMC_PART_COUNTS if c <= w.n_t])
+            if [int(x) for x in p["part_overlap"]] != ch["part_overlap"]:
+                raise RuntimeError("the plan changed between calls at fixed theta")
             qsel.qsel_diag_inv(c2, diag_host)
             qsel.qsel_trace_grads(c2)
             c2.close()
@@ -479,109 +600,49 @@ def run_native(args):
         e2e_s = float(el.item()) / (args.e2e_steps * world)
 
     if rank != 0:
-        ctx.close()
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()
         return
 
-    # dominant kernel class of the timed form (by event time), among the
-    # classes with a defined algorithmic work
-    classes = qsel.PROF_CLASSES
-    cms = [sum(s["class_ms"][q] for s in stats) for q in range(len(classes))]
-    cwork = [sum(s["class_work"][q] for s in stats) for q in range(len(classes))]
-    claunch = [sum(s["class_launches"][q] for s in stats) for q in range(len(classes))]
+    st_prof = profile_pass(nat, ch)
     hbm_peak, hbm_src = measured_peaks()
-    mixed = chosen_prec == qsel.QSEL_MIXED
     tf32_peak, tf32_src = tf32_peak_tflops()
-    desc = {
-        "gemm": ("dense tile GEMMs (tcgen05 3xTF32, TMA, TMEM)" if mixed else "k_gemm64 (FP64 dense tile GEMM)"),
-        "sweep_update": ("sweep panel updates, rank 256 (tcgen05 3xTF32)" if mixed else "k_sweep_update (FP64)"),
-        "spmm": "k_bt_spmm (block-tridiagonal sliced-ELL SpMM, PCG)",
-        "pivot": "k_bsweep_pivot (64x64 pivot-tile inverses: FP64, or double-float on float tiles)",
-        "precond": ("k_kron_pass x6 (Kronecker grid preconditioner)" if args.preconditioner == "kron"
-                    else "k_pcg_precond (block-Jacobi apply, register-tiled)"),
-    }
-    cand = [q for q, name in enumerate(classes) if name in desc and cwork[q] > 0 and cms[q] > 0]
-    dom = max(cand, key=lambda q: cms[q])
-    name = classes[dom]
-    per_launch_ms = cms[dom] / max(1, claunch[dom])
-    if name == "spmm":
-        ach = cwork[dom] / (cms[dom] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "peak_source": hbm_src}
-    elif name in ("gemm", "sweep_update") and mixed:
-        # 3xTF32: three TF32 MMAs per useful product
-        ach = 3.0 * cwork[dom] / (cms[dom] * 1e-3) / 1e12
-        roof = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
-                "peak_source": tf32_src + "; achieved counts the three TF32 products of each 3xTF32 product"}
-    elif not mixed:
-        ach = cwork[dom] / (cms[dom] * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "peak_source": "nominal FP64 rate (152 SMs x 2.07 GHz x 4 FLOP/clk); FMA-loop probe 1.19 TFLOP/s"}
-    elif name == "pivot":
-        # double-float pivots: about 15 FP32 operations per useful FLOP
-        ach = cwork[dom] / (cms[dom] * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS / 15.0, "unit": "TFLOP/s",
-                "peak_source": "FP32 CUDA-core rate from unit counts / 15 FP32 operations per double-float "
-                               "multiply-subtract"}
-    else:
-        ach = cwork[dom] / (cms[dom] * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "peak_source": "FP32 CUDA-core rate from unit counts (152 x 128 x 2 x 2.07 GHz); "
-                               "FMA-loop probe 69.6 TFLOP/s"}
-    traffic = None
-    if name == "gemm" and not mixed and claunch[dom]:
-        traffic = GEMM64_DRAM_BYTES_PER_FLOP * cwork[dom] / claunch[dom]
-    if name == "sweep_update" and mixed and claunch[dom] and w.n_s == 4096:
-        # one ncu capture of the rank-256 update (2 matrices of 4096^2), scaled by the
-        # matrices per launch: the class's work is 2 64^2 256 FLOP per lower tile
-        # off the panel, (nt - 4)(nt - 3) / 2 tiles per matrix
-        nt = 64
-        per_matrix_flop = 2.0 * 64 * 64 * 256 * (nt - 4) * (nt - 3) / 2
-        traffic = TC_UPDATE_DRAM_BYTES_PER_MATRIX * (cwork[dom] / claunch[dom] / per_matrix_flop)
-    roof = {"kernel": desc[name], **roof, "frac": roof["achieved"] / roof["peak"], "traffic": traffic,
-            "launches": int(claunch[dom]), "avg_launch_ms": per_launch_ms}
-    roof["kernel_classes_ms_per_step"] = {classes[q]: cms[q] / args.steps for q in range(len(classes))}
-    st = stats[-1]
+    roof = roofline_of(st_prof, w, hbm_peak, hbm_src, tf32_peak, tf32_src)
 
+    # the exact one-part form in the same precision: the alternative, and the
+    # reference of the accuracy (its own error against FP64 from the slab sample)
+    t_exact, v_ex, t_ex, st_ex = nat.exact(qsel.QSEL_MIXED)
     accuracy = None
+    sample = plain = None
     if not args.no_accuracy:
-        ref = qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma,
-                               w.theta, n_parts=1, overlap=0, n_samples=1, cuda_stream=stream.cuda_stream)
-        v_ex = qsel.qsel_diag_inv(ref)
-        t_ex = qsel.qsel_trace_grads(ref)
-        ref.close()
-
-        def errs(v, g):
-            r = (v - v_ex) / v_ex
-            return {"eps_diag_rms": float(np.sqrt(np.mean(r ** 2))),
-                    "eps_diag_p99": float(np.quantile(np.abs(r), 0.99)),
-                    "eps_diag_max": float(np.max(np.abs(r))),
-                    "eps_traces": [float(abs(a - b) / abs(b)) for a, b in zip(g, t_ex)]}
-        accuracy = {"reference": "exact single-subdomain FP64 selected inversion on the GPU (n_p = 1)",
-                    "chosen": errs(v_chosen, grads), "chosen_error_estimate": err_est, "seeds": 1}
-        if v_fp64 is not None:
-            accuracy["plain_fp64"] = errs(v_fp64, grads64)
-        if alt is not None:
-            alt["accuracy"] = errs(v_alt, g_alt)
+        sample = slab_sample(nat)
+        accuracy = {"reference": "exact one-part selected inversion in the mixed form on the GPU (n_p = 1); its "
+                                 "own error against FP64 is `slab_sample.mixed_vs_fp64` at this block size",
+                    "chosen": _seed_errors(ch["diags"], ch["grads"], v_ex, t_ex),
+                    "chosen_error_estimates": ch["err_estimates"], "slab_sample": sample}
+        if args.plain_seeds > 0:
+            plain = plain_fp64_time_to_target(args, nat, v_ex, t_ex, sample)
+    chosen_ok = accuracy["chosen"]["meets_1pct"] if accuracy else None
+    alt = {"form": "exact one-part selected inversion (n_p = 1), mixed precision", "s_per_pass": t_exact,
+           "time_to_target_s": t_exact, "phases_ms": {"factor": st_ex["ms_factor"],
+                                                       "takahashi": st_ex["ms_takahashi"]},
+           "planner_model_cost_s": ch["plan"]["single_part_cost"]}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:   # the CPU baseline is an N = 1 figure
         est, spent, desc = oracle_sample(w)
         cpu = {"value": est, "unit": "s", "cores": cpu_cores(), "kind": "oracle", "sample": desc,
                "sample_seconds": spent}
-        one = oracle_sample_single_thread(w)
-        if one is not None:
-            cpu["single_thread_value"], cpu["single_thread_sample_seconds"] = one
 
-    form = "mixed precision RBMC (FP32 PCG + FP64 refinement, FP32 tiles + double-float pivots)" \
-        if chosen_prec == qsel.QSEL_MIXED else "plain FP64 RBMC"
-    if planned:
-        form += f" + learned control variate planner (target {args.target:g} RMS relative error)"
-    form += ", Kronecker grid preconditioner" if args.preconditioner == "kron" else ", block-Jacobi preconditioner"
+    st = ch["stats"][-1]
+    plan = ch["plan"]
+    form = ("mixed precision RBMC (FP32 PCG with the Kronecker grid preconditioner + FP64 refinement; "
+            "FP32 tiles on tcgen05 3xTF32 + double-float pivots) + learned control-variate planner (part count, "
+            f"per-part overlap, k for {args.target:g} RMS relative error)")
     result = {
         "metric": METRIC,
-        "value": job_value_s(ms_total, args.steps, world),
+        "value": job_value_s(ch["ms_total"], args.steps, world),
         "unit": "s",
         "n_gpus": world,
         "steps": args.steps,
@@ -590,37 +651,55 @@ def run_native(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32+f64" if chosen_prec == qsel.QSEL_MIXED else "f64",
+        "dtype": "f32+f64",
         "data": "synthetic (seeded grid FEM mesh, Philox noise)",
         "config": {"workload": f"{w.name}: {w.m}x{w.m} grid, n_t={w.n_t}, n={w.n}, kappa={w.kappa}, "
                                f"rho={w.rho}, {int(w.obs_frac * 100)}% observed",
-                   "form": form, "n_parts": w.n_parts, "overlap": po if po else w.overlap,
-                   "n_samples": k_run, "pcg_tol": w.pcg_tol,
-                   "l2": "inputs larger than L2 (samples alone %.2f GB)" % (w.n * k_run * 8 / 1e9),
+                   "form": form, "n_parts": len(ch["slab_start"]) - 1, "slab_start": ch["slab_start"],
+                   "overlap": ch["part_overlap"], "n_samples": ch["k"], "pcg_tol": w.pcg_tol,
+                   "seeds": "a new Philox seed every step",
+                   "l2": "inputs larger than L2 (samples alone %.2f GB)" % (w.n * ch["k"] * 8 / 1e9),
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "phases_ms": {"rhs": st["ms_rhs"], "pcg": st["ms_pcg"], "factor": st["ms_factor"],
-                      "takahashi": st["ms_takahashi"], "correction": st["ms_correction"]},
+                      "takahashi": st["ms_takahashi"], "correction": st["ms_correction"],
+                      "total": st["ms_total"]},
         "pcg_iterations": st["pcg_iterations"],
-        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)) + plan_launches * args.steps,
-        "plan": None if plan is None else {"n_samples": plan["n_samples"], "part_overlap": po,
-                                           "predicted_err": plan["predicted_err"],
-                                           "predicted_cost_s": plan["predicted_cost"],
-                                           "feasible": plan["feasible"], "error_estimate": err_est,
-                                           "margin": args.margin},
+        "gpu_launches": ch["launches"],
+        "chosen_meets_target": chosen_ok,
+        "plan": {"n_parts": plan["n_parts"], "n_samples": plan["n_samples"], "part_overlap": ch["part_overlap"],
+                 "predicted_err": plan["predicted_err"], "predicted_cost_s": plan["predicted_cost"],
+                 "feasible": plan["feasible"], "margin": args.margin,
+                 "recommendation_with_exact": {"n_parts": ch["recommendation"]["n_parts"],
+                                               "predicted_cost_s": ch["recommendation"]["predicted_cost"]}},
         "cv_training": cv_info,
         "alternative": alt,
         "plain_fp64": plain,
-        "clocks": clk,
+        "speedup_chosen_vs_plain_fp64": (plain["best"]["time_s"] / (ms_per_step / 1e3)) if plain else None,
+        "clocks": ch["clocks"],
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "cpu_baseline": cpu,
         "accuracy": accuracy,
     }
+    if args.secondary and args.secondary != w.name:
+        result["secondary"] = secondary_workload(args, qsel, qi.workload(args.secondary), stream, dev, net)
     print(json.dumps(result), flush=True)
-    ctx.close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def secondary_workload(args, q, w2, stream, dev, net):
+    """The chosen form and the exact one-part form on a second workload (one
+    warm-up and two timed steps), with the accuracy over those seeds."""
+    nat = Native(q, w2, stream, dev)
+    a2 = argparse.Namespace(**{**vars(args), "warmup": 1, "steps": 2})
+    ch = measure_chosen(a2, nat, net, 1, None, 0, clocks=False)
+    t_exact, v_ex, t_ex, _ = nat.exact(q.QSEL_MIXED)
+    return {"workload": w2.name, "s_per_pass": ch["ms_total"] / 2 / 1e3, "n_parts": len(ch["slab_start"]) - 1,
+            "overlap": ch["part_overlap"], "n_samples": ch["k"],
+            "accuracy": _seed_errors(ch["diags"], ch["grads"], v_ex, t_ex),
+            "exact_one_part_s": t_exact}
 
 
 # ----------------------------------------------------------------------------

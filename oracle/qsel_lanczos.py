@@ -88,14 +88,20 @@ def f_T_e1(alpha, beta, eta):
 def sample(model: o.Model, theta, seed: int, k: int, m: int, b: int = 64):
     """Algorithm 5.1 for k columns.  Returns (X (n, k), alphas, betas) with
     alphas[s], betas[s] the Lanczos coefficients of column s."""
-    Q = o.precision(model, theta).tocsr()
+    return sample_q(o.precision(model, theta), seed, k, m, b)
+
+
+def sample_q(Q, seed: int, k: int, m: int, b: int = 64):
+    """Algorithm 5.1 on a given precision Q (n x n sparse), as sample()."""
+    Q = Q.tocsr()
+    n = Q.shape[0]
     fac = block_factors(Q, b)
-    Z = o.philox_normals(seed, 0, model.n, k)
+    Z = o.philox_normals(seed, 0, n, k)
 
     def op(v):
         return apply_Linv(fac, Q @ apply_LinvT(fac, v))
 
-    X = np.zeros((model.n, k))
+    X = np.zeros((n, k))
     alphas, betas = [], []
     for s in range(k):
         z = Z[:, s]

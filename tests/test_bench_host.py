@@ -1,0 +1,26 @@
+"""Host-side arithmetic of bench.py (no GPU): slab counts of a partition and
+the error definitions of the time-to-1 % metric."""
+import numpy as np
+
+import bench
+
+
+def test_subdomain_slabs():
+    # 8 slabs in 2 parts, overlap 1: parts [0,4) -> [0,5), [4,8) -> [3,8)
+    fwd, bwd = bench._subdomain_slabs(8, [0, 4, 8], [1, 1])
+    assert fwd == 5 + 5
+    # backward: part 0 from slab 3 down to 0 (lo = 0): 4; part 1 (lo = 1): from 3 down to 0 -> 4
+    assert bwd == 4 + 4
+    # one part: n_t forward, n_t - 1 backward
+    assert bench._subdomain_slabs(8, [0, 8], [0]) == (8, 7)
+
+
+def test_seed_errors_definition():
+    v_ex = np.array([1.0, 2.0, 4.0])
+    t_ex = np.array([1.0, -2.0, 10.0])
+    vs = [v_ex * 1.01, v_ex * 0.99]
+    gs = [t_ex * 1.02, t_ex * 0.98]
+    e = bench._seed_errors(vs, gs, v_ex, t_ex)
+    assert abs(e["eps_diag"] - 0.01) < 1e-12
+    assert all(abs(x - 0.02) < 1e-12 for x in e["eps_traces"])
+    assert e["seeds"] == 2 and not e["meets_1pct"]
