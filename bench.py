@@ -102,6 +102,10 @@ def parse_args():
     ap.add_argument("--batch-streams", type=int, default=16)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-e2e", default=None,
+                    help="comma list of workloads: time the CPU oracle end to end (all host cores)")
+    ap.add_argument("--oracle-e2e-single", default="grid16_nt8",
+                    help="workloads of --oracle-e2e also timed on one thread")
     ap.add_argument("--hyper-eval", action="store_true",
                     help="time the posterior mean and the hyperparameter gradient (mixed and FP64)")
     ap.add_argument("--lanczos-eval", default=None,
@@ -729,6 +733,44 @@ def run_reference(args):
     }), flush=True)
 
 
+def oracle_end_to_end(name: str):
+    """The CPU oracle end to end at a workload's own settings: exact samples by
+    its direct block-tridiagonal solve (the sampler), then Algorithm 4 and the
+    trace estimator (factorisation, Takahashi recursion, correction solves) for
+    every part.  Returns (seconds, phase seconds)."""
+    from oracle import qsel_oracle as o
+    w = qi.workload(name)
+    mesh, mask = workload_inputs(w)
+    model = o.model_from_csr(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma)
+    for _ in range(2 if w.n < 100_000 else 1):   # small workloads: the second, warm run
+        t0 = time.perf_counter()
+        X = o.samples(model, w.theta, 1000, w.n_samples)
+        t1 = time.perf_counter()
+        o.rbmc(model, w.theta, qi.balanced_slab_start(w.n_t, w.n_parts), w.overlap, X)
+        t2 = time.perf_counter()
+    return t2 - t0, {"sampler": t1 - t0, "rbmc": t2 - t1}
+
+
+def run_oracle_e2e(args):
+    """--oracle-e2e: the oracle end to end on the listed workloads with all host
+    cores, and in a child process limited to one BLAS / OpenMP thread on the
+    workloads in --oracle-e2e-single; one JSON line per run."""
+    for name in [x for x in args.oracle_e2e.split(",") if x]:
+        s, ph = oracle_end_to_end(name)
+        print(json.dumps({"mode": "oracle_e2e", "workload": name, "threads": "all", "cores": cpu_cores(),
+                          "seconds": s, "phases_s": ph}), flush=True)
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[var] = "1"
+    for name in [x for x in args.oracle_e2e_single.split(",") if x]:
+        p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-e2e", name,
+                            "--oracle-e2e-single", ""], env=env, capture_output=True, text=True, timeout=3600)
+        for line in p.stdout.strip().splitlines():
+            d = json.loads(line)
+            d["threads"] = 1
+            print(json.dumps(d), flush=True)
+
+
 def run_sweep(args):
     """Time one pass (after one warm-up) and measure the error against the exact
     single-subdomain FP64 result for each requested (form, n_p, n_l, k), with
@@ -1008,6 +1050,9 @@ def main():
     if args.oracle_sample:
         est, spent, _ = oracle_sample(qi.workload(args.workload))
         print(json.dumps({"est": est, "spent": spent}), flush=True)
+        return
+    if args.oracle_e2e is not None:
+        run_oracle_e2e(args)
         return
     if args.hyper_eval:
         run_hyper_eval(args)

@@ -85,6 +85,29 @@ enum {
   QSEL_PRECOND_KRON = 1
 };
 
+/* Space-time prior of qsel_create (qsel_options.model). */
+enum {
+  QSEL_MODEL_SEPARABLE = 0,     /* tau Q_t (x) Q_s, AR(1) in time (Section 2.2,
+                                   separable case); theta = (log kappa, log tau,
+                                   logit rho)                                    */
+  QSEL_MODEL_DIFFUSION = 1,     /* the diffusion-based non-separable model of
+                                   Section 2.2 (Eqs. spde:5-8) with (alpha_t,
+                                   alpha_s, alpha_e) = (1, 2, 1), "critical
+                                   diffusion":
+                                     Q_u = gamma_e^2 [M0 (x) K3 + 2 gamma_t M1 (x) K2
+                                                      + gamma_t^2 M2 (x) K1],
+                                   K1 = gamma_s^2 C + G, K2 = K1 C^-1 K1,
+                                   K3 = K2 C^-1 K1, and the temporal finite-element
+                                   matrices of unit spacing: lumped mass M0 =
+                                   diag(1/2, 1, .., 1, 1/2), boundary term M1 =
+                                   diag(1/2, 0, .., 0, 1/2), Neumann stiffness M2;
+                                   theta = (log gamma_s, log gamma_t, log gamma_e)
+                                   in the fields (log_kappa, log_tau, logit_rho)
+                                   of qsel_theta.  No factored form of Q exists:
+                                   needs sampler = QSEL_SAMPLER_LANCZOS.         */
+  QSEL_MODEL_BLOCK_TRIDIAGONAL = 2  /* a user-given matrix (qsel_create_bt)     */
+};
+
 /* Arithmetic of the pipeline. */
 enum {
   QSEL_FP64 = 0,      /* every kernel computes in IEEE binary64                  */
@@ -170,6 +193,8 @@ typedef struct {
                              QSEL_PIVOT_DOUBLE_FLOAT (0, default; on the binary32
                              pipe, which GB300 runs 64x faster than binary64) or
                              QSEL_PIVOT_FP64 (1).  Ignored for QSEL_FP64.       */
+  int32_t model;          /* qsel_create: QSEL_MODEL_SEPARABLE (0) or
+                             QSEL_MODEL_DIFFUSION (1); ignored by qsel_create_bt */
 } qsel_options;
 
 #define QSEL_PROF_CLASSES 11
@@ -244,14 +269,68 @@ qsel_status qsel_set_theta(qsel_ctx *ctx, const qsel_theta *theta);
 qsel_status qsel_diag_inv(qsel_ctx *ctx, double *diag_out, int32_t out_is_device);
 
 /*
- * RBMC estimate of tr(Q^-1 dQ/dtheta_j) for theta = (log kappa, log tau,
- * logit rho), by Eq. hyperpar:4: over rows of Omega_p and columns of
- * Omega_p^*, the selected entries Sigma*_il + (1/k) sum_s w_i w_l times
- * (dQ_j)_il.  Runs the pipeline if needed.  grads_out: 3 HOST doubles.
- * Requires overlap >= 1 or a single part (QSEL_EINVAL otherwise): with no
- * overlap the neighbours of the rows of Omega_p would lie in the separator.
+ * RBMC estimate of tr(Q^-1 dQ/dtheta_j) for the model's three
+ * hyperparameters (separable: log kappa, log tau, logit rho; diffusion: log
+ * gamma_s, log gamma_t, log gamma_e), by Eq. hyperpar:4: over rows of
+ * Omega_p and columns of Omega_p^*, the selected entries Sigma*_il + (1/k)
+ * sum_s w_i w_l times (dQ_j)_il.  Runs the pipeline if needed.  grads_out: 3
+ * HOST doubles.  Requires overlap >= 1 or a single part (QSEL_EINVAL
+ * otherwise): with no overlap the neighbours of the rows of Omega_p would lie
+ * in the separator.  QSEL_EINVAL for a user-given matrix whose n_theta is not
+ * 3 (use qsel_trace_grads_n).
  */
 qsel_status qsel_trace_grads(qsel_ctx *ctx, double grads_out[3]);
+/* The same for any number of derivatives: n must equal the context's n_theta
+ * (3 for the built-in models); grads_out: n HOST doubles. */
+qsel_status qsel_trace_grads_n(qsel_ctx *ctx, double *grads_out, int32_t n);
+
+/*
+ * A user-given block-tridiagonal precision (the generic form of the
+ * estimator: Algorithm 4 needs only the block structure in time, Section
+ * 3.2.3).  Q has n_t x n_t blocks of n_s x n_s on ONE spatial pattern:
+ * diagonal blocks A_t and couplings B_t = Q[t, t+1] = Q[t+1, t]; every block
+ * must be symmetric to 1e-12 relative per entry pair (the built-in models'
+ * blocks are), and Q positive definite.  All pointers are HOST pointers, read during the call.
+ *   rowptr[n_s + 1], col[nnz]   the pattern in CSR, 0-based, symmetric, with
+ *                               every diagonal entry
+ *   diag_vals[n_t * nnz]        A_t on the pattern, block after block
+ *   off_vals[(n_t - 1) * nnz]   B_t on the pattern
+ *   n_theta                     0..4 hyperparameters with trace gradients
+ *   ddiag_vals[n_theta * n_t * nnz], doff_vals[n_theta * (n_t - 1) * nnz]
+ *                               dA_t / dtheta_j and dB_t / dtheta_j, j major
+ *                               (NULL when n_theta is 0)
+ */
+typedef struct {
+  int32_t n_s, n_t;
+  const int32_t *rowptr;
+  const int32_t *col;
+  const double *diag_vals;
+  const double *off_vals;
+  int32_t n_theta;
+  const double *ddiag_vals;
+  const double *doff_vals;
+} qsel_bt_model;
+
+/*
+ * Create a context for a user-given block-tridiagonal precision; partition,
+ * overlap and options as qsel_create.  There is no factored form, so the
+ * global samples come from the Lanczos sampler (opt->sampler must be
+ * QSEL_SAMPLER_LANCZOS) or from qsel_debug_set_samples; the preconditioner
+ * is block Jacobi; theta plays no role (qsel_set_theta returns QSEL_EINVAL:
+ * use qsel_set_bt_values).  The posterior-mean and hyperparameter calls are
+ * not available (QSEL_EINVAL).
+ * Errors: QSEL_EINVAL (shapes, pattern not symmetric or without a diagonal
+ * entry, block values not symmetric or not finite, a row of more than 64
+ * pattern entries, options), QSEL_ENOMEM, QSEL_ECUDA.
+ */
+qsel_status qsel_create_bt(qsel_ctx **out, const qsel_bt_model *model, const qsel_partition *partition,
+                           int32_t overlap, const qsel_options *opt);
+/* New values on the same pattern (layouts as qsel_bt_model; the derivative
+ * arrays may be NULL when n_theta is 0).  The next qsel_diag_inv recomputes
+ * everything.  QSEL_EINVAL for a context not made by qsel_create_bt or for
+ * values that are not finite or not symmetric. */
+qsel_status qsel_set_bt_values(qsel_ctx *ctx, const double *diag_vals, const double *off_vals,
+                               const double *ddiag_vals, const double *doff_vals);
 
 /*
  * Posterior mean and the gradient of the hyperparameter marginal, for the

@@ -50,6 +50,7 @@ struct DenseSlot {
   void *SigA = nullptr, *SigB = nullptr, *Y = nullptr, *W = nullptr, *V = nullptr;
   void *P = nullptr, *U = nullptr, *Vs = nullptr, *Vk = nullptr;  // sweep scratch
   void *U2 = nullptr, *V2 = nullptr, *Wp = nullptr, *Wp2 = nullptr;  // tensor-core sweep panels
+  void *Sp[4] = {nullptr, nullptr, nullptr, nullptr};  // the panel update's operands split into TF32 hi / lo
   void *wbuf = nullptr;                // T_max x n_pad x ld correction samples
   void *tra = nullptr, *trb = nullptr; // ld x n_pad transposes (tensor-core correction products)
   void *ybuf = nullptr, *tmp = nullptr, *bright = nullptr;
@@ -72,6 +73,7 @@ struct qsel_ctx {
   SellPattern pat{};
   int n_ent = 0;
   double *d_c_pat = nullptr, *d_g_pat = nullptr, *d_h_pat = nullptr, *d_isqc_pat = nullptr;
+  double *d_h3_pat = nullptr;          // H C^-1 G (diffusion model)
   double *d_qs = nullptr, *d_dqs = nullptr, *d_kc = nullptr;
   uint8_t *d_obs = nullptr;
   // posterior mean and hyperparameter gradient (qsel_set_data and after)
@@ -96,6 +98,19 @@ struct qsel_ctx {
   int32_t *d_obs_index = nullptr;
   int n_obs = 0;
   TimeCoeffs tc{};
+  // The precision and dQ/dtheta_j as the kernels read them (block values on
+  // the pattern with per-block scales), set by set_model_views: the
+  // separable model points at Q_s, dQ_s and the time coefficients; the
+  // diffusion model and user-given matrices at per-block arrays.
+  int model_kind = 0;                  // QSEL_MODEL_*
+  BtModel mod{};
+  DerivModels dmod{};
+  // per-block arrays of the diffusion model and of user-given matrices:
+  // A_t (n_t x n_ent), B_t ((n_t - 1) x n_ent), then per theta_j dA_j, dB_j
+  double *d_blk = nullptr;
+  double *d_blk_coef = nullptr;        // per-block scales of the diffusion model
+  std::vector<int64_t> bt_slot;        // user-given matrix: SELL slot of every CSR entry
+  std::vector<int64_t> bt_mirror;      // and the CSR position of its transpose entry
   // sampler: FP64 right-hand sides and samples; FP64 PCG vectors (FP64 path)
   // or FP32 PCG vectors plus FP64 residual buffers (mixed path)
   double *d_z1 = nullptr, *d_z2 = nullptr, *d_R = nullptr, *d_X = nullptr;
@@ -315,6 +330,8 @@ static int detect_grid(const qsel_model *m) {
   return g;
 }
 
+static Err validate_options(int n_t, const qsel_partition *part, int32_t overlap, const qsel_options *opt);
+
 static Err validate(const qsel_model *m, const qsel_theta *th, const qsel_partition *part,
                     int32_t overlap, const qsel_options *opt) {
   if (!m || !th || !opt) return fail(QSEL_EINVAL, "model, theta and options must not be NULL");
@@ -337,11 +354,26 @@ static Err validate(const qsel_model *m, const qsel_theta *th, const qsel_partit
   if (!std::isfinite(th->log_kappa) || !std::isfinite(th->log_tau) || !std::isfinite(th->logit_rho))
     return fail(QSEL_EINVAL, "theta must be finite");
   if (std::fabs(th->logit_rho) > 36.0) return fail(QSEL_EINVAL, "rho too close to 0 or 1");
+  if (opt->model != QSEL_MODEL_SEPARABLE && opt->model != QSEL_MODEL_DIFFUSION)
+    return fail(QSEL_EINVAL, "model must be QSEL_MODEL_SEPARABLE or QSEL_MODEL_DIFFUSION");
+  if (opt->model == QSEL_MODEL_DIFFUSION && opt->sampler != QSEL_SAMPLER_LANCZOS)
+    return fail(QSEL_EINVAL, "the diffusion model has no factored form: it needs sampler = QSEL_SAMPLER_LANCZOS");
+  if (opt->model == QSEL_MODEL_DIFFUSION && opt->preconditioner != QSEL_PRECOND_BLOCK_JACOBI)
+    return fail(QSEL_EINVAL, "the diffusion model takes the block-Jacobi preconditioner");
+  TRY(validate_options(m->n_t, part, overlap, opt));
+  if (opt->preconditioner == QSEL_PRECOND_KRON && detect_grid(m) == 0)
+    return fail(QSEL_EINVAL, "QSEL_PRECOND_KRON needs the m x m grid mesh (stiffness T (x) D + D (x) T, lumped mass "
+                             "D (x) D away from the corners)");
+  return ok();
+}
+
+// Partition and option checks shared by every model.
+static Err validate_options(int n_t, const qsel_partition *part, int32_t overlap, const qsel_options *opt) {
   if (overlap < 0) return fail(QSEL_EINVAL, "overlap must be >= 0");
   const int np = part ? part->n_parts : 1;
-  if (np < 1 || np > m->n_t) return fail(QSEL_EINVAL, "n_parts must be in [1, n_t]");
+  if (np < 1 || np > n_t) return fail(QSEL_EINVAL, "n_parts must be in [1, n_t]");
   if (part && part->slab_start) {
-    if (part->slab_start[0] != 0 || part->slab_start[np] != m->n_t)
+    if (part->slab_start[0] != 0 || part->slab_start[np] != n_t)
       return fail(QSEL_EINVAL, "slab_start must run from 0 to n_t");
     for (int p = 0; p < np; ++p)
       if (part->slab_start[p + 1] <= part->slab_start[p])
@@ -364,9 +396,6 @@ static Err validate(const qsel_model *m, const qsel_theta *th, const qsel_partit
     return fail(QSEL_EINVAL, "pivot_precision must be QSEL_PIVOT_DOUBLE_FLOAT or QSEL_PIVOT_FP64");
   if (opt->preconditioner != QSEL_PRECOND_BLOCK_JACOBI && opt->preconditioner != QSEL_PRECOND_KRON)
     return fail(QSEL_EINVAL, "preconditioner must be QSEL_PRECOND_BLOCK_JACOBI or QSEL_PRECOND_KRON");
-  if (opt->preconditioner == QSEL_PRECOND_KRON && detect_grid(m) == 0)
-    return fail(QSEL_EINVAL, "QSEL_PRECOND_KRON needs the m x m grid mesh (stiffness T (x) D + D (x) T, lumped mass "
-                             "D (x) D away from the corners)");
   if (opt->sampler != QSEL_SAMPLER_PCG && opt->sampler != QSEL_SAMPLER_LANCZOS)
     return fail(QSEL_EINVAL, "sampler must be QSEL_SAMPLER_PCG or QSEL_SAMPLER_LANCZOS");
   if (opt->sampler == QSEL_SAMPLER_LANCZOS) {
@@ -455,25 +484,85 @@ static Err kron_prepare(qsel_ctx *c) {
   return ok();
 }
 
+static void set_separable_views(qsel_ctx *c);
+static void set_diffusion_views(qsel_ctx *c);
+
+// Rows of the spatial pattern: column -> up to four theta-free values (for
+// the mesh models C, G, H = G C^-1 G and H3 = H C^-1 G).
+using PatRows = std::vector<std::map<int, std::array<double, 4>>>;
+
+struct RestInputs {
+  const uint8_t *obs_mask = nullptr;       // n entries, or null: no observation term
+  const double *c_diag = nullptr;          // n_s lumped mass (mesh models), or null
+  std::vector<std::vector<int>> adj;       // spatial neighbours (boundary distance feature)
+};
+static Err build_rest(qsel_ctx *c, const RestInputs &in, const qsel_partition *part, int32_t overlap);
+static Err build_pattern(qsel_ctx *c, const PatRows &rows, int n_arrays, std::vector<std::vector<double>> &sell);
+
 static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, int32_t overlap) {
   const int n_s = m->n_s;
-  // spatial pattern rows: col -> (C, G, H = G C^-1 G)
-  std::vector<std::map<int, std::array<double, 3>>> rows(n_s);
-  for (int i = 0; i < n_s; ++i) {
+  const bool diffusion = c->model_kind == QSEL_MODEL_DIFFUSION;
+  // spatial pattern rows: col -> (C, G, H = G C^-1 G, H3 = H C^-1 G)
+  PatRows rows(n_s);
+  auto touch = [&](int i, int j) -> double * {
     auto &r = rows[i];
-    auto touch = [&](int j) -> double * {
-      auto it = r.find(j);
-      if (it == r.end()) it = r.emplace(j, std::array<double, 3>{0.0, 0.0, 0.0}).first;
-      return it->second.data();
-    };
-    touch(i)[0] = m->c_diag[i];
+    auto it = r.find(j);
+    if (it == r.end()) it = r.emplace(j, std::array<double, 4>{0.0, 0.0, 0.0, 0.0}).first;
+    return it->second.data();
+  };
+  for (int i = 0; i < n_s; ++i) {
+    touch(i, i)[0] = m->c_diag[i];
     for (int p = m->g_rowptr[i]; p < m->g_rowptr[i + 1]; ++p) {
       const int j = m->g_col[p];
-      touch(j)[1] += m->g_val[p];
+      touch(i, j)[1] += m->g_val[p];
       const double gij = m->g_val[p] / m->c_diag[j];
-      for (int q = m->g_rowptr[j]; q < m->g_rowptr[j + 1]; ++q) touch(m->g_col[q])[2] += gij * m->g_val[q];
+      for (int q = m->g_rowptr[j]; q < m->g_rowptr[j + 1]; ++q) touch(i, m->g_col[q])[2] += gij * m->g_val[q];
     }
   }
+  if (diffusion) {
+    for (int i = 0; i < n_s; ++i) {
+      std::vector<std::pair<int, double>> h;
+      for (auto &kv : rows[i])
+        if (kv.second[2] != 0.0) h.emplace_back(kv.first, kv.second[2]);
+      for (auto &hj : h) {
+        const int j = hj.first;
+        const double hc = hj.second / m->c_diag[j];
+        for (int q = m->g_rowptr[j]; q < m->g_rowptr[j + 1]; ++q) touch(i, m->g_col[q])[3] += hc * m->g_val[q];
+      }
+    }
+  }
+  std::vector<std::vector<double>> sell;
+  TRY(build_pattern(c, rows, 4, sell));
+  const int n_ent = c->n_ent;
+  std::vector<double> isq(n_ent, 0.0);
+  {
+    std::vector<int32_t> col(n_ent);
+    QSEL_CUDA_TRY(cudaMemcpy(col.data(), c->pat.col, n_ent * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (int e = 0; e < n_ent; ++e) isq[e] = 1.0 / std::sqrt(m->c_diag[col[e]]);
+  }
+  TRY(upload(c, &c->d_c_pat, sell[0]));
+  TRY(upload(c, &c->d_g_pat, sell[1]));
+  TRY(upload(c, &c->d_h_pat, sell[2]));
+  if (diffusion) TRY(upload(c, &c->d_h3_pat, sell[3]));
+  TRY(upload(c, &c->d_isqc_pat, isq));
+  TRY(c->alloc(&c->d_qs, n_ent));
+  TRY(c->alloc(&c->d_dqs, n_ent));
+  TRY(c->alloc(&c->d_kc, n_ent));
+  if (c->opt.preconditioner == QSEL_PRECOND_KRON) TRY(kron_setup(c, m));
+  RestInputs in;
+  in.obs_mask = m->obs_mask;
+  in.c_diag = m->c_diag;
+  in.adj.resize(n_s);
+  for (int i = 0; i < n_s; ++i)
+    for (int p = m->g_rowptr[i]; p < m->g_rowptr[i + 1]; ++p) in.adj[i].push_back(m->g_col[p]);
+  return build_rest(c, in, part, overlap);
+}
+
+// SELL-32 layout of the rows' pattern (columns in increasing order within a
+// row) and the first n_arrays value arrays in that layout; sets c->pat and
+// c->n_ent.
+static Err build_pattern(qsel_ctx *c, const PatRows &rows, int n_arrays, std::vector<std::vector<double>> &sell) {
+  const int n_s = (int)rows.size();
   const int n_slices = (n_s + kSlice - 1) / kSlice;
   std::vector<int32_t> slice_ptr(n_slices + 1, 0), slice_width(n_slices, 0);
   int max_w = 0;
@@ -489,7 +578,7 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   }
   const int n_ent = slice_ptr[n_slices];
   std::vector<int32_t> col(n_ent, 0);
-  std::vector<double> cp(n_ent, 0.0), gp(n_ent, 0.0), hp(n_ent, 0.0), isq(n_ent, 0.0);
+  sell.assign(n_arrays, std::vector<double>(n_ent, 0.0));
   for (int s = 0; s < n_slices; ++s) {
     for (int l = 0; l < kSlice; ++l) {
       const int i = s * kSlice + l;
@@ -498,10 +587,7 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
         for (auto &kv : rows[i]) {
           const int e = slice_ptr[s] + slot * kSlice + l;
           col[e] = kv.first;
-          cp[e] = kv.second[0];
-          gp[e] = kv.second[1];
-          hp[e] = kv.second[2];
-          isq[e] = 1.0 / std::sqrt(m->c_diag[kv.first]);
+          for (int a = 0; a < n_arrays; ++a) sell[a][e] = kv.second[a];
           ++slot;
         }
       }
@@ -523,29 +609,27 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   c->pat.slice_width = d_sw;
   c->pat.col = d_col;
   c->n_ent = n_ent;
-  TRY(upload(c, &c->d_c_pat, cp));
-  TRY(upload(c, &c->d_g_pat, gp));
-  TRY(upload(c, &c->d_h_pat, hp));
-  TRY(upload(c, &c->d_isqc_pat, isq));
-  TRY(c->alloc(&c->d_qs, n_ent));
-  TRY(c->alloc(&c->d_dqs, n_ent));
-  TRY(c->alloc(&c->d_kc, n_ent));
+  return ok();
+}
 
-  // observations
+// Everything after the spatial pattern: observations, time coefficients and
+// the model views, partition, sampler buffers, subdomains, dense working sets.
+static Err build_rest(qsel_ctx *c, const RestInputs &in, const qsel_partition *part, int32_t overlap) {
+  const int n_s = c->n_s;
   const int n = c->n;
-  std::vector<uint8_t> mask(m->obs_mask, m->obs_mask + n);
-  std::vector<int32_t> oidx(n, -1);
-  int n_obs = 0;
-  for (int r = 0; r < n; ++r) {
-    mask[r] = mask[r] ? 1 : 0;
-    if (mask[r]) oidx[r] = n_obs++;
+  {
+    std::vector<uint8_t> mask(n, 0);
+    std::vector<int32_t> oidx(n, -1);
+    int n_obs = 0;
+    for (int r = 0; r < n; ++r) {
+      mask[r] = (in.obs_mask && in.obs_mask[r]) ? 1 : 0;
+      if (mask[r]) oidx[r] = n_obs++;
+    }
+    c->n_obs = n_obs;
+    TRY(upload(c, &c->d_obs, mask));
+    TRY(upload(c, &c->d_obs_index, oidx));
+    if (in.c_diag) TRY(upload(c, &c->d_cdiag, std::vector<double>(in.c_diag, in.c_diag + n_s)));
   }
-  c->n_obs = n_obs;
-  TRY(upload(c, &c->d_obs, mask));
-  TRY(upload(c, &c->d_obs_index, oidx));
-  TRY(upload(c, &c->d_cdiag, std::vector<double>(m->c_diag, m->c_diag + n_s)));
-
-  if (c->opt.preconditioner == QSEL_PRECOND_KRON) TRY(kron_setup(c, m));
 
   // time coefficients
   double *tcb;
@@ -557,6 +641,13 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   c->tc.bdiag = tcb + 4 * c->n_t;
   c->tc.scalars = tcb + 5 * c->n_t;
   QSEL_CUDA_TRY(cudaMemset(tcb, 0, ((size_t)5 * c->n_t + 8) * sizeof(double)));
+  if (c->model_kind == QSEL_MODEL_SEPARABLE) {
+    set_separable_views(c);
+  } else if (c->model_kind == QSEL_MODEL_DIFFUSION) {
+    TRY(c->alloc(&c->d_blk, (size_t)(4 * c->n_t + 2) * c->n_ent));
+    TRY(c->alloc(&c->d_blk_coef, (size_t)3 * c->n_t));
+    set_diffusion_views(c);
+  }
 
   // partition
   const int np = part ? part->n_parts : 1;
@@ -585,7 +676,7 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   {
     std::vector<int> deg(n_s, 0), dist(n_s, -1), queue;
     for (int i = 0; i < n_s; ++i)
-      for (int p = m->g_rowptr[i]; p < m->g_rowptr[i + 1]; ++p) deg[i] += (m->g_col[p] != i);
+      for (int j : in.adj[i]) deg[i] += (j != i);
     const int dmax = *std::max_element(deg.begin(), deg.end());
     for (int i = 0; i < n_s; ++i)
       if (deg[i] < dmax) {
@@ -594,8 +685,7 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
       }
     for (size_t h = 0; h < queue.size(); ++h) {
       const int i = queue[h];
-      for (int p = m->g_rowptr[i]; p < m->g_rowptr[i + 1]; ++p) {
-        const int j = m->g_col[p];
+      for (int j : in.adj[i]) {
         if (dist[j] < 0) {
           dist[j] = dist[i] + 1;
           queue.push_back(j);
@@ -611,7 +701,7 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   // sampler buffers
   const size_t vec = (size_t)n * c->ld;
   TRY(c->alloc(&c->d_z1, vec));
-  TRY(c->alloc(&c->d_z2, (size_t)std::max(n_obs, 1) * c->ld));
+  TRY(c->alloc(&c->d_z2, (size_t)std::max(c->n_obs, 1) * c->ld));
   TRY(c->alloc(&c->d_R, vec));
   TRY(c->alloc(&c->d_X, vec));
   if (c->mixed) {
@@ -669,11 +759,11 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
     c->T_max = std::max(c->T_max, sd.T);
     c->parts.push_back(sd);
   }
-  TRY(c->alloc(&c->d_partials, (size_t)np * corr_grid() * 3));
-  QSEL_CUDA_TRY(cudaMemset(c->d_partials, 0, (size_t)np * corr_grid() * 3 * sizeof(double)));
-  for (int p = 0; p < np; ++p) c->parts[p].partial = c->d_partials + (size_t)p * corr_grid() * 3;
-  TRY(c->alloc(&c->d_sums, (size_t)2 * std::max(n_sums, 1)));
-  QSEL_CUDA_TRY(cudaMemset(c->d_sums, 0, (size_t)2 * std::max(n_sums, 1) * sizeof(double)));
+  TRY(c->alloc(&c->d_partials, (size_t)np * corr_grid() * kMaxTheta));
+  QSEL_CUDA_TRY(cudaMemset(c->d_partials, 0, (size_t)np * corr_grid() * kMaxTheta * sizeof(double)));
+  for (int p = 0; p < np; ++p) c->parts[p].partial = c->d_partials + (size_t)p * corr_grid() * kMaxTheta;
+  TRY(c->alloc(&c->d_sums, (size_t)kMaxTheta * std::max(n_sums, 1)));
+  QSEL_CUDA_TRY(cudaMemset(c->d_sums, 0, (size_t)kMaxTheta * std::max(n_sums, 1) * sizeof(double)));
   c->n_trace_slabs = (int)tslabs.size();
   TRY(upload(c, &c->d_slabs, tslabs));
   TRY(c->alloc(&c->d_diag, (size_t)n));
@@ -691,7 +781,9 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   // sweep scratch: two sets of U, V and the column panel W (n_pad x
   // 64 kSweepPanel each), Vk (64 kSweepPanel x 64) and P (64 x 64)
   const size_t panel = (size_t)n_pad * 64 * kSweepPanel * esz;
-  const size_t per_slot = (size_t)(c->T_max + 5) * mat + 6 * panel + (size_t)(kSweepPanel + 1) * 64 * 64 * esz +
+  const bool split_panels = c->mixed && c->tc_passes == 3;
+  const size_t per_slot = (size_t)(c->T_max + 5) * mat + (split_panels ? 10 : 6) * panel +
+                          (size_t)(kSweepPanel + 1) * 64 * 64 * esz +
                           (size_t)(c->T_max + 5) * svec + 4096;
   size_t free_b = 0, total_b = 0;
   QSEL_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
@@ -716,6 +808,8 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
     TRY(c->alloc_bytes(&sl.U2, panel));
     TRY(c->alloc_bytes(&sl.V2, panel));
     TRY(c->alloc_bytes(&sl.Wp2, panel));
+    if (split_panels)
+      for (auto &sp : sl.Sp) TRY(c->alloc_bytes(&sp, panel));
     TRY(c->alloc_bytes(&sl.Vk, (size_t)kSweepPanel * 64 * 64 * esz));
     TRY(c->alloc_bytes(&sl.wbuf, (size_t)c->T_max * svec));
     TRY(c->alloc_bytes(&sl.ybuf, svec));
@@ -748,16 +842,58 @@ static Err build(qsel_ctx *c, const qsel_model *m, const qsel_partition *part, i
   return ok();
 }
 
+// The kernels' view of the separable model (Q = tau Q_t (x) Q_s + obs):
+// every block is Q_s (or dQ_s/dlog kappa) scaled by a time coefficient.
+static void set_separable_views(qsel_ctx *c) {
+  c->mod.diag = BlockVals{c->d_qs, 0, c->tc.a0};
+  c->mod.off = BlockVals{c->d_qs, 0, c->tc.a1};
+  c->mod.obs = c->d_obs;
+  c->mod.obs_w = c->obs_w;
+  c->dmod.n = 3;
+  c->dmod.diag[0] = BlockVals{c->d_dqs, 0, c->tc.a0};   // d/dlog kappa
+  c->dmod.off[0] = BlockVals{c->d_dqs, 0, c->tc.a1};
+  c->dmod.diag[1] = BlockVals{c->d_qs, 0, c->tc.a0};    // d/dlog tau
+  c->dmod.off[1] = BlockVals{c->d_qs, 0, c->tc.a1};
+  c->dmod.diag[2] = BlockVals{c->d_qs, 0, c->tc.r0};    // d/dlogit rho
+  c->dmod.off[2] = BlockVals{c->d_qs, 0, c->tc.r1};
+}
+
+// The diffusion model's view: per-slab diagonal blocks, couplings K1 scaled
+// per slab pair (layout of d_blk and d_blk_coef in model.cu).
+static void set_diffusion_views(qsel_ctx *c) {
+  const int64_t e = c->n_ent, tot = (int64_t)c->n_t * e;
+  const double *K1 = c->d_blk + 4 * tot, *dK1 = K1 + e;
+  const double *cB = c->d_blk_coef, *cBt = cB + c->n_t, *cBe = cB + 2 * c->n_t;
+  c->mod.diag = BlockVals{c->d_blk, e, nullptr};
+  c->mod.off = BlockVals{K1, 0, cB};
+  c->mod.obs = c->d_obs;
+  c->mod.obs_w = c->obs_w;
+  c->dmod.n = 3;
+  c->dmod.diag[0] = BlockVals{c->d_blk + tot, e, nullptr};       // d/dlog gamma_s
+  c->dmod.off[0] = BlockVals{dK1, 0, cB};
+  c->dmod.diag[1] = BlockVals{c->d_blk + 2 * tot, e, nullptr};   // d/dlog gamma_t
+  c->dmod.off[1] = BlockVals{K1, 0, cBt};
+  c->dmod.diag[2] = BlockVals{c->d_blk + 3 * tot, e, nullptr};   // d/dlog gamma_e
+  c->dmod.off[2] = BlockVals{K1, 0, cBe};
+}
+
 // ---------------------------------------------------------------------------
 // Pipeline
 // ---------------------------------------------------------------------------
 static Err run_model(qsel_ctx *c) {
+  if (c->model_kind == QSEL_MODEL_BLOCK_TRIDIAGONAL) return ok();   // values set by the caller
   // theta goes through pinned host memory, so a captured graph picks up the
   // value set before each replay
   c->h_theta[0] = c->theta.log_kappa;
   c->h_theta[1] = c->theta.log_tau;
   c->h_theta[2] = c->theta.logit_rho;
   QSEL_CUDA_TRY(cudaMemcpyAsync(c->d_theta, c->h_theta, 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (c->model_kind == QSEL_MODEL_DIFFUSION) {
+    launch_diffusion_values(c->stream, c->d_theta, c->n_t, c->n_ent, c->d_c_pat, c->d_g_pat, c->d_h_pat,
+                            c->d_h3_pat, c->d_blk, c->d_blk_coef);
+    QSEL_CUDA_TRY(cudaGetLastError());
+    return ok();
+  }
   launch_time_coeffs(c->stream, c->d_theta, c->n_t, c->tc);
   launch_qs_values(c->stream, c->n_ent, c->d_c_pat, c->d_g_pat, c->d_h_pat, c->d_isqc_pat,
                    c->tc.scalars, c->d_qs, c->d_dqs, c->d_kc);
@@ -806,11 +942,7 @@ static Err pcg_solve(qsel_ctx *c, const PcgVec<T> &v, const T *pblk, double tol,
   launch_pcg_p_update<T>(s, v);
   BtSpmmArgs<T> a{};
   a.pat = c->pat;
-  a.val = c->d_qs;
-  a.c0 = c->tc.a0;
-  a.c1 = c->tc.a1;
-  a.obs = c->d_obs;
-  a.obs_w = c->obs_w;
+  a.m = c->mod;
   a.n_s = c->n_s;
   a.n_t = c->n_t;
   a.ld = c->ld;
@@ -876,7 +1008,7 @@ static Err solve_R(qsel_ctx *c) {
   if (!c->mixed) {
     double *pblk = static_cast<double *>(c->d_pblk);
     if (!c->kron)
-      launch_jacobi_setup<double>(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
+      launch_jacobi_setup<double>(s, c->pat, c->mod, c->n_s, c->n_t,
                                   c->bsize, pblk, c->d_err);
     QSEL_CUDA_TRY(cudaMemcpyAsync(c->d_r, c->d_R, vec * sizeof(double), cudaMemcpyDeviceToDevice, s));
     PcgVec<double> v = make_pcg<double>(c, c->d_X, c->d_r, c->d_zv, c->d_p, c->d_q);
@@ -893,18 +1025,14 @@ static Err solve_R(qsel_ctx *c) {
   }
   float *pblk = static_cast<float *>(c->d_pblk);
   if (!c->kron)
-    launch_jacobi_setup<float>(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
+    launch_jacobi_setup<float>(s, c->pat, c->mod, c->n_s, c->n_t,
                                c->bsize, pblk, c->d_err);
   PcgVec<float> v = make_pcg<float>(c, c->f_x, c->f_r, c->f_z, c->f_p, c->f_q);
   QSEL_CUDA_TRY(cudaMemsetAsync(c->d_X, 0, vec * sizeof(double), s));
   QSEL_CUDA_TRY(cudaMemsetAsync(c->d_q, 0, vec * sizeof(double), s));
   BtSpmmArgs<double> a{};
   a.pat = c->pat;
-  a.val = c->d_qs;
-  a.c0 = c->tc.a0;
-  a.c1 = c->tc.a1;
-  a.obs = c->d_obs;
-  a.obs_w = c->obs_w;
+  a.m = c->mod;
   a.n_s = c->n_s;
   a.n_t = c->n_t;
   a.ld = c->ld;
@@ -1000,11 +1128,7 @@ template <typename T>
 static void pcg_steps(qsel_ctx *c, cudaStream_t s, const PcgVec<T> &v, const T *pblk, double tol, int count) {
   BtSpmmArgs<T> a{};
   a.pat = c->pat;
-  a.val = c->d_qs;
-  a.c0 = c->tc.a0;
-  a.c1 = c->tc.a1;
-  a.obs = c->d_obs;
-  a.obs_w = c->obs_w;
+  a.m = c->mod;
   a.n_s = c->n_s;
   a.n_t = c->n_t;
   a.ld = c->ld;
@@ -1054,7 +1178,7 @@ static Err run_sampler_graph(qsel_ctx *c) {
   QSEL_CUDA_TRY(cudaMemsetAsync(c->d_loop, 0, 4 * sizeof(int32_t), s));
   if (!c->mixed) {
     double *pblk = static_cast<double *>(c->d_pblk);
-    launch_jacobi_setup<double>(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
+    launch_jacobi_setup<double>(s, c->pat, c->mod, c->n_s, c->n_t,
                                 c->bsize, pblk, c->d_err);
     QSEL_CUDA_TRY(cudaMemcpyAsync(c->d_r, c->d_R, vec * sizeof(double), cudaMemcpyDeviceToDevice, s));
     PcgVec<double> v = make_pcg<double>(c, c->d_X, c->d_r, c->d_zv, c->d_p, c->d_q);
@@ -1064,7 +1188,7 @@ static Err run_sampler_graph(qsel_ctx *c) {
     return ok();
   }
   float *pblk = static_cast<float *>(c->d_pblk);
-  launch_jacobi_setup<float>(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
+  launch_jacobi_setup<float>(s, c->pat, c->mod, c->n_s, c->n_t,
                              c->bsize, pblk, c->d_err);
   PcgVec<float> v = make_pcg<float>(c, c->f_x, c->f_r, c->f_z, c->f_p, c->f_q);
   v.tol2_dev = c->d_tol2;
@@ -1072,11 +1196,7 @@ static Err run_sampler_graph(qsel_ctx *c) {
   QSEL_CUDA_TRY(cudaMemsetAsync(c->d_q, 0, vec * sizeof(double), s));
   BtSpmmArgs<double> a{};
   a.pat = c->pat;
-  a.val = c->d_qs;
-  a.c0 = c->tc.a0;
-  a.c1 = c->tc.a1;
-  a.obs = c->d_obs;
-  a.obs_w = c->obs_w;
+  a.m = c->mod;
   a.n_s = c->n_s;
   a.n_t = c->n_t;
   a.ld = c->ld;
@@ -1138,16 +1258,12 @@ static Err run_sampler_lanczos(qsel_ctx *c) {
   }
   launch_philox_normals(s, c->opt.seed, 0u, c->n, c->k, c->ld, c->d_z1);
   QSEL_CUDA_TRY(cudaEventRecord(c->ev[1], s));
-  launch_bj_cholinv(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t, b, c->lz.linv,
+  launch_bj_cholinv(s, c->pat, c->mod, c->n_s, c->n_t, b, c->lz.linv,
                     c->d_err);
   LanczosArgs la{c->n, c->ld, c->k, m};
   BtSpmmArgs<double> sp{};
   sp.pat = c->pat;
-  sp.val = c->d_qs;
-  sp.c0 = c->tc.a0;
-  sp.c1 = c->tc.a1;
-  sp.obs = c->d_obs;
-  sp.obs_w = c->obs_w;
+  sp.m = c->mod;
   sp.n_s = c->n_s;
   sp.n_t = c->n_t;
   sp.ld = c->ld;
@@ -1203,6 +1319,13 @@ static Err run_sampler_lanczos(qsel_ctx *c) {
   return ok();
 }
 
+// The pattern values of the derivative blocks whose inner products with a
+// Sigma or Y block of global slab t the extraction forms.
+template <typename T>
+static void set_sum_vals(ExtractEntry<T> &xe, const BlockVals *bv, int n, int t) {
+  for (int j = 0; j < kMaxTheta; ++j) xe.sv[j] = j < n ? bv[j].at(t) : nullptr;
+}
+
 static void phase_mark(qsel_ctx *c, std::vector<std::pair<cudaEvent_t, int>> &marks, int phase) {
   if (c->graph_mode) return;
   cudaEvent_t e = c->phase_event();
@@ -1238,9 +1361,11 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       SchurEntry<T> &se = sb.e[sb.count++];
       se.W = (t > 0) ? buf(sl.W) : nullptr;
       se.D = Dinv(p, t);
-      se.a0 = c->tc.a0 + tg;
-      se.c = (t > 0) ? c->tc.a1 + tg - 1 : c->tc.a1;
-      se.obs = c->d_obs + (size_t)tg * n_s;
+      se.dval = c->mod.diag.at(tg);
+      se.a0 = c->mod.diag.scale_ptr(tg);
+      se.cval = (t > 0) ? c->mod.off.at(tg - 1) : nullptr;
+      se.c = (t > 0) ? c->mod.off.scale_ptr(tg - 1) : nullptr;
+      se.obs = c->mod.obs ? c->mod.obs + (size_t)tg * n_s : nullptr;
       wb.pivot_fp64 = c->opt.pivot_precision == QSEL_PIVOT_FP64 ? 1 : 0;
       SweepEntry<T> &we = wb.e[wb.count++];
       we.A = Dinv(p, t);
@@ -1254,19 +1379,21 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       we.Vp[1] = buf(sl.V2);
       we.Wp[1] = buf(sl.Wp2);
       we.Vk = buf(sl.Vk);
+      for (int q = 0; q < 4; ++q) we.Sp[q] = buf(sl.Sp[q]);
       if (t + 1 < sd.T) {
         SpEntry<T, T> &ge = gb.e[gb.count++];
         ge.B = Dinv(p, t);
         ge.C = nullptr;
         ge.Out = buf(sl.W);
-        ge.alpha_ptr = c->tc.a1 + tg;
+        ge.alpha_ptr = c->mod.off.scale_ptr(tg);
+        ge.val = c->mod.off.at(tg);
         ge.alpha = 1.0;
         ge.beta = 0.0;
       }
     }
-    launch_schur_assemble<T>(s, sb, c->pat, c->d_qs, c->obs_w, n_s, n_pad);
+    launch_schur_assemble<T>(s, sb, c->pat, c->mod.obs_w, n_s, n_pad);
     spd_inverse<T>(s, wb, n_pad, c->d_err, c->tc_passes, c->mixed ? &c->sweep_ss : nullptr);
-    launch_sp_rowgather<T, T>(s, gb, c->pat, c->d_qs, n_s, n_pad, n_pad, n_pad, n_pad);
+    launch_sp_rowgather<T, T>(s, gb, c->pat, n_s, n_pad, n_pad, n_pad, n_pad);
   }
   QSEL_CUDA_TRY(cudaGetLastError());
   phase_mark(c, marks, 0);
@@ -1280,11 +1407,12 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       ExtractEntry<T> &xe = xb.e[xb.count++];
       xe.S = Dinv(p, tl);
       xe.diag_out = c->d_selinv + (size_t)(sd.e0 + tl) * n_s;
-      xe.sums = c->d_sums + 2 * (size_t)(sd.slot_base + tl);
+      xe.sums = c->d_sums + kMaxTheta * (size_t)(sd.slot_base + tl);
+      set_sum_vals(xe, c->dmod.diag, c->dmod.n, sd.e0 + tl);
       xe.D0 = nullptr;
       xe.V = nullptr;
     }
-    launch_extract<T>(s, xb, c->pat, c->d_qs, c->d_dqs, n_s, n_pad, c->d_diag_scratch);
+    launch_extract<T>(s, xb, c->pat, c->dmod.n, n_s, n_pad, c->d_diag_scratch);
   }
   std::vector<T *> sig_next(p1 - p0, nullptr);
   std::vector<int> flip(p1 - p0, 0);
@@ -1313,7 +1441,8 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
           we.B = Dinv(p, tl);
           we.C = nullptr;
           we.Out = buf(sl.W);
-          we.alpha_ptr = c->tc.a1 + tg;
+          we.alpha_ptr = c->mod.off.scale_ptr(tg);
+          we.val = c->mod.off.at(tg);
           we.alpha = 1.0;
           we.beta = 0.0;
           GemmEntry<T> &ye = yb.e[yb.count++];
@@ -1328,7 +1457,8 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
             ExtractEntry<T> &xe = xy.e[xy.count++];
             xe.S = buf(sl.Y);   // <M, Y> = <M, Y^T> for symmetric M
             xe.diag_out = nullptr;
-            xe.sums = c->d_sums + 2 * (size_t)(sd.slot_base + sd.T + tl);
+            xe.sums = c->d_sums + kMaxTheta * (size_t)(sd.slot_base + sd.T + tl);
+            set_sum_vals(xe, c->dmod.off, c->dmod.n, tg);
             xe.D0 = nullptr;
             xe.V = nullptr;
           }
@@ -1347,7 +1477,8 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
               ExtractEntry<T> &xe = xs.e[xs.count++];
               xe.S = sig_cur;
               xe.diag_out = nullptr;
-              xe.sums = c->d_sums + 2 * (size_t)(sd.slot_base + tl);
+              xe.sums = c->d_sums + kMaxTheta * (size_t)(sd.slot_base + tl);
+              set_sum_vals(xe, c->dmod.diag, c->dmod.n, tg);
               xe.D0 = nullptr;
               xe.V = nullptr;
               DiagRowEntry<T> &de = db.e[db.count++];
@@ -1359,15 +1490,15 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
           }
         }
         if (active.empty()) break;
-        launch_sp_colgather<T>(s, wb, c->pat, c->d_qs, n_s, n_pad);
+        launch_sp_colgather<T>(s, wb, c->pat, n_s, n_pad);
         if (!launch_tc_gemm(s, yb, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, false, c->tc_passes, c->d_err))
           return fail(QSEL_ECUDA, "tensor-core GEMM: tensor map encoding failed");
-        launch_extract<T>(s, xy, c->pat, c->d_qs, c->d_dqs, n_s, n_pad, c->d_diag_scratch);
+        launch_extract<T>(s, xy, c->pat, c->dmod.n, n_s, n_pad, c->d_diag_scratch);
         if (!launch_tc_gemm(s, sgb, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, true, c->tc_passes, c->d_err))
           return fail(QSEL_ECUDA, "tensor-core GEMM: tensor map encoding failed");
         launch_diag64_rows<T>(s, db, n_s, n_pad);
         launch_mirror<T>(s, mb, n_pad);
-        launch_extract<T>(s, xs, c->pat, c->d_qs, c->d_dqs, n_s, n_pad, c->d_diag_scratch);
+        launch_extract<T>(s, xs, c->pat, c->dmod.n, n_s, n_pad, c->d_diag_scratch);
         for (int p : active) {
           Subdomain &sd = c->parts[p];
           DenseSlot &sl = slot(p);
@@ -1398,7 +1529,8 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       we.B = Dinv(p, tl);
       we.C = nullptr;
       we.Out = buf(sl.W);
-      we.alpha_ptr = c->tc.a1 + tg;
+      we.alpha_ptr = c->mod.off.scale_ptr(tg);
+      we.val = c->mod.off.at(tg);
       we.alpha = 1.0;
       we.beta = 0.0;
       GemmEntry<T> &ye = yb.e[yb.count++];
@@ -1413,7 +1545,8 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         ExtractEntry<T> &xe = xy.e[xy.count++];
         xe.S = buf(sl.Y);
         xe.diag_out = nullptr;
-        xe.sums = c->d_sums + 2 * (size_t)(sd.slot_base + sd.T + tl);
+        xe.sums = c->d_sums + kMaxTheta * (size_t)(sd.slot_base + sd.T + tl);
+        set_sum_vals(xe, c->dmod.off, c->dmod.n, tg);
         xe.D0 = nullptr;
         xe.V = nullptr;
       }
@@ -1423,7 +1556,8 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         ve.B = buf(sl.Y);
         ve.C = nullptr;
         ve.Out = buf(sl.V);
-        ve.alpha_ptr = c->tc.a1 + tg;
+        ve.alpha_ptr = c->mod.off.scale_ptr(tg);
+        ve.val = c->mod.off.at(tg);
         ve.alpha = 1.0;
         ve.beta = 0.0;
         GemmEntry<T> &ge = sgb.e[sgb.count++];
@@ -1439,7 +1573,8 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
           ExtractEntry<T> &xe = xs.e[xs.count++];
           xe.S = sig_cur;
           xe.diag_out = c->d_selinv + (size_t)tg * n_s;
-          xe.sums = c->d_sums + 2 * (size_t)(sd.slot_base + tl);
+          xe.sums = c->d_sums + kMaxTheta * (size_t)(sd.slot_base + tl);
+          set_sum_vals(xe, c->dmod.diag, c->dmod.n, tg);
           // mixed path: the Takahashi diagonal accumulated in double
           xe.D0 = c->mixed ? Dinv(p, tl) : nullptr;
           xe.V = c->mixed ? buf(sl.V) : nullptr;
@@ -1447,13 +1582,13 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       }
     }
     if (active.empty()) break;
-    launch_sp_rowgather<T, T>(s, wb, c->pat, c->d_qs, n_s, n_pad, n_pad, n_pad, n_pad);
+    launch_sp_rowgather<T, T>(s, wb, c->pat, n_s, n_pad, n_pad, n_pad, n_pad);
     launch_gemm<T>(s, yb, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, false);
-    launch_extract<T>(s, xy, c->pat, c->d_qs, c->d_dqs, n_s, n_pad, c->d_diag_scratch);
-    launch_sp_rowgather<T, T>(s, vb, c->pat, c->d_qs, n_s, n_pad, n_pad, n_pad, n_pad);
+    launch_extract<T>(s, xy, c->pat, c->dmod.n, n_s, n_pad, c->d_diag_scratch);
+    launch_sp_rowgather<T, T>(s, vb, c->pat, n_s, n_pad, n_pad, n_pad, n_pad);
     launch_gemm<T>(s, sgb, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, true);
     launch_mirror<T>(s, mb, n_pad);
-    launch_extract<T>(s, xs, c->pat, c->d_qs, c->d_dqs, n_s, n_pad, c->d_diag_scratch);
+    launch_extract<T>(s, xs, c->pat, c->dmod.n, n_s, n_pad, c->d_diag_scratch);
     for (int p : active) {
       Subdomain &sd = c->parts[p];
       DenseSlot &sl = slot(p);
@@ -1484,7 +1619,8 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         e.B = c->d_X + (size_t)sd.sep_left * n_s * ld;
         e.C = nullptr;
         e.Out = buf(sl.ybuf);
-        e.alpha_ptr = c->tc.a1 + sd.sep_left;
+        e.alpha_ptr = c->mod.off.scale_ptr(sd.sep_left);
+        e.val = c->mod.off.at(sd.sep_left);
         e.alpha = 1.0;
         e.beta = 0.0;
       } else {
@@ -1495,13 +1631,14 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         e.B = c->d_X + (size_t)sd.sep_right * n_s * ld;
         e.C = nullptr;
         e.Out = buf(sl.bright);
-        e.alpha_ptr = c->tc.a1 + sd.sep_right - 1;
+        e.alpha_ptr = c->mod.off.scale_ptr(sd.sep_right - 1);
+        e.val = c->mod.off.at(sd.sep_right - 1);
         e.alpha = 1.0;
         e.beta = 0.0;
       }
     }
-    launch_sp_rowgather<double, T>(s, bl, c->pat, c->d_qs, n_s, n_pad, ld, ld, ld);
-    launch_sp_rowgather<double, T>(s, br, c->pat, c->d_qs, n_s, n_pad, ld, ld, ld);
+    launch_sp_rowgather<double, T>(s, bl, c->pat, n_s, n_pad, ld, ld, ld);
+    launch_sp_rowgather<double, T>(s, br, c->pat, n_s, n_pad, ld, ld, ld);
     // D_t^-1 times an n_pad x ld block: on the tensor cores in the mixed path
     // (through the transposed product, with each part's ld x n_pad scratch
     // tra / trb), else the tile GEMM
@@ -1545,14 +1682,15 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
           const bool add_right = (t + 1 == sd.T - 1) && sd.sep_right >= 0;
           e.C = add_right ? buf(sl.bright) : nullptr;
           e.Out = buf(sl.ybuf);
-          e.alpha_ptr = c->tc.a1 + sd.e0 + t;
+          e.alpha_ptr = c->mod.off.scale_ptr(sd.e0 + t);
+          e.val = c->mod.off.at(sd.e0 + t);
           e.alpha = -1.0;
           e.beta = add_right ? 1.0 : 0.0;
         }
       }
       if (ub.count == 0) break;
       TRY(block_product(ub));
-      launch_sp_rowgather<T, T>(s, yb, c->pat, c->d_qs, n_s, n_pad, ld, ld, ld);
+      launch_sp_rowgather<T, T>(s, yb, c->pat, n_s, n_pad, ld, ld, ld);
     }
     for (int b = 0; b < maxT; ++b) {
       SpBatch<T, T> tb{};
@@ -1566,7 +1704,8 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         e.B = buf(sl.wbuf) + (size_t)(t + 1) * svec;
         e.C = nullptr;
         e.Out = buf(sl.tmp);
-        e.alpha_ptr = c->tc.a1 + sd.e0 + t;
+        e.alpha_ptr = c->mod.off.scale_ptr(sd.e0 + t);
+        e.val = c->mod.off.at(sd.e0 + t);
         e.alpha = 1.0;
         e.beta = 0.0;
         bt[wb.count] = sl.tra;
@@ -1580,7 +1719,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         g.beta = 1.0;
       }
       if (tb.count == 0) break;
-      launch_sp_rowgather<T, T>(s, tb, c->pat, c->d_qs, n_s, n_pad, ld, ld, ld);
+      launch_sp_rowgather<T, T>(s, tb, c->pat, n_s, n_pad, ld, ld, ld);
       TRY(block_product(wb));
     }
     CorrBatch<T> cb{};
@@ -1596,8 +1735,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       e.corr4_out = c->d_corr4;
       e.partial = sd.partial;
     }
-    launch_correction_terms<T>(s, cb, c->pat, c->d_qs, c->d_dqs, c->tc.a0, c->tc.a1, c->tc.r0, c->tc.r1, n_s,
-                               n_pad, ld, c->k);
+    launch_correction_terms<T>(s, cb, c->pat, c->dmod, n_s, n_pad, ld, c->k);
   }
   QSEL_CUDA_TRY(cudaGetLastError());
   phase_mark(c, marks, 2);
@@ -1696,8 +1834,8 @@ static Err run_pipeline_body(qsel_ctx *c) {
   }
   for (int p0 = first; p0 < np; p0 += c->wave) TRY(wave(p0, std::min(np, p0 + c->wave), 3));
   launch_sum(s, c->d_diag, c->d_selinv, c->d_corr, c->n);
-  launch_trace_combine(s, c->d_slabs, c->n_trace_slabs, c->d_sums, c->d_partials, np * corr_grid(), c->tc.a0,
-                       c->tc.a1, c->tc.r0, c->tc.r1, c->d_traces);
+  launch_trace_combine(s, c->d_slabs, c->n_trace_slabs, c->d_sums, c->d_partials, np * corr_grid(), c->dmod,
+                       c->d_traces);
   QSEL_CUDA_TRY(cudaEventRecord(c->ev[3], s));
   QSEL_CUDA_TRY(cudaStreamSynchronize(s));
   QSEL_CUDA_TRY(cudaGetLastError());
@@ -1752,8 +1890,8 @@ static Err enqueue_pipeline_graph(qsel_ctx *c) {
       TRY(run_wave<double>(c, p0, p1, marks));
   }
   launch_sum(s, c->d_diag, c->d_selinv, c->d_corr, c->n);
-  launch_trace_combine(s, c->d_slabs, c->n_trace_slabs, c->d_sums, c->d_partials, np * corr_grid(), c->tc.a0,
-                       c->tc.a1, c->tc.r0, c->tc.r1, c->d_traces);
+  launch_trace_combine(s, c->d_slabs, c->n_trace_slabs, c->d_sums, c->d_partials, np * corr_grid(), c->dmod,
+                       c->d_traces);
   QSEL_CUDA_TRY(cudaGetLastError());
   return ok();
 }
@@ -1883,6 +2021,30 @@ static double model_cost(const qsel_ctx *c) {
 // ---------------------------------------------------------------------------
 extern "C" {
 
+// Sizes and the option-derived settings of a new context.
+static Err init_options(qsel_ctx *c, int n_s, int n_t, const qsel_options *opt, int slot_cap) {
+  c->n_s = n_s;
+  c->n_t = n_t;
+  c->n = n_s * n_t;
+  c->k = opt->n_samples;
+  c->ld = round_up(opt->n_samples, kColPad);
+  c->n_pad = round_up(n_s, kTile);
+  c->opt = *opt;
+  c->bsize = opt->precond_block == 0 ? 64 : opt->precond_block;
+  c->mixed = opt->precision == QSEL_MIXED;
+  if (c->mixed) {
+    if (opt->tensor_passes == 0)
+      c->tc_passes = tc_gemm_available() ? 3 : 0;
+    else if (opt->tensor_passes > 0)
+      c->tc_passes = opt->tensor_passes;
+    if (c->tc_passes > 0 && !tc_gemm_available())
+      return fail(QSEL_EINVAL, "tensor_passes requested but tcgen05 tensor-core GEMMs are not available on this device");
+  }
+  c->stream = reinterpret_cast<cudaStream_t>(opt->cuda_stream);
+  c->slot_cap = slot_cap;
+  return ok();
+}
+
 static qsel_status create_ctx(qsel_ctx **out, const qsel_model *model, const qsel_theta *theta,
                               const qsel_partition *partition, int32_t overlap, const qsel_options *opt,
                               int slot_cap) {
@@ -1901,31 +2063,16 @@ static qsel_status create_ctx(qsel_ctx **out, const qsel_model *model, const qse
     g_create_error = "host allocation failed";
     return QSEL_ENOMEM;
   }
-  c->n_s = model->n_s;
-  c->n_t = model->n_t;
-  c->n = model->n_s * model->n_t;
-  c->k = opt->n_samples;
-  c->ld = round_up(opt->n_samples, kColPad);
-  c->n_pad = round_up(model->n_s, kTile);
   c->sigma = model->sigma;
   c->obs_w = 1.0 / (model->sigma * model->sigma);
   c->theta = *theta;
-  c->opt = *opt;
-  c->bsize = opt->precond_block == 0 ? 64 : opt->precond_block;
-  c->mixed = opt->precision == QSEL_MIXED;
-  if (c->mixed) {
-    if (opt->tensor_passes == 0)
-      c->tc_passes = tc_gemm_available() ? 3 : 0;
-    else if (opt->tensor_passes > 0)
-      c->tc_passes = opt->tensor_passes;
-    if (c->tc_passes > 0 && !tc_gemm_available()) {
-      g_create_error = "tensor_passes requested but tcgen05 tensor-core GEMMs are not available on this device";
-      delete c;
-      return QSEL_EINVAL;
-    }
+  c->model_kind = opt->model;
+  e = init_options(c, model->n_s, model->n_t, opt, slot_cap);
+  if (e.code) {
+    g_create_error = e.msg;
+    delete c;
+    return (qsel_status)e.code;
   }
-  c->stream = reinterpret_cast<cudaStream_t>(opt->cuda_stream);
-  c->slot_cap = slot_cap;
   e = build(c, model, partition, overlap);
   if (e.code) {
     g_create_error = e.msg;
@@ -1943,10 +2090,164 @@ qsel_status qsel_create(qsel_ctx **out, const qsel_model *model, const qsel_thet
 
 qsel_status qsel_set_theta(qsel_ctx *ctx, const qsel_theta *theta) {
   if (!ctx || !theta) return QSEL_EINVAL;
+  if (ctx->model_kind == QSEL_MODEL_BLOCK_TRIDIAGONAL)
+    return finish(ctx, fail(QSEL_EINVAL, "a user-given matrix has no theta: use qsel_set_bt_values"));
   if (!std::isfinite(theta->log_kappa) || !std::isfinite(theta->log_tau) ||
       !std::isfinite(theta->logit_rho) || std::fabs(theta->logit_rho) > 36.0)
     return finish(ctx, fail(QSEL_EINVAL, "theta must be finite with |logit rho| <= 36"));
   ctx->theta = *theta;
+  ctx->computed = false;
+  ctx->injected = false;
+  ctx->have_rhs = false;
+  return QSEL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// User-given block-tridiagonal precision
+// ---------------------------------------------------------------------------
+// Values of a user-given matrix in the SELL layout: every CSR entry of every
+// block is copied to its slot (ctx->bt_slot), padding slots stay zero.
+// Checks that every block is symmetric and finite.
+static Err bt_upload_values(qsel_ctx *c, const double *diag_vals, const double *off_vals, const double *ddiag,
+                            const double *doff) {
+  const int n_t = c->n_t, n_theta = c->dmod.n;
+  const int64_t nnz = (int64_t)c->bt_slot.size(), ne = c->n_ent;
+  if (!diag_vals || (n_t > 1 && !off_vals) || (n_theta > 0 && (!ddiag || (n_t > 1 && !doff))))
+    return fail(QSEL_EINVAL, "block value arrays must not be NULL");
+  // blocks: A_t (n_t), B_t (n_t - 1), then per theta_j dA_j (n_t), dB_j (n_t - 1)
+  const int64_t per_set = (int64_t)(2 * n_t - 1);
+  std::vector<double> sell((size_t)(per_set * (1 + n_theta)) * ne, 0.0);
+  auto put = [&](const double *src, int64_t nblk, int64_t dst_blk) -> bool {
+    for (int64_t b = 0; b < nblk; ++b) {
+      const double *v = src + b * nnz;
+      for (int64_t q = 0; q < nnz; ++q) {
+        const double w = v[c->bt_mirror[q]];
+        if (!std::isfinite(v[q]) || std::fabs(v[q] - w) > 1e-12 * (std::fabs(v[q]) + std::fabs(w))) return false;
+        sell[(size_t)((dst_blk + b) * ne + c->bt_slot[q])] = v[q];
+      }
+    }
+    return true;
+  };
+  bool good = put(diag_vals, n_t, 0) && put(off_vals, n_t - 1, n_t);
+  for (int j = 0; good && j < n_theta; ++j)
+    good = put(ddiag + (int64_t)j * n_t * nnz, n_t, per_set * (1 + j)) &&
+           put(doff + (int64_t)j * (n_t - 1) * nnz, n_t - 1, per_set * (1 + j) + n_t);
+  if (!good) return fail(QSEL_EINVAL, "block values must be finite and every block symmetric (to 1e-12 relative)");
+  QSEL_CUDA_TRY(cudaMemcpy(c->d_blk, sell.data(), sell.size() * sizeof(double), cudaMemcpyHostToDevice));
+  return ok();
+}
+
+static Err build_bt(qsel_ctx *c, const qsel_bt_model *m, const qsel_partition *part, int32_t overlap) {
+  const int n_s = m->n_s;
+  const int64_t nnz = m->rowptr[n_s];
+  // pattern rows (column -> CSR position) and the mirror position of every entry
+  PatRows rows(n_s);
+  std::vector<std::map<int, int64_t>> pos(n_s);
+  for (int i = 0; i < n_s; ++i)
+    for (int64_t q = m->rowptr[i]; q < m->rowptr[i + 1]; ++q) {
+      const int j = m->col[q];
+      if (pos[i].count(j)) return fail(QSEL_EINVAL, "the pattern repeats an entry");
+      pos[i][j] = q;
+      rows[i].emplace(j, std::array<double, 4>{(double)q, 0.0, 0.0, 0.0});
+    }
+  c->bt_mirror.assign((size_t)nnz, 0);
+  for (int i = 0; i < n_s; ++i) {
+    if (!pos[i].count(i)) return fail(QSEL_EINVAL, "every row of the pattern needs its diagonal entry");
+    for (auto &kv : pos[i]) {
+      auto it = pos[kv.first].find(i);
+      if (it == pos[kv.first].end()) return fail(QSEL_EINVAL, "the pattern must be symmetric");
+      c->bt_mirror[(size_t)kv.second] = it->second;
+    }
+  }
+  std::vector<std::vector<double>> sell;
+  TRY(build_pattern(c, rows, 1, sell));   // sell[0][slot] = CSR position (or 0 for padding)
+  c->bt_slot.assign((size_t)nnz, 0);
+  {
+    std::vector<int32_t> col(c->n_ent);
+    QSEL_CUDA_TRY(cudaMemcpy(col.data(), c->pat.col, c->n_ent * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> sp(c->pat.n_slices + 1), sw(c->pat.n_slices);
+    QSEL_CUDA_TRY(cudaMemcpy(sp.data(), c->pat.slice_ptr, sp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    QSEL_CUDA_TRY(cudaMemcpy(sw.data(), c->pat.slice_width, sw.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n_s; ++i) {
+      const int sl = i / kSlice, li = i % kSlice;
+      int slot = 0;
+      for (auto &kv : pos[i]) c->bt_slot[(size_t)kv.second] = sp[sl] + (slot++) * kSlice + li;
+    }
+  }
+  const int n_theta = m->n_theta;
+  const int64_t per_set = (int64_t)(2 * c->n_t - 1) * c->n_ent;
+  TRY(c->alloc(&c->d_blk, (size_t)(per_set * (1 + n_theta))));
+  c->dmod.n = n_theta;
+  c->mod.diag = BlockVals{c->d_blk, c->n_ent, nullptr};
+  c->mod.off = BlockVals{c->d_blk + (int64_t)c->n_t * c->n_ent, c->n_ent, nullptr};
+  c->mod.obs = nullptr;
+  c->mod.obs_w = 0.0;
+  for (int j = 0; j < n_theta; ++j) {
+    double *base = c->d_blk + per_set * (1 + j);
+    c->dmod.diag[j] = BlockVals{base, c->n_ent, nullptr};
+    c->dmod.off[j] = BlockVals{base + (int64_t)c->n_t * c->n_ent, c->n_ent, nullptr};
+  }
+  TRY(bt_upload_values(c, m->diag_vals, m->off_vals, m->ddiag_vals, m->doff_vals));
+  RestInputs in;
+  in.adj.resize(n_s);
+  for (int i = 0; i < n_s; ++i)
+    for (auto &kv : pos[i]) in.adj[i].push_back(kv.first);
+  return build_rest(c, in, part, overlap);
+}
+
+qsel_status qsel_create_bt(qsel_ctx **out, const qsel_bt_model *model, const qsel_partition *partition,
+                           int32_t overlap, const qsel_options *opt) {
+  if (!out) {
+    g_create_error = "out must not be NULL";
+    return QSEL_EINVAL;
+  }
+  *out = nullptr;
+  auto bad = [&](const std::string &msg) {
+    g_create_error = "qsel_create_bt: " + msg;
+    return QSEL_EINVAL;
+  };
+  if (!model || !opt) return bad("model and options must not be NULL");
+  if (model->n_s < 1 || model->n_t < 1) return bad("n_s and n_t must be >= 1");
+  if ((int64_t)model->n_s * model->n_t > (int64_t)1 << 30) return bad("n_s * n_t too large");
+  if (!model->rowptr || !model->col) return bad("the pattern arrays must not be NULL");
+  if (model->n_theta < 0 || model->n_theta > kMaxTheta) return bad("n_theta must be in [0, 4]");
+  if (model->rowptr[0] != 0) return bad("rowptr[0] must be 0");
+  for (int i = 0; i < model->n_s; ++i) {
+    if (model->rowptr[i + 1] < model->rowptr[i]) return bad("rowptr must be non-decreasing");
+    for (int32_t q = model->rowptr[i]; q < model->rowptr[i + 1]; ++q)
+      if (model->col[q] < 0 || model->col[q] >= model->n_s) return bad("col out of range");
+  }
+  if (opt->sampler != QSEL_SAMPLER_LANCZOS) return bad("a user-given matrix needs sampler = QSEL_SAMPLER_LANCZOS");
+  if (opt->preconditioner != QSEL_PRECOND_BLOCK_JACOBI) return bad("a user-given matrix takes block Jacobi");
+  Err e = validate_options(model->n_t, partition, overlap, opt);
+  if (e.code) {
+    g_create_error = "qsel_create_bt: " + e.msg;
+    return (qsel_status)e.code;
+  }
+  qsel_ctx *c = new (std::nothrow) qsel_ctx();
+  if (!c) {
+    g_create_error = "host allocation failed";
+    return QSEL_ENOMEM;
+  }
+  c->model_kind = QSEL_MODEL_BLOCK_TRIDIAGONAL;
+  e = init_options(c, model->n_s, model->n_t, opt, kMaxBatch);
+  if (e.code == 0) e = build_bt(c, model, partition, overlap);
+  if (e.code) {
+    g_create_error = "qsel_create_bt: " + e.msg;
+    delete c;
+    return (qsel_status)e.code;
+  }
+  *out = c;
+  return QSEL_OK;
+}
+
+qsel_status qsel_set_bt_values(qsel_ctx *ctx, const double *diag_vals, const double *off_vals,
+                               const double *ddiag_vals, const double *doff_vals) {
+  if (!ctx) return QSEL_EINVAL;
+  if (ctx->model_kind != QSEL_MODEL_BLOCK_TRIDIAGONAL)
+    return finish(ctx, fail(QSEL_EINVAL, "qsel_set_bt_values needs a context made by qsel_create_bt"));
+  Err e = bt_upload_values(ctx, diag_vals, off_vals, ddiag_vals, doff_vals);
+  if (e.code) return finish(ctx, e);
   ctx->computed = false;
   ctx->injected = false;
   ctx->have_rhs = false;
@@ -1980,25 +2281,34 @@ qsel_status qsel_diag_inv(qsel_ctx *ctx, double *diag_out, int32_t out_is_device
   return QSEL_OK;
 }
 
-qsel_status qsel_trace_grads(qsel_ctx *ctx, double grads_out[3]) {
+static qsel_status trace_grads(qsel_ctx *ctx, double *grads_out, int n) {
   if (!ctx) return QSEL_EINVAL;
   if (!grads_out) return finish(ctx, fail(QSEL_EINVAL, "grads_out must not be NULL"));
+  if (n != ctx->dmod.n)
+    return finish(ctx, fail(QSEL_EINVAL, "the context has " + std::to_string(ctx->dmod.n) + " trace gradients"));
   if (ctx->n_l < 1 && ctx->parts.size() > 1)
     return finish(ctx, fail(QSEL_EINVAL, "trace gradients need overlap >= 1 when there are several parts"));
   Err e = ensure(ctx);
   if (e.code) return finish(ctx, e);
-  cudaError_t ce = cudaMemcpyAsync(ctx->h_small, ctx->d_traces, 3 * sizeof(double),
-                                   cudaMemcpyDeviceToHost, ctx->stream);
+  if (n == 0) return QSEL_OK;
+  cudaError_t ce = cudaMemcpyAsync(ctx->h_small, ctx->d_traces, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                   ctx->stream);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
   if (ce != cudaSuccess) return finish(ctx, cuda_fail(ce, "copy of traces", __FILE__, __LINE__));
-  for (int j = 0; j < 3; ++j) grads_out[j] = ctx->h_small[j];
+  for (int j = 0; j < n; ++j) grads_out[j] = ctx->h_small[j];
   return QSEL_OK;
 }
+
+qsel_status qsel_trace_grads(qsel_ctx *ctx, double grads_out[3]) { return trace_grads(ctx, grads_out, 3); }
+
+qsel_status qsel_trace_grads_n(qsel_ctx *ctx, double *grads_out, int32_t n) { return trace_grads(ctx, grads_out, n); }
 
 // ---------------------------------------------------------------------------
 // Posterior mean and the gradient of the hyperparameter marginal (hyper.cu).
 // ---------------------------------------------------------------------------
 qsel_status qsel_set_data(qsel_ctx *ctx, const double *y_obs) {
+  if (ctx && ctx->model_kind != QSEL_MODEL_SEPARABLE)
+    return finish(ctx, fail(QSEL_EINVAL, "the posterior-mean and hyperparameter calls serve the separable model"));
   if (!ctx) return QSEL_EINVAL;
   qsel_ctx *c = ctx;
   if (!y_obs) return finish(c, fail(QSEL_EINVAL, "y_obs must not be NULL"));
@@ -2015,6 +2325,8 @@ qsel_status qsel_set_data(qsel_ctx *ctx, const double *y_obs) {
 }
 
 qsel_status qsel_set_covariates(qsel_ctx *ctx, int32_t n_beta, const double *Z, double beta_prec) {
+  if (ctx && ctx->model_kind != QSEL_MODEL_SEPARABLE)
+    return finish(ctx, fail(QSEL_EINVAL, "the posterior-mean and hyperparameter calls serve the separable model"));
   if (!ctx) return QSEL_EINVAL;
   qsel_ctx *c = ctx;
   if (n_beta < 0 || n_beta > 63 || n_beta + 1 > c->ld)
@@ -2150,8 +2462,6 @@ qsel_status qsel_loglik_grad(qsel_ctx *ctx, double grad_out[3], double terms_out
   // coefficients (no observation term), its per-column dot partials with mu
   BtSpmmArgs<double> a{};
   a.pat = c->pat;
-  a.obs = nullptr;
-  a.obs_w = 0.0;
   a.n_s = c->n_s;
   a.n_t = c->n_t;
   a.ld = c->ld;
@@ -2159,13 +2469,9 @@ qsel_status qsel_loglik_grad(qsel_ctx *ctx, double grad_out[3], double terms_out
   a.y = c->d_q;
   a.dot_partial = c->d_pa;
   a.tmp = c->d_z1;
-  const double *vals[3] = {c->d_dqs, c->d_qs, c->d_qs};
-  const double *c0s[3] = {c->tc.a0, c->tc.a0, c->tc.r0};
-  const double *c1s[3] = {c->tc.a1, c->tc.a1, c->tc.r1};
   for (int j = 0; j < 3; ++j) {
-    a.val = vals[j];
-    a.c0 = c0s[j];
-    a.c1 = c1s[j];
+    a.m.diag = c->dmod.diag[j];   // dQ_j: no observation term
+    a.m.off = c->dmod.off[j];
     launch_bt_spmm<double>(s, a);
     launch_column_sum(s, c->d_pa, bt_spmm_grid(c->n), c->ld, 0, c->d_hyp + j);
     // fixed effects: tr(S^-1 W^T dQ_j W) from the same product
@@ -2312,7 +2618,7 @@ static Err cv_features_sepd(qsel_ctx *c, const std::vector<float> &sepd, float *
   TRY(run_model(c));
   QSEL_CUDA_TRY(cudaMemcpyAsync(c->d_sepd, sepd.data(), c->n_t * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   const double th[3] = {c->theta.log_kappa, c->theta.log_tau, c->theta.logit_rho};
-  launch_cv_features(c->stream, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t, c->d_sepd,
+  launch_cv_features(c->stream, c->pat, c->mod, c->n_s, c->n_t, c->d_sepd,
                      c->d_bnd, th, F_dev);
   QSEL_CUDA_TRY(cudaStreamSynchronize(c->stream));   // sepd is a host vector
   QSEL_CUDA_TRY(cudaGetLastError());
@@ -2750,7 +3056,7 @@ qsel_status qsel_debug_apply_precond(qsel_ctx *ctx, const double *R, double *Z, 
   if (e.code) return finish(c, e);
   double *pblk = static_cast<double *>(c->d_pblk);
   if (!c->kron)
-    launch_jacobi_setup<double>(s, c->pat, c->d_qs, c->tc.a0, c->tc.a1, c->d_obs, c->obs_w, c->n_s, c->n_t,
+    launch_jacobi_setup<double>(s, c->pat, c->mod, c->n_s, c->n_t,
                                 c->bsize, pblk, c->d_err);
   const size_t vec = (size_t)c->n * c->ld;
   cudaError_t ce = cudaMemsetAsync(c->d_r, 0, vec * sizeof(double), s);

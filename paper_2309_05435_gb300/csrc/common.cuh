@@ -39,6 +39,39 @@ struct SellPattern {
   const int32_t *col = nullptr;         // entries
 };
 
+// Spatial blocks of a block-tridiagonal precision on the common SELL pattern:
+// block t has the entries scale(t) * v[t * stride + e] (stride 0: one array
+// for every block, scaled per block by coef; coef null: scale 1).  The
+// separable model stores Q_s once with the time coefficients as scales; the
+// diffusion model and user-given block-tridiagonal matrices store one array
+// per block.
+struct BlockVals {
+  const double *v = nullptr;
+  int64_t stride = 0;
+  const double *coef = nullptr;
+  __host__ __device__ const double *at(int t) const { return v + (int64_t)t * stride; }
+  __host__ __device__ const double *scale_ptr(int t) const { return coef ? coef + t : nullptr; }
+#ifdef __CUDACC__
+  __device__ double scale(int t) const { return coef ? coef[t] : 1.0; }
+#endif
+};
+// A block-tridiagonal precision with symmetric blocks on one spatial pattern:
+// diagonal blocks A_t (t < n_t) plus obs_w on the diagonal of observed nodes,
+// couplings B_t = Q[t, t+1] = Q[t+1, t] (t < n_t - 1).
+struct BtModel {
+  BlockVals diag, off;
+  const uint8_t *obs = nullptr;   // may be null: no observation diagonal
+  double obs_w = 0.0;
+};
+// Largest number of hyperparameters with a trace gradient.
+constexpr int kMaxTheta = 4;
+// dQ/dtheta_j as block-tridiagonal matrices on the same pattern (no
+// observation term).
+struct DerivModels {
+  BlockVals diag[kMaxTheta], off[kMaxTheta];
+  int n = 0;
+};
+
 // Theta-dependent scalars of the time structure, written by a device kernel.
 //   a0[t] = tau Q_t[t,t], a1[t] = tau Q_t[t,t+1]
 //   r0[t], r1[t]: the same for d/dlogit rho

@@ -694,21 +694,40 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
           if (p + 1 < n_panels) cudaStreamWaitEvent(lo, ss->gather, 0);
         }
         if (nt > bw) {
-          GemmBatch<float> gb{};
-          gb.count = b.count;
-          for (int e = 0; e < b.count; ++e) {
-            gb.e[e].A = b.e[e].Up[cur];
-            gb.e[e].B = b.e[e].Vp[cur];
-            gb.e[e].C0 = b.e[e].A;
-            gb.e[e].C = b.e[e].A;
-            gb.e[e].alpha = -1.0;
-            gb.e[e].beta = 1.0;
-          }
           // algorithmic work: the rank-64 bw update of the lower tiles off the
           // panel's rows and columns
           const double rest = (double)(nt - bw) * (nt - bw + 1) / 2.0;
-          tc_update(lo, gb, n_pad, n_pad, 64 * bw, n_pad, true, PROF_SWEEP,
-                    2.0 * 64.0 * 64.0 * 64.0 * bw * rest * b.count);
+          const double work = 2.0 * 64.0 * 64.0 * 64.0 * bw * rest * b.count;
+          if (tc_passes == 3 && b.e[0].Sp[0] != nullptr) {
+            // U and V split once per panel, then the persistent 3xTF32 update
+            {
+              ProfScope ps_(lo, PROF_PANEL);
+              for (int e = 0; e < b.count; ++e) {
+                launch_split_tf32(lo, b.e[e].Up[cur], b.e[e].Sp[0], b.e[e].Sp[1], (int64_t)n_pad * ldw);
+                launch_split_tf32(lo, b.e[e].Vp[cur], b.e[e].Sp[2], b.e[e].Sp[3], (int64_t)n_pad * ldw);
+              }
+            }
+            UpdateBatch ub{};
+            ub.count = b.count;
+            for (int e = 0; e < b.count; ++e)
+              ub.e[e] = UpdateEntry{b.e[e].Sp[0], b.e[e].Sp[1], b.e[e].Sp[2], b.e[e].Sp[3], b.e[e].A};
+            Profiler::Rec rec{PROF_SWEEP, nullptr, nullptr, work};
+            if (g_prof) g_prof->begin(lo, rec);
+            launch_tc_update(lo, ub, n_pad, 64 * bw, ldw, -1.0f, 1.0f, err_flag);
+            if (g_prof) g_prof->end(lo, rec);
+          } else {
+            GemmBatch<float> gb{};
+            gb.count = b.count;
+            for (int e = 0; e < b.count; ++e) {
+              gb.e[e].A = b.e[e].Up[cur];
+              gb.e[e].B = b.e[e].Vp[cur];
+              gb.e[e].C0 = b.e[e].A;
+              gb.e[e].C = b.e[e].A;
+              gb.e[e].alpha = -1.0;
+              gb.e[e].beta = 1.0;
+            }
+            tc_update(lo, gb, n_pad, n_pad, 64 * bw, n_pad, true, PROF_SWEEP, work);
+          }
         }
         ++g_launch_count;
         {
@@ -770,17 +789,18 @@ template void launch_mirror<double>(cudaStream_t, const SweepBatch<double> &, in
 template void launch_mirror<float>(cudaStream_t, const SweepBatch<float> &, int);
 
 // ---------------------------------------------------------------------------
-// Out = alpha Q_s B + beta C on the spatial pattern (row gather): one warp per
+// Out = alpha M B + beta C on the spatial pattern (row gather; M = the entry's
+// symmetric spatial block, values e.val): one warp per
 // row, the row's pattern entries staged once in the warp's shared slots, then
 // four 64-column chunks at a time (2 elements per lane per chunk, eight
 // independent loads per pattern entry).  Accumulation in the output type.
 // ---------------------------------------------------------------------------
 template <typename TI, typename TO>
-__global__ void __launch_bounds__(256) k_sp_rowgather(SpBatch<TI, TO> bt, SellPattern pat,
-                                                      const double *__restrict__ val, int n_s,
-                                                      int n_pad, int ncol, int ldb, int ldo) {
+__global__ void __launch_bounds__(256) k_sp_rowgather(SpBatch<TI, TO> bt, SellPattern pat, int n_s, int n_pad,
+                                                      int ncol, int ldb, int ldo) {
   extern __shared__ __align__(16) unsigned char rg_smem[];
   const SpEntry<TI, TO> e = bt.e[blockIdx.y];
+  const double *__restrict__ val = e.val;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int *w_col = reinterpret_cast<int *>(rg_smem) + warp * pat.max_width;
   TO *w_val = reinterpret_cast<TO *>(reinterpret_cast<int *>(rg_smem) + 8 * pat.max_width) + warp * pat.max_width;
@@ -837,8 +857,8 @@ __global__ void __launch_bounds__(256) k_sp_rowgather(SpBatch<TI, TO> bt, SellPa
 }
 
 template <typename TI, typename TO>
-void launch_sp_rowgather(cudaStream_t s, const SpBatch<TI, TO> &b, const SellPattern &pat, const double *val,
-                         int n_s, int n_pad, int ncol, int ldb, int ldo) {
+void launch_sp_rowgather(cudaStream_t s, const SpBatch<TI, TO> &b, const SellPattern &pat, int n_s, int n_pad,
+                         int ncol, int ldb, int ldo) {
   if (b.count <= 0) return;
   ++g_launch_count;
   int grid = (n_pad + 7) / 8;
@@ -846,15 +866,15 @@ void launch_sp_rowgather(cudaStream_t s, const SpBatch<TI, TO> &b, const SellPat
   const size_t smem = (size_t)8 * pat.max_width * (sizeof(int) + sizeof(TO));
   {
     ProfScope ps_(s, PROF_GATHER);
-    k_sp_rowgather<TI, TO><<<dim3(grid, b.count), 256, smem, s>>>(b, pat, val, n_s, n_pad, ncol, ldb, ldo);
+    k_sp_rowgather<TI, TO><<<dim3(grid, b.count), 256, smem, s>>>(b, pat, n_s, n_pad, ncol, ldb, ldo);
   }
 }
 template void launch_sp_rowgather<double, double>(cudaStream_t, const SpBatch<double, double> &,
-                                                  const SellPattern &, const double *, int, int, int, int, int);
+                                                  const SellPattern &, int, int, int, int, int);
 template void launch_sp_rowgather<float, float>(cudaStream_t, const SpBatch<float, float> &, const SellPattern &,
-                                                const double *, int, int, int, int, int);
+                                                int, int, int, int, int);
 template void launch_sp_rowgather<double, float>(cudaStream_t, const SpBatch<double, float> &,
-                                                 const SellPattern &, const double *, int, int, int, int, int);
+                                                 const SellPattern &, int, int, int, int, int);
 
 // ---------------------------------------------------------------------------
 // Column gathers over the symmetric pattern, (B Q_s)[r, l] =
@@ -884,18 +904,18 @@ size_t col_pattern_smem(const SellPattern &pat) {
   return (size_t)pat.max_width * 256 * (sizeof(int) + sizeof(T));
 }
 
-// Out = alpha B Q_s + beta C; rows and columns past n_s of Out are zero.  With
-// B = D^-1 (symmetric) this is (Q_s D^-1)^T.
+// Out = alpha B M + beta C (M = the entry's symmetric spatial block); rows and
+// columns past n_s of Out are zero.  With B = D^-1 (symmetric) this is
+// (M D^-1)^T.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sp_colgather(SpBatch<T, T> bt, SellPattern pat,
-                                                      const double *__restrict__ val, int n_s, int n_pad) {
+__global__ void __launch_bounds__(256) k_sp_colgather(SpBatch<T, T> bt, SellPattern pat, int n_s, int n_pad) {
   extern __shared__ __align__(16) unsigned char cg_smem[];
   int *s_col = reinterpret_cast<int *>(cg_smem);
   T *s_val = reinterpret_cast<T *>(s_col + pat.max_width * 256);
   const SpEntry<T, T> e = bt.e[blockIdx.z];
   const int l = blockIdx.x * 256 + threadIdx.x;
   if (l >= n_pad) return;
-  const int w = stage_col_pattern(pat, val, l, n_s, s_col, s_val);
+  const int w = stage_col_pattern(pat, e.val, l, n_s, s_col, s_val);
   const T alpha = (T)(e.alpha * (e.alpha_ptr ? *e.alpha_ptr : 1.0));
   const bool add_c = e.C != nullptr && e.beta != 0.0;
   const int r1 = min(n_pad, (int)(blockIdx.y + 1) * kGatherRows);
@@ -913,20 +933,18 @@ __global__ void __launch_bounds__(256) k_sp_colgather(SpBatch<T, T> bt, SellPatt
 }
 
 template <typename T>
-void launch_sp_colgather(cudaStream_t s, const SpBatch<T, T> &b, const SellPattern &pat, const double *val,
-                         int n_s, int n_pad) {
+void launch_sp_colgather(cudaStream_t s, const SpBatch<T, T> &b, const SellPattern &pat, int n_s, int n_pad) {
   if (b.count <= 0) return;
   ++g_launch_count;
   dim3 grid((n_pad + 255) / 256, (n_pad + kGatherRows - 1) / kGatherRows, b.count);
   {
     ProfScope ps_(s, PROF_GATHER);
-    k_sp_colgather<T><<<grid, 256, col_pattern_smem<T>(pat), s>>>(b, pat, val, n_s, n_pad);
+    k_sp_colgather<T><<<grid, 256, col_pattern_smem<T>(pat), s>>>(b, pat, n_s, n_pad);
   }
 }
-template void launch_sp_colgather<double>(cudaStream_t, const SpBatch<double, double> &, const SellPattern &,
-                                          const double *, int, int);
-template void launch_sp_colgather<float>(cudaStream_t, const SpBatch<float, float> &, const SellPattern &,
-                                         const double *, int, int);
+template void launch_sp_colgather<double>(cudaStream_t, const SpBatch<double, double> &, const SellPattern &, int,
+                                          int);
+template void launch_sp_colgather<float>(cudaStream_t, const SpBatch<float, float> &, const SellPattern &, int, int);
 
 // diag_out[i] = D0[i, i] + sum_l P[i, l] R[i, l] accumulated in double (one
 // warp per row, coalesced along the row): the diagonal of
@@ -958,10 +976,11 @@ template void launch_diag64_rows<double>(cudaStream_t, const DiagRowBatch<double
 template void launch_diag64_rows<float>(cudaStream_t, const DiagRowBatch<float> &, int, int);
 
 // ---------------------------------------------------------------------------
-// D = a0 Q_s + w_obs diag(obs) - c W Q_s (column gather over the symmetric
-// pattern: (W Q_s)[r, l] = sum_{j in pat(l)} W[r, j] Q_s[l, j]), blocked and
-// staged like k_sp_colgather.  The Schur term accumulates in T.  Entries off
-// the pattern of Q_s are -c times the Schur sum in T; afterwards each thread
+// D = a0 A_t + w_obs diag(obs) - c W B (column gather over the symmetric
+// pattern: (W B)[r, l] = sum_{j in pat(l)} W[r, j] B[l, j], B = the coupling
+// B_{t-1} without its scale c), blocked and staged like k_sp_colgather.  The
+// Schur term accumulates in T.  Entries off the pattern are -c times the
+// Schur sum in T; afterwards each thread
 // rewrites the entries of its column on the pattern (and the diagonal), at
 // most max_width of them, combining the terms in double.  Keeping that path
 // out of the row loop keeps the FP64 pipe out of the common case.
@@ -974,17 +993,17 @@ __device__ __forceinline__ T schur_sum(const T *__restrict__ Wr, int w, const in
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch<T> bt, SellPattern pat,
-                                                        const double *__restrict__ qs, double obs_w,
-                                                        int n_s, int n_pad) {
+__global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch<T> bt, SellPattern pat, double obs_w, int n_s,
+                                                        int n_pad) {
   extern __shared__ __align__(16) unsigned char sa_smem[];
   int *s_col = reinterpret_cast<int *>(sa_smem);
   T *s_val = reinterpret_cast<T *>(s_col + pat.max_width * 256);
   const SchurEntry<T> e = bt.e[blockIdx.z];
   const int l = blockIdx.x * 256 + threadIdx.x;
   if (l >= n_pad) return;
-  const int w = stage_col_pattern(pat, qs, l, n_s, s_col, s_val);
-  const T neg_c = e.W ? (T)(-*e.c) : T(0);
+  const int w = stage_col_pattern(pat, e.W ? e.cval : e.dval, l, n_s, s_col, s_val);
+  const double *__restrict__ dval = e.dval;
+  const T neg_c = e.W ? (T)(-(e.c ? *e.c : 1.0)) : T(0);
   const int r0 = blockIdx.y * kGatherRows, r1 = min(n_pad, r0 + kGatherRows);
   for (int r = r0; r < r1; ++r) {
     T out;
@@ -999,8 +1018,8 @@ __global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch<T> bt, SellPa
   // A row can fill several slots (padding slots repeat the diagonal with a
   // zero value): its first slot sums them all.
   const int base = pat.slice_ptr[l >> 5] + (l & 31);
-  const double a0 = *e.a0;
-  const double c = e.W ? *e.c : 0.0;
+  const double a0 = e.a0 ? *e.a0 : 1.0;
+  const double c = e.W ? (e.c ? *e.c : 1.0) : 0.0;
   bool diag_seen = false;
   for (int s = 0; s <= w; ++s) {
     int r;
@@ -1013,28 +1032,28 @@ __global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch<T> bt, SellPa
       for (int q = 0; q < s; ++q) first &= (s_col[q * 256 + threadIdx.x] != r);
       if (!first) continue;
       for (int q = s; q < w; ++q)
-        if (s_col[q * 256 + threadIdx.x] == r) aq += qs[base + q * kSlice];
+        if (s_col[q * 256 + threadIdx.x] == r) aq += dval[base + q * kSlice];
     } else {
       if (diag_seen) break;
       r = l;  // a diagonal outside the pattern still gets its observation term
       if (r < r0 || r >= r1) continue;
     }
     double o = a0 * aq;
-    if (r == l && e.obs[r]) o += obs_w;
+    if (r == l && e.obs && e.obs[r]) o += obs_w;
     if (e.W) o -= c * (double)schur_sum(e.W + (int64_t)r * n_pad, w, s_col, s_val);
     e.D[(int64_t)r * n_pad + l] = (T)o;
   }
 }
 
 template <typename T>
-void launch_schur_assemble(cudaStream_t s, const SchurBatch<T> &b, const SellPattern &pat,
-                           const double *qs, double obs_w, int n_s, int n_pad) {
+void launch_schur_assemble(cudaStream_t s, const SchurBatch<T> &b, const SellPattern &pat, double obs_w, int n_s,
+                           int n_pad) {
   if (b.count <= 0) return;
   ++g_launch_count;
   dim3 grid((n_pad + 255) / 256, (n_pad + kGatherRows - 1) / kGatherRows, b.count);
   {
     ProfScope ps_(s, PROF_SCHUR);
-    k_schur_assemble<T><<<grid, 256, col_pattern_smem<T>(pat), s>>>(b, pat, qs, obs_w, n_s, n_pad);
+    k_schur_assemble<T><<<grid, 256, col_pattern_smem<T>(pat), s>>>(b, pat, obs_w, n_s, n_pad);
   }
 }
 // Opt the pattern-staging kernels in to the shared memory that
@@ -1060,14 +1079,15 @@ bool configure_pattern_kernels(const SellPattern &pat) {
   return ok;
 }
 
-template void launch_schur_assemble<double>(cudaStream_t, const SchurBatch<double> &, const SellPattern &,
-                                            const double *, double, int, int);
-template void launch_schur_assemble<float>(cudaStream_t, const SchurBatch<float> &, const SellPattern &,
-                                           const double *, double, int, int);
+template void launch_schur_assemble<double>(cudaStream_t, const SchurBatch<double> &, const SellPattern &, double,
+                                            int, int);
+template void launch_schur_assemble<float>(cudaStream_t, const SchurBatch<float> &, const SellPattern &, double, int,
+                                           int);
 
 // ---------------------------------------------------------------------------
-// diag(S) and the pattern inner products <dQ_s, S>, <Q_s, S> in double (one
-// block per entry, fixed reduction order).  With D0 set, the diagonal is
+// diag(S) and the pattern inner products <M_j, S> with the entry's spatial
+// derivative blocks M_j (j < n_sums) in double (one block per entry, fixed
+// reduction order).  With D0 set, the diagonal is
 // instead diag(D0) + diag(D0 V) accumulated in double over column chunks
 // (k_diag64), D0 symmetric so that D0[i, l] = D0[l, i] reads coalesce.
 // ---------------------------------------------------------------------------
@@ -1086,13 +1106,11 @@ __global__ void __launch_bounds__(256) k_diag64(ExtractBatch<T> bt, int n_s, int
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) k_extract(ExtractBatch<T> bt, SellPattern pat,
-                                                  const double *__restrict__ qs,
-                                                  const double *__restrict__ dqs, int n_s, int n_pad,
+__global__ void __launch_bounds__(1024) k_extract(ExtractBatch<T> bt, SellPattern pat, int n_sums, int n_s, int n_pad,
                                                   const double *__restrict__ diag_partial) {
-  __shared__ double red0[32], red1[32];
+  __shared__ double red[kMaxTheta][32];
   const ExtractEntry<T> e = bt.e[blockIdx.x];
-  double s0 = 0.0, s1 = 0.0;
+  double acc[kMaxTheta] = {0.0, 0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < n_s; i += blockDim.x) {
     const T *Si = e.S + (int64_t)i * n_pad;
     if (e.diag_out) {
@@ -1109,31 +1127,25 @@ __global__ void __launch_bounds__(1024) k_extract(ExtractBatch<T> bt, SellPatter
       const int w = pat.slice_width[sl];
       const int base = pat.slice_ptr[sl] + li;
       for (int s = 0; s < w; ++s) {
-        const int j = pat.col[base + s * kSlice];
-        const double sv = (double)Si[j];
-        s0 = fma(dqs[base + s * kSlice], sv, s0);
-        s1 = fma(qs[base + s * kSlice], sv, s1);
+        const int idx = base + s * kSlice;
+        const double sv = (double)Si[pat.col[idx]];
+#pragma unroll
+        for (int j = 0; j < kMaxTheta; ++j)
+          if (j < n_sums) acc[j] = fma(e.sv[j][idx], sv, acc[j]);
       }
     }
   }
   if (!e.sums) return;
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 += __shfl_down_sync(0xffffffffu, s0, o);
-    s1 += __shfl_down_sync(0xffffffffu, s1, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red0[threadIdx.x >> 5] = s0;
-    red1[threadIdx.x >> 5] = s1;
+#pragma unroll
+  for (int j = 0; j < kMaxTheta; ++j) {
+    for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
+    if ((threadIdx.x & 31) == 0) red[j][threadIdx.x >> 5] = acc[j];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      a += red0[w];
-      b += red1[w];
-    }
-    e.sums[0] = a;
-    e.sums[1] = b;
+  if (threadIdx.x < n_sums) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[threadIdx.x][w];
+    e.sums[threadIdx.x] = a;
   }
 }
 
@@ -1142,8 +1154,8 @@ __global__ void __launch_bounds__(1024) k_extract(ExtractBatch<T> bt, SellPatter
 size_t extract_scratch_bytes(int n_pad) { return (size_t)kMaxBatch * kDiagChunks * n_pad * sizeof(double); }
 
 template <typename T>
-void launch_extract(cudaStream_t s, const ExtractBatch<T> &b, const SellPattern &pat, const double *qs,
-                    const double *dqs, int n_s, int n_pad, double *diag_scratch) {
+void launch_extract(cudaStream_t s, const ExtractBatch<T> &b, const SellPattern &pat, int n_sums, int n_s,
+                    int n_pad, double *diag_scratch) {
   if (b.count <= 0) return;
   bool any_d0 = false;
   for (int q = 0; q < b.count; ++q) any_d0 |= (b.e[q].D0 != nullptr);
@@ -1157,12 +1169,12 @@ void launch_extract(cudaStream_t s, const ExtractBatch<T> &b, const SellPattern 
   ++g_launch_count;
   {
     ProfScope ps_(s, PROF_EXTRACT);
-    k_extract<T><<<b.count, 1024, 0, s>>>(b, pat, qs, dqs, n_s, n_pad, diag_scratch);
+    k_extract<T><<<b.count, 1024, 0, s>>>(b, pat, n_sums, n_s, n_pad, diag_scratch);
   }
 }
-template void launch_extract<double>(cudaStream_t, const ExtractBatch<double> &, const SellPattern &,
-                                     const double *, const double *, int, int, double *);
-template void launch_extract<float>(cudaStream_t, const ExtractBatch<float> &, const SellPattern &,
-                                    const double *, const double *, int, int, double *);
+template void launch_extract<double>(cudaStream_t, const ExtractBatch<double> &, const SellPattern &, int, int, int,
+                                     double *);
+template void launch_extract<float>(cudaStream_t, const ExtractBatch<float> &, const SellPattern &, int, int, int,
+                                    double *);
 
 }  // namespace qsel

@@ -91,6 +91,12 @@ void launch_qs_values(cudaStream_t s, int n_ent, const double *c_pat, const doub
                       const double *h_pat, const double *isqc_pat, const double *scalars,
                       double *qs, double *dqs, double *kc);
 
+// Per-block values of the diffusion model for theta_dev = (log gamma_s, log
+// gamma_t, log gamma_e); layout of blk and coef in model.cu.
+void launch_diffusion_values(cudaStream_t s, const double *theta_dev, int n_t, int n_ent, const double *c_pat,
+                             const double *g_pat, const double *h_pat, const double *h3_pat, double *blk,
+                             double *coef);
+
 // ---------------------------------------------------------------- sampler.cu
 void launch_philox_normals(cudaStream_t s, uint64_t seed, uint32_t stream_id, int n_rows, int k,
                            int ld, double *z);
@@ -102,16 +108,14 @@ void launch_perturbation_rhs(cudaStream_t s, const SellPattern &pat, const doubl
 template <typename T>
 struct BtSpmmArgs {
   SellPattern pat;
-  const double *val;      // spatial values on the pattern
-  const double *c0;       // diagonal-block time coefficient per slab
-  const double *c1;       // off-diagonal time coefficient per slab pair (t, t+1)
-  const uint8_t *obs;     // observation mask (may be null)
-  double obs_w;           // weight of the observation diagonal
+  BtModel m;              // the block-tridiagonal matrix
   int n_s, n_t, ld;
   const T *x;
   T *y;
   double *dot_partial;    // if non-null: per-CTA per-column partial sums of x*y
-  T *tmp = nullptr;       // if non-null: n x ld scratch for the time combination
+  T *tmp = nullptr;       // if non-null and the model is separable (one spatial
+                          // array scaled per block): n x ld scratch for the
+                          // time combination
 };
 // Number of dot-partial rows launch_bt_spmm writes.
 int bt_spmm_grid(int n_rows);
@@ -142,9 +146,8 @@ void launch_refine_ctl(cudaStream_t s, cudaGraphConditionalHandle h, const int32
                        const double *max_rel, int32_t *loop, int first, int max_outer, int max_iter, double tol,
                        double inner_floor, double *tol2_dev);
 template <typename T>
-void launch_jacobi_setup(cudaStream_t s, const SellPattern &pat, const double *qs, const double *a0,
-                         const double *a1, const uint8_t *obs, double obs_w, int n_s, int n_t,
-                         int bsize, T *pblk, int32_t *err_flag);
+void launch_jacobi_setup(cudaStream_t s, const SellPattern &pat, const BtModel &m, int n_s, int n_t, int bsize,
+                         T *pblk, int32_t *err_flag);
 // Grid of the PCG update (also the number of its partial rows, PcgVec::n_tiles).
 int pcg_update_grid(int n);
 struct KronOperator;
@@ -205,6 +208,8 @@ struct SweepEntry {
   // columns V and the column panel W, n_pad x 64 kSweepPanel each (row-major)
   T *Up[2], *Vp[2], *Wp[2];
   T *Vk;         // tensor-core path: 64 kSweepPanel x 64 (panel rows of the pivot column)
+  T *Sp[4];      // tensor-core path: the panel update's U and V split into TF32 hi / lo
+                 // (U_hi, U_lo, V_hi, V_lo; n_pad x 64 kSweepPanel each), or null
 };
 // Streams and events of the tensor-core sweep's look-ahead: the panels run on
 // hi (high priority), the rank-64 kSweepPanel updates and scatters on lo.
@@ -240,23 +245,24 @@ struct SpEntry {
   TO *Out;
   const double *alpha_ptr;  // optional device scalar multiplying alpha
   double alpha, beta;
+  const double *val;        // spatial values of this entry's block on the pattern
 };
 template <typename TI, typename TO>
 struct SpBatch {
   SpEntry<TI, TO> e[kMaxBatch];
   int count;
 };
-// Out[i, :] = alpha (Q_s B)[i, :] + beta C[i, :] for i < n_s (rows n_s..n_pad-1
-// of Out are set to beta C, or zero when C is null).  B has leading dimension
-// ldb, Out and C have ldo.
+// Out[i, :] = alpha (M B)[i, :] + beta C[i, :] for i < n_s with M the
+// symmetric spatial block of each entry (e.val on the pattern); rows
+// n_s..n_pad-1 of Out are set to beta C, or zero when C is null.  B has
+// leading dimension ldb, Out and C have ldo.
 template <typename TI, typename TO>
-void launch_sp_rowgather(cudaStream_t s, const SpBatch<TI, TO> &b, const SellPattern &pat,
-                         const double *val, int n_s, int n_pad, int ncol, int ldb, int ldo);
+void launch_sp_rowgather(cudaStream_t s, const SpBatch<TI, TO> &b, const SellPattern &pat, int n_s, int n_pad,
+                         int ncol, int ldb, int ldo);
 
-// Out = alpha B Q_s + beta C on n_pad x n_pad blocks (column gather).
+// Out = alpha B M + beta C on n_pad x n_pad blocks (column gather).
 template <typename T>
-void launch_sp_colgather(cudaStream_t s, const SpBatch<T, T> &b, const SellPattern &pat, const double *val,
-                         int n_s, int n_pad);
+void launch_sp_colgather(cudaStream_t s, const SpBatch<T, T> &b, const SellPattern &pat, int n_s, int n_pad);
 
 template <typename T>
 struct DiagRowEntry {
@@ -278,6 +284,22 @@ void launch_diag64_rows(cudaStream_t s, const DiagRowBatch<T> &b, int n_s, int n
 bool tc_gemm_available();
 bool launch_tc_gemm(cudaStream_t s, const GemmBatch<float> &b, int M, int N, int K, int lda, int ldb, int ldc,
                     bool lower, int passes, int32_t *err);
+// Persistent tcgen05 update of the lower 128 x 128 tiles of n x n matrices:
+// C = alpha U V^T + beta C with U, V (n x K, leading dimension ldp) given as
+// TF32 hi / lo parts (3xTF32), K a multiple of 32 (tc_update.cu).  False when
+// a tensor map cannot be encoded (nothing is launched then).
+struct UpdateEntry {
+  const float *Uh, *Ul, *Vh, *Vl;
+  float *C;
+};
+struct UpdateBatch {
+  UpdateEntry e[kMaxBatch];
+  int count;
+};
+bool launch_tc_update(cudaStream_t s, const UpdateBatch &b, int n, int K, int ldp, float alpha, float beta,
+                      int32_t *err);
+// hi = rn_tf32(x), lo = rn_tf32(x - hi) elementwise (count a multiple of 4).
+void launch_split_tf32(cudaStream_t s, const float *src, float *hi, float *lo, int64_t count);
 // out[r, c] = alpha in[c, r] + beta c0[r, c] for each entry (see dense.cu).
 struct TransEntry {
   const float *in, *c0;
@@ -299,11 +321,13 @@ bool launch_symm_block_tc(cudaStream_t s, const GemmBatch<float> &b, float *cons
 
 template <typename T>
 struct SchurEntry {
-  const T *W;               // W_{t-1} = c Q_s Dinv_{t-1} (null for the first slab)
+  const T *W;               // W_{t-1} = B_{t-1} Dinv_{t-1} (null for the first slab)
   T *D;                     // output diagonal block
-  const double *a0;         // device pointer to tau Q_t[t,t]
-  const double *c;          // device pointer to the coupling c_{t-1} (ignored if W null)
-  const uint8_t *obs;       // mask of slab t (n_s entries)
+  const double *dval;       // spatial values of A_t on the pattern
+  const double *a0;         // device scale of A_t, or null (1)
+  const double *cval;       // spatial values of B_{t-1} on the pattern (ignored if W null)
+  const double *c;          // device scale of B_{t-1}, or null (1)
+  const uint8_t *obs;       // mask of slab t (n_s entries), or null
 };
 template <typename T>
 struct SchurBatch {
@@ -311,8 +335,8 @@ struct SchurBatch {
   int count;
 };
 template <typename T>
-void launch_schur_assemble(cudaStream_t s, const SchurBatch<T> &b, const SellPattern &pat,
-                           const double *qs, double obs_w, int n_s, int n_pad);
+void launch_schur_assemble(cudaStream_t s, const SchurBatch<T> &b, const SellPattern &pat, double obs_w, int n_s,
+                           int n_pad);
 // The row / column gathers and the Schur assembly stage each row's or
 // column's pattern in shared memory; widest pattern they accept, and the
 // opt-in of those kernels to the shared memory pat.max_width needs.
@@ -323,7 +347,8 @@ template <typename T>
 struct ExtractEntry {
   const T *S;               // n_pad x n_pad dense
   double *diag_out;         // n_s outputs (null: skip)
-  double *sums;             // 2 outputs: <dQs, S>_pattern, <Qs, S>_pattern (null: skip)
+  double *sums;             // n_sums outputs <sv[j], S>_pattern (null: skip)
+  const double *sv[kMaxTheta];  // spatial values of the derivative blocks
   // optional FP64 diagonal: when D0 is set, diag_out gets
   // D0[i,i] + sum_l D0[i,l] V[l,i] accumulated in double instead of S[i,i]
   const T *D0, *V;
@@ -337,8 +362,8 @@ struct ExtractBatch {
 // an entry sets D0).
 size_t extract_scratch_bytes(int n_pad);
 template <typename T>
-void launch_extract(cudaStream_t s, const ExtractBatch<T> &b, const SellPattern &pat, const double *qs,
-                    const double *dqs, int n_s, int n_pad, double *diag_scratch);
+void launch_extract(cudaStream_t s, const ExtractBatch<T> &b, const SellPattern &pat, int n_sums, int n_s,
+                    int n_pad, double *diag_scratch);
 
 // ---------------------------------------------------------------- rbmc.cu
 template <typename T>
@@ -347,7 +372,7 @@ struct CorrEntry {
   int T_, lo, hi, e0;       // slabs, local own range [lo, hi], global slab of local 0
   double *corr_out;         // global correction output (own rows written)
   double *corr4_out;        // (1/k) sum w^4 of the own rows, or nullptr
-  double *partial;          // per-CTA trace partials (3 per CTA)
+  double *partial;          // per-CTA trace partials (kMaxTheta per CTA)
 };
 template <typename T>
 struct CorrBatch {
@@ -356,16 +381,15 @@ struct CorrBatch {
 };
 int corr_grid();
 template <typename T>
-void launch_correction_terms(cudaStream_t s, const CorrBatch<T> &b, const SellPattern &pat,
-                             const double *qs, const double *dqs, const double *a0, const double *a1,
-                             const double *r0, const double *r1, int n_s, int n_pad, int ld, int k);
+void launch_correction_terms(cudaStream_t s, const CorrBatch<T> &b, const SellPattern &pat, const DerivModels &dm,
+                             int n_s, int n_pad, int ld, int k);
 struct TraceSlab {
   int t;            // global slab of the row block
   int sd, sy, sym;  // indices into sums: Sigma_tt, Y_t (pair t,t+1), Y_{t-1} (pair t-1,t); -1 = absent
 };
+// sums: kMaxTheta per index; partials: kMaxTheta per CTA; out: dm.n traces
 void launch_trace_combine(cudaStream_t s, const TraceSlab *slabs_dev, int n_slabs, const double *sums,
-                          const double *partials, int n_partials, const double *a0, const double *a1,
-                          const double *r0, const double *r1, double *out3);
+                          const double *partials, int n_partials, const DerivModels &dm, double *out);
 template <typename T>
 void launch_add(cudaStream_t s, T *y, const T *x, int64_t n);
 // out = a + b (n doubles)
@@ -433,8 +457,8 @@ struct LanczosArgs {
   int n, ld, k, m;
 };
 int lz_grid(int n);
-void launch_bj_cholinv(cudaStream_t s, const SellPattern &pat, const double *qs, const double *a0, const double *a1,
-                       const uint8_t *obs, double obs_w, int n_s, int n_t, int b, double *linv, int32_t *err_flag);
+void launch_bj_cholinv(cudaStream_t s, const SellPattern &pat, const BtModel &m, int n_s, int n_t, int b,
+                       double *linv, int32_t *err_flag);
 void launch_block_apply(cudaStream_t s, const double *linv, int b, int n, int ld, const double *x, double *y,
                         bool trans);
 void launch_lz_vec(cudaStream_t s, int mode, const LanczosArgs &a, const double *vprev, const double *v, double *w,
@@ -446,9 +470,8 @@ void launch_lz_quadrature(cudaStream_t s, const LanczosArgs &a, const double *al
                           const double *eta, double *dwork, double *U, double *coef, int32_t *err_flag);
 
 // ---------------------------------------------------------------- mlp.cu
-void launch_cv_features(cudaStream_t s, const SellPattern &pat, const double *qs, const double *a0,
-                        const double *a1, const uint8_t *obs, double obs_w, int n_s, int n_t, const float *sep_dist,
-                        const float *bnd_dist, const double th[3], float *F);
+void launch_cv_features(cudaStream_t s, const SellPattern &pat, const BtModel &m, int n_s, int n_t,
+                        const float *sep_dist, const float *bnd_dist, const double th[3], float *F);
 void launch_cv_part_m2(cudaStream_t s, const float *y, const int32_t *slab_start_dev, int n_parts, int n_s,
                        double *out);
 constexpr int kCvMaxTargets = 8;

@@ -22,14 +22,12 @@ namespace qsel {
 // Block factor: Linv_b = chol(Q_bb)^-1 (lower triangular), b <= 64, FP64.
 // A non-positive pivot sets bit 0 of *err_flag.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_bj_cholinv(SellPattern pat, const double *__restrict__ qs,
-                                                    const double *__restrict__ a0, const double *__restrict__ a1,
-                                                    const uint8_t *__restrict__ obs, double obs_w, int n_s, int n_t,
-                                                    int b, double *__restrict__ linv, int32_t *err_flag) {
+__global__ void __launch_bounds__(256) k_bj_cholinv(SellPattern pat, BtModel m, int n_s, int n_t, int b,
+                                                    double *__restrict__ linv, int32_t *err_flag) {
   extern __shared__ __align__(16) double smem_chol[];
   double *S = smem_chol;              // [64][65]
   double *X = smem_chol + 64 * 65;    // [64][65]
-  assemble_diag_block(S, 65, pat, qs, a0, a1, obs, obs_w, n_s, n_t, blockIdx.x * b, b);
+  assemble_diag_block(S, 65, pat, m, n_s, n_t, blockIdx.x * b, b);
   // right-looking Cholesky, lower triangle of S
   for (int k = 0; k < b; ++k) {
     if (threadIdx.x == 0) {
@@ -334,8 +332,8 @@ __global__ void __launch_bounds__(32) k_lz_quadrature(const LanczosArgs a, const
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-void launch_bj_cholinv(cudaStream_t s, const SellPattern &pat, const double *qs, const double *a0, const double *a1,
-                       const uint8_t *obs, double obs_w, int n_s, int n_t, int b, double *linv, int32_t *err_flag) {
+void launch_bj_cholinv(cudaStream_t s, const SellPattern &pat, const BtModel &m, int n_s, int n_t, int b,
+                       double *linv, int32_t *err_flag) {
   constexpr int smem = 2 * 64 * 65 * (int)sizeof(double);
   static bool attr = false;
   if (!attr) {
@@ -344,7 +342,7 @@ void launch_bj_cholinv(cudaStream_t s, const SellPattern &pat, const double *qs,
   }
   ++g_launch_count;
   const int nblk = (n_s * n_t + b - 1) / b;
-  k_bj_cholinv<<<nblk, 256, smem, s>>>(pat, qs, a0, a1, obs, obs_w, n_s, n_t, b, linv, err_flag);
+  k_bj_cholinv<<<nblk, 256, smem, s>>>(pat, m, n_s, n_t, b, linv, err_flag);
 }
 
 void launch_block_apply(cudaStream_t s, const double *linv, int b, int n, int ld, const double *x, double *y,

@@ -266,9 +266,7 @@ __global__ void k_feature_stats(const float *__restrict__ X, int n, float *__res
 // Per-node features of the current model for a given overlap (see the oracle
 // documentation for the definition).  One thread per node.
 // ---------------------------------------------------------------------------
-__global__ void k_cv_features(SellPattern pat, const double *__restrict__ qs, const double *__restrict__ a0,
-                              const double *__restrict__ a1, const uint8_t *__restrict__ obs, double obs_w,
-                              int n_s, int n_t, const float *__restrict__ sep_dist,
+__global__ void k_cv_features(SellPattern pat, BtModel m, int n_s, int n_t, const float *__restrict__ sep_dist,
                               const float *__restrict__ bnd_dist, double th0, double th1, double th2,
                               float *__restrict__ F) {
   const int n = n_s * n_t;
@@ -277,7 +275,7 @@ __global__ void k_cv_features(SellPattern pat, const double *__restrict__ qs, co
     const int sl = i >> 5, li = i & 31;
     const int w = pat.slice_width[sl];
     const int base = pat.slice_ptr[sl] + li;
-    double diag = (obs && obs[r]) ? obs_w : 0.0;
+    double diag = (m.obs && m.obs[r]) ? m.obs_w : 0.0;
     double top[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) top[q] = 0.0;
@@ -290,16 +288,21 @@ __global__ void k_cv_features(SellPattern pat, const double *__restrict__ qs, co
       }
       top[q] = v;
     };
+    const double c0 = m.diag.scale(t);
+    const double cm = t > 0 ? m.off.scale(t - 1) : 0.0, cp = t + 1 < n_t ? m.off.scale(t) : 0.0;
+    const double *v0 = m.diag.at(t);
+    const double *vm = m.off.at(t > 0 ? t - 1 : 0);
+    const double *vp = m.off.at(t + 1 < n_t ? t : 0);
     for (int s = 0; s < w; ++s) {
-      const int j = pat.col[base + s * kSlice];
-      const double v = qs[base + s * kSlice];
-      if (v == 0.0) continue;
+      const int idx = base + s * kSlice;
+      const int j = pat.col[idx];
+      const double v = c0 * v0[idx];
       if (j == i)
-        diag += a0[t] * v;
-      else
-        push(fabs(a0[t] * v));
-      if (t > 0) push(fabs(a1[t - 1] * v));
-      if (t + 1 < n_t) push(fabs(a1[t] * v));
+        diag += v;
+      else if (v != 0.0)
+        push(fabs(v));
+      if (t > 0 && vm[idx] != 0.0) push(fabs(cm * vm[idx]));
+      if (t + 1 < n_t && vp[idx] != 0.0) push(fabs(cp * vp[idx]));
     }
     float *f = F + (int64_t)r * mlp::NF;
     f[0] = (float)log(diag);
@@ -313,15 +316,13 @@ __global__ void k_cv_features(SellPattern pat, const double *__restrict__ qs, co
   }
 }
 
-void launch_cv_features(cudaStream_t s, const SellPattern &pat, const double *qs, const double *a0,
-                        const double *a1, const uint8_t *obs, double obs_w, int n_s, int n_t, const float *sep_dist,
-                        const float *bnd_dist, const double th[3], float *F) {
+void launch_cv_features(cudaStream_t s, const SellPattern &pat, const BtModel &m, int n_s, int n_t,
+                        const float *sep_dist, const float *bnd_dist, const double th[3], float *F) {
   ++g_launch_count;
   const int n = n_s * n_t;
   int grid = (n + 255) / 256;
   if (grid > 152 * 8) grid = 152 * 8;
-  k_cv_features<<<grid, 256, 0, s>>>(pat, qs, a0, a1, obs, obs_w, n_s, n_t, sep_dist, bnd_dist, th[0], th[1], th[2],
-                                     F);
+  k_cv_features<<<grid, 256, 0, s>>>(pat, m, n_s, n_t, sep_dist, bnd_dist, th[0], th[1], th[2], F);
 }
 
 // Per part p: sum over the rows of Omega_p (slabs [slab_start[p],

@@ -8,9 +8,8 @@
 // slab tau this kernel adds
 //   diag:   (1/k) sum_s w_i^2
 //   traces: (1/k) sum_s w_i (dQ_j w)_i,
-// with dQ_j block (t, t+d) = e_j(t, d) M_j on the spatial pattern:
-//   j = 0: M = dQ_s/dlog kappa, e = tau Q_t;        j = 1: M = Q_s, e = tau Q_t;
-//   j = 2: M = Q_s, e = tau rho (1 - rho) dQ_t/drho.
+// with dQ_j the block-tridiagonal derivative of theta_j: diagonal blocks
+// dA_j(t), couplings dB_j(t) on the spatial pattern.
 #include "kernels.cuh"
 
 namespace qsel {
@@ -19,148 +18,120 @@ constexpr int kCorrGrid = 152 * 2;
 
 int corr_grid() { return kCorrGrid; }
 
+// (w_i^T dQ_j w) = sum over pattern entries l of row i and time offsets d of
+// M_{j,d}[i, l] * sum_c w_i(c) w_{l, t+d}(c): the column sums q_d are formed
+// once per entry and shared by every j.
 template <typename T>
-__global__ void __launch_bounds__(256) k_correction_terms(CorrBatch<T> bt, SellPattern pat,
-                                                          const double *__restrict__ qs,
-                                                          const double *__restrict__ dqs,
-                                                          const double *__restrict__ a0,
-                                                          const double *__restrict__ a1,
-                                                          const double *__restrict__ r0,
-                                                          const double *__restrict__ r1, int n_s,
+__global__ void __launch_bounds__(256) k_correction_terms(CorrBatch<T> bt, SellPattern pat, DerivModels dm, int n_s,
                                                           int n_pad, int ld, int k) {
-  __shared__ double red[8][3];
+  __shared__ double red[8][kMaxTheta];
   const CorrEntry<T> e = bt.e[blockIdx.y];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double inv_k = 1.0 / (double)k;
   const int n_own = (e.hi - e.lo + 1) * n_s;
   const int64_t slab = (int64_t)n_pad * ld;
-  double tr0 = 0.0, tr1 = 0.0, tr2 = 0.0;
+  double tr[kMaxTheta] = {0.0, 0.0, 0.0, 0.0};
   for (int item = blockIdx.x * 8 + warp; item < n_own; item += gridDim.x * 8) {
     const int tl = e.lo + item / n_s;      // local slab
     const int i = item - (item / n_s) * n_s;
     const int t = e.e0 + tl;               // global slab
     const bool has_m = tl > 0, has_p = tl + 1 < e.T_;
-    const double ea[3] = {has_m ? a1[t - 1] : 0.0, a0[t], has_p ? a1[t] : 0.0};
-    const double er[3] = {has_m ? r1[t - 1] : 0.0, r0[t], has_p ? r1[t] : 0.0};
     const int sl = i >> 5, li = i & 31;
     const int w = pat.slice_width[sl];
     const int base = pat.slice_ptr[sl] + li;
     const T *wrow = e.w + tl * slab + (int64_t)i * ld;
-    double sq = 0.0, q4 = 0.0, p0 = 0.0, p1 = 0.0, p2 = 0.0;
+    double sq = 0.0, q4 = 0.0;
     for (int c = lane; c < ld; c += 32) {
-      double g0 = 0.0, g1 = 0.0, g2 = 0.0;
-      for (int s = 0; s < w; ++s) {
-        const int j = pat.col[base + s * kSlice];
-        const double vq = qs[base + s * kSlice], vd = dqs[base + s * kSlice];
-        const T *wc = e.w + tl * slab + (int64_t)j * ld + c;
-        const double x0 = (double)wc[0];
-        const double xm = has_m ? (double)wc[-slab] : 0.0;
-        const double xp = has_p ? (double)wc[slab] : 0.0;
-        const double za = ea[0] * xm + ea[1] * x0 + ea[2] * xp;
-        const double zr = er[0] * xm + er[1] * x0 + er[2] * xp;
-        g0 = fma(vd, za, g0);
-        g1 = fma(vq, za, g1);
-        g2 = fma(vq, zr, g2);
-      }
       const double wi = (double)wrow[c];
       sq = fma(wi, wi, sq);
       q4 = fma(wi * wi, wi * wi, q4);
-      p0 = fma(wi, g0, p0);
-      p1 = fma(wi, g1, p1);
-      p2 = fma(wi, g2, p2);
+    }
+    double p[kMaxTheta] = {0.0, 0.0, 0.0, 0.0};
+    for (int s = 0; s < w; ++s) {
+      const int idx = base + s * kSlice;
+      const T *wc = e.w + tl * slab + (int64_t)pat.col[idx] * ld;
+      double q0 = 0.0, qm = 0.0, qp = 0.0;
+      for (int c = lane; c < ld; c += 32) {
+        const double wi = (double)wrow[c];
+        q0 = fma(wi, (double)wc[c], q0);
+        if (has_m) qm = fma(wi, (double)wc[c - slab], qm);
+        if (has_p) qp = fma(wi, (double)wc[c + slab], qp);
+      }
+#pragma unroll
+      for (int j = 0; j < kMaxTheta; ++j) {
+        if (j >= dm.n) break;
+        double acc = dm.diag[j].scale(t) * dm.diag[j].at(t)[idx] * q0;
+        if (has_m) acc = fma(dm.off[j].scale(t - 1) * dm.off[j].at(t - 1)[idx], qm, acc);
+        if (has_p) acc = fma(dm.off[j].scale(t) * dm.off[j].at(t)[idx], qp, acc);
+        p[j] += acc;
+      }
     }
     for (int o = 16; o > 0; o >>= 1) {
       sq += __shfl_down_sync(0xffffffffu, sq, o);
       q4 += __shfl_down_sync(0xffffffffu, q4, o);
-      p0 += __shfl_down_sync(0xffffffffu, p0, o);
-      p1 += __shfl_down_sync(0xffffffffu, p1, o);
-      p2 += __shfl_down_sync(0xffffffffu, p2, o);
+#pragma unroll
+      for (int j = 0; j < kMaxTheta; ++j) p[j] += __shfl_down_sync(0xffffffffu, p[j], o);
     }
     if (lane == 0) {
       e.corr_out[(int64_t)t * n_s + i] = sq * inv_k;
       if (e.corr4_out) e.corr4_out[(int64_t)t * n_s + i] = q4 * inv_k;
-      tr0 += p0;
-      tr1 += p1;
-      tr2 += p2;
+#pragma unroll
+      for (int j = 0; j < kMaxTheta; ++j) tr[j] += p[j];
     }
   }
   if (lane == 0) {
-    red[warp][0] = tr0;
-    red[warp][1] = tr1;
-    red[warp][2] = tr2;
+#pragma unroll
+    for (int j = 0; j < kMaxTheta; ++j) red[warp][j] = tr[j];
   }
   __syncthreads();
-  if (threadIdx.x < 3) {
+  if (threadIdx.x < kMaxTheta) {
     double s = 0.0;
     for (int ww = 0; ww < 8; ++ww) s += red[ww][threadIdx.x];
-    e.partial[blockIdx.x * 3 + threadIdx.x] = s * inv_k;
+    e.partial[blockIdx.x * kMaxTheta + threadIdx.x] = s * inv_k;
   }
 }
 
 template <typename T>
-void launch_correction_terms(cudaStream_t s, const CorrBatch<T> &b, const SellPattern &pat,
-                             const double *qs, const double *dqs, const double *a0, const double *a1,
-                             const double *r0, const double *r1, int n_s, int n_pad, int ld, int k) {
+void launch_correction_terms(cudaStream_t s, const CorrBatch<T> &b, const SellPattern &pat, const DerivModels &dm,
+                             int n_s, int n_pad, int ld, int k) {
   if (b.count <= 0) return;
   ++g_launch_count;
   ProfScope ps_(s, PROF_CORR);
-  k_correction_terms<T><<<dim3(kCorrGrid, b.count), 256, 0, s>>>(b, pat, qs, dqs, a0, a1, r0, r1, n_s,
-                                                                 n_pad, ld, k);
+  k_correction_terms<T><<<dim3(kCorrGrid, b.count), 256, 0, s>>>(b, pat, dm, n_s, n_pad, ld, k);
 }
 template void launch_correction_terms<double>(cudaStream_t, const CorrBatch<double> &, const SellPattern &,
-                                              const double *, const double *, const double *, const double *,
-                                              const double *, const double *, int, int, int, int);
+                                              const DerivModels &, int, int, int, int);
 template void launch_correction_terms<float>(cudaStream_t, const CorrBatch<float> &, const SellPattern &,
-                                             const double *, const double *, const double *, const double *,
-                                             const double *, const double *, int, int, int, int);
+                                             const DerivModels &, int, int, int, int);
 
 // tr_j = sum over own row slabs t of
-//   e_j(t,0) <M_j, Sigma_tt> - e_j(t,+1) <M_j, Y_t> - e_j(t,-1) <M_j, Y_{t-1}>
-// (Sigma_{t,t+1} = -Y_t^T, Sigma_{t,t-1} = -Y_{t-1}, M_j symmetric) plus the
+//   <dA_j(t), Sigma_tt> - <dB_j(t), Y_t> - <dB_j(t-1), Y_{t-1}>
+// (Sigma_{t,t+1} = -Y_t^T, Sigma_{t,t-1} = -Y_{t-1}, the blocks symmetric;
+// sums hold the pattern inner products without the scales) plus the
 // correction partials.  One thread, fixed order.
 __global__ void k_trace_combine(const TraceSlab *__restrict__ slabs, int n_slabs,
                                 const double *__restrict__ sums, const double *__restrict__ partials,
-                                int n_partials, const double *__restrict__ a0,
-                                const double *__restrict__ a1, const double *__restrict__ r0,
-                                const double *__restrict__ r1, double *out3) {
+                                int n_partials, DerivModels dm, double *out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+  double acc[kMaxTheta] = {0.0, 0.0, 0.0, 0.0};
   for (int q = 0; q < n_slabs; ++q) {
     const TraceSlab sl = slabs[q];
     const int t = sl.t;
-    const double *sd = sums + 2 * sl.sd;
-    t0 += a0[t] * sd[0];
-    t1 += a0[t] * sd[1];
-    t2 += r0[t] * sd[1];
-    if (sl.sy >= 0) {
-      const double *sy = sums + 2 * sl.sy;
-      t0 -= a1[t] * sy[0];
-      t1 -= a1[t] * sy[1];
-      t2 -= r1[t] * sy[1];
-    }
-    if (sl.sym >= 0) {
-      const double *sy = sums + 2 * sl.sym;
-      t0 -= a1[t - 1] * sy[0];
-      t1 -= a1[t - 1] * sy[1];
-      t2 -= r1[t - 1] * sy[1];
+    for (int j = 0; j < dm.n; ++j) {
+      acc[j] += dm.diag[j].scale(t) * sums[kMaxTheta * sl.sd + j];
+      if (sl.sy >= 0) acc[j] -= dm.off[j].scale(t) * sums[kMaxTheta * sl.sy + j];
+      if (sl.sym >= 0) acc[j] -= dm.off[j].scale(t - 1) * sums[kMaxTheta * sl.sym + j];
     }
   }
-  for (int q = 0; q < n_partials; ++q) {
-    t0 += partials[3 * q + 0];
-    t1 += partials[3 * q + 1];
-    t2 += partials[3 * q + 2];
-  }
-  out3[0] = t0;
-  out3[1] = t1;
-  out3[2] = t2;
+  for (int q = 0; q < n_partials; ++q)
+    for (int j = 0; j < dm.n; ++j) acc[j] += partials[kMaxTheta * q + j];
+  for (int j = 0; j < dm.n; ++j) out[j] = acc[j];
 }
 
 void launch_trace_combine(cudaStream_t s, const TraceSlab *slabs_dev, int n_slabs, const double *sums,
-                          const double *partials, int n_partials, const double *a0, const double *a1,
-                          const double *r0, const double *r1, double *out3) {
+                          const double *partials, int n_partials, const DerivModels &dm, double *out) {
   ++g_launch_count;
-  k_trace_combine<<<1, 32, 0, s>>>(slabs_dev, n_slabs, sums, partials, n_partials, a0, a1, r0, r1,
-                                   out3);
+  k_trace_combine<<<1, 32, 0, s>>>(slabs_dev, n_slabs, sums, partials, n_partials, dm, out);
 }
 
 template <typename T>

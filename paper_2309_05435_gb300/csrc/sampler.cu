@@ -167,7 +167,8 @@ int bt_spmm_grid(int n_rows) {
 
 
 
-// Time combination of the block-tridiagonal product:
+// Time combination of the block-tridiagonal product of a separable model
+// (every block the same spatial array V, scaled per block):
 //   zc_t = c0_t x_t + c1_{t-1} x_{t-1} + c1_t x_{t+1}   (16-byte vectors)
 // so that y_t = V zc_t + w_obs diag(obs_t) x_t needs one spatial pass that
 // reads w neighbour rows per output row instead of 3w.
@@ -179,9 +180,9 @@ __global__ void __launch_bounds__(256) k_time_combine(BtSpmmArgs<T> a) {
   const int64_t total = slab * a.n_t;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int t = (int)(e / slab);
-    const T c0 = (T)a.c0[t];
-    const T cm = (t > 0) ? (T)a.c1[t - 1] : T(0);
-    const T cp = (t + 1 < a.n_t) ? (T)a.c1[t] : T(0);
+    const T c0 = (T)a.m.diag.scale(t);
+    const T cm = (t > 0) ? (T)a.m.off.scale(t - 1) : T(0);
+    const T cp = (t + 1 < a.n_t) ? (T)a.m.off.scale(t) : T(0);
     const V4 x0 = reinterpret_cast<const V4 *>(a.x)[e];
     V4 z;
     const T *xs = reinterpret_cast<const T *>(&x0);
@@ -228,9 +229,12 @@ __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs<T> a) {
     const int w = a.pat.slice_width[sl];
     const int base = a.pat.slice_ptr[sl] + li;
     // per-row scalars in T: the FP32 path issues no double arithmetic per element
-    const T c0 = (T)a.c0[t];
-    const T cm = (t > 0) ? (T)a.c1[t - 1] : T(0);
-    const T cp = (t + 1 < a.n_t) ? (T)a.c1[t] : T(0);
+    const T c0 = (T)a.m.diag.scale(t);
+    const T cm = (t > 0) ? (T)a.m.off.scale(t - 1) : T(0);
+    const T cp = (t + 1 < a.n_t) ? (T)a.m.off.scale(t) : T(0);
+    const double *v0p = a.m.diag.at(t);
+    const double *vmp = a.m.off.at(t > 0 ? t - 1 : 0);
+    const double *vpp = a.m.off.at(t + 1 < a.n_t ? t : 0);
     const int coff = ch * chunk_cols + 2 * lane;
     T ax[NV], ay[NV];
 #pragma unroll
@@ -240,17 +244,24 @@ __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs<T> a) {
       // the row's pattern entries, one per lane, then broadcast: no dependent
       // loads inside the neighbour loop
       int my_col = i;
-      T my_val = T(0);
+      T my_val = T(0), my_f0 = T(0), my_fm = T(0), my_fp = T(0);
       if (s0 + lane < w) {
-        my_col = a.pat.col[base + (s0 + lane) * kSlice];
-        my_val = (T)a.val[base + (s0 + lane) * kSlice];
+        const int idx = base + (s0 + lane) * kSlice;
+        my_col = a.pat.col[idx];
+        if (COMB) {
+          my_val = (T)v0p[idx];
+        } else {
+          my_f0 = c0 * (T)v0p[idx];
+          my_fm = has_m ? cm * (T)vmp[idx] : T(0);
+          my_fp = has_p ? cp * (T)vpp[idx] : T(0);
+        }
       }
       const int cnt = min(32, w - s0);
 #pragma unroll 4
       for (int s = 0; s < cnt; ++s) {
         const int j = __shfl_sync(0xffffffffu, my_col, s);
-        const T val = __shfl_sync(0xffffffffu, my_val, s);
         if (COMB) {
+          const T val = __shfl_sync(0xffffffffu, my_val, s);
           const T *zc = a.tmp + ((int64_t)t * a.n_s + j) * ld + coff;
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
@@ -261,7 +272,9 @@ __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs<T> a) {
           continue;
         }
         const T *xc = a.x + ((int64_t)t * a.n_s + j) * ld + coff;
-        const T f0 = c0 * val, fm = cm * val, fp = cp * val;
+        const T f0 = __shfl_sync(0xffffffffu, my_f0, s);
+        const T fm = __shfl_sync(0xffffffffu, my_fm, s);
+        const T fp = __shfl_sync(0xffffffffu, my_fp, s);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           const auto x0 = load2(xc + 64 * v);
@@ -281,7 +294,7 @@ __global__ void __launch_bounds__(256) k_bt_spmm(BtSpmmArgs<T> a) {
       }
     }
     const T *xr = a.x + (int64_t)row * ld + coff;
-    const T ow = (a.obs != nullptr && a.obs[row]) ? (T)a.obs_w : T(0);
+    const T ow = (a.m.obs != nullptr && a.m.obs[row]) ? (T)a.m.obs_w : T(0);
     T *yr = a.y + (int64_t)row * ld + coff;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -322,7 +335,10 @@ void launch_bt_spmm(cudaStream_t s, const BtSpmmArgs<T> &a) {
     rec.work = 2.0 * (double)a.n_s * a.n_t * a.ld * sizeof(T);
     g_prof->begin(s, rec);
   }
-  if (a.tmp) {
+  // the time combination needs every block to be the same spatial array
+  const bool separable = a.m.diag.stride == 0 && a.m.off.stride == 0 && a.m.diag.v == a.m.off.v &&
+                         a.m.diag.coef != nullptr && a.m.off.coef != nullptr;
+  if (a.tmp && separable) {
     ++g_launch_count;
     const int64_t vec = (int64_t)a.n_s * a.n_t * a.ld / (16 / (int)sizeof(T));
     k_time_combine<T><<<(int)std::min<int64_t>((vec + 255) / 256, 152 * 8), 256, 0, s>>>(a);
@@ -350,14 +366,10 @@ template void launch_bt_spmm<float>(cudaStream_t, const BtSpmmArgs<float> &);
 // sweep in shared memory (double).  Rows past n are padded with the identity.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_jacobi_setup(SellPattern pat, const double *__restrict__ qs,
-                                                      const double *__restrict__ a0,
-                                                      const double *__restrict__ a1,
-                                                      const uint8_t *__restrict__ obs, double obs_w,
-                                                      int n_s, int n_t, int b, T *__restrict__ pblk,
-                                                      int32_t *err_flag) {
+__global__ void __launch_bounds__(256) k_jacobi_setup(SellPattern pat, BtModel m, int n_s, int n_t, int b,
+                                                      T *__restrict__ pblk, int32_t *err_flag) {
   __shared__ double S[64 * 65];
-  assemble_diag_block(S, 65, pat, qs, a0, a1, obs, obs_w, n_s, n_t, blockIdx.x * b, b);
+  assemble_diag_block(S, 65, pat, m, n_s, n_t, blockIdx.x * b, b);
   sym_sweep_inverse_smem(S, 65, b, err_flag);
   T *P = pblk + (int64_t)blockIdx.x * b * b;
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
@@ -367,20 +379,16 @@ __global__ void __launch_bounds__(256) k_jacobi_setup(SellPattern pat, const dou
 }
 
 template <typename T>
-void launch_jacobi_setup(cudaStream_t s, const SellPattern &pat, const double *qs, const double *a0,
-                         const double *a1, const uint8_t *obs, double obs_w, int n_s, int n_t,
-                         int bsize, T *pblk, int32_t *err_flag) {
+void launch_jacobi_setup(cudaStream_t s, const SellPattern &pat, const BtModel &m, int n_s, int n_t, int bsize,
+                         T *pblk, int32_t *err_flag) {
   ++g_launch_count;
   const int n = n_s * n_t;
   const int nblk = (n + bsize - 1) / bsize;
-  k_jacobi_setup<T><<<nblk, bsize >= 16 ? 256 : 32, 0, s>>>(pat, qs, a0, a1, obs, obs_w, n_s, n_t,
-                                                            bsize, pblk, err_flag);
+  k_jacobi_setup<T><<<nblk, bsize >= 16 ? 256 : 32, 0, s>>>(pat, m, n_s, n_t, bsize, pblk, err_flag);
 }
-template void launch_jacobi_setup<double>(cudaStream_t, const SellPattern &, const double *, const double *,
-                                          const double *, const uint8_t *, double, int, int, int, double *,
+template void launch_jacobi_setup<double>(cudaStream_t, const SellPattern &, const BtModel &, int, int, int, double *,
                                           int32_t *);
-template void launch_jacobi_setup<float>(cudaStream_t, const SellPattern &, const double *, const double *,
-                                         const double *, const uint8_t *, double, int, int, int, float *,
+template void launch_jacobi_setup<float>(cudaStream_t, const SellPattern &, const BtModel &, int, int, int, float *,
                                          int32_t *);
 
 // ---------------------------------------------------------------------------

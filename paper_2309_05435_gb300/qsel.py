@@ -20,6 +20,9 @@ QSEL_PRECOND_BLOCK_JACOBI = 0
 QSEL_PRECOND_KRON = 1
 QSEL_PIVOT_DOUBLE_FLOAT = 0
 QSEL_PIVOT_FP64 = 1
+QSEL_MODEL_SEPARABLE = 0
+QSEL_MODEL_DIFFUSION = 1
+QSEL_MODEL_BLOCK_TRIDIAGONAL = 2
 
 _STATUS = {0: "QSEL_OK", 1: "QSEL_EINVAL", 2: "QSEL_ENOMEM", 3: "QSEL_ECUDA", 4: "QSEL_ENOTSPD",
            5: "QSEL_ENOCONV", 6: "QSEL_ETIMEOUT", 7: "QSEL_ESTATE"}
@@ -46,7 +49,13 @@ class qsel_options(ctypes.Structure):
                 ("pcg_max_iter", c_int32), ("precond_block", c_int32), ("control_variate", c_int32),
                 ("cuda_stream", c_void_p), ("profile_kernels", c_int32), ("tensor_passes", c_int32),
                 ("sampler", c_int32), ("lanczos_steps", c_int32), ("preconditioner", c_int32),
-                ("part_overlap", POINTER(c_int32)), ("pivot_precision", c_int32)]
+                ("part_overlap", POINTER(c_int32)), ("pivot_precision", c_int32), ("model", c_int32)]
+
+
+class qsel_bt_model(ctypes.Structure):
+    _fields_ = [("n_s", c_int32), ("n_t", c_int32), ("rowptr", POINTER(c_int32)), ("col", POINTER(c_int32)),
+                ("diag_vals", POINTER(c_double)), ("off_vals", POINTER(c_double)), ("n_theta", c_int32),
+                ("ddiag_vals", POINTER(c_double)), ("doff_vals", POINTER(c_double))]
 
 
 class qsel_batch_info_t(ctypes.Structure):
@@ -88,7 +97,8 @@ def _fields(s) -> dict:
     return out
 
 
-EXPORTED = ["qsel_create", "qsel_set_seed", "qsel_set_theta", "qsel_diag_inv", "qsel_trace_grads", "qsel_stats",
+EXPORTED = ["qsel_create", "qsel_create_bt", "qsel_set_bt_values", "qsel_set_seed", "qsel_set_theta",
+            "qsel_diag_inv", "qsel_trace_grads", "qsel_trace_grads_n", "qsel_stats",
             "qsel_set_data", "qsel_posterior_mean", "qsel_loglik_grad", "qsel_set_covariates",
             "qsel_fixed_effects",
             "qsel_debug_set_samples", "qsel_debug_get_samples", "qsel_debug_get_rhs",
@@ -123,6 +133,9 @@ def load_library(path: str = LIB_PATH):
     lib.qsel_set_seed.argtypes = [c_void_p, c_uint64]
     lib.qsel_diag_inv.argtypes = [c_void_p, c_void_p, c_int32]
     lib.qsel_trace_grads.argtypes = [c_void_p, P(c_double)]
+    lib.qsel_trace_grads_n.argtypes = [c_void_p, P(c_double), c_int32]
+    lib.qsel_create_bt.argtypes = [P(c_void_p), P(qsel_bt_model), P(qsel_partition), c_int32, P(qsel_options)]
+    lib.qsel_set_bt_values.argtypes = [c_void_p, P(c_double), P(c_double), P(c_double), P(c_double)]
     lib.qsel_set_data.argtypes = [c_void_p, P(c_double)]
     lib.qsel_posterior_mean.argtypes = [c_void_p, c_void_p, c_int32]
     lib.qsel_loglik_grad.argtypes = [c_void_p, P(c_double), P(c_double)]
@@ -223,16 +236,17 @@ def qsel_create(n_s, n_t, c_diag, g_rowptr, g_col, g_val, obs_mask, sigma, theta
                 pcg_max_iter=20000, precond_block=0, control_variate=0, cuda_stream=None,
                 profile_kernels=0, tensor_passes=0, part_overlap=None, sampler=QSEL_SAMPLER_PCG,
                 lanczos_steps=0, preconditioner=QSEL_PRECOND_BLOCK_JACOBI,
-                pivot_precision=QSEL_PIVOT_DOUBLE_FLOAT) -> Context:
-    """Create a context from host arrays (copied by the library)."""
+                pivot_precision=QSEL_PIVOT_DOUBLE_FLOAT, model=QSEL_MODEL_SEPARABLE) -> Context:
+    """Create a context from host arrays (copied by the library).  With
+    model=QSEL_MODEL_DIFFUSION, theta = (log gamma_s, log gamma_t, log gamma_e)."""
     lib = load_library()
     c = np.ascontiguousarray(c_diag, dtype=np.float64)
     rp = np.ascontiguousarray(g_rowptr, dtype=np.int32)
     gc = np.ascontiguousarray(g_col, dtype=np.int32)
     gv = np.ascontiguousarray(g_val, dtype=np.float64)
     mk = np.ascontiguousarray(obs_mask, dtype=np.uint8)
-    model = qsel_model(int(n_s), int(n_t), _ptr(c, c_double), _ptr(rp, c_int32), _ptr(gc, c_int32),
-                       _ptr(gv, c_double), _ptr(mk, c_uint8), float(sigma))
+    model_s = qsel_model(int(n_s), int(n_t), _ptr(c, c_double), _ptr(rp, c_int32), _ptr(gc, c_int32),
+                         _ptr(gv, c_double), _ptr(mk, c_uint8), float(sigma))
     th = qsel_theta(*[float(x) for x in theta])
     ss = None
     if slab_start is not None:
@@ -247,12 +261,66 @@ def qsel_create(n_s, n_t, c_diag, g_rowptr, g_col, g_val, obs_mask, sigma, theta
                        int(precond_block), int(control_variate),
                        c_void_p(int(cuda_stream)) if cuda_stream else None, int(profile_kernels),
                        int(tensor_passes), int(sampler), int(lanczos_steps), int(preconditioner),
-                       _ptr(po, c_int32) if po is not None else None, int(pivot_precision))
+                       _ptr(po, c_int32) if po is not None else None, int(pivot_precision), int(model))
     h = c_void_p()
-    st = lib.qsel_create(ctypes.byref(h), ctypes.byref(model), ctypes.byref(th), ctypes.byref(part),
+    st = lib.qsel_create(ctypes.byref(h), ctypes.byref(model_s), ctypes.byref(th), ctypes.byref(part),
                          int(overlap), ctypes.byref(opt))
     _check(st, None)
     return Context(h, int(n_s) * int(n_t), int(n_samples), int(n_parts))
+
+
+def qsel_create_bt(n_s, n_t, rowptr, col, diag_vals, off_vals, ddiag_vals=None, doff_vals=None, n_parts=1,
+                   slab_start=None, overlap=0, n_samples=64, seed=0, precision=QSEL_FP64, pcg_tol=1e-10,
+                   cuda_stream=None, sampler=QSEL_SAMPLER_LANCZOS, lanczos_steps=64, precond_block=0,
+                   profile_kernels=0, tensor_passes=0, part_overlap=None,
+                   pivot_precision=QSEL_PIVOT_DOUBLE_FLOAT) -> Context:
+    """Context for a user-given block-tridiagonal precision: the pattern in
+    CSR (rowptr, col), diag_vals (n_t x nnz), off_vals ((n_t - 1) x nnz),
+    and optional derivatives ddiag_vals (n_theta x n_t x nnz), doff_vals
+    (n_theta x (n_t - 1) x nnz)."""
+    lib = load_library()
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    dv = np.ascontiguousarray(diag_vals, dtype=np.float64)
+    ov = np.ascontiguousarray(off_vals, dtype=np.float64)
+    n_theta = 0 if ddiag_vals is None else int(np.asarray(ddiag_vals).shape[0])
+    ddv = None if ddiag_vals is None else np.ascontiguousarray(ddiag_vals, dtype=np.float64)
+    dov = None if doff_vals is None else np.ascontiguousarray(doff_vals, dtype=np.float64)
+    m = qsel_bt_model(int(n_s), int(n_t), _ptr(rp, c_int32), _ptr(cl, c_int32), _ptr(dv, c_double),
+                      _ptr(ov, c_double), n_theta, _ptr(ddv, c_double) if ddv is not None else None,
+                      _ptr(dov, c_double) if dov is not None else None)
+    ss = None if slab_start is None else np.ascontiguousarray(slab_start, dtype=np.int32)
+    part = qsel_partition(int(n_parts), _ptr(ss, c_int32) if ss is not None else None)
+    po = None if part_overlap is None else np.ascontiguousarray(part_overlap, dtype=np.int32)
+    opt = qsel_options(int(n_samples), int(seed), int(precision), float(pcg_tol), 20000, int(precond_block), 0,
+                       c_void_p(int(cuda_stream)) if cuda_stream else None, int(profile_kernels),
+                       int(tensor_passes), int(sampler), int(lanczos_steps), QSEL_PRECOND_BLOCK_JACOBI,
+                       _ptr(po, c_int32) if po is not None else None, int(pivot_precision),
+                       QSEL_MODEL_BLOCK_TRIDIAGONAL)
+    h = c_void_p()
+    _check(lib.qsel_create_bt(ctypes.byref(h), ctypes.byref(m), ctypes.byref(part), int(overlap),
+                              ctypes.byref(opt)), None)
+    ctx = Context(h, int(n_s) * int(n_t), int(n_samples), int(n_parts))
+    ctx.n_theta = n_theta
+    return ctx
+
+
+def qsel_set_bt_values(ctx: Context, diag_vals, off_vals, ddiag_vals=None, doff_vals=None):
+    """New block values on the pattern of a qsel_create_bt context."""
+    dv = np.ascontiguousarray(diag_vals, dtype=np.float64)
+    ov = np.ascontiguousarray(off_vals, dtype=np.float64)
+    ddv = None if ddiag_vals is None else np.ascontiguousarray(ddiag_vals, dtype=np.float64)
+    dov = None if doff_vals is None else np.ascontiguousarray(doff_vals, dtype=np.float64)
+    _check(load_library().qsel_set_bt_values(ctx.handle, _ptr(dv, c_double), _ptr(ov, c_double),
+                                             _ptr(ddv, c_double) if ddv is not None else None,
+                                             _ptr(dov, c_double) if dov is not None else None), ctx.handle)
+
+
+def qsel_trace_grads_n(ctx: Context, n: int) -> np.ndarray:
+    """The n trace gradients of the context's hyperparameters."""
+    out = np.zeros(max(1, int(n)), dtype=np.float64)
+    _check(load_library().qsel_trace_grads_n(ctx.handle, _ptr(out, c_double), int(n)), ctx.handle)
+    return out[:int(n)]
 
 
 def qsel_set_data(ctx: Context, y_obs):
