@@ -437,7 +437,9 @@ qsel_status qsel_debug_get_selinv_diag(const qsel_ctx *ctx, double *diag_out);
 qsel_status qsel_debug_get_lanczos(const qsel_ctx *ctx, double *alpha, double *beta, int32_t ld);
 /* Apply the context's PCG preconditioner to R (HOST, n x n_samples,
  * row-major, leading dimension ld) at the current theta and write Z = M^-1 R
- * (HOST, same layout).  FP64 contexts only (QSEL_ESTATE otherwise). */
+ * (HOST, same layout).  A QSEL_MIXED context applies its binary32
+ * preconditioner (R rounded to float, on the tensor cores where the mixed
+ * sampler uses them). */
 qsel_status qsel_debug_apply_precond(qsel_ctx *ctx, const double *R, double *Z, int32_t ld);
 
 /*

@@ -427,12 +427,15 @@ static Err kron_setup(qsel_ctx *c, const qsel_model *m) {
   TRY(c->alloc(&c->d_kU, (size_t)c->n_t * c->n_t));
   TRY(c->alloc(&c->d_kmu, (size_t)c->n_t));
   {
-    // V, V^T, U, U^T, dh dh^T, spec (KronOperator), each segment 16-byte aligned
+    // V, V^T, U, U^T, dh dh^T, spec (KronOperator), then for the mixed
+    // form's tensor-core passes V, V^T, U, U^T as TF32 hi and lo; each
+    // segment 256-byte aligned
     const size_t esz = c->mixed ? sizeof(float) : sizeof(double);
-    const size_t seg[6] = {(size_t)g * g, (size_t)g * g, (size_t)c->n_t * c->n_t, (size_t)c->n_t * c->n_t,
-                           (size_t)g * g, (size_t)c->n_t * g * g};
-    size_t off[6], total = 0;
-    for (int i = 0; i < 6; ++i) {
+    const size_t gg = (size_t)g * g, tt = (size_t)c->n_t * c->n_t;
+    const size_t seg[14] = {gg, gg, tt, tt, gg, (size_t)c->n_t * g * g, gg, gg, gg, gg, tt, tt, tt, tt};
+    const int nseg = c->mixed ? 14 : 6;
+    size_t off[14], total = 0;
+    for (int i = 0; i < nseg; ++i) {
       off[i] = total;
       total += (seg[i] * esz + 255) / 256 * 256;
     }
@@ -440,6 +443,9 @@ static Err kron_setup(qsel_ctx *c, const qsel_model *m) {
     char *b = static_cast<char *>(c->d_ktab);
     void **dst[6] = {&c->kop.tV, &c->kop.tVT, &c->kop.tU, &c->kop.tUT, &c->kop.dhdh, &c->kop.spec};
     for (int i = 0; i < 6; ++i) *dst[i] = b + off[i];
+    for (int q = 0; q < 4; ++q)
+      for (int h = 0; h < 2; ++h)
+        c->kop.split[q][h] = c->mixed ? reinterpret_cast<float *>(b + off[6 + 2 * q + h]) : nullptr;
   }
   c->kron = true;
   c->kron_m = g;
@@ -476,6 +482,9 @@ static Err kron_prepare(qsel_ctx *c) {
   k.kappa2 = std::exp(2.0 * c->theta.log_kappa);
   k.tau = std::exp(c->theta.log_tau);
   k.omega = (double)c->n_obs / (double)c->n * c->obs_w;
+  // the passes on the tensor cores in the mixed form with 3xTF32 products
+  k.use_tc = (c->mixed && c->tc_passes == 3 && kron_tc_supported(k.m, c->ld) && kron_tc_supported(n_t, c->ld)) ? 1 : 0;
+  k.err = c->d_err;
   if (c->mixed)
     launch_kron_tables<float>(c->stream, k);
   else
@@ -3049,11 +3058,34 @@ qsel_status qsel_debug_apply_precond(qsel_ctx *ctx, const double *R, double *Z, 
   if (!ctx) return QSEL_EINVAL;
   qsel_ctx *c = ctx;
   if (!R || !Z || ld < c->k) return finish(c, fail(QSEL_EINVAL, "NULL buffer or ld < n_samples"));
-  if (c->mixed) return finish(c, fail(QSEL_ESTATE, "the preconditioner hook needs an FP64 context"));
   cudaStream_t s = c->stream;
   Err e = run_model(c);
   if (e.code == 0 && c->kron) e = kron_prepare(c);
   if (e.code) return finish(c, e);
+  if (c->mixed) {
+    // the mixed form's binary32 preconditioner: R rounded to float, Z widened
+    const size_t vec = (size_t)c->n * c->ld;
+    std::vector<float> hr(vec, 0.0f), hz(vec);
+    for (int i = 0; i < c->n; ++i)
+      for (int j = 0; j < c->k; ++j) hr[(size_t)i * c->ld + j] = (float)R[(size_t)i * ld + j];
+    float *pblk = static_cast<float *>(c->d_pblk);
+    if (!c->kron) launch_jacobi_setup<float>(s, c->pat, c->mod, c->n_s, c->n_t, c->bsize, pblk, c->d_err);
+    cudaError_t ce = cudaMemcpyAsync(c->f_r, hr.data(), vec * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->d_scal, 0, (size_t)c->ld * sizeof(double), s);   // alpha = 0
+    if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "preconditioner input", __FILE__, __LINE__));
+    PcgVec<float> v = make_pcg<float>(c, c->f_x, c->f_r, c->f_z, c->f_p, c->f_q);
+    launch_pcg_update<float>(s, v, pblk, c->bsize, c->kron ? &c->kop : nullptr);
+    ce = cudaMemcpyAsync(hz.data(), c->f_z, vec * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "preconditioner output", __FILE__, __LINE__));
+    int32_t err = 0;
+    ce = cudaMemcpy(&err, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return finish(c, cuda_fail(ce, "error flag", __FILE__, __LINE__));
+    if (err & 2) return finish(c, fail(QSEL_ETIMEOUT, "a bounded device-side wait of the tensor-core pass gave up"));
+    for (int i = 0; i < c->n; ++i)
+      for (int j = 0; j < c->k; ++j) Z[(size_t)i * ld + j] = (double)hz[(size_t)i * c->ld + j];
+    return QSEL_OK;
+  }
   double *pblk = static_cast<double *>(c->d_pblk);
   if (!c->kron)
     launch_jacobi_setup<double>(s, c->pat, c->mod, c->n_s, c->n_t,

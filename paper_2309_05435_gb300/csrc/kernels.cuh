@@ -298,7 +298,7 @@ struct UpdateBatch {
 };
 bool launch_tc_update(cudaStream_t s, const UpdateBatch &b, int n, int K, int ldp, float alpha, float beta,
                       int32_t *err);
-// hi = rn_tf32(x), lo = rn_tf32(x - hi) elementwise (count a multiple of 4).
+// hi = rn_tf32(x), lo = rn_tf32(x - hi) elementwise (16-byte aligned arrays).
 void launch_split_tf32(cudaStream_t s, const float *src, float *hi, float *lo, int64_t count);
 // out[r, c] = alpha in[c, r] + beta c0[r, c] for each entry (see dense.cu).
 struct TransEntry {
@@ -420,7 +420,19 @@ struct KronOperator {
   // V, V^T, U, U^T, dh_i dh_j (m x m), spec[t m^2 + s] = 1 / (tau mu_t
   // (kappa^2 + lambda_a + lambda_b)^2 + omega) with s = a m + b
   void *tV, *tVT, *tU, *tUT, *dhdh, *spec;
+  // tensor-core passes (float tables only): V, V^T, U, U^T split into TF32
+  // hi / lo parts, [table][hi, lo]; use_tc selects them; err gets bit 1 when
+  // a bounded wait of the tensor-core pass gives up
+  float *split[4][2];
+  int use_tc;
+  int32_t *err;
 };
+// One pass on the tcgen05 tensor cores with op(B) given row-major as TF32
+// hi / lo parts (kron_tc.cu); false when the shape is not supported or a
+// tensor map cannot be encoded (nothing is launched then).
+bool kron_tc_supported(int dim, int ld);
+bool launch_kron_pass_tc(cudaStream_t s, const KronPass &p, const float *Bop_hi, const float *Bop_lo, const float *x,
+                         float *y, int32_t *err);
 template <typename T>
 void launch_kron_tables(cudaStream_t s, const KronOperator &op);
 template <typename T>

@@ -227,12 +227,32 @@ template <typename T>
 void launch_kron_tables(cudaStream_t s, const KronOperator &op) {
   ++g_launch_count;
   k_kron_tables<T><<<152, 256, 0, s>>>(op);
+  if constexpr (std::is_same<T, float>::value) {
+    if (op.use_tc) {
+      const int64_t mm = (int64_t)op.m * op.m, tt = (int64_t)op.n_t * op.n_t;
+      const void *src[4] = {op.tV, op.tVT, op.tU, op.tUT};
+      const int64_t cnt[4] = {mm, mm, tt, tt};
+      for (int q = 0; q < 4; ++q)
+        launch_split_tf32(s, static_cast<const float *>(src[q]), op.split[q][0], op.split[q][1], cnt[q]);
+    }
+  }
 }
 template void launch_kron_tables<double>(cudaStream_t, const KronOperator &);
 template void launch_kron_tables<float>(cudaStream_t, const KronOperator &);
 
 // z = M^-1 r: six passes, ping-pong between the scratch q and z (q is free
 // once the AXPY has consumed Q p); the result ends in z.
+// One pass y = op(B) x: on the tensor cores for float tables when the
+// operator has split tables (op(B) row-major is the transpose table of Bt:
+// table index bop), else on the CUDA cores.
+template <typename T>
+static void kron_pass(cudaStream_t s, const KronOperator &op, const KronPass &p, int bop, const T *x, T *y) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (op.use_tc && launch_kron_pass_tc(s, p, op.split[bop][0], op.split[bop][1], x, y, op.err)) return;
+  }
+  launch_kron_pass<T>(s, p, x, y);
+}
+
 template <typename T>
 void launch_kron_apply(cudaStream_t s, const KronOperator &op, const T *r, T *q, T *z) {
   const int m = op.m, n_s = m * m, n_t = op.n_t;
@@ -265,28 +285,28 @@ void launch_kron_apply(cudaStream_t s, const KronOperator &op, const T *r, T *q,
   KronPass a = over_i;          // (V^T over i) after the input scaling Dh (x) Dh
   a.Bt = op.tV;
   a.mode = KRON_IN_DH;
-  launch_kron_pass<T>(s, a, r, q);
+  kron_pass<T>(s, op, a, 1, r, q);
   KronPass b = over_j;          // V^T over j
   b.Bt = op.tV;
   b.mode = KRON_NONE;
-  launch_kron_pass<T>(s, b, q, z);
+  kron_pass<T>(s, op, b, 1, q, z);
   KronPass c = over_t;          // U^T over t, then the spectral scaling
   c.Bt = op.tU;
   c.mode = KRON_OUT_SPEC;
   c.scale = op.spec;
-  launch_kron_pass<T>(s, c, z, q);
+  kron_pass<T>(s, op, c, 3, z, q);
   KronPass d = over_t;          // U over t
   d.Bt = op.tUT;
   d.mode = KRON_NONE;
-  launch_kron_pass<T>(s, d, q, z);
+  kron_pass<T>(s, op, d, 2, q, z);
   KronPass e = over_j;          // V over j
   e.Bt = op.tVT;
   e.mode = KRON_NONE;
-  launch_kron_pass<T>(s, e, z, q);
+  kron_pass<T>(s, op, e, 0, z, q);
   KronPass f = over_i;          // V over i, then Dh (x) Dh
   f.Bt = op.tVT;
   f.mode = KRON_OUT_DH;
-  launch_kron_pass<T>(s, f, q, z);
+  kron_pass<T>(s, op, f, 0, q, z);
 }
 template void launch_kron_apply<double>(cudaStream_t, const KronOperator &, const double *, double *, double *);
 template void launch_kron_apply<float>(cudaStream_t, const KronOperator &, const float *, float *, float *);

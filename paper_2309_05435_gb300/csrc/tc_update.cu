@@ -245,9 +245,17 @@ __global__ void __launch_bounds__(192, 1) k_tc_update(const __grid_constant__ Pa
   }
 }
 
-// hi = rn_tf32(x), lo = rn_tf32(x - hi) for `count` floats (16-byte vectors).
+// hi = rn_tf32(x), lo = rn_tf32(x - hi) for `count` floats (16-byte vectors,
+// then the last count % 4 one by one).
 __global__ void __launch_bounds__(256) k_split_tf32(const float4 *__restrict__ src, float4 *__restrict__ hi,
-                                                    float4 *__restrict__ lo, int64_t count4) {
+                                                    float4 *__restrict__ lo, int64_t count4, int tail) {
+  if (blockIdx.x == 0 && (int)threadIdx.x < tail) {
+    const int64_t i = 4 * count4 + threadIdx.x;
+    const float v = reinterpret_cast<const float *>(src)[i];
+    const float h = tf32_rn(v);
+    reinterpret_cast<float *>(hi)[i] = h;
+    reinterpret_cast<float *>(lo)[i] = tf32_rn(v - h);
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count4; i += (int64_t)gridDim.x * blockDim.x) {
     const float4 v = src[i];
     float4 h, l;
@@ -275,7 +283,8 @@ void launch_split_tf32(cudaStream_t s, const float *src, float *hi, float *lo, i
   const int grid = (int)std::min<int64_t>((c4 + 255) / 256, 152 * 4);
   tcu::k_split_tf32<<<grid < 1 ? 1 : grid, 256, 0, s>>>(reinterpret_cast<const float4 *>(src),
                                                          reinterpret_cast<float4 *>(hi),
-                                                         reinterpret_cast<float4 *>(lo), c4);
+                                                         reinterpret_cast<float4 *>(lo), c4,
+                                                         (int)(count - 4 * c4));
 }
 
 bool launch_tc_update(cudaStream_t s, const UpdateBatch &b, int n, int K, int ldp, float alpha, float beta,

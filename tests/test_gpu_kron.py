@@ -36,6 +36,22 @@ def test_applied_preconditioner_matches_oracle(q, m, n_t, k):
     assert np.max(np.abs(Z - Z_or)) <= 1e-10 * np.max(np.abs(Z_or))
 
 
+@pytest.mark.parametrize("m,n_t,k", [(16, 8, 128), (12, 20, 128), (8, 68, 256), (16, 8, 64)])
+def test_mixed_preconditioner_matches_oracle(q, m, n_t, k):
+    """The mixed form's binary32 apply: on the tcgen05 tensor cores (3xTF32,
+    samples in blocks of 128, every dimension a multiple of 4 and <= 256:
+    n_t = 68 takes a partial K chunk and N padded to 80) or, for 64 samples,
+    on the CUDA cores; within binary32 accuracy (2e-5 of the largest entry)
+    of the oracle's FP64 operator applied to the same (rounded) input."""
+    ctx, model, th = _grid_ctx(q, m, n_t, k, preconditioner=q.QSEL_PRECOND_KRON, precision=q.QSEL_MIXED)
+    R = qi.seeded_normal((model.n, k), 19).astype(np.float32).astype(np.float64)
+    Z = q.qsel_debug_apply_precond(ctx, R)
+    Z_or = kr.preconditioner_inverse(model, th) @ R
+    err = np.max(np.abs(Z - Z_or)) / np.max(np.abs(Z_or))
+    print(f"m={m} n_t={n_t} k={k}: mixed apply error {err:.2e}")
+    assert err <= 2e-5
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_sampler_with_kron_preconditioner(q, precision):
     prec = q.QSEL_FP64 if precision == "fp64" else q.QSEL_MIXED
