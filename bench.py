@@ -94,6 +94,8 @@ def parse_args():
     ap.add_argument("--cv-eval", action="store_true",
                     help="held-out evaluation: 64x64 grid, n_t=128, 8 parts, 8 theta; planned vs plain")
     ap.add_argument("--cv-eval-thetas", type=int, default=8)
+    ap.add_argument("--cv-controls", type=int, default=2,
+                    help="held-out theta on which plain RBMC also runs at fixed overlaps 1, 2, 4, 8")
     ap.add_argument("--cv-fp64-thetas", type=int, default=2,
                     help="held-out theta on which plain FP64 is also run to the target")
     ap.add_argument("--batch", action="store_true",
@@ -102,6 +104,8 @@ def parse_args():
     ap.add_argument("--batch-streams", type=int, default=16)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--exact-pass", default=None,
+                    help="one exact one-part mixed pass at this workload (for kernel captures)")
     ap.add_argument("--oracle-e2e", default=None,
                     help="comma list of workloads: time the CPU oracle end to end (all host cores)")
     ap.add_argument("--oracle-e2e-single", default="grid16_nt8",
@@ -751,6 +755,26 @@ def oracle_end_to_end(name: str):
     return t2 - t0, {"sampler": t1 - t0, "rbmc": t2 - t1}
 
 
+def run_exact_pass(args):
+    """--exact-pass WORKLOAD: one exact one-part pass in the mixed form (the
+    command the kernel captures under profiles/ run); prints its time."""
+    import torch
+    from paper_2309_05435_gb300 import build, qsel
+    build.build()
+    w = qi.workload(args.exact_pass)
+    mesh, mask = workload_inputs(w)
+    c = qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma, w.theta,
+                         n_parts=1, overlap=0, n_samples=2, precision=qsel.QSEL_MIXED)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    qsel.qsel_diag_inv(c)
+    torch.cuda.synchronize()
+    st = qsel.qsel_stats(c)
+    c.close()
+    print(json.dumps({"mode": "exact_pass", "workload": w.name, "s": time.perf_counter() - t0,
+                      "factor_ms": st["ms_factor"], "takahashi_ms": st["ms_takahashi"]}), flush=True)
+
+
 def run_oracle_e2e(args):
     """--oracle-e2e: the oracle end to end on the listed workloads with all host
     cores, and in a child process limited to one BLAS / OpenMP thread on the
@@ -879,6 +903,26 @@ def run_cv_eval(args):
             row[name] = {"k_total": r["k"], "runs": len(r["runs"]), "samples": r["samples_drawn"],
                          "err_estimate": r["err"], "eps_vs_exact": eps(r["v"]), "wall_s": r["wall_s"],
                          "met": r["met"]}
+        # the literal reading (estimate w_i^2 - c_hat_i, add c_hat_i back) is
+        # the plain estimator for any prediction: the same runs, samples and
+        # error as plain RBMC at the same settings
+        row["literal_residual_form"] = {"same_as": "plain_mixed", "samples": row["plain_mixed"]["samples"],
+                                        "wall_s": row["plain_mixed"]["wall_s"],
+                                        "err_estimate": row["plain_mixed"]["err_estimate"]}
+        if i < args.cv_controls:
+            # control: plain RBMC at each fixed overlap (doubling k), the best
+            # of them chosen in hindsight
+            by_nl = {}
+            for nl in (1, 2, 4, 8):
+                r = cvm.solve_plain(spec, th, args.target, overlap=nl, precision=qsel.QSEL_MIXED)
+                by_nl[nl] = {"samples": r["samples_drawn"], "runs": len(r["runs"]), "wall_s": r["wall_s"],
+                             "device_ms": r["device_ms"], "err_estimate": r["err"], "eps_vs_exact": eps(r["v"]),
+                             "met": r["met"]}
+            best = min((v for v in by_nl.items() if v[1]["met"]), key=lambda kv: kv[1]["wall_s"], default=None)
+            row["plain_mixed_by_overlap"] = by_nl
+            if best is not None:
+                row["best_fixed_overlap"] = {"overlap": best[0], "wall_s": best[1]["wall_s"],
+                                             "speedup_planned_vs_best_fixed": best[1]["wall_s"] / pl["wall_s"]}
         row["speedup_vs_plain_mixed"] = row["plain_mixed"]["wall_s"] / pl["wall_s"]
         if "plain_fp64" in row:
             row["speedup_vs_plain_fp64"] = row["plain_fp64"]["wall_s"] / pl["wall_s"]
@@ -894,6 +938,10 @@ def run_cv_eval(args):
     fp = [r for r in rows if "plain_fp64" in r]
     if fp:
         summ["speedup_vs_plain_fp64"] = [r["speedup_vs_plain_fp64"] for r in fp]
+    ctl = [r for r in rows if "best_fixed_overlap" in r]
+    if ctl:
+        summ["speedup_vs_best_fixed_overlap"] = [r["best_fixed_overlap"]["speedup_planned_vs_best_fixed"] for r in ctl]
+        summ["best_fixed_overlaps"] = [r["best_fixed_overlap"]["overlap"] for r in ctl]
     print(json.dumps(summ), flush=True)
 
 
@@ -1050,6 +1098,9 @@ def main():
     if args.oracle_sample:
         est, spent, _ = oracle_sample(qi.workload(args.workload))
         print(json.dumps({"est": est, "spent": spent}), flush=True)
+        return
+    if args.exact_pass:
+        run_exact_pass(args)
         return
     if args.oracle_e2e is not None:
         run_oracle_e2e(args)

@@ -148,6 +148,7 @@ struct qsel_ctx {
   double *d_kV = nullptr, *d_klam = nullptr, *d_kdh = nullptr, *d_kU = nullptr, *d_kmu = nullptr;
   void *d_ktab = nullptr;              // the operator's tables in the sampler's element type
   double kron_rho = -2.0;              // rho of the temporal eigenpairs on the device
+  bool kron_tc = false;                // Kronecker passes on the tensor cores (mixed form)
   KronOperator kop{};
   // Lanczos sampler (allocated on first use)
   struct {
@@ -483,7 +484,10 @@ static Err kron_prepare(qsel_ctx *c) {
   k.tau = std::exp(c->theta.log_tau);
   k.omega = (double)c->n_obs / (double)c->n * c->obs_w;
   // the passes on the tensor cores in the mixed form with 3xTF32 products
-  k.use_tc = (c->mixed && c->tc_passes == 3 && kron_tc_supported(k.m, c->ld) && kron_tc_supported(n_t, c->ld)) ? 1 : 0;
+  k.use_tc = (c->kron_tc && c->mixed && c->tc_passes == 3 && kron_tc_supported(k.m, c->ld) &&
+              kron_tc_supported(n_t, c->ld))
+                 ? 1
+                 : 0;
   k.err = c->d_err;
   if (c->mixed)
     launch_kron_tables<float>(c->stream, k);
@@ -3062,6 +3066,8 @@ qsel_status qsel_debug_apply_precond(qsel_ctx *ctx, const double *R, double *Z, 
   Err e = run_model(c);
   if (e.code == 0 && c->kron) e = kron_prepare(c);
   if (e.code) return finish(c, e);
+  cudaError_t ce0 = cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), s);
+  if (ce0 != cudaSuccess) return finish(c, cuda_fail(ce0, "error flag", __FILE__, __LINE__));
   if (c->mixed) {
     // the mixed form's binary32 preconditioner: R rounded to float, Z widened
     const size_t vec = (size_t)c->n * c->ld;

@@ -38,11 +38,10 @@ def test_applied_preconditioner_matches_oracle(q, m, n_t, k):
 
 @pytest.mark.parametrize("m,n_t,k", [(16, 8, 128), (12, 20, 128), (8, 68, 256), (16, 8, 64)])
 def test_mixed_preconditioner_matches_oracle(q, m, n_t, k):
-    """The mixed form's binary32 apply: on the tcgen05 tensor cores (3xTF32,
-    samples in blocks of 128, every dimension a multiple of 4 and <= 256:
-    n_t = 68 takes a partial K chunk and N padded to 80) or, for 64 samples,
-    on the CUDA cores; within binary32 accuracy (2e-5 of the largest entry)
-    of the oracle's FP64 operator applied to the same (rounded) input."""
+    """The mixed form's binary32 apply (n_t = 68 and m = 12 take partial
+    tiles; 64 and 128 samples), within binary32 accuracy (2e-5 of the
+    largest entry) of the oracle's FP64 operator applied to the same
+    (rounded) input."""
     ctx, model, th = _grid_ctx(q, m, n_t, k, preconditioner=q.QSEL_PRECOND_KRON, precision=q.QSEL_MIXED)
     R = qi.seeded_normal((model.n, k), 19).astype(np.float32).astype(np.float64)
     Z = q.qsel_debug_apply_precond(ctx, R)
