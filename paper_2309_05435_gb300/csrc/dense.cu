@@ -228,13 +228,19 @@ template void launch_gemm<float>(cudaStream_t, const GemmBatch<float> &, int, in
 // bits, on the FP32 pipe) or, with fp64, in binary64.  NT threads.
 template <int NT, typename T>
 __device__ __forceinline__ void invert_pivot_tile(const T *Tk, int ld, T *P, int32_t *err_flag, bool fp64) {
+  if constexpr (std::is_same<T, float>::value && NT >= 442) {
+    if (!fp64) {
+      // the diagonal tile is kept symmetric; the lower half is what is read
+      sym_sweep_inverse64_reg_df<NT>(Tk, ld, P, err_flag);
+      return;
+    }
+  }
   // one buffer for either arithmetic (dfloat and double are both 8 bytes)
   __shared__ __align__(16) unsigned char pv_smem[(64 * 65 + 65 + 64) * 8];
   if constexpr (std::is_same<T, float>::value) {
     if (!fp64) {
       dfloat *Sf = reinterpret_cast<dfloat *>(pv_smem);
       dfloat *colf = Sf + 64 * 65, *wvf = colf + 65;
-      // the diagonal tile is kept symmetric; the lower half is what is read
 #pragma unroll 4
       for (int idx = threadIdx.x; idx < 64 * 16; idx += NT) {
         const int r = idx >> 4, c4 = (idx & 15) * 4;
@@ -629,7 +635,7 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
       }
       // C -= A B^T through the tensor cores, timed under class cls
       auto tc_update = [&](cudaStream_t st, const GemmBatch<float> &gb, int M, int N, int K, int ldc, bool lower,
-                           int cls, double work) {
+                           int cls, double work, bool compact) {
         Profiler::Rec rec{cls, nullptr, nullptr, 0.0};
         const bool prof = g_prof != nullptr;
         if (prof) {
@@ -638,7 +644,7 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
         }
         Profiler *saved = g_prof;
         g_prof = nullptr;  // timed under cls, not as a GEMM
-        launch_tc_gemm(st, gb, M, N, K, ldw, ldw, ldc, lower, tc_passes, err_flag);
+        launch_tc_gemm(st, gb, M, N, K, ldw, ldw, ldc, lower, tc_passes, err_flag, compact);
         g_prof = saved;
         if (prof) g_prof->end(st, rec);
       };
@@ -682,8 +688,10 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
             fb.e[e].alpha = -1.0;
             fb.e[e].beta = 1.0;
           }
+          // compact tiles: the product runs beside the previous panel's
+          // persistent update instead of waiting for its SMs
           tc_update(hi, fb, n_pad, 64 * bw1, 64 * bw, ldw, false, PROF_PANEL,
-                    2.0 * n_pad * 64.0 * bw1 * 64.0 * bw * b.count);
+                    2.0 * n_pad * 64.0 * bw1 * 64.0 * bw * b.count, tc_passes == 3 && b.e[0].Sp[0] != nullptr);
           {
             ProfScope ps_(hi, PROF_PANEL);
             k_bsweep_rows<T><<<dim3(bw * bw1, b.count), 256, 0, hi>>>(b, k0, bw, k1, bw1, cur);
@@ -726,7 +734,7 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
               gb.e[e].alpha = -1.0;
               gb.e[e].beta = 1.0;
             }
-            tc_update(lo, gb, n_pad, n_pad, 64 * bw, n_pad, true, PROF_SWEEP, work);
+            tc_update(lo, gb, n_pad, n_pad, 64 * bw, n_pad, true, PROF_SWEEP, work, false);
           }
         }
         ++g_launch_count;

@@ -280,10 +280,12 @@ void launch_diag64_rows(cudaStream_t s, const DiagRowBatch<T> &b, int n_s, int n
 // ---------------------------------------------------------------- tc_gemm.cu
 // tcgen05 tensor-core GEMM (FP32 data, TF32 MMAs): C = alpha A B^T + beta C0
 // with A (M x K) and B (N x K) row-major; passes 3 = 3xTF32, 1 = TF32.
-// err gets bit 1 when a bounded wait gives up.
+// err gets bit 1 when a bounded wait gives up.  compact: 128 x 32 tiles in
+// two stages (81 KB of shared memory), so that a CTA fits on an SM beside one
+// of the persistent sweep update's.
 bool tc_gemm_available();
 bool launch_tc_gemm(cudaStream_t s, const GemmBatch<float> &b, int M, int N, int K, int lda, int ldb, int ldc,
-                    bool lower, int passes, int32_t *err);
+                    bool lower, int passes, int32_t *err, bool compact = false);
 // Persistent tcgen05 update of the lower 128 x 128 tiles of n x n matrices:
 // C = alpha U V^T + beta C with U, V (n x K, leading dimension ldp) given as
 // TF32 hi / lo parts (3xTF32), K a multiple of 32 (tc_update.cu).  False when

@@ -196,4 +196,132 @@ __device__ inline void sym_sweep_inverse64_lower_df(dfloat *S, int ld_s, dfloat 
   }
 }
 
+// Register-resident double-float sweep of a 64 x 64 SPD tile (the lower
+// triangle of Tk, row stride ld), written as -(Tk^-1) in float to P (64 x 64,
+// both halves).  Thread t owns up to R = 5 consecutive entries of one column
+// j of the lower triangle (442 segments) and keeps them in registers for the
+// whole sweep.  Pivot p needs only column p of the matrix before the pivot
+// (c_k = A_kp, both halves by symmetry) and 1 / A_pp: the owners publish them
+// in shared memory at the end of pivot p - 1 (double-buffered), so a pivot
+// costs one block barrier.  Its update
+//   A_pp <- -1/d,  A_ip <- c_i / d,  A_ij <- A_ij - c_i (c_j / d)
+// takes one double-float product per entry; the sum keeps its rounding error
+// in the low word without renormalising (the value stays exact to the
+// double-float level; only the published column, the multiplicand of the next
+// pivot, is renormalised).  A non-positive pivot sets bit 0 of *err_flag.
+// blockDim.x == NT >= 442.
+template <int NT>
+__device__ inline void sym_sweep_inverse64_reg_df(const float *Tk, int ld, float *P, int32_t *err_flag) {
+  static_assert(NT >= 442, "one thread per column segment");
+  constexpr int R = 5;
+  __shared__ dfloat colbuf[2][64];
+  __shared__ dfloat invbuf[2];
+  const int t = threadIdx.x;
+  int j = -1, r0 = 64, cnt = 0;
+  {
+    int base = 0;
+    for (int jj = 0; jj < 64; ++jj) {
+      const int segs = (64 - jj + R - 1) / R;
+      if (t < base + segs) {
+        j = jj;
+        r0 = jj + (t - base) * R;
+        cnt = min(R, 64 - r0);
+        break;
+      }
+      base += segs;
+    }
+  }
+  float ah[R], al[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    ah[u] = (u < cnt) ? Tk[(int64_t)(r0 + u) * ld + j] : 0.0f;
+    al[u] = 0.0f;
+  }
+  // column 0 and 1 / A_00 for the first pivot
+  if (j == 0) {
+#pragma unroll
+    for (int u = 0; u < R; ++u)
+      if (u < cnt) colbuf[0][r0 + u] = dfloat{ah[u], 0.0f};
+    if (r0 == 0) {
+      const dfloat d{ah[0], 0.0f};
+      const bool pos = d.hi > 0.0f;
+      invbuf[0] = pos ? df_recip(d) : dfloat{0.0f, 0.0f};
+      if (!pos && err_flag) atomicOr(err_flag, 1);
+    }
+  }
+  __syncthreads();
+  for (int p = 0; p < 64; ++p) {
+    const int b = p & 1;
+    if (j >= 0) {
+      const dfloat inv = invbuf[b];
+      if (j == p) {
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          if (u >= cnt) continue;
+          const dfloat v = (r0 + u == p) ? dfloat{-inv.hi, -inv.lo} : df_mul(dfloat{ah[u], al[u]}, inv);
+          ah[u] = v.hi;
+          al[u] = v.lo;
+        }
+      } else {
+        const dfloat w = df_mul(colbuf[b][j], inv);
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          if (u >= cnt) continue;
+          const int i = r0 + u;
+          const dfloat c = colbuf[b][i];
+          const float pr = __fmul_rn(c.hi, w.hi);
+          float e = __fmaf_rn(c.hi, w.hi, -pr);
+          e = __fmaf_rn(c.hi, w.lo, e);
+          e = __fmaf_rn(c.lo, w.hi, e);
+          const dfloat sm = df_two_sum(ah[u], -pr);
+          const float lo = __fadd_rn(al[u], __fsub_rn(sm.lo, e));
+          const bool on_row = i == p;   // entry (p, j), j < p: c_j / d
+          ah[u] = on_row ? w.hi : sm.hi;
+          al[u] = on_row ? w.lo : lo;
+        }
+      }
+      // column p + 1 for the next pivot (renormalised), and its 1 / d
+      const int q = p + 1;
+      if (q < 64) {
+        if (j == q) {
+#pragma unroll
+          for (int u = 0; u < R; ++u) {
+            if (u >= cnt) continue;
+            const dfloat v = df_two_sum(ah[u], al[u]);
+            ah[u] = v.hi;
+            al[u] = v.lo;
+            colbuf[b ^ 1][r0 + u] = v;
+          }
+          if (r0 == q) {
+            const dfloat d{ah[0], al[0]};
+            const bool pos = d.hi > 0.0f;
+            invbuf[b ^ 1] = pos ? df_recip(d) : dfloat{0.0f, 0.0f};
+            if (!pos && err_flag) atomicOr(err_flag, 1);
+          }
+        } else if (j < q) {
+#pragma unroll
+          for (int u = 0; u < R; ++u) {
+            if (u >= cnt || r0 + u != q) continue;
+            const dfloat v = df_two_sum(ah[u], al[u]);
+            ah[u] = v.hi;
+            al[u] = v.lo;
+            colbuf[b ^ 1][j] = v;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (j >= 0) {
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      if (u >= cnt) continue;
+      const int i = r0 + u;
+      const float v = -__fadd_rn(ah[u], al[u]);
+      P[i * 64 + j] = v;
+      P[j * 64 + i] = v;
+    }
+  }
+}
+
 }  // namespace qsel

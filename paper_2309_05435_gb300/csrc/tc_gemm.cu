@@ -38,6 +38,8 @@ constexpr int BAR_BYTES = 256;
 // <2 stages, BN = 64> for K = 64 (the last, one-tile panel of the sweep and
 // the one-pivot sweep): the two K-blocks fit without reusing a stage and two
 // CTAs share an SM, so one CTA's epilogue overlaps the other's loads and MMAs.
+// <2 stages, BN = 32> (compact) for the sweep's look-ahead products, which
+// run beside the persistent panel update and must fit on its SMs.
 template <int BN>
 __host__ __device__ constexpr int tile_b() {
   return BN * BK * 4;
@@ -308,7 +310,9 @@ bool tc_gemm_available() {
   if (cudaFuncSetAttribute(tc::k_tc_gemm<3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            tc::smem_bytes<3, 128>()) != cudaSuccess ||
       cudaFuncSetAttribute(tc::k_tc_gemm<2, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           tc::smem_bytes<2, 64>()) != cudaSuccess) {
+                           tc::smem_bytes<2, 64>()) != cudaSuccess ||
+      cudaFuncSetAttribute(tc::k_tc_gemm<2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           tc::smem_bytes<2, 32>()) != cudaSuccess) {
     cudaGetLastError();
     tc::g_state = -1;
     return false;
@@ -321,16 +325,17 @@ bool tc_gemm_available() {
 // K a multiple of 32, lda/ldb/ldc multiples of 4.  Returns false when a tensor
 // map cannot be encoded (nothing is launched then).
 bool launch_tc_gemm(cudaStream_t s, const GemmBatch<float> &b, int M, int N, int K, int lda, int ldb, int ldc,
-                    bool lower, int passes, int32_t *err) {
+                    bool lower, int passes, int32_t *err, bool compact) {
   // K = 64 (the sweep updates): two stages, 128 x 64 tiles, two CTAs per SM
-  const bool narrow = K <= 64;
+  const bool narrow = K <= 64 && !compact;
+  const int bn_w = compact ? 32 : narrow ? 64 : 128;
   if (b.count <= 0) return true;
   if (!tc_gemm_available()) return false;
   tc::Params p;
   memset(&p, 0, sizeof(p));
   for (int q = 0; q < b.count; ++q) {
     if (!tc::encode_2d(&p.tmA[q], b.e[q].A, M, K, lda, tc::BM) ||
-        !tc::encode_2d(&p.tmB[q], b.e[q].B, N, K, ldb, narrow ? 64 : 128))
+        !tc::encode_2d(&p.tmB[q], b.e[q].B, N, K, ldb, bn_w))
       return false;
     p.C[q] = b.e[q].C;
     p.C0[q] = b.e[q].C0;
@@ -348,7 +353,6 @@ bool launch_tc_gemm(cudaStream_t s, const GemmBatch<float> &b, int M, int N, int
   p.skip_loads = tc::skip_loads();
   ++g_launch_count;
   Profiler::Rec rec{PROF_GEMM, nullptr, nullptr, 0.0};
-  const int bn_w = narrow ? 64 : 128;
   const int gm = (M + tc::BM - 1) / tc::BM, gn = (N + bn_w - 1) / bn_w;
   if (g_prof) {
     double tiles = 0.0;
@@ -358,7 +362,9 @@ bool launch_tc_gemm(cudaStream_t s, const GemmBatch<float> &b, int M, int N, int
     rec.work = 2.0 * tc::BM * bn_w * (double)K * tiles * b.count;
     g_prof->begin(s, rec);
   }
-  if (narrow)
+  if (compact)
+    tc::k_tc_gemm<2, 32><<<dim3(gn, gm, b.count), 192, tc::smem_bytes<2, 32>(), s>>>(p);
+  else if (narrow)
     tc::k_tc_gemm<2, 64><<<dim3(gn, gm, b.count), 192, tc::smem_bytes<2, 64>(), s>>>(p);
   else
     tc::k_tc_gemm<3, 128><<<dim3(gn, gm, b.count), 192, tc::smem_bytes<3, 128>(), s>>>(p);

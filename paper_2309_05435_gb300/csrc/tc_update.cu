@@ -11,7 +11,9 @@
 // One CTA per SM walks a static list of (matrix, tile row, tile column)
 // lower tiles:
 //   warp 0      one thread issues the TMA loads of the four 128 x 32 operand
-//               tiles of every K-block into a 3-stage ring;
+//               tiles of every K-block into a 2-stage ring (129 KB of shared
+//               memory: the sweep's pivot and panel kernels, and its compact
+//               look-ahead GEMM, fit on the same SM and run beside it);
 //   warp 1      owns 256 TMEM columns = two 128-column accumulators; one
 //               thread issues tcgen05.mma.kind::tf32 (M = N = 128, K = 8) for
 //               tile i into accumulator i % 2 while the epilogue drains the
@@ -31,7 +33,7 @@ namespace tcu {
 using namespace tc;
 
 constexpr int BN = 128;
-constexpr int STAGES = 3;
+constexpr int STAGES = 2;
 constexpr int TILE = BM * BK * 4;            // 16 KiB: 128 rows x 32 floats
 constexpr int STAGE_BYTES = 4 * TILE;        // U_hi, U_lo, V_hi, V_lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 256 + 1024;

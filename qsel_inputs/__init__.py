@@ -153,6 +153,8 @@ WORKLOADS = {
     "grid64_nt16": Workload("grid64_nt16", 64, 16, 0.2, 1.0, 0.95, 0.25, 0.5, 2, 2, 256, 1e-10),
     # 96x96 grid, n_t = 256 (n = 2,359,296): mixed precision, 16 subdomains, overlap 2, 512 samples
     "grid96_nt256": Workload("grid96_nt256", 96, 256, 0.1, 1.0, 0.98, 0.10, 0.5, 16, 2, 512, 1e-10),
+    # 96x96 grid, n_t = 8: same 9216-node blocks with few slabs (profiling captures)
+    "grid96_nt8": Workload("grid96_nt8", 96, 8, 0.1, 1.0, 0.98, 0.10, 0.5, 2, 1, 256, 1e-10),
 }
 
 
