@@ -148,7 +148,7 @@ struct qsel_ctx {
   double *d_kV = nullptr, *d_klam = nullptr, *d_kdh = nullptr, *d_kU = nullptr, *d_kmu = nullptr;
   void *d_ktab = nullptr;              // the operator's tables in the sampler's element type
   double kron_rho = -2.0;              // rho of the temporal eigenpairs on the device
-  bool kron_tc = false;                // Kronecker passes on the tensor cores (mixed form)
+  bool kron_tc = true;                 // Kronecker apply on the tensor cores (mixed form)
   KronOperator kop{};
   // Lanczos sampler (allocated on first use)
   struct {

@@ -429,12 +429,11 @@ struct KronOperator {
   int use_tc;
   int32_t *err;
 };
-// One pass on the tcgen05 tensor cores with op(B) given row-major as TF32
-// hi / lo parts (kron_tc.cu); false when the shape is not supported or a
-// tensor map cannot be encoded (nothing is launched then).
+// The whole apply z = M^-1 r on the tcgen05 tensor cores (kron_tc.cu), q as
+// scratch; false when the shape is not supported or a tensor map cannot be
+// encoded (nothing is launched then).
 bool kron_tc_supported(int dim, int ld);
-bool launch_kron_pass_tc(cudaStream_t s, const KronPass &p, const float *Bop_hi, const float *Bop_lo, const float *x,
-                         float *y, int32_t *err);
+bool launch_kron_apply_tc(cudaStream_t s, const KronOperator &op, const float *r, float *q, float *z);
 template <typename T>
 void launch_kron_tables(cudaStream_t s, const KronOperator &op);
 template <typename T>

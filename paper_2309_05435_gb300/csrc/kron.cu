@@ -241,20 +241,16 @@ template void launch_kron_tables<double>(cudaStream_t, const KronOperator &);
 template void launch_kron_tables<float>(cudaStream_t, const KronOperator &);
 
 // z = M^-1 r: six passes, ping-pong between the scratch q and z (q is free
-// once the AXPY has consumed Q p); the result ends in z.
-// One pass y = op(B) x: on the tensor cores for float tables when the
-// operator has split tables (op(B) row-major is the transpose table of Bt:
-// table index bop), else on the CUDA cores.
-template <typename T>
-static void kron_pass(cudaStream_t s, const KronOperator &op, const KronPass &p, int bop, const T *x, T *y) {
-  if constexpr (std::is_same<T, float>::value) {
-    if (op.use_tc && launch_kron_pass_tc(s, p, op.split[bop][0], op.split[bop][1], x, y, op.err)) return;
-  }
-  launch_kron_pass<T>(s, p, x, y);
-}
-
+// once the AXPY has consumed Q p); the result ends in z.  With split float
+// tables the whole apply runs on the tensor cores (kron_tc.cu).
 template <typename T>
 void launch_kron_apply(cudaStream_t s, const KronOperator &op, const T *r, T *q, T *z) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (op.use_tc) {
+      ProfScope ps_(s, PROF_PRECOND);
+      if (launch_kron_apply_tc(s, op, r, q, z)) return;
+    }
+  }
   const int m = op.m, n_s = m * m, n_t = op.n_t;
   KronPass p{};
   p.ld = op.ld;
@@ -285,28 +281,28 @@ void launch_kron_apply(cudaStream_t s, const KronOperator &op, const T *r, T *q,
   KronPass a = over_i;          // (V^T over i) after the input scaling Dh (x) Dh
   a.Bt = op.tV;
   a.mode = KRON_IN_DH;
-  kron_pass<T>(s, op, a, 1, r, q);
+  launch_kron_pass<T>(s, a, r, q);
   KronPass b = over_j;          // V^T over j
   b.Bt = op.tV;
   b.mode = KRON_NONE;
-  kron_pass<T>(s, op, b, 1, q, z);
+  launch_kron_pass<T>(s, b, q, z);
   KronPass c = over_t;          // U^T over t, then the spectral scaling
   c.Bt = op.tU;
   c.mode = KRON_OUT_SPEC;
   c.scale = op.spec;
-  kron_pass<T>(s, op, c, 3, z, q);
+  launch_kron_pass<T>(s, c, z, q);
   KronPass d = over_t;          // U over t
   d.Bt = op.tUT;
   d.mode = KRON_NONE;
-  kron_pass<T>(s, op, d, 2, q, z);
+  launch_kron_pass<T>(s, d, q, z);
   KronPass e = over_j;          // V over j
   e.Bt = op.tVT;
   e.mode = KRON_NONE;
-  kron_pass<T>(s, op, e, 0, z, q);
+  launch_kron_pass<T>(s, e, z, q);
   KronPass f = over_i;          // V over i, then Dh (x) Dh
   f.Bt = op.tVT;
   f.mode = KRON_OUT_DH;
-  kron_pass<T>(s, op, f, 0, q, z);
+  launch_kron_pass<T>(s, f, q, z);
 }
 template void launch_kron_apply<double>(cudaStream_t, const KronOperator &, const double *, double *, double *);
 template void launch_kron_apply<float>(cudaStream_t, const KronOperator &, const float *, float *, float *);

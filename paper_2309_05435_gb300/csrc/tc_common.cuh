@@ -59,6 +59,34 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm,
       : "memory");
 }
 
+// 4-D tiled load: coordinates innermost first.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *tm, int x0, int x1, int x2, int x3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x0), "r"(x1), "r"(x2), "r"(x3), "r"(bar)
+      : "memory");
+}
+
+// 4-D tiled store from shared memory (bulk async-group of the issuing
+// thread); parts of the box outside the tensor are not written.
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *tm, uint32_t src, int x0, int x1, int x2, int x3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+          reinterpret_cast<uint64_t>(tm)),
+      "r"(src), "r"(x0), "r"(x1), "r"(x2), "r"(x3)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// until at most N of this thread's bulk groups still read shared memory
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+// until every bulk group of this thread has completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // Shared-memory matrix descriptor: K-major operand tile with 128-byte rows
 // and the 128B swizzle; 8-row core groups 1024 bytes apart (SBO), descriptor
 // version 1, layout type 2 (SWIZZLE_128B).  The start address advances by 32
@@ -123,6 +151,15 @@ __device__ __forceinline__ float tf32_rn(float x) {
 // with boxes of BK columns x box_rows rows, 128B swizzle, zero fill outside
 // (tc_gemm.cu; needs tc_gemm_available() first).
 bool encode_2d(CUtensorMap *tm, const float *ptr, int rows, int cols, int ld, int box_rows);
+// Tensor map of a 4-D FP32 array: dims[0] innermost (contiguous), byte
+// strides of dims 1-3, box {BK, box[1], box[2], box[3]}; 128B swizzle, zero
+// fill outside.
+bool encode_4d(CUtensorMap *tm, const float *ptr, const uint64_t dims[4], const uint64_t strides[3],
+               const uint32_t box[4]);
+// The same without swizzle and with the full box given (box[0] elements
+// innermost, a multiple of 4): the layout of a staged store tile.
+bool encode_4d_plain(CUtensorMap *tm, const float *ptr, const uint64_t dims[4], const uint64_t strides[3],
+                     const uint32_t box[4]);
 // Limits of the bounded waits and the test hook's skip flag (tc_gemm.cu).
 long long wait_limit();
 int skip_loads();
