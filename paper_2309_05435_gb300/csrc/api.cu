@@ -51,6 +51,7 @@ struct DenseSlot {
   void *P = nullptr, *U = nullptr, *Vs = nullptr, *Vk = nullptr;  // sweep scratch
   void *U2 = nullptr, *V2 = nullptr, *Wp = nullptr, *Wp2 = nullptr;  // tensor-core sweep panels
   void *Sp[4] = {nullptr, nullptr, nullptr, nullptr};  // the panel update's operands split into TF32 hi / lo
+  void *Gs[4] = {nullptr, nullptr, nullptr, nullptr};  // Takahashi operands split into TF32 hi / lo (2 matrices)
   void *wbuf = nullptr;                // T_max x n_pad x ld correction samples
   void *tra = nullptr, *trb = nullptr; // ld x n_pad transposes (tensor-core correction products)
   void *ybuf = nullptr, *tmp = nullptr, *bright = nullptr;
@@ -795,7 +796,7 @@ static Err build_rest(qsel_ctx *c, const RestInputs &in, const qsel_partition *p
   // 64 kSweepPanel each), Vk (64 kSweepPanel x 64) and P (64 x 64)
   const size_t panel = (size_t)n_pad * 64 * kSweepPanel * esz;
   const bool split_panels = c->mixed && c->tc_passes == 3;
-  const size_t per_slot = (size_t)(c->T_max + 5) * mat + (split_panels ? 10 : 6) * panel +
+  const size_t per_slot = (size_t)(c->T_max + 5 + (split_panels ? 4 : 0)) * mat + (split_panels ? 10 : 6) * panel +
                           (size_t)(kSweepPanel + 1) * 64 * 64 * esz +
                           (size_t)(c->T_max + 5) * svec + 4096;
   size_t free_b = 0, total_b = 0;
@@ -821,8 +822,10 @@ static Err build_rest(qsel_ctx *c, const RestInputs &in, const qsel_partition *p
     TRY(c->alloc_bytes(&sl.U2, panel));
     TRY(c->alloc_bytes(&sl.V2, panel));
     TRY(c->alloc_bytes(&sl.Wp2, panel));
-    if (split_panels)
+    if (split_panels) {
       for (auto &sp : sl.Sp) TRY(c->alloc_bytes(&sp, panel));
+      for (auto &gs : sl.Gs) TRY(c->alloc_bytes(&gs, mat));
+    }
     TRY(c->alloc_bytes(&sl.Vk, (size_t)kSweepPanel * 64 * 64 * esz));
     TRY(c->alloc_bytes(&sl.wbuf, (size_t)c->T_max * svec));
     TRY(c->alloc_bytes(&sl.ybuf, svec));
@@ -1504,11 +1507,49 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         }
         if (active.empty()) break;
         launch_sp_colgather<T>(s, wb, c->pat, n_s, n_pad);
-        if (!launch_tc_gemm(s, yb, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, false, c->tc_passes, c->d_err))
-          return fail(QSEL_ECUDA, "tensor-core GEMM: tensor map encoding failed");
-        launch_extract<T>(s, xy, c->pat, c->dmod.n, n_s, n_pad, c->d_diag_scratch);
-        if (!launch_tc_gemm(s, sgb, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, true, c->tc_passes, c->d_err))
-          return fail(QSEL_ECUDA, "tensor-core GEMM: tensor map encoding failed");
+        const int64_t mm = (int64_t)n_pad * n_pad;
+        if (slot(active[0]).Gs[0] != nullptr) {
+          // 3xTF32 on operands split once in HBM: W and Sigma_{t+1}, then
+          // Y; the persistent 128 x 256-tile kernel
+          SplitGemmBatch y2{}, s2{};
+          {
+            ProfScope ps_(s, PROF_GATHER);
+            for (int q = 0; q < yb.count; ++q) {
+              DenseSlot &sl = slot(active[q]);
+              launch_split_tf32(s, yb.e[q].A, static_cast<float *>(sl.Gs[0]), static_cast<float *>(sl.Gs[1]), mm);
+              launch_split_tf32(s, yb.e[q].B, static_cast<float *>(sl.Gs[2]), static_cast<float *>(sl.Gs[3]), mm);
+              y2.e[y2.count++] = SplitGemmEntry{static_cast<float *>(sl.Gs[0]), static_cast<float *>(sl.Gs[1]),
+                                                static_cast<float *>(sl.Gs[2]), static_cast<float *>(sl.Gs[3]),
+                                                nullptr, yb.e[q].C, 1.0f, 0.0f};
+            }
+          }
+          if (!launch_tc_gemm_split(s, y2, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, false, c->d_err))
+            return fail(QSEL_ECUDA, "tensor-core GEMM: tensor map encoding failed");
+          launch_extract<T>(s, xy, c->pat, c->dmod.n, n_s, n_pad, c->d_diag_scratch);
+          {
+            // the parts with a Sigma_t product (the first sgb.count active parts
+            // in order); Y's parts replace Sigma_{t+1}'s
+            ProfScope ps_(s, PROF_GATHER);
+            int q = 0;
+            for (int a = 0; a < (int)active.size() && q < sgb.count; ++a) {
+              DenseSlot &sl = slot(active[a]);
+              if (sgb.e[q].A != buf(sl.Y)) continue;
+              launch_split_tf32(s, buf(sl.Y), static_cast<float *>(sl.Gs[2]), static_cast<float *>(sl.Gs[3]), mm);
+              s2.e[s2.count++] = SplitGemmEntry{static_cast<float *>(sl.Gs[2]), static_cast<float *>(sl.Gs[3]),
+                                                static_cast<float *>(sl.Gs[0]), static_cast<float *>(sl.Gs[1]),
+                                                sgb.e[q].C0, sgb.e[q].C, 1.0f, 1.0f};
+              ++q;
+            }
+          }
+          if (!launch_tc_gemm_split(s, s2, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, true, c->d_err))
+            return fail(QSEL_ECUDA, "tensor-core GEMM: tensor map encoding failed");
+        } else {
+          if (!launch_tc_gemm(s, yb, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, false, c->tc_passes, c->d_err))
+            return fail(QSEL_ECUDA, "tensor-core GEMM: tensor map encoding failed");
+          launch_extract<T>(s, xy, c->pat, c->dmod.n, n_s, n_pad, c->d_diag_scratch);
+          if (!launch_tc_gemm(s, sgb, n_pad, n_pad, n_pad, n_pad, n_pad, n_pad, true, c->tc_passes, c->d_err))
+            return fail(QSEL_ECUDA, "tensor-core GEMM: tensor map encoding failed");
+        }
         launch_diag64_rows<T>(s, db, n_s, n_pad);
         launch_mirror<T>(s, mb, n_pad);
         launch_extract<T>(s, xs, c->pat, c->dmod.n, n_s, n_pad, c->d_diag_scratch);

@@ -300,6 +300,23 @@ struct UpdateBatch {
 };
 bool launch_tc_update(cudaStream_t s, const UpdateBatch &b, int n, int K, int ldp, float alpha, float beta,
                       int32_t *err);
+// C = alpha A B^T + beta C0 on operands given as TF32 hi / lo parts (A: M x K,
+// B: N x K, row-major; K a multiple of 32, leading dimensions multiples of 4):
+// the persistent 128 x 256-tile kernel of tc_gemm2.cu.  lower = only the tiles
+// on or below the diagonal.  False when a tensor map cannot be encoded
+// (nothing is launched then).
+struct SplitGemmEntry {
+  const float *Ah, *Al, *Bh, *Bl;
+  const float *C0;
+  float *C;
+  float alpha, beta;
+};
+struct SplitGemmBatch {
+  SplitGemmEntry e[kMaxBatch];
+  int count;
+};
+bool launch_tc_gemm_split(cudaStream_t s, const SplitGemmBatch &b, int M, int N, int K, int lda, int ldb, int ldc,
+                          bool lower, int32_t *err);
 // hi = rn_tf32(x), lo = rn_tf32(x - hi) elementwise (16-byte aligned arrays).
 void launch_split_tf32(cudaStream_t s, const float *src, float *hi, float *lo, int64_t count);
 // out[r, c] = alpha in[c, r] + beta c0[r, c] for each entry (see dense.cu).
