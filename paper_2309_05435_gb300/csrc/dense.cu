@@ -228,15 +228,17 @@ template void launch_gemm<float>(cudaStream_t, const GemmBatch<float> &, int, in
 // bits, on the FP32 pipe) or, with fp64, in binary64.  NT threads.
 template <int NT, typename T>
 __device__ __forceinline__ void invert_pivot_tile(const T *Tk, int ld, T *P, int32_t *err_flag, bool fp64) {
-  if constexpr (std::is_same<T, float>::value && NT >= 442) {
+  // one buffer for either arithmetic (dfloat and double are both 8 bytes)
+  constexpr int kSweepBytes = (64 * 65 + 65 + 64) * 8;
+  constexpr int kBytes = (int)sizeof(Inverse64Smem) > kSweepBytes ? (int)sizeof(Inverse64Smem) : kSweepBytes;
+  __shared__ __align__(16) unsigned char pv_smem[kBytes];
+  if constexpr (std::is_same<T, float>::value && NT >= 512) {
     if (!fp64) {
       // the diagonal tile is kept symmetric; the lower half is what is read
-      sym_sweep_inverse64_reg_df<NT>(Tk, ld, P, err_flag);
+      sym_inverse64_df_2x2<NT>(Tk, ld, P, *reinterpret_cast<Inverse64Smem *>(pv_smem), err_flag);
       return;
     }
   }
-  // one buffer for either arithmetic (dfloat and double are both 8 bytes)
-  __shared__ __align__(16) unsigned char pv_smem[(64 * 65 + 65 + 64) * 8];
   if constexpr (std::is_same<T, float>::value) {
     if (!fp64) {
       dfloat *Sf = reinterpret_cast<dfloat *>(pv_smem);

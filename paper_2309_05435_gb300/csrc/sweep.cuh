@@ -196,131 +196,163 @@ __device__ inline void sym_sweep_inverse64_lower_df(dfloat *S, int ld_s, dfloat 
   }
 }
 
-// Register-resident double-float sweep of a 64 x 64 SPD tile (the lower
-// triangle of Tk, row stride ld), written as -(Tk^-1) in float to P (64 x 64,
-// both halves).  Thread t owns up to R = 5 consecutive entries of one column
-// j of the lower triangle (442 segments) and keeps them in registers for the
-// whole sweep.  Pivot p needs only column p of the matrix before the pivot
-// (c_k = A_kp, both halves by symmetry) and 1 / A_pp: the owners publish them
-// in shared memory at the end of pivot p - 1 (double-buffered), so a pivot
-// costs one block barrier.  Its update
-//   A_pp <- -1/d,  A_ip <- c_i / d,  A_ij <- A_ij - c_i (c_j / d)
-// takes one double-float product per entry; the sum keeps its rounding error
-// in the low word without renormalising (the value stays exact to the
-// double-float level; only the published column, the multiplicand of the next
-// pivot, is renormalised).  A non-positive pivot sets bit 0 of *err_flag.
-// blockDim.x == NT >= 442.
+// acc += a b in double-float: the product's rounding error (exact through the
+// FMA) and the two-sum error of the addition collect in acc.lo, which stays a
+// few ulp of acc.hi over a short sum; df_renorm makes the pair canonical.
+__device__ __forceinline__ void df_fma_acc(dfloat &acc, dfloat a, dfloat b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const dfloat s = df_two_sum(acc.hi, p);
+  acc.hi = s.hi;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, e));
+}
+__device__ __forceinline__ dfloat df_renorm(dfloat a) { return df_two_sum(a.hi, a.lo); }
+
+// Scalar sweep of a 32 x 32 SPD block held in the lower triangle of S (row
+// stride 33) in double-float: after the 32 pivots the lower triangle holds that
+// of -S^-1, then both halves are filled.  Each pivot: threads 0-31 snapshot
+// column p (c_k) and w_k = c_k / d, then the owner of each lower entry (528,
+// about one per thread) applies S_ij - c_i w_j.  col holds 33 entries (col[32]
+// = 1 / d), w 32.  blockDim.x == NT.
 template <int NT>
-__device__ inline void sym_sweep_inverse64_reg_df(const float *Tk, int ld, float *P, int32_t *err_flag) {
-  static_assert(NT >= 442, "one thread per column segment");
-  constexpr int R = 5;
-  __shared__ dfloat colbuf[2][64];
-  __shared__ dfloat invbuf[2];
-  const int t = threadIdx.x;
-  int j = -1, r0 = 64, cnt = 0;
-  {
-    int base = 0;
-    for (int jj = 0; jj < 64; ++jj) {
-      const int segs = (64 - jj + R - 1) / R;
-      if (t < base + segs) {
-        j = jj;
-        r0 = jj + (t - base) * R;
-        cnt = min(R, 64 - r0);
-        break;
-      }
-      base += segs;
+__device__ inline void df_sweep32(dfloat *S, dfloat *col, dfloat *w, int32_t *err_flag) {
+  constexpr int EPT = (528 + NT - 1) / NT;
+  int ei[EPT], ej[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = (int)threadIdx.x + q * NT;
+    ei[q] = -1;
+    ej[q] = 0;
+    if (e < 528) {
+      int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      while (i * (i + 1) / 2 > e) --i;
+      ei[q] = i;
+      ej[q] = e - i * (i + 1) / 2;
     }
   }
-  float ah[R], al[R];
-#pragma unroll
-  for (int u = 0; u < R; ++u) {
-    ah[u] = (u < cnt) ? Tk[(int64_t)(r0 + u) * ld + j] : 0.0f;
-    al[u] = 0.0f;
-  }
-  // column 0 and 1 / A_00 for the first pivot
-  if (j == 0) {
-#pragma unroll
-    for (int u = 0; u < R; ++u)
-      if (u < cnt) colbuf[0][r0 + u] = dfloat{ah[u], 0.0f};
-    if (r0 == 0) {
-      const dfloat d{ah[0], 0.0f};
+  for (int p = 0; p < 32; ++p) {
+    if (threadIdx.x < 32) {
+      const int k = threadIdx.x;
+      const dfloat d = S[p * 33 + p];
       const bool pos = d.hi > 0.0f;
-      invbuf[0] = pos ? df_recip(d) : dfloat{0.0f, 0.0f};
-      if (!pos && err_flag) atomicOr(err_flag, 1);
-    }
-  }
-  __syncthreads();
-  for (int p = 0; p < 64; ++p) {
-    const int b = p & 1;
-    if (j >= 0) {
-      const dfloat inv = invbuf[b];
-      if (j == p) {
-#pragma unroll
-        for (int u = 0; u < R; ++u) {
-          if (u >= cnt) continue;
-          const dfloat v = (r0 + u == p) ? dfloat{-inv.hi, -inv.lo} : df_mul(dfloat{ah[u], al[u]}, inv);
-          ah[u] = v.hi;
-          al[u] = v.lo;
-        }
-      } else {
-        const dfloat w = df_mul(colbuf[b][j], inv);
-#pragma unroll
-        for (int u = 0; u < R; ++u) {
-          if (u >= cnt) continue;
-          const int i = r0 + u;
-          const dfloat c = colbuf[b][i];
-          const float pr = __fmul_rn(c.hi, w.hi);
-          float e = __fmaf_rn(c.hi, w.hi, -pr);
-          e = __fmaf_rn(c.hi, w.lo, e);
-          e = __fmaf_rn(c.lo, w.hi, e);
-          const dfloat sm = df_two_sum(ah[u], -pr);
-          const float lo = __fadd_rn(al[u], __fsub_rn(sm.lo, e));
-          const bool on_row = i == p;   // entry (p, j), j < p: c_j / d
-          ah[u] = on_row ? w.hi : sm.hi;
-          al[u] = on_row ? w.lo : lo;
-        }
-      }
-      // column p + 1 for the next pivot (renormalised), and its 1 / d
-      const int q = p + 1;
-      if (q < 64) {
-        if (j == q) {
-#pragma unroll
-          for (int u = 0; u < R; ++u) {
-            if (u >= cnt) continue;
-            const dfloat v = df_two_sum(ah[u], al[u]);
-            ah[u] = v.hi;
-            al[u] = v.lo;
-            colbuf[b ^ 1][r0 + u] = v;
-          }
-          if (r0 == q) {
-            const dfloat d{ah[0], al[0]};
-            const bool pos = d.hi > 0.0f;
-            invbuf[b ^ 1] = pos ? df_recip(d) : dfloat{0.0f, 0.0f};
-            if (!pos && err_flag) atomicOr(err_flag, 1);
-          }
-        } else if (j < q) {
-#pragma unroll
-          for (int u = 0; u < R; ++u) {
-            if (u >= cnt || r0 + u != q) continue;
-            const dfloat v = df_two_sum(ah[u], al[u]);
-            ah[u] = v.hi;
-            al[u] = v.lo;
-            colbuf[b ^ 1][j] = v;
-          }
-        }
+      const dfloat inv = pos ? df_recip(d) : dfloat{0.0f, 0.0f};
+      const dfloat c = (k >= p) ? S[k * 33 + p] : S[p * 33 + k];
+      col[k] = c;
+      w[k] = df_mul(c, inv);
+      if (k == 0) {
+        col[32] = inv;
+        if (!pos && err_flag) atomicOr(err_flag, 1);
       }
     }
     __syncthreads();
-  }
-  if (j >= 0) {
 #pragma unroll
-    for (int u = 0; u < R; ++u) {
-      if (u >= cnt) continue;
-      const int i = r0 + u;
-      const float v = -__fadd_rn(ah[u], al[u]);
-      P[i * 64 + j] = v;
-      P[j * 64 + i] = v;
+    for (int q = 0; q < EPT; ++q) {
+      const int i = ei[q], j = ej[q];
+      if (i < 0) continue;
+      dfloat v;
+      if (i == p && j == p)
+        v = dfloat{-col[32].hi, -col[32].lo};
+      else if (i == p)
+        v = w[j];
+      else if (j == p)
+        v = w[i];
+      else
+        v = df_sub(S[i * 33 + j], df_mul(col[i], w[j]));
+      S[i * 33 + j] = v;   // read only by its owner during the pivot
     }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < 1024; e += NT) {
+    const int i = e >> 5, j = e & 31;
+    if (i < j) S[i * 33 + j] = S[j * 33 + i];
+  }
+  __syncthreads();
+}
+
+// Shared scratch of sym_inverse64_df_2x2: the three blocks of the tile and
+// the two products, 32 x 32 each with row stride 33.
+struct Inverse64Smem {
+  dfloat B11[32 * 33], B21[32 * 33], B22[32 * 33], U[32 * 33], X[32 * 33];
+  dfloat col[33], w[32];
+};
+
+// P = Tk^-1 (64 x 64 float, both halves) for the SPD tile whose lower half is
+// at Tk (row stride ld), in double-float, as a 2 x 2 block sweep: sweeping the
+// index blocks K1 = [0, 32) and then K2 = [32, 64) is the same as sweeping the
+// 64 indices one by one, and reads (N = -inverse of a swept block)
+//   N11 = -B11^-1,  U = B21 B11^-1 = -B21 N11,  B22' = B22 - U B21^T,
+//   N22 = -B22'^-1, X = B22'^-1 U = -N22 U,
+//   -Tk^-1 = [[N11 - U^T X, X^T], [X, N22]].
+// The 32 x 32 sweeps take one barrier pair per pivot with about one entry per
+// thread; the four 32-term block products run on all threads with their
+// sums in double-float.  A non-positive pivot sets bit 0 of *err_flag.
+// blockDim.x == NT >= 512.
+template <int NT>
+__device__ inline void sym_inverse64_df_2x2(const float *Tk, int ld, float *P, Inverse64Smem &S,
+                                             int32_t *err_flag) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 1024; e += NT) {
+    const int i = e >> 5, j = e & 31;
+    S.B11[i * 33 + j] = dfloat{Tk[(int64_t)max(i, j) * ld + min(i, j)], 0.0f};
+    S.B21[i * 33 + j] = dfloat{Tk[(int64_t)(32 + i) * ld + j], 0.0f};
+    if (i >= j) S.B22[i * 33 + j] = dfloat{Tk[(int64_t)(32 + i) * ld + 32 + j], 0.0f};
+  }
+  __syncthreads();
+  df_sweep32<NT>(S.B11, S.col, S.w, err_flag);   // B11 <- N11 (both halves)
+  // U = -B21 N11
+  for (int e = tid; e < 1024; e += NT) {
+    const int i = e >> 5, j = e & 31;
+    dfloat acc{0.0f, 0.0f};
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) df_fma_acc(acc, S.B21[i * 33 + k], S.B11[k * 33 + j]);
+    acc = df_renorm(acc);
+    S.U[i * 33 + j] = dfloat{-acc.hi, -acc.lo};
+  }
+  __syncthreads();
+  // B22 <- B22 - U B21^T (lower)
+  for (int e = tid; e < 1024; e += NT) {
+    const int i = e >> 5, j = e & 31;
+    if (i < j) continue;
+    dfloat acc{0.0f, 0.0f};
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) df_fma_acc(acc, S.U[i * 33 + k], S.B21[j * 33 + k]);
+    S.B22[i * 33 + j] = df_sub(S.B22[i * 33 + j], df_renorm(acc));
+  }
+  __syncthreads();
+  df_sweep32<NT>(S.B22, S.col, S.w, err_flag);   // B22 <- N22 (both halves)
+  // X = -N22 U
+  for (int e = tid; e < 1024; e += NT) {
+    const int i = e >> 5, j = e & 31;
+    dfloat acc{0.0f, 0.0f};
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) df_fma_acc(acc, S.B22[i * 33 + k], S.U[k * 33 + j]);
+    acc = df_renorm(acc);
+    S.X[i * 33 + j] = dfloat{-acc.hi, -acc.lo};
+  }
+  __syncthreads();
+  // N11 <- N11 - U^T X (lower), and the output
+  for (int e = tid; e < 1024; e += NT) {
+    const int i = e >> 5, j = e & 31;
+    if (i < j) continue;
+    dfloat acc{0.0f, 0.0f};
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) df_fma_acc(acc, S.U[k * 33 + i], S.X[k * 33 + j]);
+    const dfloat v = df_sub(S.B11[i * 33 + j], df_renorm(acc));
+    const float f = -__fadd_rn(v.hi, v.lo);
+    P[i * 64 + j] = f;
+    P[j * 64 + i] = f;
+  }
+  for (int e = tid; e < 1024; e += NT) {
+    const int i = e >> 5, j = e & 31;
+    const dfloat x = S.X[i * 33 + j];
+    const float fx = -__fadd_rn(x.hi, x.lo);
+    P[(32 + i) * 64 + j] = fx;
+    P[j * 64 + 32 + i] = fx;
+    const dfloat n = S.B22[i * 33 + j];
+    P[(32 + i) * 64 + 32 + j] = -__fadd_rn(n.hi, n.lo);
   }
 }
 
