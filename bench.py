@@ -373,12 +373,50 @@ class Native:
         return e0.elapsed_time(e1) / 1e3, v, np.asarray(g), st
 
 
+def measure_exact(args, nat, world, dist, clocks=True):
+    """The exact one-part form (n_p = 1, the whole chain one subdomain, no
+    samples) timed like the RBMC form: W untimed and K timed steps, each one
+    full pass (set theta + diag + traces)."""
+    import torch
+    q, w, stream = nat.q, nat.w, nat.stream
+    ctx = nat.ctx(q.QSEL_MIXED, n_parts=1, overlap=0, k=2)
+    outs = [torch.empty(w.n, dtype=torch.float64, device=nat.dev) for _ in range(args.warmup + args.steps)]
+    grads = []
+
+    def step(i):
+        q.qsel_set_theta(ctx, w.theta)
+        q.qsel_diag_inv(ctx, outs[i])
+        grads.append(np.asarray(q.qsel_trace_grads(ctx)))
+        return q.qsel_stats(ctx)
+
+    for i in range(args.warmup):
+        step(i)
+    sampler = ClockSampler(int(str(nat.dev).split(":")[-1])) if clocks else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = [step(args.warmup + i) for i in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = sampler.stop() if sampler else None
+    ms_total = job_time_ms(e0.elapsed_time(e1), world, dist if world > 1 else None, nat.dev)
+    v = outs[-1].cpu().numpy()
+    ctx.close()
+    return {"ms_total": ms_total, "stats": stats, "clocks": clk, "diag": v, "grads": grads[-1],
+            "launches": int(sum(s["kernel_launches"] for s in stats))}
+
+
 def measure_chosen(args, nat, net, world, dist, rank, clocks=True):
-    """Plan (part count, per-part overlaps, k) with the network, then time the
-    chosen RBMC form: W untimed and K timed steps, each one full pass with a
-    new seed (plan + set seed + set theta + diag + traces + error estimate).
-    Returns the measurements and the per-step estimates (for the accuracy
-    over seeds)."""
+    """Plan (part count >= 2, per-part overlaps, k) with the network, then time
+    the RBMC form: W untimed and K timed steps, each one full pass with a new
+    seed (plan + set seed + set theta + diag + traces + error estimate).
+    Returns the measurements, the per-step estimates (for the accuracy over
+    seeds) and the planner's recommendation over part counts including the
+    exact one-part form."""
     import torch
     q, w, stream = nat.q, nat.w, nat.stream
     counts = [p for p in RBMC_PART_COUNTS if p <= w.n_t]
@@ -436,12 +474,16 @@ def measure_chosen(args, nat, net, world, dist, rank, clocks=True):
             "err_estimates": errs, "launches": launches}
 
 
-def profile_pass(nat, ch):
-    """One pass of the chosen form with per-launch event timing (class
-    breakdown for the roofline), on a context of its own."""
+def profile_pass(nat, ch, exact=False):
+    """One pass of the RBMC plan (or of the exact one-part form) with
+    per-launch event timing (class breakdown for the roofline), on a context
+    of its own."""
     q = nat.q
-    c = nat.ctx(q.QSEL_MIXED, n_parts=len(ch["slab_start"]) - 1, slab_start=ch["slab_start"],
-                overlap=min(ch["part_overlap"]), k=ch["k"], part_overlap=ch["part_overlap"], profile=1)
+    if exact:
+        c = nat.ctx(q.QSEL_MIXED, n_parts=1, overlap=0, k=2, profile=1)
+    else:
+        c = nat.ctx(q.QSEL_MIXED, n_parts=len(ch["slab_start"]) - 1, slab_start=ch["slab_start"],
+                    overlap=min(ch["part_overlap"]), k=ch["k"], part_overlap=ch["part_overlap"], profile=1)
     q.qsel_set_seed(c, 4242)
     q.qsel_diag_inv(c)
     q.qsel_trace_grads(c)
@@ -456,11 +498,12 @@ def roofline_of(st, w, hbm_peak, hbm_src, tf32_peak, tf32_src):
     from paper_2309_05435_gb300 import qsel as q
     classes = q.PROF_CLASSES
     cms, cwork, cl = st["class_ms"], st["class_work"], st["class_launches"]
-    desc = {"gemm": "k_tc_gemm<3,128> (Takahashi and correction products, tcgen05 3xTF32, TMA, TMEM)",
-            "sweep_update": "k_tc_gemm<3,128> rank-256 sweep panel updates (tcgen05 3xTF32)",
+    desc = {"gemm": "k_tc_gemm256 (Takahashi products: persistent 128x256 tiles, tcgen05 3xTF32 on operands "
+                    "split once in HBM, TMA, double-buffered TMEM accumulators)",
+            "sweep_update": "k_tc_update (persistent rank-256 sweep panel updates, tcgen05 3xTF32)",
             "spmm": "k_bt_spmm (block-tridiagonal sliced-ELL SpMM, PCG)",
-            "pivot": "k_bsweep_pivot (64x64 double-float pivot-tile inverses)",
-            "precond": "k_kron_pass x6 (Kronecker grid preconditioner)"}
+            "pivot": "k_bsweep_pivot (64x64 double-float pivot-tile inverses, 2x2 block sweep)",
+            "precond": "k_kron_transpose_in + k_kron_tc x6 (Kronecker preconditioner on tcgen05)"}
     cand = [i for i, nm in enumerate(classes) if nm in desc and cwork[i] > 0 and cms[i] > 0]
     dom = max(cand, key=lambda i: cms[i])
     name = classes[dom]
@@ -571,7 +614,10 @@ def run_native(args):
             np.save(args.save_cv_params, qsel.qsel_cv_get_params(net))
 
     ch = measure_chosen(args, nat, net, world, dist, rank)
-    ms_per_step = ch["ms_total"] / args.steps
+    ex = measure_exact(args, nat, world, dist)
+    # the planner over part counts {1} + the RBMC counts picks the form
+    chosen_exact = int(ch["recommendation"]["n_parts"]) == 1
+    ms_per_step = (ex if chosen_exact else ch)["ms_total"] / args.steps
 
     # end to end through the public API with host buffers: create from pinned
     # host arrays, plan, diag to pinned host memory, traces, destroy
@@ -589,14 +635,21 @@ def run_native(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(args.e2e_steps):
-            c2 = qsel.qsel_create(w.n_s, w.n_t, c_pin, rp_pin, gc_pin, gv_pin, mk_pin, w.sigma, w.theta,
-                                  n_parts=len(ch["slab_start"]) - 1, slab_start=ch["slab_start"],
-                                  overlap=min(ch["part_overlap"]), n_samples=ch["k"], seed=6000 + i,
-                                  precision=qsel.QSEL_MIXED, pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream,
-                                  part_overlap=ch["part_overlap"], preconditioner=qsel.QSEL_PRECOND_KRON)
+            if chosen_exact:
+                c2 = qsel.qsel_create(w.n_s, w.n_t, c_pin, rp_pin, gc_pin, gv_pin, mk_pin, w.sigma, w.theta,
+                                      n_parts=1, overlap=0, n_samples=2, precision=qsel.QSEL_MIXED,
+                                      pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream)
+            else:
+                c2 = qsel.qsel_create(w.n_s, w.n_t, c_pin, rp_pin, gc_pin, gv_pin, mk_pin, w.sigma, w.theta,
+                                      n_parts=len(ch["slab_start"]) - 1, slab_start=ch["slab_start"],
+                                      overlap=min(ch["part_overlap"]), n_samples=ch["k"], seed=6000 + i,
+                                      precision=qsel.QSEL_MIXED, pcg_tol=w.pcg_tol, cuda_stream=stream.cuda_stream,
+                                      part_overlap=ch["part_overlap"], preconditioner=qsel.QSEL_PRECOND_KRON)
+            # the plan over part counts including the exact form, as in the timed steps
             p = qsel.qsel_cv_plan(c2, net, args.margin * args.target, max_overlap=PLAN_MAX_OVERLAP,
-                                  cost_pcg=KRON_PCG_COST, part_counts=[c for c in RBMC_PART_COUNTS if c <= w.n_t])
-            if [int(x) for x in p["part_overlap"]] != ch["part_overlap"]:
+                                  cost_pcg=KRON_PCG_COST,
+                                  part_counts=[1] + [c for c in RBMC_PART_COUNTS if c <= w.n_t])
+            if (int(p["n_parts"]) == 1) != chosen_exact:
                 raise RuntimeError("the plan changed between calls at fixed theta")
             qsel.qsel_diag_inv(c2, diag_host)
             qsel.qsel_trace_grads(c2)
@@ -613,29 +666,48 @@ def run_native(args):
             dist.destroy_process_group()
         return
 
-    st_prof = profile_pass(nat, ch)
     hbm_peak, hbm_src = measured_peaks()
     tf32_peak, tf32_src = tf32_peak_tflops()
+    st_prof = profile_pass(nat, ch, exact=chosen_exact)
     roof = roofline_of(st_prof, w, hbm_peak, hbm_src, tf32_peak, tf32_src)
+    roof_rbmc = None
+    if chosen_exact:
+        roof_rbmc = roofline_of(profile_pass(nat, ch), w, hbm_peak, hbm_src, tf32_peak, tf32_src)
 
-    # the exact one-part form in the same precision: the alternative, and the
-    # reference of the accuracy (its own error against FP64 from the slab sample)
-    t_exact, v_ex, t_ex, st_ex = nat.exact(qsel.QSEL_MIXED)
+    # the exact one-part form in the same precision is also the reference of
+    # the RBMC form's accuracy (its own error against FP64 from the slab sample)
+    v_ex, t_ex, st_ex = ex["diag"], ex["grads"], ex["stats"][-1]
     accuracy = None
     sample = plain = None
     if not args.no_accuracy:
         sample = slab_sample(nat)
+        rb = _seed_errors(ch["diags"], ch["grads"], v_ex, t_ex)
+        own = sample["mixed_vs_fp64"]
+        exact_acc = {"eps_diag": own["eps_diag_rms"], "eps_diag_p99": own["eps_diag_p99"],
+                     "eps_traces": own["eps_traces"], "against": "FP64 on the slab sample",
+                     "meets_1pct": bool(own["eps_diag_rms"] <= 0.01 and max(own["eps_traces"]) <= 0.01)}
         accuracy = {"reference": "exact one-part selected inversion in the mixed form on the GPU (n_p = 1); its "
                                  "own error against FP64 is `slab_sample.mixed_vs_fp64` at this block size",
-                    "chosen": _seed_errors(ch["diags"], ch["grads"], v_ex, t_ex),
-                    "chosen_error_estimates": ch["err_estimates"], "slab_sample": sample}
+                    "chosen": exact_acc if chosen_exact else rb, "rbmc": rb, "exact": exact_acc,
+                    "rbmc_error_estimates": ch["err_estimates"], "slab_sample": sample}
         if args.plain_seeds > 0:
             plain = plain_fp64_time_to_target(args, nat, v_ex, t_ex, sample)
     chosen_ok = accuracy["chosen"]["meets_1pct"] if accuracy else None
-    alt = {"form": "exact one-part selected inversion (n_p = 1), mixed precision", "s_per_pass": t_exact,
-           "time_to_target_s": t_exact, "phases_ms": {"factor": st_ex["ms_factor"],
-                                                       "takahashi": st_ex["ms_takahashi"]},
-           "planner_model_cost_s": ch["plan"]["single_part_cost"]}
+    forms = {
+        "exact": {"form": "exact one-part selected inversion (n_p = 1), mixed precision",
+                  "s_per_pass": ex["ms_total"] / args.steps / 1e3,
+                  "phases_ms": {"factor": st_ex["ms_factor"], "takahashi": st_ex["ms_takahashi"]},
+                  "planner_model_cost_s": ch["plan"]["single_part_cost"], "gpu_launches": ex["launches"],
+                  "clocks": ex["clocks"]},
+        "rbmc": {"form": "mixed-precision RBMC at the planner's part count >= 2", "s_per_pass":
+                 ch["ms_total"] / args.steps / 1e3, "n_parts": len(ch["slab_start"]) - 1,
+                 "slab_start": ch["slab_start"], "overlap": ch["part_overlap"], "n_samples": ch["k"],
+                 "planner_model_cost_s": ch["plan"]["predicted_cost"], "gpu_launches": ch["launches"],
+                 "phases_ms": {k: ch["stats"][-1]["ms_" + k] for k in
+                               ("rhs", "pcg", "factor", "takahashi", "correction", "total")},
+                 "pcg_iterations": ch["stats"][-1]["pcg_iterations"], "clocks": ch["clocks"],
+                 "roofline": roof_rbmc},
+    }
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:   # the CPU baseline is an N = 1 figure
@@ -643,14 +715,19 @@ def run_native(args):
         cpu = {"value": est, "unit": "s", "cores": cpu_cores(), "kind": "oracle", "sample": desc,
                "sample_seconds": spent}
 
-    st = ch["stats"][-1]
+    cm = ex if chosen_exact else ch
+    st = cm["stats"][-1]
     plan = ch["plan"]
-    form = ("mixed precision RBMC (FP32 PCG with the Kronecker grid preconditioner + FP64 refinement; "
-            "FP32 tiles on tcgen05 3xTF32 + double-float pivots) + learned control-variate planner (part count, "
-            f"per-part overlap, k for {args.target:g} RMS relative error)")
+    planner = ("the learned control-variate planner over part counts {1, %s} (per-part overlap and k for %g RMS "
+               "relative error; n_p = 1 is the exact one-part form)"
+               % (", ".join(str(c) for c in RBMC_PART_COUNTS if c <= w.n_t), args.target))
+    form = (("exact one-part selected inversion (mixed precision: FP32 tiles on tcgen05 3xTF32, double-float "
+             "pivots), chosen by " if chosen_exact else
+             "mixed precision RBMC (FP32 PCG with the Kronecker grid preconditioner on tcgen05 + FP64 refinement; "
+             "FP32 tiles on tcgen05 3xTF32 + double-float pivots), chosen by ") + planner)
     result = {
         "metric": METRIC,
-        "value": job_value_s(ch["ms_total"], args.steps, world),
+        "value": job_value_s(cm["ms_total"], args.steps, world),
         "unit": "s",
         "n_gpus": world,
         "steps": args.steps,
@@ -663,28 +740,32 @@ def run_native(args):
         "data": "synthetic (seeded grid FEM mesh, Philox noise)",
         "config": {"workload": f"{w.name}: {w.m}x{w.m} grid, n_t={w.n_t}, n={w.n}, kappa={w.kappa}, "
                                f"rho={w.rho}, {int(w.obs_frac * 100)}% observed",
-                   "form": form, "n_parts": len(ch["slab_start"]) - 1, "slab_start": ch["slab_start"],
-                   "overlap": ch["part_overlap"], "n_samples": ch["k"], "pcg_tol": w.pcg_tol,
+                   "form": form, "n_parts": 1 if chosen_exact else len(ch["slab_start"]) - 1,
+                   "slab_start": [0, w.n_t] if chosen_exact else ch["slab_start"],
+                   "overlap": [0] if chosen_exact else ch["part_overlap"],
+                   "n_samples": 0 if chosen_exact else ch["k"], "pcg_tol": w.pcg_tol,
                    "seeds": "a new Philox seed every step",
-                   "l2": "inputs larger than L2 (samples alone %.2f GB)" % (w.n * ch["k"] * 8 / 1e9),
+                   "l2": ("inputs larger than L2 (each 9216^2 FP32 block 340 MB)" if chosen_exact else
+                          "inputs larger than L2 (samples alone %.2f GB)" % (w.n * ch["k"] * 8 / 1e9)),
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "phases_ms": {"rhs": st["ms_rhs"], "pcg": st["ms_pcg"], "factor": st["ms_factor"],
                       "takahashi": st["ms_takahashi"], "correction": st["ms_correction"],
                       "total": st["ms_total"]},
         "pcg_iterations": st["pcg_iterations"],
-        "gpu_launches": ch["launches"],
+        "gpu_launches": cm["launches"],
         "chosen_meets_target": chosen_ok,
-        "plan": {"n_parts": plan["n_parts"], "n_samples": plan["n_samples"], "part_overlap": ch["part_overlap"],
-                 "predicted_err": plan["predicted_err"], "predicted_cost_s": plan["predicted_cost"],
-                 "feasible": plan["feasible"], "margin": args.margin,
-                 "recommendation_with_exact": {"n_parts": ch["recommendation"]["n_parts"],
-                                               "predicted_cost_s": ch["recommendation"]["predicted_cost"]}},
+        "plan": {"chosen_n_parts": int(ch["recommendation"]["n_parts"]),
+                 "chosen_predicted_cost_s": ch["recommendation"]["predicted_cost"],
+                 "rbmc_n_parts": plan["n_parts"], "rbmc_n_samples": plan["n_samples"],
+                 "rbmc_part_overlap": ch["part_overlap"], "rbmc_predicted_err": plan["predicted_err"],
+                 "rbmc_predicted_cost_s": plan["predicted_cost"], "feasible": plan["feasible"],
+                 "margin": args.margin},
         "cv_training": cv_info,
-        "alternative": alt,
+        "forms": forms,
         "plain_fp64": plain,
         "speedup_chosen_vs_plain_fp64": (plain["best"]["time_s"] / (ms_per_step / 1e3)) if plain else None,
-        "clocks": ch["clocks"],
+        "clocks": cm["clocks"],
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "cpu_baseline": cpu,
         "accuracy": accuracy,
