@@ -9,7 +9,6 @@
 #include <cstring>
 #include <map>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "qsel.h"
@@ -174,8 +173,6 @@ struct qsel_ctx {
   std::vector<cudaEvent_t> phase_ev;   // pairs per (wave, phase)
   size_t phase_used = 0;
   Profiler prof;
-  Profiler prof_sampler;               // the sampler thread's launches (merged into prof)
-  cudaStream_t wave_stream = nullptr;  // set: the dense waves' stream while the sampler thread owns `stream`
   bool computed = false, injected = false, have_rhs = false;
   qsel_stats_t stats{};
   std::string last_error;
@@ -471,8 +468,13 @@ static Err kron_prepare(qsel_ctx *c) {
       if (t + 1 < n_t) e[t] = -rho / om;
     }
     if (!host_tridiag_eig(n_t, d, e, mu, U)) return fail(QSEL_EINVAL, "temporal eigendecomposition did not converge");
-    QSEL_CUDA_TRY(cudaMemcpy(c->d_kU, U.data(), U.size() * sizeof(double), cudaMemcpyHostToDevice));
-    QSEL_CUDA_TRY(cudaMemcpy(c->d_kmu, mu.data(), mu.size() * sizeof(double), cudaMemcpyHostToDevice));
+    // stream-ordered uploads (the tables below read them on the same stream;
+    // a plain cudaMemcpy would go through the legacy default stream, which
+    // the sampler's non-blocking stream does not wait for)
+    QSEL_CUDA_TRY(cudaMemcpyAsync(c->d_kU, U.data(), U.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    QSEL_CUDA_TRY(cudaMemcpyAsync(c->d_kmu, mu.data(), mu.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                  c->stream));
+    QSEL_CUDA_TRY(cudaStreamSynchronize(c->stream));   // the host vectors go out of scope
     c->kron_rho = rho;
   }
   KronOperator &k = c->kop;
@@ -1348,7 +1350,7 @@ static void set_sum_vals(ExtractEntry<T> &xe, const BlockVals *bv, int n, int t)
 static void phase_mark(qsel_ctx *c, std::vector<std::pair<cudaEvent_t, int>> &marks, int phase) {
   if (c->graph_mode) return;
   cudaEvent_t e = c->phase_event();
-  cudaEventRecord(e, c->wave_stream ? c->wave_stream : c->stream);
+  cudaEventRecord(e, c->stream);
   marks.emplace_back(e, phase);
 }
 
@@ -1357,7 +1359,7 @@ static void phase_mark(qsel_ctx *c, std::vector<std::pair<cudaEvent_t, int>> &ma
 // stages: 1 = factorisation and Takahashi, 2 = correction (needs the samples).
 template <typename T>
 static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent_t, int>> &marks, int stages = 3) {
-  cudaStream_t s = c->wave_stream ? c->wave_stream : c->stream;
+  cudaStream_t s = c->stream;
   const int n_pad = c->n_pad, n_s = c->n_s, ld = c->ld;
   const size_t svec = (size_t)n_pad * ld;
   int maxT = 0;
@@ -1858,46 +1860,25 @@ static Err run_pipeline_body(qsel_ctx *c) {
   int first = 0;   // first wave still to run in full
   if (c->mixed && !c->injected && need_samples && c->opt.sampler == QSEL_SAMPLER_PCG) {
     // The samples are needed only by the correction: the first wave's
-    // factorisation and Takahashi recursion run on the context's stream
-    // while the PCG runs on pcg_stream.  The PCG's host loop (which
-    // synchronises only its own stream) runs on a second host thread, so
-    // that its first kernels are enqueued at once and not after the tens of
-    // thousands of dense launches; during that time the sampler owns
-    // c->stream and the dense waves use wave_stream.  Mixed form only: in
-    // FP64 both parts run on the FP64 pipe, and sequential phases keep its
-    // phase times (which the plain-FP64 time-to-target model scales) additive.
+    // factorisation and Takahashi recursion are enqueued on the context's
+    // stream and run while the PCG (whose host loop synchronises only its
+    // own stream) runs on pcg_stream.  Mixed form only: in FP64 both parts
+    // run on the FP64 pipe, and sequential phases keep its phase times
+    // (which the plain-FP64 time-to-target model scales) additive.
     QSEL_CUDA_TRY(cudaEventRecord(c->ev_fork, s));
-    QSEL_CUDA_TRY(cudaStreamWaitEvent(c->pcg_stream, c->ev_fork, 0));
     first = std::min(np, c->wave);
-    c->wave_stream = s;
+    TRY(wave(0, first, 1));
+    QSEL_CUDA_TRY(cudaStreamWaitEvent(c->pcg_stream, c->ev_fork, 0));
     c->stream = c->pcg_stream;
-    Profiler *main_prof = g_prof;
-    if (main_prof) c->prof_sampler.reset();
-    Err se = ok();
-    int64_t sampler_launches = 0;
-    std::thread sampler([&] {
-      g_prof = main_prof ? &c->prof_sampler : nullptr;   // thread-local
-      const int64_t l0 = g_launch_count;
-      se = run_sampler(c);
-      if (se.code == 0 && cudaEventRecord(c->ev[2], c->pcg_stream) != cudaSuccess)
-        se = fail(QSEL_ECUDA, "event record failed");
-      if (se.code == 0 && cudaEventRecord(c->ev_samples, c->pcg_stream) != cudaSuccess)
-        se = fail(QSEL_ECUDA, "event record failed");
-      sampler_launches = g_launch_count - l0;
-      g_prof = nullptr;
-    });
-    Err we = wave(0, first, 1);
-    sampler.join();
+    Err e = run_sampler(c);
+    if (e.code == 0 && cudaEventRecord(c->ev[2], c->pcg_stream) != cudaSuccess)
+      e = fail(QSEL_ECUDA, "event record failed");
+    if (e.code == 0 && cudaEventRecord(c->ev_samples, c->pcg_stream) != cudaSuccess)
+      e = fail(QSEL_ECUDA, "event record failed");
     c->stream = s;
-    c->wave_stream = nullptr;
-    g_launch_count += sampler_launches;
-    if (main_prof)
-      main_prof->recs.insert(main_prof->recs.end(), c->prof_sampler.recs.begin(), c->prof_sampler.recs.end());
-    if (we.code == 0 && se.code) we = se;
-    if (we.code) {
-      cudaStreamSynchronize(s);   // leave no work of this call in flight
-      cudaStreamSynchronize(c->pcg_stream);
-      return we;
+    if (e.code) {
+      cudaStreamSynchronize(s);   // leave no dense work of this call in flight
+      return e;
     }
     QSEL_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_samples, 0));
     TRY(wave(0, first, 2));
