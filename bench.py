@@ -104,6 +104,8 @@ def parse_args():
     ap.add_argument("--batch-streams", type=int, default=16)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--kron-apply", default=None,
+                    help="one mixed Kronecker preconditioner apply (k = 256) on WORKLOAD (profiling captures)")
     ap.add_argument("--exact-pass", default=None,
                     help="one exact one-part mixed pass at this workload (for kernel captures)")
     ap.add_argument("--oracle-e2e", default=None,
@@ -856,6 +858,25 @@ def run_exact_pass(args):
                       "factor_ms": st["ms_factor"], "takahashi_ms": st["ms_takahashi"]}), flush=True)
 
 
+def run_kron_apply(args):
+    """--kron-apply WORKLOAD: one apply of the mixed form's Kronecker
+    preconditioner to 256 seeded columns (the command the tensor-core passes
+    are captured with under profiles/); prints its host-side time."""
+    from paper_2309_05435_gb300 import build, qsel
+    build.build()
+    w = qi.workload(args.kron_apply)
+    mesh, mask = workload_inputs(w)
+    c = qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma, w.theta,
+                         n_parts=2, overlap=1, n_samples=256, precision=qsel.QSEL_MIXED,
+                         preconditioner=qsel.QSEL_PRECOND_KRON)
+    R = qi.seeded_normal((w.n, 256), 17)
+    t0 = time.perf_counter()
+    Z = qsel.qsel_debug_apply_precond(c, R)
+    c.close()
+    print(json.dumps({"mode": "kron_apply", "workload": w.name, "s_with_host_copies": time.perf_counter() - t0,
+                      "max_abs": float(np.max(np.abs(Z)))}), flush=True)
+
+
 def run_oracle_e2e(args):
     """--oracle-e2e: the oracle end to end on the listed workloads with all host
     cores, and in a child process limited to one BLAS / OpenMP thread on the
@@ -1179,6 +1200,9 @@ def main():
     if args.oracle_sample:
         est, spent, _ = oracle_sample(qi.workload(args.workload))
         print(json.dumps({"est": est, "spent": spent}), flush=True)
+        return
+    if args.kron_apply:
+        run_kron_apply(args)
         return
     if args.exact_pass:
         run_exact_pass(args)
