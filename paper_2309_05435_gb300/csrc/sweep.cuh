@@ -212,12 +212,15 @@ __device__ __forceinline__ dfloat df_renorm(dfloat a) { return df_two_sum(a.hi, 
 
 // Scalar sweep of a 32 x 32 SPD block held in the lower triangle of S (row
 // stride 33) in double-float: after the 32 pivots the lower triangle holds that
-// of -S^-1, then both halves are filled.  Each pivot: threads 0-31 snapshot
-// column p (c_k) and w_k = c_k / d, then the owner of each lower entry (528,
-// about one per thread) applies S_ij - c_i w_j.  col holds 33 entries (col[32]
-// = 1 / d), w 32.  blockDim.x == NT.
+// of -S^-1, then both halves are filled.  Each pivot reads the block as it
+// stood before the pivot from one buffer and writes the new values to the
+// other (S and T alternate; 32 pivots end in S), so a pivot costs one block
+// barrier: every thread forms 1 / d and reads column p itself, then updates
+// the lower entries it owns (528 entries, about one per thread):
+//   S_pp <- -1/d,  S_ip <- c_i / d,  S_ij <- S_ij - c_i (c_j / d).
+// A non-positive pivot sets bit 0 of *err_flag.  blockDim.x == NT.
 template <int NT>
-__device__ inline void df_sweep32(dfloat *S, dfloat *col, dfloat *w, int32_t *err_flag) {
+__device__ inline void df_sweep32(dfloat *S, dfloat *T, int32_t *err_flag) {
   constexpr int EPT = (528 + NT - 1) / NT;
   int ei[EPT], ej[EPT];
 #pragma unroll
@@ -233,38 +236,36 @@ __device__ inline void df_sweep32(dfloat *S, dfloat *col, dfloat *w, int32_t *er
       ej[q] = e - i * (i + 1) / 2;
     }
   }
+  dfloat *src = S, *dst = T;
   for (int p = 0; p < 32; ++p) {
-    if (threadIdx.x < 32) {
-      const int k = threadIdx.x;
-      const dfloat d = S[p * 33 + p];
-      const bool pos = d.hi > 0.0f;
-      const dfloat inv = pos ? df_recip(d) : dfloat{0.0f, 0.0f};
-      const dfloat c = (k >= p) ? S[k * 33 + p] : S[p * 33 + k];
-      col[k] = c;
-      w[k] = df_mul(c, inv);
-      if (k == 0) {
-        col[32] = inv;
-        if (!pos && err_flag) atomicOr(err_flag, 1);
-      }
-    }
-    __syncthreads();
+    const dfloat d = src[p * 33 + p];
+    const bool pos = d.hi > 0.0f;
+    const dfloat inv = pos ? df_recip(d) : dfloat{0.0f, 0.0f};
+    if (threadIdx.x == 0 && !pos && err_flag) atomicOr(err_flag, 1);
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
       const int i = ei[q], j = ej[q];
       if (i < 0) continue;
+      const dfloat ci = (i >= p) ? src[i * 33 + p] : src[p * 33 + i];
+      const dfloat cj = (j >= p) ? src[j * 33 + p] : src[p * 33 + j];
+      const dfloat wj = df_mul(cj, inv);
       dfloat v;
       if (i == p && j == p)
-        v = dfloat{-col[32].hi, -col[32].lo};
+        v = dfloat{-inv.hi, -inv.lo};
       else if (i == p)
-        v = w[j];
+        v = wj;
       else if (j == p)
-        v = w[i];
+        v = df_mul(ci, inv);
       else
-        v = df_sub(S[i * 33 + j], df_mul(col[i], w[j]));
-      S[i * 33 + j] = v;   // read only by its owner during the pivot
+        v = df_sub(src[i * 33 + j], df_mul(ci, wj));
+      dst[i * 33 + j] = v;
     }
     __syncthreads();
+    dfloat *t = src;
+    src = dst;
+    dst = t;
   }
+  // 32 pivots: the result is in S
   for (int e = threadIdx.x; e < 1024; e += NT) {
     const int i = e >> 5, j = e & 31;
     if (i < j) S[i * 33 + j] = S[j * 33 + i];
@@ -276,7 +277,6 @@ __device__ inline void df_sweep32(dfloat *S, dfloat *col, dfloat *w, int32_t *er
 // the two products, 32 x 32 each with row stride 33.
 struct Inverse64Smem {
   dfloat B11[32 * 33], B21[32 * 33], B22[32 * 33], U[32 * 33], X[32 * 33];
-  dfloat col[33], w[32];
 };
 
 // P = Tk^-1 (64 x 64 float, both halves) for the SPD tile whose lower half is
@@ -286,7 +286,7 @@ struct Inverse64Smem {
 //   N11 = -B11^-1,  U = B21 B11^-1 = -B21 N11,  B22' = B22 - U B21^T,
 //   N22 = -B22'^-1, X = B22'^-1 U = -N22 U,
 //   -Tk^-1 = [[N11 - U^T X, X^T], [X, N22]].
-// The 32 x 32 sweeps take one barrier pair per pivot with about one entry per
+// The 32 x 32 sweeps take one barrier per pivot with about one entry per
 // thread; the four 32-term block products run on all threads with their
 // sums in double-float.  A non-positive pivot sets bit 0 of *err_flag.
 // blockDim.x == NT >= 512.
@@ -301,7 +301,7 @@ __device__ inline void sym_inverse64_df_2x2(const float *Tk, int ld, float *P, I
     if (i >= j) S.B22[i * 33 + j] = dfloat{Tk[(int64_t)(32 + i) * ld + 32 + j], 0.0f};
   }
   __syncthreads();
-  df_sweep32<NT>(S.B11, S.col, S.w, err_flag);   // B11 <- N11 (both halves)
+  df_sweep32<NT>(S.B11, S.U, err_flag);   // B11 <- N11 (both halves; U as the second buffer)
   // U = -B21 N11
   for (int e = tid; e < 1024; e += NT) {
     const int i = e >> 5, j = e & 31;
@@ -322,7 +322,7 @@ __device__ inline void sym_inverse64_df_2x2(const float *Tk, int ld, float *P, I
     S.B22[i * 33 + j] = df_sub(S.B22[i * 33 + j], df_renorm(acc));
   }
   __syncthreads();
-  df_sweep32<NT>(S.B22, S.col, S.w, err_flag);   // B22 <- N22 (both halves)
+  df_sweep32<NT>(S.B22, S.X, err_flag);   // B22 <- N22 (both halves; X as the second buffer)
   // X = -N22 U
   for (int e = tid; e < 1024; e += NT) {
     const int i = e >> 5, j = e & 31;
