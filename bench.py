@@ -94,7 +94,7 @@ def parse_args():
     ap.add_argument("--cv-eval", action="store_true",
                     help="held-out evaluation: 64x64 grid, n_t=128, 8 parts, 8 theta; planned vs plain")
     ap.add_argument("--cv-eval-thetas", type=int, default=8)
-    ap.add_argument("--cv-controls", type=int, default=2,
+    ap.add_argument("--cv-controls", type=int, default=8,
                     help="held-out theta on which plain RBMC also runs at fixed overlaps 1, 2, 4, 8")
     ap.add_argument("--cv-fp64-thetas", type=int, default=2,
                     help="held-out theta on which plain FP64 is also run to the target")
