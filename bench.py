@@ -108,6 +108,8 @@ def parse_args():
                     help="one mixed Kronecker preconditioner apply (k = 256) on WORKLOAD (profiling captures)")
     ap.add_argument("--exact-pass", default=None,
                     help="one exact one-part mixed pass at this workload (for kernel captures)")
+    ap.add_argument("--chain", choices=["two_ended", "forward"], default="two_ended",
+                    help="order of the one-part block factorisation (qsel_options.chain)")
     ap.add_argument("--oracle-e2e", default=None,
                     help="comma list of workloads: time the CPU oracle end to end (all host cores)")
     ap.add_argument("--oracle-e2e-single", default="grid16_nt8",
@@ -342,9 +344,10 @@ def _subdomain_slabs(n_t, slab_start, overlaps):
 class Native:
     """The library's contexts for one workload (inputs resident in HBM)."""
 
-    def __init__(self, q, w, stream, dev):
+    def __init__(self, q, w, stream, dev, chain="two_ended"):
         self.q, self.w, self.stream, self.dev = q, w, stream, dev
         self.mesh, self.mask = workload_inputs(w)
+        self.chain = q.QSEL_CHAIN_FORWARD if chain == "forward" else q.QSEL_CHAIN_TWO_ENDED
 
     def ctx(self, precision, n_parts=None, slab_start=None, overlap=None, k=None, part_overlap=None, seed=1000,
             preconditioner=None, profile=0, mesh_mask=None, n_t=None):
@@ -357,7 +360,7 @@ class Native:
                              overlap=w.overlap if overlap is None else overlap,
                              n_samples=k or w.n_samples, seed=seed, precision=precision, pcg_tol=w.pcg_tol,
                              cuda_stream=self.stream.cuda_stream, profile_kernels=profile,
-                             part_overlap=part_overlap, preconditioner=pc)
+                             part_overlap=part_overlap, preconditioner=pc, chain=self.chain)
 
     def exact(self, precision):
         """One pass of the exact one-part form: (s, diag, traces, stats)."""
@@ -604,7 +607,7 @@ def run_native(args):
     dev = f"cuda:{local}"
     stream = torch.cuda.current_stream()
     w = qi.workload(args.workload)
-    nat = Native(qsel, w, stream, dev)
+    nat = Native(qsel, w, stream, dev, chain=args.chain)
 
     if args.cv_params:
         net = qsel.qsel_cv_create(0)
@@ -783,7 +786,7 @@ def run_native(args):
 def secondary_workload(args, q, w2, stream, dev, net):
     """The chosen form and the exact one-part form on a second workload (one
     warm-up and two timed steps), with the accuracy over those seeds."""
-    nat = Native(q, w2, stream, dev)
+    nat = Native(q, w2, stream, dev, chain=args.chain)
     a2 = argparse.Namespace(**{**vars(args), "warmup": 1, "steps": 2})
     ch = measure_chosen(a2, nat, net, 1, None, 0, clocks=False)
     t_exact, v_ex, t_ex, _ = nat.exact(q.QSEL_MIXED)
@@ -847,14 +850,15 @@ def run_exact_pass(args):
     w = qi.workload(args.exact_pass)
     mesh, mask = workload_inputs(w)
     c = qsel.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma, w.theta,
-                         n_parts=1, overlap=0, n_samples=2, precision=qsel.QSEL_MIXED)
+                         n_parts=1, overlap=0, n_samples=2, precision=qsel.QSEL_MIXED,
+                         chain=qsel.QSEL_CHAIN_FORWARD if args.chain == "forward" else qsel.QSEL_CHAIN_TWO_ENDED)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     qsel.qsel_diag_inv(c)
     torch.cuda.synchronize()
     st = qsel.qsel_stats(c)
     c.close()
-    print(json.dumps({"mode": "exact_pass", "workload": w.name, "s": time.perf_counter() - t0,
+    print(json.dumps({"mode": "exact_pass", "workload": w.name, "chain": args.chain, "s": time.perf_counter() - t0,
                       "factor_ms": st["ms_factor"], "takahashi_ms": st["ms_takahashi"]}), flush=True)
 
 

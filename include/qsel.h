@@ -85,6 +85,10 @@ enum {
   QSEL_PRECOND_KRON = 1
 };
 
+/* Order of the one-part block factorisation (qsel_options.chain). */
+#define QSEL_CHAIN_TWO_ENDED 0
+#define QSEL_CHAIN_FORWARD 1
+
 /* Space-time prior of qsel_create (qsel_options.model). */
 enum {
   QSEL_MODEL_SEPARABLE = 0,     /* tau Q_t (x) Q_s, AR(1) in time (Section 2.2,
@@ -195,6 +199,14 @@ typedef struct {
                              QSEL_PIVOT_FP64 (1).  Ignored for QSEL_FP64.       */
   int32_t model;          /* qsel_create: QSEL_MODEL_SEPARABLE (0) or
                              QSEL_MODEL_DIFFUSION (1); ignored by qsel_create_bt */
+  int32_t chain;          /* order of the one-part (n_parts = 1) block
+                             factorisation: QSEL_CHAIN_TWO_ENDED (0, default;
+                             Schur complements from slab 0 and from slab n_t-1
+                             toward the middle slab, two chains batched side by
+                             side, the selected inverse then outward from the
+                             middle; n_t >= 3) or QSEL_CHAIN_FORWARD (1; one
+                             chain from slab 0).  Both are exact; they differ
+                             in rounding order only.  Ignored with n_parts > 1 */
 } qsel_options;
 
 #define QSEL_PROF_CLASSES 11
@@ -455,6 +467,19 @@ qsel_status qsel_debug_apply_precond(qsel_ctx *ctx, const double *R, double *Z, 
  * operation.  Errors: QSEL_EINVAL for wait_cycles < 0.
  */
 qsel_status qsel_debug_tc_wait(int32_t skip_loads, int64_t wait_cycles);
+
+/*
+ * Scheduling hook of the mixed form's panel-blocked sweep (every pivot block
+ * inverse), for measuring how its two streams share the GPU.  No work is
+ * skipped and results are unchanged.  serial non-zero: each panel's
+ * rank-64 bw update of the rest runs on the same stream as the pivot chain,
+ * after it, instead of beside the next panel's pivots.  update_ctas > 0: the
+ * persistent update kernel runs on at most that many CTAs (one per SM), so
+ * that SMs stay free for the pivot chain; 0 = one per SM.  Process-wide;
+ * qsel_debug_sweep_schedule(0, 0) restores the default.  Errors: QSEL_EINVAL
+ * for update_ctas < 0.
+ */
+qsel_status qsel_debug_sweep_schedule(int32_t serial, int32_t update_ctas);
 
 /*
  * Allocation-free SPD inverse.  The paper has no counterpart: this entry point

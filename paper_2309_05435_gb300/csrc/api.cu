@@ -40,6 +40,13 @@ struct Subdomain {
   int sep_left, sep_right;             // separator slabs or -1
   double *partial = nullptr;           // corr_grid x 3 trace partials
   int slot_base = 0;                   // first pattern-sum slot (2 T slots)
+  // Two-ended factorisation of the one-part form: the reversed half numbers
+  // its slabs from e1 - 1 down to e0 (its last local slab, e0, is the middle
+  // slab that the forward half factors), and factors nfac = T - 1 of them.
+  int rev = 0;
+  int nfac = 0;
+  int g(int tl) const { return rev ? e1 - 1 - tl : e0 + tl; }         // global slab of local tl
+  int cpl(int tl) const { return rev ? e1 - 2 - tl : e0 + tl; }       // coupling block of tl, tl + 1
 };
 
 // Dense working set of one subdomain in flight; the wave holds up to
@@ -123,6 +130,10 @@ struct qsel_ctx {
   int32_t *d_active = nullptr, *d_counters = nullptr;
   // estimator
   std::vector<Subdomain> parts;
+  // one-part form factored from both ends: forward half (slabs 0..m) and
+  // reversed half (slabs n_t-1..m+1, then the middle m), run as one wave
+  bool twist = false;
+  Subdomain half[2];
   std::vector<DenseSlot> slots;
   int wave = 1, T_max = 1;
   int slot_cap = kMaxBatch;            // at most this many subdomains in flight
@@ -398,6 +409,8 @@ static Err validate_options(int n_t, const qsel_partition *part, int32_t overlap
     return fail(QSEL_EINVAL, "pivot_precision must be QSEL_PIVOT_DOUBLE_FLOAT or QSEL_PIVOT_FP64");
   if (opt->preconditioner != QSEL_PRECOND_BLOCK_JACOBI && opt->preconditioner != QSEL_PRECOND_KRON)
     return fail(QSEL_EINVAL, "preconditioner must be QSEL_PRECOND_BLOCK_JACOBI or QSEL_PRECOND_KRON");
+  if (opt->chain != QSEL_CHAIN_TWO_ENDED && opt->chain != QSEL_CHAIN_FORWARD)
+    return fail(QSEL_EINVAL, "chain must be QSEL_CHAIN_TWO_ENDED or QSEL_CHAIN_FORWARD");
   if (opt->sampler != QSEL_SAMPLER_PCG && opt->sampler != QSEL_SAMPLER_LANCZOS)
     return fail(QSEL_EINVAL, "sampler must be QSEL_SAMPLER_PCG or QSEL_SAMPLER_LANCZOS");
   if (opt->sampler == QSEL_SAMPLER_LANCZOS) {
@@ -766,6 +779,7 @@ static Err build_rest(qsel_ctx *c, const RestInputs &in, const qsel_partition *p
     sd.sep_left = sd.e0 > 0 ? sd.e0 - 1 : -1;
     sd.sep_right = sd.e1 < c->n_t ? sd.e1 : -1;
     sd.slot_base = n_sums;
+    sd.nfac = sd.T;
     n_sums += 2 * sd.T;
     for (int tl = sd.lo; tl <= sd.hi; ++tl) {
       TraceSlab ts;
@@ -778,13 +792,63 @@ static Err build_rest(qsel_ctx *c, const RestInputs &in, const qsel_partition *p
     c->T_max = std::max(c->T_max, sd.T);
     c->parts.push_back(sd);
   }
+  // Two-ended form of the one-part factorisation: D_t by Schur complements
+  // from slab 0 up to the middle slab m and from slab n_t - 1 down to m + 1;
+  // D_m takes both neighbours' terms, so D_m^-1 = Sigma_mm, and the
+  // selected inverse runs outward from m in both halves.  The halves' steps
+  // are batched into the same launches, which halves the sequential chain.
+  // The reversed half's last factor step (local m' - 1 with m' = n_t - 1 - m)
+  // runs before the forward half's middle step (local m) because m' <= m.
+  c->twist = np == 1 && c->opt.chain == QSEL_CHAIN_TWO_ENDED && c->n_t >= 3;
+  if (c->twist) {
+    const int m = c->n_t / 2;
+    Subdomain &f = c->half[0], &r = c->half[1];
+    f = c->parts[0];
+    r = c->parts[0];
+    f.e0 = 0;
+    f.e1 = m + 1;
+    f.s0 = 0;
+    f.s1 = m + 1;
+    f.T = f.nfac = m + 1;
+    f.lo = 0;
+    f.hi = m;
+    f.rev = 0;
+    f.slot_base = 0;
+    r.e0 = m;
+    r.e1 = c->n_t;
+    r.s0 = m + 1;
+    r.s1 = c->n_t;
+    r.T = c->n_t - m;
+    r.nfac = r.T - 1;
+    r.lo = 0;
+    r.hi = r.T - 2;
+    r.rev = 1;
+    r.slot_base = 2 * f.T;
+    n_sums = 2 * (f.T + r.T);
+    // per global slab: Sigma_tt, Y of the pair (t, t+1), Y of (t-1, t);
+    // the reversed half's Y slot tl holds the pair (g(tl + 1), g(tl))
+    tslabs.clear();
+    for (int t = 0; t < c->n_t; ++t) {
+      TraceSlab ts;
+      ts.t = t;
+      if (t <= m) {
+        ts.sd = f.slot_base + t;
+        ts.sy = (t < m) ? f.slot_base + f.T + t : r.slot_base + r.T + (r.T - 2);
+        ts.sym = (t > 0) ? f.slot_base + f.T + t - 1 : -1;
+      } else {
+        const int tl = c->n_t - 1 - t;
+        ts.sd = r.slot_base + tl;
+        ts.sy = (tl >= 1) ? r.slot_base + r.T + tl - 1 : -1;
+        ts.sym = r.slot_base + r.T + tl;
+      }
+      tslabs.push_back(ts);
+    }
+    c->T_max = f.T;
+  }
   TRY(c->alloc(&c->d_partials, (size_t)np * corr_grid() * kMaxTheta));
   QSEL_CUDA_TRY(cudaMemset(c->d_partials, 0, (size_t)np * corr_grid() * kMaxTheta * sizeof(double)));
   for (int p = 0; p < np; ++p) c->parts[p].partial = c->d_partials + (size_t)p * corr_grid() * kMaxTheta;
-  TRY(c->alloc(&c->d_sums, (size_t)kMaxTheta * std::max(n_sums, 1)));
-  QSEL_CUDA_TRY(cudaMemset(c->d_sums, 0, (size_t)kMaxTheta * std::max(n_sums, 1) * sizeof(double)));
-  c->n_trace_slabs = (int)tslabs.size();
-  TRY(upload(c, &c->d_slabs, tslabs));
+  c->half[0].partial = c->half[1].partial = c->d_partials;
   TRY(c->alloc(&c->d_diag, (size_t)n));
   TRY(c->alloc(&c->d_selinv, (size_t)n));
   TRY(c->alloc(&c->d_corr, (size_t)n));
@@ -801,20 +865,43 @@ static Err build_rest(qsel_ctx *c, const RestInputs &in, const qsel_partition *p
   // 64 kSweepPanel each), Vk (64 kSweepPanel x 64) and P (64 x 64)
   const size_t panel = (size_t)n_pad * 64 * kSweepPanel * esz;
   const bool split_panels = c->mixed && c->tc_passes == 3;
-  const size_t per_slot = (size_t)(c->T_max + 5 + (split_panels ? 4 : 0)) * mat + (split_panels ? 10 : 6) * panel +
-                          (size_t)(kSweepPanel + 1) * 64 * 64 * esz +
-                          (size_t)(c->T_max + 5) * svec + 4096;
+  auto slot_bytes = [&](int T) {
+    return (size_t)(T + 5 + (split_panels ? 4 : 0)) * mat + (split_panels ? 10 : 6) * panel +
+           (size_t)(kSweepPanel + 1) * 64 * 64 * esz + (size_t)(T + 5) * svec + 4096;
+  };
   size_t free_b = 0, total_b = 0;
   QSEL_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-  const size_t fit = (size_t)(0.85 * (double)free_b) / per_slot;
+  const size_t budget = (size_t)(0.85 * (double)free_b);
+  if (c->twist && budget / slot_bytes(c->T_max) < 2) {
+    // the two halves' working sets do not fit: the one chain after all, with
+    // the part's own bookkeeping
+    c->twist = false;
+    const Subdomain &sd = c->parts[0];
+    tslabs.clear();
+    n_sums = 2 * sd.T;
+    for (int tl = sd.lo; tl <= sd.hi; ++tl)
+      tslabs.push_back(TraceSlab{sd.e0 + tl, sd.slot_base + tl, (tl + 1 < sd.T) ? sd.slot_base + sd.T + tl : -1,
+                                 (tl > 0) ? sd.slot_base + sd.T + tl - 1 : -1});
+    c->T_max = sd.T;
+  }
+  const size_t per_slot = slot_bytes(c->T_max);
+  const size_t fit = budget / per_slot;
   if (fit < 1)
     return fail(QSEL_ENOMEM, "one subdomain's dense working set (" + std::to_string(per_slot >> 20) +
                                  " MiB) does not fit in device memory");
   c->wave = (int)std::min<size_t>(std::min<size_t>(fit, (size_t)std::min(kMaxBatch, c->slot_cap)), (size_t)np);
-  c->slots.resize(c->wave);
-  for (auto &sl : c->slots) {
-    sl.Dinv.resize(c->T_max);
-    for (auto &d : sl.Dinv) TRY(c->alloc_bytes(&d, mat));
+  TRY(c->alloc(&c->d_sums, (size_t)kMaxTheta * std::max(n_sums, 1)));
+  QSEL_CUDA_TRY(cudaMemset(c->d_sums, 0, (size_t)kMaxTheta * std::max(n_sums, 1) * sizeof(double)));
+  c->n_trace_slabs = (int)tslabs.size();
+  TRY(upload(c, &c->d_slabs, tslabs));
+  c->slots.resize(c->twist ? 2 : c->wave);
+  for (size_t i = 0; i < c->slots.size(); ++i) {
+    DenseSlot &sl = c->slots[i];
+    // the reversed half's last pivot block is the forward half's middle one
+    const int own = c->twist ? c->half[i].nfac : c->T_max;
+    sl.Dinv.resize(c->twist ? c->half[i].T : c->T_max);
+    for (int t = 0; t < own; ++t) TRY(c->alloc_bytes(&sl.Dinv[t], mat));
+    if (c->twist && i == 1) sl.Dinv[c->half[1].T - 1] = c->slots[0].Dinv[c->half[0].T - 1];
     TRY(c->alloc_bytes(&sl.SigA, mat));
     TRY(c->alloc_bytes(&sl.SigB, mat));
     TRY(c->alloc_bytes(&sl.Y, mat));
@@ -1361,9 +1448,13 @@ template <typename T>
 static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent_t, int>> &marks, int stages = 3) {
   cudaStream_t s = c->stream;
   const int n_pad = c->n_pad, n_s = c->n_s, ld = c->ld;
+  // the wave's parts: p0..p1 of the partition, or the two halves of the
+  // one-part form factored from both ends
+  if (c->twist) p1 = p0 + 2;
+  auto part = [&](int p) -> Subdomain & { return c->twist ? c->half[p - p0] : c->parts[p]; };
   const size_t svec = (size_t)n_pad * ld;
   int maxT = 0;
-  for (int p = p0; p < p1; ++p) maxT = std::max(maxT, c->parts[p].T);
+  for (int p = p0; p < p1; ++p) maxT = std::max(maxT, part(p).T);
   auto slot = [&](int p) -> DenseSlot & { return c->slots[p - p0]; };
   auto Dinv = [&](int p, int t) { return static_cast<T *>(slot(p).Dinv[t]); };
   auto buf = [](void *x) { return static_cast<T *>(x); };
@@ -1375,17 +1466,17 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
     SweepBatch<T> wb{};
     SpBatch<T, T> gb{};
     for (int p = p0; p < p1; ++p) {
-      Subdomain &sd = c->parts[p];
-      if (t >= sd.T) continue;
+      Subdomain &sd = part(p);
+      if (t >= sd.nfac) continue;
       DenseSlot &sl = slot(p);
-      const int tg = sd.e0 + t;
+      const int tg = sd.g(t);
       SchurEntry<T> &se = sb.e[sb.count++];
       se.W = (t > 0) ? buf(sl.W) : nullptr;
       se.D = Dinv(p, t);
       se.dval = c->mod.diag.at(tg);
       se.a0 = c->mod.diag.scale_ptr(tg);
-      se.cval = (t > 0) ? c->mod.off.at(tg - 1) : nullptr;
-      se.c = (t > 0) ? c->mod.off.scale_ptr(tg - 1) : nullptr;
+      se.cval = (t > 0) ? c->mod.off.at(sd.cpl(t - 1)) : nullptr;
+      se.c = (t > 0) ? c->mod.off.scale_ptr(sd.cpl(t - 1)) : nullptr;
       se.obs = c->mod.obs ? c->mod.obs + (size_t)tg * n_s : nullptr;
       wb.pivot_fp64 = c->opt.pivot_precision == QSEL_PIVOT_FP64 ? 1 : 0;
       SweepEntry<T> &we = wb.e[wb.count++];
@@ -1406,13 +1497,26 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         ge.B = Dinv(p, t);
         ge.C = nullptr;
         ge.Out = buf(sl.W);
-        ge.alpha_ptr = c->mod.off.scale_ptr(tg);
-        ge.val = c->mod.off.at(tg);
+        ge.alpha_ptr = c->mod.off.scale_ptr(sd.cpl(t));
+        ge.val = c->mod.off.at(sd.cpl(t));
         ge.alpha = 1.0;
         ge.beta = 0.0;
       }
     }
     launch_schur_assemble<T>(s, sb, c->pat, c->mod.obs_w, n_s, n_pad);
+    if (c->twist && t == part(p0).T - 1) {
+      // the middle slab m: its other neighbour's term - B_m W'^T, W' = B_m
+      // D'^-1 of the reversed half's last factored slab m + 1
+      const int m = part(p0).e1 - 1;
+      SchurBatch<T> ab{};
+      SchurEntry<T> &ae = ab.e[ab.count++];
+      ae.W = buf(slot(p0 + 1).W);
+      ae.D = Dinv(p0, t);
+      ae.cval = c->mod.off.at(m);
+      ae.c = c->mod.off.scale_ptr(m);
+      ae.accumulate = 1;
+      launch_schur_assemble<T>(s, ab, c->pat, c->mod.obs_w, n_s, n_pad);
+    }
     spd_inverse<T>(s, wb, n_pad, c->d_err, c->tc_passes, c->mixed ? &c->sweep_ss : nullptr);
     launch_sp_rowgather<T, T>(s, gb, c->pat, n_s, n_pad, n_pad, n_pad, n_pad);
   }
@@ -1422,14 +1526,14 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
   {
     ExtractBatch<T> xb{};
     for (int p = p0; p < p1; ++p) {
-      Subdomain &sd = c->parts[p];
+      Subdomain &sd = part(p);
       const int tl = sd.T - 1;
       if (tl < sd.lo || tl > sd.hi) continue;
       ExtractEntry<T> &xe = xb.e[xb.count++];
       xe.S = Dinv(p, tl);
-      xe.diag_out = c->d_selinv + (size_t)(sd.e0 + tl) * n_s;
+      xe.diag_out = c->d_selinv + (size_t)sd.g(tl) * n_s;
       xe.sums = c->d_sums + kMaxTheta * (size_t)(sd.slot_base + tl);
-      set_sum_vals(xe, c->dmod.diag, c->dmod.n, sd.e0 + tl);
+      set_sum_vals(xe, c->dmod.diag, c->dmod.n, sd.g(tl));
       xe.D0 = nullptr;
       xe.V = nullptr;
     }
@@ -1437,7 +1541,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
   }
   std::vector<T *> sig_next(p1 - p0, nullptr);
   std::vector<int> flip(p1 - p0, 0);
-  for (int p = p0; p < p1; ++p) sig_next[p - p0] = Dinv(p, c->parts[p].T - 1);
+  for (int p = p0; p < p1; ++p) sig_next[p - p0] = Dinv(p, part(p).T - 1);
   bool use_tc = false;
   if constexpr (std::is_same<T, float>::value) use_tc = c->tc_passes > 0;
   if (use_tc) {
@@ -1452,18 +1556,18 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         DiagRowBatch<T> db{};
         std::vector<int> active;
         for (int p = p0; p < p1; ++p) {
-          Subdomain &sd = c->parts[p];
+          Subdomain &sd = part(p);
           DenseSlot &sl = slot(p);
           const int tl = sd.T - 2 - b;
           if (tl < std::max(sd.lo - 1, 0)) continue;
           active.push_back(p);
-          const int tg = sd.e0 + tl;
+          const int tg = sd.g(tl), tc = sd.cpl(tl);
           SpEntry<T, T> &we = wb.e[wb.count++];
           we.B = Dinv(p, tl);
           we.C = nullptr;
           we.Out = buf(sl.W);
-          we.alpha_ptr = c->mod.off.scale_ptr(tg);
-          we.val = c->mod.off.at(tg);
+          we.alpha_ptr = c->mod.off.scale_ptr(tc);
+          we.val = c->mod.off.at(tc);
           we.alpha = 1.0;
           we.beta = 0.0;
           GemmEntry<T> &ye = yb.e[yb.count++];
@@ -1479,7 +1583,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
             xe.S = buf(sl.Y);   // <M, Y> = <M, Y^T> for symmetric M
             xe.diag_out = nullptr;
             xe.sums = c->d_sums + kMaxTheta * (size_t)(sd.slot_base + sd.T + tl);
-            set_sum_vals(xe, c->dmod.off, c->dmod.n, tg);
+            set_sum_vals(xe, c->dmod.off, c->dmod.n, tc);
             xe.D0 = nullptr;
             xe.V = nullptr;
           }
@@ -1559,7 +1663,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         launch_mirror<T>(s, mb, n_pad);
         launch_extract<T>(s, xs, c->pat, c->dmod.n, n_s, n_pad, c->d_diag_scratch);
         for (int p : active) {
-          Subdomain &sd = c->parts[p];
+          Subdomain &sd = part(p);
           DenseSlot &sl = slot(p);
           const int tl = sd.T - 2 - b;
           if (tl >= sd.lo) {
@@ -1578,18 +1682,18 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
     ExtractBatch<T> xy{}, xs{};
     std::vector<int> active;
     for (int p = p0; p < p1; ++p) {
-      Subdomain &sd = c->parts[p];
+      Subdomain &sd = part(p);
       DenseSlot &sl = slot(p);
       const int tl = sd.T - 2 - b;
       if (tl < std::max(sd.lo - 1, 0)) continue;
       active.push_back(p);
-      const int tg = sd.e0 + tl;
+      const int tg = sd.g(tl), tc = sd.cpl(tl);
       SpEntry<T, T> &we = wb.e[wb.count++];
       we.B = Dinv(p, tl);
       we.C = nullptr;
       we.Out = buf(sl.W);
-      we.alpha_ptr = c->mod.off.scale_ptr(tg);
-      we.val = c->mod.off.at(tg);
+      we.alpha_ptr = c->mod.off.scale_ptr(tc);
+      we.val = c->mod.off.at(tc);
       we.alpha = 1.0;
       we.beta = 0.0;
       GemmEntry<T> &ye = yb.e[yb.count++];
@@ -1605,7 +1709,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         xe.S = buf(sl.Y);
         xe.diag_out = nullptr;
         xe.sums = c->d_sums + kMaxTheta * (size_t)(sd.slot_base + sd.T + tl);
-        set_sum_vals(xe, c->dmod.off, c->dmod.n, tg);
+        set_sum_vals(xe, c->dmod.off, c->dmod.n, tc);
         xe.D0 = nullptr;
         xe.V = nullptr;
       }
@@ -1615,8 +1719,8 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
         ve.B = buf(sl.Y);
         ve.C = nullptr;
         ve.Out = buf(sl.V);
-        ve.alpha_ptr = c->mod.off.scale_ptr(tg);
-        ve.val = c->mod.off.at(tg);
+        ve.alpha_ptr = c->mod.off.scale_ptr(tc);
+        ve.val = c->mod.off.at(tc);
         ve.alpha = 1.0;
         ve.beta = 0.0;
         GemmEntry<T> &ge = sgb.e[sgb.count++];
@@ -1649,7 +1753,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
     launch_mirror<T>(s, mb, n_pad);
     launch_extract<T>(s, xs, c->pat, c->dmod.n, n_s, n_pad, c->d_diag_scratch);
     for (int p : active) {
-      Subdomain &sd = c->parts[p];
+      Subdomain &sd = part(p);
       DenseSlot &sl = slot(p);
       const int tl = sd.T - 2 - b;
       if (tl >= sd.lo) {
@@ -1667,11 +1771,11 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
   //   backward w_{T-1} = u_{T-1}, w_t = u_t - D_t^-1 (c_t Q_s w_{t+1})
   std::vector<int> grp;
   for (int p = p0; p < p1; ++p)
-    if (c->parts[p].sep_left >= 0 || c->parts[p].sep_right >= 0) grp.push_back(p);
+    if (part(p).sep_left >= 0 || part(p).sep_right >= 0) grp.push_back(p);
   if (!grp.empty()) {
     SpBatch<double, T> bl{}, br{};
     for (int p : grp) {
-      Subdomain &sd = c->parts[p];
+      Subdomain &sd = part(p);
       DenseSlot &sl = slot(p);
       if (sd.sep_left >= 0) {
         SpEntry<double, T> &e = bl.e[bl.count++];
@@ -1715,7 +1819,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       return ok();
     };
     for (int p : grp) {
-      Subdomain &sd = c->parts[p];
+      Subdomain &sd = part(p);
       DenseSlot &sl = slot(p);
       if (sd.T == 1 && sd.sep_right >= 0) launch_add<T>(s, buf(sl.ybuf), buf(sl.bright), (int64_t)svec);
     }
@@ -1723,7 +1827,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       GemmBatch<T> ub{};
       SpBatch<T, T> yb{};
       for (int p : grp) {
-        Subdomain &sd = c->parts[p];
+        Subdomain &sd = part(p);
         DenseSlot &sl = slot(p);
         if (t >= sd.T) continue;
         bt[ub.count] = sl.tra;
@@ -1755,7 +1859,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
       SpBatch<T, T> tb{};
       GemmBatch<T> wb{};
       for (int p : grp) {
-        Subdomain &sd = c->parts[p];
+        Subdomain &sd = part(p);
         DenseSlot &sl = slot(p);
         const int t = sd.T - 2 - b;
         if (t < std::max(sd.lo - 1, 0)) continue;
@@ -1783,7 +1887,7 @@ static Err run_wave(qsel_ctx *c, int p0, int p1, std::vector<std::pair<cudaEvent
     }
     CorrBatch<T> cb{};
     for (int p : grp) {
-      Subdomain &sd = c->parts[p];
+      Subdomain &sd = part(p);
       CorrEntry<T> &e = cb.e[cb.count++];
       e.w = buf(slot(p).wbuf);
       e.T_ = sd.T;

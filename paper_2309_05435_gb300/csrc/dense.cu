@@ -14,6 +14,8 @@
 // Sigma_{t+1} W_t and the D_t^-1 V products are dense n_s^3 work; they run
 // here as 64 x 64 FP64 tiles.  Every dense matrix is n_pad x n_pad row-major
 // (n_pad = n_s rounded up to 64, identity on the padded diagonal).
+#include <atomic>
+#include "qsel.h"
 #include "kernels.cuh"
 #include "sweep.cuh"
 
@@ -614,10 +616,15 @@ __global__ void __launch_bounds__(256) k_sweep_mirror(SweepBatch<T> bt, int ld, 
   }
 }
 
+static std::atomic<int> g_sweep_serial{0}, g_update_ctas{0};
+int sweep_serial() { return g_sweep_serial.load(); }
+int update_cta_cap() { return g_update_ctas.load(); }
+
 template <typename T>
 void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err_flag, int tc_passes,
                  const SweepStreams *ss) {
   if (b.count <= 0) return;
+  if (sweep_serial()) ss = nullptr;
   const int nt = n_pad / 64;
   const int n_lower = nt * (nt + 1) / 2;
   if constexpr (std::is_same<T, float>::value) {
@@ -1015,6 +1022,17 @@ __global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch<T> bt, SellPa
   const double *__restrict__ dval = e.dval;
   const T neg_c = e.W ? (T)(-(e.c ? *e.c : 1.0)) : T(0);
   const int r0 = blockIdx.y * kGatherRows, r1 = min(n_pad, r0 + kGatherRows);
+  if (e.accumulate) {
+    // a second Schur term on the spatial block (the middle slab of a
+    // two-ended factorisation), combined in double like the pattern entries
+    if (l >= n_s || !e.W) return;
+    const double c = e.c ? *e.c : 1.0;
+    for (int r = r0; r < min(r1, n_s); ++r) {
+      T *d = e.D + (int64_t)r * n_pad + l;
+      *d = (T)((double)*d - c * (double)schur_sum(e.W + (int64_t)r * n_pad, w, s_col, s_val));
+    }
+    return;
+  }
   for (int r = r0; r < r1; ++r) {
     T out;
     if (r < n_s && l < n_s)
@@ -1188,3 +1206,10 @@ template void launch_extract<float>(cudaStream_t, const ExtractBatch<float> &, c
                                     double *);
 
 }  // namespace qsel
+
+extern "C" qsel_status qsel_debug_sweep_schedule(int32_t serial, int32_t update_ctas) {
+  if (update_ctas < 0) return QSEL_EINVAL;
+  qsel::g_sweep_serial.store(serial ? 1 : 0);
+  qsel::g_update_ctas.store(update_ctas);
+  return QSEL_OK;
+}

@@ -347,6 +347,8 @@ struct SchurEntry {
   const double *cval;       // spatial values of B_{t-1} on the pattern (ignored if W null)
   const double *c;          // device scale of B_{t-1}, or null (1)
   const uint8_t *obs;       // mask of slab t (n_s entries), or null
+  int accumulate;           // 1: D -= c W B^T on the n_s x n_s block only (a second
+                            // neighbour's term; dval, a0, obs ignored)
 };
 template <typename T>
 struct SchurBatch {
@@ -360,6 +362,9 @@ void launch_schur_assemble(cudaStream_t s, const SchurBatch<T> &b, const SellPat
 // column's pattern in shared memory; widest pattern they accept, and the
 // opt-in of those kernels to the shared memory pat.max_width needs.
 constexpr int kMaxPatternWidth = 64;
+// scheduling hook of the panel-blocked sweep (qsel_debug_sweep_schedule)
+int sweep_serial();
+int update_cta_cap();
 bool configure_pattern_kernels(const SellPattern &pat);
 
 template <typename T>

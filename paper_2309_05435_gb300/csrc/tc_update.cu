@@ -322,6 +322,7 @@ bool launch_tc_update(cudaStream_t s, const UpdateBatch &b, int n, int K, int ld
   int sms = 152;
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (update_cta_cap() > 0) sms = std::min(sms, update_cta_cap());
   const int grid = std::min(p.total_tiles, sms);
   ++g_launch_count;
   tcu::k_tc_update<<<grid, 192, tcu::SMEM_BYTES, s>>>(p);

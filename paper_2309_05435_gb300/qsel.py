@@ -23,6 +23,8 @@ QSEL_PIVOT_FP64 = 1
 QSEL_MODEL_SEPARABLE = 0
 QSEL_MODEL_DIFFUSION = 1
 QSEL_MODEL_BLOCK_TRIDIAGONAL = 2
+QSEL_CHAIN_TWO_ENDED = 0
+QSEL_CHAIN_FORWARD = 1
 
 _STATUS = {0: "QSEL_OK", 1: "QSEL_EINVAL", 2: "QSEL_ENOMEM", 3: "QSEL_ECUDA", 4: "QSEL_ENOTSPD",
            5: "QSEL_ENOCONV", 6: "QSEL_ETIMEOUT", 7: "QSEL_ESTATE"}
@@ -49,7 +51,8 @@ class qsel_options(ctypes.Structure):
                 ("pcg_max_iter", c_int32), ("precond_block", c_int32), ("control_variate", c_int32),
                 ("cuda_stream", c_void_p), ("profile_kernels", c_int32), ("tensor_passes", c_int32),
                 ("sampler", c_int32), ("lanczos_steps", c_int32), ("preconditioner", c_int32),
-                ("part_overlap", POINTER(c_int32)), ("pivot_precision", c_int32), ("model", c_int32)]
+                ("part_overlap", POINTER(c_int32)), ("pivot_precision", c_int32), ("model", c_int32),
+                ("chain", c_int32)]
 
 
 class qsel_bt_model(ctypes.Structure):
@@ -103,7 +106,7 @@ EXPORTED = ["qsel_create", "qsel_create_bt", "qsel_set_bt_values", "qsel_set_see
             "qsel_fixed_effects",
             "qsel_debug_set_samples", "qsel_debug_get_samples", "qsel_debug_get_rhs",
             "qsel_debug_get_selinv_diag", "qsel_debug_get_lanczos", "qsel_debug_apply_precond",
-            "qsel_spd_inverse_noalloc", "qsel_debug_tc_wait",
+            "qsel_spd_inverse_noalloc", "qsel_debug_tc_wait", "qsel_debug_sweep_schedule",
             "qsel_error_estimate",
             "qsel_cv_create", "qsel_cv_set_params", "qsel_cv_get_params", "qsel_cv_predict", "qsel_cv_grad",
             "qsel_cv_train", "qsel_cv_features", "qsel_cv_targets", "qsel_cv_plan",
@@ -150,6 +153,7 @@ def load_library(path: str = LIB_PATH):
     lib.qsel_debug_apply_precond.argtypes = [c_void_p, P(c_double), P(c_double), c_int32]
     lib.qsel_spd_inverse_noalloc.argtypes = [c_void_p, c_int32, c_int32, c_void_p]
     lib.qsel_debug_tc_wait.argtypes = [c_int32, c_int64]
+    lib.qsel_debug_sweep_schedule.argtypes = [c_int32, c_int32]
     lib.qsel_error_estimate.argtypes = [c_void_p, P(c_double), P(c_double)]
     lib.qsel_cv_create.argtypes = [P(c_void_p), c_uint64, c_void_p]
     lib.qsel_cv_set_params.argtypes = [c_void_p, P(c_float)]
@@ -236,7 +240,8 @@ def qsel_create(n_s, n_t, c_diag, g_rowptr, g_col, g_val, obs_mask, sigma, theta
                 pcg_max_iter=20000, precond_block=0, control_variate=0, cuda_stream=None,
                 profile_kernels=0, tensor_passes=0, part_overlap=None, sampler=QSEL_SAMPLER_PCG,
                 lanczos_steps=0, preconditioner=QSEL_PRECOND_BLOCK_JACOBI,
-                pivot_precision=QSEL_PIVOT_DOUBLE_FLOAT, model=QSEL_MODEL_SEPARABLE) -> Context:
+                pivot_precision=QSEL_PIVOT_DOUBLE_FLOAT, model=QSEL_MODEL_SEPARABLE,
+                chain=QSEL_CHAIN_TWO_ENDED) -> Context:
     """Create a context from host arrays (copied by the library).  With
     model=QSEL_MODEL_DIFFUSION, theta = (log gamma_s, log gamma_t, log gamma_e)."""
     lib = load_library()
@@ -261,7 +266,8 @@ def qsel_create(n_s, n_t, c_diag, g_rowptr, g_col, g_val, obs_mask, sigma, theta
                        int(precond_block), int(control_variate),
                        c_void_p(int(cuda_stream)) if cuda_stream else None, int(profile_kernels),
                        int(tensor_passes), int(sampler), int(lanczos_steps), int(preconditioner),
-                       _ptr(po, c_int32) if po is not None else None, int(pivot_precision), int(model))
+                       _ptr(po, c_int32) if po is not None else None, int(pivot_precision), int(model),
+                       int(chain))
     h = c_void_p()
     st = lib.qsel_create(ctypes.byref(h), ctypes.byref(model_s), ctypes.byref(th), ctypes.byref(part),
                          int(overlap), ctypes.byref(opt))
@@ -273,7 +279,7 @@ def qsel_create_bt(n_s, n_t, rowptr, col, diag_vals, off_vals, ddiag_vals=None, 
                    slab_start=None, overlap=0, n_samples=64, seed=0, precision=QSEL_FP64, pcg_tol=1e-10,
                    cuda_stream=None, sampler=QSEL_SAMPLER_LANCZOS, lanczos_steps=64, precond_block=0,
                    profile_kernels=0, tensor_passes=0, part_overlap=None,
-                   pivot_precision=QSEL_PIVOT_DOUBLE_FLOAT) -> Context:
+                   pivot_precision=QSEL_PIVOT_DOUBLE_FLOAT, chain=QSEL_CHAIN_TWO_ENDED) -> Context:
     """Context for a user-given block-tridiagonal precision: the pattern in
     CSR (rowptr, col), diag_vals (n_t x nnz), off_vals ((n_t - 1) x nnz),
     and optional derivatives ddiag_vals (n_theta x n_t x nnz), doff_vals
@@ -296,7 +302,7 @@ def qsel_create_bt(n_s, n_t, rowptr, col, diag_vals, off_vals, ddiag_vals=None, 
                        c_void_p(int(cuda_stream)) if cuda_stream else None, int(profile_kernels),
                        int(tensor_passes), int(sampler), int(lanczos_steps), QSEL_PRECOND_BLOCK_JACOBI,
                        _ptr(po, c_int32) if po is not None else None, int(pivot_precision),
-                       QSEL_MODEL_BLOCK_TRIDIAGONAL)
+                       QSEL_MODEL_BLOCK_TRIDIAGONAL, int(chain))
     h = c_void_p()
     _check(lib.qsel_create_bt(ctypes.byref(h), ctypes.byref(m), ctypes.byref(part), int(overlap),
                               ctypes.byref(opt)), None)
@@ -462,6 +468,13 @@ def qsel_spd_inverse_noalloc(a, n: int, lda: int | None = None, cuda_stream=None
     st = load_library().qsel_spd_inverse_noalloc(c_void_p(ptr), int(n), int(lda if lda is not None else n),
                                                   c_void_p(int(cuda_stream)) if cuda_stream else None)
     _check(st, None)
+
+
+def qsel_debug_sweep_schedule(serial: bool, update_ctas: int = 0):
+    """Scheduling hook of the mixed sweep: serial runs each panel's update after
+    the pivot chain on one stream; update_ctas > 0 caps the persistent update
+    kernel's CTAs.  qsel_debug_sweep_schedule(False, 0) restores the default."""
+    _check(load_library().qsel_debug_sweep_schedule(1 if serial else 0, int(update_ctas)), None)
 
 
 def qsel_debug_tc_wait(skip_loads: bool, wait_cycles: int = 0):

@@ -161,16 +161,20 @@ def test_mixed_matches_fp64_same_seed_full_size(q):
     assert rel(t32, t64) <= MIXED_TRACE_TOL
 
 
+@pytest.mark.parametrize("chain", ["two_ended", "forward"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_single_part_exact_full_size(q, precision):
+def test_single_part_exact_full_size(q, precision, chain):
     """One part: the exact selected inverse through every panel of every
-    pivot block, against the oracle's block Takahashi recursion."""
+    pivot block, against the oracle's block Takahashi recursion; factored
+    from both ends toward the middle slab (two halves batched in every
+    launch) or in one chain from slab 0."""
     prec = q.QSEL_FP64 if precision == "fp64" else q.QSEL_MIXED
-    c = Big(q, "panels40_ragged", precision=prec, parts=1, overlap=0)
+    ch = q.QSEL_CHAIN_TWO_ENDED if chain == "two_ended" else q.QSEL_CHAIN_FORWARD
+    c = Big(q, "panels40_ragged", precision=prec, parts=1, overlap=0, chain=ch)
     v, t = c.ctx.diag_inv(), c.ctx.trace_grads()
     v_or, t_or, _ = o.rbmc(c.model, c.theta, np.array([0, c.n_t]), 0, np.zeros((c.n_s * c.n_t, 1)))
     tol_v, tol_t = (1e-10, 1e-10) if precision == "fp64" else (MIXED_DIAG_TOL, MIXED_TRACE_TOL)
-    print(f"exact one part {precision}: diag {rel(v, v_or):.2e} traces {rel(t, np.asarray(t_or)):.2e}")
+    print(f"exact one part {precision} {chain}: diag {rel(v, v_or):.2e} traces {rel(t, np.asarray(t_or)):.2e}")
     assert rel(v, v_or) <= tol_v
     assert rel(t, np.asarray(t_or)) <= tol_t
 

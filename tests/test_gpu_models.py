@@ -194,6 +194,28 @@ def test_bt_single_part_exact(q, precision):
     assert rel(t, t_ex) <= tt
 
 
+@pytest.mark.parametrize("chain", ["two_ended", "forward"])
+@pytest.mark.parametrize("n_t", [2, 3, 4, 5, 9])
+def test_bt_single_part_both_chains(q, n_t, chain):
+    """One part, factored from both ends toward the middle slab n_t // 2 (or,
+    for n_t = 2 and with QSEL_CHAIN_FORWARD, in one chain from slab 0): the
+    exact selected inverse and traces of the oracle.  The blocks and the
+    derivatives differ from slab to slab, so a wrong slab or coupling index in
+    either half, or a missing neighbour term of the middle slab, shows."""
+    n_s, n_t, Q, dQs = random_bt(n_t=n_t, seed=5)
+    rowptr, col, diag, off, dd, do = bt_inputs(Q, dQs, n_s, n_t)
+    v_ex, t_ex = o.exact_selinv(Q, dQs)
+    ch = q.QSEL_CHAIN_TWO_ENDED if chain == "two_ended" else q.QSEL_CHAIN_FORWARD
+    for prec, tv, tt in ((q.QSEL_FP64, 1e-10, 1e-10), (q.QSEL_MIXED, MIXED_DIAG_TOL, MIXED_TRACE_TOL)):
+        ctx = q.qsel_create_bt(n_s, n_t, rowptr, col, diag, off, dd, do, n_parts=1, n_samples=4,
+                               precision=prec, chain=ch)
+        v = ctx.diag_inv()
+        t = q.qsel_trace_grads_n(ctx, 2)
+        ctx.close()
+        assert rel(v, v_ex) <= tv
+        assert rel(t, t_ex) <= tt
+
+
 @pytest.mark.parametrize("parts,n_l", [(2, 1), ([0, 1, 4, 6], 2)])
 def test_bt_injected_samples_match_oracle(q, parts, n_l):
     n_s, n_t, Q, dQs = random_bt()
