@@ -475,11 +475,18 @@ qsel_status qsel_debug_tc_wait(int32_t skip_loads, int64_t wait_cycles);
  * rank-64 bw update of the rest runs on the same stream as the pivot chain,
  * after it, instead of beside the next panel's pivots.  update_ctas > 0: the
  * persistent update kernel runs on at most that many CTAs (one per SM), so
- * that SMs stay free for the pivot chain; 0 = one per SM.  Process-wide;
- * qsel_debug_sweep_schedule(0, 0) restores the default.  Errors: QSEL_EINVAL
- * for update_ctas < 0.
+ * that SMs stay free for the pivot chain; 0 = one per SM.  update_stages 2
+ * or 3: the update's shared-memory ring (3 stages leave no room for the
+ * pivot chain's CTAs on the update's SMs); 0 = the default.  By default
+ * each pivot CTA asks for unused shared memory so that it cannot share an SM
+ * with an update CTA, and the update (unless update_ctas says otherwise)
+ * leaves one SM per pivot CTA free; shared_pivot non-zero lets the pivot CTAs
+ * run beside update CTAs instead.  Process-wide;
+ * qsel_debug_sweep_schedule(0, 0, 0, 0) restores the default.  Errors:
+ * QSEL_EINVAL for update_ctas < 0 or update_stages not 0, 2 or 3.
  */
-qsel_status qsel_debug_sweep_schedule(int32_t serial, int32_t update_ctas);
+qsel_status qsel_debug_sweep_schedule(int32_t serial, int32_t update_ctas, int32_t update_stages,
+                                      int32_t shared_pivot);
 
 /*
  * Allocation-free SPD inverse.  The paper has no counterpart: this entry point

@@ -217,7 +217,7 @@ struct qsel_ctx {
     if (h_theta) cudaFreeHost(h_theta);
     for (auto &e : ev)
       if (e) cudaEventDestroy(e);
-    for (cudaEvent_t e : {sweep_ss.fork, sweep_ss.panel, sweep_ss.gather, sweep_ss.scatter})
+    for (cudaEvent_t e : {sweep_ss.fork, sweep_ss.panel, sweep_ss.lookahead, sweep_ss.scatter})
       if (e) cudaEventDestroy(e);
     if (sweep_ss.hi) cudaStreamDestroy(sweep_ss.hi);
     if (sweep_ss.lo) cudaStreamDestroy(sweep_ss.lo);
@@ -867,7 +867,7 @@ static Err build_rest(qsel_ctx *c, const RestInputs &in, const qsel_partition *p
   const bool split_panels = c->mixed && c->tc_passes == 3;
   auto slot_bytes = [&](int T) {
     return (size_t)(T + 5 + (split_panels ? 4 : 0)) * mat + (split_panels ? 10 : 6) * panel +
-           (size_t)(kSweepPanel + 1) * 64 * 64 * esz + (size_t)(T + 5) * svec + 4096;
+           (size_t)2 * kSweepPanel * (kSweepPanel + 1) * 64 * 64 * esz + (size_t)(T + 5) * svec + 4096;
   };
   size_t free_b = 0, total_b = 0;
   QSEL_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
@@ -907,7 +907,7 @@ static Err build_rest(qsel_ctx *c, const RestInputs &in, const qsel_partition *p
     TRY(c->alloc_bytes(&sl.Y, mat));
     TRY(c->alloc_bytes(&sl.W, mat));
     TRY(c->alloc_bytes(&sl.V, mat));
-    TRY(c->alloc_bytes(&sl.P, 64 * 64 * esz));
+    TRY(c->alloc_bytes(&sl.P, (size_t)2 * kSweepPanel * 64 * 64 * esz));   // per panel parity and pivot
     TRY(c->alloc_bytes(&sl.U, panel));
     TRY(c->alloc_bytes(&sl.Vs, panel));
     TRY(c->alloc_bytes(&sl.Wp, panel));
@@ -918,7 +918,7 @@ static Err build_rest(qsel_ctx *c, const RestInputs &in, const qsel_partition *p
       for (auto &sp : sl.Sp) TRY(c->alloc_bytes(&sp, panel));
       for (auto &gs : sl.Gs) TRY(c->alloc_bytes(&gs, mat));
     }
-    TRY(c->alloc_bytes(&sl.Vk, (size_t)kSweepPanel * 64 * 64 * esz));
+    TRY(c->alloc_bytes(&sl.Vk, (size_t)2 * kSweepPanel * kSweepPanel * 64 * 64 * esz));
     TRY(c->alloc_bytes(&sl.wbuf, (size_t)c->T_max * svec));
     TRY(c->alloc_bytes(&sl.ybuf, svec));
     TRY(c->alloc_bytes(&sl.tmp, svec));
@@ -944,7 +944,7 @@ static Err build_rest(qsel_ctx *c, const RestInputs &in, const qsel_partition *p
     QSEL_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
     QSEL_CUDA_TRY(cudaStreamCreateWithPriority(&c->sweep_ss.hi, cudaStreamNonBlocking, greatest));
     QSEL_CUDA_TRY(cudaStreamCreateWithPriority(&c->sweep_ss.lo, cudaStreamNonBlocking, least));
-    for (cudaEvent_t *e : {&c->sweep_ss.fork, &c->sweep_ss.panel, &c->sweep_ss.gather, &c->sweep_ss.scatter})
+    for (cudaEvent_t *e : {&c->sweep_ss.fork, &c->sweep_ss.panel, &c->sweep_ss.lookahead, &c->sweep_ss.scatter})
       QSEL_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   }
   return ok();

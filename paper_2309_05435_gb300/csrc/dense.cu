@@ -15,6 +15,7 @@
 // here as 64 x 64 FP64 tiles.  Every dense matrix is n_pad x n_pad row-major
 // (n_pad = n_s rounded up to 64, identity on the padded diagonal).
 #include <atomic>
+#include <mutex>
 #include "qsel.h"
 #include "kernels.cuh"
 #include "sweep.cuh"
@@ -351,22 +352,34 @@ __global__ void __launch_bounds__(256) k_bsweep_gather(SweepBatch<T> bt, int k0,
 // column q as they stand before the pivot.
 constexpr int kPivotThreads = 512;
 
+// P and Vk of pivot q of a panel of parity buf, kept until the rows outside
+// the panel have taken the panel's pivots: 2 kSweepPanel slots of each
+template <typename T>
+__device__ __forceinline__ T *pivot_P(const SweepEntry<T> &e, int buf, int q) {
+  return e.P + (int64_t)(buf * kSweepPanel + q) * 4096;
+}
+template <typename T>
+__device__ __forceinline__ T *pivot_Vk(const SweepEntry<T> &e, int buf, int q) {
+  return e.Vk + (int64_t)(buf * kSweepPanel + q) * kSweepPanel * 4096;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kPivotThreads) k_bsweep_pivot(SweepBatch<T> bt, int k0, int q, int bw, int buf,
                                                                 int32_t *err_flag) {
   const SweepEntry<T> e = bt.e[blockIdx.x];
   constexpr int ldw = 64 * kSweepPanel;
   const T *W = (buf ? e.Wp[1] : e.Wp[0]);
+  T *Vk = pivot_Vk(e, buf, q);
   // 16-byte rows: ldw, q * 64 and the Vk row length are multiples of 4 elements
   constexpr int V = 16 / sizeof(T);
   using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < bw * 64 * (64 / V); idx += kPivotThreads) {
     const int r = idx / (64 / V), c = (idx % (64 / V)) * V;
-    *reinterpret_cast<Vec *>(e.Vk + r * 64 + c) =
+    *reinterpret_cast<Vec *>(Vk + r * 64 + c) =
         *reinterpret_cast<const Vec *>(W + (int64_t)(k0 * 64 + r) * ldw + q * 64 + c);
   }
-  invert_pivot_tile<kPivotThreads>(W + (int64_t)(k0 + q) * 64 * ldw + q * 64, ldw, e.P, err_flag,
+  invert_pivot_tile<kPivotThreads>(W + (int64_t)(k0 + q) * 64 * ldw + q * 64, ldw, pivot_P(e, buf, q), err_flag,
                                    bt.pivot_fp64 != 0);
 }
 
@@ -407,34 +420,54 @@ __device__ __forceinline__ void panel_load_transposed(float *dst, const float *s
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_bsweep_panel(SweepBatch<T> bt, int k0, int q, int bw, int buf) {
-  static_assert(std::is_same<T, float>::value, "the panel-blocked sweep runs on float tiles");
-  __shared__ __align__(16) float sA[64 * kPanelLd];
-  __shared__ __align__(16) float sB[64 * kPanelLd];
-  const SweepEntry<T> e = bt.e[blockIdx.y];
-  constexpr int ldw = 64 * kSweepPanel;
-  const int i = blockIdx.x, k = k0 + q;
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  float *Wi = (buf ? e.Wp[1] : e.Wp[0]) + (int64_t)i * 64 * ldw;
-  float *Ui = (buf ? e.Up[1] : e.Up[0]) + (int64_t)i * 64 * ldw + q * 64;
-  float *Vi = (buf ? e.Vp[1] : e.Vp[0]) + (int64_t)i * 64 * ldw + q * 64;
-  if (i == k) {
-    for (int idx = threadIdx.x; idx < 4096; idx += 256) {
-      const int64_t o = (int64_t)(idx >> 6) * ldw + (idx & 63);
-      Wi[o + q * 64] = -e.P[idx];
-      Ui[o] = 0.0f;
-      Vi[o] = 0.0f;
-    }
-    return;
+// A 64 x 64 tile (row stride lds) into registers, 4 float4 per thread: element
+// group e = threadIdx.x + 256 m holds row e & 63, columns 4 (e >> 6) .. + 3.
+__device__ __forceinline__ void tile_to_regs(const float *src, int64_t lds, float4 (&r)[4]) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int e = threadIdx.x + 256 * m;
+    r[m] = *reinterpret_cast<const float4 *>(src + (int64_t)(e & 63) * lds + (e >> 6) * 4);
   }
-  panel_load_transposed(sA, Wi + q * 64, ldw);
-  for (int idx = threadIdx.x; idx < 64 * 16; idx += 256) {
-    const int r = idx >> 4, c4 = (idx & 15) * 4;
-    *reinterpret_cast<float4 *>(sB + r * kPanelLd + c4) = *reinterpret_cast<const float4 *>(e.P + r * 64 + c4);
+}
+// the same groups into shared memory transposed: dst[kk][r] = tile[r][kk]
+__device__ __forceinline__ void regs_to_smem_transposed(float *dst, const float4 (&r)[4]) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int e = threadIdx.x + 256 * m;
+    const int row = e & 63, k4 = (e >> 6) * 4;
+    dst[(k4 + 0) * kPanelLd + row] = r[m].x;
+    dst[(k4 + 1) * kPanelLd + row] = r[m].y;
+    dst[(k4 + 2) * kPanelLd + row] = r[m].z;
+    dst[(k4 + 3) * kPanelLd + row] = r[m].w;
+  }
+}
+
+// Pivot q of the panel on row tile i != k of the panel W (CTA-wide; sA, sB
+// staging of 64 x kPanelLd floats each).  Wk: row tile k's panel row, written
+// with U_i^T when i lies in the panel (else null).  Every global operand is
+// loaded into registers a step ahead of its use, so that the CTA waits on
+// memory about once per product instead of once per load.
+__device__ __forceinline__ void panel_row_step(float *Wi, float *Ui, float *Vi, const float *P, const float *Vk,
+                                               float *Wk, int q, int bw, float *sA, float *sB) {
+  constexpr int ldw = 64 * kSweepPanel;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  float4 w[4], pr[4], vk[4];
+  tile_to_regs(Wi + q * 64, ldw, w);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int idx = threadIdx.x + 256 * m;
+    pr[m] = *reinterpret_cast<const float4 *>(P + (idx >> 4) * 64 + (idx & 15) * 4);
+  }
+  int jj = (q == 0) ? 1 : 0;   // first panel column other than q
+  if (jj < bw) tile_to_regs(Vk + jj * 4096, 64, vk);
+  regs_to_smem_transposed(sA, w);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int idx = threadIdx.x + 256 * m;
+    *reinterpret_cast<float4 *>(sB + (idx >> 4) * kPanelLd + (idx & 15) * 4) = pr[m];
     // V_i = A_ik before the pivot
-    *reinterpret_cast<float4 *>(Vi + (int64_t)r * ldw + c4) =
-        *reinterpret_cast<const float4 *>(Wi + (int64_t)r * ldw + q * 64 + c4);
+    const int e = idx;
+    *reinterpret_cast<float4 *>(Vi + (int64_t)(e & 63) * ldw + (e >> 6) * 4) = w[m];
   }
   __syncthreads();
   float acc[4][4];
@@ -444,8 +477,6 @@ __global__ void __launch_bounds__(256) k_bsweep_panel(SweepBatch<T> bt, int k0, 
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
   panel_mma64(sA, sB, acc);
   __syncthreads();  // sA is reused for U_i below; column q of W was read
-  const bool in_panel = i >= k0 && i < k0 + bw;
-  float *Wk = (buf ? e.Wp[1] : e.Wp[0]) + (int64_t)k * 64 * ldw + (i - k0) * 64;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int r = 4 * ty + a;
@@ -459,13 +490,19 @@ __global__ void __launch_bounds__(256) k_bsweep_panel(SweepBatch<T> bt, int k0, 
     const float4 v = make_float4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
     // U_i^T staged as the left operand of the updates: sA[kk][r] = U_i[r][kk]
     *reinterpret_cast<float4 *>(sA + c * kPanelLd + 4 * ty) = v;
-    if (in_panel) *reinterpret_cast<float4 *>(Wk + (int64_t)c * ldw + 4 * ty) = v;
+    if (Wk) *reinterpret_cast<float4 *>(Wk + (int64_t)c * ldw + 4 * ty) = v;
   }
-  for (int jj = 0; jj < bw; ++jj) {
-    if (jj == q) continue;
+  while (jj < bw) {
+    int nx = jj + 1;
+    if (nx == q) ++nx;
     __syncthreads();  // sB free, sA complete
     // sB[kk][c] = Vk_jj[c][kk]
-    panel_load_transposed(sB, e.Vk + jj * 4096, 64);
+    regs_to_smem_transposed(sB, vk);
+    if (nx < bw) tile_to_regs(Vk + nx * 4096, 64, vk);
+    float4 wij[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+      wij[a] = *reinterpret_cast<const float4 *>(Wi + (int64_t)(4 * ty + a) * ldw + jj * 64 + 4 * tx);
     __syncthreads();
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -474,15 +511,42 @@ __global__ void __launch_bounds__(256) k_bsweep_panel(SweepBatch<T> bt, int k0, 
     panel_mma64(sA, sB, acc);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      float4 *p = reinterpret_cast<float4 *>(Wi + (int64_t)(4 * ty + a) * ldw + jj * 64 + 4 * tx);
-      float4 w = *p;
-      w.x -= acc[a][0];
-      w.y -= acc[a][1];
-      w.z -= acc[a][2];
-      w.w -= acc[a][3];
-      *p = w;
+      float4 w2 = wij[a];
+      w2.x -= acc[a][0];
+      w2.y -= acc[a][1];
+      w2.z -= acc[a][2];
+      w2.w -= acc[a][3];
+      *reinterpret_cast<float4 *>(Wi + (int64_t)(4 * ty + a) * ldw + jj * 64 + 4 * tx) = w2;
     }
+    jj = nx;
   }
+}
+
+// Pivot q of the panel on the panel's own row tiles i = k0 + blockIdx.x (the
+// rows the next pivot reads).  Row k takes -P; the other rows the step above.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bsweep_panel(SweepBatch<T> bt, int k0, int q, int bw, int buf) {
+  static_assert(std::is_same<T, float>::value, "the panel-blocked sweep runs on float tiles");
+  __shared__ __align__(16) float sA[64 * kPanelLd];
+  __shared__ __align__(16) float sB[64 * kPanelLd];
+  const SweepEntry<T> e = bt.e[blockIdx.y];
+  constexpr int ldw = 64 * kSweepPanel;
+  const int i = k0 + blockIdx.x, k = k0 + q;
+  float *Wi = (buf ? e.Wp[1] : e.Wp[0]) + (int64_t)i * 64 * ldw;
+  float *Ui = (buf ? e.Up[1] : e.Up[0]) + (int64_t)i * 64 * ldw + q * 64;
+  float *Vi = (buf ? e.Vp[1] : e.Vp[0]) + (int64_t)i * 64 * ldw + q * 64;
+  const float *P = pivot_P(e, buf, q);
+  if (i == k) {
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) {
+      const int64_t o = (int64_t)(idx >> 6) * ldw + (idx & 63);
+      Wi[o + q * 64] = -P[idx];
+      Ui[o] = 0.0f;
+      Vi[o] = 0.0f;
+    }
+    return;
+  }
+  float *Wk = (buf ? e.Wp[1] : e.Wp[0]) + (int64_t)k * 64 * ldw + (i - k0) * 64;
+  panel_row_step(Wi, Ui, Vi, P, pivot_Vk(e, buf, q), Wk, q, bw, sA, sB);
 }
 
 // Column panel back into the lower tiles: A_ij for j in K from W row tile i
@@ -492,33 +556,33 @@ __global__ void __launch_bounds__(256) k_bsweep_scatter(SweepBatch<T> bt, int k0
   __shared__ T S[64 * 65];
   const SweepEntry<T> e = bt.e[blockIdx.y];
   constexpr int ldw = 64 * kSweepPanel;
-  const int i = blockIdx.x;
+  // CTA per (row tile i, panel column q)
+  const int i = (int)blockIdx.x / bw, q = (int)blockIdx.x % bw;
   const bool in_panel = i >= k0 && i < k0 + bw;
-  for (int q = 0; q < bw; ++q) {
-    const int j = k0 + q;
-    const T *src = (buf ? e.Wp[1] : e.Wp[0]) + (int64_t)i * 64 * ldw + q * 64;
-    if (i >= j) {
-      T *dst = e.A + (int64_t)i * 64 * ld + j * 64;
-      for (int idx = threadIdx.x; idx < 4096; idx += 256)
-        dst[(int64_t)(idx >> 6) * ld + (idx & 63)] = src[(int64_t)(idx >> 6) * ldw + (idx & 63)];
-    } else if (!in_panel) {
-      for (int idx = threadIdx.x; idx < 4096; idx += 256)
-        S[(idx >> 6) * 65 + (idx & 63)] = src[(int64_t)(idx >> 6) * ldw + (idx & 63)];
-      __syncthreads();
-      T *dst = e.A + (int64_t)j * 64 * ld + i * 64;
-      for (int idx = threadIdx.x; idx < 4096; idx += 256) {
-        const int r = idx >> 6, c = idx & 63;
-        dst[(int64_t)r * ld + c] = S[c * 65 + r];
-      }
-      __syncthreads();
+  // the swept panel: rows K in W, the other rows in U (= W A_KK^-1)
+  const T *src = (in_panel ? (buf ? e.Wp[1] : e.Wp[0]) : (buf ? e.Up[1] : e.Up[0])) + (int64_t)i * 64 * ldw + q * 64;
+  const int j = k0 + q;
+  if (i >= j) {
+    T *dst = e.A + (int64_t)i * 64 * ld + j * 64;
+    for (int idx = threadIdx.x; idx < 4096; idx += 256)
+      dst[(int64_t)(idx >> 6) * ld + (idx & 63)] = src[(int64_t)(idx >> 6) * ldw + (idx & 63)];
+  } else if (!in_panel) {
+    for (int idx = threadIdx.x; idx < 4096; idx += 256)
+      S[(idx >> 6) * 65 + (idx & 63)] = src[(int64_t)(idx >> 6) * ldw + (idx & 63)];
+    __syncthreads();
+    T *dst = e.A + (int64_t)j * 64 * ld + i * 64;
+    for (int idx = threadIdx.x; idx < 4096; idx += 256) {
+      const int r = idx >> 6, c = idx & 63;
+      dst[(int64_t)r * ld + c] = S[c * 65 + r];
     }
   }
 }
 
 // Look-ahead: the next panel K' was gathered before the update of panel K
 // reached it.  Its rows outside K get that update as a small tensor-core
-// product; its rows K are final in panel K's W, where A_{K', K} stands, and
-// are copied transposed here: Wp[nxt](K, :) = Wp[cur](K', 0 : 64 bw)^T.
+// product; its rows K are final in panel K's U (rows K' of the swept panel,
+// where A_{K', K} stands), and are copied transposed here:
+// Wp[nxt](K, :) = Up[cur](K', 0 : 64 bw)^T.
 // CTA per (a, c) tile pair, a < bw rows of K, c < bw1 columns of K'.
 template <typename T>
 __global__ void __launch_bounds__(256) k_bsweep_rows(SweepBatch<T> bt, int k0, int bw, int k1, int bw1, int cur) {
@@ -526,7 +590,7 @@ __global__ void __launch_bounds__(256) k_bsweep_rows(SweepBatch<T> bt, int k0, i
   const SweepEntry<T> e = bt.e[blockIdx.y];
   constexpr int ldw = 64 * kSweepPanel;
   const int a = (int)blockIdx.x / bw1, c = (int)blockIdx.x % bw1;
-  const T *src = (cur ? e.Wp[1] : e.Wp[0]) + (int64_t)(k1 + c) * 64 * ldw + a * 64;
+  const T *src = (cur ? e.Up[1] : e.Up[0]) + (int64_t)(k1 + c) * 64 * ldw + a * 64;
   T *dst = (cur ? e.Wp[0] : e.Wp[1]) + (int64_t)(k0 + a) * 64 * ldw + c * 64;
   for (int idx = threadIdx.x; idx < 4096; idx += 256)
     S[(idx >> 6) * 65 + (idx & 63)] = src[(int64_t)(idx >> 6) * ldw + (idx & 63)];
@@ -616,9 +680,16 @@ __global__ void __launch_bounds__(256) k_sweep_mirror(SweepBatch<T> bt, int ld, 
   }
 }
 
-static std::atomic<int> g_sweep_serial{0}, g_update_ctas{0};
+static std::atomic<int> g_sweep_serial{0}, g_update_ctas{0}, g_update_stages{2}, g_pivot_shared{0};
 int sweep_serial() { return g_sweep_serial.load(); }
 int update_cta_cap() { return g_update_ctas.load(); }
+int update_stages() { return g_update_stages.load(); }
+int pivot_exclusive() { return !g_pivot_shared.load(); }
+// Unused dynamic shared memory that keeps a pivot CTA (42 KB static) off the
+// SMs of the persistent rank-64 bw update (129 KB): 42 + 64 + 129 KB plus the
+// per-CTA reserve exceed the SM's 228 KB, so the pivot runs on an SM that the
+// update leaves free, beside panel CTAs only.
+constexpr int kPivotPad = 64 * 1024;
 
 template <typename T>
 void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err_flag, int tc_passes,
@@ -629,10 +700,17 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
   const int n_lower = nt * (nt + 1) / 2;
   if constexpr (std::is_same<T, float>::value) {
     if (tc_passes > 0) {
-      // Panels of kSweepPanel pivots.  Panel p is pivoted on hi; its rank-64 bw
-      // update of the rest of the matrix and its scatter run on lo while panel
-      // p + 1 (gathered before that update reached it, then patched) is pivoted
-      // on hi.  Buffers alternate with the panel's parity.
+      // Panels of kSweepPanel pivots K.  The pivots sweep the panel's own rows
+      // K in turn (pivot tile inverse, then the panel step on rows K), which
+      // leaves W_KK = -A_KK^-1; every other row takes the whole panel at once,
+      // U_i = W_iK (-W_KK) = A_iK A_KK^-1 (the block form of the same sweep), and
+      // the rest of the matrix the rank-64 bw update A -= U W^T.  On hi (the
+      // critical path): the pivots, then the next panel's rows K' (their U),
+      // its gather, its look-ahead product on rows K' and its rows K; the next
+      // panel's pivots follow at once.  On lo: U on every other row, the
+      // look-ahead on those rows, the update and the scatter.  Buffers (W, U,
+      // V, P, Vk) alternate with the panel's parity; the events order the two
+      // streams' shared rows.
       constexpr int ldw = 64 * kSweepPanel;
       cudaStream_t hi = s, lo = s;
       if (ss) {
@@ -642,7 +720,8 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
         cudaStreamWaitEvent(hi, ss->fork, 0);
         cudaStreamWaitEvent(lo, ss->fork, 0);
       }
-      // C -= A B^T through the tensor cores, timed under class cls
+      const bool split_ops = tc_passes == 3 && b.e[0].Sp[0] != nullptr;
+      // C = alpha A B^T + beta C0 through the tensor cores, timed under class cls
       auto tc_update = [&](cudaStream_t st, const GemmBatch<float> &gb, int M, int N, int K, int ldc, bool lower,
                            int cls, double work, bool compact) {
         Profiler::Rec rec{cls, nullptr, nullptr, 0.0};
@@ -657,7 +736,60 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
         g_prof = saved;
         if (prof) g_prof->end(st, rec);
       };
+      // the swept panel on row tiles [r0, r1) outside K: U = W (-W_KK); W_KK is
+      // symmetric up to rounding, so it serves as the K-major right operand
+      auto panel_apply = [&](cudaStream_t st, int cur, int k0, int bw, int r0, int r1, bool compact) {
+        if (r1 <= r0) return;
+        GemmBatch<float> gb{};
+        gb.count = b.count;
+        for (int e = 0; e < b.count; ++e) {
+          gb.e[e].A = b.e[e].Wp[cur] + (int64_t)r0 * 64 * ldw;
+          gb.e[e].B = b.e[e].Wp[cur] + (int64_t)k0 * 64 * ldw;
+          gb.e[e].C0 = nullptr;
+          gb.e[e].C = b.e[e].Up[cur] + (int64_t)r0 * 64 * ldw;
+          gb.e[e].alpha = -1.0;
+          gb.e[e].beta = 0.0;
+        }
+        tc_update(st, gb, 64 * (r1 - r0), 64 * bw, 64 * bw, ldw, false, PROF_PANEL,
+                  2.0 * 64.0 * (r1 - r0) * 64.0 * bw * 64.0 * bw * b.count, compact);
+      };
+      // look-ahead rows [r0, r1) of panel K' = (k1, bw1): W'(r, :) -= U(r, :) W(K', :)^T
+      auto lookahead = [&](cudaStream_t st, int cur, int k1, int bw, int bw1, int r0, int r1, bool compact) {
+        if (r1 <= r0) return;
+        GemmBatch<float> fb{};
+        fb.count = b.count;
+        for (int e = 0; e < b.count; ++e) {
+          fb.e[e].A = b.e[e].Up[cur] + (int64_t)r0 * 64 * ldw;
+          fb.e[e].B = b.e[e].Wp[cur] + (int64_t)k1 * 64 * ldw;
+          fb.e[e].C0 = b.e[e].Wp[cur ^ 1] + (int64_t)r0 * 64 * ldw;
+          fb.e[e].C = b.e[e].Wp[cur ^ 1] + (int64_t)r0 * 64 * ldw;
+          fb.e[e].alpha = -1.0;
+          fb.e[e].beta = 1.0;
+        }
+        tc_update(st, fb, 64 * (r1 - r0), 64 * bw1, 64 * bw, ldw, false, PROF_PANEL,
+                  2.0 * 64.0 * (r1 - r0) * 64.0 * bw1 * 64.0 * bw * b.count, compact);
+      };
       const int n_panels = (nt + kSweepPanel - 1) / kSweepPanel;
+      // the update's CTA count, and the pivot CTAs' padding
+      int upd_ctas = update_cta_cap();
+      int pad = 0;
+      if (pivot_exclusive()) {
+        static std::once_flag once;
+        static bool pad_ok = false;
+        std::call_once(once, [] {
+          pad_ok = cudaFuncSetAttribute(k_bsweep_pivot<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kPivotPad) == cudaSuccess;
+          if (!pad_ok) cudaGetLastError();
+        });
+        if (pad_ok) {
+          pad = kPivotPad;
+          if (upd_ctas == 0) {
+            int sms = 152, dev = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            upd_ctas = std::max(1, sms - b.count);
+          }
+        }
+      }
       ++g_launch_count;
       {
         ProfScope ps_(hi, PROF_PANEL);
@@ -665,64 +797,67 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
       }
       for (int p = 0; p < n_panels; ++p) {
         const int k0 = p * kSweepPanel, bw = std::min(kSweepPanel, nt - k0), cur = p & 1;
+        const bool has_next = p + 1 < n_panels;
+        const int k1 = k0 + bw, bw1 = has_next ? std::min(kSweepPanel, nt - k1) : 0;
         g_launch_count += 2 * bw;
         for (int q = 0; q < bw; ++q) {
           {
             ProfScope ps_(hi, PROF_PIVOT, 2.0 * 64.0 * 64.0 * 64.0 * b.count);
-            k_bsweep_pivot<T><<<b.count, kPivotThreads, 0, hi>>>(b, k0, q, bw, cur, err_flag);
+            k_bsweep_pivot<T><<<b.count, kPivotThreads, pad, hi>>>(b, k0, q, bw, cur, err_flag);
           }
           {
             ProfScope ps_(hi, PROF_PANEL);
-            k_bsweep_panel<T><<<dim3(nt, b.count), 256, 0, hi>>>(b, k0, q, bw, cur);
+            k_bsweep_panel<T><<<dim3(bw, b.count), 256, 0, hi>>>(b, k0, q, bw, cur);
           }
         }
-        if (ss) cudaEventRecord(ss->panel, hi);
-        if (p + 1 < n_panels) {
-          const int k1 = k0 + bw, bw1 = std::min(kSweepPanel, nt - k1);
+        if (has_next) {
+          // rows K' of this panel: the previous panel's look-ahead on them ran on lo
+          if (ss && p > 0) cudaStreamWaitEvent(hi, ss->lookahead, 0);
+          g_launch_count += 2;
+          panel_apply(hi, cur, k0, bw, k1, k1 + bw1, split_ops);
           // columns K' as the previous update and scatter left them
           if (ss && p > 0) cudaStreamWaitEvent(hi, ss->scatter, 0);
-          g_launch_count += 2;
           {
             ProfScope ps_(hi, PROF_PANEL);
             k_bsweep_gather<T><<<dim3(nt, b.count), 256, 0, hi>>>(b, k1, bw1, n_pad, cur ^ 1);
           }
-          if (ss) cudaEventRecord(ss->gather, hi);
-          GemmBatch<float> fb{};
-          fb.count = b.count;
-          for (int e = 0; e < b.count; ++e) {
-            fb.e[e].A = b.e[e].Up[cur];
-            fb.e[e].B = b.e[e].Vp[cur] + (int64_t)k1 * 64 * ldw;
-            fb.e[e].C0 = b.e[e].Wp[cur ^ 1];
-            fb.e[e].C = b.e[e].Wp[cur ^ 1];
-            fb.e[e].alpha = -1.0;
-            fb.e[e].beta = 1.0;
-          }
           // compact tiles: the product runs beside the previous panel's
           // persistent update instead of waiting for its SMs
-          tc_update(hi, fb, n_pad, 64 * bw1, 64 * bw, ldw, false, PROF_PANEL,
-                    2.0 * n_pad * 64.0 * bw1 * 64.0 * bw * b.count, tc_passes == 3 && b.e[0].Sp[0] != nullptr);
+          lookahead(hi, cur, k1, bw, bw1, k1, k1 + bw1, split_ops);
           {
             ProfScope ps_(hi, PROF_PANEL);
             k_bsweep_rows<T><<<dim3(bw * bw1, b.count), 256, 0, hi>>>(b, k0, bw, k1, bw1, cur);
           }
         }
         if (ss) {
+          cudaEventRecord(ss->panel, hi);
           cudaStreamWaitEvent(lo, ss->panel, 0);
-          if (p + 1 < n_panels) cudaStreamWaitEvent(lo, ss->gather, 0);
+        }
+        // the swept panel on the other rows: outside K and K'
+        panel_apply(lo, cur, k0, bw, 0, k0, false);
+        panel_apply(lo, cur, k0, bw, has_next ? k1 + bw1 : k1, nt, false);
+        if (has_next) {
+          // the look-ahead on the rows outside K and K' (rows K come from
+          // k_bsweep_rows above)
+          lookahead(lo, cur, k1, bw, bw1, 0, k0, false);
+          lookahead(lo, cur, k1, bw, bw1, k1 + bw1, nt, false);
+          if (ss) cudaEventRecord(ss->lookahead, lo);
         }
         if (nt > bw) {
           // algorithmic work: the rank-64 bw update of the lower tiles off the
           // panel's rows and columns
           const double rest = (double)(nt - bw) * (nt - bw + 1) / 2.0;
           const double work = 2.0 * 64.0 * 64.0 * 64.0 * bw * rest * b.count;
-          if (tc_passes == 3 && b.e[0].Sp[0] != nullptr) {
+          if (split_ops) {
             // U and V split once per panel, then the persistent 3xTF32 update
             {
               ProfScope ps_(lo, PROF_PANEL);
+              SplitJobs jobs{};
               for (int e = 0; e < b.count; ++e) {
-                launch_split_tf32(lo, b.e[e].Up[cur], b.e[e].Sp[0], b.e[e].Sp[1], (int64_t)n_pad * ldw);
-                launch_split_tf32(lo, b.e[e].Vp[cur], b.e[e].Sp[2], b.e[e].Sp[3], (int64_t)n_pad * ldw);
+                jobs.j[jobs.count++] = SplitJob{b.e[e].Up[cur], b.e[e].Sp[0], b.e[e].Sp[1]};
+                jobs.j[jobs.count++] = SplitJob{b.e[e].Wp[cur], b.e[e].Sp[2], b.e[e].Sp[3]};
               }
+              launch_split_tf32_jobs(lo, jobs, (int64_t)n_pad * ldw);
             }
             UpdateBatch ub{};
             ub.count = b.count;
@@ -730,14 +865,14 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
               ub.e[e] = UpdateEntry{b.e[e].Sp[0], b.e[e].Sp[1], b.e[e].Sp[2], b.e[e].Sp[3], b.e[e].A};
             Profiler::Rec rec{PROF_SWEEP, nullptr, nullptr, work};
             if (g_prof) g_prof->begin(lo, rec);
-            launch_tc_update(lo, ub, n_pad, 64 * bw, ldw, -1.0f, 1.0f, err_flag);
+            launch_tc_update(lo, ub, n_pad, 64 * bw, ldw, -1.0f, 1.0f, err_flag, upd_ctas);
             if (g_prof) g_prof->end(lo, rec);
           } else {
             GemmBatch<float> gb{};
             gb.count = b.count;
             for (int e = 0; e < b.count; ++e) {
               gb.e[e].A = b.e[e].Up[cur];
-              gb.e[e].B = b.e[e].Vp[cur];
+              gb.e[e].B = b.e[e].Wp[cur];
               gb.e[e].C0 = b.e[e].A;
               gb.e[e].C = b.e[e].A;
               gb.e[e].alpha = -1.0;
@@ -749,7 +884,7 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
         ++g_launch_count;
         {
           ProfScope ps_(lo, PROF_PANEL);
-          k_bsweep_scatter<T><<<dim3(nt, b.count), 256, 0, lo>>>(b, k0, bw, n_pad, cur);
+          k_bsweep_scatter<T><<<dim3(nt * bw, b.count), 256, 0, lo>>>(b, k0, bw, n_pad, cur);
         }
         if (ss) cudaEventRecord(ss->scatter, lo);
       }
@@ -1207,9 +1342,12 @@ template void launch_extract<float>(cudaStream_t, const ExtractBatch<float> &, c
 
 }  // namespace qsel
 
-extern "C" qsel_status qsel_debug_sweep_schedule(int32_t serial, int32_t update_ctas) {
-  if (update_ctas < 0) return QSEL_EINVAL;
+extern "C" qsel_status qsel_debug_sweep_schedule(int32_t serial, int32_t update_ctas, int32_t update_stages,
+                                                 int32_t shared_pivot) {
+  if (update_ctas < 0 || (update_stages != 0 && update_stages != 2 && update_stages != 3)) return QSEL_EINVAL;
   qsel::g_sweep_serial.store(serial ? 1 : 0);
   qsel::g_update_ctas.store(update_ctas);
+  qsel::g_update_stages.store(update_stages == 0 ? 2 : update_stages);
+  qsel::g_pivot_shared.store(shared_pivot ? 1 : 0);
   return QSEL_OK;
 }

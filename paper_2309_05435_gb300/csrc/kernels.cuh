@@ -202,20 +202,25 @@ constexpr int kSweepPanel = 4;
 template <typename T>
 struct SweepEntry {
   T *A;          // n_pad x n_pad, row-major, lower tiles used
-  T *P;          // 64 x 64 scratch
+  T *P;          // 64 x 64 scratch (tensor-core path: 2 kSweepPanel of them, one
+                 // per panel parity and pivot)
   T *U, *V;      // n_pad x 64 scratch each (tile-major)
   // tensor-core path, one set per panel parity: the products U, the pivot
   // columns V and the column panel W, n_pad x 64 kSweepPanel each (row-major)
   T *Up[2], *Vp[2], *Wp[2];
-  T *Vk;         // tensor-core path: 64 kSweepPanel x 64 (panel rows of the pivot column)
+  T *Vk;         // tensor-core path: 2 kSweepPanel blocks of 64 kSweepPanel x 64 (the
+                 // panel rows of the pivot column, per panel parity and pivot)
   T *Sp[4];      // tensor-core path: the panel update's U and V split into TF32 hi / lo
                  // (U_hi, U_lo, V_hi, V_lo; n_pad x 64 kSweepPanel each), or null
 };
-// Streams and events of the tensor-core sweep's look-ahead: the panels run on
-// hi (high priority), the rank-64 kSweepPanel updates and scatters on lo.
+// Streams and events of the tensor-core sweep's look-ahead: the pivot chain
+// (pivots, the panel's and the next panel's rows) runs on hi (high priority);
+// the other rows' panel steps and look-ahead, the rank-64 kSweepPanel updates
+// and the scatters on lo.  panel: hi's part of a panel done; lookahead: lo's
+// look-ahead rows written; scatter: the panel back in A.
 struct SweepStreams {
   cudaStream_t hi = nullptr, lo = nullptr;
-  cudaEvent_t fork = nullptr, panel = nullptr, gather = nullptr, scatter = nullptr;
+  cudaEvent_t fork = nullptr, panel = nullptr, lookahead = nullptr, scatter = nullptr;
 };
 template <typename T>
 struct SweepBatch {
@@ -299,7 +304,7 @@ struct UpdateBatch {
   int count;
 };
 bool launch_tc_update(cudaStream_t s, const UpdateBatch &b, int n, int K, int ldp, float alpha, float beta,
-                      int32_t *err);
+                      int32_t *err, int max_ctas = 0);
 // C = alpha A B^T + beta C0 on operands given as TF32 hi / lo parts (A: M x K,
 // B: N x K, row-major; K a multiple of 32, leading dimensions multiples of 4):
 // the persistent 128 x 256-tile kernel of tc_gemm2.cu.  lower = only the tiles
@@ -319,6 +324,17 @@ bool launch_tc_gemm_split(cudaStream_t s, const SplitGemmBatch &b, int M, int N,
                           bool lower, int32_t *err);
 // hi = rn_tf32(x), lo = rn_tf32(x - hi) elementwise (16-byte aligned arrays).
 void launch_split_tf32(cudaStream_t s, const float *src, float *hi, float *lo, int64_t count);
+// the same for up to 2 kMaxBatch arrays of `count` floats each (count a
+// multiple of 4, 16-byte aligned arrays), in one launch
+struct SplitJob {
+  const float *src;
+  float *hi, *lo;
+};
+struct SplitJobs {
+  SplitJob j[2 * kMaxBatch];
+  int count;
+};
+void launch_split_tf32_jobs(cudaStream_t s, const SplitJobs &jobs, int64_t count);
 // out[r, c] = alpha in[c, r] + beta c0[r, c] for each entry (see dense.cu).
 struct TransEntry {
   const float *in, *c0;
@@ -365,6 +381,8 @@ constexpr int kMaxPatternWidth = 64;
 // scheduling hook of the panel-blocked sweep (qsel_debug_sweep_schedule)
 int sweep_serial();
 int update_cta_cap();
+int update_stages();
+int pivot_exclusive();
 bool configure_pattern_kernels(const SellPattern &pat);
 
 template <typename T>

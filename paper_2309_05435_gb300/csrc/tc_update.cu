@@ -33,10 +33,13 @@ namespace tcu {
 using namespace tc;
 
 constexpr int BN = 128;
-constexpr int STAGES = 2;
 constexpr int TILE = BM * BK * 4;            // 16 KiB: 128 rows x 32 floats
 constexpr int STAGE_BYTES = 4 * TILE;        // U_hi, U_lo, V_hi, V_lo
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 256 + 1024;
+// Two stages (129 KB) leave room on the SM for the sweep's pivot and panel
+// CTAs beside the update; three (193 KB) do not, so those run on the SMs
+// that a capped update grid leaves free.
+template <int STAGES>
+constexpr int smem_bytes() { return STAGES * STAGE_BYTES + 256 + 1024; }
 constexpr uint32_t kTmemCols = 2 * BN;
 
 struct Params {
@@ -62,6 +65,7 @@ __device__ __forceinline__ void lower_tile(int r, int &bm, int &bn) {
 
 __device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
+template <int STAGES>
 __global__ void __launch_bounds__(192, 1) k_tc_update(const __grid_constant__ Params p) {
   extern __shared__ unsigned char smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -187,15 +191,47 @@ __global__ void __launch_bounds__(192, 1) k_tc_update(const __grid_constant__ Pa
     for (int L = blockIdx.x; L < p.total_tiles; L += gridDim.x, ++i) {
       const int b = i & 1;
       const uint32_t ub = (uint32_t)(i >> 1);
-      if (threadIdx.x == 64) *ep_ok = (mbar_wait(accf_bar(b), ub & 1, abort, p.err, p.wait_cycles) && !*abort) ? 1 : 0;
-      epilogue_sync();
-      if (!*ep_ok) break;   // uniform across the four warps: tcgen05.ld is warp-collective
-      tc_fence_after();
       const int z = L / p.tiles_per_matrix;
       int bm, bn;
       lower_tile(L - z * p.tiles_per_matrix, bm, bn);
       const int row = bm * BM + 32 * q + lane;
       float *C = p.C[z];
+      // a whole row segment in range: C is read a chunk ahead, the first chunk
+      // while the tile's MMAs still run (C does not depend on them)
+      const bool full = row < p.n && (bn + 1) * BN <= p.n && p.beta != 0.0f;
+      float *crow0 = C + (int64_t)row * p.ldc + bn * BN;
+      float4 cb[2][8];
+      if (full) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cb[0][j] = *reinterpret_cast<const float4 *>(crow0 + 4 * j);
+      }
+      if (threadIdx.x == 64) *ep_ok = (mbar_wait(accf_bar(b), ub & 1, abort, p.err, p.wait_cycles) && !*abort) ? 1 : 0;
+      epilogue_sync();
+      if (!*ep_ok) break;   // uniform across the four warps: tcgen05.ld is warp-collective
+      tc_fence_after();
+      if (full) {
+#pragma unroll
+        for (int cc = 0; cc < BN / 32; ++cc) {
+          if (cc + 1 < BN / 32) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              cb[(cc + 1) & 1][j] = *reinterpret_cast<const float4 *>(crow0 + (cc + 1) * 32 + 4 * j);
+          }
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cc * 32), v);
+          float *crow = crow0 + cc * 32;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 c = cb[cc & 1][j];
+            float4 o;
+            o.x = fmaf(p.beta, c.x, p.alpha * __uint_as_float(v[4 * j]));
+            o.y = fmaf(p.beta, c.y, p.alpha * __uint_as_float(v[4 * j + 1]));
+            o.z = fmaf(p.beta, c.z, p.alpha * __uint_as_float(v[4 * j + 2]));
+            o.w = fmaf(p.beta, c.w, p.alpha * __uint_as_float(v[4 * j + 3]));
+            *reinterpret_cast<float4 *>(crow + 4 * j) = o;
+          }
+        }
+      } else {
 #pragma unroll 1
       for (int cc = 0; cc < BN / 32; ++cc) {
         uint32_t v[32];
@@ -219,6 +255,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_update(const __grid_constant__ Pa
             for (int j = 0; j < ncol; ++j) crow[j] = fmaf(p.beta, crow[j], p.alpha * __uint_as_float(v[j]));
           }
         }
+      }
       }
       tc_fence_before();
       epilogue_sync();   // every epilogue thread has read the accumulator
@@ -274,6 +311,29 @@ __global__ void __launch_bounds__(256) k_split_tf32(const float4 *__restrict__ s
   }
 }
 
+// The same split for several arrays of count4 16-byte vectors each (one per
+// grid row): the sweep's U and W of every matrix of a batch in one launch.
+__global__ void __launch_bounds__(256) k_split_tf32_jobs(SplitJobs jobs, int64_t count4) {
+  const SplitJob jb = jobs.j[blockIdx.y];
+  const float4 *__restrict__ src = reinterpret_cast<const float4 *>(jb.src);
+  float4 *__restrict__ hi = reinterpret_cast<float4 *>(jb.hi);
+  float4 *__restrict__ lo = reinterpret_cast<float4 *>(jb.lo);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count4; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = src[i];
+    float4 h, l;
+    h.x = tf32_rn(v.x);
+    h.y = tf32_rn(v.y);
+    h.z = tf32_rn(v.z);
+    h.w = tf32_rn(v.w);
+    l.x = tf32_rn(v.x - h.x);
+    l.y = tf32_rn(v.y - h.y);
+    l.z = tf32_rn(v.z - h.z);
+    l.w = tf32_rn(v.w - h.w);
+    hi[i] = h;
+    lo[i] = l;
+  }
+}
+
 std::once_flag g_attr_once;
 bool g_attr_ok = false;
 
@@ -289,13 +349,23 @@ void launch_split_tf32(cudaStream_t s, const float *src, float *hi, float *lo, i
                                                          (int)(count - 4 * c4));
 }
 
+void launch_split_tf32_jobs(cudaStream_t s, const SplitJobs &jobs, int64_t count) {
+  if (jobs.count <= 0) return;
+  ++g_launch_count;
+  const int64_t c4 = count / 4;
+  const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((c4 + 255) / 256, (152 * 4 + jobs.count - 1) / jobs.count));
+  tcu::k_split_tf32_jobs<<<dim3(gx, jobs.count), 256, 0, s>>>(jobs, c4);
+}
+
 bool launch_tc_update(cudaStream_t s, const UpdateBatch &b, int n, int K, int ldp, float alpha, float beta,
-                      int32_t *err) {
+                      int32_t *err, int max_ctas) {
   if (b.count <= 0) return true;
   if (!tc_gemm_available()) return false;
   std::call_once(tcu::g_attr_once, [] {
-    tcu::g_attr_ok = cudaFuncSetAttribute(tcu::k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          tcu::SMEM_BYTES) == cudaSuccess;
+    tcu::g_attr_ok = cudaFuncSetAttribute(tcu::k_tc_update<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          tcu::smem_bytes<2>()) == cudaSuccess &&
+                     cudaFuncSetAttribute(tcu::k_tc_update<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          tcu::smem_bytes<3>()) == cudaSuccess;
     if (!tcu::g_attr_ok) cudaGetLastError();
   });
   if (!tcu::g_attr_ok) return false;
@@ -322,10 +392,13 @@ bool launch_tc_update(cudaStream_t s, const UpdateBatch &b, int n, int K, int ld
   int sms = 152;
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (update_cta_cap() > 0) sms = std::min(sms, update_cta_cap());
+  if (max_ctas > 0) sms = std::min(sms, max_ctas);
   const int grid = std::min(p.total_tiles, sms);
   ++g_launch_count;
-  tcu::k_tc_update<<<grid, 192, tcu::SMEM_BYTES, s>>>(p);
+  if (update_stages() == 3)
+    tcu::k_tc_update<3><<<grid, 192, tcu::smem_bytes<3>(), s>>>(p);
+  else
+    tcu::k_tc_update<2><<<grid, 192, tcu::smem_bytes<2>(), s>>>(p);
   return true;
 }
 

@@ -153,7 +153,7 @@ def load_library(path: str = LIB_PATH):
     lib.qsel_debug_apply_precond.argtypes = [c_void_p, P(c_double), P(c_double), c_int32]
     lib.qsel_spd_inverse_noalloc.argtypes = [c_void_p, c_int32, c_int32, c_void_p]
     lib.qsel_debug_tc_wait.argtypes = [c_int32, c_int64]
-    lib.qsel_debug_sweep_schedule.argtypes = [c_int32, c_int32]
+    lib.qsel_debug_sweep_schedule.argtypes = [c_int32, c_int32, c_int32, c_int32]
     lib.qsel_error_estimate.argtypes = [c_void_p, P(c_double), P(c_double)]
     lib.qsel_cv_create.argtypes = [P(c_void_p), c_uint64, c_void_p]
     lib.qsel_cv_set_params.argtypes = [c_void_p, P(c_float)]
@@ -470,11 +470,15 @@ def qsel_spd_inverse_noalloc(a, n: int, lda: int | None = None, cuda_stream=None
     _check(st, None)
 
 
-def qsel_debug_sweep_schedule(serial: bool, update_ctas: int = 0):
+def qsel_debug_sweep_schedule(serial: bool, update_ctas: int = 0, update_stages: int = 0,
+                              shared_pivot: bool = False):
     """Scheduling hook of the mixed sweep: serial runs each panel's update after
     the pivot chain on one stream; update_ctas > 0 caps the persistent update
-    kernel's CTAs.  qsel_debug_sweep_schedule(False, 0) restores the default."""
-    _check(load_library().qsel_debug_sweep_schedule(1 if serial else 0, int(update_ctas)), None)
+    kernel's CTAs; update_stages (2 or 3) sets its shared-memory ring;
+    shared_pivot lets the pivot CTAs share SMs with the update.
+    qsel_debug_sweep_schedule(False) restores the default."""
+    _check(load_library().qsel_debug_sweep_schedule(1 if serial else 0, int(update_ctas), int(update_stages),
+                                                    1 if shared_pivot else 0), None)
 
 
 def qsel_debug_tc_wait(skip_loads: bool, wait_cycles: int = 0):
