@@ -3,10 +3,13 @@ as plain numpy emulations of the kernels' steps (no GPU, no oracle, no
 library code):
 
 * the panel-blocked symmetric sweep with look-ahead (Goodnight's sweep
-  operator taken four 64-pivots at a time on a gathered column panel, one
-  low-rank update of the rest per panel, the next panel gathered before that
-  update reached it and patched) reproduces A^-1, also with a ragged last
-  panel and garbage in the unused upper triangle;
+  operator taken four 64-pivots at a time on a gathered column panel: the
+  pivots sweep the panel's own rows K, which leaves W_KK = -A_KK^-1; every
+  other row takes the whole panel as one product U = W (-W_KK)^T, the rest
+  of the matrix one low-rank update A -= U W^T; the next panel is gathered
+  before that update reached it and patched, its rows K copied from U)
+  reproduces A^-1, also with a ragged last panel and garbage in the unused
+  upper triangle;
 * the double-float pivot-tile sweep (hi + lo binary32 pairs, Dekker's
   two-sum / two-product with fused multiply-adds, one Newton step for 1/d)
   tracks the binary64 inverse to about cond x 1e-15, far below binary32.
@@ -30,14 +33,15 @@ def _gather(A, W, k0, bw, nt):
             W[B * i:B * i + B, B * q:B * q + B] = blk
 
 
-def _panel(W, U, V, k0, bw, nt):
+def _panel_rows_K(W, U, V, k0, bw):
+    """The pivots of the panel, one after another, on the panel's own rows."""
     for q in range(bw):
         k = k0 + q
         Vk = W[B * k0:B * (k0 + bw), B * q:B * q + B].copy()
         Wkk = W[B * k:B * k + B, B * q:B * q + B]
         P = np.linalg.inv(np.tril(Wkk) + np.tril(Wkk, -1).T)
         Wn = W.copy()
-        for i in range(nt):
+        for i in range(k0, k0 + bw):
             rows = slice(B * i, B * i + B)
             col_q = slice(B * q, B * q + B)
             if i == k:
@@ -49,13 +53,16 @@ def _panel(W, U, V, k0, bw, nt):
             V[rows, col_q] = W[rows, col_q]
             U[rows, col_q] = Ui
             Wn[rows, col_q] = Ui
-            if k0 <= i < k0 + bw:
-                Wn[B * k:B * k + B, B * (i - k0):B * (i - k0) + B] = Ui.T
+            Wn[B * k:B * k + B, B * (i - k0):B * (i - k0) + B] = Ui.T
             for jj in range(bw):
                 if jj != q:
                     cj = slice(B * jj, B * jj + B)
                     Wn[rows, cj] = W[rows, cj] - Ui @ Vk[B * jj:B * jj + B].T
         W[:] = Wn
+
+
+def _rows(tiles):
+    return np.concatenate([np.arange(B * i, B * i + B) for i in tiles]) if tiles else np.zeros(0, dtype=int)
 
 
 def _update_lower(A, U, V, K):
@@ -67,21 +74,23 @@ def _update_lower(A, U, V, K):
             A[128 * bm:128 * bm + 128, 128 * bn:128 * bn + 128] = C[128 * bm:128 * bm + 128, 128 * bn:128 * bn + 128]
 
 
-def _scatter(A, W, k0, bw, nt):
+def _scatter(A, W, U, k0, bw, nt):
     for i in range(nt):
+        in_panel = k0 <= i < k0 + bw
+        src_m = W if in_panel else U     # rows K stand in W, the other rows in U
         for q in range(bw):
             j = k0 + q
-            src = W[B * i:B * i + B, B * q:B * q + B]
+            src = src_m[B * i:B * i + B, B * q:B * q + B]
             if i >= j:
                 A[B * i:B * i + B, B * j:B * j + B] = src
-            elif not (k0 <= i < k0 + bw):
+            elif not in_panel:
                 A[B * j:B * j + B, B * i:B * i + B] = src.T
 
 
 def blocked_sweep_inverse(A0, panel=4, seed=0):
     """Emulation of the panel-blocked sweep with look-ahead, in the order the
-    two streams' dependencies allow (panel p, gather + patch of panel p+1,
-    update and scatter of panel p)."""
+    two streams' dependencies allow (panel p on its rows, the other rows'
+    product, gather + patch of panel p+1, update and scatter of panel p)."""
     n = A0.shape[0]
     nt = n // B
     rng = np.random.default_rng(seed)
@@ -94,15 +103,19 @@ def blocked_sweep_inverse(A0, panel=4, seed=0):
     _gather(A, W[0], *panels[0], nt)
     for p, (k0, bw) in enumerate(panels):
         cur, nxt = p & 1, (p & 1) ^ 1
-        _panel(W[cur], U[cur], V[cur], k0, bw, nt)
+        K = B * bw
+        _panel_rows_K(W[cur], U[cur], V[cur], k0, bw)
+        Wkk = W[cur][B * k0:B * (k0 + bw), :K].copy()                 # -A_KK^-1
+        other = _rows([i for i in range(nt) if not k0 <= i < k0 + bw])
+        U[cur][other, :K] = -W[cur][other, :K] @ Wkk.T                 # A_iK A_KK^-1
         if p + 1 < len(panels):
             k1, bw1 = panels[p + 1]
             _gather(A, W[nxt], k1, bw1, nt)           # before the update of panel p reaches it
-            W[nxt][:, :B * bw1] -= U[cur][:, :B * bw] @ V[cur][B * k1:B * (k1 + bw1), :B * bw].T
-            W[nxt][B * k0:B * (k0 + bw), :B * bw1] = W[cur][B * k1:B * (k1 + bw1), :B * bw].T
+            W[nxt][other, :B * bw1] -= U[cur][other, :K] @ W[cur][B * k1:B * (k1 + bw1), :K].T
+            W[nxt][B * k0:B * (k0 + bw), :B * bw1] = U[cur][B * k1:B * (k1 + bw1), :K].T
         if nt > bw:
-            _update_lower(A, U[cur], V[cur], B * bw)
-        _scatter(A, W[cur], k0, bw, nt)
+            _update_lower(A, U[cur], W[cur], K)
+        _scatter(A, W[cur], U[cur], k0, bw, nt)
     L = np.tril(A)
     return -(L + np.tril(L, -1).T)   # the sweep leaves -A^-1
 
