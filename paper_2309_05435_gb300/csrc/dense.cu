@@ -833,29 +833,88 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
           cudaEventRecord(ss->panel, hi);
           cudaStreamWaitEvent(lo, ss->panel, 0);
         }
-        // the swept panel on the other rows: outside K and K'
-        panel_apply(lo, cur, k0, bw, 0, k0, false);
-        panel_apply(lo, cur, k0, bw, has_next ? k1 + bw1 : k1, nt, false);
-        if (has_next) {
-          // the look-ahead on the rows outside K and K' (rows K come from
-          // k_bsweep_rows above)
-          lookahead(lo, cur, k1, bw, bw1, 0, k0, false);
-          lookahead(lo, cur, k1, bw, bw1, k1 + bw1, nt, false);
-          if (ss) cudaEventRecord(ss->lookahead, lo);
+        // the swept panel on the other rows (outside K and K'), their look-ahead
+        // (rows K come from k_bsweep_rows above), the update of the rest
+        const int r1s = has_next ? k1 + bw1 : k1;   // other rows: [0, k0) and [r1s, nt)
+        bool fused = false;
+        if (split_ops) {
+          // W (the products' left operand and the update's right one) and U's
+          // rows K' (the look-ahead's right operand) split once
+          {
+            ProfScope ps_(lo, PROF_PANEL);
+            SplitJobs jobs{};
+            for (int e = 0; e < b.count; ++e) {
+              jobs.j[jobs.count++] = SplitJob{b.e[e].Wp[cur], b.e[e].Sp[2], b.e[e].Sp[3], 0};
+              if (has_next) {
+                const int64_t off = (int64_t)k1 * 64 * ldw;
+                jobs.j[jobs.count++] = SplitJob{b.e[e].Up[cur] + off, b.e[e].Sp[0] + off, b.e[e].Sp[1] + off,
+                                                (int64_t)64 * bw1 * ldw};
+              }
+            }
+            launch_split_tf32_jobs(lo, jobs, (int64_t)n_pad * ldw);
+          }
+          // U = W (-W_KK)^T and W' -= W U_K'^T (= U W_K'^T: W_KK is symmetric)
+          // on both row ranges of every matrix: one persistent launch per
+          // kMaxBatch products
+          Profiler::Rec rec{PROF_PANEL, nullptr, nullptr, 0.0};
+          Profiler *saved = g_prof;
+          if (saved) saved->begin(lo, rec);
+          g_prof = nullptr;
+          fused = true;
+          SplitGemmBatch gb{};
+          auto flush = [&]() {
+            if (gb.count > 0 && !launch_tc_gemm_split(lo, gb, n_pad, 64 * kSweepPanel, 64 * bw, ldw, ldw, ldw, false,
+                                                      err_flag))
+              fused = false;
+            gb.count = 0;
+          };
+          for (int e = 0; e < b.count && fused; ++e) {
+            const int ranges[2][2] = {{0, k0}, {r1s, nt}};
+            for (const auto &rg : ranges) {
+              if (rg[1] <= rg[0]) continue;
+              const int64_t ro = (int64_t)rg[0] * 64 * ldw;
+              const int rows = 64 * (rg[1] - rg[0]);
+              if (gb.count == kMaxBatch) flush();
+              gb.e[gb.count++] = SplitGemmEntry{b.e[e].Sp[2] + ro, b.e[e].Sp[3] + ro,
+                                                b.e[e].Sp[2] + (int64_t)k0 * 64 * ldw,
+                                                b.e[e].Sp[3] + (int64_t)k0 * 64 * ldw, nullptr, b.e[e].Up[cur] + ro,
+                                                -1.0f, 0.0f, rows, 64 * bw};
+              if (has_next) {
+                if (gb.count == kMaxBatch) flush();
+                gb.e[gb.count++] = SplitGemmEntry{b.e[e].Sp[2] + ro, b.e[e].Sp[3] + ro,
+                                                  b.e[e].Sp[0] + (int64_t)k1 * 64 * ldw,
+                                                  b.e[e].Sp[1] + (int64_t)k1 * 64 * ldw, b.e[e].Wp[cur ^ 1] + ro,
+                                                  b.e[e].Wp[cur ^ 1] + ro, -1.0f, 1.0f, rows, 64 * bw1};
+              }
+            }
+          }
+          flush();
+          g_prof = saved;
+          if (saved) saved->end(lo, rec);
         }
+        if (!fused) {
+          panel_apply(lo, cur, k0, bw, 0, k0, false);
+          panel_apply(lo, cur, k0, bw, r1s, nt, false);
+          if (has_next) {
+            lookahead(lo, cur, k1, bw, bw1, 0, k0, false);
+            lookahead(lo, cur, k1, bw, bw1, r1s, nt, false);
+          }
+        }
+        if (ss && has_next) cudaEventRecord(ss->lookahead, lo);
         if (nt > bw) {
           // algorithmic work: the rank-64 bw update of the lower tiles off the
           // panel's rows and columns
           const double rest = (double)(nt - bw) * (nt - bw + 1) / 2.0;
           const double work = 2.0 * 64.0 * 64.0 * 64.0 * bw * rest * b.count;
           if (split_ops) {
-            // U and V split once per panel, then the persistent 3xTF32 update
+            // U split (W was split above, or is split here), then the
+            // persistent 3xTF32 update
             {
               ProfScope ps_(lo, PROF_PANEL);
               SplitJobs jobs{};
               for (int e = 0; e < b.count; ++e) {
-                jobs.j[jobs.count++] = SplitJob{b.e[e].Up[cur], b.e[e].Sp[0], b.e[e].Sp[1]};
-                jobs.j[jobs.count++] = SplitJob{b.e[e].Wp[cur], b.e[e].Sp[2], b.e[e].Sp[3]};
+                jobs.j[jobs.count++] = SplitJob{b.e[e].Up[cur], b.e[e].Sp[0], b.e[e].Sp[1], 0};
+                if (!fused) jobs.j[jobs.count++] = SplitJob{b.e[e].Wp[cur], b.e[e].Sp[2], b.e[e].Sp[3], 0};
               }
               launch_split_tf32_jobs(lo, jobs, (int64_t)n_pad * ldw);
             }

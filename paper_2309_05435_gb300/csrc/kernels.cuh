@@ -315,6 +315,7 @@ struct SplitGemmEntry {
   const float *C0;
   float *C;
   float alpha, beta;
+  int rows = 0, cols = 0;   // this entry's M and N (0: the launch's M and N); full tiles only
 };
 struct SplitGemmBatch {
   SplitGemmEntry e[kMaxBatch];
@@ -329,6 +330,7 @@ void launch_split_tf32(cudaStream_t s, const float *src, float *hi, float *lo, i
 struct SplitJob {
   const float *src;
   float *hi, *lo;
+  int64_t count;   // floats, a multiple of 4 (0: the launch's count)
 };
 struct SplitJobs {
   SplitJob j[2 * kMaxBatch];

@@ -47,6 +47,10 @@ struct Params {
   float alpha[kMaxBatch], beta[kMaxBatch];
   int M, N, K, ldc, lower;
   int tiles_m, tiles_n, tiles_per_matrix, total_tiles;
+  // ragged batches: every entry its own M and N (full tiles), its tiles at
+  // tstart[z] .. tstart[z + 1] - 1 of the static list
+  int ragged, count;
+  int Mz[kMaxBatch], Nz[kMaxBatch], tm_z[kMaxBatch], tn_z[kMaxBatch], tstart[kMaxBatch + 1];
   int32_t *err;
   long long wait_cycles;
   int skip_loads;
@@ -74,6 +78,26 @@ __device__ __forceinline__ void tile_of(const Params &p, int l, int &bm, int &bn
   }
   bm = r;
   bn = l;
+}
+
+// Entry z and tile (bm, bn) of static tile L.
+__device__ __forceinline__ void tile_at(const Params &p, int L, int &z, int &bm, int &bn) {
+  if (!p.ragged) {
+    z = L / p.tiles_per_matrix;
+    tile_of(p, L - z * p.tiles_per_matrix, bm, bn);
+    return;
+  }
+  z = 0;
+  while (z + 1 < p.count && L >= p.tstart[z + 1]) ++z;
+  const int l = L - p.tstart[z];
+  const int tiles_m = p.tm_z[z], tiles_n = p.tn_z[z];
+  const int per_group = GROUP * tiles_n;
+  const int g = l / per_group;
+  const int g0 = g * GROUP;
+  const int rows = min(GROUP, tiles_m - g0);
+  const int w = l - g * per_group;
+  bn = w / rows;
+  bm = g0 + (w - bn * rows);
 }
 
 __device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
@@ -139,9 +163,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm256(const __grid_constant__ P
       long long g = 0;   // K-blocks issued
       bool go = !p.skip_loads;
       for (int L = blockIdx.x; L < p.total_tiles && go; L += gridDim.x) {
-        const int z = L / p.tiles_per_matrix;
-        int bm, bn;
-        tile_of(p, L - z * p.tiles_per_matrix, bm, bn);
+        int z, bm, bn;
+        tile_at(p, L, z, bm, bn);
         for (int kb = 0; kb < nk; ++kb) {
           const int s = (int)(g % STAGES);
           const uint32_t u = (uint32_t)(g / STAGES);
@@ -210,9 +233,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm256(const __grid_constant__ P
       epilogue_sync();
       if (!*ep_ok) break;   // uniform across the four warps: tcgen05.ld is warp-collective
       tc_fence_after();
-      const int z = L / p.tiles_per_matrix;
-      int bm, bn;
-      tile_of(p, L - z * p.tiles_per_matrix, bm, bn);
+      int z, bm, bn;
+      tile_at(p, L, z, bm, bn);
+      const int Mlim = p.ragged ? p.Mz[z] : p.M, Nlim = p.ragged ? p.Nz[z] : p.N;
       const int row = bm * BM + 32 * q + lane;
       float *C = p.C[z];
       const float *C0 = p.C0[z];
@@ -222,10 +245,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm256(const __grid_constant__ P
         uint32_t v[32];
         tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cc * 32), v);
         const int col0 = bn * BN + cc * 32;
-        if (row < p.M && col0 < p.N) {
+        if (row < Mlim && col0 < Nlim) {
           float *crow = C + (int64_t)row * p.ldc + col0;
           const float *c0row = (C0 != nullptr && beta != 0.0f) ? C0 + (int64_t)row * p.ldc + col0 : nullptr;
-          const int ncol = min(32, p.N - col0);
+          const int ncol = min(32, Nlim - col0);
           if (ncol == 32) {
 #pragma unroll
             for (int j = 0; j < 32; j += 4) {
@@ -281,16 +304,31 @@ bool launch_tc_gemm_split(cudaStream_t s, const SplitGemmBatch &b, int M, int N,
   if (!tcw::g_attr_ok) return false;
   tcw::Params p;
   memset(&p, 0, sizeof(p));
+  bool ragged = false;
+  for (int q = 0; q < b.count; ++q) ragged |= b.e[q].rows > 0 || b.e[q].cols > 0;
+  if (ragged && lower) return false;
+  int tiles_sum = 0;
   for (int q = 0; q < b.count; ++q) {
     const SplitGemmEntry &e = b.e[q];
-    if (!tc::encode_2d(&p.tm[q][0], e.Ah, M, K, lda, tc::BM) || !tc::encode_2d(&p.tm[q][1], e.Al, M, K, lda, tc::BM) ||
-        !tc::encode_2d(&p.tm[q][2], e.Bh, N, K, ldb, tcw::BN) || !tc::encode_2d(&p.tm[q][3], e.Bl, N, K, ldb, tcw::BN))
+    const int Mq = e.rows > 0 ? e.rows : M, Nq = e.cols > 0 ? e.cols : N;
+    if (!tc::encode_2d(&p.tm[q][0], e.Ah, Mq, K, lda, tc::BM) ||
+        !tc::encode_2d(&p.tm[q][1], e.Al, Mq, K, lda, tc::BM) ||
+        !tc::encode_2d(&p.tm[q][2], e.Bh, Nq, K, ldb, tcw::BN) || !tc::encode_2d(&p.tm[q][3], e.Bl, Nq, K, ldb, tcw::BN))
       return false;
     p.C[q] = e.C;
     p.C0[q] = e.C0;
     p.alpha[q] = e.alpha;
     p.beta[q] = e.beta;
+    p.Mz[q] = Mq;
+    p.Nz[q] = Nq;
+    p.tm_z[q] = (Mq + tc::BM - 1) / tc::BM;
+    p.tn_z[q] = (Nq + tcw::BN - 1) / tcw::BN;
+    p.tstart[q] = tiles_sum;
+    tiles_sum += p.tm_z[q] * p.tn_z[q];
   }
+  p.tstart[b.count] = tiles_sum;
+  p.ragged = ragged ? 1 : 0;
+  p.count = b.count;
   p.M = M;
   p.N = N;
   p.K = K;
@@ -308,6 +346,10 @@ bool launch_tc_gemm_split(cudaStream_t s, const SplitGemmBatch &b, int M, int N,
   }
   tiles = (double)p.tiles_per_matrix;
   p.total_tiles = p.tiles_per_matrix * b.count;
+  if (ragged) {
+    p.total_tiles = tiles_sum;
+    tiles = (double)tiles_sum / b.count;
+  }
   p.err = err;
   p.wait_cycles = tc::wait_limit();
   p.skip_loads = tc::skip_loads();

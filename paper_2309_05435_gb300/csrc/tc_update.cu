@@ -313,8 +313,9 @@ __global__ void __launch_bounds__(256) k_split_tf32(const float4 *__restrict__ s
 
 // The same split for several arrays of count4 16-byte vectors each (one per
 // grid row): the sweep's U and W of every matrix of a batch in one launch.
-__global__ void __launch_bounds__(256) k_split_tf32_jobs(SplitJobs jobs, int64_t count4) {
+__global__ void __launch_bounds__(256) k_split_tf32_jobs(SplitJobs jobs, int64_t count4_all) {
   const SplitJob jb = jobs.j[blockIdx.y];
+  const int64_t count4 = jb.count > 0 ? jb.count / 4 : count4_all;
   const float4 *__restrict__ src = reinterpret_cast<const float4 *>(jb.src);
   float4 *__restrict__ hi = reinterpret_cast<float4 *>(jb.hi);
   float4 *__restrict__ lo = reinterpret_cast<float4 *>(jb.lo);
