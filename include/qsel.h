@@ -477,13 +477,14 @@ qsel_status qsel_debug_tc_wait(int32_t skip_loads, int64_t wait_cycles);
  * persistent update kernel runs on at most that many CTAs (one per SM), so
  * that SMs stay free for the pivot chain; 0 = one per SM.  update_stages 2
  * or 3: the update's shared-memory ring (3 stages leave no room for the
- * pivot chain's CTAs on the update's SMs); 0 = the default.  By default
+ * pivot chain's CTAs on the update's SMs); 4: the update on 128 x 256
+ * tiles by the persistent split-operand GEMM; 0 = the default.  By default
  * each pivot CTA asks for unused shared memory so that it cannot share an SM
  * with an update CTA, and the update (unless update_ctas says otherwise)
  * leaves one SM per pivot CTA free; shared_pivot non-zero lets the pivot CTAs
  * run beside update CTAs instead.  Process-wide;
  * qsel_debug_sweep_schedule(0, 0, 0, 0) restores the default.  Errors:
- * QSEL_EINVAL for update_ctas < 0 or update_stages not 0, 2 or 3.
+ * QSEL_EINVAL for update_ctas < 0 or update_stages not 0, 2, 3 or 4.
  */
 qsel_status qsel_debug_sweep_schedule(int32_t serial, int32_t update_ctas, int32_t update_stages,
                                       int32_t shared_pivot);

@@ -918,14 +918,30 @@ void spd_inverse(cudaStream_t s, const SweepBatch<T> &b, int n_pad, int32_t *err
               }
               launch_split_tf32_jobs(lo, jobs, (int64_t)n_pad * ldw);
             }
-            UpdateBatch ub{};
-            ub.count = b.count;
-            for (int e = 0; e < b.count; ++e)
-              ub.e[e] = UpdateEntry{b.e[e].Sp[0], b.e[e].Sp[1], b.e[e].Sp[2], b.e[e].Sp[3], b.e[e].A};
             Profiler::Rec rec{PROF_SWEEP, nullptr, nullptr, work};
-            if (g_prof) g_prof->begin(lo, rec);
-            launch_tc_update(lo, ub, n_pad, 64 * bw, ldw, -1.0f, 1.0f, err_flag, upd_ctas);
-            if (g_prof) g_prof->end(lo, rec);
+            Profiler *saved = g_prof;
+            if (saved) saved->begin(lo, rec);
+            bool done = false;
+            if (update_stages() == 4) {
+              // the persistent 128 x 256-tile kernel over the lower tiles (the
+              // tiles' parts above the diagonal are written too; the sweep
+              // reads lower tiles only)
+              g_prof = nullptr;
+              SplitGemmBatch ug{};
+              for (int e = 0; e < b.count; ++e)
+                ug.e[ug.count++] = SplitGemmEntry{b.e[e].Sp[0], b.e[e].Sp[1], b.e[e].Sp[2], b.e[e].Sp[3], b.e[e].A,
+                                                  b.e[e].A, -1.0f, 1.0f};
+              done = launch_tc_gemm_split(lo, ug, n_pad, n_pad, 64 * bw, ldw, ldw, n_pad, true, err_flag, upd_ctas);
+              g_prof = saved;
+            }
+            if (!done) {
+              UpdateBatch ub{};
+              ub.count = b.count;
+              for (int e = 0; e < b.count; ++e)
+                ub.e[e] = UpdateEntry{b.e[e].Sp[0], b.e[e].Sp[1], b.e[e].Sp[2], b.e[e].Sp[3], b.e[e].A};
+              launch_tc_update(lo, ub, n_pad, 64 * bw, ldw, -1.0f, 1.0f, err_flag, upd_ctas);
+            }
+            if (saved) saved->end(lo, rec);
           } else {
             GemmBatch<float> gb{};
             gb.count = b.count;
@@ -1403,7 +1419,8 @@ template void launch_extract<float>(cudaStream_t, const ExtractBatch<float> &, c
 
 extern "C" qsel_status qsel_debug_sweep_schedule(int32_t serial, int32_t update_ctas, int32_t update_stages,
                                                  int32_t shared_pivot) {
-  if (update_ctas < 0 || (update_stages != 0 && update_stages != 2 && update_stages != 3)) return QSEL_EINVAL;
+  if (update_ctas < 0 || (update_stages != 0 && update_stages != 2 && update_stages != 3 && update_stages != 4))
+    return QSEL_EINVAL;
   qsel::g_sweep_serial.store(serial ? 1 : 0);
   qsel::g_update_ctas.store(update_ctas);
   qsel::g_update_stages.store(update_stages == 0 ? 2 : update_stages);

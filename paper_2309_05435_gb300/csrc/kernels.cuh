@@ -322,7 +322,7 @@ struct SplitGemmBatch {
   int count;
 };
 bool launch_tc_gemm_split(cudaStream_t s, const SplitGemmBatch &b, int M, int N, int K, int lda, int ldb, int ldc,
-                          bool lower, int32_t *err);
+                          bool lower, int32_t *err, int max_ctas = 0);
 // hi = rn_tf32(x), lo = rn_tf32(x - hi) elementwise (16-byte aligned arrays).
 void launch_split_tf32(cudaStream_t s, const float *src, float *hi, float *lo, int64_t count);
 // the same for up to 2 kMaxBatch arrays of `count` floats each (count a

@@ -229,10 +229,6 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm256(const __grid_constant__ P
     for (int L = blockIdx.x; L < p.total_tiles; L += gridDim.x, ++i) {
       const int b = i & 1;
       const uint32_t ub = (uint32_t)(i >> 1);
-      if (threadIdx.x == 64) *ep_ok = (mbar_wait(accf_bar(b), ub & 1, abort, p.err, p.wait_cycles) && !*abort) ? 1 : 0;
-      epilogue_sync();
-      if (!*ep_ok) break;   // uniform across the four warps: tcgen05.ld is warp-collective
-      tc_fence_after();
       int z, bm, bn;
       tile_at(p, L, z, bm, bn);
       const int Mlim = p.ragged ? p.Mz[z] : p.M, Nlim = p.ragged ? p.Nz[z] : p.N;
@@ -240,6 +236,42 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm256(const __grid_constant__ P
       float *C = p.C[z];
       const float *C0 = p.C0[z];
       const float alpha = p.alpha[z], beta = p.beta[z];
+      // a whole row segment in range with C0: C0 is read a chunk ahead, the
+      // first chunk while the tile's MMAs still run (it does not depend on them)
+      const bool full = row < Mlim && (bn + 1) * BN <= Nlim && C0 != nullptr && beta != 0.0f;
+      const float *c0row0 = full ? C0 + (int64_t)row * p.ldc + bn * BN : nullptr;
+      float4 cb[2][8];
+      if (full) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cb[0][j] = *reinterpret_cast<const float4 *>(c0row0 + 4 * j);
+      }
+      if (threadIdx.x == 64) *ep_ok = (mbar_wait(accf_bar(b), ub & 1, abort, p.err, p.wait_cycles) && !*abort) ? 1 : 0;
+      epilogue_sync();
+      if (!*ep_ok) break;   // uniform across the four warps: tcgen05.ld is warp-collective
+      tc_fence_after();
+      if (full) {
+        float *crow0 = C + (int64_t)row * p.ldc + bn * BN;
+#pragma unroll
+        for (int cc = 0; cc < BN / 32; ++cc) {
+          if (cc + 1 < BN / 32) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              cb[(cc + 1) & 1][j] = *reinterpret_cast<const float4 *>(c0row0 + (cc + 1) * 32 + 4 * j);
+          }
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + cc * 32), v);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 c = cb[cc & 1][j];
+            float4 o;
+            o.x = fmaf(beta, c.x, alpha * __uint_as_float(v[4 * j]));
+            o.y = fmaf(beta, c.y, alpha * __uint_as_float(v[4 * j + 1]));
+            o.z = fmaf(beta, c.z, alpha * __uint_as_float(v[4 * j + 2]));
+            o.w = fmaf(beta, c.w, alpha * __uint_as_float(v[4 * j + 3]));
+            *reinterpret_cast<float4 *>(crow0 + cc * 32 + 4 * j) = o;
+          }
+        }
+      } else {
 #pragma unroll 1
       for (int cc = 0; cc < BN / 32; ++cc) {
         uint32_t v[32];
@@ -272,6 +304,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm256(const __grid_constant__ P
           }
         }
       }
+      }
       tc_fence_before();
       epilogue_sync();   // every epilogue thread has read the accumulator
       if (threadIdx.x == 64) mbar_arrive(acce_bar(b));
@@ -293,7 +326,7 @@ bool g_attr_ok = false;
 }  // namespace tcw
 
 bool launch_tc_gemm_split(cudaStream_t s, const SplitGemmBatch &b, int M, int N, int K, int lda, int ldb, int ldc,
-                          bool lower, int32_t *err) {
+                          bool lower, int32_t *err, int max_ctas) {
   if (b.count <= 0) return true;
   if (K % tc::BK != 0 || !tc_gemm_available()) return false;
   std::call_once(tcw::g_attr_once, [] {
@@ -355,6 +388,7 @@ bool launch_tc_gemm_split(cudaStream_t s, const SplitGemmBatch &b, int M, int N,
   p.skip_loads = tc::skip_loads();
   int sms = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (max_ctas > 0) sms = std::min(sms, max_ctas);
   const int grid = std::min(p.total_tiles, sms);
   ++g_launch_count;
   Profiler::Rec rec{PROF_GEMM, nullptr, nullptr, 2.0 * tc::BM * tcw::BN * (double)K * tiles * b.count};
