@@ -784,15 +784,19 @@ def run_native(args):
 
 
 def secondary_workload(args, q, w2, stream, dev, net):
-    """The chosen form and the exact one-part form on a second workload (one
-    warm-up and two timed steps), with the accuracy over those seeds."""
+    """The planner's best RBMC plan and the exact one-part form on a second
+    workload (one warm-up and two timed steps), with the accuracy over those
+    seeds and the form the planner picks over part counts including one."""
     nat = Native(q, w2, stream, dev, chain=args.chain)
     a2 = argparse.Namespace(**{**vars(args), "warmup": 1, "steps": 2})
     ch = measure_chosen(a2, nat, net, 1, None, 0, clocks=False)
     t_exact, v_ex, t_ex, _ = nat.exact(q.QSEL_MIXED)
-    return {"workload": w2.name, "s_per_pass": ch["ms_total"] / 2 / 1e3, "n_parts": len(ch["slab_start"]) - 1,
-            "overlap": ch["part_overlap"], "n_samples": ch["k"],
-            "accuracy": _seed_errors(ch["diags"], ch["grads"], v_ex, t_ex),
+    t_rbmc = ch["ms_total"] / 2 / 1e3
+    picked_exact = int(ch["recommendation"]["n_parts"]) == 1
+    return {"workload": w2.name, "picked": "exact one-part" if picked_exact else "rbmc",
+            "picked_s_per_pass": t_exact if picked_exact else t_rbmc,
+            "rbmc": {"s_per_pass": t_rbmc, "n_parts": len(ch["slab_start"]) - 1, "overlap": ch["part_overlap"],
+                     "n_samples": ch["k"], "accuracy": _seed_errors(ch["diags"], ch["grads"], v_ex, t_ex)},
             "exact_one_part_s": t_exact}
 
 
