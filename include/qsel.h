@@ -118,7 +118,14 @@ enum {
   QSEL_MIXED = 1      /* binary32 solves and factorisations, extended-precision
                          pivot tiles (double-float or binary64, see
                          pivot_precision), binary64 refinement residuals and
-                         accumulators                                             */
+                         accumulators.  The dense blocks are binary32, so the
+                         diagonal's accuracy depends on the conditioning of the
+                         pivot blocks in their smallest eigen-directions:
+                         about 2e-4 relative (RMS) on observed models such as
+                         the 96 x 96 bench workload, but tens of percent on an
+                         unobserved prior with cond(Q_s) >= 1e4 (or
+                         QSEL_ENOTSPD); use QSEL_FP64 for weakly observed,
+                         ill-conditioned models                                   */
 };
 
 /*

@@ -200,3 +200,51 @@ def test_tensor_core_wait_timeout_is_reported(q):
     Q = o.precision(c2.model, c2.theta)
     v_ex, _ = o.exact_selinv(Q, o.precision_derivatives(c2.model, c2.theta))
     assert rel(v, v_ex) <= MIXED_DIAG_TOL
+
+
+def test_full_size_mixed_unobserved_closed_form(q):
+    """The bench's size and launch configuration -- 96x96 grid, 256 slabs
+    (n = 2,359,296), mixed form, one part factored from both ends -- on the
+    unobserved prior, whose selected inverse has a closed form at any size
+    (tests.models.unobserved_closed_form, pinned against the oracle's exact
+    selected inverse): every diagonal entry of every slab within the mixed
+    tolerance at this block size (2e-3) and the traces within 5e-4.  kappa = 1
+    keeps Q_s = K C^-1 K well conditioned (cond ~ 80): with no observations
+    the pivot blocks are multiples of Q_s, and at kappa <= 0.3 (cond >= 8e3)
+    binary32 blocks lose its smallest eigen-directions (the FP64 form is the
+    one to use there)."""
+    from tests.models import unobserved_closed_form
+    w = qi.workload("grid96_nt256")
+    kappa = 1.0
+    mesh = w.mesh()
+    th = mk_theta(kappa, w.tau, w.rho)
+    ctx = q.qsel_create(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val,
+                        np.zeros(w.n, np.uint8), w.sigma, th, n_parts=1, overlap=0, n_samples=2,
+                        precision=q.QSEL_MIXED)
+    v, t = ctx.diag_inv(), ctx.trace_grads()
+    ctx.close()
+    v_cf, t_cf = unobserved_closed_form(mesh, w.n_t, kappa, w.tau, w.rho)
+    print(f"full size mixed: diag max {rel(v, v_cf):.2e} traces {rel(np.asarray(t), t_cf):.2e}")
+    assert rel(v, v_cf) <= 2e-3
+    assert rel(np.asarray(t), t_cf) <= 5e-4
+
+
+def test_full_block_fp64_unobserved_closed_form(q):
+    """The FP64 form at the bench's block size (9216 nodes, four slabs) on the
+    unobserved prior at the bench's kappa = 0.1, where cond(Q_s) ~ 6.4e5:
+    diagonal within 1e-7 (about cond(Q_s) x n_s x 2^-53 x 1.5; measured
+    1.2e-8) and traces within 1e-9 of the closed form."""
+    from tests.models import unobserved_closed_form
+    w = qi.workload("grid96_nt256")
+    n_t = 4
+    mesh = w.mesh()
+    th = mk_theta(w.kappa, w.tau, w.rho)
+    ctx = q.qsel_create(w.n_s, n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val,
+                        np.zeros(w.n_s * n_t, np.uint8), w.sigma, th, n_parts=1, overlap=0, n_samples=2,
+                        precision=q.QSEL_FP64)
+    v, t = ctx.diag_inv(), ctx.trace_grads()
+    ctx.close()
+    v_cf, t_cf = unobserved_closed_form(mesh, n_t, w.kappa, w.tau, w.rho)
+    print(f"full block fp64: diag max {rel(v, v_cf):.2e} traces {rel(np.asarray(t), t_cf):.2e}")
+    assert rel(v, v_cf) <= 1e-7
+    assert rel(np.asarray(t), t_cf) <= 1e-9

@@ -113,3 +113,22 @@ def test_precision_derivatives_match_central_differences(th):
 def test_theta_convention():
     kappa, tau, rho = o.theta_to_natural((math.log(0.2), math.log(3.0), math.log(0.95 / 0.05)))
     assert abs(kappa - 0.2) < 1e-15 and abs(tau - 3.0) < 1e-14 and abs(rho - 0.95) < 1e-14
+
+
+@pytest.mark.parametrize("m,n_t,kappa,rho", [(5, 4, 0.7, 0.9), (6, 7, 0.3, 0.98)])
+def test_unobserved_closed_form_matches_exact_selinv(m, n_t, kappa, rho):
+    """The Kronecker closed form used by the full-size GPU tests equals the
+    oracle's dense selected inverse of the unobserved prior, diagonal and all
+    three traces (each term of the closed form is checked by one of them)."""
+    from tests.models import unobserved_closed_form
+    tau = 1.7
+    mesh = qi.grid_mesh(m)
+    model = o.model_from_csr(mesh.n_s, n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val,
+                             np.zeros(mesh.n_s * n_t, np.uint8), 0.5)
+    th = (np.log(kappa), np.log(tau), np.log(rho / (1 - rho)))
+    v_ex, t_ex = o.exact_selinv(o.precision(model, th), o.precision_derivatives(model, th))
+    v_cf, t_cf = unobserved_closed_form(mesh, n_t, kappa, tau, rho)
+    # both sides round at about cond(Q) x 1e-16 (cond ~ 1e6 at rho = 0.98,
+    # kappa = 0.3); a wrong term of the closed form is an O(1) error
+    assert np.max(np.abs(v_cf - v_ex) / np.abs(v_ex)) < 1e-8
+    assert np.max(np.abs(t_cf - np.asarray(t_ex)) / np.abs(np.asarray(t_ex))) < 1e-8
