@@ -255,12 +255,13 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------
-def oracle_sample(w):
+def oracle_sample(w, exact=True):
     """Time the oracle's per-slab dense work at the workload's block size: block
-    Cholesky and Takahashi of a 2-slab chain of Q's blocks.  The full oracle
-    run needs sum_p T_p slab units of factor + Takahashi plus n_t units of
-    factor for its direct sampler; returns (extrapolated seconds, sample
-    seconds, description)."""
+    Cholesky and Takahashi of a 2-slab chain of Q's blocks.  The exact one-part
+    form (the form the GPU line times when the planner picks it) needs n_t slab
+    units of factor + Takahashi; plain RBMC at the workload's partition needs
+    sum_p T_p of them plus n_t units of factor for the oracle's direct sampler.
+    Returns (extrapolated seconds, sample seconds, description)."""
     from oracle import qsel_oracle as o
     mesh, mask = workload_inputs(w)
     model = o.model_from_csr(w.n_s, w.n_t, mesh.c_diag, mesh.g_rowptr, mesh.g_col, mesh.g_val, mask, w.sigma)
@@ -273,11 +274,17 @@ def oracle_sample(w):
     o.block_takahashi(L_diag, L_sub)
     t2 = time.perf_counter()
     chol, tak = (t1 - t0) / 2, (t2 - t1) / 2
+    if exact:
+        est = w.n_t * (chol + tak)
+        desc = (f"oracle block Cholesky + Takahashi of a 2-slab chain of {w.n_s}x{w.n_s} blocks "
+                f"({t2 - t0:.1f} s), extrapolated to the {w.n_t} slabs of the exact one-part selected inversion "
+                "(the form of the GPU line)")
+        return est, t2 - t0, desc
     parts = o.partition(w.n_t, qi.balanced_slab_start(w.n_t, w.n_parts), w.overlap)
     units = sum(p.ext[1] - p.ext[0] for p in parts)
     est = units * (chol + tak) + w.n_t * chol
     desc = (f"oracle block Cholesky + Takahashi of a 2-slab chain of {w.n_s}x{w.n_s} blocks "
-            f"({t2 - t0:.1f} s), extrapolated to {units} subdomain slabs + {w.n_t} sampler slabs; "
+            f"({t2 - t0:.1f} s), extrapolated to {units} subdomain slabs + {w.n_t} sampler slabs of plain RBMC; "
             "excludes the correction solves (lower bound)")
     return est, t2 - t0, desc
 
@@ -716,7 +723,7 @@ def run_native(args):
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:   # the CPU baseline is an N = 1 figure
-        est, spent, desc = oracle_sample(w)
+        est, spent, desc = oracle_sample(w, exact=chosen_exact)
         cpu = {"value": est, "unit": "s", "cores": cpu_cores(), "kind": "oracle", "sample": desc,
                "sample_seconds": spent}
 
@@ -821,7 +828,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": spent / args.steps * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded grid FEM mesh)",
-        "config": {"workload": w.name, "form": "CPU FP64 oracle"},
+        "config": {"workload": w.name, "form": "CPU FP64 oracle: exact one-part selected inversion "
+                   "(block Cholesky + Takahashi), the form the planner picks on this workload"},
         "cpu_baseline": {"value": v, "unit": "s", "kind": "oracle", "cores": cpu_cores(), "sample": desc},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
