@@ -504,7 +504,15 @@ def profile_pass(nat, ch, exact=False):
     return st
 
 
-def roofline_of(st, w, hbm_peak, hbm_src, tf32_peak, tf32_src):
+# DRAM traffic of the Takahashi products on 9216-node blocks, two matrices per
+# launch (the exact one-part form factored from both ends): dram__bytes_read.sum
+# + dram__bytes_write.sum of one ncu capture (`bench.py --exact-pass
+# grid96_nt8`, a full-size launch of this kernel), the mean of the Y launch
+# (18.88 GB) and the Sigma launch (11.24 GB)
+TAKAHASHI_TRAFFIC_9216_X2 = 15.06e9
+
+
+def roofline_of(st, w, hbm_peak, hbm_src, tf32_peak, tf32_src, exact=False):
     """Dominant kernel class of one profiled pass (event time), with its
     algorithmic work per launch over its average event-timed launch."""
     from paper_2309_05435_gb300 import qsel as q
@@ -535,8 +543,15 @@ def roofline_of(st, w, hbm_peak, hbm_src, tf32_peak, tf32_src):
         ach = cwork[dom] / (cms[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "peak_source": "FP32 CUDA-core rate from unit counts (152 x 128 x 2 x 2.07 GHz)"}
+    traffic = None
+    if exact and name == "gemm" and w.n_s == 9216:
+        traffic = {"bytes_per_launch": TAKAHASHI_TRAFFIC_9216_X2,
+                   "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of full-size launches "
+                             "(bench.py --exact-pass grid96_nt8, two 9216^2 matrices per launch): about 5.6x the "
+                             "operand and output bytes, the right operand re-read once per group of 8 tile rows; "
+                             "1.7 TB/s at the tensor-bound rate"}
     return {"kernel": desc[name], "class": name, **roof, "frac": roof["achieved"] / roof["peak"],
-            "traffic": None, "launches": int(cl[dom]), "avg_launch_ms": cms[dom] / max(1, cl[dom]),
+            "traffic": traffic, "launches": int(cl[dom]), "avg_launch_ms": cms[dom] / max(1, cl[dom]),
             "timing": "per-launch CUDA events on the launching streams in a separate profiled pass of the "
                       "chosen form (the timed steps run without per-launch events)",
             "kernel_classes_ms_per_pass": {classes[i]: cms[i] for i in range(len(classes))}}
@@ -681,7 +696,7 @@ def run_native(args):
     hbm_peak, hbm_src = measured_peaks()
     tf32_peak, tf32_src = tf32_peak_tflops()
     st_prof = profile_pass(nat, ch, exact=chosen_exact)
-    roof = roofline_of(st_prof, w, hbm_peak, hbm_src, tf32_peak, tf32_src)
+    roof = roofline_of(st_prof, w, hbm_peak, hbm_src, tf32_peak, tf32_src, exact=chosen_exact)
     roof_rbmc = None
     if chosen_exact:
         roof_rbmc = roofline_of(profile_pass(nat, ch), w, hbm_peak, hbm_src, tf32_peak, tf32_src)
