@@ -543,15 +543,16 @@ def roofline_of(st, w, hbm_peak, hbm_src, tf32_peak, tf32_src, exact=False):
         ach = cwork[dom] / (cms[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "peak_source": "FP32 CUDA-core rate from unit counts (152 x 128 x 2 x 2.07 GHz)"}
-    traffic = None
+    traffic, traffic_src = None, "not captured for this kernel at this size"
     if exact and name == "gemm" and w.n_s == 9216:
-        traffic = {"bytes_per_launch": TAKAHASHI_TRAFFIC_9216_X2,
-                   "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of full-size launches "
-                             "(bench.py --exact-pass grid96_nt8, two 9216^2 matrices per launch): about 5.6x the "
-                             "operand and output bytes, the right operand re-read once per group of 8 tile rows; "
-                             "1.7 TB/s at the tensor-bound rate"}
+        traffic = TAKAHASHI_TRAFFIC_9216_X2
+        traffic_src = ("bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum of full-size launches "
+                       "(bench.py --exact-pass grid96_nt8, two 9216^2 matrices per launch), mean of a Y and a Sigma "
+                       "launch; about 5.6x the operand and output bytes (the right operand re-read once per group "
+                       "of 8 tile rows), 1.7 TB/s at the tensor-bound rate")
     return {"kernel": desc[name], "class": name, **roof, "frac": roof["achieved"] / roof["peak"],
-            "traffic": traffic, "launches": int(cl[dom]), "avg_launch_ms": cms[dom] / max(1, cl[dom]),
+            "traffic": traffic, "traffic_source": traffic_src, "launches": int(cl[dom]),
+            "avg_launch_ms": cms[dom] / max(1, cl[dom]),
             "timing": "per-launch CUDA events on the launching streams in a separate profiled pass of the "
                       "chosen form (the timed steps run without per-launch events)",
             "kernel_classes_ms_per_pass": {classes[i]: cms[i] for i in range(len(classes))}}
