@@ -1110,7 +1110,8 @@ template void launch_sp_rowgather<double, float>(cudaStream_t, const SpBatch<dou
 // its own shared slots [s * 256 + t] (no sharing, no block barrier) and reuses
 // it for every row.  Shared memory: max_width * 256 * (4 + sizeof(T)) bytes.
 // ---------------------------------------------------------------------------
-constexpr int kGatherRows = 16;
+constexpr int kGatherRows = 64;   // rows per block (a multiple of kGatherRowBlock)
+constexpr int kGatherRowBlock = 4; // rows per thread at a time: one pattern read, four FMAs
 
 template <typename T>
 __device__ __forceinline__ int stage_col_pattern(const SellPattern &pat, const double *__restrict__ val, int l,
@@ -1145,17 +1146,31 @@ __global__ void __launch_bounds__(256) k_sp_colgather(SpBatch<T, T> bt, SellPatt
   const int w = stage_col_pattern(pat, e.val, l, n_s, s_col, s_val);
   const T alpha = (T)(e.alpha * (e.alpha_ptr ? *e.alpha_ptr : 1.0));
   const bool add_c = e.C != nullptr && e.beta != 0.0;
-  const int r1 = min(n_pad, (int)(blockIdx.y + 1) * kGatherRows);
-  for (int r = blockIdx.y * kGatherRows; r < r1; ++r) {
-    T out = T(0);
-    if (r < n_s && l < n_s) {
+  const int r0 = blockIdx.y * kGatherRows, r1 = min(n_pad, r0 + kGatherRows);
+  for (int r = r0; r < r1; r += kGatherRowBlock) {
+    // kGatherRowBlock rows per pattern entry read (n_pad is a multiple of 64)
+    T acc[kGatherRowBlock];
+#pragma unroll
+    for (int q = 0; q < kGatherRowBlock; ++q) acc[q] = T(0);
+    if (l < n_s && r < n_s) {
       const T *Br = e.B + (int64_t)r * n_pad;
-      T acc = T(0);
-      for (int s = 0; s < w; ++s) acc = fma(Br[s_col[s * 256 + threadIdx.x]], s_val[s * 256 + threadIdx.x], acc);
-      out = alpha * acc;
-      if (add_c) out = fma((T)e.beta, e.C[(int64_t)r * n_pad + l], out);
+      for (int s = 0; s < w; ++s) {
+        const int j = s_col[s * 256 + threadIdx.x];
+        const T v = s_val[s * 256 + threadIdx.x];
+#pragma unroll
+        for (int q = 0; q < kGatherRowBlock; ++q) acc[q] = fma(Br[(int64_t)q * n_pad + j], v, acc[q]);
+      }
     }
-    e.Out[(int64_t)r * n_pad + l] = out;
+#pragma unroll
+    for (int q = 0; q < kGatherRowBlock; ++q) {
+      const int rq = r + q;
+      T out = T(0);
+      if (rq < n_s && l < n_s) {
+        out = alpha * acc[q];
+        if (add_c) out = fma((T)e.beta, e.C[(int64_t)rq * n_pad + l], out);
+      }
+      e.Out[(int64_t)rq * n_pad + l] = out;
+    }
   }
 }
 
@@ -1185,7 +1200,18 @@ __global__ void __launch_bounds__(256) k_diag64_rows(DiagRowBatch<T> bt, int n_s
   const T *Pi = e.P + (int64_t)i * n_pad;
   const T *Ri = e.R + (int64_t)i * n_pad;
   double acc = 0.0;
-  for (int l = lane; l < n_s; l += 32) acc = fma((double)Pi[l], (double)Ri[l], acc);
+  if constexpr (std::is_same<T, float>::value) {
+    // 16-byte loads; four products summed in binary32 (about 4 units of
+    // roundoff of that partial), the partials in double: a quarter of the
+    // FP64 operations.  Entries past n_s are zero in both operands.
+    for (int l = 4 * lane; l < n_pad; l += 128) {
+      const float4 p = *reinterpret_cast<const float4 *>(Pi + l);
+      const float4 r = *reinterpret_cast<const float4 *>(Ri + l);
+      acc += (double)fmaf(p.w, r.w, fmaf(p.z, r.z, fmaf(p.y, r.y, p.x * r.x)));
+    }
+  } else {
+    for (int l = lane; l < n_s; l += 32) acc = fma((double)Pi[l], (double)Ri[l], acc);
+  }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0) e.diag_out[i] = (double)e.D0[(int64_t)i * n_pad + i] + acc;
 }
@@ -1243,13 +1269,30 @@ __global__ void __launch_bounds__(256) k_schur_assemble(SchurBatch<T> bt, SellPa
     }
     return;
   }
-  for (int r = r0; r < r1; ++r) {
-    T out;
-    if (r < n_s && l < n_s)
-      out = e.W ? neg_c * schur_sum(e.W + (int64_t)r * n_pad, w, s_col, s_val) : T(0);
-    else
-      out = (r == l) ? T(1) : T(0);
-    e.D[(int64_t)r * n_pad + l] = out;
+  for (int r = r0; r < r1; r += kGatherRowBlock) {
+    // kGatherRowBlock rows per pattern entry read (n_pad is a multiple of 64)
+    T acc[kGatherRowBlock];
+#pragma unroll
+    for (int q = 0; q < kGatherRowBlock; ++q) acc[q] = T(0);
+    if (e.W && l < n_s && r < n_s) {
+      const T *Wr = e.W + (int64_t)r * n_pad;
+      for (int s = 0; s < w; ++s) {
+        const int j = s_col[s * 256 + threadIdx.x];
+        const T v = s_val[s * 256 + threadIdx.x];
+#pragma unroll
+        for (int q = 0; q < kGatherRowBlock; ++q) acc[q] = fma(Wr[(int64_t)q * n_pad + j], v, acc[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kGatherRowBlock; ++q) {
+      const int rq = r + q;
+      T out;
+      if (rq < n_s && l < n_s)
+        out = e.W ? neg_c * acc[q] : T(0);
+      else
+        out = (rq == l) ? T(1) : T(0);
+      e.D[(int64_t)rq * n_pad + l] = out;
+    }
   }
   if (l >= n_s) return;
   // entries on the pattern of column l within this block's rows, in double.
