@@ -508,8 +508,8 @@ def profile_pass(nat, ch, exact=False):
 # launch (the exact one-part form factored from both ends): dram__bytes_read.sum
 # + dram__bytes_write.sum of one ncu capture (`bench.py --exact-pass
 # grid96_nt8`, a full-size launch of this kernel), the mean of the Y launch
-# (18.88 GB) and the Sigma launch (11.24 GB)
-TAKAHASHI_TRAFFIC_9216_X2 = 15.06e9
+# (14.03 GB) and the Sigma launch (11.58 GB)
+TAKAHASHI_TRAFFIC_9216_X2 = 12.81e9
 
 
 def roofline_of(st, w, hbm_peak, hbm_src, tf32_peak, tf32_src, exact=False):
@@ -548,8 +548,8 @@ def roofline_of(st, w, hbm_peak, hbm_src, tf32_peak, tf32_src, exact=False):
         traffic = TAKAHASHI_TRAFFIC_9216_X2
         traffic_src = ("bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum of full-size launches "
                        "(bench.py --exact-pass grid96_nt8, two 9216^2 matrices per launch), mean of a Y and a Sigma "
-                       "launch; about 5.6x the operand and output bytes (the right operand re-read once per group "
-                       "of 8 tile rows), 1.7 TB/s at the tensor-bound rate")
+                       "launch; about 3.8x the operand and output bytes (the right operand re-read once per group "
+                       "of 16 tile rows), 1.3-2.1 TB/s at the tensor-bound rate")
     return {"kernel": desc[name], "class": name, **roof, "frac": roof["achieved"] / roof["peak"],
             "traffic": traffic, "traffic_source": traffic_src, "launches": int(cl[dom]),
             "avg_launch_ms": cms[dom] / max(1, cl[dom]),

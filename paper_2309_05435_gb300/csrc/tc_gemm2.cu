@@ -33,7 +33,7 @@ using namespace tc;
 
 constexpr int BN = 256;
 constexpr int STAGES = 2;
-constexpr int GROUP = 8;
+constexpr int GROUP = 16;
 constexpr int TA = BM * BK * 4;              // 16 KiB
 constexpr int TB = BN * BK * 4;              // 32 KiB
 constexpr int STAGE_BYTES = 2 * TA + 2 * TB;  // A_hi, A_lo, B_hi, B_lo
