@@ -248,3 +248,29 @@ def test_full_block_fp64_unobserved_closed_form(q):
     print(f"full block fp64: diag max {rel(v, v_cf):.2e} traces {rel(np.asarray(t), t_cf):.2e}")
     assert rel(v, v_cf) <= 1e-7
     assert rel(np.asarray(t), t_cf) <= 1e-9
+
+
+def test_sweep_schedules_give_identical_results(q):
+    """The sweep's scheduling hook changes only where and when its kernels run:
+    the update after the pivot chain on one stream, a capped update grid, a
+    three-stage update ring, the update on 128 x 256 tiles and pivot CTAs
+    beside update CTAs all give the default's results bit for bit (three
+    sweep panels per pivot block, the last ragged; two matrices per launch)."""
+    def run():
+        c = Big(q, "panels24_p3_l2_k256", precision=q.QSEL_MIXED, parts=1, overlap=0)
+        v, t = c.ctx.diag_inv(), np.asarray(c.ctx.trace_grads())
+        c.ctx.close()
+        return v, t
+    v0, t0 = run()
+    try:
+        for args in [(True, 0, 0, False), (False, 100, 0, False), (False, 0, 3, False), (False, 0, 4, False),
+                     (False, 0, 0, True)]:
+            q.qsel_debug_sweep_schedule(*args)
+            v, t = run()
+            assert np.array_equal(v, v0) and np.array_equal(t, t0), args
+    finally:
+        q.qsel_debug_sweep_schedule(False)
+    with pytest.raises(q.QselError):
+        q.qsel_debug_sweep_schedule(False, -1)
+    with pytest.raises(q.QselError):
+        q.qsel_debug_sweep_schedule(False, 0, 5)
