@@ -24,3 +24,18 @@ def test_seed_errors_definition():
     assert abs(e["eps_diag"] - 0.01) < 1e-12
     assert all(abs(x - 0.02) < 1e-12 for x in e["eps_traces"])
     assert e["seeds"] == 2 and not e["meets_1pct"]
+
+
+def test_oracle_sample_exact_form_and_half_blocks():
+    """The CPU baseline's sample: the exact one-part form extrapolates the
+    2-slab chain to n_t slabs, plain RBMC to its parts' slabs plus the direct
+    sampler; the half-block sample takes the leading half of every block and
+    states its cubic scaling."""
+    import qsel_inputs as qi
+    w = qi.workload("grid16_nt8")
+    est_ex, spent, desc = bench.oracle_sample(w)
+    assert est_ex > 0 and spent > 0 and f"the {w.n_t} slabs of the exact one-part" in desc
+    est_rb, _, desc_rb = bench.oracle_sample(w, exact=False)
+    assert "plain RBMC" in desc_rb and est_rb > 0
+    est_h, _, desc_h = bench.oracle_sample(w, frac=0.5)
+    assert est_h > 0 and "leading 128x128 of every block" in desc_h and "x 8.0" in desc_h
